@@ -1,0 +1,305 @@
+#!/usr/bin/env python
+"""Benchmark of the GLM log-likelihood + gradient hot path: neuron*bins/s on the N = 1000 neuron,
+1800 s (1.8M bins of 1 ms) balanced-network workload.
+
+One step = the whole hot path once: filter scan and spike term from the device-resident spikes
+(steps a0-a2), then U = b + W X with the fused link epilogue, the gradient product and the FP64
+reductions (a3-a5, a7).  `value` times K such steps with the inputs already in HBM; `e2e` times the
+same through the public API from host buffers (spike upload and validation, W/b upload, L and G read
+back).  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec f32|bf16|f16] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "glm_n1000_t1800s"
+METRIC = "GLM loglik+grad neuron*bins/s at N=1000"
+UNIT = "neuron*bins/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default=None)
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def cpu_baseline(w, cores: int, n_rows: int | None = None, t_frac: float = 0.25):
+    """The FP64 oracle as it stands, on a bounded sample: `cores` rows over the first t_frac of the bins."""
+    import numpy as np
+    import oracle
+    n, T = w["n"], w["n_bins"]
+    Ts = max(1, int(T * t_frac))
+    offs, bins = w["offs"], w["bins"]
+    # restrict the recording to its first Ts bins (a valid, shorter recording)
+    keep = bins < Ts
+    counts = np.array([keep[offs[i]:offs[i + 1]].sum() for i in range(n)], dtype=np.int64)
+    offs_s = np.zeros(n + 1, dtype=np.int64)
+    offs_s[1:] = np.cumsum(counts)
+    bins_s = bins[keep]
+    rows = np.linspace(0, n - 1, n_rows or cores).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.eval_rows(offs_s, bins_s, Ts, w["dt"], w["tau"], w["W_true"], w["b_true"], rows, threads=cores)
+    el = time.perf_counter() - t0
+    units = rows.size * Ts
+    return {"value": units / el, "unit": UNIT, "cores": int(min(cores, rows.size)), "kind": "oracle",
+            "sample": f"{rows.size} rows x first {Ts} of {T} bins (FP64 oracle, log-likelihood + gradient)",
+            "seconds": el}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    import synth
+    w = synth.make_workload(args.workload)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        cpu_baseline(w, cores, t_frac=0.05)
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        r = cpu_baseline(w, cores, t_frac=0.05)
+        vals.append(r["value"])
+        secs += r["seconds"]
+    value = args.steps / sum(1.0 / v for v in vals)  # units per second over all steps
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": w["n"], "n_bins": w["n_bins"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    import paper_1502_04993_gb300 as glm
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    device = local if ws > 1 else 0
+    torch.cuda.set_device(device)
+    prec = args.prec or glm.available_precisions()[-1]
+    cfg = dict(synth.WORKLOADS[args.workload])
+    w = synth.make_workload(args.workload, seed=cfg["seed"] + rank)  # independent recording per rank
+    n, T = w["n"], w["n_bins"]
+    stream = torch.cuda.current_stream(device)
+    ctx = glm.GLM(device, stream=stream)
+    ctx.set_problem(w["offs"], w["bins"], T, w["dt"], w["tau"], prec=prec)
+    W = torch.from_numpy(w["W_true"].astype(np.float32)).cuda(device)
+    b = torch.from_numpy(w["b_true"].astype(np.float32)).cuda(device)
+    out = {"L_rows": torch.empty(n, dtype=torch.float64, device=device),
+           "G": torch.empty((n, n), dtype=torch.float64, device=device),
+           "gb": torch.empty(n, dtype=torch.float64, device=device)}
+
+    def step():
+        ctx.prepare()
+        ctx.loglik_grad(W, b, total=False, out=out)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(device)
+    if ws > 1:
+        dist.barrier()
+    clocks = Clocks(device)
+    clocks.start()
+    ctx.profile(True)
+    launches0 = ctx.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(device)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(device)
+    ms = ev0.elapsed_time(ev1)
+    launches = ctx.launch_count() - launches0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    clk = clocks.stop()
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    units = n * T * args.steps * ws
+    value = units / (ms / 1000.0)
+
+    # ---- end to end through the public API from host buffers ----
+    k2 = args.e2e_steps or max(1, min(args.steps, 5))
+    W_h = torch.from_numpy(w["W_true"].astype(np.float32)).pin_memory()
+    b_h = torch.from_numpy(w["b_true"].astype(np.float32)).pin_memory()
+    G_h = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize(device)
+    if ws > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(k2):
+        ctx.set_problem(w["offs"], w["bins"], T, w["dt"], w["tau"], prec=prec)
+        Wd = W_h.to(device, non_blocking=True)
+        bd = b_h.to(device, non_blocking=True)
+        r = ctx.loglik_grad(Wd, bd, total=True, out=out)
+        G_h.copy_(r["G"], non_blocking=True)
+        torch.cuda.synchronize(device)
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = w["offs"].nbytes + w["bins"].nbytes + W_h.numel() * 4 + b_h.numel() * 4
+    d2h = G_h.numel() * 8 + 8
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel group ----
+    peaks, peak_src = measured_peaks()
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (cnt, tot_ms) = top
+    per_launch_s = tot_ms / cnt / 1000.0
+    if name in ("u_epilogue", "grad"):
+        flops = 2.0 * n * n * T * (2 if (name == "u_epilogue" and prec != "f32") else 1)
+        if prec == "f32":
+            # FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x max SM clock
+            sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+            peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+            roof = {"bound": "alu", "achieved": flops / per_launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+        else:
+            peak = peaks["bf16_tflops"]
+            roof = {"bound": "tensor", "achieved": flops / per_launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                    "peak_source": f"{peak_src} bf16_tflops (burst)"}
+    else:
+        esz = 4 if prec == "f32" else 2
+        nbytes = {"filter_scan": n * T * esz * (1 if prec == "f32" else 2) + w["bins"].nbytes,
+                  "spike_term": w["bins"].nbytes * (n // 8 + 1)}.get(name, n * T * esz)
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": nbytes / per_launch_s / 1e9, "peak": peak, "unit": "GB/s",
+                "peak_source": f"{peak_src} hbm_gbs"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = name
+    roof["ms_per_launch"] = tot_ms / cnt
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": prec, "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "n_bins": T, "precision": prec,
+                   "l2": "inputs larger than L2 (filtered trains %.1f GB)" % (n * T * (4 if prec == "f32" else 4) / 1e9),
+                   "parallelism": f"replicas x{ws}: one independent recording per GPU"},
+        "e2e": {"value": n * T * k2 * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "steps": k2},
+        "gpu_launches": int(launches),
+        "kernel_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
+        "roofline": roof,
+        "clocks": clk,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, os.cpu_count() or 1)
+        line["cpu_baseline"].pop("seconds", None)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

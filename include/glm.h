@@ -1,0 +1,157 @@
+/*
+ * glm.h - C ABI of libglm: maximum-likelihood reconstruction of recurrent
+ * synaptic connectivity from spike trains with a point-process generalised
+ * linear model (Zaytsev, Morrison & Deger, "Reconstruction of recurrent
+ * synaptic connectivity of thousands of neurons from simulated spiking
+ * activity"), evaluated on a time grid on one NVIDIA GB300 (sm_103a).
+ *
+ * Problem statement (Sec. 2.1-2.3).  N neurons are recorded for T bins of
+ * width dt seconds; S_i[t] in {0, 1} says whether neuron i spiked in bin t
+ * (Sec. 2.1: spike trains {t_ik} on [T0, T1]).  With a = exp(-dt / tau):
+ *   X_j[0] = 0,  X_j[t] = a X_j[t-1] + S_j[t-1]            filtered trains, Eq. 13
+ *   U_i[t] = b_i + sum_j W_ij X_j[t]                       potential, Eq. 3
+ *   L_i    = sum_t S_i[t] U_i[t] - dt sum_t exp(U_i[t])    log-likelihood, Eq. 2/5/7
+ *   dL_i/dW_ij = sum_t R_i[t] X_j[t],  dL_i/db_i = sum_t R_i[t],
+ *   R_i[t] = S_i[t] - dt exp(U_i[t])                       gradient, Eq. 11-12
+ * b_i is the paper's baseline J_i0 (base rate c_i = exp(b_i) in 1/s, Eq. 6),
+ * W_ij its J_ij (weight of the connection j -> i, gain du = 1), tau the
+ * membrane time constant of the exponential kernel (Sec. 2.2).  A spike
+ * acts from the next bin on: every connection, the self-connection included,
+ * carries a delay of one bin (the paper's d_s = dt, Sec. 2.4 and 3.1).
+ * L = sum_i L_i (Eq. 1) and every row is an independent concave problem
+ * (Sec. 2.2, App. A).
+ *
+ * Conventions for every call:
+ *   - Return value: GLM_OK (0) on success, a negative GLM_ERR_* on error, a
+ *     positive GLM_STATUS_* for a finished call with a noteworthy outcome.
+ *     A call that fails validation changes nothing.  glm_strerror() names
+ *     every code; glm_last_error() gives a message for the context's last
+ *     failure.
+ *   - Ownership: the caller owns every buffer it passes and the library
+ *     never frees or keeps one.  The context owns its device workspace
+ *     (spikes, filtered trains, spike term, partial sums) and frees it in
+ *     glm_destroy().
+ *   - Memory kinds: parameters named *_dev are device pointers on the
+ *     context's device, *_host are host pointers.  Matrices are row-major.
+ *   - Streams: work is queued on the stream given to glm_create() (NULL =
+ *     the legacy default stream).  A call that writes a *_host output
+ *     synchronises that stream before returning; other calls may return
+ *     before the device work is finished.
+ *   - Thread safety: a context must not be used from two threads at once;
+ *     different contexts are independent.
+ */
+#ifndef GLM_H
+#define GLM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define GLM_OK 0
+#define GLM_ERR_INVALID_ARG (-1)        /* null pointer, non-positive size, dt/tau not finite and > 0, ... */
+#define GLM_ERR_UNSORTED_SPIKES (-2)    /* bins of a row not strictly increasing (two spikes in one bin) */
+#define GLM_ERR_SPIKE_OUT_OF_RANGE (-3) /* a bin outside [0, n_bins), or offsets not a valid CSR */
+#define GLM_ERR_OOM (-4)                /* device allocation failed or the workspace cap was exceeded */
+#define GLM_ERR_CUDA (-5)               /* a CUDA runtime/driver call failed */
+#define GLM_ERR_NONFINITE (-6)          /* non-finite W or b, or exp(U) overflowed */
+#define GLM_ERR_TIMEOUT (-7)            /* a bounded device-side wait gave up */
+#define GLM_ERR_UNSUPPORTED_ARCH (-8)   /* a tensor-core precision was asked for on a GPU other than sm_103 */
+#define GLM_ERR_NO_PROBLEM (-9)         /* the call needs glm_set_problem() first */
+#define GLM_ERR_UNSUPPORTED (-10)       /* valid request outside what this build implements */
+
+/* ---- precision of the contractions U = b + W X and G = R X^T ----
+ * GLM_PREC_F32:  the plain FP32 form.  X and exp-rates stored in FP32,
+ *                SIMT FP32 products on CUDA cores, FP64 sums across tiles.
+ * GLM_PREC_BF16: tcgen05 tensor cores.  X and the rates dt*exp(U) stored in
+ *                BF16; W split into hi + lo BF16 parts so that
+ *                W_hi X + W_lo X keeps W to ~16 significant bits; FP32
+ *                accumulation in tensor memory; FP64 sums across tiles.
+ * GLM_PREC_F16:  as GLM_PREC_BF16 with IEEE half instead of BF16.
+ * In every precision the spike term sum_t S_i[t] X_j[t] (Eq. 12, the part
+ * that does not depend on W, computed once per problem as Sec. 2.3.3 and
+ * 2.6.1 advise) is summed from FP32 X in a double-float (hi + lo) pair. */
+typedef enum { GLM_PREC_F32 = 0, GLM_PREC_BF16 = 1, GLM_PREC_F16 = 2 } glm_prec_t;
+
+/* element types for glm_filter outputs */
+typedef enum { GLM_DTYPE_F32 = 0, GLM_DTYPE_BF16 = 1, GLM_DTYPE_F16 = 2 } glm_dtype_t;
+
+typedef struct glm_ctx glm_ctx;
+
+/* Version of the library as major * 10000 + minor * 100 + patch. */
+int glm_version(void);
+
+/* Static name of a status code; never NULL. */
+const char* glm_strerror(int code);
+
+/* Message describing the last error raised on ctx (empty if none); valid until the next call on ctx. */
+const char* glm_last_error(const glm_ctx* ctx);
+
+/* Create a context on CUDA device `device`.
+ *   workspace_cap_bytes: upper bound on the device memory the context may hold (0 = no bound);
+ *                        exceeding it makes the call that needed more return GLM_ERR_OOM.
+ *   cuda_stream:         a cudaStream_t on that device, or NULL for the legacy default stream.
+ * On success *out receives the context.  Errors: INVALID_ARG, CUDA. */
+int glm_create(glm_ctx** out, int device, size_t workspace_cap_bytes, void* cuda_stream);
+
+/* Release the context and all device memory it owns.  NULL is ignored. */
+void glm_destroy(glm_ctx* ctx);
+
+/* Set the recording (Sec. 2.1) and the model constants, then prepare the per-problem caches
+ * (steps a0-a2: filtered trains X for the chosen precision and the spike term).
+ *   n, n_bins:  neurons and bins, n >= 1, 1 <= n_bins < 2^31.
+ *   dt, tau:    bin width and kernel time constant in seconds, both finite and > 0.
+ *   offs_host:  int64[n + 1] CSR offsets, offs[0] = 0, non-decreasing.
+ *   bins_host:  int32[offs[n]] spike bins; row i is bins[offs[i] .. offs[i+1]), strictly increasing,
+ *               each in [0, n_bins).  At most one spike per neuron and bin.
+ *   prec:       precision of the contractions (glm_prec_t).
+ * The spikes are copied to the device; the host arrays may be freed on return.  Replaces any previous
+ * problem.  Errors: INVALID_ARG, UNSORTED_SPIKES, SPIKE_OUT_OF_RANGE, OOM, CUDA, UNSUPPORTED_ARCH. */
+int glm_set_problem(glm_ctx* ctx, int32_t n, int64_t n_bins, double dt, double tau, const int64_t* offs_host,
+                    const int32_t* bins_host, glm_prec_t prec);
+
+/* Recompute the per-problem caches (filter scan, spike term) from the device-resident spikes, for a new
+ * tau (tau > 0) or, with tau <= 0, the current one.  Errors: NO_PROBLEM, INVALID_ARG, CUDA. */
+int glm_prepare(glm_ctx* ctx, double tau);
+
+/* Write the filtered trains X[:, t0 : t0 + t_len] (Eq. 13) of the current problem into X_dev, row-major
+ * with leading dimension ldx elements (ldx >= t_len), element type dtype.  Computed afresh by the scan
+ * kernel.  Errors: NO_PROBLEM, INVALID_ARG (range outside [0, n_bins), ldx < t_len), CUDA. */
+int glm_filter(glm_ctx* ctx, int64_t t0, int64_t t_len, void* X_dev, int64_t ldx, glm_dtype_t dtype);
+
+/* Copy the spike term C_ij = sum_t S_i[t] X_j[t] (n x n, FP64, row-major) and the spike counts
+ * q_i (FP64) of the current problem into device buffers; either may be NULL.
+ * Errors: NO_PROBLEM, CUDA. */
+int glm_spike_term(glm_ctx* ctx, double* C_dev, double* q_dev);
+
+/* Log-likelihood and gradient of the current problem at (W, b) (steps a3-a5, a7):
+ *   W_dev: float[n * n], b_dev: float[n]  (inputs, device)
+ *   L_rows_dev:   double[n]      L_i                    (or NULL)
+ *   L_total_host: double         L = sum_i L_i          (or NULL; synchronises)
+ *   G_dev:        double[n * n]  dL_i / dW_ij           (or NULL: the gradient product is skipped)
+ *   gb_dev:       double[n]      dL_i / db_i            (or NULL)
+ * Errors: NO_PROBLEM, INVALID_ARG, NONFINITE (exp(U) overflowed; outputs are then undefined), CUDA,
+ * TIMEOUT. */
+int glm_loglik_grad(glm_ctx* ctx, const float* W_dev, const float* b_dev, double* L_rows_dev,
+                    double* L_total_host, double* G_dev, double* gb_dev);
+
+/* ---- tracing ----
+ * While profiling is enabled, every kernel group the context launches (filter_scan, carry, spike_term,
+ * u_epilogue, grad, reduce, ...) is bracketed by CUDA events recorded on the context's stream.
+ * glm_profile_read() synchronises that stream and writes, for up to max_entries groups, the group name
+ * (NUL-terminated, 32 bytes per entry in names), the number of launches and the summed device time in
+ * milliseconds since profiling was last enabled; it returns the number of entries written (>= 0) or a
+ * negative GLM_ERR_*.  glm_profile_enable(ctx, 1) also resets the totals. */
+int glm_profile_enable(glm_ctx* ctx, int enable);
+int glm_profile_read(glm_ctx* ctx, int max_entries, char* names, int64_t* launches, double* ms);
+
+/* Number of CUDA kernels the context has launched since it was created (a running counter). */
+int64_t glm_launch_count(const glm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GLM_H */

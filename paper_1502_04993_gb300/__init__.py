@@ -1,0 +1,199 @@
+"""GB300 (sm_103a) maximum-likelihood reconstruction of recurrent synaptic connectivity from spike
+trains with the point-process GLM of Zaytsev, Morrison & Deger.
+
+Thin ctypes binding over ``libglm.so`` (C ABI in ``include/glm.h``).  Every step of the computation
+runs in the library's CUDA kernels; this module only marshals arguments.  PyTorch supplies device
+memory and streams.  There is no CPU fallback: importing the binding without the built library, or
+using it without a CUDA device, raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libglm.so")
+
+GLM_OK = 0
+ERRORS = {
+    -1: "GLM_ERR_INVALID_ARG", -2: "GLM_ERR_UNSORTED_SPIKES", -3: "GLM_ERR_SPIKE_OUT_OF_RANGE", -4: "GLM_ERR_OOM",
+    -5: "GLM_ERR_CUDA", -6: "GLM_ERR_NONFINITE", -7: "GLM_ERR_TIMEOUT", -8: "GLM_ERR_UNSUPPORTED_ARCH",
+    -9: "GLM_ERR_NO_PROBLEM", -10: "GLM_ERR_UNSUPPORTED",
+}
+PREC = {"f32": 0, "bf16": 1, "f16": 2}
+DTYPE = {"f32": 0, "bf16": 1, "f16": 2}
+
+# every symbol include/glm.h declares, with its ctypes signature
+_vp, _i32, _i64, _f64, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+SIGNATURES = {
+    "glm_version": ([], ctypes.c_int),
+    "glm_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "glm_last_error": ([_vp], ctypes.c_char_p),
+    "glm_create": ([ctypes.POINTER(_vp), ctypes.c_int, _sz, _vp], ctypes.c_int),
+    "glm_destroy": ([_vp], None),
+    "glm_set_problem": ([_vp, _i32, _i64, _f64, _f64, _vp, _vp, ctypes.c_int], ctypes.c_int),
+    "glm_prepare": ([_vp, _f64], ctypes.c_int),
+    "glm_filter": ([_vp, _i64, _i64, _vp, _i64, ctypes.c_int], ctypes.c_int),
+    "glm_spike_term": ([_vp, _vp, _vp], ctypes.c_int),
+    "glm_loglik_grad": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "glm_profile_enable": ([_vp, ctypes.c_int], ctypes.c_int),
+    "glm_profile_read": ([_vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
+    "glm_launch_count": ([_vp], _i64),
+}
+
+# precisions this build implements
+AVAILABLE_PRECISIONS = ("f32",)
+
+
+def available_precisions():
+    return AVAILABLE_PRECISIONS
+
+_lib = None
+
+
+class GLMError(RuntimeError):
+    def __init__(self, code: int, msg: str = ""):
+        self.code = code
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}" if msg else f"{ERRORS.get(code, code)}")
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libglm.so and declare its signatures.  Raises if the library was not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libglm.so not found at {path}: build it first (python -m paper_1502_04993_gb300.build "
+                          "or __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+class GLM:
+    """One libglm context on one CUDA device, bound to a torch stream."""
+
+    def __init__(self, device: int = 0, workspace_cap: int = 0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libglm needs a CUDA device; there is no CPU fallback")
+        self.lib = load_library()
+        self.device = device
+        self.torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        h = ctypes.c_void_p()
+        rc = self.lib.glm_create(ctypes.byref(h), device, workspace_cap, ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != GLM_OK:
+            raise GLMError(rc, "glm_create")
+        self.h = h
+        self.n = self.n_bins = None
+
+    # ---- helpers ----
+    def _check(self, rc: int, what: str):
+        if rc != GLM_OK:
+            msg = self.lib.glm_last_error(self.h)
+            raise GLMError(rc, f"{what}: {msg.decode() if msg else ''}")
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.glm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- API ----
+    def set_problem(self, offs, bins, n_bins: int, dt: float, tau: float, prec: str = "f32"):
+        offs = np.ascontiguousarray(offs, dtype=np.int64)
+        bins = np.ascontiguousarray(bins, dtype=np.int32)
+        n = offs.size - 1
+        rc = self.lib.glm_set_problem(self.h, n, int(n_bins), float(dt), float(tau), offs.ctypes.data,
+                                      bins.ctypes.data if bins.size else None, PREC[prec])
+        self._check(rc, "glm_set_problem")
+        self.n, self.n_bins, self.dt, self.tau, self.prec = n, int(n_bins), dt, tau, prec
+
+    def prepare(self, tau: float | None = None):
+        self._check(self.lib.glm_prepare(self.h, float(tau) if tau else -1.0), "glm_prepare")
+        if tau:
+            self.tau = tau
+
+    def filter(self, t0: int = 0, t_len: int | None = None, dtype: str = "f32", out=None):
+        torch = self.torch
+        t_len = self.n_bins - t0 if t_len is None else t_len
+        tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dtype]
+        if out is None:
+            out = torch.empty((self.n, t_len), dtype=tdt, device=f"cuda:{self.device}")
+        self._check(self.lib.glm_filter(self.h, int(t0), int(t_len), _ptr(out), out.stride(0), DTYPE[dtype]),
+                    "glm_filter")
+        return out
+
+    def spike_term(self):
+        torch = self.torch
+        C = torch.empty((self.n, self.n), dtype=torch.float64, device=f"cuda:{self.device}")
+        q = torch.empty(self.n, dtype=torch.float64, device=f"cuda:{self.device}")
+        self._check(self.lib.glm_spike_term(self.h, _ptr(C), _ptr(q)), "glm_spike_term")
+        return C, q
+
+    def profile(self, enable: bool = True):
+        self._check(self.lib.glm_profile_enable(self.h, int(enable)), "glm_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{group name: (launches, total ms)} since profiling was enabled (synchronises)."""
+        m = 16
+        names = ctypes.create_string_buffer(32 * m)
+        cnt = (ctypes.c_int64 * m)()
+        ms = (ctypes.c_double * m)()
+        k = self.lib.glm_profile_read(self.h, m, names, cnt, ms)
+        if k < 0:
+            raise GLMError(k, "glm_profile_read")
+        raw = names.raw
+        out = {}
+        for e in range(k):
+            nm = raw[32 * e:32 * e + 32].split(b"\0", 1)[0].decode()
+            out[nm] = (int(cnt[e]), float(ms[e]))
+        return out
+
+    def launch_count(self) -> int:
+        return int(self.lib.glm_launch_count(self.h))
+
+    def loglik_grad(self, W, b, *, grad: bool = True, total: bool = True, out=None):
+        """L_i, L, dL/dW and dL/db at (W, b).  W: (n, n) float32 cuda, b: (n,) float32 cuda."""
+        torch = self.torch
+        dev = f"cuda:{self.device}"
+        W = W.to(device=dev, dtype=torch.float32).contiguous()
+        b = b.to(device=dev, dtype=torch.float32).contiguous()
+        out = out or {}
+        L_rows = out.get("L_rows")
+        if L_rows is None:
+            L_rows = torch.empty(self.n, dtype=torch.float64, device=dev)
+        G = out.get("G") if grad else None
+        if grad and G is None:
+            G = torch.empty((self.n, self.n), dtype=torch.float64, device=dev)
+        gb = out.get("gb") if grad else None
+        if grad and gb is None:
+            gb = torch.empty(self.n, dtype=torch.float64, device=dev)
+        tot = ctypes.c_double(0.0)
+        rc = self.lib.glm_loglik_grad(self.h, _ptr(W), _ptr(b), _ptr(L_rows),
+                                      ctypes.byref(tot) if total else None, _ptr(G), _ptr(gb))
+        self._check(rc, "glm_loglik_grad")
+        return dict(L_rows=L_rows, L_total=tot.value if total else None, G=G, gb=gb)

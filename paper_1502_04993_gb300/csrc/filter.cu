@@ -1,0 +1,290 @@
+// Step a0/a1: spike ingest and the filter scan X_j[t] = a X_j[t-1] + S_j[t-1] (Eq. 13 on the grid; the
+// exponential kernel h(t) = H(t) exp(-t/tau) of Sec. 2.2 with a one-bin delay).
+//
+//   carry pass  (FP64, O(q + n * nseg)):  per row and 256-bin segment, X at the segment start and the
+//               index of the first spike in or after the segment.
+//   write pass  (FP32 scan, HBM-write bound):  one warp per (8 rows, 4096-bin chunk); the segments of
+//               a chunk are scanned in order, starting from the FP64 carry, and stored as
+//                 F32:    X row-major [n][Tpad]
+//                 16-bit: X row-major [n][Tpad] and X^T [Tpad][ldn] (the K-major operand of U = W X)
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+
+#include "glm_internal.h"
+#include "scan_dev.cuh"
+
+namespace glm {
+
+void fill_scan_consts(double a, ScanConsts* sc) {
+    auto split = [](double v, float* hi, float* lo) {
+        const float h = (float)v;
+        *hi = h;
+        *lo = (float)(v - (double)h);
+    };
+    split(a, &sc->a_hi, &sc->a_lo);
+    for (int m = 0; m <= 8; ++m) split(std::pow(a, (double)m), &sc->pm_hi[m], &sc->pm_lo[m]);
+    for (int d = 0; d < 5; ++d) split(std::pow(a, 8.0 * (1 << d)), &sc->ps_hi[d], &sc->ps_lo[d]);
+    for (int l = 0; l < 32; ++l) split(std::pow(a, 8.0 * l), &sc->pl_hi[l], &sc->pl_lo[l]);
+}
+
+// Block per row: segment-first indices and, in seg_carry, the contribution of each segment's own
+// spikes to X at the next segment start: sum_{t in seg s} a^(256 (s+1) - 1 - t).
+__global__ void seg_local_kernel(int32_t n, int64_t nseg, const int64_t* __restrict__ offs,
+                                 const int32_t* __restrict__ bins, const double* __restrict__ pow_seg,
+                                 double* __restrict__ seg_local, int32_t* __restrict__ seg_first) {
+    const int32_t j = blockIdx.x;
+    if (j >= n) return;
+    const int64_t o0 = offs[j], q = offs[j + 1] - o0;
+    const int32_t* b = bins + o0;
+    double* loc = seg_local + (int64_t)j * nseg;
+    int32_t* first = seg_first + (int64_t)j * nseg;
+    for (int64_t s = threadIdx.x; s < nseg; s += blockDim.x) loc[s] = 0.0;
+    if (q == 0) {
+        for (int64_t s = threadIdx.x; s < nseg; s += blockDim.x) first[s] = 0;
+        return;
+    }
+    __syncthreads();
+    for (int64_t k = threadIdx.x; k < q; k += blockDim.x) {
+        const int64_t s = b[k] / SEG;
+        const int64_t ps = (k > 0) ? (int64_t)(b[k - 1] / SEG) : -1;
+        if (s != ps) {
+            for (int64_t ss = ps + 1; ss <= s; ++ss) first[ss] = (int32_t)k;
+            double acc = 0.0;
+            const int64_t end = (s + 1) * SEG;
+            for (int64_t kk = k; kk < q && b[kk] < end; ++kk) acc += pow_seg[end - 1 - b[kk]];
+            loc[s] = acc;
+        }
+        if (k == q - 1)
+            for (int64_t ss = s + 1; ss < nseg; ++ss) first[ss] = (int32_t)q;
+    }
+}
+
+// Thread per row, in place: seg_carry[s] <- X_j[256 s] = a^256 X_j[256 (s-1)] + local[s-1].
+__global__ void seg_carry_kernel(int32_t n, int64_t nseg, double a_seg, double* __restrict__ seg) {
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double* p = seg + (int64_t)j * nseg;
+    double c = 0.0;
+    for (int64_t s = 0; s < nseg; ++s) {
+        const double l = p[s];
+        p[s] = c;
+        c = fma(a_seg, c, l);
+    }
+}
+
+constexpr int CHUNK_SEGS = 16;  // 4096 bins per warp unit
+constexpr int FW_WARPS = 4;
+
+template <typename T16>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi);
+template <>
+__device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+template <>
+__device__ __forceinline__ uint32_t pack2<__half>(float lo, float hi) {
+    __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+struct FilterArgs {
+    int32_t n;
+    int64_t T, nseg, Tpad, ldn;
+    int32_t ngroups;
+    int64_t nchunks;
+    const int64_t* offs;
+    const int32_t* bins;
+    const double* seg_carry;
+    const int32_t* seg_first;
+    void* X;
+    void* XT;
+};
+
+// MODE 0: F32 X.  MODE 1: 16-bit X and X^T (T16 = __nv_bfloat16 or __half).
+template <int MODE, typename T16>
+__global__ void __launch_bounds__(FW_WARPS * 32) filter_cache_kernel(const __grid_constant__ ScanConsts K,
+                                                                     const __grid_constant__ FilterArgs A) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wg = (int64_t)blockIdx.x * FW_WARPS + (threadIdx.x >> 5);
+    const int64_t c = wg / A.ngroups;
+    const int32_t g = (int32_t)(wg % A.ngroups);
+    if (c >= A.nchunks) return;
+    const float pl_hi = K.pl_hi[lane], pl_lo = K.pl_lo[lane];
+    const int64_t s0 = c * CHUNK_SEGS;
+    const int64_t s1 = min(s0 + (int64_t)CHUNK_SEGS, A.nseg);
+    float xs[8];
+    int64_t cur[8], end[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int32_t r = g * 8 + k;
+        if (r < A.n) {
+            xs[k] = (float)A.seg_carry[(int64_t)r * A.nseg + s0];
+            const int64_t o0 = A.offs[r];
+            cur[k] = o0 + A.seg_first[(int64_t)r * A.nseg + s0];
+            end[k] = A.offs[r + 1];
+        } else {
+            xs[k] = 0.f;
+            cur[k] = 0;
+            end[k] = 0;
+        }
+    }
+    for (int64_t s = s0; s < s1; ++s) {
+        const int64_t t0 = s * SEG;
+        const int64_t tl = t0 + 8 * lane;
+        uint32_t pk[8][4];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int32_t r = g * 8 + k;
+            const uint32_t bits = seg_bits(A.bins, cur[k], end[k], t0, lane);
+            float v[8];
+            xs[k] = seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v);
+            if (MODE == 0) {
+                if (r < A.n) {
+                    float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(A.X) + (int64_t)r * A.Tpad + tl);
+                    dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+                    dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+                }
+            } else {
+#pragma unroll
+                for (int p = 0; p < 4; ++p) pk[k][p] = pack2<T16>(v[2 * p], v[2 * p + 1]);
+                if (r < A.n) {
+                    uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<T16*>(A.X) + (int64_t)r * A.Tpad + tl);
+                    *dst = make_uint4(pk[k][0], pk[k][1], pk[k][2], pk[k][3]);
+                }
+            }
+        }
+        if (MODE == 1) {
+            // 8x8 transpose in registers: for bin m, the 8 rows of this group are contiguous in X^T.
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const uint32_t sel = (m & 1) ? 0x7632u : 0x5410u;
+                uint32_t w[4];
+#pragma unroll
+                for (int qd = 0; qd < 4; ++qd) w[qd] = __byte_perm(pk[2 * qd][m >> 1], pk[2 * qd + 1][m >> 1], sel);
+                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<T16*>(A.XT) + (tl + m) * A.ldn + g * 8);
+                *dst = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+    }
+}
+
+struct RangeArgs {
+    int32_t n;
+    int64_t T, nseg;
+    int32_t ngroups;
+    int64_t s_begin, nchunks;
+    int64_t t0, t_len, ldx;
+    int dtype;
+    const int64_t* offs;
+    const int32_t* bins;
+    const double* seg_carry;
+    const int32_t* seg_first;
+    void* out;
+};
+
+// X[:, t0 : t0 + t_len] into a caller buffer (any leading dimension, element-wise stores).
+__global__ void __launch_bounds__(FW_WARPS * 32) filter_range_kernel(const __grid_constant__ ScanConsts K,
+                                                                     const __grid_constant__ RangeArgs A) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wg = (int64_t)blockIdx.x * FW_WARPS + (threadIdx.x >> 5);
+    const int64_t c = wg / A.ngroups;
+    const int32_t g = (int32_t)(wg % A.ngroups);
+    if (c >= A.nchunks) return;
+    const float pl_hi = K.pl_hi[lane], pl_lo = K.pl_lo[lane];
+    const int64_t s0 = A.s_begin + c * CHUNK_SEGS;
+    const int64_t s1 = min(s0 + (int64_t)CHUNK_SEGS, A.nseg);
+    const int64_t te = A.t0 + A.t_len;
+    for (int k = 0; k < 8; ++k) {
+        const int32_t r = g * 8 + k;
+        if (r >= A.n) break;
+        float xs = (float)A.seg_carry[(int64_t)r * A.nseg + s0];
+        int64_t cur = A.offs[r] + A.seg_first[(int64_t)r * A.nseg + s0];
+        const int64_t end = A.offs[r + 1];
+        for (int64_t s = s0; s < s1; ++s) {
+            const int64_t t0 = s * SEG;
+            if (t0 >= te) break;
+            const uint32_t bits = seg_bits(A.bins, cur, end, t0, lane);
+            float v[8];
+            xs = seg_scan(K, xs, bits, pl_hi, pl_lo, lane, v);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int64_t t = t0 + 8 * lane + m;
+                if (t < A.t0 || t >= te) continue;
+                const int64_t o = (int64_t)r * A.ldx + (t - A.t0);
+                if (A.dtype == GLM_DTYPE_F32)
+                    reinterpret_cast<float*>(A.out)[o] = v[m];
+                else if (A.dtype == GLM_DTYPE_BF16)
+                    reinterpret_cast<__nv_bfloat16*>(A.out)[o] = __float2bfloat16_rn(v[m]);
+                else
+                    reinterpret_cast<__half*>(A.out)[o] = __float2half_rn(v[m]);
+            }
+        }
+    }
+}
+
+cudaError_t launch_carry(glm_ctx* c) {
+    const Problem& P = c->pb;
+    seg_local_kernel<<<P.n, 256, 0, c->stream>>>(P.n, P.nseg, c->buf.offs, c->buf.bins, c->buf.pow_seg,
+                                                 c->buf.seg_carry, c->buf.seg_first);
+    const double a_seg = std::exp(-(double)SEG * P.dt / P.tau);
+    seg_carry_kernel<<<(P.n + 127) / 128, 128, 0, c->stream>>>(P.n, P.nseg, a_seg, c->buf.seg_carry);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_filter_cache(glm_ctx* c) {
+    const Problem& P = c->pb;
+    FilterArgs A;
+    A.n = P.n;
+    A.T = P.T;
+    A.nseg = P.nseg;
+    A.Tpad = P.Tpad;
+    A.ldn = c->buf.ldn;
+    A.ngroups = (P.n + 7) / 8;
+    A.nchunks = (P.nseg + CHUNK_SEGS - 1) / CHUNK_SEGS;
+    A.offs = c->buf.offs;
+    A.bins = c->buf.bins;
+    A.seg_carry = c->buf.seg_carry;
+    A.seg_first = c->buf.seg_first;
+    A.X = c->buf.X;
+    A.XT = c->buf.XT;
+    const int64_t warps = (int64_t)A.ngroups * A.nchunks;
+    const int64_t blocks = (warps + FW_WARPS - 1) / FW_WARPS;
+    if (P.prec == GLM_PREC_F32)
+        filter_cache_kernel<0, __half><<<(unsigned)blocks, FW_WARPS * 32, 0, c->stream>>>(c->sc, A);
+    else if (P.prec == GLM_PREC_BF16)
+        filter_cache_kernel<1, __nv_bfloat16><<<(unsigned)blocks, FW_WARPS * 32, 0, c->stream>>>(c->sc, A);
+    else
+        filter_cache_kernel<1, __half><<<(unsigned)blocks, FW_WARPS * 32, 0, c->stream>>>(c->sc, A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_filter_range(glm_ctx* c, int64_t t0, int64_t t_len, void* out, int64_t ldx,
+                                glm_dtype_t dtype) {
+    const Problem& P = c->pb;
+    RangeArgs A;
+    A.n = P.n;
+    A.T = P.T;
+    A.nseg = P.nseg;
+    A.ngroups = (P.n + 7) / 8;
+    A.s_begin = t0 / SEG;
+    const int64_t s_end = (t0 + t_len + SEG - 1) / SEG;
+    A.nchunks = (s_end - A.s_begin + CHUNK_SEGS - 1) / CHUNK_SEGS;
+    A.t0 = t0;
+    A.t_len = t_len;
+    A.ldx = ldx;
+    A.dtype = (int)dtype;
+    A.offs = c->buf.offs;
+    A.bins = c->buf.bins;
+    A.seg_carry = c->buf.seg_carry;
+    A.seg_first = c->buf.seg_first;
+    A.out = out;
+    const int64_t warps = (int64_t)A.ngroups * A.nchunks;
+    const int64_t blocks = (warps + FW_WARPS - 1) / FW_WARPS;
+    filter_range_kernel<<<(unsigned)blocks, FW_WARPS * 32, 0, c->stream>>>(c->sc, A);
+    return cudaGetLastError();
+}
+
+}  // namespace glm

@@ -1,0 +1,398 @@
+// C ABI of libglm (declared in include/glm.h): contexts, problem set-up and the log-likelihood /
+// gradient evaluation.  Host-side validation of the spike trains, device workspace, stream plumbing.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "glm_internal.h"
+
+using namespace glm;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int fail(glm_ctx* c, int code, const std::string& msg) {
+    if (c) c->last_error = msg;
+    return code;
+}
+
+int cuda_fail(glm_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, GLM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define GLM_CK(call)                                   \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+    } while (0)
+
+void free_all(glm_ctx* c) {
+    for (int k = 0; k < c->n_allocs; ++k) cudaFree(c->allocs[k]);
+    c->n_allocs = 0;
+    c->ws_used = 0;
+    c->buf = Buffers();
+    c->has_problem = false;
+}
+
+// Device allocation charged against the workspace cap.
+int ws_alloc(glm_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (c->ws_cap && c->ws_used + bytes > c->ws_cap)
+        return fail(c, GLM_ERR_OOM, "workspace cap exceeded (" + std::to_string(c->ws_used + bytes) + " > " +
+                                        std::to_string(c->ws_cap) + " bytes)");
+    if (c->n_allocs >= 64) return fail(c, GLM_ERR_OOM, "too many workspace buffers");
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, GLM_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " +
+                                        cudaGetErrorString(e));
+    }
+    c->allocs[c->n_allocs] = *p;
+    c->alloc_bytes[c->n_allocs] = bytes;
+    c->n_allocs++;
+    c->ws_used += bytes;
+    return GLM_OK;
+}
+
+template <typename T>
+int ws_alloc_t(glm_ctx* c, T** p, size_t count) {
+    void* v = nullptr;
+    int rc = ws_alloc(c, &v, count * sizeof(T));
+    *p = reinterpret_cast<T*>(v);
+    return rc;
+}
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// ---- tracing: CUDA events around each kernel group while profiling is enabled ----
+int prof_begin(glm_ctx* c, const char* name) {
+    if (!c->prof_on) return -1;
+    int id = -1;
+    for (int k = 0; k < c->prof_nnames; ++k)
+        if (std::strcmp(c->prof_names[k], name) == 0) id = k;
+    if (id < 0) {
+        if (c->prof_nnames == glm_ctx::PROF_NAMES) return -1;
+        id = c->prof_nnames++;
+        c->prof_names[id] = name;
+    }
+    if (c->prof_n == c->prof_cap) {
+        const int ncap = c->prof_cap ? 2 * c->prof_cap : 256;
+        auto* nr = new (std::nothrow) glm_ctx::ProfRec[ncap];
+        if (!nr) return -1;
+        for (int k = 0; k < c->prof_cap; ++k) nr[k] = c->prof_recs[k];
+        for (int k = c->prof_cap; k < ncap; ++k) {
+            cudaEventCreate(&nr[k].a);
+            cudaEventCreate(&nr[k].b);
+        }
+        delete[] c->prof_recs;
+        c->prof_recs = nr;
+        c->prof_cap = ncap;
+    }
+    const int slot = c->prof_n++;
+    c->prof_recs[slot].name = id;
+    cudaEventRecord(c->prof_recs[slot].a, c->stream);
+    return slot;
+}
+
+void prof_end(glm_ctx* c, int slot) {
+    if (slot >= 0) cudaEventRecord(c->prof_recs[slot].b, c->stream);
+}
+
+// fold the recorded event pairs into the per-name totals (synchronises the stream)
+void prof_fold(glm_ctx* c) {
+    if (c->prof_n == 0) return;
+    cudaStreamSynchronize(c->stream);
+    for (int k = 0; k < c->prof_n; ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->prof_recs[k].a, c->prof_recs[k].b) == cudaSuccess) {
+            c->prof_ms[c->prof_recs[k].name] += ms;
+            c->prof_count[c->prof_recs[k].name] += 1;
+        }
+    }
+    cudaGetLastError();
+    c->prof_n = 0;
+}
+
+#define GLM_RUN(name, nkernels, call)                  \
+    do {                                               \
+        const int slot_ = prof_begin(c, name);         \
+        GLM_CK(call);                                  \
+        prof_end(c, slot_);                            \
+        c->launches += (nkernels);                     \
+    } while (0)
+
+int validate_spikes(glm_ctx* c, int32_t n, int64_t T, const int64_t* offs, const int32_t* bins) {
+    if (offs[0] != 0) return fail(c, GLM_ERR_SPIKE_OUT_OF_RANGE, "offs[0] must be 0");
+    for (int32_t i = 0; i < n; ++i)
+        if (offs[i + 1] < offs[i]) return fail(c, GLM_ERR_SPIKE_OUT_OF_RANGE, "offs must be non-decreasing");
+    const int64_t q = offs[n];
+    if (q > 0 && !bins) return fail(c, GLM_ERR_INVALID_ARG, "bins is NULL but offs[n] > 0");
+    for (int32_t i = 0; i < n; ++i) {
+        int64_t prev = -1;
+        for (int64_t k = offs[i]; k < offs[i + 1]; ++k) {
+            const int64_t s = bins[k];
+            if (s < 0 || s >= T)
+                return fail(c, GLM_ERR_SPIKE_OUT_OF_RANGE,
+                            "spike bin " + std::to_string(s) + " of row " + std::to_string(i) + " outside [0, n_bins)");
+            if (s <= prev)
+                return fail(c, GLM_ERR_UNSORTED_SPIKES,
+                            "row " + std::to_string(i) + ": bins not strictly increasing at index " + std::to_string(k));
+            prev = s;
+        }
+    }
+    return GLM_OK;
+}
+
+int do_prepare(glm_ctx* c) {
+    Problem& P = c->pb;
+    P.a = std::exp(-P.dt / P.tau);
+    fill_scan_consts(P.a, &c->sc);
+    std::vector<double> pw(SEG + 1);
+    for (int k = 0; k <= SEG; ++k) pw[k] = std::exp(-(double)k * P.dt / P.tau);
+    GLM_CK(cudaMemcpyAsync(c->buf.pow_seg, pw.data(), sizeof(double) * (SEG + 1), cudaMemcpyHostToDevice,
+                           c->stream));
+    GLM_RUN("carry", 2, launch_carry(c));
+    GLM_RUN("filter_scan", 1, launch_filter_cache(c));
+    GLM_RUN("spike_term", 2, launch_spike_term(c));
+    // pw is a pageable host buffer: the copy above has been staged before cudaMemcpyAsync returned
+    return GLM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int glm_version(void) { return 100; }
+
+const char* glm_strerror(int code) {
+    switch (code) {
+        case GLM_OK: return "ok";
+        case GLM_ERR_INVALID_ARG: return "invalid argument";
+        case GLM_ERR_UNSORTED_SPIKES: return "spike bins of a row are not strictly increasing";
+        case GLM_ERR_SPIKE_OUT_OF_RANGE: return "spike bin outside [0, n_bins) or malformed offsets";
+        case GLM_ERR_OOM: return "out of device memory or workspace cap exceeded";
+        case GLM_ERR_CUDA: return "CUDA error";
+        case GLM_ERR_NONFINITE: return "non-finite value (input or exp overflow)";
+        case GLM_ERR_TIMEOUT: return "device-side wait timed out";
+        case GLM_ERR_UNSUPPORTED_ARCH: return "tensor-core precision needs an sm_103 GPU";
+        case GLM_ERR_NO_PROBLEM: return "no problem set (call glm_set_problem first)";
+        case GLM_ERR_UNSUPPORTED: return "unsupported request";
+        default: return "unknown status";
+    }
+}
+
+const char* glm_last_error(const glm_ctx* c) { return c ? c->last_error.c_str() : ""; }
+
+int glm_create(glm_ctx** out, int device, size_t workspace_cap_bytes, void* cuda_stream) {
+    if (!out) return GLM_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return GLM_ERR_CUDA;
+    }
+    if (device < 0 || device >= ndev) return GLM_ERR_INVALID_ARG;
+    glm_ctx* c = new (std::nothrow) glm_ctx();
+    if (!c) return GLM_ERR_OOM;
+    c->device = device;
+    c->ws_cap = workspace_cap_bytes;
+    c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete c;
+        return GLM_ERR_CUDA;
+    }
+    c->sm_count = prop.multiProcessorCount;
+    c->cc_major = prop.major;
+    c->cc_minor = prop.minor;
+    *out = c;
+    return GLM_OK;
+}
+
+void glm_destroy(glm_ctx* c) {
+    if (!c) return;
+    {
+        DeviceGuard g(c->device);
+        if (c->stream) cudaStreamSynchronize(c->stream);
+        else cudaDeviceSynchronize();
+        free_all(c);
+        for (int k = 0; k < c->prof_cap; ++k) {
+            cudaEventDestroy(c->prof_recs[k].a);
+            cudaEventDestroy(c->prof_recs[k].b);
+        }
+        delete[] c->prof_recs;
+    }
+    delete c;
+}
+
+int glm_profile_enable(glm_ctx* c, int enable) {
+    if (!c) return GLM_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    prof_fold(c);
+    c->prof_on = enable != 0;
+    if (c->prof_on) {
+        for (int k = 0; k < glm_ctx::PROF_NAMES; ++k) {
+            c->prof_count[k] = 0;
+            c->prof_ms[k] = 0.0;
+        }
+        c->prof_nnames = 0;
+    }
+    return GLM_OK;
+}
+
+int glm_profile_read(glm_ctx* c, int max_entries, char* names, int64_t* launches, double* ms) {
+    if (!c || max_entries < 0 || (max_entries > 0 && (!names || !launches || !ms))) return GLM_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    prof_fold(c);
+    const int m = c->prof_nnames < max_entries ? c->prof_nnames : max_entries;
+    for (int k = 0; k < m; ++k) {
+        std::strncpy(names + 32 * k, c->prof_names[k], 31);
+        names[32 * k + 31] = 0;
+        launches[k] = c->prof_count[k];
+        ms[k] = c->prof_ms[k];
+    }
+    return m;
+}
+
+int64_t glm_launch_count(const glm_ctx* c) { return c ? c->launches : 0; }
+
+int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau, const int64_t* offs,
+                    const int32_t* bins, glm_prec_t prec) {
+    if (!c) return GLM_ERR_INVALID_ARG;
+    if (n < 1 || n_bins < 1 || n_bins >= (int64_t)1 << 31 || !offs)
+        return fail(c, GLM_ERR_INVALID_ARG, "need n >= 1, 1 <= n_bins < 2^31 and offs");
+    if (!(std::isfinite(dt) && dt > 0) || !(std::isfinite(tau) && tau > 0))
+        return fail(c, GLM_ERR_INVALID_ARG, "dt and tau must be finite and > 0");
+    if (prec != GLM_PREC_F32 && prec != GLM_PREC_BF16 && prec != GLM_PREC_F16)
+        return fail(c, GLM_ERR_INVALID_ARG, "unknown precision");
+    if (prec != GLM_PREC_F32)
+        return fail(c, GLM_ERR_UNSUPPORTED, "tensor-core precisions are not built into this library yet");
+    int rc = validate_spikes(c, n, n_bins, offs, bins);
+    if (rc) return rc;
+    DeviceGuard g(c->device);
+    GLM_CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+    free_all(c);
+    Problem& P = c->pb;
+    P = Problem();
+    P.n = n;
+    P.T = n_bins;
+    P.dt = dt;
+    P.tau = tau;
+    P.q = offs[n];
+    P.nseg = (n_bins + SEG - 1) / SEG;
+    P.Tpad = P.nseg * SEG;
+    P.prec = prec;
+    Buffers& B = c->buf;
+    const size_t nn = (size_t)n * n;
+    const size_t esz = (prec == GLM_PREC_F32) ? 4 : 2;
+    B.ldn = round_up(n, 8);
+    if ((rc = ws_alloc_t(c, &B.offs, n + 1)) || (rc = ws_alloc_t(c, &B.bins, P.q > 0 ? P.q : 1)) ||
+        (rc = ws_alloc_t(c, &B.seg_carry, (size_t)n * P.nseg)) ||
+        (rc = ws_alloc_t(c, &B.seg_first, (size_t)n * P.nseg)) || (rc = ws_alloc_t(c, &B.pow_seg, SEG + 1)) ||
+        (rc = ws_alloc_t(c, &B.qd, n)) || (rc = ws_alloc_t(c, &B.C, nn)) ||
+        (rc = ws_alloc_t(c, &B.C_part, nn * spike_term_parts(c))) || (rc = ws_alloc(c, &B.X, (size_t)n * P.Tpad * esz)) ||
+        (rc = ws_alloc(c, &B.E, (size_t)n * P.Tpad * esz)) ||
+        (rc = ws_alloc_t(c, &B.part_e, (size_t)n * (P.Tpad / simt_tile_t()))) ||
+        (rc = ws_alloc_t(c, &B.part_g, nn * grad_nsplit(c))) || (rc = ws_alloc_t(c, &B.flags, 4)) ||
+        (rc = ws_alloc_t(c, &B.Lrows, n)) || (rc = ws_alloc_t(c, &B.scal, 8))) {
+        free_all(c);
+        return rc;
+    }
+    std::vector<double> qd(n);
+    for (int32_t i = 0; i < n; ++i) qd[i] = (double)(offs[i + 1] - offs[i]);
+    GLM_CK(cudaMemcpyAsync(B.offs, offs, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, c->stream));
+    if (P.q > 0)
+        GLM_CK(cudaMemcpyAsync(B.bins, bins, sizeof(int32_t) * P.q, cudaMemcpyHostToDevice, c->stream));
+    GLM_CK(cudaMemcpyAsync(B.qd, qd.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    GLM_CK(cudaMemsetAsync(B.flags, 0, 4 * sizeof(int), c->stream));
+    rc = do_prepare(c);
+    if (rc) {
+        free_all(c);
+        return rc;
+    }
+    // the host staging buffers (qd, powers) go out of scope: finish the copies first
+    GLM_CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+    c->has_problem = true;
+    return GLM_OK;
+}
+
+int glm_prepare(glm_ctx* c, double tau) {
+    if (!c) return GLM_ERR_INVALID_ARG;
+    if (!c->has_problem) return fail(c, GLM_ERR_NO_PROBLEM, "no problem set");
+    if (tau > 0) {
+        if (!std::isfinite(tau)) return fail(c, GLM_ERR_INVALID_ARG, "tau must be finite");
+        c->pb.tau = tau;
+    }
+    DeviceGuard g(c->device);
+    return do_prepare(c);
+}
+
+int glm_filter(glm_ctx* c, int64_t t0, int64_t t_len, void* X_dev, int64_t ldx, glm_dtype_t dtype) {
+    if (!c) return GLM_ERR_INVALID_ARG;
+    if (!c->has_problem) return fail(c, GLM_ERR_NO_PROBLEM, "no problem set");
+    if (!X_dev || t0 < 0 || t_len < 1 || t0 + t_len > c->pb.T || ldx < t_len)
+        return fail(c, GLM_ERR_INVALID_ARG, "bad range, buffer or leading dimension");
+    if (dtype != GLM_DTYPE_F32 && dtype != GLM_DTYPE_BF16 && dtype != GLM_DTYPE_F16)
+        return fail(c, GLM_ERR_INVALID_ARG, "unknown dtype");
+    DeviceGuard g(c->device);
+    GLM_RUN("filter_range", 1, launch_filter_range(c, t0, t_len, X_dev, ldx, dtype));
+    return GLM_OK;
+}
+
+int glm_spike_term(glm_ctx* c, double* C_dev, double* q_dev) {
+    if (!c) return GLM_ERR_INVALID_ARG;
+    if (!c->has_problem) return fail(c, GLM_ERR_NO_PROBLEM, "no problem set");
+    DeviceGuard g(c->device);
+    const size_t nn = (size_t)c->pb.n * c->pb.n;
+    if (C_dev) GLM_CK(cudaMemcpyAsync(C_dev, c->buf.C, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if (q_dev)
+        GLM_CK(cudaMemcpyAsync(q_dev, c->buf.qd, c->pb.n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    return GLM_OK;
+}
+
+int glm_loglik_grad(glm_ctx* c, const float* W, const float* b, double* L_rows, double* L_total_host,
+                    double* G, double* gb) {
+    if (!c) return GLM_ERR_INVALID_ARG;
+    if (!c->has_problem) return fail(c, GLM_ERR_NO_PROBLEM, "no problem set");
+    if (!W || !b) return fail(c, GLM_ERR_INVALID_ARG, "W and b are required");
+    DeviceGuard g(c->device);
+    double* Lr = L_rows ? L_rows : c->buf.Lrows;
+    const bool want_grad = G != nullptr;
+    GLM_CK(cudaMemsetAsync(c->buf.flags, 0, sizeof(int), c->stream));
+    GLM_RUN("u_epilogue", 1, launch_simt_u_epilogue(c, W, b));
+    if (want_grad) GLM_RUN("grad", 1, launch_simt_grad(c));
+    GLM_RUN("reduce", want_grad ? 2 : 1, launch_reduce(c, W, b, Lr, G, gb, want_grad));
+    if (L_total_host) {
+        double* dtot = c->buf.scal;
+        GLM_RUN("total", 1, launch_total(c, Lr, dtot));
+        double tot = 0;
+        int flags = 0;
+        GLM_CK(cudaMemcpyAsync(&tot, dtot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        GLM_CK(cudaMemcpyAsync(&flags, c->buf.flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        GLM_CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+        *L_total_host = tot;
+        if (flags & 1) return fail(c, GLM_ERR_NONFINITE, "exp(U) overflowed or was not finite");
+    }
+    return GLM_OK;
+}
+
+}  // extern "C"

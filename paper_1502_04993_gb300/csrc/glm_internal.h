@@ -1,0 +1,115 @@
+// Internal declarations of libglm (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "glm.h"
+
+namespace glm {
+
+// ---------------------------------------------------------------------------------------------
+// Time-grid layout.  Bins are processed in segments of SEG = 256 (one warp, 8 bins per lane).
+// Per row j and segment s the carry X_j[256 s] (FP64) and the index of the first spike of row j
+// at or after bin 256 s are precomputed once per problem.
+// ---------------------------------------------------------------------------------------------
+constexpr int SEG = 256;
+
+// Powers of a = exp(-dt/tau) split into FP32 hi + lo parts, so that the FP32 scan multiplies by a
+// with ~48 significant bits (the product is hi*x + lo*x).
+struct ScanConsts {
+    float a_hi, a_lo;
+    float pm_hi[9], pm_lo[9];    // a^m,          m = 0..8
+    float ps_hi[5], ps_lo[5];    // a^(8*2^d),    d = 0..4   (warp scan strides)
+    float pl_hi[32], pl_lo[32];  // a^(8*l),      l = 0..31  (lane offsets)
+};
+
+struct Problem {
+    int32_t n = 0;
+    int64_t T = 0;        // bins
+    double dt = 0, tau = 0, a = 0;
+    int64_t q = 0;        // total spikes
+    int64_t nseg = 0;     // ceil(T / SEG)
+    int64_t Tpad = 0;     // nseg * SEG
+    glm_prec_t prec = GLM_PREC_F32;
+};
+
+// Device buffers owned by a context.  Row-major everywhere; ld* in elements.
+struct Buffers {
+    int64_t* offs = nullptr;      // [n+1]
+    int32_t* bins = nullptr;      // [q]
+    double* seg_carry = nullptr;  // [n][nseg]   X_j[256 s]
+    int32_t* seg_first = nullptr; // [n][nseg]   first spike index (relative to offs[j]) at bin >= 256 s
+    double* pow_seg = nullptr;    // [SEG + 1]   a^k, k = 0..SEG
+    double* qd = nullptr;         // [n]         spike counts
+    double* C = nullptr;          // [n][n]      spike term
+    double* C_part = nullptr;     // [parts][n][n]
+    void* X = nullptr;            // F32: float [n][Tpad]; 16-bit: [n][Tpad]
+    void* XT = nullptr;           // 16-bit only: [Tpad][ldn]
+    int64_t ldn = 0;              // leading dim of XT (n rounded up to 8... 64)
+    void* E = nullptr;            // F32: float [n][Tpad]; 16-bit: [n][Tpad]   dt * exp(U)
+    double* part_e = nullptr;     // [n][ntile_t]  per-(row, bin tile) sums of exp(U)
+    float* part_g = nullptr;      // [nsplit][n][n] FP32 partial sums of E X^T
+    void* Wsplit = nullptr;       // 16-bit: hi and lo parts of W, [2][n][ldn]
+    int* flags = nullptr;         // [4] device error flags
+    double* Lrows = nullptr;      // [n] scratch when the caller passes no L_rows
+    double* scal = nullptr;       // [8] device scalars (total log-likelihood, ...)
+};
+
+}  // namespace glm
+
+struct glm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    int cc_major = 0, cc_minor = 0;
+    size_t ws_cap = 0;
+    size_t ws_used = 0;
+    glm::Problem pb;
+    glm::Buffers buf;
+    glm::ScanConsts sc;
+    bool has_problem = false;
+    std::string last_error;
+    // tracing: event pairs per launched kernel group while profiling is on
+    bool prof_on = false;
+    struct ProfRec {
+        int name;
+        cudaEvent_t a, b;
+    };
+    ProfRec* prof_recs = nullptr;
+    int prof_n = 0, prof_cap = 0;
+    static constexpr int PROF_NAMES = 16;
+    const char* prof_names[PROF_NAMES] = {};
+    int64_t prof_count[PROF_NAMES] = {};
+    double prof_ms[PROF_NAMES] = {};
+    int prof_nnames = 0;
+    int64_t launches = 0;
+    // bookkeeping for the allocations (pointer, bytes)
+    void* allocs[64];
+    size_t alloc_bytes[64];
+    int n_allocs = 0;
+};
+
+namespace glm {
+
+// ---- launchers (each returns cudaError_t of the launch) ----
+cudaError_t launch_carry(glm_ctx* c);
+cudaError_t launch_filter_cache(glm_ctx* c);
+cudaError_t launch_filter_range(glm_ctx* c, int64_t t0, int64_t t_len, void* out, int64_t ldx, glm_dtype_t dtype);
+cudaError_t launch_spike_term(glm_ctx* c);
+cudaError_t launch_simt_u_epilogue(glm_ctx* c, const float* W, const float* b);
+cudaError_t launch_simt_grad(glm_ctx* c);
+cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_rows, double* G, double* gb,
+                          bool want_grad);
+cudaError_t launch_total(glm_ctx* c, const double* L_rows, double* out1);
+
+// ---- sizes shared between the launchers and the allocator ----
+int simt_tile_t();          // bins per SIMT GEMM1 tile
+int grad_nsplit(const glm_ctx* c);
+int spike_term_parts(const glm_ctx* c);
+
+void fill_scan_consts(double a, ScanConsts* sc);
+
+}  // namespace glm

@@ -1,0 +1,269 @@
+// The plain FP32 form of the two contractions (CUDA cores, no tensor cores):
+//   step a3/a4:  U = b 1^T + W X (Eq. 3) with the link applied in the epilogue (Eq. 5):
+//                E[i][t] = dt exp(U_i[t]) stored FP32, per (bin tile, row) FP64 sums of exp(U)
+//   step a5:     P_s = E X^T over a split s of the bins (FP32, two-level accumulation)
+// 128 x 128 output tiles, 256 threads, 8 x 8 outputs per thread, operands staged in shared memory.
+#include <cmath>
+
+#include "glm_internal.h"
+
+namespace glm {
+
+constexpr int SB = 128;   // tile edge
+constexpr int SK = 16;    // k step
+constexpr int ST = 256;   // threads
+constexpr int G_INNER = 1024;  // bins accumulated in the inner FP32 sum of the gradient product
+
+int simt_tile_t() { return SB; }
+
+struct SimtUArgs {
+    int32_t n;
+    int64_t T, Tpad;
+    double dt;
+    const float* W;   // [n][n]
+    const float* b;   // [n]
+    const float* X;   // [n][Tpad]
+    float* E;         // [n][Tpad]
+    double* part_e;   // [n][ntile]
+    int* flags;
+};
+
+// U tile rows i0..i0+127, bins t0..t0+127.  A = W (row-major, K contiguous), B = X (K x N, N contiguous).
+__global__ void __launch_bounds__(ST) simt_u_kernel(const __grid_constant__ SimtUArgs A) {
+    __shared__ __align__(16) float As[2][SK][SB];
+    __shared__ __align__(16) float Bs[2][SK][SB];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int32_t i0 = blockIdx.y * SB;
+    const int64_t t0 = (int64_t)blockIdx.x * SB;
+    const int32_t n = A.n;
+    float acc[8][8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+    // loader mapping
+    const int a_row = tid >> 2, a_col = (tid & 3) * 4;  // rows a_row and a_row + 64, k a_col..+3
+    const int b_row = tid >> 5, b_col = (tid & 31) * 4; // k rows b_row and b_row + 8, bins b_col..+3
+    float ra[2][4];
+    float4 rb[2];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int32_t i = i0 + a_row + 64 * h;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int32_t k = k0 + a_col + q;
+                ra[h][q] = (i < n && k < n) ? A.W[(int64_t)i * n + k] : 0.f;
+            }
+            const int32_t kb = k0 + b_row + 8 * h;
+            rb[h] = (kb < n) ? *reinterpret_cast<const float4*>(A.X + (int64_t)kb * A.Tpad + t0 + b_col)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) As[buf][a_col + q][a_row + 64 * h] = ra[h][q];
+            *reinterpret_cast<float4*>(&Bs[buf][b_row + 8 * h][b_col]) = rb[h];
+        }
+    };
+    const int nk = (n + SK - 1) / SK;
+    load(0);
+    store(0);
+    __syncthreads();
+    for (int kt = 0; kt < nk; ++kt) {
+        const int cur = kt & 1;
+        if (kt + 1 < nk) load((kt + 1) * SK);
+#pragma unroll
+        for (int k = 0; k < SK; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][k][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][k][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][k][64 + tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+        }
+        if (kt + 1 < nk) store(cur ^ 1);
+        __syncthreads();
+    }
+    // epilogue: u = acc + b, e = exp(u); E = dt e (0 beyond T); FP64 row sums of e
+    bool bad = false;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int32_t i = i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4));
+        const float bi = (i < n) ? A.b[i] : 0.f;
+        double rs = 0.0;
+        float ev[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int64_t t = t0 + (c < 4 ? tx * 4 + c : 64 + tx * 4 + (c - 4));
+            const float u = acc[r][c] + bi;
+            float e = expf(u);
+            if (t >= A.T) e = 0.f;
+            bad |= !(e <= 3.0e38f);
+            rs += (double)e;
+            ev[c] = (float)(A.dt * (double)e);
+        }
+        // the 16 threads with the same ty share these rows
+#pragma unroll
+        for (int off = 8; off >= 1; off >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, off);
+        if (i < n) {
+            float* dst = A.E + (int64_t)i * A.Tpad + t0;
+            *reinterpret_cast<float4*>(dst + tx * 4) = make_float4(ev[0], ev[1], ev[2], ev[3]);
+            *reinterpret_cast<float4*>(dst + 64 + tx * 4) = make_float4(ev[4], ev[5], ev[6], ev[7]);
+            if (tx == 0) A.part_e[(int64_t)i * gridDim.x + blockIdx.x] = rs;
+        }
+    }
+    if (bad) atomicOr(A.flags, 1);
+}
+
+struct SimtGArgs {
+    int32_t n;
+    int64_t Tpad;
+    int64_t k_per_split;
+    const float* E;   // [n][Tpad]
+    const float* X;   // [n][Tpad]
+    float* part_g;    // [nsplit][n][n]
+};
+
+// part_g[s][i][j] = sum over bins of split s of E[i][t] X[j][t].  Both operands K contiguous.
+__global__ void __launch_bounds__(ST) simt_grad_kernel(const __grid_constant__ SimtGArgs A) {
+    __shared__ __align__(16) float As[2][SK][SB];
+    __shared__ __align__(16) float Bs[2][SK][SB];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int32_t i0 = blockIdx.y * SB, j0 = blockIdx.x * SB;
+    const int64_t kb = (int64_t)blockIdx.z * A.k_per_split;
+    const int64_t ke = min(kb + A.k_per_split, A.Tpad);
+    const int32_t n = A.n;
+    float acc[8][8], tot[8][8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = tot[r][c] = 0.f;
+    const int l_row = tid >> 2, l_col = (tid & 3) * 4;  // rows l_row, l_row + 64; k l_col..+3
+    float4 ra[2], rb[2];
+    auto load = [&](int64_t k0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int32_t i = i0 + l_row + 64 * h, j = j0 + l_row + 64 * h;
+            ra[h] = (i < n) ? *reinterpret_cast<const float4*>(A.E + (int64_t)i * A.Tpad + k0 + l_col)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+            rb[h] = (j < n) ? *reinterpret_cast<const float4*>(A.X + (int64_t)j * A.Tpad + k0 + l_col)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = l_row + 64 * h;
+            As[buf][l_col + 0][r] = ra[h].x;
+            As[buf][l_col + 1][r] = ra[h].y;
+            As[buf][l_col + 2][r] = ra[h].z;
+            As[buf][l_col + 3][r] = ra[h].w;
+            Bs[buf][l_col + 0][r] = rb[h].x;
+            Bs[buf][l_col + 1][r] = rb[h].y;
+            Bs[buf][l_col + 2][r] = rb[h].z;
+            Bs[buf][l_col + 3][r] = rb[h].w;
+        }
+    };
+    if (kb < ke) {
+        load(kb);
+        store(0);
+    }
+    __syncthreads();
+    int64_t since = 0;
+    for (int64_t k0 = kb; k0 < ke; k0 += SK) {
+        const int cur = (int)(((k0 - kb) / SK) & 1);
+        const bool more = k0 + SK < ke;
+        if (more) load(k0 + SK);
+#pragma unroll
+        for (int k = 0; k < SK; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][k][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][k][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][k][64 + tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+        }
+        since += SK;
+        if (since == G_INNER) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    tot[r][c] += acc[r][c];
+                    acc[r][c] = 0.f;
+                }
+            since = 0;
+        }
+        if (more) store(cur ^ 1);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int32_t i = i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4));
+        if (i >= n) continue;
+        float* dst = A.part_g + ((int64_t)blockIdx.z * n + i) * n;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int32_t j = j0 + (c < 4 ? tx * 4 + c : 64 + tx * 4 + (c - 4));
+            if (j < n) dst[j] = tot[r][c] + acc[r][c];
+        }
+    }
+}
+
+int grad_nsplit(const glm_ctx* c) {
+    const int64_t tiles = (int64_t)((c->pb.n + SB - 1) / SB) * ((c->pb.n + SB - 1) / SB);
+    int64_t s = (4 * (int64_t)c->sm_count + tiles - 1) / tiles;
+    const int64_t kmax = c->pb.Tpad / SK;
+    if (s > kmax) s = kmax;
+    if (s < 1) s = 1;
+    if (s > 256) s = 256;
+    return (int)s;
+}
+
+cudaError_t launch_simt_u_epilogue(glm_ctx* c, const float* W, const float* b) {
+    const Problem& P = c->pb;
+    SimtUArgs A;
+    A.n = P.n;
+    A.T = P.T;
+    A.Tpad = P.Tpad;
+    A.dt = P.dt;
+    A.W = W;
+    A.b = b;
+    A.X = reinterpret_cast<const float*>(c->buf.X);
+    A.E = reinterpret_cast<float*>(c->buf.E);
+    A.part_e = c->buf.part_e;
+    A.flags = c->buf.flags;
+    dim3 grid((unsigned)(P.Tpad / SB), (P.n + SB - 1) / SB);
+    simt_u_kernel<<<grid, ST, 0, c->stream>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_simt_grad(glm_ctx* c) {
+    const Problem& P = c->pb;
+    const int ns = grad_nsplit(c);
+    SimtGArgs A;
+    A.n = P.n;
+    A.Tpad = P.Tpad;
+    int64_t kps = (P.Tpad + ns - 1) / ns;
+    kps = ((kps + G_INNER - 1) / G_INNER) * G_INNER;
+    A.k_per_split = kps;
+    A.E = reinterpret_cast<const float*>(c->buf.E);
+    A.X = reinterpret_cast<const float*>(c->buf.X);
+    A.part_g = c->buf.part_g;
+    dim3 grid((P.n + SB - 1) / SB, (P.n + SB - 1) / SB, ns);
+    simt_grad_kernel<<<grid, ST, 0, c->stream>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace glm
