@@ -173,7 +173,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     device = local if ws > 1 else 0
     torch.cuda.set_device(device)
-    prec = args.prec or glm.available_precisions()[-1]
+    prec = args.prec or "bf16"
     cfg = dict(synth.WORKLOADS[args.workload])
     w = synth.make_workload(args.workload, seed=cfg["seed"] + rank)  # independent recording per rank
     n, T = w["n"], w["n_bins"]

@@ -44,7 +44,7 @@ SIGNATURES = {
 }
 
 # precisions this build implements
-AVAILABLE_PRECISIONS = ("f32",)
+AVAILABLE_PRECISIONS = ("f32", "bf16", "f16")
 
 
 def available_precisions():

@@ -61,16 +61,41 @@ __global__ void seg_local_kernel(int32_t n, int64_t nseg, const int64_t* __restr
     }
 }
 
-// Thread per row, in place: seg_carry[s] <- X_j[256 s] = a^256 X_j[256 (s-1)] + local[s-1].
+// Warp per row, in place: seg_carry[s] <- X_j[256 s] = a^256 X_j[256 (s-1)] + local[s-1].
+// The segments of a row are split into 32 contiguous parts, one per lane: each lane runs the recursion
+// over its part from zero, a shuffle scan over the lanes supplies every part's true carry-in
+// (multiplier a^(256 * part length) per lane step), and each lane then rewrites its part.
 __global__ void seg_carry_kernel(int32_t n, int64_t nseg, double a_seg, double* __restrict__ seg) {
-    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (j >= n) return;
     double* p = seg + (int64_t)j * nseg;
+    const int64_t len = (nseg + 31) / 32;
+    const int64_t s0 = min((int64_t)lane * len, nseg), s1 = min(s0 + len, nseg);
     double c = 0.0;
-    for (int64_t s = 0; s < nseg; ++s) {
+    for (int64_t s = s0; s < s1; ++s) c = fma(a_seg, c, p[s]);  // this part's contribution at its end
+    // multiplier across one full part: a_seg^len (parts shorter than len only occur at the end)
+    double mul = 1.0, base = a_seg;
+    for (int64_t e = len; e > 0; e >>= 1) {
+        if (e & 1) mul *= base;
+        base *= base;
+    }
+    // inclusive scan over lanes of carry_out(l) = mul * carry_out(l-1) + c(l)
+    double v = c, m = mul;
+    for (int d = 1; d < 32; d <<= 1) {
+        const double o = __shfl_up_sync(0xffffffffu, v, d);
+        const double om = __shfl_up_sync(0xffffffffu, m, d);
+        if (lane >= d) {
+            v = fma(m, o, v);
+            m = m * om;
+        }
+    }
+    double cin = __shfl_up_sync(0xffffffffu, v, 1);
+    if (lane == 0) cin = 0.0;
+    for (int64_t s = s0; s < s1; ++s) {
         const double l = p[s];
-        p[s] = c;
-        c = fma(a_seg, c, l);
+        p[s] = cin;
+        cin = fma(a_seg, cin, l);
     }
 }
 
@@ -230,7 +255,7 @@ cudaError_t launch_carry(glm_ctx* c) {
     seg_local_kernel<<<P.n, 256, 0, c->stream>>>(P.n, P.nseg, c->buf.offs, c->buf.bins, c->buf.pow_seg,
                                                  c->buf.seg_carry, c->buf.seg_first);
     const double a_seg = std::exp(-(double)SEG * P.dt / P.tau);
-    seg_carry_kernel<<<(P.n + 127) / 128, 128, 0, c->stream>>>(P.n, P.nseg, a_seg, c->buf.seg_carry);
+    seg_carry_kernel<<<(P.n + 3) / 4, 128, 0, c->stream>>>(P.n, P.nseg, a_seg, c->buf.seg_carry);
     return cudaGetLastError();
 }
 

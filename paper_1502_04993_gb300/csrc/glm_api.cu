@@ -284,8 +284,10 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
         return fail(c, GLM_ERR_INVALID_ARG, "dt and tau must be finite and > 0");
     if (prec != GLM_PREC_F32 && prec != GLM_PREC_BF16 && prec != GLM_PREC_F16)
         return fail(c, GLM_ERR_INVALID_ARG, "unknown precision");
-    if (prec != GLM_PREC_F32)
-        return fail(c, GLM_ERR_UNSUPPORTED, "tensor-core precisions are not built into this library yet");
+    const bool tensor = prec != GLM_PREC_F32;
+    if (tensor && !(c->cc_major == 10 && c->cc_minor == 3))
+        return fail(c, GLM_ERR_UNSUPPORTED_ARCH, "BF16/F16 tensor-core paths need an sm_103 GPU (found sm_" +
+                                                     std::to_string(c->cc_major) + std::to_string(c->cc_minor) + ")");
     int rc = validate_spikes(c, n, n_bins, offs, bins);
     if (rc) return rc;
     DeviceGuard g(c->device);
@@ -311,11 +313,20 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
         (rc = ws_alloc_t(c, &B.qd, n)) || (rc = ws_alloc_t(c, &B.C, nn)) ||
         (rc = ws_alloc_t(c, &B.C_part, nn * spike_term_parts(c))) || (rc = ws_alloc(c, &B.X, (size_t)n * P.Tpad * esz)) ||
         (rc = ws_alloc(c, &B.E, (size_t)n * P.Tpad * esz)) ||
-        (rc = ws_alloc_t(c, &B.part_e, (size_t)n * (P.Tpad / simt_tile_t()))) ||
-        (rc = ws_alloc_t(c, &B.part_g, nn * grad_nsplit(c))) || (rc = ws_alloc_t(c, &B.flags, 4)) ||
-        (rc = ws_alloc_t(c, &B.Lrows, n)) || (rc = ws_alloc_t(c, &B.scal, 8))) {
+        (rc = ws_alloc_t(c, &B.part_e, (size_t)n * (P.Tpad / (tensor ? tc_tile_t() : simt_tile_t())))) ||
+        (rc = ws_alloc_t(c, &B.part_g, nn * (tensor ? tc_nsplit(c) : grad_nsplit(c)))) ||
+        (rc = ws_alloc_t(c, &B.flags, 4)) || (rc = ws_alloc_t(c, &B.Lrows, n)) || (rc = ws_alloc_t(c, &B.scal, 8)) ||
+        (tensor && (rc = ws_alloc(c, &B.XT, (size_t)P.Tpad * B.ldn * 2))) ||
+        (tensor && (rc = ws_alloc(c, &B.Wsplit, 2 * (size_t)n * B.ldn * 2)))) {
         free_all(c);
         return rc;
+    }
+    if (tensor) {
+        cudaError_t e = tc_prepare_maps(c);
+        if (e != cudaSuccess) {
+            free_all(c);
+            return cuda_fail(c, e, "cuTensorMapEncodeTiled");
+        }
     }
     std::vector<double> qd(n);
     for (int32_t i = 0; i < n; ++i) qd[i] = (double)(offs[i + 1] - offs[i]);
@@ -377,20 +388,29 @@ int glm_loglik_grad(glm_ctx* c, const float* W, const float* b, double* L_rows, 
     DeviceGuard g(c->device);
     double* Lr = L_rows ? L_rows : c->buf.Lrows;
     const bool want_grad = G != nullptr;
-    GLM_CK(cudaMemsetAsync(c->buf.flags, 0, sizeof(int), c->stream));
-    GLM_RUN("u_epilogue", 1, launch_simt_u_epilogue(c, W, b));
-    if (want_grad) GLM_RUN("grad", 1, launch_simt_grad(c));
-    GLM_RUN("reduce", want_grad ? 2 : 1, launch_reduce(c, W, b, Lr, G, gb, want_grad));
+    GLM_CK(cudaMemsetAsync(c->buf.flags, 0, 2 * sizeof(int), c->stream));
+    const bool tensor = c->pb.prec != GLM_PREC_F32;
+    if (tensor) {
+        GLM_RUN("u_epilogue", 2, launch_tc_u_epilogue(c, W, b));
+        if (want_grad) GLM_RUN("grad", 1, launch_tc_grad(c));
+    } else {
+        GLM_RUN("u_epilogue", 1, launch_simt_u_epilogue(c, W, b));
+        if (want_grad) GLM_RUN("grad", 1, launch_simt_grad(c));
+    }
+    const int64_t ntile = c->pb.Tpad / (tensor ? tc_tile_t() : simt_tile_t());
+    const int nsplit = tensor ? tc_nsplit(c) : grad_nsplit(c);
+    GLM_RUN("reduce", want_grad ? 2 : 1, launch_reduce(c, W, b, Lr, G, gb, want_grad, ntile, nsplit));
     if (L_total_host) {
         double* dtot = c->buf.scal;
         GLM_RUN("total", 1, launch_total(c, Lr, dtot));
         double tot = 0;
-        int flags = 0;
         GLM_CK(cudaMemcpyAsync(&tot, dtot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        GLM_CK(cudaMemcpyAsync(&flags, c->buf.flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        int fl[2] = {0, 0};
+        GLM_CK(cudaMemcpyAsync(fl, c->buf.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         GLM_CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
         *L_total_host = tot;
-        if (flags & 1) return fail(c, GLM_ERR_NONFINITE, "exp(U) overflowed or was not finite");
+        if (fl[1]) return fail(c, GLM_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
+        if (fl[0] & 1) return fail(c, GLM_ERR_NONFINITE, "exp(U) overflowed or an input was not finite");
     }
     return GLM_OK;
 }

@@ -1,6 +1,7 @@
 // Internal declarations of libglm (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -70,6 +71,7 @@ struct glm_ctx {
     glm::Problem pb;
     glm::Buffers buf;
     glm::ScanConsts sc;
+    CUtensorMap tmap[5];  // tensor-core path: W_hi, W_lo, X^T, E, X
     bool has_problem = false;
     std::string last_error;
     // tracing: event pairs per launched kernel group while profiling is on
@@ -102,7 +104,12 @@ cudaError_t launch_spike_term(glm_ctx* c);
 cudaError_t launch_simt_u_epilogue(glm_ctx* c, const float* W, const float* b);
 cudaError_t launch_simt_grad(glm_ctx* c);
 cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_rows, double* G, double* gb,
-                          bool want_grad);
+                          bool want_grad, int64_t ntile, int nsplit);
+cudaError_t tc_prepare_maps(glm_ctx* c);
+cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b);
+cudaError_t launch_tc_grad(glm_ctx* c);
+int tc_nsplit(const glm_ctx* c);
+int tc_tile_t();
 cudaError_t launch_total(glm_ctx* c, const double* L_rows, double* out1);
 
 // ---- sizes shared between the launchers and the allocator ----

@@ -69,11 +69,11 @@ __global__ void total_kernel(int32_t n, const double* __restrict__ L_rows, doubl
 }
 
 cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_rows, double* G, double* gb,
-                          bool want_grad) {
+                          bool want_grad, int64_t ntile, int nsplit) {
     const Problem& P = c->pb;
     ReduceArgs A;
     A.n = P.n;
-    A.ntile = P.Tpad / simt_tile_t();
+    A.ntile = ntile;
     A.dt = P.dt;
     A.W = W;
     A.b = b;
@@ -85,7 +85,7 @@ cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_
     reduce_rows_kernel<<<(P.n + 7) / 8, 256, 0, c->stream>>>(A);
     if (want_grad && G) {
         const int64_t nn = (int64_t)P.n * P.n;
-        reduce_grad_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(nn, grad_nsplit(c), c->buf.C,
+        reduce_grad_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(nn, nsplit, c->buf.C,
                                                                               c->buf.part_g, G);
     }
     return cudaGetLastError();

@@ -95,16 +95,18 @@ __global__ void __launch_bounds__(ST_THREADS) spike_term_kernel(const __grid_con
         for (int k = 0; k < ST_KI; ++k) {
             const int32_t i = i_base + threadIdx.x + k * ST_THREADS;
             if (i >= A.n) continue;
-            int64_t cur = A.offs[i] + A.seg_first[(int64_t)i * A.nseg + sc];
-            const int64_t end = A.offs[i + 1];
+            // this row's spikes in [tb, te) are bins[k0 .. k1): independent loads, no pointer chase
+            const int64_t o0 = A.offs[i];
+            const int64_t k0 = o0 + A.seg_first[(int64_t)i * A.nseg + sc];
+            const int64_t sn = min(sp1, sc + ST_SUBSEGS);
+            const int64_t k1 = (sn < A.nseg) ? o0 + A.seg_first[(int64_t)i * A.nseg + sn] : A.offs[i + 1];
             float sh[8];
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj) sh[jj] = 0.f;
             int cnt = 0;
-            while (cur < end) {
-                const int64_t t = A.bins[cur];
-                if (t >= te) break;
-                ++cur;
+#pragma unroll 4
+            for (int64_t kk = k0; kk < k1; ++kk) {
+                const int64_t t = __ldg(A.bins + kk);
                 const float4* src = reinterpret_cast<const float4*>(Xs + (int64_t)swz((int)(t - tb)) * 8);
                 const float4 x0 = src[0], x1 = src[1];
                 sh[0] += x0.x; sh[1] += x0.y; sh[2] += x0.z; sh[3] += x0.w;

@@ -1,0 +1,455 @@
+// Tensor-core (tcgen05) form of the two contractions, for X and the rates held in BF16 or FP16:
+//   MODE 0, steps a3/a4:  U = b 1^T + (W_hi + W_lo) X  (Eq. 3; W split into two 16-bit parts so the
+//                         product keeps ~16 significant bits of W), link in the epilogue (Eq. 5):
+//                         E[i][t] = dt exp(U_i[t]) stored 16-bit, FP64 per-(row, 256-bin tile) sums of exp(U).
+//   MODE 1, step a5:      P_s = E X^T over a split s of the bins (FP32 per split, FP64 across splits later).
+// Output tiles are 128 x 256 with an FP32 accumulator in tensor memory (TMEM); both operands are K-major
+// and arrive by TMA with 128-byte swizzling.  One persistent block per SM, 6 warps:
+//   warp 0      TMA producer (one thread)
+//   warp 1      TMEM owner and MMA issuer (one thread)
+//   warps 2-5   epilogue: TMEM -> registers -> link / partial sums -> global
+// Two TMEM accumulators (2 x 256 columns) let the epilogue of one tile overlap the MMAs of the next.
+// Every wait is bounded; on a timeout the block raises flags[1], drains its own copies and MMAs, frees
+// its TMEM and exits.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+
+#include "glm_internal.h"
+#include "tc_ptx.cuh"
+
+namespace glm {
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int NUM_THREADS = 192;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t A_BYTES = BM * BK * 2;
+constexpr uint32_t B_BYTES = BN * BK * 2;
+
+template <int MODE>
+struct Cfg {
+    static constexpr int NA = (MODE == 0) ? 2 : 1;
+    static constexpr int STAGES = (MODE == 0) ? 3 : 4;
+    static constexpr uint32_t STAGE_BYTES = NA * A_BYTES + B_BYTES;
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 512;
+};
+
+struct TcArgs {
+    int32_t n;
+    int64_t T, Tpad;
+    int32_t mt, nt;
+    int64_t units;
+    int32_t kb_per_unit;  // MODE 0: k-blocks over the neurons; MODE 1: k-blocks per split
+    int64_t kb_total;     // MODE 1: k-blocks over the bins
+    uint32_t idesc;
+    double dt;
+    const float* b;
+    void* E;
+    double* part_e;
+    int64_t ntile;
+    float* part_g;
+    int* flags;
+    uint64_t limit_ns;
+};
+
+struct Unit {
+    int32_t m0, n0;
+    int64_t kb0, kb1, split;
+};
+
+template <int MODE>
+__device__ __forceinline__ Unit decode(const TcArgs& A, int64_t u) {
+    Unit r;
+    if (MODE == 0) {
+        r.m0 = (int32_t)(u % A.mt) * BM;
+        r.n0 = (int32_t)(u / A.mt) * BN;
+        r.kb0 = 0;
+        r.kb1 = A.kb_per_unit;
+        r.split = 0;
+    } else {
+        const int64_t tiles = (int64_t)A.mt * A.nt;
+        const int64_t tile = u % tiles;
+        r.split = u / tiles;
+        r.m0 = (int32_t)(tile % A.mt) * BM;
+        r.n0 = (int32_t)(tile / A.mt) * BN;
+        r.kb0 = r.split * A.kb_per_unit;
+        r.kb1 = min(r.kb0 + A.kb_per_unit, A.kb_total);
+    }
+    return r;
+}
+
+template <typename T16>
+__device__ __forceinline__ uint32_t pack16(float lo, float hi);
+template <>
+__device__ __forceinline__ uint32_t pack16<__nv_bfloat16>(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+template <>
+__device__ __forceinline__ uint32_t pack16<__half>(float lo, float hi) {
+    __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+template <int MODE, typename T16>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
+                   const __grid_constant__ CUtensorMap mapB, const __grid_constant__ TcArgs A) {
+    using C = Cfg<MODE>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE_BYTES);
+    uint64_t* empty = full + C::STAGES;
+    uint64_t* tfull = empty + C::STAGES;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* done = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            tc::mbar_init(&tfull[a], 1);
+            tc::mbar_init(&tempty[a], 4);
+        }
+        tc::mbar_init(done, 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 0 && lane == 0) {
+        tc::prefetch_tensormap(&mapA0);
+        if (C::NA == 2) tc::prefetch_tensormap(&mapA1);
+        tc::prefetch_tensormap(&mapB);
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tmem_slot, TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    auto raise = [&]() {
+        *abort_flag = 1;
+        atomicOr(A.flags + 1, 1);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued_phase[C::STAGES];
+            for (int s = 0; s < C::STAGES; ++s) issued_phase[s] = -1;
+            bool ok = true;
+            for (int64_t u = blockIdx.x; u < A.units && ok; u += gridDim.x) {
+                const Unit w = decode<MODE>(A, u);
+                for (int64_t kb = w.kb0; kb < w.kb1; ++kb) {
+                    if (!tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag, A.limit_ns)) {
+                        raise();
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* sa = smem + stage * C::STAGE_BYTES;
+                    tc::mbar_arrive_expect_tx(&full[stage], C::STAGE_BYTES);
+                    const int32_t kx = (int32_t)(kb * BK);
+                    tc::tma_load_2d(sa, &mapA0, kx, w.m0, &full[stage]);
+                    if (C::NA == 2) tc::tma_load_2d(sa + A_BYTES, &mapA1, kx, w.m0, &full[stage]);
+                    tc::tma_load_2d(sa + C::NA * A_BYTES, &mapB, kx, w.n0, &full[stage]);
+                    issued_phase[stage] = (int)phase;
+                    if (++stage == C::STAGES) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+            }
+            // drain: every issued copy has landed before the block may exit
+            volatile int never = 0;
+            for (int s = 0; s < C::STAGES; ++s)
+                if (issued_phase[s] >= 0) tc::mbar_wait(&full[s], (uint32_t)issued_phase[s], &never, A.limit_ns);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            int stage = 0;
+            uint32_t phase = 0;
+            int it = 0;
+            bool ok = true;
+            for (int64_t u = blockIdx.x; u < A.units && ok; u += gridDim.x, ++it) {
+                const Unit w = decode<MODE>(A, u);
+                const int acc = it & 1;
+                const uint32_t acc_phase = (uint32_t)((it >> 1) & 1);
+                if (!tc::mbar_wait(&tempty[acc], acc_phase ^ 1, abort_flag, A.limit_ns)) {
+                    raise();
+                    break;
+                }
+                tc::tc_fence_after();
+                const uint32_t d = tmem_base + (uint32_t)(acc * BN);
+                for (int64_t kb = w.kb0; kb < w.kb1; ++kb) {
+                    if (!tc::mbar_wait(&full[stage], phase, abort_flag, A.limit_ns)) {
+                        raise();
+                        ok = false;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                    const uint32_t sa = tc::smem_u32(smem + stage * C::STAGE_BYTES);
+                    const uint64_t da0 = tc::sw128_desc(sa);
+                    const uint64_t da1 = tc::sw128_desc(sa + A_BYTES);
+                    const uint64_t db = tc::sw128_desc(sa + C::NA * A_BYTES);
+#pragma unroll
+                    for (int k = 0; k < BK / 16; ++k) {
+                        const uint32_t first = (kb == w.kb0 && k == 0) ? 0u : 1u;
+                        tc::mma_f16(d, da0 + 2 * k, db + 2 * k, A.idesc, first);
+                        if (C::NA == 2) tc::mma_f16(d, da1 + 2 * k, db + 2 * k, A.idesc, 1u);
+                    }
+                    tc::mma_commit(&empty[stage]);
+                    if (++stage == C::STAGES) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+                if (!ok) break;
+                tc::mma_commit(&tfull[acc]);
+            }
+            // drain: all issued MMAs have completed before TMEM is released
+            tc::mma_commit(done);
+            volatile int never = 0;
+            tc::mbar_wait(done, 0, &never, A.limit_ns);
+        }
+    } else {
+        // ---------------- epilogue ----------------
+        const int q = warp & 3;
+        const int row = q * 32 + lane;
+        int it = 0;
+        for (int64_t u = blockIdx.x; u < A.units; u += gridDim.x, ++it) {
+            const Unit w = decode<MODE>(A, u);
+            const int acc = it & 1;
+            const uint32_t acc_phase = (uint32_t)((it >> 1) & 1);
+            if (!tc::mbar_wait(&tfull[acc], acc_phase, abort_flag, A.limit_ns)) {
+                raise();
+                break;
+            }
+            tc::tc_fence_after();
+            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+            const int32_t i = w.m0 + row;
+            if (MODE == 0) {
+                const float bi = (i < A.n) ? A.b[i] : 0.f;
+                const float dtf = (float)A.dt;
+                double rsum = 0.0;
+                bool bad = false;
+                T16* erow = reinterpret_cast<T16*>(A.E) + (int64_t)i * A.Tpad + w.n0;
+#pragma unroll 1
+                for (int c = 0; c < BN / 32; ++c) {
+                    uint32_t r[32];
+                    tc::tmem_ld32(taddr + c * 32, r);
+                    tc::tmem_ld_wait();
+                    float s = 0.f;
+                    uint32_t pk[16];
+#pragma unroll
+                    for (int e = 0; e < 32; e += 2) {
+                        const int64_t t = (int64_t)w.n0 + c * 32 + e;
+                        float e0 = __expf(__uint_as_float(r[e]) + bi);
+                        float e1 = __expf(__uint_as_float(r[e + 1]) + bi);
+                        if (t >= A.T) e0 = 0.f;
+                        if (t + 1 >= A.T) e1 = 0.f;
+                        bad |= !(e0 <= 3.0e38f) || !(e1 <= 3.0e38f);
+                        s += e0 + e1;
+                        pk[e >> 1] = pack16<T16>(dtf * e0, dtf * e1);
+                    }
+                    rsum += (double)s;
+                    if (i < A.n) {
+                        uint4* dst = reinterpret_cast<uint4*>(erow + c * 32);
+#pragma unroll
+                        for (int v = 0; v < 4; ++v)
+                            dst[v] = make_uint4(pk[4 * v], pk[4 * v + 1], pk[4 * v + 2], pk[4 * v + 3]);
+                    }
+                }
+                if (i < A.n) A.part_e[(int64_t)i * A.ntile + w.n0 / BN] = rsum;
+                if (bad) atomicOr(A.flags, 1);
+            } else {
+                float* grow = A.part_g + ((int64_t)w.split * A.n + i) * A.n;
+#pragma unroll 1
+                for (int c = 0; c < BN / 32; ++c) {
+                    uint32_t r[32];
+                    tc::tmem_ld32(taddr + c * 32, r);
+                    tc::tmem_ld_wait();
+                    if (i < A.n) {
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) {
+                            const int32_t j = w.n0 + c * 32 + e;
+                            if (j < A.n) grow[j] = __uint_as_float(r[e]);
+                        }
+                    }
+                }
+            }
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&tempty[acc]);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem_base, TMEM_COLS);
+    }
+}
+
+template <typename T16>
+__global__ void split_w_kernel(int32_t n, int64_t ldk, const float* __restrict__ W, T16* __restrict__ hi,
+                               T16* __restrict__ lo, int* flags) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * ldk) return;
+    const int64_t i = e / ldk, k = e % ldk;
+    float w = 0.f;
+    if (k < n) w = W[i * n + k];
+    if (!isfinite(w)) atomicOr(flags, 1);
+    T16 h, l;
+    if constexpr (sizeof(T16) == 2 && std::is_same<T16, __nv_bfloat16>::value) {
+        h = __float2bfloat16_rn(w);
+        l = __float2bfloat16_rn(w - __bfloat162float(h));
+    } else {
+        h = __float2half_rn(w);
+        l = __float2half_rn(w - __half2float(h));
+    }
+    hi[e] = h;
+    lo[e] = l;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2-D map over a row-major matrix [rows][inner] with row stride ld elements; box = 64 x box_rows.
+bool encode_map(CUtensorMap* m, bool bf16, const void* base, uint64_t inner, uint64_t rows, uint64_t ld,
+                uint32_t box_rows) {
+    auto fn = get_encode();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {inner, rows};
+    const cuuint64_t strides[1] = {ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                    const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int tc_nsplit(const glm_ctx* c) {
+    const int64_t tiles = (int64_t)((c->pb.n + BM - 1) / BM) * ((c->pb.n + BN - 1) / BN);
+    const int64_t kb_total = (c->pb.T + BK - 1) / BK;
+    int64_t s = (4 * (int64_t)c->sm_count + tiles - 1) / tiles;
+    if (s > kb_total) s = kb_total;
+    if (s < 1) s = 1;
+    const int64_t kps = (kb_total + s - 1) / s;
+    return (int)((kb_total + kps - 1) / kps);  // no empty split
+}
+
+int tc_tile_t() { return BN; }
+
+cudaError_t tc_prepare_maps(glm_ctx* c) {
+    const Problem& P = c->pb;
+    const bool bf = P.prec == GLM_PREC_BF16;
+    const int64_t ldk = c->buf.ldn;
+    const size_t wsz = (size_t)P.n * ldk * 2;
+    const uint8_t* Wsplit = reinterpret_cast<const uint8_t*>(c->buf.Wsplit);
+    bool ok = encode_map(&c->tmap[0], bf, Wsplit, P.n, P.n, ldk, BM) &&
+              encode_map(&c->tmap[1], bf, Wsplit + wsz, P.n, P.n, ldk, BM) &&
+              encode_map(&c->tmap[2], bf, c->buf.XT, P.n, P.T, c->buf.ldn, BN) &&
+              encode_map(&c->tmap[3], bf, c->buf.E, P.T, P.n, P.Tpad, BM) &&
+              encode_map(&c->tmap[4], bf, c->buf.X, P.T, P.n, P.Tpad, BN);
+    return ok ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int MODE, typename T16>
+static cudaError_t run(glm_ctx* c, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b,
+                       const TcArgs& A) {
+    using Cf = Cfg<MODE>;
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<MODE, T16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Cf::SMEM);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = A.units < c->sm_count ? A.units : c->sm_count;
+    tc_gemm_kernel<MODE, T16><<<(unsigned)grid, NUM_THREADS, Cf::SMEM, c->stream>>>(a0, a1, b, A);
+    return cudaGetLastError();
+}
+
+static TcArgs base_args(glm_ctx* c) {
+    const Problem& P = c->pb;
+    TcArgs A;
+    A.n = P.n;
+    A.T = P.T;
+    A.Tpad = P.Tpad;
+    A.dt = P.dt;
+    A.flags = c->buf.flags;
+    A.limit_ns = 4000000000ull;  // 4 s per wait
+    A.idesc = tc::idesc_f16(P.prec == GLM_PREC_BF16 ? 1u : 0u, BM, BN);
+    A.b = nullptr;
+    A.E = nullptr;
+    A.part_e = nullptr;
+    A.part_g = nullptr;
+    A.ntile = P.Tpad / BN;
+    A.kb_total = 0;
+    return A;
+}
+
+cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b) {
+    const Problem& P = c->pb;
+    const int64_t ldk = c->buf.ldn;
+    const int64_t total = (int64_t)P.n * ldk;
+    const size_t wsz = (size_t)P.n * ldk;
+    if (P.prec == GLM_PREC_BF16) {
+        auto* hi = reinterpret_cast<__nv_bfloat16*>(c->buf.Wsplit);
+        split_w_kernel<__nv_bfloat16><<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(P.n, ldk, W, hi,
+                                                                                             hi + wsz, c->buf.flags);
+    } else {
+        auto* hi = reinterpret_cast<__half*>(c->buf.Wsplit);
+        split_w_kernel<__half><<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(P.n, ldk, W, hi, hi + wsz,
+                                                                                      c->buf.flags);
+    }
+    TcArgs A = base_args(c);
+    A.mt = (P.n + BM - 1) / BM;
+    A.nt = (int32_t)(P.Tpad / BN);
+    A.units = (int64_t)A.mt * A.nt;
+    A.kb_per_unit = (P.n + BK - 1) / BK;
+    A.b = b;
+    A.E = c->buf.E;
+    A.part_e = c->buf.part_e;
+    if (P.prec == GLM_PREC_BF16) return run<0, __nv_bfloat16>(c, c->tmap[0], c->tmap[1], c->tmap[2], A);
+    return run<0, __half>(c, c->tmap[0], c->tmap[1], c->tmap[2], A);
+}
+
+cudaError_t launch_tc_grad(glm_ctx* c) {
+    const Problem& P = c->pb;
+    TcArgs A = base_args(c);
+    A.mt = (P.n + BM - 1) / BM;
+    A.nt = (P.n + BN - 1) / BN;
+    const int ns = tc_nsplit(c);
+    A.kb_total = (P.T + BK - 1) / BK;
+    A.kb_per_unit = (int32_t)((A.kb_total + ns - 1) / ns);
+    A.units = (int64_t)A.mt * A.nt * ns;
+    A.part_g = c->buf.part_g;
+    if (P.prec == GLM_PREC_BF16) return run<1, __nv_bfloat16>(c, c->tmap[3], c->tmap[3], c->tmap[4], A);
+    return run<1, __half>(c, c->tmap[3], c->tmap[3], c->tmap[4], A);
+}
+
+}  // namespace glm
