@@ -182,6 +182,9 @@ class GLM:
         dev = f"cuda:{self.device}"
         W = W.to(device=dev, dtype=torch.float32).contiguous()
         b = b.to(device=dev, dtype=torch.float32).contiguous()
+        if self.n is None:  # no problem yet: let the library report it
+            self._check(self.lib.glm_loglik_grad(self.h, _ptr(W), _ptr(b), None, None, None, None),
+                        "glm_loglik_grad")
         out = out or {}
         L_rows = out.get("L_rows")
         if L_rows is None:

@@ -3,10 +3,11 @@
 //
 //   carry pass  (FP64, O(q + n * nseg)):  per row and 256-bin segment, X at the segment start and the
 //               index of the first spike in or after the segment.
-//   write pass  (FP32 scan, HBM-write bound):  one warp per (8 rows, 4096-bin chunk); the segments of
-//               a chunk are scanned in order, starting from the FP64 carry, and stored as
+//   write pass  (FP32 scan, HBM-write bound):  the segments of a 4096-bin chunk are scanned in order,
+//               starting from the FP64 carry, and stored as
 //                 F32:    X row-major [n][Tpad]
-//                 16-bit: X row-major [n][Tpad] and X^T [Tpad][ldn] (the K-major operand of U = W X)
+//                 16-bit: X_hi row-major [n][Tpad] (operand of E X^T) and X_hi^T, X_lo^T [Tpad][ldn]
+//                         (K-major operands of U = W X; X_lo = X - X_hi rounded once more)
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -128,10 +129,9 @@ struct FilterArgs {
     void* XT;
 };
 
-// MODE 0: F32 X.  MODE 1: 16-bit X and X^T (T16 = __nv_bfloat16 or __half).
-template <int MODE, typename T16>
-__global__ void __launch_bounds__(FW_WARPS * 32) filter_cache_kernel(const __grid_constant__ ScanConsts K,
-                                                                     const __grid_constant__ FilterArgs A) {
+// F32 X, one warp per (8 rows, 4096-bin chunk).
+__global__ void __launch_bounds__(FW_WARPS * 32) filter_cache_f32_kernel(const __grid_constant__ ScanConsts K,
+                                                                         const __grid_constant__ FilterArgs A) {
     const int lane = threadIdx.x & 31;
     const int64_t wg = (int64_t)blockIdx.x * FW_WARPS + (threadIdx.x >> 5);
     const int64_t c = wg / A.ngroups;
@@ -147,8 +147,7 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache_kernel(const __gri
         const int32_t r = g * 8 + k;
         if (r < A.n) {
             xs[k] = (float)A.seg_carry[(int64_t)r * A.nseg + s0];
-            const int64_t o0 = A.offs[r];
-            cur[k] = o0 + A.seg_first[(int64_t)r * A.nseg + s0];
+            cur[k] = A.offs[r] + A.seg_first[(int64_t)r * A.nseg + s0];
             end[k] = A.offs[r + 1];
         } else {
             xs[k] = 0.f;
@@ -159,40 +158,116 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache_kernel(const __gri
     for (int64_t s = s0; s < s1; ++s) {
         const int64_t t0 = s * SEG;
         const int64_t tl = t0 + 8 * lane;
-        uint32_t pk[8][4];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int32_t r = g * 8 + k;
             const uint32_t bits = seg_bits(A.bins, cur[k], end[k], t0, lane);
             float v[8];
             xs[k] = seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v);
-            if (MODE == 0) {
-                if (r < A.n) {
-                    float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(A.X) + (int64_t)r * A.Tpad + tl);
-                    dst[0] = make_float4(v[0], v[1], v[2], v[3]);
-                    dst[1] = make_float4(v[4], v[5], v[6], v[7]);
-                }
-            } else {
-#pragma unroll
-                for (int p = 0; p < 4; ++p) pk[k][p] = pack2<T16>(v[2 * p], v[2 * p + 1]);
-                if (r < A.n) {
-                    uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<T16*>(A.X) + (int64_t)r * A.Tpad + tl);
-                    *dst = make_uint4(pk[k][0], pk[k][1], pk[k][2], pk[k][3]);
-                }
+            if (r < A.n) {
+                float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(A.X) + (int64_t)r * A.Tpad + tl);
+                dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+                dst[1] = make_float4(v[4], v[5], v[6], v[7]);
             }
         }
-        if (MODE == 1) {
-            // 8x8 transpose in registers: for bin m, the 8 rows of this group are contiguous in X^T.
+    }
+}
+
+// 16-bit caches: X_hi row-major [n][Tpad] (operand of E X^T), and X_hi^T, X_lo^T [Tpad][ldn] with
+// X_lo = X - X_hi rounded again (operands of U = W X).  Block = 8 warps = 64 rows x one 4096-bin chunk.
+// Per 256-bin segment each warp scans its 8 rows, stores X_hi rows directly, and drops the transposed
+// 8 x 8 blocks into a shared tile [256 bins][64 rows] whose 16-byte chunks are XOR-swizzled by bin, so
+// that the block then writes every X^T row segment as one 128-byte line.
+constexpr int F16_WARPS = 8;
+
+__device__ __forceinline__ uint32_t trans_word(const uint32_t (&pk)[8][4], int m, int qd) {
+    const uint32_t sel = (m & 1) ? 0x7632u : 0x5410u;
+    return __byte_perm(pk[2 * qd][m >> 1], pk[2 * qd + 1][m >> 1], sel);
+}
+
+template <typename T16>
+__device__ __forceinline__ float to_f(T16 v);
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <>
+__device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
+
+template <typename T16>
+__device__ __forceinline__ T16 from_f(float v);
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+
+template <typename T16>
+__global__ void __launch_bounds__(F16_WARPS * 32, 2) filter_cache16_kernel(const __grid_constant__ ScanConsts K,
+                                                                           const __grid_constant__ FilterArgs A) {
+    extern __shared__ uint4 f16_smem[];
+    uint4* tile_hi = f16_smem;            // [SEG][8] 16-byte chunks
+    uint4* tile_lo = f16_smem + SEG * 8;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t c = blockIdx.x;
+    const int32_t r0 = blockIdx.y * 64 + warp * 8;
+    const float pl_hi = K.pl_hi[lane], pl_lo = K.pl_lo[lane];
+    const int64_t s0 = c * CHUNK_SEGS;
+    const int64_t s1 = min(s0 + (int64_t)CHUNK_SEGS, A.nseg);
+    float xs[8];
+    int64_t cur[8], end[8];
 #pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                const uint32_t sel = (m & 1) ? 0x7632u : 0x5410u;
-                uint32_t w[4];
+    for (int k = 0; k < 8; ++k) {
+        const int32_t r = r0 + k;
+        if (r < A.n) {
+            xs[k] = (float)A.seg_carry[(int64_t)r * A.nseg + s0];
+            cur[k] = A.offs[r] + A.seg_first[(int64_t)r * A.nseg + s0];
+            end[k] = A.offs[r + 1];
+        } else {
+            xs[k] = 0.f;
+            cur[k] = 0;
+            end[k] = 0;
+        }
+    }
+    T16* XT_hi = reinterpret_cast<T16*>(A.XT);
+    T16* XT_lo = XT_hi + A.Tpad * A.ldn;
+    for (int64_t s = s0; s < s1; ++s) {
+        const int64_t t0 = s * SEG;
+        const int64_t tl = t0 + 8 * lane;
+        uint32_t ph[8][4], plo[8][4];
 #pragma unroll
-                for (int qd = 0; qd < 4; ++qd) w[qd] = __byte_perm(pk[2 * qd][m >> 1], pk[2 * qd + 1][m >> 1], sel);
-                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<T16*>(A.XT) + (tl + m) * A.ldn + g * 8);
-                *dst = make_uint4(w[0], w[1], w[2], w[3]);
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t bits = seg_bits(A.bins, cur[k], end[k], t0, lane);
+            float v[8];
+            xs[k] = seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v);
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const T16 h0 = from_f<T16>(v[2 * p]), h1 = from_f<T16>(v[2 * p + 1]);
+                ph[k][p] = pack2<T16>(to_f<T16>(h0), to_f<T16>(h1));
+                plo[k][p] = pack2<T16>(v[2 * p] - to_f<T16>(h0), v[2 * p + 1] - to_f<T16>(h1));
+            }
+            if (r0 + k < A.n) {
+                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<T16*>(A.X) + (int64_t)(r0 + k) * A.Tpad + tl);
+                *dst = make_uint4(ph[k][0], ph[k][1], ph[k][2], ph[k][3]);
             }
         }
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int bin = 8 * lane + m;
+            const int slot = bin * 8 + (warp ^ (lane & 7));
+            tile_hi[slot] = make_uint4(trans_word(ph, m, 0), trans_word(ph, m, 1), trans_word(ph, m, 2),
+                                       trans_word(ph, m, 3));
+            tile_lo[slot] = make_uint4(trans_word(plo, m, 0), trans_word(plo, m, 1), trans_word(plo, m, 2),
+                                       trans_word(plo, m, 3));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int idx = e * (F16_WARPS * 32) + threadIdx.x;
+            const int bin = idx >> 3, ch = idx & 7;
+            const int slot = bin * 8 + (ch ^ ((bin >> 3) & 7));
+            const int64_t o = (t0 + bin) * A.ldn + (int64_t)blockIdx.y * 64 + ch * 8;
+            *reinterpret_cast<uint4*>(XT_hi + o) = tile_hi[slot];
+            *reinterpret_cast<uint4*>(XT_lo + o) = tile_lo[slot];
+        }
+        __syncthreads();
     }
 }
 
@@ -275,14 +350,26 @@ cudaError_t launch_filter_cache(glm_ctx* c) {
     A.seg_first = c->buf.seg_first;
     A.X = c->buf.X;
     A.XT = c->buf.XT;
-    const int64_t warps = (int64_t)A.ngroups * A.nchunks;
-    const int64_t blocks = (warps + FW_WARPS - 1) / FW_WARPS;
-    if (P.prec == GLM_PREC_F32)
-        filter_cache_kernel<0, __half><<<(unsigned)blocks, FW_WARPS * 32, 0, c->stream>>>(c->sc, A);
-    else if (P.prec == GLM_PREC_BF16)
-        filter_cache_kernel<1, __nv_bfloat16><<<(unsigned)blocks, FW_WARPS * 32, 0, c->stream>>>(c->sc, A);
-    else
-        filter_cache_kernel<1, __half><<<(unsigned)blocks, FW_WARPS * 32, 0, c->stream>>>(c->sc, A);
+    if (P.prec == GLM_PREC_F32) {
+        const int64_t warps = (int64_t)A.ngroups * A.nchunks;
+        const int64_t blocks = (warps + FW_WARPS - 1) / FW_WARPS;
+        filter_cache_f32_kernel<<<(unsigned)blocks, FW_WARPS * 32, 0, c->stream>>>(c->sc, A);
+    } else {
+        dim3 grid((unsigned)A.nchunks, (unsigned)((P.n + 63) / 64));
+        const int smem = 2 * SEG * 8 * (int)sizeof(uint4);
+        cudaError_t e;
+        if (P.prec == GLM_PREC_BF16) {
+            e = cudaFuncSetAttribute(filter_cache16_kernel<__nv_bfloat16>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            filter_cache16_kernel<__nv_bfloat16><<<grid, F16_WARPS * 32, smem, c->stream>>>(c->sc, A);
+        } else {
+            e = cudaFuncSetAttribute(filter_cache16_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem);
+            if (e != cudaSuccess) return e;
+            filter_cache16_kernel<__half><<<grid, F16_WARPS * 32, smem, c->stream>>>(c->sc, A);
+        }
+    }
     return cudaGetLastError();
 }
 

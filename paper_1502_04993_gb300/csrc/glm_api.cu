@@ -306,7 +306,7 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
     Buffers& B = c->buf;
     const size_t nn = (size_t)n * n;
     const size_t esz = (prec == GLM_PREC_F32) ? 4 : 2;
-    B.ldn = round_up(n, 8);
+    B.ldn = round_up(n, 64);
     if ((rc = ws_alloc_t(c, &B.offs, n + 1)) || (rc = ws_alloc_t(c, &B.bins, P.q > 0 ? P.q : 1)) ||
         (rc = ws_alloc_t(c, &B.seg_carry, (size_t)n * P.nseg)) ||
         (rc = ws_alloc_t(c, &B.seg_first, (size_t)n * P.nseg)) || (rc = ws_alloc_t(c, &B.pow_seg, SEG + 1)) ||
@@ -315,8 +315,8 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
         (rc = ws_alloc(c, &B.E, (size_t)n * P.Tpad * esz)) ||
         (rc = ws_alloc_t(c, &B.part_e, (size_t)n * (P.Tpad / (tensor ? tc_tile_t() : simt_tile_t())))) ||
         (rc = ws_alloc_t(c, &B.part_g, nn * (tensor ? tc_nsplit(c) : grad_nsplit(c)))) ||
-        (rc = ws_alloc_t(c, &B.flags, 4)) || (rc = ws_alloc_t(c, &B.Lrows, n)) || (rc = ws_alloc_t(c, &B.scal, 8)) ||
-        (tensor && (rc = ws_alloc(c, &B.XT, (size_t)P.Tpad * B.ldn * 2))) ||
+        (rc = ws_alloc_t(c, &B.flags, 4)) || (rc = ws_alloc_t(c, &B.Lrows, n)) || (rc = ws_alloc_t(c, &B.scal, 8)) || (rc = ws_alloc_t(c, &B.eb, n)) ||
+        (tensor && (rc = ws_alloc(c, &B.XT, 2 * (size_t)P.Tpad * B.ldn * 2))) ||
         (tensor && (rc = ws_alloc(c, &B.Wsplit, 2 * (size_t)n * B.ldn * 2)))) {
         free_all(c);
         return rc;
@@ -394,7 +394,7 @@ int glm_loglik_grad(glm_ctx* c, const float* W, const float* b, double* L_rows, 
         GLM_RUN("u_epilogue", 2, launch_tc_u_epilogue(c, W, b));
         if (want_grad) GLM_RUN("grad", 1, launch_tc_grad(c));
     } else {
-        GLM_RUN("u_epilogue", 1, launch_simt_u_epilogue(c, W, b));
+        GLM_RUN("u_epilogue", 2, launch_simt_u_epilogue(c, W, b));
         if (want_grad) GLM_RUN("grad", 1, launch_simt_grad(c));
     }
     const int64_t ntile = c->pb.Tpad / (tensor ? tc_tile_t() : simt_tile_t());

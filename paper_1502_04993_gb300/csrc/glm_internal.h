@@ -48,8 +48,8 @@ struct Buffers {
     double* C = nullptr;          // [n][n]      spike term
     double* C_part = nullptr;     // [parts][n][n]
     void* X = nullptr;            // F32: float [n][Tpad]; 16-bit: [n][Tpad]
-    void* XT = nullptr;           // 16-bit only: [Tpad][ldn]
-    int64_t ldn = 0;              // leading dim of XT (n rounded up to 8... 64)
+    void* XT = nullptr;           // 16-bit only: X_hi^T then X_lo^T, each [Tpad][ldn]
+    int64_t ldn = 0;              // leading dim of X^T and of the W parts (n rounded up to 64)
     void* E = nullptr;            // F32: float [n][Tpad]; 16-bit: [n][Tpad]   dt * exp(U)
     double* part_e = nullptr;     // [n][ntile_t]  per-(row, bin tile) sums of exp(U)
     float* part_g = nullptr;      // [nsplit][n][n] FP32 partial sums of E X^T
@@ -57,6 +57,7 @@ struct Buffers {
     int* flags = nullptr;         // [4] device error flags
     double* Lrows = nullptr;      // [n] scratch when the caller passes no L_rows
     double* scal = nullptr;       // [8] device scalars (total log-likelihood, ...)
+    double* eb = nullptr;         // [n] exp(b_i) in FP64 (plain FP32 form)
 };
 
 }  // namespace glm
@@ -71,7 +72,7 @@ struct glm_ctx {
     glm::Problem pb;
     glm::Buffers buf;
     glm::ScanConsts sc;
-    CUtensorMap tmap[5];  // tensor-core path: W_hi, W_lo, X^T, E, X
+    CUtensorMap tmap[6];  // tensor-core path: W_hi, W_lo, X_hi^T, X_lo^T, E, X_hi
     bool has_problem = false;
     std::string last_error;
     // tracing: event pairs per launched kernel group while profiling is on

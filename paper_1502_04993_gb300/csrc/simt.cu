@@ -22,6 +22,7 @@ struct SimtUArgs {
     double dt;
     const float* W;   // [n][n]
     const float* b;   // [n]
+    const double* eb; // [n]  exp(b_i) in FP64
     const float* X;   // [n][Tpad]
     float* E;         // [n][Tpad]
     double* part_e;   // [n][ntile]
@@ -91,24 +92,32 @@ __global__ void __launch_bounds__(ST) simt_u_kernel(const __grid_constant__ Simt
         if (kt + 1 < nk) store(cur ^ 1);
         __syncthreads();
     }
-    // epilogue: u = acc + b, e = exp(u); E = dt e (0 beyond T); FP64 row sums of e
+    // epilogue.  With v = (W X)_i[t]:  e^{U} = e^{b_i} (1 + expm1(v)).  e^{b_i} comes in FP64 and the
+    // integer count of bins is kept apart from the FP32 sum of expm1(v), so the part of the integral that
+    // repeats over quiet bins (U ~ b_i) carries no FP32 rounding of exp or of b + v.
+    // E = dt e (0 beyond T) in FP32; FP64 row sums of e per tile.
     bool bad = false;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
         const int32_t i = i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4));
-        const float bi = (i < n) ? A.b[i] : 0.f;
-        double rs = 0.0;
+        const double ebi = (i < n) ? A.eb[i] : 0.0;
+        const float dteb = (float)(A.dt * ebi);
+        float msum = 0.f;
+        int cnt = 0;
         float ev[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const int64_t t = t0 + (c < 4 ? tx * 4 + c : 64 + tx * 4 + (c - 4));
-            const float u = acc[r][c] + bi;
-            float e = expf(u);
-            if (t >= A.T) e = 0.f;
-            bad |= !(e <= 3.0e38f);
-            rs += (double)e;
-            ev[c] = (float)(A.dt * (double)e);
+            const float m = expm1f(acc[r][c]);
+            const bool valid = t < A.T;
+            bad |= valid && !(m <= 3.0e38f);
+            if (valid) {
+                msum += m;
+                ++cnt;
+            }
+            ev[c] = valid ? fmaf(dteb, m, dteb) : 0.f;
         }
+        double rs = ebi * ((double)cnt + (double)msum);
         // the 16 threads with the same ty share these rows
 #pragma unroll
         for (int off = 8; off >= 1; off >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, off);
@@ -231,8 +240,18 @@ int grad_nsplit(const glm_ctx* c) {
     return (int)s;
 }
 
+// exp(b_i) in FP64 for the epilogue; flags non-finite b
+__global__ void exp_bias_kernel(int32_t n, const float* __restrict__ b, double* __restrict__ eb, int* flags) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = exp((double)b[i]);
+    if (!isfinite(b[i]) || !(v <= 1e300)) atomicOr(flags, 1);
+    eb[i] = v;
+}
+
 cudaError_t launch_simt_u_epilogue(glm_ctx* c, const float* W, const float* b) {
     const Problem& P = c->pb;
+    exp_bias_kernel<<<(P.n + 255) / 256, 256, 0, c->stream>>>(P.n, b, c->buf.eb, c->buf.flags);
     SimtUArgs A;
     A.n = P.n;
     A.T = P.T;
@@ -240,6 +259,7 @@ cudaError_t launch_simt_u_epilogue(glm_ctx* c, const float* W, const float* b) {
     A.dt = P.dt;
     A.W = W;
     A.b = b;
+    A.eb = c->buf.eb;
     A.X = reinterpret_cast<const float*>(c->buf.X);
     A.E = reinterpret_cast<float*>(c->buf.E);
     A.part_e = c->buf.part_e;

@@ -171,13 +171,8 @@ cudaError_t launch_spike_term(glm_ctx* c) {
     A.seg_first = c->buf.seg_first;
     A.C_part = c->buf.C_part;
     const size_t smem = (size_t)ST_SUB * 8 * sizeof(float);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(spike_term_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    cudaError_t e = cudaFuncSetAttribute(spike_term_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     dim3 grid((P.n + 7) / 8, parts, (P.n + ST_ROWS_PER_SLICE - 1) / ST_ROWS_PER_SLICE);
     spike_term_kernel<<<grid, ST_THREADS, smem, c->stream>>>(c->sc, A);
     const int64_t nn = (int64_t)P.n * P.n;

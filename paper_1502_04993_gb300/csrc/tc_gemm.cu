@@ -1,22 +1,25 @@
-// Tensor-core (tcgen05) form of the two contractions, for X and the rates held in BF16 or FP16:
-//   MODE 0, steps a3/a4:  U = b 1^T + (W_hi + W_lo) X  (Eq. 3; W split into two 16-bit parts so the
-//                         product keeps ~16 significant bits of W), link in the epilogue (Eq. 5):
-//                         E[i][t] = dt exp(U_i[t]) stored 16-bit, FP64 per-(row, 256-bin tile) sums of exp(U).
-//   MODE 1, step a5:      P_s = E X^T over a split s of the bins (FP32 per split, FP64 across splits later).
-// Output tiles are 128 x 256 with an FP32 accumulator in tensor memory (TMEM); both operands are K-major
-// and arrive by TMA with 128-byte swizzling.  One persistent block per SM, 6 warps:
-//   warp 0      TMA producer (one thread)
-//   warp 1      TMEM owner and MMA issuer (one thread)
-//   warps 2-5   epilogue: TMEM -> registers -> link / partial sums -> global
-// Two TMEM accumulators (2 x 256 columns) let the epilogue of one tile overlap the MMAs of the next.
-// Every wait is bounded; on a timeout the block raises flags[1], drains its own copies and MMAs, frees
-// its TMEM and exits.
+// Tensor-core (tcgen05) form of the two contractions, for X and the rates held in BF16 or FP16.
+//
+//   MODE 0, steps a3/a4:  U = b 1^T + W X  (Eq. 3) from split operands W = W_hi + W_lo, X = X_hi + X_lo:
+//                         U ~ W_hi X_hi + W_lo X_hi + W_hi X_lo (the dropped W_lo X_lo is ~2^-16 of U - b),
+//                         with the link in the epilogue (Eq. 5): E[i][t] = dt exp(U_i[t]) stored 16-bit,
+//                         FP64 per-(row, 256-bin tile) sums of exp(U).
+//                         Tile 128 x 256, K step 32 (64-byte swizzle), 4 stages of (W_hi, W_lo, X_hi^T, X_lo^T),
+//                         3 MMAs per 16-wide k slice, 2 TMEM accumulators (epilogue overlaps the next tile).
+//   MODE 1, step a5:      P_s = E X^T over a split s of the bins.  Tile 256 x 256 per block as two 128 x 256
+//                         accumulators that share every X tile (A0 = E rows m0.., A1 = E rows m0+128..),
+//                         K step 64 (128-byte swizzle), 3 stages, FP32 partials per split.
+//
+// One persistent block per SM, 6 warps: warp 0 issues TMA loads, warp 1 owns TMEM and issues the MMAs
+// (one thread), warps 2-5 are the epilogue (TMEM -> registers -> global).  Every mbarrier wait is bounded;
+// on a timeout the block raises flags[1], drains its own copies and MMAs, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include <cmath>
+#include <type_traits>
 
 #include "glm_internal.h"
 #include "tc_ptx.cuh"
@@ -25,18 +28,42 @@ namespace glm {
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64;
 constexpr int NUM_THREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t A_BYTES = BM * BK * 2;
-constexpr uint32_t B_BYTES = BN * BK * 2;
+constexpr int BN = 256;
 
 template <int MODE>
-struct Cfg {
-    static constexpr int NA = (MODE == 0) ? 2 : 1;
-    static constexpr int STAGES = (MODE == 0) ? 3 : 4;
-    static constexpr uint32_t STAGE_BYTES = NA * A_BYTES + B_BYTES;
-    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 512;
+struct Cfg;
+template <>
+struct Cfg<0> {
+    static constexpr int BM = 128;            // rows per block
+    static constexpr int BK = 32;             // K elements per stage (64 bytes)
+    static constexpr int NA = 2, NB = 2;      // W_hi, W_lo ; X_hi^T, X_lo^T
+    static constexpr int STAGES = 4;
+    static constexpr int NBUF = 2;            // TMEM accumulator buffers (double buffering)
+    static constexpr uint32_t SWZ = 4;        // descriptor layout: 64-byte swizzle
+    static constexpr uint32_t SBO = 8 * 64;   // bytes between 8-row groups
+    static constexpr uint32_t A_BYTES = 128 * BK * 2;
+    static constexpr uint32_t B_BYTES = BN * BK * 2;
+};
+template <>
+struct Cfg<1> {
+    static constexpr int BM = 256;            // two 128-row halves
+    static constexpr int BK = 64;
+    static constexpr int NA = 2, NB = 1;      // E rows m0.., E rows m0+128.. ; X
+    static constexpr int STAGES = 3;
+    static constexpr int NBUF = 1;
+    static constexpr uint32_t SWZ = 2;        // 128-byte swizzle
+    static constexpr uint32_t SBO = 8 * 128;
+    static constexpr uint32_t A_BYTES = 128 * BK * 2;
+    static constexpr uint32_t B_BYTES = BN * BK * 2;
+};
+
+template <int MODE>
+struct Layout {
+    using C = Cfg<MODE>;
+    static constexpr uint32_t STAGE_BYTES = C::NA * C::A_BYTES + C::NB * C::B_BYTES;
+    static constexpr size_t SMEM = (size_t)C::STAGES * STAGE_BYTES + 1024 + 512;
 };
 
 struct TcArgs {
@@ -44,8 +71,8 @@ struct TcArgs {
     int64_t T, Tpad;
     int32_t mt, nt;
     int64_t units;
-    int32_t kb_per_unit;  // MODE 0: k-blocks over the neurons; MODE 1: k-blocks per split
-    int64_t kb_total;     // MODE 1: k-blocks over the bins
+    int32_t kb_per_unit;  // MODE 0: k-steps over the neurons; MODE 1: k-steps per split
+    int64_t kb_total;     // MODE 1: k-steps over the bins
     uint32_t idesc;
     double dt;
     const float* b;
@@ -66,7 +93,7 @@ template <int MODE>
 __device__ __forceinline__ Unit decode(const TcArgs& A, int64_t u) {
     Unit r;
     if (MODE == 0) {
-        r.m0 = (int32_t)(u % A.mt) * BM;
+        r.m0 = (int32_t)(u % A.mt) * Cfg<0>::BM;
         r.n0 = (int32_t)(u / A.mt) * BN;
         r.kb0 = 0;
         r.kb1 = A.kb_per_unit;
@@ -75,12 +102,22 @@ __device__ __forceinline__ Unit decode(const TcArgs& A, int64_t u) {
         const int64_t tiles = (int64_t)A.mt * A.nt;
         const int64_t tile = u % tiles;
         r.split = u / tiles;
-        r.m0 = (int32_t)(tile % A.mt) * BM;
+        r.m0 = (int32_t)(tile % A.mt) * Cfg<1>::BM;
         r.n0 = (int32_t)(tile / A.mt) * BN;
         r.kb0 = r.split * A.kb_per_unit;
         r.kb1 = min(r.kb0 + A.kb_per_unit, A.kb_total);
     }
     return r;
+}
+
+// Shared-memory descriptor of a K-major operand tile written by TMA with the matching swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t swz, uint32_t sbo) {
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;               // leading-dimension offset: unused for swizzled K-major
+    d |= (uint64_t)(sbo >> 4) << 32;       // stride between 8-row groups
+    d |= (uint64_t)1u << 46;               // descriptor version
+    d |= (uint64_t)swz << 61;              // swizzle mode
+    return d;
 }
 
 template <typename T16>
@@ -99,11 +136,13 @@ __device__ __forceinline__ uint32_t pack16<__half>(float lo, float hi) {
 template <int MODE, typename T16>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
-                   const __grid_constant__ CUtensorMap mapB, const __grid_constant__ TcArgs A) {
+                   const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1,
+                   const __grid_constant__ TcArgs A) {
     using C = Cfg<MODE>;
+    using L = Layout<MODE>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE_BYTES);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * L::STAGE_BYTES);
     uint64_t* empty = full + C::STAGES;
     uint64_t* tfull = empty + C::STAGES;
     uint64_t* tempty = tfull + 2;
@@ -127,8 +166,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
     if (warp == 0 && lane == 0) {
         tc::prefetch_tensormap(&mapA0);
-        if (C::NA == 2) tc::prefetch_tensormap(&mapA1);
-        tc::prefetch_tensormap(&mapB);
+        tc::prefetch_tensormap(&mapA1);
+        tc::prefetch_tensormap(&mapB0);
+        if (C::NB == 2) tc::prefetch_tensormap(&mapB1);
     }
     if (warp == 1) {
         tc::tmem_alloc(tmem_slot, TMEM_COLS);
@@ -160,12 +200,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         ok = false;
                         break;
                     }
-                    uint8_t* sa = smem + stage * C::STAGE_BYTES;
-                    tc::mbar_arrive_expect_tx(&full[stage], C::STAGE_BYTES);
-                    const int32_t kx = (int32_t)(kb * BK);
-                    tc::tma_load_2d(sa, &mapA0, kx, w.m0, &full[stage]);
-                    if (C::NA == 2) tc::tma_load_2d(sa + A_BYTES, &mapA1, kx, w.m0, &full[stage]);
-                    tc::tma_load_2d(sa + C::NA * A_BYTES, &mapB, kx, w.n0, &full[stage]);
+                    uint8_t* sa = smem + stage * L::STAGE_BYTES;
+                    tc::mbar_arrive_expect_tx(&full[stage], L::STAGE_BYTES);
+                    const int32_t kx = (int32_t)(kb * C::BK);
+                    if (MODE == 0) {
+                        tc::tma_load_2d(sa, &mapA0, kx, w.m0, &full[stage]);
+                        tc::tma_load_2d(sa + C::A_BYTES, &mapA1, kx, w.m0, &full[stage]);
+                        tc::tma_load_2d(sa + 2 * C::A_BYTES, &mapB0, kx, w.n0, &full[stage]);
+                        tc::tma_load_2d(sa + 2 * C::A_BYTES + C::B_BYTES, &mapB1, kx, w.n0, &full[stage]);
+                    } else {
+                        tc::tma_load_2d(sa, &mapA0, kx, w.m0, &full[stage]);
+                        tc::tma_load_2d(sa + C::A_BYTES, &mapA0, kx, w.m0 + 128, &full[stage]);
+                        tc::tma_load_2d(sa + 2 * C::A_BYTES, &mapB0, kx, w.n0, &full[stage]);
+                    }
                     issued_phase[stage] = (int)phase;
                     if (++stage == C::STAGES) {
                         stage = 0;
@@ -187,14 +234,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             bool ok = true;
             for (int64_t u = blockIdx.x; u < A.units && ok; u += gridDim.x, ++it) {
                 const Unit w = decode<MODE>(A, u);
-                const int acc = it & 1;
-                const uint32_t acc_phase = (uint32_t)((it >> 1) & 1);
-                if (!tc::mbar_wait(&tempty[acc], acc_phase ^ 1, abort_flag, A.limit_ns)) {
+                const int buf = (C::NBUF == 2) ? (it & 1) : 0;
+                const uint32_t buf_phase = (uint32_t)((C::NBUF == 2 ? (it >> 1) : it) & 1);
+                if (!tc::mbar_wait(&tempty[buf], buf_phase ^ 1, abort_flag, A.limit_ns)) {
                     raise();
                     break;
                 }
                 tc::tc_fence_after();
-                const uint32_t d = tmem_base + (uint32_t)(acc * BN);
+                const uint32_t d0 = tmem_base + (uint32_t)(buf * BN);
+                const uint32_t d1 = tmem_base + (uint32_t)BN;  // MODE 1: second row half
                 for (int64_t kb = w.kb0; kb < w.kb1; ++kb) {
                     if (!tc::mbar_wait(&full[stage], phase, abort_flag, A.limit_ns)) {
                         raise();
@@ -202,15 +250,22 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         break;
                     }
                     tc::tc_fence_after();
-                    const uint32_t sa = tc::smem_u32(smem + stage * C::STAGE_BYTES);
-                    const uint64_t da0 = tc::sw128_desc(sa);
-                    const uint64_t da1 = tc::sw128_desc(sa + A_BYTES);
-                    const uint64_t db = tc::sw128_desc(sa + C::NA * A_BYTES);
+                    const uint32_t sa = tc::smem_u32(smem + stage * L::STAGE_BYTES);
+                    const uint64_t da0 = smem_desc(sa, C::SWZ, C::SBO);
+                    const uint64_t da1 = smem_desc(sa + C::A_BYTES, C::SWZ, C::SBO);
+                    const uint64_t db0 = smem_desc(sa + 2 * C::A_BYTES, C::SWZ, C::SBO);
+                    const uint64_t db1 = smem_desc(sa + 2 * C::A_BYTES + C::B_BYTES, C::SWZ, C::SBO);
 #pragma unroll
-                    for (int k = 0; k < BK / 16; ++k) {
-                        const uint32_t first = (kb == w.kb0 && k == 0) ? 0u : 1u;
-                        tc::mma_f16(d, da0 + 2 * k, db + 2 * k, A.idesc, first);
-                        if (C::NA == 2) tc::mma_f16(d, da1 + 2 * k, db + 2 * k, A.idesc, 1u);
+                    for (int k = 0; k < C::BK / 16; ++k) {
+                        const uint32_t acc = (kb == w.kb0 && k == 0) ? 0u : 1u;
+                        if (MODE == 0) {
+                            tc::mma_f16(d0, da0 + 2 * k, db0 + 2 * k, A.idesc, acc);   // W_hi X_hi
+                            tc::mma_f16(d0, da1 + 2 * k, db0 + 2 * k, A.idesc, 1u);    // W_lo X_hi
+                            tc::mma_f16(d0, da0 + 2 * k, db1 + 2 * k, A.idesc, 1u);    // W_hi X_lo
+                        } else {
+                            tc::mma_f16(d0, da0 + 2 * k, db0 + 2 * k, A.idesc, acc);   // rows m0..
+                            tc::mma_f16(d1, da1 + 2 * k, db0 + 2 * k, A.idesc, acc);   // rows m0+128..
+                        }
                     }
                     tc::mma_commit(&empty[stage]);
                     if (++stage == C::STAGES) {
@@ -219,7 +274,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     }
                 }
                 if (!ok) break;
-                tc::mma_commit(&tfull[acc]);
+                tc::mma_commit(&tfull[buf]);
             }
             // drain: all issued MMAs have completed before TMEM is released
             tc::mma_commit(done);
@@ -233,16 +288,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         int it = 0;
         for (int64_t u = blockIdx.x; u < A.units; u += gridDim.x, ++it) {
             const Unit w = decode<MODE>(A, u);
-            const int acc = it & 1;
-            const uint32_t acc_phase = (uint32_t)((it >> 1) & 1);
-            if (!tc::mbar_wait(&tfull[acc], acc_phase, abort_flag, A.limit_ns)) {
+            const int buf = (C::NBUF == 2) ? (it & 1) : 0;
+            const uint32_t buf_phase = (uint32_t)((C::NBUF == 2 ? (it >> 1) : it) & 1);
+            if (!tc::mbar_wait(&tfull[buf], buf_phase, abort_flag, A.limit_ns)) {
                 raise();
                 break;
             }
             tc::tc_fence_after();
-            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
-            const int32_t i = w.m0 + row;
+            const uint32_t lane_base = tmem_base + ((uint32_t)(q * 32) << 16);
             if (MODE == 0) {
+                const uint32_t taddr = lane_base + (uint32_t)(buf * BN);
+                const int32_t i = w.m0 + row;
                 const float bi = (i < A.n) ? A.b[i] : 0.f;
                 const float dtf = (float)A.dt;
                 double rsum = 0.0;
@@ -277,24 +333,29 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 if (i < A.n) A.part_e[(int64_t)i * A.ntile + w.n0 / BN] = rsum;
                 if (bad) atomicOr(A.flags, 1);
             } else {
-                float* grow = A.part_g + ((int64_t)w.split * A.n + i) * A.n;
 #pragma unroll 1
-                for (int c = 0; c < BN / 32; ++c) {
-                    uint32_t r[32];
-                    tc::tmem_ld32(taddr + c * 32, r);
-                    tc::tmem_ld_wait();
-                    if (i < A.n) {
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t taddr = lane_base + (uint32_t)(h * BN);
+                    const int32_t i = w.m0 + h * 128 + row;
+                    float* grow = A.part_g + ((int64_t)w.split * A.n + i) * A.n;
+#pragma unroll 1
+                    for (int c = 0; c < BN / 32; ++c) {
+                        uint32_t r[32];
+                        tc::tmem_ld32(taddr + c * 32, r);
+                        tc::tmem_ld_wait();
+                        if (i < A.n) {
 #pragma unroll
-                        for (int e = 0; e < 32; ++e) {
-                            const int32_t j = w.n0 + c * 32 + e;
-                            if (j < A.n) grow[j] = __uint_as_float(r[e]);
+                            for (int e = 0; e < 32; ++e) {
+                                const int32_t j = w.n0 + c * 32 + e;
+                                if (j < A.n) grow[j] = __uint_as_float(r[e]);
+                            }
                         }
                     }
                 }
             }
             tc::tc_fence_before();
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&tempty[acc]);
+            if (lane == 0) tc::mbar_arrive(&tempty[buf]);
         }
     }
     __syncthreads();
@@ -314,7 +375,7 @@ __global__ void split_w_kernel(int32_t n, int64_t ldk, const float* __restrict__
     if (k < n) w = W[i * n + k];
     if (!isfinite(w)) atomicOr(flags, 1);
     T16 h, l;
-    if constexpr (sizeof(T16) == 2 && std::is_same<T16, __nv_bfloat16>::value) {
+    if constexpr (std::is_same<T16, __nv_bfloat16>::value) {
         h = __float2bfloat16_rn(w);
         l = __float2bfloat16_rn(w - __bfloat162float(h));
     } else {
@@ -338,26 +399,26 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-// 2-D map over a row-major matrix [rows][inner] with row stride ld elements; box = 64 x box_rows.
+// 2-D map over a row-major matrix [rows][inner] with row stride ld elements; box = box_k x box_rows.
 bool encode_map(CUtensorMap* m, bool bf16, const void* base, uint64_t inner, uint64_t rows, uint64_t ld,
-                uint32_t box_rows) {
+                uint32_t box_k, uint32_t box_rows, CUtensorMapSwizzle swz) {
     auto fn = get_encode();
     if (!fn) return false;
     const cuuint64_t dims[2] = {inner, rows};
     const cuuint64_t strides[1] = {ld * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+    const cuuint32_t box[2] = {box_k, box_rows};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
-                    const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
 }  // namespace
 
 int tc_nsplit(const glm_ctx* c) {
-    const int64_t tiles = (int64_t)((c->pb.n + BM - 1) / BM) * ((c->pb.n + BN - 1) / BN);
-    const int64_t kb_total = (c->pb.T + BK - 1) / BK;
+    const int64_t tiles = (int64_t)((c->pb.n + 255) / 256) * ((c->pb.n + BN - 1) / BN);
+    const int64_t kb_total = (c->pb.T + Cfg<1>::BK - 1) / Cfg<1>::BK;
     int64_t s = (4 * (int64_t)c->sm_count + tiles - 1) / tiles;
     if (s > kb_total) s = kb_total;
     if (s < 1) s = 1;
@@ -367,29 +428,34 @@ int tc_nsplit(const glm_ctx* c) {
 
 int tc_tile_t() { return BN; }
 
+// Maps: 0 W_hi, 1 W_lo, 2 X_hi^T, 3 X_lo^T (U = W X, 64-byte swizzle), 4 E, 5 X_hi (E X^T, 128-byte swizzle).
 cudaError_t tc_prepare_maps(glm_ctx* c) {
     const Problem& P = c->pb;
     const bool bf = P.prec == GLM_PREC_BF16;
-    const int64_t ldk = c->buf.ldn;
-    const size_t wsz = (size_t)P.n * ldk * 2;
+    const int64_t ld = c->buf.ldn;
+    const size_t wsz = (size_t)P.n * ld * 2;
+    const size_t xtsz = (size_t)P.Tpad * ld * 2;
     const uint8_t* Wsplit = reinterpret_cast<const uint8_t*>(c->buf.Wsplit);
-    bool ok = encode_map(&c->tmap[0], bf, Wsplit, P.n, P.n, ldk, BM) &&
-              encode_map(&c->tmap[1], bf, Wsplit + wsz, P.n, P.n, ldk, BM) &&
-              encode_map(&c->tmap[2], bf, c->buf.XT, P.n, P.T, c->buf.ldn, BN) &&
-              encode_map(&c->tmap[3], bf, c->buf.E, P.T, P.n, P.Tpad, BM) &&
-              encode_map(&c->tmap[4], bf, c->buf.X, P.T, P.n, P.Tpad, BN);
+    const uint8_t* XT = reinterpret_cast<const uint8_t*>(c->buf.XT);
+    const auto S64 = CU_TENSOR_MAP_SWIZZLE_64B, S128 = CU_TENSOR_MAP_SWIZZLE_128B;
+    bool ok = encode_map(&c->tmap[0], bf, Wsplit, P.n, P.n, ld, 32, 128, S64) &&
+              encode_map(&c->tmap[1], bf, Wsplit + wsz, P.n, P.n, ld, 32, 128, S64) &&
+              encode_map(&c->tmap[2], bf, XT, P.n, P.T, ld, 32, BN, S64) &&
+              encode_map(&c->tmap[3], bf, XT + xtsz, P.n, P.T, ld, 32, BN, S64) &&
+              encode_map(&c->tmap[4], bf, c->buf.E, P.T, P.n, P.Tpad, 64, 128, S128) &&
+              encode_map(&c->tmap[5], bf, c->buf.X, P.T, P.n, P.Tpad, 64, BN, S128);
     return ok ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 template <int MODE, typename T16>
-static cudaError_t run(glm_ctx* c, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b,
-                       const TcArgs& A) {
-    using Cf = Cfg<MODE>;
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<MODE, T16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Cf::SMEM);
+static cudaError_t run(glm_ctx* c, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0,
+                       const CUtensorMap& b1, const TcArgs& A) {
+    const size_t smem = Layout<MODE>::SMEM;
+    cudaError_t e =
+        cudaFuncSetAttribute(tc_gemm_kernel<MODE, T16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t grid = A.units < c->sm_count ? A.units : c->sm_count;
-    tc_gemm_kernel<MODE, T16><<<(unsigned)grid, NUM_THREADS, Cf::SMEM, c->stream>>>(a0, a1, b, A);
+    tc_gemm_kernel<MODE, T16><<<(unsigned)grid, NUM_THREADS, smem, c->stream>>>(a0, a1, b0, b1, A);
     return cudaGetLastError();
 }
 
@@ -402,7 +468,7 @@ static TcArgs base_args(glm_ctx* c) {
     A.dt = P.dt;
     A.flags = c->buf.flags;
     A.limit_ns = 4000000000ull;  // 4 s per wait
-    A.idesc = tc::idesc_f16(P.prec == GLM_PREC_BF16 ? 1u : 0u, BM, BN);
+    A.idesc = tc::idesc_f16(P.prec == GLM_PREC_BF16 ? 1u : 0u, 128, BN);
     A.b = nullptr;
     A.E = nullptr;
     A.part_e = nullptr;
@@ -427,29 +493,31 @@ cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b) {
                                                                                       c->buf.flags);
     }
     TcArgs A = base_args(c);
-    A.mt = (P.n + BM - 1) / BM;
+    A.mt = (P.n + 127) / 128;
     A.nt = (int32_t)(P.Tpad / BN);
     A.units = (int64_t)A.mt * A.nt;
-    A.kb_per_unit = (P.n + BK - 1) / BK;
+    A.kb_per_unit = (P.n + Cfg<0>::BK - 1) / Cfg<0>::BK;
     A.b = b;
     A.E = c->buf.E;
     A.part_e = c->buf.part_e;
-    if (P.prec == GLM_PREC_BF16) return run<0, __nv_bfloat16>(c, c->tmap[0], c->tmap[1], c->tmap[2], A);
-    return run<0, __half>(c, c->tmap[0], c->tmap[1], c->tmap[2], A);
+    if (P.prec == GLM_PREC_BF16)
+        return run<0, __nv_bfloat16>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
+    return run<0, __half>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
 }
 
 cudaError_t launch_tc_grad(glm_ctx* c) {
     const Problem& P = c->pb;
     TcArgs A = base_args(c);
-    A.mt = (P.n + BM - 1) / BM;
+    A.mt = (P.n + 255) / 256;
     A.nt = (P.n + BN - 1) / BN;
     const int ns = tc_nsplit(c);
-    A.kb_total = (P.T + BK - 1) / BK;
+    A.kb_total = (P.T + Cfg<1>::BK - 1) / Cfg<1>::BK;
     A.kb_per_unit = (int32_t)((A.kb_total + ns - 1) / ns);
     A.units = (int64_t)A.mt * A.nt * ns;
     A.part_g = c->buf.part_g;
-    if (P.prec == GLM_PREC_BF16) return run<1, __nv_bfloat16>(c, c->tmap[3], c->tmap[3], c->tmap[4], A);
-    return run<1, __half>(c, c->tmap[3], c->tmap[3], c->tmap[4], A);
+    if (P.prec == GLM_PREC_BF16)
+        return run<1, __nv_bfloat16>(c, c->tmap[4], c->tmap[4], c->tmap[5], c->tmap[5], A);
+    return run<1, __half>(c, c->tmap[4], c->tmap[4], c->tmap[5], c->tmap[5], A);
 }
 
 }  // namespace glm
