@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--n-bins", type=int, default=None,
+                    help="record a shorter recording of the same network (profiling captures)")
     return ap.parse_args()
 
 
@@ -175,7 +177,8 @@ def main():
     torch.cuda.set_device(device)
     prec = args.prec or "bf16"
     cfg = dict(synth.WORKLOADS[args.workload])
-    w = synth.make_workload(args.workload, seed=cfg["seed"] + rank)  # independent recording per rank
+    extra = {"n_bins": args.n_bins} if args.n_bins else {}
+    w = synth.make_workload(args.workload, seed=cfg["seed"] + rank, **extra)  # independent recording per rank
     n, T = w["n"], w["n_bins"]
     stream = torch.cuda.current_stream(device)
     ctx = glm.GLM(device, stream=stream)

@@ -138,6 +138,41 @@ int glm_spike_term(glm_ctx* ctx, double* C_dev, double* q_dev);
 int glm_loglik_grad(glm_ctx* ctx, const float* W_dev, const float* b_dev, double* L_rows_dev,
                     double* L_total_host, double* G_dev, double* gb_dev);
 
+/* ---- classification of reconstructed weights (Sec. 3.1 GMM, Sec. 3.3 k-means, Table 2, Eq. 20) ---- */
+#define GLM_CLASSIFY_GMM 0    /* 3-component Gaussian mixture by EM, started from 3-means (default) */
+#define GLM_CLASSIFY_KMEANS 1 /* 3-means (Lloyd) */
+
+typedef struct {
+    int32_t method;   /* GLM_CLASSIFY_GMM or GLM_CLASSIFY_KMEANS */
+    int32_t max_iter; /* iteration cap of each stage (default 1000) */
+    double tol;       /* GMM stop: relative change of the mixture log-likelihood (default 1e-12) */
+} glm_classify_opts_t;
+
+typedef struct {
+    double centers[3];   /* cluster centres / component means, ascending: inhibitory, absent, excitatory */
+    double weights[3];   /* GMM mixing weights (0 for k-means) */
+    double variances[3]; /* GMM variances (0 for k-means) */
+    double loglik;       /* final GMM log-likelihood */
+    int32_t iterations;  /* iterations of the last stage */
+    int64_t errors;      /* misclassified off-diagonal pairs (needs truth) */
+    double mer;          /* errors / (n (n - 1)), the denominator of Eq. 20 */
+    double mer_n2;       /* errors / n^2, the denominator of Table 2 */
+    int64_t fp[3], fn[3], nd[3]; /* per class (index 0 inhibitory, 1 absent, 2 excitatory): false
+                                    positives, false negatives, and false positives that contradict
+                                    Dale's law for the presynaptic type (needs types) */
+} glm_classify_report_t;
+
+/* Classify the off-diagonal weights of W_host (n x n, row-major, W[i][j] = weight of j -> i; host) into
+ * labels_out (n x n int8, host): -1 inhibitory, 0 absent, +1 excitatory; the diagonal is set to 0.
+ *   opts:  NULL for the defaults.
+ *   truth: optional n x n int8 ground-truth labels (host) for the error report; types: optional int8[n]
+ *          (+1 excitatory, -1 inhibitory presynaptic neuron) for the Dale's-law count.
+ *   report: optional.
+ * Runs on the host; needs no context.  Errors: INVALID_ARG (n < 2, null W or labels, bad options),
+ * NONFINITE (a non-finite weight). */
+int glm_classify(const double* W_host, int32_t n, const glm_classify_opts_t* opts, int8_t* labels_out,
+                 const int8_t* truth_host, const int8_t* types_host, glm_classify_report_t* report);
+
 /* ---- tracing ----
  * While profiling is enabled, every kernel group the context launches (filter_scan, carry, spike_term,
  * u_epilogue, grad, reduce, ...) is bracketed by CUDA events recorded on the context's stream.

@@ -43,6 +43,22 @@ SIGNATURES = {
     "glm_launch_count": ([_vp], _i64),
 }
 
+
+
+class ClassifyOpts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double)]
+
+
+class ClassifyReport(ctypes.Structure):
+    _fields_ = [("centers", ctypes.c_double * 3), ("weights", ctypes.c_double * 3),
+                ("variances", ctypes.c_double * 3), ("loglik", ctypes.c_double), ("iterations", ctypes.c_int32),
+                ("errors", ctypes.c_int64), ("mer", ctypes.c_double), ("mer_n2", ctypes.c_double),
+                ("fp", ctypes.c_int64 * 3), ("fn", ctypes.c_int64 * 3), ("nd", ctypes.c_int64 * 3)]
+
+
+SIGNATURES["glm_classify"] = ([_vp, _i32, ctypes.POINTER(ClassifyOpts), _vp, _vp, _vp, ctypes.POINTER(ClassifyReport)],
+                              ctypes.c_int)
+
 # precisions this build implements
 AVAILABLE_PRECISIONS = ("f32", "bf16", "f16")
 
@@ -78,6 +94,33 @@ def load_library(path: str = LIB_PATH):
 
 def _ptr(t) -> int | None:
     return None if t is None else t.data_ptr()
+
+
+def classify(W, method: str = "gmm", truth=None, types=None, max_iter: int = 1000, tol: float = 1e-12):
+    """Labels (n x n int8: -1 inhibitory, 0 absent, +1 excitatory) of the off-diagonal weights and a report
+    dict (cluster centres, and with `truth` the misclassification rate and its FP/FN/ND breakdown).
+    Host computation in libglm (glm_classify)."""
+    lib = load_library()
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    n = W.shape[0]
+    labels = np.zeros((n, n), dtype=np.int8)
+    tr = None if truth is None else np.ascontiguousarray(truth, dtype=np.int8)
+    ty = None if types is None else np.ascontiguousarray(types, dtype=np.int8)
+    o = ClassifyOpts({"gmm": 0, "kmeans": 1}[method], max_iter, tol)
+    rep = ClassifyReport()
+    rc = lib.glm_classify(W.ctypes.data, n, ctypes.byref(o), labels.ctypes.data,
+                          None if tr is None else tr.ctypes.data, None if ty is None else ty.ctypes.data,
+                          ctypes.byref(rep))
+    if rc != GLM_OK:
+        raise GLMError(rc, "glm_classify")
+    names = ("inh", "absent", "exc")
+    out = dict(centers=list(rep.centers), weights=list(rep.weights), variances=list(rep.variances),
+               loglik=rep.loglik, iterations=rep.iterations)
+    if tr is not None:
+        out.update(errors=rep.errors, mer=rep.mer, mer_n2=rep.mer_n2)
+        for k, nm in enumerate(names):
+            out[nm] = dict(errors=rep.fp[k] + rep.fn[k], fp=rep.fp[k], fn=rep.fn[k], nd=rep.nd[k])
+    return labels, out
 
 
 class GLM:

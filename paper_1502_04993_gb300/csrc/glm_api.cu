@@ -391,7 +391,7 @@ int glm_loglik_grad(glm_ctx* c, const float* W, const float* b, double* L_rows, 
     GLM_CK(cudaMemsetAsync(c->buf.flags, 0, 2 * sizeof(int), c->stream));
     const bool tensor = c->pb.prec != GLM_PREC_F32;
     if (tensor) {
-        GLM_RUN("u_epilogue", 2, launch_tc_u_epilogue(c, W, b));
+        GLM_RUN("u_epilogue", 3, launch_tc_u_epilogue(c, W, b));
         if (want_grad) GLM_RUN("grad", 1, launch_tc_grad(c));
     } else {
         GLM_RUN("u_epilogue", 2, launch_simt_u_epilogue(c, W, b));

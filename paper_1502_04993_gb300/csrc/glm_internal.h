@@ -106,6 +106,7 @@ cudaError_t launch_simt_u_epilogue(glm_ctx* c, const float* W, const float* b);
 cudaError_t launch_simt_grad(glm_ctx* c);
 cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_rows, double* G, double* gb,
                           bool want_grad, int64_t ntile, int nsplit);
+void launch_exp_bias(glm_ctx* c, const float* b);
 cudaError_t tc_prepare_maps(glm_ctx* c);
 cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b);
 cudaError_t launch_tc_grad(glm_ctx* c);

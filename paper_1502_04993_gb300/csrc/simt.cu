@@ -249,9 +249,13 @@ __global__ void exp_bias_kernel(int32_t n, const float* __restrict__ b, double* 
     eb[i] = v;
 }
 
+void launch_exp_bias(glm_ctx* c, const float* b) {
+    exp_bias_kernel<<<(c->pb.n + 255) / 256, 256, 0, c->stream>>>(c->pb.n, b, c->buf.eb, c->buf.flags);
+}
+
 cudaError_t launch_simt_u_epilogue(glm_ctx* c, const float* W, const float* b) {
     const Problem& P = c->pb;
-    exp_bias_kernel<<<(P.n + 255) / 256, 256, 0, c->stream>>>(P.n, b, c->buf.eb, c->buf.flags);
+    launch_exp_bias(c, b);
     SimtUArgs A;
     A.n = P.n;
     A.T = P.T;

@@ -76,6 +76,7 @@ struct TcArgs {
     uint32_t idesc;
     double dt;
     const float* b;
+    const double* eb;  // exp(b_i) in FP64
     void* E;
     double* part_e;
     int64_t ntile;
@@ -297,10 +298,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             tc::tc_fence_after();
             const uint32_t lane_base = tmem_base + ((uint32_t)(q * 32) << 16);
             if (MODE == 0) {
+                // e^{U} = e^{b_i} e^{v}, v = (W X)_i[t]: e^{b_i} in FP64, and the row sum is kept as
+                // e^{b_i} (count + sum (e^{v} - 1)), so quiet bins (v ~ 0) add no FP32 rounding of b + v.
                 const uint32_t taddr = lane_base + (uint32_t)(buf * BN);
                 const int32_t i = w.m0 + row;
-                const float bi = (i < A.n) ? A.b[i] : 0.f;
-                const float dtf = (float)A.dt;
+                const double ebi = (i < A.n) ? A.eb[i] : 0.0;
+                const float dteb = (float)(A.dt * ebi);
                 double rsum = 0.0;
                 bool bad = false;
                 T16* erow = reinterpret_cast<T16*>(A.E) + (int64_t)i * A.Tpad + w.n0;
@@ -310,19 +313,30 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     tc::tmem_ld32(taddr + c * 32, r);
                     tc::tmem_ld_wait();
                     float s = 0.f;
+                    int cnt = 0;
                     uint32_t pk[16];
 #pragma unroll
                     for (int e = 0; e < 32; e += 2) {
                         const int64_t t = (int64_t)w.n0 + c * 32 + e;
-                        float e0 = __expf(__uint_as_float(r[e]) + bi);
-                        float e1 = __expf(__uint_as_float(r[e + 1]) + bi);
-                        if (t >= A.T) e0 = 0.f;
-                        if (t + 1 >= A.T) e1 = 0.f;
-                        bad |= !(e0 <= 3.0e38f) || !(e1 <= 3.0e38f);
-                        s += e0 + e1;
-                        pk[e >> 1] = pack16<T16>(dtf * e0, dtf * e1);
+                        float e0 = __expf(__uint_as_float(r[e]));
+                        float e1 = __expf(__uint_as_float(r[e + 1]));
+                        const bool v0 = t < A.T, v1 = t + 1 < A.T;
+                        bad |= (v0 && !(e0 <= 3.0e38f)) || (v1 && !(e1 <= 3.0e38f));
+                        if (v0) {
+                            s += e0 - 1.f;
+                            ++cnt;
+                        } else {
+                            e0 = 0.f;
+                        }
+                        if (v1) {
+                            s += e1 - 1.f;
+                            ++cnt;
+                        } else {
+                            e1 = 0.f;
+                        }
+                        pk[e >> 1] = pack16<T16>(dteb * e0, dteb * e1);
                     }
-                    rsum += (double)s;
+                    rsum += (double)cnt + (double)s;
                     if (i < A.n) {
                         uint4* dst = reinterpret_cast<uint4*>(erow + c * 32);
 #pragma unroll
@@ -330,7 +344,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                             dst[v] = make_uint4(pk[4 * v], pk[4 * v + 1], pk[4 * v + 2], pk[4 * v + 3]);
                     }
                 }
-                if (i < A.n) A.part_e[(int64_t)i * A.ntile + w.n0 / BN] = rsum;
+                bad |= !(dteb <= 3.0e38f);
+                if (i < A.n) A.part_e[(int64_t)i * A.ntile + w.n0 / BN] = ebi * rsum;
                 if (bad) atomicOr(A.flags, 1);
             } else {
 #pragma unroll 1
@@ -470,6 +485,7 @@ static TcArgs base_args(glm_ctx* c) {
     A.limit_ns = 4000000000ull;  // 4 s per wait
     A.idesc = tc::idesc_f16(P.prec == GLM_PREC_BF16 ? 1u : 0u, 128, BN);
     A.b = nullptr;
+    A.eb = c->buf.eb;
     A.E = nullptr;
     A.part_e = nullptr;
     A.part_g = nullptr;
@@ -492,6 +508,7 @@ cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b) {
         split_w_kernel<__half><<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(P.n, ldk, W, hi, hi + wsz,
                                                                                       c->buf.flags);
     }
+    launch_exp_bias(c, b);
     TcArgs A = base_args(c);
     A.mt = (P.n + 127) / 128;
     A.nt = (int32_t)(P.Tpad / BN);
