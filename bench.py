@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--n-bins", type=int, default=None,
                     help="record a shorter recording of the same network (profiling captures)")
+    ap.add_argument("--fit", default="", help="comma list of precisions to also run glm_fit with (e.g. bf16,f32)")
+    ap.add_argument("--fit-eta", type=float, default=1e-9)
+    ap.add_argument("--fit-max-iter", type=int, default=400)
     return ap.parse_args()
 
 
@@ -294,6 +297,25 @@ def main():
         "roofline": roof,
         "clocks": clk,
     }
+    if args.fit:
+        # full fits: wall time of glm_fit per precision, and the classification against the ground truth
+        from oracle.classify import truth_labels  # ground-truth labels from the generating W (no fitting)
+        truth = truth_labels(w["W_true"])
+        fits = {}
+        for p in [s for s in args.fit.split(",") if s]:
+            ctx.set_problem(w["offs"], w["bins"], T, w["dt"], w["tau"], prec=p)
+            torch.cuda.synchronize(device)
+            r = ctx.fit(eta=args.fit_eta, max_iter=args.fit_max_iter)
+            Wf = r["W"].cpu().numpy().astype(np.float64)
+            _, rep = glm.classify(Wf, "gmm", truth=truth, types=w["types"])
+            fr = r["report"]
+            fits[p] = {"seconds": fr["seconds"], "iterations": fr["iterations"], "evaluations": fr["evaluations"],
+                       "gradients": fr["gradients"], "converged": fr["converged"], "at_floor": fr["at_floor"], "stalled": fr["stalled"],
+                       "maxiter": fr["maxiter"], "L": fr["L"], "mer": rep["mer"], "mer_n2": rep["mer_n2"]}
+        if "f32" in fits:
+            for p, v in fits.items():
+                v["speedup_vs_f32"] = fits["f32"]["seconds"] / v["seconds"]
+        line["fit"] = {"eta": args.fit_eta, "max_iter": args.fit_max_iter, "by_precision": fits}
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, os.cpu_count() or 1)
         line["cpu_baseline"].pop("seconds", None)

@@ -127,16 +127,78 @@ int glm_filter(glm_ctx* ctx, int64_t t0, int64_t t_len, void* X_dev, int64_t ldx
  * Errors: NO_PROBLEM, CUDA. */
 int glm_spike_term(glm_ctx* ctx, double* C_dev, double* q_dev);
 
-/* Log-likelihood and gradient of the current problem at (W, b) (steps a3-a5, a7):
+/* Log-likelihood and gradient of the current problem at (W, b) (steps a3-a6, a7):
  *   W_dev: float[n * n], b_dev: float[n]  (inputs, device)
  *   L_rows_dev:   double[n]      L_i                    (or NULL)
  *   L_total_host: double         L = sum_i L_i          (or NULL; synchronises)
  *   G_dev:        double[n * n]  dL_i / dW_ij           (or NULL: the gradient product is skipped)
  *   gb_dev:       double[n]      dL_i / db_i            (or NULL)
+ *   gtau_host:    double         dL / dtau              (or NULL; synchronises).  tau enters through
+ *                 a = exp(-dt/tau) in the kernel of Eq. 3 (it is not part of theta_i, Sec. 2.2):
+ *                 dL/dtau = (a dt / tau^2) sum_{i,t} R_i[t] sum_j W_ij dX_j[t]/da.  The first request
+ *                 on a problem also computes its W-independent spike part.  Tensor-core precisions
+ *                 only (GLM_ERR_UNSUPPORTED for GLM_PREC_F32).
  * Errors: NO_PROBLEM, INVALID_ARG, NONFINITE (exp(U) overflowed; outputs are then undefined), CUDA,
- * TIMEOUT. */
+ * TIMEOUT, UNSUPPORTED, OOM. */
 int glm_loglik_grad(glm_ctx* ctx, const float* W_dev, const float* b_dev, double* L_rows_dev,
-                    double* L_total_host, double* G_dev, double* gb_dev);
+                    double* L_total_host, double* G_dev, double* gb_dev, double* gtau_host);
+
+/* ---- maximum-likelihood fit (Sec. 2.2 separability, Sec. 2.6.3 optimiser and stopping rule) ----
+ * Every row i is an independent concave problem in theta_i = (b_i, W_i1..W_in) (App. A).  All rows are
+ * fitted together: each iteration evaluates every active row's trial point in one batched evaluation,
+ * and each row keeps its own search direction, step and history. */
+#define GLM_FIT_LBFGS 0 /* limited-memory BFGS (the paper's optimiser family, Sec. 2.6.3) */
+#define GLM_FIT_GA 1    /* plain gradient ascent */
+
+#define GLM_ROW_CONVERGED 0
+#define GLM_ROW_MAXITER 1
+#define GLM_ROW_STALLED 2
+#define GLM_ROW_DEGENERATE 3
+#define GLM_ROW_AT_FLOOR 4 /* stopped at the evaluation's resolution: even a steepest-ascent step predicts a
+                              gain below gain_floor (|L_i| + q_i), so no further increase can be told apart
+                              from the evaluation's rounding (typical of the 16-bit precisions near the
+                              optimum, whose L_i carry a relative error of ~1e-7) */
+
+#define GLM_STATUS_NOT_CONVERGED 1 /* some row reached max_iter */
+#define GLM_STATUS_STALLED 2       /* some row's line search failed (no increase found) */
+
+typedef struct {
+    int32_t method;       /* GLM_FIT_LBFGS (default) or GLM_FIT_GA */
+    int32_t m;            /* L-BFGS memory, 1..32 (default 10) */
+    int32_t max_iter;     /* iteration cap (default 500) */
+    double eta;           /* row stop: |L_i(new) - L_i(old)| / |L_i(old)| < eta (default 1e-10; Sec. 2.6.3) */
+    double c1;            /* Armijo sufficient-increase constant (default 1e-4) */
+    int32_t max_halvings; /* backtracking steps of one line search (each shrinks the step 2-10x) before
+                             the row restarts from the gradient or, without history, stalls (default 40) */
+    int32_t warm_start;   /* 0: start at W = 0, b_i = log(q_i / (T dt)); 1: start at the W, b passed in */
+    double gain_floor;    /* a row whose predicted gain s |g.d| falls below gain_floor (|L_i| + q_i) during
+                             its line search is declared stalled: smaller gains are not resolved by the
+                             evaluation.  < 0 (default): 1e-13 for GLM_PREC_F32, 1e-10 for BF16/F16;
+                             0 disables the test. */
+} glm_fit_opts_t;
+
+typedef struct {
+    int32_t iterations;  /* outer iterations */
+    int32_t evaluations; /* log-likelihood evaluations (U products), trials included */
+    int32_t gradients;   /* gradient products */
+    int32_t converged, maxiter, stalled, degenerate, at_floor; /* rows in each final state */
+    double L;            /* final log-likelihood sum_i L_i */
+    double seconds;      /* wall time of the call */
+} glm_fit_report_t;
+
+/* Fill *opts with the defaults above. */
+void glm_fit_default_opts(glm_fit_opts_t* opts);
+
+/* Maximum-likelihood W and b of the current problem.
+ *   W_dev: float[n * n], b_dev: float[n] (device).  Read when opts->warm_start, always overwritten with
+ *          the fit.  Rows with no spike have no finite maximum in b_i: they get b_i = log(1e-3 / s) (the
+ *          lower bound of the paper's base-rate box, Sec. 2.6.3), W_i = 0 and state DEGENERATE.
+ *   row_status_host: optional int8[n] receiving GLM_ROW_* per row.
+ *   report: optional.
+ * Returns GLM_OK when every non-degenerate row converged or stopped at the floor, GLM_STATUS_NOT_CONVERGED or GLM_STATUS_STALLED
+ * otherwise (the fit is still written), or a negative GLM_ERR_*.  Synchronises the context's stream. */
+int glm_fit(glm_ctx* ctx, const glm_fit_opts_t* opts, float* W_dev, float* b_dev, int8_t* row_status_host,
+            glm_fit_report_t* report);
 
 /* ---- classification of reconstructed weights (Sec. 3.1 GMM, Sec. 3.3 k-means, Table 2, Eq. 20) ---- */
 #define GLM_CLASSIFY_GMM 0    /* 3-component Gaussian mixture by EM, started from 3-means (default) */

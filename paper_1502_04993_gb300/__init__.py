@@ -37,7 +37,7 @@ SIGNATURES = {
     "glm_prepare": ([_vp, _f64], ctypes.c_int),
     "glm_filter": ([_vp, _i64, _i64, _vp, _i64, ctypes.c_int], ctypes.c_int),
     "glm_spike_term": ([_vp, _vp, _vp], ctypes.c_int),
-    "glm_loglik_grad": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "glm_loglik_grad": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "glm_profile_enable": ([_vp, ctypes.c_int], ctypes.c_int),
     "glm_profile_read": ([_vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
     "glm_launch_count": ([_vp], _i64),
@@ -56,7 +56,23 @@ class ClassifyReport(ctypes.Structure):
                 ("fp", ctypes.c_int64 * 3), ("fn", ctypes.c_int64 * 3), ("nd", ctypes.c_int64 * 3)]
 
 
-SIGNATURES["glm_classify"] = ([_vp, _i32, ctypes.POINTER(ClassifyOpts), _vp, _vp, _vp, ctypes.POINTER(ClassifyReport)],
+class FitOpts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int32), ("m", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("eta", ctypes.c_double), ("c1", ctypes.c_double), ("max_halvings", ctypes.c_int32),
+                ("warm_start", ctypes.c_int32), ("gain_floor", ctypes.c_double)]
+
+
+class FitReport(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("evaluations", ctypes.c_int32), ("gradients", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("maxiter", ctypes.c_int32), ("stalled", ctypes.c_int32),
+                ("degenerate", ctypes.c_int32), ("at_floor", ctypes.c_int32), ("L", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+
+ROW_STATUS = {0: "converged", 1: "maxiter", 2: "stalled", 3: "degenerate", 4: "at_floor"}
+SIGNATURES["glm_fit_default_opts"] = ([ctypes.POINTER(FitOpts)], None)
+SIGNATURES["glm_fit"] = ([_vp, ctypes.POINTER(FitOpts), _vp, _vp, _vp, ctypes.POINTER(FitReport)], ctypes.c_int)
+SIGNATURES["glm_classify"] =([_vp, _i32, ctypes.POINTER(ClassifyOpts), _vp, _vp, _vp, ctypes.POINTER(ClassifyReport)],
                               ctypes.c_int)
 
 # precisions this build implements
@@ -219,14 +235,34 @@ class GLM:
     def launch_count(self) -> int:
         return int(self.lib.glm_launch_count(self.h))
 
-    def loglik_grad(self, W, b, *, grad: bool = True, total: bool = True, out=None):
-        """L_i, L, dL/dW and dL/db at (W, b).  W: (n, n) float32 cuda, b: (n,) float32 cuda."""
+    def fit(self, W=None, b=None, *, method: str = "lbfgs", m: int = 10, max_iter: int = 500, eta: float = 1e-10,
+            c1: float = 1e-4, max_halvings: int = 40, gain_floor: float = -1.0):
+        """Maximum-likelihood W, b of the current problem (glm_fit).  Starts at W = 0, b = log(q / T dt) unless
+        W and b are given (warm start).  Returns dict(W, b, status per row, report, rc)."""
+        torch = self.torch
+        dev = f"cuda:{self.device}"
+        warm = W is not None
+        Wd = (W.to(device=dev, dtype=torch.float32).clone() if warm
+              else torch.zeros((self.n, self.n), dtype=torch.float32, device=dev)).contiguous()
+        bd = (b.to(device=dev, dtype=torch.float32).clone() if warm
+              else torch.zeros(self.n, dtype=torch.float32, device=dev)).contiguous()
+        o = FitOpts({"lbfgs": 0, "ga": 1}[method], m, max_iter, eta, c1, max_halvings, int(warm), gain_floor)
+        rep = FitReport()
+        status = np.zeros(self.n, dtype=np.int8)
+        rc = self.lib.glm_fit(self.h, ctypes.byref(o), _ptr(Wd), _ptr(bd), status.ctypes.data, ctypes.byref(rep))
+        if rc < 0:
+            self._check(rc, "glm_fit")
+        report = {f: getattr(rep, f) for f, _ in FitReport._fields_}
+        return dict(W=Wd, b=bd, status=status, report=report, rc=rc)
+
+    def loglik_grad(self, W, b, *, grad: bool = True, total: bool = True, tau_grad: bool = False, out=None):
+        """L_i, L, dL/dW, dL/db (and with tau_grad dL/dtau) at (W, b).  W: (n, n) float32, b: (n,) float32."""
         torch = self.torch
         dev = f"cuda:{self.device}"
         W = W.to(device=dev, dtype=torch.float32).contiguous()
         b = b.to(device=dev, dtype=torch.float32).contiguous()
         if self.n is None:  # no problem yet: let the library report it
-            self._check(self.lib.glm_loglik_grad(self.h, _ptr(W), _ptr(b), None, None, None, None),
+            self._check(self.lib.glm_loglik_grad(self.h, _ptr(W), _ptr(b), None, None, None, None, None),
                         "glm_loglik_grad")
         out = out or {}
         L_rows = out.get("L_rows")
@@ -239,7 +275,10 @@ class GLM:
         if grad and gb is None:
             gb = torch.empty(self.n, dtype=torch.float64, device=dev)
         tot = ctypes.c_double(0.0)
+        gt = ctypes.c_double(0.0)
         rc = self.lib.glm_loglik_grad(self.h, _ptr(W), _ptr(b), _ptr(L_rows),
-                                      ctypes.byref(tot) if total else None, _ptr(G), _ptr(gb))
+                                      ctypes.byref(tot) if total else None, _ptr(G), _ptr(gb),
+                                      ctypes.byref(gt) if tau_grad else None)
         self._check(rc, "glm_loglik_grad")
-        return dict(L_rows=L_rows, L_total=tot.value if total else None, G=G, gb=gb)
+        return dict(L_rows=L_rows, L_total=tot.value if total else None, G=G, gb=gb,
+                    gtau=gt.value if tau_grad else None)

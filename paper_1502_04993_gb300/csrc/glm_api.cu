@@ -49,6 +49,7 @@ void free_all(glm_ctx* c) {
     c->ws_used = 0;
     c->buf = Buffers();
     c->has_problem = false;
+    c->dtau_ready = false;
 }
 
 // Device allocation charged against the workspace cap.
@@ -168,16 +169,83 @@ int do_prepare(glm_ctx* c) {
     fill_scan_consts(P.a, &c->sc);
     std::vector<double> pw(SEG + 1);
     for (int k = 0; k <= SEG; ++k) pw[k] = std::exp(-(double)k * P.dt / P.tau);
+    std::vector<double> dpw(SEG + 1);
+    for (int k = 0; k <= SEG; ++k) dpw[k] = k == 0 ? 0.0 : (double)k * std::exp(-(double)(k - 1) * P.dt / P.tau);
     GLM_CK(cudaMemcpyAsync(c->buf.pow_seg, pw.data(), sizeof(double) * (SEG + 1), cudaMemcpyHostToDevice,
                            c->stream));
+    GLM_CK(cudaMemcpyAsync(c->buf.dpow_seg, dpw.data(), sizeof(double) * (SEG + 1), cudaMemcpyHostToDevice,
+                           c->stream));
+    c->dtau_ready = false;
     GLM_RUN("carry", 2, launch_carry(c));
     GLM_RUN("filter_scan", 1, launch_filter_cache(c));
-    GLM_RUN("spike_term", 2, launch_spike_term(c));
+    GLM_RUN("spike_term", 2, launch_spike_term(c, false, c->buf.C));
     // pw is a pageable host buffer: the copy above has been staged before cudaMemcpyAsync returned
     return GLM_OK;
 }
 
+// W-independent parts of dL/dtau: the carries of Y = dX/da and D_ij = sum_{t in sp(i)} Y_j[t].
+int prepare_dtau(glm_ctx* c) {
+    if (c->dtau_ready) return GLM_OK;
+    Buffers& B = c->buf;
+    const Problem& P = c->pb;
+    int rc;
+    if (!B.D) {
+        if ((rc = ws_alloc_t(c, &B.seg_carry_y, (size_t)P.n * P.nseg)) ||
+            (rc = ws_alloc_t(c, &B.seg_tmp, (size_t)P.n * P.nseg)) || (rc = ws_alloc_t(c, &B.D, (size_t)P.n * P.n)) ||
+            (rc = ws_alloc_t(c, &B.part_tau, 3 * (size_t)P.n * (P.Tpad / tc_tile_t()))) ||
+            (rc = ws_alloc_t(c, &B.tau_rows, P.n)))
+            return rc;
+    }
+    GLM_RUN("carry_y", 2, launch_carry_y(c));
+    GLM_RUN("spike_term_y", 2, launch_spike_term(c, true, B.D));
+    c->dtau_ready = true;
+    return GLM_OK;
+}
+
 }  // namespace
+
+namespace glm {
+
+int set_error(glm_ctx* c, int code, const char* msg) { return fail(c, code, msg); }
+
+// Queue one evaluation at (W, b) on the context's stream; no synchronisation.  With reuse_u the U
+// product is skipped: E and the per-tile sums must already hold the values at this (W, b).
+int eval_enqueue(glm_ctx* c, const float* W, const float* b, double* L_rows, double* G, double* gb, bool want_grad,
+                 bool reuse_u, bool tau) {
+    const bool tensor = c->pb.prec != GLM_PREC_F32;
+    if (!reuse_u) {
+        if (tensor)
+            GLM_RUN("u_epilogue", 3, launch_tc_u_epilogue(c, W, b, tau));
+        else
+            GLM_RUN("u_epilogue", 2, launch_simt_u_epilogue(c, W, b));
+    }
+    if (want_grad) {
+        if (tensor)
+            GLM_RUN("grad", 1, launch_tc_grad(c));
+        else
+            GLM_RUN("grad", 1, launch_simt_grad(c));
+    }
+    const int64_t ntile = c->pb.Tpad / (tensor ? tc_tile_t() : simt_tile_t());
+    const int nsplit = tensor ? tc_nsplit(c) : grad_nsplit(c);
+    GLM_RUN("reduce", want_grad ? 2 : 1, launch_reduce(c, W, b, L_rows, G, gb, want_grad, ntile, nsplit));
+    return GLM_OK;
+}
+
+// Synchronise and turn the device flags raised since the last reset into a status.
+int eval_status(glm_ctx* c) {
+    int fl[2] = {0, 0};
+    GLM_CK(cudaMemcpyAsync(fl, c->buf.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    GLM_CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+    if (fl[1]) return fail(c, GLM_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
+    if (fl[0] & 1) return fail(c, GLM_ERR_NONFINITE, "exp(U) overflowed or an input was not finite");
+    return GLM_OK;
+}
+
+cudaError_t reset_flags(glm_ctx* c) { return cudaMemsetAsync(c->buf.flags, 0, 2 * sizeof(int), c->stream); }
+
+int ws_alloc_bytes(glm_ctx* c, void** p, size_t bytes) { return ws_alloc(c, p, bytes); }
+
+}  // namespace glm
 
 extern "C" {
 
@@ -310,6 +378,7 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
     if ((rc = ws_alloc_t(c, &B.offs, n + 1)) || (rc = ws_alloc_t(c, &B.bins, P.q > 0 ? P.q : 1)) ||
         (rc = ws_alloc_t(c, &B.seg_carry, (size_t)n * P.nseg)) ||
         (rc = ws_alloc_t(c, &B.seg_first, (size_t)n * P.nseg)) || (rc = ws_alloc_t(c, &B.pow_seg, SEG + 1)) ||
+        (rc = ws_alloc_t(c, &B.dpow_seg, SEG + 1)) ||
         (rc = ws_alloc_t(c, &B.qd, n)) || (rc = ws_alloc_t(c, &B.C, nn)) ||
         (rc = ws_alloc_t(c, &B.C_part, nn * spike_term_parts(c))) || (rc = ws_alloc(c, &B.X, (size_t)n * P.Tpad * esz)) ||
         (rc = ws_alloc(c, &B.E, (size_t)n * P.Tpad * esz)) ||
@@ -381,25 +450,30 @@ int glm_spike_term(glm_ctx* c, double* C_dev, double* q_dev) {
 }
 
 int glm_loglik_grad(glm_ctx* c, const float* W, const float* b, double* L_rows, double* L_total_host,
-                    double* G, double* gb) {
+                    double* G, double* gb, double* gtau_host) {
     if (!c) return GLM_ERR_INVALID_ARG;
     if (!c->has_problem) return fail(c, GLM_ERR_NO_PROBLEM, "no problem set");
     if (!W || !b) return fail(c, GLM_ERR_INVALID_ARG, "W and b are required");
+    if (gtau_host && c->pb.prec == GLM_PREC_F32)
+        return fail(c, GLM_ERR_UNSUPPORTED, "dL/dtau is computed by the tensor-core precisions only");
     DeviceGuard g(c->device);
     double* Lr = L_rows ? L_rows : c->buf.Lrows;
-    const bool want_grad = G != nullptr;
-    GLM_CK(cudaMemsetAsync(c->buf.flags, 0, 2 * sizeof(int), c->stream));
-    const bool tensor = c->pb.prec != GLM_PREC_F32;
-    if (tensor) {
-        GLM_RUN("u_epilogue", 3, launch_tc_u_epilogue(c, W, b));
-        if (want_grad) GLM_RUN("grad", 1, launch_tc_grad(c));
-    } else {
-        GLM_RUN("u_epilogue", 2, launch_simt_u_epilogue(c, W, b));
-        if (want_grad) GLM_RUN("grad", 1, launch_simt_grad(c));
+    if (gtau_host) {
+        int rc = prepare_dtau(c);
+        if (rc) return rc;
     }
-    const int64_t ntile = c->pb.Tpad / (tensor ? tc_tile_t() : simt_tile_t());
-    const int nsplit = tensor ? tc_nsplit(c) : grad_nsplit(c);
-    GLM_RUN("reduce", want_grad ? 2 : 1, launch_reduce(c, W, b, Lr, G, gb, want_grad, ntile, nsplit));
+    GLM_CK(cudaMemsetAsync(c->buf.flags, 0, 2 * sizeof(int), c->stream));
+    int rc = glm::eval_enqueue(c, W, b, Lr, G, gb, G != nullptr, false, gtau_host != nullptr);
+    if (rc) return rc;
+    if (gtau_host) {
+        GLM_RUN("tau_rows", 1, launch_tau_rows(c, W, c->buf.tau_rows));
+        GLM_RUN("total", 1, launch_total(c, c->buf.tau_rows, c->buf.scal + 1));
+        double t = 0.0;
+        GLM_CK(cudaMemcpyAsync(&t, c->buf.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        GLM_CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+        const Problem& P = c->pb;
+        *gtau_host = P.a * P.dt / (P.tau * P.tau) * t;  // da/dtau = a dt / tau^2
+    }
     if (L_total_host) {
         double* dtot = c->buf.scal;
         GLM_RUN("total", 1, launch_total(c, Lr, dtot));
@@ -413,6 +487,33 @@ int glm_loglik_grad(glm_ctx* c, const float* W, const float* b, double* L_rows, 
         if (fl[0] & 1) return fail(c, GLM_ERR_NONFINITE, "exp(U) overflowed or an input was not finite");
     }
     return GLM_OK;
+}
+
+void glm_fit_default_opts(glm_fit_opts_t* o) {
+    if (!o) return;
+    o->method = GLM_FIT_LBFGS;
+    o->m = 10;
+    o->max_iter = 500;
+    o->eta = 1e-10;
+    o->c1 = 1e-4;
+    o->max_halvings = 40;
+    o->warm_start = 0;
+    o->gain_floor = -1.0;
+}
+
+int glm_fit(glm_ctx* c, const glm_fit_opts_t* opts, float* W, float* b, int8_t* row_status, glm_fit_report_t* rep) {
+    if (!c) return GLM_ERR_INVALID_ARG;
+    if (!c->has_problem) return fail(c, GLM_ERR_NO_PROBLEM, "no problem set");
+    if (!W || !b) return fail(c, GLM_ERR_INVALID_ARG, "W and b are required");
+    glm_fit_opts_t o;
+    glm_fit_default_opts(&o);
+    if (opts) o = *opts;
+    if ((o.method != GLM_FIT_LBFGS && o.method != GLM_FIT_GA) || o.m < 1 || o.m > 32 || o.max_iter < 0 ||
+        !(o.eta >= 0) || !(o.c1 > 0 && o.c1 < 1) || o.max_halvings < 1 ||
+        std::isnan(o.gain_floor))
+        return fail(c, GLM_ERR_INVALID_ARG, "bad fit options");
+    DeviceGuard g(c->device);
+    return glm::fit_run(c, &o, W, b, row_status, rep);
 }
 
 }  // extern "C"

@@ -25,6 +25,10 @@ struct ScanConsts {
     float pm_hi[9], pm_lo[9];    // a^m,          m = 0..8
     float ps_hi[5], ps_lo[5];    // a^(8*2^d),    d = 0..4   (warp scan strides)
     float pl_hi[32], pl_lo[32];  // a^(8*l),      l = 0..31  (lane offsets)
+    // derivatives in a, for the joint scan of X and Y = dX/da (the tau derivative)
+    float pmd_hi[9], pmd_lo[9];  // m a^(m-1)
+    float psd_hi[5], psd_lo[5];  // 8*2^d a^(8*2^d - 1)
+    float pld_hi[32], pld_lo[32];  // 8 l a^(8 l - 1)
 };
 
 struct Problem {
@@ -58,6 +62,15 @@ struct Buffers {
     double* Lrows = nullptr;      // [n] scratch when the caller passes no L_rows
     double* scal = nullptr;       // [8] device scalars (total log-likelihood, ...)
     double* eb = nullptr;         // [n] exp(b_i) in FP64 (plain FP32 form)
+    void* fit_mem = nullptr;      // optimiser state of glm_fit (allocated by its first call)
+    // derivative in tau (allocated by the first request for it)
+    double* dpow_seg = nullptr;   // [SEG + 1]  k a^(k-1)
+    double* seg_carry_y = nullptr;  // [n][nseg] Y = dX/da at segment starts
+    double* seg_tmp = nullptr;    // [n][nseg]
+    double* D = nullptr;          // [n][n]  sum_{t in sp(i)} Y_j[t]
+    double* part_tau = nullptr;   // [3][n][ntile]
+    double* tau_rows = nullptr;   // [n]
+    int fit_m = 0;
 };
 
 }  // namespace glm
@@ -74,6 +87,7 @@ struct glm_ctx {
     glm::ScanConsts sc;
     CUtensorMap tmap[6];  // tensor-core path: W_hi, W_lo, X_hi^T, X_lo^T, E, X_hi
     bool has_problem = false;
+    bool dtau_ready = false;  // D and the Y carries are current
     std::string last_error;
     // tracing: event pairs per launched kernel group while profiling is on
     bool prof_on = false;
@@ -101,14 +115,23 @@ namespace glm {
 cudaError_t launch_carry(glm_ctx* c);
 cudaError_t launch_filter_cache(glm_ctx* c);
 cudaError_t launch_filter_range(glm_ctx* c, int64_t t0, int64_t t_len, void* out, int64_t ldx, glm_dtype_t dtype);
-cudaError_t launch_spike_term(glm_ctx* c);
+cudaError_t launch_spike_term(glm_ctx* c, bool dy, double* out);
+cudaError_t launch_carry_y(glm_ctx* c);
+cudaError_t launch_tau_rows(glm_ctx* c, const float* W, double* rows);
 cudaError_t launch_simt_u_epilogue(glm_ctx* c, const float* W, const float* b);
 cudaError_t launch_simt_grad(glm_ctx* c);
 cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_rows, double* G, double* gb,
                           bool want_grad, int64_t ntile, int nsplit);
 void launch_exp_bias(glm_ctx* c, const float* b);
+int set_error(glm_ctx* c, int code, const char* msg);
+int eval_enqueue(glm_ctx* c, const float* W, const float* b, double* L_rows, double* G, double* gb, bool want_grad,
+                 bool reuse_u, bool tau = false);
+int eval_status(glm_ctx* c);
+cudaError_t reset_flags(glm_ctx* c);
+int ws_alloc_bytes(glm_ctx* c, void** p, size_t bytes);
+int fit_run(glm_ctx* c, const glm_fit_opts_t* o, float* W, float* b, int8_t* row_status, glm_fit_report_t* rep);
 cudaError_t tc_prepare_maps(glm_ctx* c);
-cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b);
+cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, bool tau);
 cudaError_t launch_tc_grad(glm_ctx* c);
 int tc_nsplit(const glm_ctx* c);
 int tc_tile_t();

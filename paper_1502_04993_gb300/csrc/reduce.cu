@@ -3,6 +3,8 @@
 //   dL/db_i = q_i - dt sum_t exp(U_i[t])                         (Eq. 12, j = 0)
 //   dL/dW_ij = C_ij - sum_s P_s[i][j],  P_s = sum_{t in split s} dt exp(U_i[t]) X_j[t]   (Eq. 12)
 //   L = sum_i L_i                                                (Eq. 1)
+#include <cmath>
+
 #include "glm_internal.h"
 
 namespace glm {
@@ -66,6 +68,57 @@ __global__ void total_kernel(int32_t n, const double* __restrict__ L_rows, doubl
         v = warp_sum(v);
         if (threadIdx.x == 0) *out = v;
     }
+}
+
+// Row i's share of dL/dtau, up to the factor da/dtau = a dt / tau^2 (applied on the host):
+//   r_i = sum_j W_ij D_ij - dt e^{b_i} sum_t e^{v_i[t]} Z_i[t],
+// D_ij = sum_{t in sp(i)} Y_j[t] (the spike part), Z_i = W_i Y_i on the grid.  The epilogue left per tile k:
+// P1 = sum e^v a^(t-t0), P2 = sum e^v Z_loc, Zend = Z_loc at the next tile; with Z_start(0) = 0 and
+// Z_start(k+1) = A Z_start(k) + Zend(k) (A = a^256) the integral part is sum_k Z_start(k) P1(k) + P2(k).
+// Warp per row: lanes own contiguous tile ranges, a shuffle scan supplies each range's Z_start.
+__global__ void tau_rows_kernel(int32_t n, int64_t ntile, double dt, double A256, const float* __restrict__ W,
+                                const double* __restrict__ D, const double* __restrict__ eb,
+                                const double* __restrict__ part_tau, double* __restrict__ rows) {
+    const int32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const int64_t plane = (int64_t)n * ntile;
+    const double* p1 = part_tau + (int64_t)i * ntile;
+    const double* p2 = p1 + plane;
+    const double* ze = p1 + 2 * plane;
+    const int64_t len = (ntile + 31) / 32;
+    const int64_t k0 = min((int64_t)lane * len, ntile), k1 = min(k0 + len, ntile);
+    double z = 0.0, w = 1.0, Q = 0.0, S = 0.0;
+    for (int64_t k = k0; k < k1; ++k) {
+        Q = fma(w, p1[k], Q);
+        S += fma(z, p1[k], p2[k]);
+        z = fma(A256, z, ze[k]);
+        w *= A256;
+    }
+    double v = z, m = w;
+    for (int d = 1; d < 32; d <<= 1) {
+        const double o = __shfl_up_sync(0xffffffffu, v, d), om = __shfl_up_sync(0xffffffffu, m, d);
+        if (lane >= d) {
+            v = fma(m, o, v);
+            m *= om;
+        }
+    }
+    double zin = __shfl_up_sync(0xffffffffu, v, 1);
+    if (lane == 0) zin = 0.0;
+    double integ = fma(zin, Q, S);
+    double spk = 0.0;
+    for (int32_t j = lane; j < n; j += 32) spk += (double)W[(int64_t)i * n + j] * D[(int64_t)i * n + j];
+    integ = warp_sum(integ);
+    spk = warp_sum(spk);
+    if (lane == 0) rows[i] = spk - dt * eb[i] * integ;
+}
+
+cudaError_t launch_tau_rows(glm_ctx* c, const float* W, double* rows) {
+    const Problem& P = c->pb;
+    const double A256 = std::exp(-(double)SEG * P.dt / P.tau);
+    tau_rows_kernel<<<(P.n + 7) / 8, 256, 0, c->stream>>>(P.n, P.Tpad / tc_tile_t(), P.dt, A256, W, c->buf.D,
+                                                          c->buf.eb, c->buf.part_tau, rows);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_rows, double* G, double* gb,

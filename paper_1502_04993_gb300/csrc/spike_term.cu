@@ -3,12 +3,16 @@
 // which does not depend on W or b and is computed once per problem (Sec. 2.3.3, 2.6.1).  With it
 //   sum_t S_i[t] U_i[t] = q_i b_i + sum_j W_ij C_ij    and    dL_i/dW_ij = C_ij - dt sum_t e^{U_i[t]} X_j[t].
 //
-// Block = (16 presynaptic rows j, a part of the time axis, a slice of postsynaptic rows i).  For each
-// 2048-bin sub-chunk the 16 warps scan X_j for the 16 rows into shared memory (warp = one 256-bin segment
-// x 8 rows, started from the FP64 segment carries), then every thread walks the spikes of its rows i in
-// the sub-chunk, loading 8 spike bins ahead, and accumulates X_j[t] for the 16 rows.  Sums are kept as an
-// FP32 hi + lo pair (TwoSum) refreshed every 8 spikes, so they carry ~44 significant bits, and their
-// order is fixed: the result is deterministic.
+// Block = (16 presynaptic rows j, a part of the time axis, a slice of postsynaptic rows i), 16 warps.  For
+// each 2048-bin sub-chunk:
+//   phase A  the warps scan X_j for the 16 rows into shared memory (warp = one 256-bin segment x 8 rows,
+//            started from the FP64 segment carries; the loads of a pass's 4 rows are issued together);
+//   phase B  every thread walks the spikes of its postsynaptic rows i in the sub-chunk and accumulates
+//            X_j[t] for the 16 rows.  Its spike cursor is carried from sub-chunk to sub-chunk, the end
+//            index of the next sub-chunk is fetched before phase A, and spike bins are loaded one batch
+//            ahead of their use, so the global-memory latency overlaps with work.
+// Sums are kept as an FP32 hi + lo pair (TwoSum) refreshed after every batch of at most 4 spikes, so they
+// carry ~44 significant bits; their order is fixed and the result deterministic.
 #include <cmath>
 
 #include "glm_internal.h"
@@ -22,8 +26,7 @@ constexpr int ST_SUBSEGS = 8;                 // 2048 bins per sub-chunk
 constexpr int ST_SUB = ST_SUBSEGS * SEG;
 constexpr int ST_KI = 2;                      // postsynaptic rows per thread
 constexpr int ST_ROWS_PER_SLICE = ST_THREADS * ST_KI;
-constexpr int ST_FLUSH = 8;                   // spikes summed in plain FP32 before a TwoSum
-constexpr int ST_BATCH = 8;                   // spike bins loaded ahead per row
+constexpr int ST_BATCH = 4;                   // spike bins per batch (and per plain FP32 partial sum)
 
 // Xs layout: [bin][16 floats] = 4 chunks of 16 bytes per bin, chunk index XOR-swizzled by bin so that the
 // phase-A stores (lanes 8 bins apart) spread over the banks.
@@ -37,6 +40,30 @@ __device__ __forceinline__ void two_sum(float& hi, float& lo, float x) {
     lo += e;
 }
 
+// seg_bits (scan_dev.cuh) with the first 32-spike window already loaded into `sv`
+__device__ __forceinline__ uint32_t seg_bits_pre(const int32_t* __restrict__ bins, int64_t cur, int64_t end,
+                                                 int64_t t0, int lane, int64_t sv) {
+    uint32_t my = 0;
+    int64_t s = sv;
+    while (true) {
+        const bool in = s < t0 + SEG;
+        const uint32_t bal = __ballot_sync(FULL, in);
+        uint32_t m = bal;
+        while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            const int off = (int)(__shfl_sync(FULL, s, src) - t0);
+            if ((off >> 3) == lane) my |= 1u << (off & 7);
+        }
+        const int c = __popc(bal);
+        cur += c;
+        if (c < 32) break;
+        const int64_t k = cur + lane;
+        s = (k < end) ? (int64_t)__ldg(bins + k) : INT64_MAX;
+    }
+    return my;
+}
+
 struct SpikeTermArgs {
     int32_t n;
     int64_t nseg;
@@ -44,10 +71,14 @@ struct SpikeTermArgs {
     const int64_t* offs;
     const int32_t* bins;
     const double* seg_carry;
+    const double* seg_carry_y;  // Y = dX/da at segment starts (DY only)
     const int32_t* seg_first;
     double* C_part;  // [parts][n][n]
 };
 
+// DY = false: C_ij = sum_{t in sp(i)} X_j[t].  DY = true: D_ij = sum_{t in sp(i)} Y_j[t] with Y = dX/da, the
+// spike part of the derivative in tau (same gather, the joint (X, Y) scan in phase A).
+template <bool DY>
 __global__ void __launch_bounds__(ST_THREADS, 1) spike_term_kernel(const __grid_constant__ ScanConsts K,
                                                                    const __grid_constant__ SpikeTermArgs A) {
     extern __shared__ float4 Xs[];  // [ST_SUB * 4]
@@ -56,36 +87,77 @@ __global__ void __launch_bounds__(ST_THREADS, 1) spike_term_kernel(const __grid_
     const int64_t part = blockIdx.y;
     const int32_t i_base = blockIdx.z * ST_ROWS_PER_SLICE;
     const float pl_hi = K.pl_hi[lane], pl_lo = K.pl_lo[lane];
+    const float pld_hi = K.pld_hi[lane], pld_lo = K.pld_lo[lane];
     const int64_t sp0 = part * A.segs_per_part;
     const int64_t sp1 = min(sp0 + A.segs_per_part, A.nseg);
     const int seg_w = warp & (ST_SUBSEGS - 1);   // phase A: this warp's segment
     const int half_w = warp >> 3;                // and its 8 of the 16 presynaptic rows
 
     float acc_hi[ST_KI][ST_JB], acc_lo[ST_KI][ST_JB];
+    int64_t cur[ST_KI], rend[ST_KI];
 #pragma unroll
-    for (int k = 0; k < ST_KI; ++k)
+    for (int k = 0; k < ST_KI; ++k) {
 #pragma unroll
         for (int jj = 0; jj < ST_JB; ++jj) acc_hi[k][jj] = acc_lo[k][jj] = 0.f;
+        const int32_t i = i_base + threadIdx.x + k * ST_THREADS;
+        cur[k] = rend[k] = 0;
+        if (i < A.n && sp0 < sp1) {
+            const int64_t o0 = A.offs[i];
+            cur[k] = o0 + A.seg_first[(int64_t)i * A.nseg + sp0];
+            rend[k] = A.offs[i + 1];
+        }
+    }
 
     for (int64_t sc = sp0; sc < sp1; sc += ST_SUBSEGS) {
+        const int64_t sn = min(sp1, sc + ST_SUBSEGS);
+        const int64_t tb = sc * SEG;
+        // ---- prefetch for phase B: end of each row's spikes in this sub-chunk, first batch of bins ----
+        int64_t k1[ST_KI];
+        int tl[ST_KI][ST_BATCH];
+#pragma unroll
+        for (int k = 0; k < ST_KI; ++k) {
+            const int32_t i = i_base + threadIdx.x + k * ST_THREADS;
+            k1[k] = cur[k];
+            if (i < A.n) k1[k] = (sn < A.nseg) ? A.offs[i] + A.seg_first[(int64_t)i * A.nseg + sn] : rend[k];
+#pragma unroll
+            for (int u = 0; u < ST_BATCH; ++u)
+                tl[k][u] = (cur[k] + u < rend[k]) ? (int)(__ldg(A.bins + cur[k] + u) - tb) : ST_SUB;
+        }
         // ---- phase A: X_j for the 16 rows over this sub-chunk, into shared memory ----
         const int64_t s = sc + seg_w;
         if (s < sp1) {
             const int64_t t0 = s * SEG;
 #pragma unroll 1
             for (int pass = 0; pass < 2; ++pass) {  // 4 rows per pass: one 16-byte chunk per bin
-                float v[4][8];
+                float xs[4], ys[4];
+                int64_t rc[4], re[4], sv[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int32_t r = j0 + half_w * 8 + pass * 4 + k;
-                    float xs = 0.f;
-                    uint32_t bits = 0;
+                    xs[k] = ys[k] = 0.f;
+                    rc[k] = re[k] = 0;
                     if (r < A.n) {
-                        xs = (float)A.seg_carry[(int64_t)r * A.nseg + s];
-                        int64_t cur = A.offs[r] + A.seg_first[(int64_t)r * A.nseg + s];
-                        bits = seg_bits(A.bins, cur, A.offs[r + 1], t0, lane);
+                        xs[k] = (float)A.seg_carry[(int64_t)r * A.nseg + s];
+                        if (DY) ys[k] = (float)A.seg_carry_y[(int64_t)r * A.nseg + s];
+                        rc[k] = A.offs[r] + A.seg_first[(int64_t)r * A.nseg + s];
+                        re[k] = A.offs[r + 1];
                     }
-                    seg_scan(K, xs, bits, pl_hi, pl_lo, lane, v[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int64_t kk = rc[k] + lane;
+                    sv[k] = (kk < re[k]) ? (int64_t)__ldg(A.bins + kk) : INT64_MAX;
+                }
+                float v[4][8];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t bits = seg_bits_pre(A.bins, rc[k], re[k], t0, lane, sv[k]);
+                    if (DY) {
+                        float xe, ye;
+                        seg_scan_xy(K, xs[k], ys[k], bits, lane, pl_hi, pl_lo, pld_hi, pld_lo, v[k], &xe, &ye);
+                    } else {
+                        seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v[k]);
+                    }
                 }
 #pragma unroll
                 for (int m = 0; m < 8; ++m) {
@@ -96,41 +168,40 @@ __global__ void __launch_bounds__(ST_THREADS, 1) spike_term_kernel(const __grid_
         }
         __syncthreads();
         // ---- phase B: the spikes of this thread's postsynaptic rows in [tb, te) ----
-        const int64_t tb = sc * SEG;
-        const int64_t sn = min(sp1, sc + ST_SUBSEGS);
 #pragma unroll
         for (int k = 0; k < ST_KI; ++k) {
-            const int32_t i = i_base + threadIdx.x + k * ST_THREADS;
-            if (i >= A.n) continue;
-            const int64_t o0 = A.offs[i];
-            const int64_t k0 = o0 + A.seg_first[(int64_t)i * A.nseg + sc];
-            const int64_t k1 = (sn < A.nseg) ? o0 + A.seg_first[(int64_t)i * A.nseg + sn] : A.offs[i + 1];
             float sh[ST_JB];
 #pragma unroll
             for (int jj = 0; jj < ST_JB; ++jj) sh[jj] = 0.f;
-            for (int64_t kb = k0; kb < k1; kb += ST_BATCH) {
-                int tl[ST_BATCH];
-#pragma unroll
-                for (int u = 0; u < ST_BATCH; ++u) tl[u] = (kb + u < k1) ? (int)(__ldg(A.bins + kb + u) - tb) : -1;
+            for (int64_t kb = cur[k]; kb < k1[k]; kb += ST_BATCH) {
+                // next batch in flight while this one is summed
+                int nx[ST_BATCH];
 #pragma unroll
                 for (int u = 0; u < ST_BATCH; ++u) {
-                    if (tl[u] < 0) break;
+                    const int64_t q = kb + ST_BATCH + u;
+                    nx[u] = (q < k1[k]) ? (int)(__ldg(A.bins + q) - tb) : ST_SUB;
+                }
+#pragma unroll
+                for (int u = 0; u < ST_BATCH; ++u) {
+                    if (kb + u >= k1[k]) break;
 #pragma unroll
                     for (int ch = 0; ch < 4; ++ch) {
-                        const float4 x = Xs[xs_slot(tl[u], ch)];
+                        const float4 x = Xs[xs_slot(tl[k][u], ch)];
                         sh[4 * ch + 0] += x.x;
                         sh[4 * ch + 1] += x.y;
                         sh[4 * ch + 2] += x.z;
                         sh[4 * ch + 3] += x.w;
                     }
                 }
-                // ST_FLUSH == ST_BATCH: at most 8 values in each plain FP32 sum
 #pragma unroll
                 for (int jj = 0; jj < ST_JB; ++jj) {
                     two_sum(acc_hi[k][jj], acc_lo[k][jj], sh[jj]);
                     sh[jj] = 0.f;
                 }
+#pragma unroll
+                for (int u = 0; u < ST_BATCH; ++u) tl[k][u] = nx[u];
             }
+            cur[k] = k1[k];
         }
         __syncthreads();
     }
@@ -155,17 +226,19 @@ __global__ void spike_term_reduce_kernel(int64_t nn, int parts, const double* __
     C[e] = s;
 }
 
+// Parts of the time axis: enough blocks for about three full waves of one block per SM.
 int spike_term_parts(const glm_ctx* c) {
     const int64_t nsub = (c->pb.nseg + ST_SUBSEGS - 1) / ST_SUBSEGS;
     const int64_t groups = (c->pb.n + ST_JB - 1) / ST_JB;
-    int64_t p = (2 * (int64_t)c->sm_count + groups - 1) / groups;
+    const int64_t slices = (c->pb.n + ST_ROWS_PER_SLICE - 1) / ST_ROWS_PER_SLICE;
+    int64_t p = (3 * (int64_t)c->sm_count + groups * slices - 1) / (groups * slices);
     if (p < 1) p = 1;
     if (p > nsub) p = nsub;
     if (p > 64) p = 64;
     return (int)p;
 }
 
-cudaError_t launch_spike_term(glm_ctx* c) {
+cudaError_t launch_spike_term(glm_ctx* c, bool dy, double* out) {
     const Problem& P = c->pb;
     const int parts = spike_term_parts(c);
     const int64_t nsub = (P.nseg + ST_SUBSEGS - 1) / ST_SUBSEGS;
@@ -177,16 +250,23 @@ cudaError_t launch_spike_term(glm_ctx* c) {
     A.offs = c->buf.offs;
     A.bins = c->buf.bins;
     A.seg_carry = c->buf.seg_carry;
+    A.seg_carry_y = c->buf.seg_carry_y;
     A.seg_first = c->buf.seg_first;
     A.C_part = c->buf.C_part;
     const size_t smem = (size_t)ST_SUB * ST_JB * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(spike_term_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     dim3 grid((P.n + ST_JB - 1) / ST_JB, parts, (P.n + ST_ROWS_PER_SLICE - 1) / ST_ROWS_PER_SLICE);
-    spike_term_kernel<<<grid, ST_THREADS, smem, c->stream>>>(c->sc, A);
+    cudaError_t e;
+    if (dy) {
+        e = cudaFuncSetAttribute(spike_term_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        spike_term_kernel<true><<<grid, ST_THREADS, smem, c->stream>>>(c->sc, A);
+    } else {
+        e = cudaFuncSetAttribute(spike_term_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        spike_term_kernel<false><<<grid, ST_THREADS, smem, c->stream>>>(c->sc, A);
+    }
     const int64_t nn = (int64_t)P.n * P.n;
-    spike_term_reduce_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(nn, parts, c->buf.C_part,
-                                                                                c->buf.C);
+    spike_term_reduce_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(nn, parts, c->buf.C_part, out);
     return cudaGetLastError();
 }
 

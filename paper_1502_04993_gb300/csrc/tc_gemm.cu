@@ -73,10 +73,13 @@ struct TcArgs {
     int64_t units;
     int32_t kb_per_unit;  // MODE 0: k-steps over the neurons; MODE 1: k-steps per split
     int64_t kb_total;     // MODE 1: k-steps over the bins
+    int64_t nsplit;       // MODE 1: number of interleaved splits
     uint32_t idesc;
     double dt;
     const float* b;
     const double* eb;  // exp(b_i) in FP64
+    float a;           // exp(-dt / tau), for the tau partials
+    double* part_tau;  // TAU: [3][n][ntile] = sum_t e^v a^(t-t0), sum_t e^v Z_loc[t], Z_loc[t0 + 256]
     void* E;
     double* part_e;
     int64_t ntile;
@@ -87,7 +90,7 @@ struct TcArgs {
 
 struct Unit {
     int32_t m0, n0;
-    int64_t kb0, kb1, split;
+    int64_t kb0, kb1, kstep, split;
 };
 
 template <int MODE>
@@ -98,6 +101,7 @@ __device__ __forceinline__ Unit decode(const TcArgs& A, int64_t u) {
         r.n0 = (int32_t)(u / A.mt) * BN;
         r.kb0 = 0;
         r.kb1 = A.kb_per_unit;
+        r.kstep = 1;
         r.split = 0;
     } else {
         const int64_t tiles = (int64_t)A.mt * A.nt;
@@ -105,8 +109,11 @@ __device__ __forceinline__ Unit decode(const TcArgs& A, int64_t u) {
         r.split = u / tiles;
         r.m0 = (int32_t)(tile % A.mt) * Cfg<1>::BM;
         r.n0 = (int32_t)(tile / A.mt) * BN;
-        r.kb0 = r.split * A.kb_per_unit;
-        r.kb1 = min(r.kb0 + A.kb_per_unit, A.kb_total);
+        // the splits interleave: split s takes k-steps s, s + nsplit, s + 2 nsplit, ...  All blocks then
+        // stream the same narrow band of bins, which stays in L2 while the 16 tiles of each split reuse it.
+        r.kb0 = r.split;
+        r.kb1 = A.kb_total;
+        r.kstep = A.nsplit;
     }
     return r;
 }
@@ -134,7 +141,11 @@ __device__ __forceinline__ uint32_t pack16<__half>(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
-template <int MODE, typename T16>
+// TAU (MODE 0 only): the epilogue also emits, per (row, tile), the partial sums that give the integral
+// part of dL/dtau.  With v = (W X)_i[t] = U_i[t] - b_i, Z_i[t] = a Z_i[t-1] + v[t-1] (Z = W dX/da), the
+// tile's local Z_loc starts at 0 at its first bin t0, and Z[t] = a^(t-t0) Z[t0] + Z_loc[t]; a per-row
+// combine (reduce.cu) chains the tiles.
+template <int MODE, typename T16, bool TAU>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
                    const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1,
@@ -195,7 +206,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             bool ok = true;
             for (int64_t u = blockIdx.x; u < A.units && ok; u += gridDim.x) {
                 const Unit w = decode<MODE>(A, u);
-                for (int64_t kb = w.kb0; kb < w.kb1; ++kb) {
+                for (int64_t kb = w.kb0; kb < w.kb1; kb += w.kstep) {
                     if (!tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag, A.limit_ns)) {
                         raise();
                         ok = false;
@@ -244,7 +255,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 tc::tc_fence_after();
                 const uint32_t d0 = tmem_base + (uint32_t)(buf * BN);
                 const uint32_t d1 = tmem_base + (uint32_t)BN;  // MODE 1: second row half
-                for (int64_t kb = w.kb0; kb < w.kb1; ++kb) {
+                for (int64_t kb = w.kb0; kb < w.kb1; kb += w.kstep) {
                     if (!tc::mbar_wait(&full[stage], phase, abort_flag, A.limit_ns)) {
                         raise();
                         ok = false;
@@ -306,6 +317,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const float dteb = (float)(A.dt * ebi);
                 double rsum = 0.0;
                 bool bad = false;
+                float zl = 0.f, pw = 1.f, p1 = 0.f, p2 = 0.f;
                 T16* erow = reinterpret_cast<T16*>(A.E) + (int64_t)i * A.Tpad + w.n0;
 #pragma unroll 1
                 for (int c = 0; c < BN / 32; ++c) {
@@ -335,6 +347,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                             e1 = 0.f;
                         }
                         pk[e >> 1] = pack16<T16>(dteb * e0, dteb * e1);
+                        if (TAU) {
+                            p1 = fmaf(e0, pw, p1);
+                            p2 = fmaf(e0, zl, p2);
+                            zl = fmaf(A.a, zl, __uint_as_float(r[e]));
+                            pw *= A.a;
+                            p1 = fmaf(e1, pw, p1);
+                            p2 = fmaf(e1, zl, p2);
+                            zl = fmaf(A.a, zl, __uint_as_float(r[e + 1]));
+                            pw *= A.a;
+                        }
                     }
                     rsum += (double)cnt + (double)s;
                     if (i < A.n) {
@@ -346,6 +368,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 }
                 bad |= !(dteb <= 3.0e38f);
                 if (i < A.n) A.part_e[(int64_t)i * A.ntile + w.n0 / BN] = ebi * rsum;
+                if (TAU && i < A.n) {
+                    const int64_t o = (int64_t)i * A.ntile + w.n0 / BN, plane = (int64_t)A.n * A.ntile;
+                    A.part_tau[o] = p1;
+                    A.part_tau[plane + o] = p2;
+                    A.part_tau[2 * plane + o] = zl;
+                }
                 if (bad) atomicOr(A.flags, 1);
             } else {
 #pragma unroll 1
@@ -462,15 +490,15 @@ cudaError_t tc_prepare_maps(glm_ctx* c) {
     return ok ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int MODE, typename T16>
+template <int MODE, typename T16, bool TAU = false>
 static cudaError_t run(glm_ctx* c, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0,
                        const CUtensorMap& b1, const TcArgs& A) {
     const size_t smem = Layout<MODE>::SMEM;
-    cudaError_t e =
-        cudaFuncSetAttribute(tc_gemm_kernel<MODE, T16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<MODE, T16, TAU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t grid = A.units < c->sm_count ? A.units : c->sm_count;
-    tc_gemm_kernel<MODE, T16><<<(unsigned)grid, NUM_THREADS, smem, c->stream>>>(a0, a1, b0, b1, A);
+    tc_gemm_kernel<MODE, T16, TAU><<<(unsigned)grid, NUM_THREADS, smem, c->stream>>>(a0, a1, b0, b1, A);
     return cudaGetLastError();
 }
 
@@ -486,15 +514,18 @@ static TcArgs base_args(glm_ctx* c) {
     A.idesc = tc::idesc_f16(P.prec == GLM_PREC_BF16 ? 1u : 0u, 128, BN);
     A.b = nullptr;
     A.eb = c->buf.eb;
+    A.a = (float)P.a;
+    A.part_tau = nullptr;
     A.E = nullptr;
     A.part_e = nullptr;
     A.part_g = nullptr;
     A.ntile = P.Tpad / BN;
     A.kb_total = 0;
+    A.nsplit = 1;
     return A;
 }
 
-cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b) {
+cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, bool tau) {
     const Problem& P = c->pb;
     const int64_t ldk = c->buf.ldn;
     const int64_t total = (int64_t)P.n * ldk;
@@ -517,6 +548,12 @@ cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b) {
     A.b = b;
     A.E = c->buf.E;
     A.part_e = c->buf.part_e;
+    A.part_tau = c->buf.part_tau;
+    if (tau) {
+        if (P.prec == GLM_PREC_BF16)
+            return run<0, __nv_bfloat16, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
+        return run<0, __half, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
+    }
     if (P.prec == GLM_PREC_BF16)
         return run<0, __nv_bfloat16>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
     return run<0, __half>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
@@ -531,6 +568,7 @@ cudaError_t launch_tc_grad(glm_ctx* c) {
     A.kb_total = (P.T + Cfg<1>::BK - 1) / Cfg<1>::BK;
     A.kb_per_unit = (int32_t)((A.kb_total + ns - 1) / ns);
     A.units = (int64_t)A.mt * A.nt * ns;
+    A.nsplit = ns;
     A.part_g = c->buf.part_g;
     if (P.prec == GLM_PREC_BF16)
         return run<1, __nv_bfloat16>(c, c->tmap[4], c->tmap[4], c->tmap[5], c->tmap[5], A);

@@ -3,14 +3,16 @@ inputs that span several tiles and ragged tails, plus edge cases, error paths an
 full N = 1000, 1.8M-bin size.
 
 Tolerances.  Plain FP32 form: filtered trains within a few FP32 ulps; spike term relative 5e-7 (a sum
-of FP32 X values, each rounded once or twice); log-likelihood relative 2e-9 (total) and 5e-8 (per row).
+of FP32 X values, each rounded once or twice); log-likelihood relative 2e-9 (total) and, per row, 5e-8 of
+(|L_i| + q_i), the size of its terms (L_i itself can cross zero).
 The total-L bound is set by the FP32 storage of X itself: the rounding of the kernel values
 e^{-k dt/tau} (Eq. 13) repeats identically after every spike, so it does not average out over bins; its
 effect on the integral term is about 2^-24 E|U - b| ~ 1e-9 relative.
 gradient componentwise relative 1e-5 against the size of its two terms, |dG_ij| / (C_ij + dt sum_t
 e^{U_i} X_j).  Tensor-core forms (X and the rates in BF16 or FP16, W as hi + lo): total log-likelihood
 relative 1e-6, gradient 2e-3 in the same componentwise measure.  Per row, the X rounding error
-(relative 2^-9 for BF16, 2^-12 for FP16, random over bins) bounds the integral term's error by about
+(relative 2^-9 for BF16, 2^-12 for FP16, random over bins; per-row errors are also measured against
+(|L_i| + q_i)) bounds the integral term's error by about
 sqrt(T) * dt e^U * 2^-9 |W X|: the per-row bounds below (3e-5 BF16, 4e-6 FP16) follow from that.
 """
 import math
@@ -135,7 +137,7 @@ def test_loglik_grad_f32_matches_oracle(ctx, n, T, seed, scale):
     ref = oracle.loglik_grad(w["offs"], w["bins"], T, w["dt"], w["tau"], W.astype(np.float64), b.astype(np.float64))
     assert abs(r["L_total"] - ref["L_total"]) <= 2e-9 * abs(ref["L_total"])
     Lr = r["L_rows"].cpu().numpy()
-    assert np.all(np.abs(Lr - ref["L"]) <= 5e-8 * np.abs(ref["L"]) + 1e-9)
+    assert np.all(np.abs(Lr - ref["L"]) <= 5e-8 * (np.abs(ref["L"]) + np.diff(w["offs"])))
     gb = r["gb"].cpu().numpy()
     q = np.diff(w["offs"]).astype(np.float64)
     assert np.all(np.abs(gb - ref["gb"]) <= 1e-8 * (q + np.abs(q - ref["gb"])) + 1e-9)
@@ -159,7 +161,7 @@ def test_loglik_grad_tensor_core_matches_oracle(ctx, prec, n, T, seed, scale):
     ref = oracle.loglik_grad(w["offs"], w["bins"], T, w["dt"], w["tau"], W.astype(np.float64), b.astype(np.float64))
     rel_tot = abs(r["L_total"] - ref["L_total"]) / abs(ref["L_total"])
     Lr = r["L_rows"].cpu().numpy()
-    rel_rows = np.max(np.abs(Lr - ref["L"]) / np.abs(ref["L"]))
+    rel_rows = np.max(np.abs(Lr - ref["L"]) / (np.abs(ref["L"]) + np.diff(w["offs"])))
     C, _ = ctx.spike_term()
     g = metric10(r["G"].cpu().numpy(), ref["G"], C.cpu().numpy())
     print(f"{prec} n={n} T={T}: L total rel {rel_tot:.2e}, rows max rel {rel_rows:.2e}, grad {g:.2e}")
@@ -190,7 +192,7 @@ def test_zero_spike_rows_and_single_neuron(ctx):
     ctx.set_problem(offs, bins, T, 1e-3, 0.01, prec="f32")
     r = ctx.loglik_grad(to_dev(W), to_dev(b))
     ref = oracle.loglik_grad(offs, bins, T, 1e-3, 0.01, W.astype(np.float64), b.astype(np.float64))
-    assert np.allclose(r["L_rows"].cpu().numpy(), ref["L"], rtol=1e-9)
+    assert np.all(np.abs(r["L_rows"].cpu().numpy() - ref["L"]) <= 5e-8 * (np.abs(ref["L"]) + np.diff(offs)))
     assert np.allclose(r["G"].cpu().numpy(), ref["G"], rtol=1e-6, atol=1e-9)
     # one neuron, one bin
     ctx.set_problem(np.array([0, 1], dtype=np.int64), np.array([0], dtype=np.int32), 1, 1e-3, 0.01, prec="f32")
@@ -263,7 +265,7 @@ def test_full_size_sampled_rows_bf16(ctx, full_size):
     ref = oracle.eval_rows(w["offs"], w["bins"], T, w["dt"], w["tau"], W.astype(np.float64), b.astype(np.float64),
                            rows)
     Lr = r["L_rows"].cpu().numpy()[rows]
-    rel = np.abs(Lr - ref["L"]) / np.abs(ref["L"])
+    rel = np.abs(Lr - ref["L"]) / (np.abs(ref["L"]) + np.diff(w["offs"])[rows])
     C, _ = ctx.spike_term()
     g = metric10(r["G"].cpu().numpy()[rows], ref["G"], C.cpu().numpy()[rows])
     print(f"full-size bf16: rows rel {rel}, grad {g:.2e}")
@@ -283,7 +285,7 @@ def test_full_size_sampled_rows_f32(ctx, full_size):
     ref = oracle.eval_rows(w["offs"], w["bins"], T, w["dt"], w["tau"], W.astype(np.float64), b.astype(np.float64),
                            rows)
     Lr = r["L_rows"].cpu().numpy()[rows]
-    assert np.all(np.abs(Lr - ref["L"]) <= 5e-8 * np.abs(ref["L"])), (Lr, ref["L"])
+    assert np.all(np.abs(Lr - ref["L"]) <= 5e-8 * (np.abs(ref["L"]) + np.diff(w["offs"])[rows])), (Lr, ref["L"])
     C, _ = ctx.spike_term()
     Cr = C.cpu().numpy()[rows]
     assert metric10(r["G"].cpu().numpy()[rows], ref["G"], Cr) <= 1e-5
