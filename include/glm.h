@@ -235,6 +235,31 @@ typedef struct {
 int glm_classify(const double* W_host, int32_t n, const glm_classify_opts_t* opts, int8_t* labels_out,
                  const int8_t* truth_host, const int8_t* types_host, glm_classify_report_t* report);
 
+/* ---- allocation-free log-likelihood ----
+ * The paper has no counterpart to this call; it exists for callers that may not allocate device memory:
+ * processes whose device memory belongs to another allocator (a framework's caching pool, a pre-reserved
+ * arena) and loops that must not call cudaMalloc after start-up.  It needs no context and allocates
+ * nothing: its temporary storage is one fixed array of GLM_NOALLOC_SCRATCH_BYTES in device memory, part
+ * of the library image, which every GPU that loads the library holds until the process exits.
+ *
+ * Computes the per-row log-likelihood of the plain FP32 form (the same quantity as glm_loglik_grad's
+ * L_rows for a GLM_PREC_F32 problem) from caller buffers, all device pointers on the current device:
+ *   X_dev:  float [n][ldx], the filtered trains X[:, 0 : n_bins] (e.g. from glm_filter), ldx >= n_bins
+ *   C_dev:  double [n][n], the spike term (e.g. from glm_spike_term);  q_dev: double [n], spike counts
+ *   W_dev:  float [n][n];  b_dev: float [n]
+ *   L_rows_dev: double [n] output.  A non-finite exp(U) or input shows up as a non-finite L_i.
+ *   cuda_stream: the stream to queue the work on (NULL = legacy default stream); the call does not wait.
+ * Needs n * (ceil(n_bins / 128) + 1) * 8 bytes <= GLM_NOALLOC_SCRATCH_BYTES, else returns
+ * GLM_ERR_SCRATCH_TOO_SMALL without doing anything.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) once for that device: make that first call outside any stream
+ * capture.  All calls share the one array, so calls whose work overlaps on the GPU (two streams, two host
+ * threads) race; serialise them.  Errors: INVALID_ARG, SCRATCH_TOO_SMALL, CUDA. */
+#define GLM_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define GLM_ERR_SCRATCH_TOO_SMALL (-11)
+int glm_loglik_noalloc(int32_t n, int64_t n_bins, double dt, const float* X_dev, int64_t ldx, const double* C_dev,
+                       const double* q_dev, const float* W_dev, const float* b_dev, double* L_rows_dev,
+                       void* cuda_stream);
+
 /* ---- tracing ----
  * While profiling is enabled, every kernel group the context launches (filter_scan, carry, spike_term,
  * u_epilogue, grad, reduce, ...) is bracketed by CUDA events recorded on the context's stream.

@@ -70,6 +70,8 @@ class FitReport(ctypes.Structure):
 
 
 ROW_STATUS = {0: "converged", 1: "maxiter", 2: "stalled", 3: "degenerate", 4: "at_floor"}
+ERRORS[-11] = "GLM_ERR_SCRATCH_TOO_SMALL"
+SIGNATURES["glm_loglik_noalloc"] = ([_i32, _i64, _f64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int)
 SIGNATURES["glm_fit_default_opts"] = ([ctypes.POINTER(FitOpts)], None)
 SIGNATURES["glm_fit"] = ([_vp, ctypes.POINTER(FitOpts), _vp, _vp, _vp, ctypes.POINTER(FitReport)], ctypes.c_int)
 SIGNATURES["glm_classify"] =([_vp, _i32, ctypes.POINTER(ClassifyOpts), _vp, _vp, _vp, ctypes.POINTER(ClassifyReport)],

@@ -264,6 +264,7 @@ const char* glm_strerror(int code) {
         case GLM_ERR_UNSUPPORTED_ARCH: return "tensor-core precision needs an sm_103 GPU";
         case GLM_ERR_NO_PROBLEM: return "no problem set (call glm_set_problem first)";
         case GLM_ERR_UNSUPPORTED: return "unsupported request";
+        case GLM_ERR_SCRATCH_TOO_SMALL: return "problem too large for the fixed scratch of glm_loglik_noalloc";
         default: return "unknown status";
     }
 }
