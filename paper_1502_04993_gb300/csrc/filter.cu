@@ -225,7 +225,7 @@ struct FilterArgs {
     const double* seg_carry;
     const int32_t* seg_first;
     void* X;
-    void* XT;
+    void* Xlo;  // 16-bit forms: X_lo [n][Tpad]
 };
 
 // F32 X, one warp per (8 rows, 4096-bin chunk).
@@ -272,18 +272,10 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache_f32_kernel(const _
     }
 }
 
-// 16-bit caches: X_hi row-major [n][Tpad] (operand of E X^T), and X_hi^T, X_lo^T [Tpad][ldn] with
-// X_lo = X - X_hi rounded again (operands of U = W X).  Block = 8 warps = 64 rows x one 4096-bin chunk.
-// Per 256-bin segment each warp scans its 8 rows, stores X_hi rows directly, and drops the transposed
-// 8 x 8 blocks into a shared tile [256 bins][64 rows] whose 16-byte chunks are XOR-swizzled by bin, so
-// that the block then writes every X^T row segment as one 128-byte line.
-constexpr int F16_WARPS = 8;
-
-__device__ __forceinline__ uint32_t trans_word(const uint32_t (&pk)[8][4], int m, int qd) {
-    const uint32_t sel = (m & 1) ? 0x7632u : 0x5410u;
-    return __byte_perm(pk[2 * qd][m >> 1], pk[2 * qd + 1][m >> 1], sel);
-}
-
+// 16-bit caches: X_hi and X_lo, X_lo = X - X_hi rounded again, both bin-blocked [Tpad / 64][n][64] (bins
+// [64 b, 64 b + 64) of row r at (b n + r) 64), the layout the tensor-core products read.  One warp per
+// (8 rows, 4096-bin chunk), as for the FP32 form: each lane stores its 8 bins of a row as one 16-byte
+// word of X_hi and one of X_lo, so every warp store covers four whole 128-byte lines.
 template <typename T16>
 __device__ __forceinline__ float to_f(T16 v);
 template <>
@@ -299,14 +291,13 @@ template <>
 __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
 
 template <typename T16>
-__global__ void __launch_bounds__(F16_WARPS * 32, 2) filter_cache16_kernel(const __grid_constant__ ScanConsts K,
-                                                                           const __grid_constant__ FilterArgs A) {
-    extern __shared__ uint4 f16_smem[];
-    uint4* tile_hi = f16_smem;            // [SEG][8] 16-byte chunks
-    uint4* tile_lo = f16_smem + SEG * 8;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t c = blockIdx.x;
-    const int32_t r0 = blockIdx.y * 64 + warp * 8;
+__global__ void __launch_bounds__(FW_WARPS * 32) filter_cache16_kernel(const __grid_constant__ ScanConsts K,
+                                                                       const __grid_constant__ FilterArgs A) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wg = (int64_t)blockIdx.x * FW_WARPS + (threadIdx.x >> 5);
+    const int64_t c = wg / A.ngroups;
+    const int32_t g = (int32_t)(wg % A.ngroups);
+    if (c >= A.nchunks) return;
     const float pl_hi = K.pl_hi[lane], pl_lo = K.pl_lo[lane];
     const int64_t s0 = c * CHUNK_SEGS;
     const int64_t s1 = min(s0 + (int64_t)CHUNK_SEGS, A.nseg);
@@ -314,7 +305,7 @@ __global__ void __launch_bounds__(F16_WARPS * 32, 2) filter_cache16_kernel(const
     int64_t cur[8], end[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const int32_t r = r0 + k;
+        const int32_t r = g * 8 + k;
         if (r < A.n) {
             xs[k] = (float)A.seg_carry[(int64_t)r * A.nseg + s0];
             cur[k] = A.offs[r] + A.seg_first[(int64_t)r * A.nseg + s0];
@@ -325,48 +316,30 @@ __global__ void __launch_bounds__(F16_WARPS * 32, 2) filter_cache16_kernel(const
             end[k] = 0;
         }
     }
-    T16* XT_hi = reinterpret_cast<T16*>(A.XT);
-    T16* XT_lo = XT_hi + A.Tpad * A.ldn;
+    T16* Xh = reinterpret_cast<T16*>(A.X);
+    T16* Xl = reinterpret_cast<T16*>(A.Xlo);
     for (int64_t s = s0; s < s1; ++s) {
         const int64_t t0 = s * SEG;
         const int64_t tl = t0 + 8 * lane;
-        uint32_t ph[8][4], plo[8][4];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
+            const int32_t r = g * 8 + k;
             const uint32_t bits = seg_bits(A.bins, cur[k], end[k], t0, lane);
             float v[8];
             xs[k] = seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v);
+            uint32_t ph[4], pl[4];
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
                 const T16 h0 = from_f<T16>(v[2 * p]), h1 = from_f<T16>(v[2 * p + 1]);
-                ph[k][p] = pack2<T16>(to_f<T16>(h0), to_f<T16>(h1));
-                plo[k][p] = pack2<T16>(v[2 * p] - to_f<T16>(h0), v[2 * p + 1] - to_f<T16>(h1));
+                ph[p] = pack2<T16>(to_f<T16>(h0), to_f<T16>(h1));
+                pl[p] = pack2<T16>(v[2 * p] - to_f<T16>(h0), v[2 * p + 1] - to_f<T16>(h1));
             }
-            if (r0 + k < A.n) {
-                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<T16*>(A.X) + (int64_t)(r0 + k) * A.Tpad + tl);
-                *dst = make_uint4(ph[k][0], ph[k][1], ph[k][2], ph[k][3]);
+            if (r < A.n) {
+                const int64_t o = ((tl >> 6) * A.n + r) * 64 + (tl & 63);
+                *reinterpret_cast<uint4*>(Xh + o) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+                *reinterpret_cast<uint4*>(Xl + o) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
             }
         }
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            const int bin = 8 * lane + m;
-            const int slot = bin * 8 + (warp ^ (lane & 7));
-            tile_hi[slot] = make_uint4(trans_word(ph, m, 0), trans_word(ph, m, 1), trans_word(ph, m, 2),
-                                       trans_word(ph, m, 3));
-            tile_lo[slot] = make_uint4(trans_word(plo, m, 0), trans_word(plo, m, 1), trans_word(plo, m, 2),
-                                       trans_word(plo, m, 3));
-        }
-        __syncthreads();
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int idx = e * (F16_WARPS * 32) + threadIdx.x;
-            const int bin = idx >> 3, ch = idx & 7;
-            const int slot = bin * 8 + (ch ^ ((bin >> 3) & 7));
-            const int64_t o = (t0 + bin) * A.ldn + (int64_t)blockIdx.y * 64 + ch * 8;
-            *reinterpret_cast<uint4*>(XT_hi + o) = tile_hi[slot];
-            *reinterpret_cast<uint4*>(XT_lo + o) = tile_lo[slot];
-        }
-        __syncthreads();
     }
 }
 
@@ -448,26 +421,18 @@ cudaError_t launch_filter_cache(glm_ctx* c) {
     A.seg_carry = c->buf.seg_carry;
     A.seg_first = c->buf.seg_first;
     A.X = c->buf.X;
-    A.XT = c->buf.XT;
+    A.Xlo = c->buf.Xlo;
     if (P.prec == GLM_PREC_F32) {
         const int64_t warps = (int64_t)A.ngroups * A.nchunks;
         const int64_t blocks = (warps + FW_WARPS - 1) / FW_WARPS;
         filter_cache_f32_kernel<<<(unsigned)blocks, FW_WARPS * 32, 0, c->stream>>>(c->sc, A);
     } else {
-        dim3 grid((unsigned)A.nchunks, (unsigned)((P.n + 63) / 64));
-        const int smem = 2 * SEG * 8 * (int)sizeof(uint4);
-        cudaError_t e;
-        if (P.prec == GLM_PREC_BF16) {
-            e = cudaFuncSetAttribute(filter_cache16_kernel<__nv_bfloat16>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e != cudaSuccess) return e;
-            filter_cache16_kernel<__nv_bfloat16><<<grid, F16_WARPS * 32, smem, c->stream>>>(c->sc, A);
-        } else {
-            e = cudaFuncSetAttribute(filter_cache16_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     smem);
-            if (e != cudaSuccess) return e;
-            filter_cache16_kernel<__half><<<grid, F16_WARPS * 32, smem, c->stream>>>(c->sc, A);
-        }
+        const int64_t warps = (int64_t)A.ngroups * A.nchunks;
+        const int64_t blocks = (warps + FW_WARPS - 1) / FW_WARPS;
+        if (P.prec == GLM_PREC_BF16)
+            filter_cache16_kernel<__nv_bfloat16><<<(unsigned)blocks, FW_WARPS * 32, 0, c->stream>>>(c->sc, A);
+        else
+            filter_cache16_kernel<__half><<<(unsigned)blocks, FW_WARPS * 32, 0, c->stream>>>(c->sc, A);
     }
     return cudaGetLastError();
 }

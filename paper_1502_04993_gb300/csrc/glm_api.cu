@@ -386,7 +386,7 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
         (rc = ws_alloc_t(c, &B.part_e, (size_t)n * (P.Tpad / (tensor ? tc_tile_t() : simt_tile_t())))) ||
         (rc = ws_alloc_t(c, &B.part_g, nn * (tensor ? tc_nsplit(c) : grad_nsplit(c)))) ||
         (rc = ws_alloc_t(c, &B.flags, 4)) || (rc = ws_alloc_t(c, &B.Lrows, n)) || (rc = ws_alloc_t(c, &B.scal, 8)) || (rc = ws_alloc_t(c, &B.eb, n)) ||
-        (tensor && (rc = ws_alloc(c, &B.XT, 2 * (size_t)P.Tpad * B.ldn * 2))) ||
+        (tensor && (rc = ws_alloc(c, &B.Xlo, (size_t)P.n * P.Tpad * 2))) ||
         (tensor && (rc = ws_alloc(c, &B.Wsplit, 2 * (size_t)n * B.ldn * 2)))) {
         free_all(c);
         return rc;

@@ -52,7 +52,7 @@ struct Buffers {
     double* C = nullptr;          // [n][n]      spike term
     double* C_part = nullptr;     // [parts][n][n]
     void* X = nullptr;            // F32: float [n][Tpad]; 16-bit: [n][Tpad]
-    void* XT = nullptr;           // 16-bit only: X_hi^T then X_lo^T, each [Tpad][ldn]
+    void* Xlo = nullptr;          // 16-bit only: X_lo = X - X_hi, [n][Tpad]
     int64_t ldn = 0;              // leading dim of X^T and of the W parts (n rounded up to 64)
     void* E = nullptr;            // F32: float [n][Tpad]; 16-bit: [n][Tpad]   dt * exp(U)
     double* part_e = nullptr;     // [n][ntile_t]  per-(row, bin tile) sums of exp(U)

@@ -3,16 +3,17 @@
 // which does not depend on W or b and is computed once per problem (Sec. 2.3.3, 2.6.1).  With it
 //   sum_t S_i[t] U_i[t] = q_i b_i + sum_j W_ij C_ij    and    dL_i/dW_ij = C_ij - dt sum_t e^{U_i[t]} X_j[t].
 //
-// Block = (16 presynaptic rows j, a part of the time axis, a slice of postsynaptic rows i), 16 warps.  For
-// each 2048-bin sub-chunk:
-//   phase A  the warps scan X_j for the 16 rows into shared memory (warp = one 256-bin segment x 8 rows,
-//            started from the FP64 segment carries; the loads of a pass's 4 rows are issued together);
-//   phase B  every thread walks the spikes of its postsynaptic rows i in the sub-chunk and accumulates
-//            X_j[t] for the 16 rows.  Its spike cursor is carried from sub-chunk to sub-chunk, the end
-//            index of the next sub-chunk is fetched before phase A, and spike bins are loaded one batch
-//            ahead of their use, so the global-memory latency overlaps with work.
-// Sums are kept as an FP32 hi + lo pair (TwoSum) refreshed after every batch of at most 4 spikes, so they
-// carry ~44 significant bits; their order is fixed and the result deterministic.
+// Block = (16 presynaptic rows j, a part of the time axis, a slice of 1024 postsynaptic rows i), 16 warps,
+// two rows i per thread.  For each 1024-bin sub-chunk:
+//   staging  every thread starts asynchronous copies (cp.async) of its rows' spike bins in the sub-chunk
+//            (up to 24 per row) into shared memory, laid out [spike][row slot][thread] so that the later
+//            reads of a warp are conflict-free;
+//   phase A  meanwhile the warps scan X_j for the 16 rows into shared memory (warp = one 256-bin segment x
+//            4 rows, started from the FP64 segment carries);
+//   phase B  every thread walks the staged spikes of its rows and accumulates X_j[t] for the 16 rows (spikes
+//            beyond the staged 24 are read from global memory).
+// Each row's spikes in a sub-chunk are summed in plain FP32, and these partial sums enter an FP32 hi + lo
+// pair (TwoSum) that carries ~44 significant bits; the order is fixed and the result deterministic.
 #include <cmath>
 
 #include "glm_internal.h"
@@ -22,15 +23,25 @@ namespace glm {
 
 constexpr int ST_THREADS = 512;
 constexpr int ST_JB = 16;                     // presynaptic rows per block
-constexpr int ST_SUBSEGS = 8;                 // 2048 bins per sub-chunk
+constexpr int ST_SUBSEGS = 4;                 // 1024 bins per sub-chunk
 constexpr int ST_SUB = ST_SUBSEGS * SEG;
 constexpr int ST_KI = 2;                      // postsynaptic rows per thread
 constexpr int ST_ROWS_PER_SLICE = ST_THREADS * ST_KI;
-constexpr int ST_BATCH = 4;                   // spike bins per batch (and per plain FP32 partial sum)
+constexpr int ST_CAP = 24;                    // spike bins per row and sub-chunk staged in shared memory
+static_assert(ST_THREADS / 32 == ST_SUBSEGS * (ST_JB / 4), "phase A: one warp per (segment, 4 rows)");
 
-// Xs layout: [bin][16 floats] = 4 chunks of 16 bytes per bin, chunk index XOR-swizzled by bin so that the
-// phase-A stores (lanes 8 bins apart) spread over the banks.
-__device__ __forceinline__ int xs_slot(int bin, int chunk) { return bin * 4 + (chunk ^ ((bin >> 3) & 3)); }
+// Xs layout: [bin][16 floats] = 4 chunks of 16 bytes per bin, plus one 16-byte pad after every 8 bins.  The
+// phase-A stores (lane l writes bin 8 l + m) then fall 33 chunks apart, i.e. on 8 different bank groups per
+// quarter warp, and the phase-B loads of one bin are 4 consecutive chunks (one base, immediate offsets).
+constexpr int XS_CHUNKS = ST_SUB * 4 + ST_SUB / 8;
+constexpr size_t ST_SMEM = (size_t)XS_CHUNKS * 16 + (size_t)ST_CAP * ST_KI * ST_THREADS * 4;
+__device__ __forceinline__ int xs_base(int bin) { return bin * 4 + (bin >> 3); }
+
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 __device__ __forceinline__ void two_sum(float& hi, float& lo, float x) {
     const float s = hi + x;
@@ -81,7 +92,9 @@ struct SpikeTermArgs {
 template <bool DY>
 __global__ void __launch_bounds__(ST_THREADS, 1) spike_term_kernel(const __grid_constant__ ScanConsts K,
                                                                    const __grid_constant__ SpikeTermArgs A) {
-    extern __shared__ float4 Xs[];  // [ST_SUB * 4]
+    extern __shared__ float4 Xs[];  // [XS_CHUNKS], then the staged spike bins
+    int32_t* Sp = reinterpret_cast<int32_t*>(Xs + XS_CHUNKS);  // [ST_CAP][ST_KI][ST_THREADS], bin - sub-chunk start
+    const uint32_t sp_addr = (uint32_t)__cvta_generic_to_shared(Sp);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int32_t j0 = blockIdx.x * ST_JB;
     const int64_t part = blockIdx.y;
@@ -91,116 +104,124 @@ __global__ void __launch_bounds__(ST_THREADS, 1) spike_term_kernel(const __grid_
     const int64_t sp0 = part * A.segs_per_part;
     const int64_t sp1 = min(sp0 + A.segs_per_part, A.nseg);
     const int seg_w = warp & (ST_SUBSEGS - 1);   // phase A: this warp's segment
-    const int half_w = warp >> 3;                // and its 8 of the 16 presynaptic rows
+    const int grp_w = warp / ST_SUBSEGS;         // and its 4 of the 16 presynaptic rows
 
     float acc_hi[ST_KI][ST_JB], acc_lo[ST_KI][ST_JB];
-    int64_t cur[ST_KI], rend[ST_KI];
+    int64_t cur[ST_KI], rend[ST_KI], nxt[ST_KI];
 #pragma unroll
     for (int k = 0; k < ST_KI; ++k) {
 #pragma unroll
         for (int jj = 0; jj < ST_JB; ++jj) acc_hi[k][jj] = acc_lo[k][jj] = 0.f;
         const int32_t i = i_base + threadIdx.x + k * ST_THREADS;
-        cur[k] = rend[k] = 0;
+        cur[k] = rend[k] = nxt[k] = 0;
         if (i < A.n && sp0 < sp1) {
             const int64_t o0 = A.offs[i];
             cur[k] = o0 + A.seg_first[(int64_t)i * A.nseg + sp0];
             rend[k] = A.offs[i + 1];
+            const int64_t sn = min(sp1, sp0 + ST_SUBSEGS);
+            nxt[k] = (sn < A.nseg) ? o0 + A.seg_first[(int64_t)i * A.nseg + sn] : rend[k];
         }
     }
 
     for (int64_t sc = sp0; sc < sp1; sc += ST_SUBSEGS) {
-        const int64_t sn = min(sp1, sc + ST_SUBSEGS);
         const int64_t tb = sc * SEG;
-        // ---- prefetch for phase B: end of each row's spikes in this sub-chunk, first batch of bins ----
+        // ---- staging: this sub-chunk's spike bins of the thread's rows, asynchronously ----
         int64_t k1[ST_KI];
-        int tl[ST_KI][ST_BATCH];
+        int cnt[ST_KI];
+#pragma unroll
+        for (int k = 0; k < ST_KI; ++k) {
+            k1[k] = nxt[k];
+            cnt[k] = (int)(k1[k] - cur[k]);
+            const int c = min(cnt[k], ST_CAP);
+            for (int u = 0; u < c; ++u)
+                cp_async4(sp_addr + 4u * (uint32_t)((u * ST_KI + k) * ST_THREADS + threadIdx.x), A.bins + cur[k] + u);
+        }
+        cp_async_commit();
+        // end of each row's spikes in the next sub-chunk, for the next staging step
+        const int64_t s2 = min(sp1, sc + 2 * ST_SUBSEGS);
 #pragma unroll
         for (int k = 0; k < ST_KI; ++k) {
             const int32_t i = i_base + threadIdx.x + k * ST_THREADS;
-            k1[k] = cur[k];
-            if (i < A.n) k1[k] = (sn < A.nseg) ? A.offs[i] + A.seg_first[(int64_t)i * A.nseg + sn] : rend[k];
-#pragma unroll
-            for (int u = 0; u < ST_BATCH; ++u)
-                tl[k][u] = (cur[k] + u < rend[k]) ? (int)(__ldg(A.bins + cur[k] + u) - tb) : ST_SUB;
+            if (i < A.n && sc + ST_SUBSEGS < sp1)
+                nxt[k] = (s2 < A.nseg) ? A.offs[i] + A.seg_first[(int64_t)i * A.nseg + s2] : rend[k];
         }
         // ---- phase A: X_j for the 16 rows over this sub-chunk, into shared memory ----
         const int64_t s = sc + seg_w;
         if (s < sp1) {
             const int64_t t0 = s * SEG;
-#pragma unroll 1
-            for (int pass = 0; pass < 2; ++pass) {  // 4 rows per pass: one 16-byte chunk per bin
-                float xs[4], ys[4];
-                int64_t rc[4], re[4], sv[4];
+            float xs[4], ys[4];
+            int64_t rc[4], re[4], sv[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int32_t r = j0 + half_w * 8 + pass * 4 + k;
-                    xs[k] = ys[k] = 0.f;
-                    rc[k] = re[k] = 0;
-                    if (r < A.n) {
-                        xs[k] = (float)A.seg_carry[(int64_t)r * A.nseg + s];
-                        if (DY) ys[k] = (float)A.seg_carry_y[(int64_t)r * A.nseg + s];
-                        rc[k] = A.offs[r] + A.seg_first[(int64_t)r * A.nseg + s];
-                        re[k] = A.offs[r + 1];
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int64_t kk = rc[k] + lane;
-                    sv[k] = (kk < re[k]) ? (int64_t)__ldg(A.bins + kk) : INT64_MAX;
-                }
-                float v[4][8];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint32_t bits = seg_bits_pre(A.bins, rc[k], re[k], t0, lane, sv[k]);
-                    if (DY) {
-                        float xe, ye;
-                        seg_scan_xy(K, xs[k], ys[k], bits, lane, pl_hi, pl_lo, pld_hi, pld_lo, v[k], &xe, &ye);
-                    } else {
-                        seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v[k]);
-                    }
-                }
-#pragma unroll
-                for (int m = 0; m < 8; ++m) {
-                    const int bin = seg_w * SEG + 8 * lane + m;
-                    Xs[xs_slot(bin, half_w * 2 + pass)] = make_float4(v[0][m], v[1][m], v[2][m], v[3][m]);
+            for (int k = 0; k < 4; ++k) {
+                const int32_t r = j0 + grp_w * 4 + k;
+                xs[k] = ys[k] = 0.f;
+                rc[k] = re[k] = 0;
+                if (r < A.n) {
+                    xs[k] = (float)A.seg_carry[(int64_t)r * A.nseg + s];
+                    if (DY) ys[k] = (float)A.seg_carry_y[(int64_t)r * A.nseg + s];
+                    rc[k] = A.offs[r] + A.seg_first[(int64_t)r * A.nseg + s];
+                    re[k] = A.offs[r + 1];
                 }
             }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t kk = rc[k] + lane;
+                sv[k] = (kk < re[k]) ? (int64_t)__ldg(A.bins + kk) : INT64_MAX;
+            }
+            float v[4][8];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t bits = seg_bits_pre(A.bins, rc[k], re[k], t0, lane, sv[k]);
+                if (DY) {
+                    float xe, ye;
+                    seg_scan_xy(K, xs[k], ys[k], bits, lane, pl_hi, pl_lo, pld_hi, pld_lo, v[k], &xe, &ye);
+                } else {
+                    seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v[k]);
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int bin = seg_w * SEG + 8 * lane + m;
+                Xs[xs_base(bin) + grp_w] = make_float4(v[0][m], v[1][m], v[2][m], v[3][m]);
+            }
         }
+        cp_async_wait_all();
         __syncthreads();
-        // ---- phase B: the spikes of this thread's postsynaptic rows in [tb, te) ----
+        // ---- phase B: the spikes of this thread's postsynaptic rows in the sub-chunk ----
 #pragma unroll
         for (int k = 0; k < ST_KI; ++k) {
             float sh[ST_JB];
 #pragma unroll
             for (int jj = 0; jj < ST_JB; ++jj) sh[jj] = 0.f;
-            for (int64_t kb = cur[k]; kb < k1[k]; kb += ST_BATCH) {
-                // next batch in flight while this one is summed
-                int nx[ST_BATCH];
+            const int c = min(cnt[k], ST_CAP);
+            const int32_t* sk = Sp + k * ST_THREADS + threadIdx.x;
+#pragma unroll 2
+            for (int u = 0; u < c; ++u) {
+                const int t = sk[u * ST_KI * ST_THREADS] - (int)tb;
+                const float4* xp = Xs + xs_base(t);
 #pragma unroll
-                for (int u = 0; u < ST_BATCH; ++u) {
-                    const int64_t q = kb + ST_BATCH + u;
-                    nx[u] = (q < k1[k]) ? (int)(__ldg(A.bins + q) - tb) : ST_SUB;
+                for (int ch = 0; ch < 4; ++ch) {
+                    const float4 x = xp[ch];
+                    sh[4 * ch + 0] += x.x;
+                    sh[4 * ch + 1] += x.y;
+                    sh[4 * ch + 2] += x.z;
+                    sh[4 * ch + 3] += x.w;
                 }
-#pragma unroll
-                for (int u = 0; u < ST_BATCH; ++u) {
-                    if (kb + u >= k1[k]) break;
-#pragma unroll
-                    for (int ch = 0; ch < 4; ++ch) {
-                        const float4 x = Xs[xs_slot(tl[k][u], ch)];
-                        sh[4 * ch + 0] += x.x;
-                        sh[4 * ch + 1] += x.y;
-                        sh[4 * ch + 2] += x.z;
-                        sh[4 * ch + 3] += x.w;
-                    }
-                }
-#pragma unroll
-                for (int jj = 0; jj < ST_JB; ++jj) {
-                    two_sum(acc_hi[k][jj], acc_lo[k][jj], sh[jj]);
-                    sh[jj] = 0.f;
-                }
-#pragma unroll
-                for (int u = 0; u < ST_BATCH; ++u) tl[k][u] = nx[u];
             }
+            for (int u = ST_CAP; u < cnt[k]; ++u) {  // beyond the staged spikes (rows firing fast)
+                const int t = (int)(__ldg(A.bins + cur[k] + u) - tb);
+                const float4* xp = Xs + xs_base(t);
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch) {
+                    const float4 x = xp[ch];
+                    sh[4 * ch + 0] += x.x;
+                    sh[4 * ch + 1] += x.y;
+                    sh[4 * ch + 2] += x.z;
+                    sh[4 * ch + 3] += x.w;
+                }
+            }
+#pragma unroll
+            for (int jj = 0; jj < ST_JB; ++jj) two_sum(acc_hi[k][jj], acc_lo[k][jj], sh[jj]);
             cur[k] = k1[k];
         }
         __syncthreads();
@@ -253,7 +274,7 @@ cudaError_t launch_spike_term(glm_ctx* c, bool dy, double* out) {
     A.seg_carry_y = c->buf.seg_carry_y;
     A.seg_first = c->buf.seg_first;
     A.C_part = c->buf.C_part;
-    const size_t smem = (size_t)ST_SUB * ST_JB * sizeof(float);
+    const size_t smem = ST_SMEM;
     dim3 grid((P.n + ST_JB - 1) / ST_JB, parts, (P.n + ST_ROWS_PER_SLICE - 1) / ST_ROWS_PER_SLICE);
     cudaError_t e;
     if (dy) {

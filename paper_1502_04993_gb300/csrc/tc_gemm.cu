@@ -4,11 +4,16 @@
 //                         U ~ W_hi X_hi + W_lo X_hi + W_hi X_lo (the dropped W_lo X_lo is ~2^-16 of U - b),
 //                         with the link in the epilogue (Eq. 5): E[i][t] = dt exp(U_i[t]) stored 16-bit,
 //                         FP64 per-(row, 256-bin tile) sums of exp(U).
-//                         Tile 128 x 256, K step 32 (64-byte swizzle), 4 stages of (W_hi, W_lo, X_hi^T, X_lo^T),
-//                         3 MMAs per 16-wide k slice, 2 TMEM accumulators (epilogue overlaps the next tile).
+//                         Tile 128 x 256, K step 32, 4 stages of (W_hi, W_lo, X_hi, X_lo).  W is K-major (64-byte
+//                         swizzle); X is an N-major operand: one 3-D box of 4 bin blocks x 32 neurons x 64 bins
+//                         (128-byte swizzle) per stage.  3 MMAs per 16-wide k slice, 2 TMEM accumulators
+//                         (epilogue overlaps the next tile).
 //   MODE 1, step a5:      P_s = E X^T over a split s of the bins.  Tile 256 x 256 per block as two 128 x 256
 //                         accumulators that share every X tile (A0 = E rows m0.., A1 = E rows m0+128..),
 //                         K step 64 (128-byte swizzle), 3 stages, FP32 partials per split.
+//
+// X_hi, X_lo and E are stored bin-blocked, [Tpad / 64][n][64]: a block of 64 bins of every neuron is one
+// contiguous n x 128-byte array, so every TMA box of either product is a contiguous stretch of memory.
 //
 // One persistent block per SM, 6 warps: warp 0 issues TMA loads, warp 1 owns TMEM and issues the MMAs
 // (one thread), warps 2-5 are the epilogue (TMEM -> registers -> global).  Every mbarrier wait is bounded;
@@ -38,11 +43,17 @@ template <>
 struct Cfg<0> {
     static constexpr int BM = 128;            // rows per block
     static constexpr int BK = 32;             // K elements per stage (64 bytes)
-    static constexpr int NA = 2, NB = 2;      // W_hi, W_lo ; X_hi^T, X_lo^T
+    static constexpr int NA = 2, NB = 2;      // W_hi, W_lo ; X_hi, X_lo
     static constexpr int STAGES = 4;
     static constexpr int NBUF = 2;            // TMEM accumulator buffers (double buffering)
-    static constexpr uint32_t SWZ = 4;        // descriptor layout: 64-byte swizzle
-    static constexpr uint32_t SBO = 8 * 64;   // bytes between 8-row groups
+    static constexpr uint32_t SWZ = 4;        // A (K-major): 64-byte swizzle
+    static constexpr uint32_t SBO = 8 * 64;   // A: bytes between 8-row groups
+    static constexpr uint32_t A_KSTEP = 2;    // A: descriptor advance per 16-wide k slice (32 bytes)
+    // B is N-major: an atom of the 128-byte swizzle is 8 k-rows x 64 bins
+    static constexpr uint32_t B_SWZ = 2;
+    static constexpr uint32_t B_SBO = 1024;   // B: bytes between 8-row groups along K
+    static constexpr uint32_t B_LBO = BK * 128;  // B: bytes between 64-bin blocks along N (one TMA box)
+    static constexpr uint32_t B_KSTEP = 128;  // B: advance per k slice (16 k-rows of 128 bytes)
     static constexpr uint32_t A_BYTES = 128 * BK * 2;
     static constexpr uint32_t B_BYTES = BN * BK * 2;
 };
@@ -53,8 +64,13 @@ struct Cfg<1> {
     static constexpr int NA = 2, NB = 1;      // E rows m0.., E rows m0+128.. ; X
     static constexpr int STAGES = 3;
     static constexpr int NBUF = 1;
-    static constexpr uint32_t SWZ = 2;        // 128-byte swizzle
+    static constexpr uint32_t SWZ = 2;        // 128-byte swizzle, both operands K-major
     static constexpr uint32_t SBO = 8 * 128;
+    static constexpr uint32_t A_KSTEP = 2;
+    static constexpr uint32_t B_SWZ = SWZ;
+    static constexpr uint32_t B_SBO = SBO;
+    static constexpr uint32_t B_LBO = 16;     // unused for swizzled K-major operands
+    static constexpr uint32_t B_KSTEP = 2;
     static constexpr uint32_t A_BYTES = 128 * BK * 2;
     static constexpr uint32_t B_BYTES = BN * BK * 2;
 };
@@ -118,13 +134,16 @@ __device__ __forceinline__ Unit decode(const TcArgs& A, int64_t u) {
     return r;
 }
 
-// Shared-memory descriptor of a K-major operand tile written by TMA with the matching swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t swz, uint32_t sbo) {
+// Shared-memory descriptor of an operand tile written by TMA with the matching swizzle.
+//   K-major:  sbo = bytes between 8-row groups along M/N; lbo unused (16).
+//   N-major (128-byte swizzle): an atom is 8 k-rows of 64 elements along N; lbo = bytes between atoms
+//             along N, sbo = bytes between atoms along K.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t swz, uint32_t sbo, uint32_t lbo = 16) {
     uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1u << 16;               // leading-dimension offset: unused for swizzled K-major
-    d |= (uint64_t)(sbo >> 4) << 32;       // stride between 8-row groups
-    d |= (uint64_t)1u << 46;               // descriptor version
-    d |= (uint64_t)swz << 61;              // swizzle mode
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;  // leading-dimension byte offset
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;  // stride-dimension byte offset
+    d |= (uint64_t)1u << 46;                      // descriptor version
+    d |= (uint64_t)swz << 61;                     // swizzle mode
     return d;
 }
 
@@ -218,12 +237,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     if (MODE == 0) {
                         tc::tma_load_2d(sa, &mapA0, kx, w.m0, &full[stage]);
                         tc::tma_load_2d(sa + C::A_BYTES, &mapA1, kx, w.m0, &full[stage]);
-                        tc::tma_load_2d(sa + 2 * C::A_BYTES, &mapB0, kx, w.n0, &full[stage]);
-                        tc::tma_load_2d(sa + 2 * C::A_BYTES + C::B_BYTES, &mapB1, kx, w.n0, &full[stage]);
+                        // (bin in block, neuron = k, bin block): 4 blocks of 32 x 64
+                        tc::tma_load_3d(sa + 2 * C::A_BYTES, &mapB0, 0, kx, w.n0 / 64, &full[stage]);
+                        tc::tma_load_3d(sa + 2 * C::A_BYTES + C::B_BYTES, &mapB1, 0, kx, w.n0 / 64, &full[stage]);
                     } else {
-                        tc::tma_load_2d(sa, &mapA0, kx, w.m0, &full[stage]);
-                        tc::tma_load_2d(sa + C::A_BYTES, &mapA0, kx, w.m0 + 128, &full[stage]);
-                        tc::tma_load_2d(sa + 2 * C::A_BYTES, &mapB0, kx, w.n0, &full[stage]);
+                        // (bin in block, neuron, bin block = k-step)
+                        tc::tma_load_3d(sa, &mapA0, 0, w.m0, (int32_t)kb, &full[stage]);
+                        tc::tma_load_3d(sa + C::A_BYTES, &mapA0, 0, w.m0 + 128, (int32_t)kb, &full[stage]);
+                        tc::tma_load_3d(sa + 2 * C::A_BYTES, &mapB0, 0, w.n0, (int32_t)kb, &full[stage]);
                     }
                     issued_phase[stage] = (int)phase;
                     if (++stage == C::STAGES) {
@@ -265,18 +286,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     const uint32_t sa = tc::smem_u32(smem + stage * L::STAGE_BYTES);
                     const uint64_t da0 = smem_desc(sa, C::SWZ, C::SBO);
                     const uint64_t da1 = smem_desc(sa + C::A_BYTES, C::SWZ, C::SBO);
-                    const uint64_t db0 = smem_desc(sa + 2 * C::A_BYTES, C::SWZ, C::SBO);
-                    const uint64_t db1 = smem_desc(sa + 2 * C::A_BYTES + C::B_BYTES, C::SWZ, C::SBO);
+                    const uint64_t db0 = smem_desc(sa + 2 * C::A_BYTES, C::B_SWZ, C::B_SBO, C::B_LBO);
+                    const uint64_t db1 = smem_desc(sa + 2 * C::A_BYTES + C::B_BYTES, C::B_SWZ, C::B_SBO, C::B_LBO);
 #pragma unroll
                     for (int k = 0; k < C::BK / 16; ++k) {
                         const uint32_t acc = (kb == w.kb0 && k == 0) ? 0u : 1u;
+                        const uint64_t ka = C::A_KSTEP * k, kb16 = C::B_KSTEP * k;
                         if (MODE == 0) {
-                            tc::mma_f16(d0, da0 + 2 * k, db0 + 2 * k, A.idesc, acc);   // W_hi X_hi
-                            tc::mma_f16(d0, da1 + 2 * k, db0 + 2 * k, A.idesc, 1u);    // W_lo X_hi
-                            tc::mma_f16(d0, da0 + 2 * k, db1 + 2 * k, A.idesc, 1u);    // W_hi X_lo
+                            tc::mma_f16(d0, da0 + ka, db0 + kb16, A.idesc, acc);   // W_hi X_hi
+                            tc::mma_f16(d0, da1 + ka, db0 + kb16, A.idesc, 1u);    // W_lo X_hi
+                            tc::mma_f16(d0, da0 + ka, db1 + kb16, A.idesc, 1u);    // W_hi X_lo
                         } else {
-                            tc::mma_f16(d0, da0 + 2 * k, db0 + 2 * k, A.idesc, acc);   // rows m0..
-                            tc::mma_f16(d1, da1 + 2 * k, db0 + 2 * k, A.idesc, acc);   // rows m0+128..
+                            tc::mma_f16(d0, da0 + ka, db0 + kb16, A.idesc, acc);   // rows m0..
+                            tc::mma_f16(d1, da1 + ka, db0 + kb16, A.idesc, acc);   // rows m0+128..
                         }
                     }
                     tc::mma_commit(&empty[stage]);
@@ -318,7 +340,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 double rsum = 0.0;
                 bool bad = false;
                 float zl = 0.f, pw = 1.f, p1 = 0.f, p2 = 0.f;
-                T16* erow = reinterpret_cast<T16*>(A.E) + (int64_t)i * A.Tpad + w.n0;
+                // E is bin-blocked: bins [64 b, 64 b + 64) of row i at (b n + i) 64
+                T16* erow = reinterpret_cast<T16*>(A.E) + ((int64_t)(w.n0 / 64) * A.n + i) * 64;
 #pragma unroll 1
                 for (int c = 0; c < BN / 32; ++c) {
                     uint32_t r[32];
@@ -360,7 +383,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     }
                     rsum += (double)cnt + (double)s;
                     if (i < A.n) {
-                        uint4* dst = reinterpret_cast<uint4*>(erow + c * 32);
+                        uint4* dst = reinterpret_cast<uint4*>(erow + (int64_t)(c >> 1) * A.n * 64 + (c & 1) * 32);
 #pragma unroll
                         for (int v = 0; v < 4; ++v)
                             dst[v] = make_uint4(pk[4 * v], pk[4 * v + 1], pk[4 * v + 2], pk[4 * v + 3]);
@@ -457,6 +480,22 @@ bool encode_map(CUtensorMap* m, bool bf16, const void* base, uint64_t inner, uin
     return r == CUDA_SUCCESS;
 }
 
+// 3-D map over a bin-blocked array [Tpad / 64][n][64]: dims (64 bins, n neurons, Tpad / 64 blocks),
+// box = 64 x box_rows x box_blocks, 128-byte swizzle.  Neurons beyond n read as zero.
+bool encode_blocked(CUtensorMap* m, bool bf16, const void* base, uint64_t n, uint64_t Tpad, uint32_t box_rows,
+                    uint32_t box_blocks) {
+    auto fn = get_encode();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {64, n, Tpad / 64};
+    const cuuint64_t strides[2] = {128, n * 128};
+    const cuuint32_t box[3] = {64, box_rows, box_blocks};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
+                    const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 int tc_nsplit(const glm_ctx* c) {
@@ -471,22 +510,22 @@ int tc_nsplit(const glm_ctx* c) {
 
 int tc_tile_t() { return BN; }
 
-// Maps: 0 W_hi, 1 W_lo, 2 X_hi^T, 3 X_lo^T (U = W X, 64-byte swizzle), 4 E, 5 X_hi (E X^T, 128-byte swizzle).
+// Maps: 0 W_hi, 1 W_lo (U = W X, K-major, 64-byte swizzle), 2 X_hi, 3 X_lo (U = W X, N-major boxes of 4 x 32 x 64),
+// 4 E, 5 X_hi (E X^T, K-major boxes of 1 x 128 (E) or 1 x 256 (X) x 64).  The last four are 3-D maps over the
+// bin-blocked arrays (bin in block, neuron, bin block), all with the 128-byte swizzle.
 cudaError_t tc_prepare_maps(glm_ctx* c) {
     const Problem& P = c->pb;
     const bool bf = P.prec == GLM_PREC_BF16;
     const int64_t ld = c->buf.ldn;
     const size_t wsz = (size_t)P.n * ld * 2;
-    const size_t xtsz = (size_t)P.Tpad * ld * 2;
     const uint8_t* Wsplit = reinterpret_cast<const uint8_t*>(c->buf.Wsplit);
-    const uint8_t* XT = reinterpret_cast<const uint8_t*>(c->buf.XT);
-    const auto S64 = CU_TENSOR_MAP_SWIZZLE_64B, S128 = CU_TENSOR_MAP_SWIZZLE_128B;
+    const auto S64 = CU_TENSOR_MAP_SWIZZLE_64B;
     bool ok = encode_map(&c->tmap[0], bf, Wsplit, P.n, P.n, ld, 32, 128, S64) &&
               encode_map(&c->tmap[1], bf, Wsplit + wsz, P.n, P.n, ld, 32, 128, S64) &&
-              encode_map(&c->tmap[2], bf, XT, P.n, P.T, ld, 32, BN, S64) &&
-              encode_map(&c->tmap[3], bf, XT + xtsz, P.n, P.T, ld, 32, BN, S64) &&
-              encode_map(&c->tmap[4], bf, c->buf.E, P.T, P.n, P.Tpad, 64, 128, S128) &&
-              encode_map(&c->tmap[5], bf, c->buf.X, P.T, P.n, P.Tpad, 64, BN, S128);
+              encode_blocked(&c->tmap[2], bf, c->buf.X, P.n, P.Tpad, Cfg<0>::BK, BN / 64) &&
+              encode_blocked(&c->tmap[3], bf, c->buf.Xlo, P.n, P.Tpad, Cfg<0>::BK, BN / 64) &&
+              encode_blocked(&c->tmap[4], bf, c->buf.E, P.n, P.Tpad, 128, 1) &&
+              encode_blocked(&c->tmap[5], bf, c->buf.X, P.n, P.Tpad, BN, 1);
     return ok ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -511,7 +550,7 @@ static TcArgs base_args(glm_ctx* c) {
     A.dt = P.dt;
     A.flags = c->buf.flags;
     A.limit_ns = 4000000000ull;  // 4 s per wait
-    A.idesc = tc::idesc_f16(P.prec == GLM_PREC_BF16 ? 1u : 0u, 128, BN);
+    A.idesc = tc::idesc_f16(P.prec == GLM_PREC_BF16 ? 1u : 0u, 128, BN);  // both operands K-major
     A.b = nullptr;
     A.eb = c->buf.eb;
     A.a = (float)P.a;
@@ -549,6 +588,7 @@ cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, boo
     A.E = c->buf.E;
     A.part_e = c->buf.part_e;
     A.part_tau = c->buf.part_tau;
+    A.idesc |= 1u << 16;  // B (X) is N-major
     if (tau) {
         if (P.prec == GLM_PREC_BF16)
             return run<0, __nv_bfloat16, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
