@@ -54,6 +54,28 @@ def dist_info():
     return ws, rank, local
 
 
+def rank_seed(base_seed: int, rank: int) -> int:
+    """Seed of rank `rank`'s recording: every GPU fits its own independent recording (weak scaling)."""
+    return base_seed + rank
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest per-rank value over the process group (the job takes as long as its slowest rank);
+    the value itself on a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(n: int, n_bins: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job neuron*bins/s: every rank processed steps x n x n_bins units in `seconds` (the max)."""
+    return n * n_bins * steps * world / seconds
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -181,7 +203,7 @@ def main():
     prec = args.prec or "bf16"
     cfg = dict(synth.WORKLOADS[args.workload])
     extra = {"n_bins": args.n_bins} if args.n_bins else {}
-    w = synth.make_workload(args.workload, seed=cfg["seed"] + rank, **extra)  # independent recording per rank
+    w = synth.make_workload(args.workload, seed=rank_seed(cfg["seed"], rank), **extra)  # independent recording per rank
     n, T = w["n"], w["n_bins"]
     stream = torch.cuda.current_stream(device)
     ctx = glm.GLM(device, stream=stream)
@@ -217,13 +239,10 @@ def main():
     prof = ctx.profile_read()
     ctx.profile(False)
     clk = clocks.stop()
+    ms = max_over_ranks(ms, device)
     if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    units = n * T * args.steps * ws
-    value = units / (ms / 1000.0)
+    value = job_throughput(n, T, args.steps, ws, ms / 1000.0)
 
     # ---- end to end through the public API from host buffers ----
     k2 = args.e2e_steps or max(1, min(args.steps, 5))
@@ -242,10 +261,7 @@ def main():
         G_h.copy_(r["G"], non_blocking=True)
         torch.cuda.synchronize(device)
     e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, device)
     h2d = w["offs"].nbytes + w["bins"].nbytes + W_h.numel() * 4 + b_h.numel() * 4
     d2h = G_h.numel() * 8 + 8
 
@@ -260,7 +276,9 @@ def main():
     name, (cnt, tot_ms) = top
     per_launch_s = tot_ms / cnt / 1000.0
     if name in ("u_epilogue", "grad"):
-        flops = 2.0 * n * n * T * (2 if (name == "u_epilogue" and prec != "f32") else 1)
+        # 2 N flop per neuron-bin per product; the 16-bit U product executes 3 of them (W_hi X_hi, W_lo X_hi,
+        # W_hi X_lo), the precision split of the operands
+        flops = 2.0 * n * n * T * (3 if (name == "u_epilogue" and prec != "f32") else 1)
         if prec == "f32":
             # FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x max SM clock
             sm_mhz = peaks.get("sm_max_mhz", 2070.0)
@@ -290,7 +308,7 @@ def main():
         "config": {"workload": args.workload, "n": n, "n_bins": T, "precision": prec,
                    "l2": "inputs larger than L2 (filtered trains %.1f GB)" % (n * T * (4 if prec == "f32" else 4) / 1e9),
                    "parallelism": f"replicas x{ws}: one independent recording per GPU"},
-        "e2e": {"value": n * T * k2 * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        "e2e": {"value": job_throughput(n, T, k2, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "steps": k2},
         "gpu_launches": int(launches),
         "kernel_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
