@@ -29,10 +29,6 @@ void fill_scan_consts(double a, ScanConsts* sc) {
     for (int d = 0; d < 5; ++d) split(std::pow(a, 8.0 * (1 << d)), &sc->ps_hi[d], &sc->ps_lo[d]);
     for (int l = 0; l < 32; ++l) split(std::pow(a, 8.0 * l), &sc->pl_hi[l], &sc->pl_lo[l]);
     // d/da of the same powers: k a^(k-1)
-    auto dpow = [a](double k) { return k == 0.0 ? 0.0 : k * std::pow(a, k - 1.0); };
-    for (int m = 0; m <= 8; ++m) split(dpow(m), &sc->pmd_hi[m], &sc->pmd_lo[m]);
-    for (int d = 0; d < 5; ++d) split(dpow(8.0 * (1 << d)), &sc->psd_hi[d], &sc->psd_lo[d]);
-    for (int l = 0; l < 32; ++l) split(dpow(8.0 * l), &sc->pld_hi[l], &sc->pld_lo[l]);
 }
 
 // Block per row: segment-first indices and, in seg_carry, the contribution of each segment's own
@@ -103,100 +99,6 @@ __global__ void seg_carry_kernel(int32_t n, int64_t nseg, double a_seg, double* 
         p[s] = cin;
         cin = fma(a_seg, cin, l);
     }
-}
-
-// ---- carries of Y = dX/da (needed only for the derivative in tau) ----
-// Block per row: each segment's own contribution to (X, Y) at the next segment start E:
-//   lx = sum_{t in seg} a^(E-1-t),   ly = sum_{t in seg} (E-1-t) a^(E-2-t)
-__global__ void seg_local_xy_kernel(int32_t n, int64_t nseg, const int64_t* __restrict__ offs,
-                                    const int32_t* __restrict__ bins, const double* __restrict__ pow_seg,
-                                    const double* __restrict__ dpow_seg, double* __restrict__ lx,
-                                    double* __restrict__ ly) {
-    const int32_t j = blockIdx.x;
-    if (j >= n) return;
-    const int64_t o0 = offs[j], q = offs[j + 1] - o0;
-    const int32_t* b = bins + o0;
-    double* px = lx + (int64_t)j * nseg;
-    double* py = ly + (int64_t)j * nseg;
-    for (int64_t s = threadIdx.x; s < nseg; s += blockDim.x) px[s] = py[s] = 0.0;
-    __syncthreads();
-    for (int64_t k = threadIdx.x; k < q; k += blockDim.x) {
-        const int64_t s = b[k] / SEG;
-        const int64_t ps = (k > 0) ? (int64_t)(b[k - 1] / SEG) : -1;
-        if (s != ps) {
-            double ax = 0.0, ay = 0.0;
-            const int64_t end = (s + 1) * SEG;
-            for (int64_t kk = k; kk < q && b[kk] < end; ++kk) {
-                ax += pow_seg[end - 1 - b[kk]];
-                ay += dpow_seg[end - 1 - b[kk]];
-            }
-            px[s] = ax;
-            py[s] = ay;
-        }
-    }
-}
-
-// Warp per row, in place: py[s] <- Y_j[256 s] from the local pairs (px, py).  Over one segment
-// (X, Y) -> (A X + lx, A Y + A' X + ly), A = a^256, A' = 256 a^255.  Lanes own contiguous parts; a shuffle
-// scan over lanes composes the pair maps (multipliers (M, M') compose as (M1 M2, M1 M2' + M1' M2)).
-__global__ void seg_carry_xy_kernel(int32_t n, int64_t nseg, double A, double Ad, double* __restrict__ px,
-                                    double* __restrict__ py) {
-    const int32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (j >= n) return;
-    double* p = px + (int64_t)j * nseg;
-    double* q = py + (int64_t)j * nseg;
-    const int64_t len = (nseg + 31) / 32;
-    const int64_t s0 = min((int64_t)lane * len, nseg), s1 = min(s0 + len, nseg);
-    double cx = 0.0, cy = 0.0;
-    for (int64_t s = s0; s < s1; ++s) {
-        cy = fma(A, cy, fma(Ad, cx, q[s]));
-        cx = fma(A, cx, p[s]);
-    }
-    // (M, M') = (A, A')^(s1 - s0)
-    double M = 1.0, Md = 0.0, B = A, Bd = Ad;
-    for (int64_t e = s1 - s0; e > 0; e >>= 1) {
-        if (e & 1) {
-            const double nM = M * B, nMd = M * Bd + Md * B;
-            M = nM;
-            Md = nMd;
-        }
-        const double nB = B * B, nBd = 2.0 * B * Bd;
-        B = nB;
-        Bd = nBd;
-    }
-    double vx = cx, vy = cy;
-    for (int d = 1; d < 32; d <<= 1) {
-        const double ox = __shfl_up_sync(0xffffffffu, vx, d), oy = __shfl_up_sync(0xffffffffu, vy, d);
-        const double oM = __shfl_up_sync(0xffffffffu, M, d), oMd = __shfl_up_sync(0xffffffffu, Md, d);
-        if (lane >= d) {
-            vy = fma(M, oy, fma(Md, ox, vy));
-            vx = fma(M, ox, vx);
-            const double nM = M * oM, nMd = M * oMd + Md * oM;
-            M = nM;
-            Md = nMd;
-        }
-    }
-    double ix = __shfl_up_sync(0xffffffffu, vx, 1), iy = __shfl_up_sync(0xffffffffu, vy, 1);
-    if (lane == 0) ix = iy = 0.0;
-    for (int64_t s = s0; s < s1; ++s) {
-        const double lxs = p[s], lys = q[s];
-        p[s] = ix;
-        q[s] = iy;
-        const double ny = fma(A, iy, fma(Ad, ix, lys));
-        ix = fma(A, ix, lxs);
-        iy = ny;
-    }
-}
-
-cudaError_t launch_carry_y(glm_ctx* c) {
-    const Problem& P = c->pb;
-    seg_local_xy_kernel<<<P.n, 256, 0, c->stream>>>(P.n, P.nseg, c->buf.offs, c->buf.bins, c->buf.pow_seg,
-                                                    c->buf.dpow_seg, c->buf.seg_tmp, c->buf.seg_carry_y);
-    const double A = std::exp(-(double)SEG * P.dt / P.tau);
-    const double Ad = (double)SEG * std::exp(-(double)(SEG - 1) * P.dt / P.tau);
-    seg_carry_xy_kernel<<<(P.n + 3) / 4, 128, 0, c->stream>>>(P.n, P.nseg, A, Ad, c->buf.seg_tmp, c->buf.seg_carry_y);
-    return cudaGetLastError();
 }
 
 constexpr int CHUNK_SEGS = 16;  // 4096 bins per warp unit

@@ -49,7 +49,7 @@ void free_all(glm_ctx* c) {
     c->ws_used = 0;
     c->buf = Buffers();
     c->has_problem = false;
-    c->dtau_ready = false;
+    c->c_ready = false;
 }
 
 // Device allocation charged against the workspace cap.
@@ -163,42 +163,53 @@ int validate_spikes(glm_ctx* c, int32_t n, int64_t T, const int64_t* offs, const
     return GLM_OK;
 }
 
+int ensure_spike_term(glm_ctx* c);
+
 int do_prepare(glm_ctx* c) {
     Problem& P = c->pb;
     P.a = std::exp(-P.dt / P.tau);
     fill_scan_consts(P.a, &c->sc);
     std::vector<double> pw(SEG + 1);
     for (int k = 0; k <= SEG; ++k) pw[k] = std::exp(-(double)k * P.dt / P.tau);
-    std::vector<double> dpw(SEG + 1);
-    for (int k = 0; k <= SEG; ++k) dpw[k] = k == 0 ? 0.0 : (double)k * std::exp(-(double)(k - 1) * P.dt / P.tau);
     GLM_CK(cudaMemcpyAsync(c->buf.pow_seg, pw.data(), sizeof(double) * (SEG + 1), cudaMemcpyHostToDevice,
                            c->stream));
-    GLM_CK(cudaMemcpyAsync(c->buf.dpow_seg, dpw.data(), sizeof(double) * (SEG + 1), cudaMemcpyHostToDevice,
-                           c->stream));
-    c->dtau_ready = false;
+    c->c_ready = false;
     GLM_RUN("carry", 2, launch_carry(c));
     GLM_RUN("filter_scan", 1, launch_filter_cache(c));
-    GLM_RUN("spike_term", 2, launch_spike_term(c, false, c->buf.C));
+    // The spike term C (the W-independent part of dL/dW, Eq. 12): a gather of X at the spike bins for the
+    // plain FP32 form, S (X_hi + X_lo)^T on the tensor cores for the 16-bit forms.  The plain form also
+    // takes the spike part of L from it; the 16-bit forms take that from U at the spike bins.
+    int rc = ensure_spike_term(c);
+    if (rc) return rc;
     // pw is a pageable host buffer: the copy above has been staged before cudaMemcpyAsync returned
     return GLM_OK;
 }
 
-// W-independent parts of dL/dtau: the carries of Y = dX/da and D_ij = sum_{t in sp(i)} Y_j[t].
+// The spike term C of the current problem and tau (computed on the first request).
+int ensure_spike_term(glm_ctx* c) {
+    if (c->c_ready) return GLM_OK;
+    Buffers& B = c->buf;
+    const size_t nn = (size_t)c->pb.n * c->pb.n;
+    if (c->pb.prec != GLM_PREC_F32) {
+        GLM_RUN("spike_term", 5, launch_tc_spike_term(c));
+    } else {
+        int rc;
+        if (!B.C_part && (rc = ws_alloc_t(c, &B.C_part, nn * spike_term_parts(c)))) return rc;
+        GLM_RUN("spike_term", 2, launch_spike_term(c, B.C));
+    }
+    c->c_ready = true;
+    return GLM_OK;
+}
+
+// Buffers of dL/dtau (allocated by the first request for it).
 int prepare_dtau(glm_ctx* c) {
-    if (c->dtau_ready) return GLM_OK;
     Buffers& B = c->buf;
     const Problem& P = c->pb;
     int rc;
-    if (!B.D) {
-        if ((rc = ws_alloc_t(c, &B.seg_carry_y, (size_t)P.n * P.nseg)) ||
-            (rc = ws_alloc_t(c, &B.seg_tmp, (size_t)P.n * P.nseg)) || (rc = ws_alloc_t(c, &B.D, (size_t)P.n * P.n)) ||
-            (rc = ws_alloc_t(c, &B.part_tau, 3 * (size_t)P.n * (P.Tpad / tc_tile_t()))) ||
-            (rc = ws_alloc_t(c, &B.tau_rows, P.n)))
-            return rc;
-    }
-    GLM_RUN("carry_y", 2, launch_carry_y(c));
-    GLM_RUN("spike_term_y", 2, launch_spike_term(c, true, B.D));
-    c->dtau_ready = true;
+    if (!B.part_tau &&
+        ((rc = ws_alloc_t(c, &B.part_tau, 5 * (size_t)P.n * (P.Tpad / tc_tile_t()))) ||
+         (rc = ws_alloc_t(c, &B.tau_rows, P.n))))
+        return rc;
     return GLM_OK;
 }
 
@@ -379,14 +390,14 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
     if ((rc = ws_alloc_t(c, &B.offs, n + 1)) || (rc = ws_alloc_t(c, &B.bins, P.q > 0 ? P.q : 1)) ||
         (rc = ws_alloc_t(c, &B.seg_carry, (size_t)n * P.nseg)) ||
         (rc = ws_alloc_t(c, &B.seg_first, (size_t)n * P.nseg)) || (rc = ws_alloc_t(c, &B.pow_seg, SEG + 1)) ||
-        (rc = ws_alloc_t(c, &B.dpow_seg, SEG + 1)) ||
         (rc = ws_alloc_t(c, &B.qd, n)) || (rc = ws_alloc_t(c, &B.C, nn)) ||
-        (rc = ws_alloc_t(c, &B.C_part, nn * spike_term_parts(c))) || (rc = ws_alloc(c, &B.X, (size_t)n * P.Tpad * esz)) ||
+        (rc = ws_alloc(c, &B.X, (size_t)n * P.Tpad * esz)) ||
         (rc = ws_alloc(c, &B.E, (size_t)n * P.Tpad * esz)) ||
         (rc = ws_alloc_t(c, &B.part_e, (size_t)n * (P.Tpad / (tensor ? tc_tile_t() : simt_tile_t())))) ||
         (rc = ws_alloc_t(c, &B.part_g, nn * (tensor ? tc_nsplit(c) : grad_nsplit(c)))) ||
         (rc = ws_alloc_t(c, &B.flags, 4)) || (rc = ws_alloc_t(c, &B.Lrows, n)) || (rc = ws_alloc_t(c, &B.scal, 8)) || (rc = ws_alloc_t(c, &B.eb, n)) ||
         (tensor && (rc = ws_alloc(c, &B.Xlo, (size_t)P.n * P.Tpad * 2))) ||
+        (tensor && (rc = ws_alloc_t(c, &B.part_s, (size_t)n * (P.Tpad / tc_tile_t())))) ||
         (tensor && (rc = ws_alloc(c, &B.Wsplit, 2 * (size_t)n * B.ldn * 2)))) {
         free_all(c);
         return rc;
@@ -444,7 +455,11 @@ int glm_spike_term(glm_ctx* c, double* C_dev, double* q_dev) {
     if (!c->has_problem) return fail(c, GLM_ERR_NO_PROBLEM, "no problem set");
     DeviceGuard g(c->device);
     const size_t nn = (size_t)c->pb.n * c->pb.n;
-    if (C_dev) GLM_CK(cudaMemcpyAsync(C_dev, c->buf.C, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if (C_dev) {
+        const int rc = ensure_spike_term(c);
+        if (rc) return rc;
+        GLM_CK(cudaMemcpyAsync(C_dev, c->buf.C, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    }
     if (q_dev)
         GLM_CK(cudaMemcpyAsync(q_dev, c->buf.qd, c->pb.n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     return GLM_OK;
@@ -467,7 +482,7 @@ int glm_loglik_grad(glm_ctx* c, const float* W, const float* b, double* L_rows, 
     int rc = glm::eval_enqueue(c, W, b, Lr, G, gb, G != nullptr, false, gtau_host != nullptr);
     if (rc) return rc;
     if (gtau_host) {
-        GLM_RUN("tau_rows", 1, launch_tau_rows(c, W, c->buf.tau_rows));
+        GLM_RUN("tau_rows", 1, launch_tau_rows(c, c->buf.tau_rows));
         GLM_RUN("total", 1, launch_total(c, c->buf.tau_rows, c->buf.scal + 1));
         double t = 0.0;
         GLM_CK(cudaMemcpyAsync(&t, c->buf.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));

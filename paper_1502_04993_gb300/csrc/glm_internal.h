@@ -26,9 +26,6 @@ struct ScanConsts {
     float ps_hi[5], ps_lo[5];    // a^(8*2^d),    d = 0..4   (warp scan strides)
     float pl_hi[32], pl_lo[32];  // a^(8*l),      l = 0..31  (lane offsets)
     // derivatives in a, for the joint scan of X and Y = dX/da (the tau derivative)
-    float pmd_hi[9], pmd_lo[9];  // m a^(m-1)
-    float psd_hi[5], psd_lo[5];  // 8*2^d a^(8*2^d - 1)
-    float pld_hi[32], pld_lo[32];  // 8 l a^(8 l - 1)
 };
 
 struct Problem {
@@ -50,12 +47,13 @@ struct Buffers {
     double* pow_seg = nullptr;    // [SEG + 1]   a^k, k = 0..SEG
     double* qd = nullptr;         // [n]         spike counts
     double* C = nullptr;          // [n][n]      spike term
-    double* C_part = nullptr;     // [parts][n][n]
+    double* C_part = nullptr;     // [parts][n][n] (plain FP32 form)
     void* X = nullptr;            // F32: float [n][Tpad]; 16-bit: [n][Tpad]
     void* Xlo = nullptr;          // 16-bit only: X_lo = X - X_hi, [n][Tpad]
-    int64_t ldn = 0;              // leading dim of X^T and of the W parts (n rounded up to 64)
-    void* E = nullptr;            // F32: float [n][Tpad]; 16-bit: [n][Tpad]   dt * exp(U)
+    int64_t ldn = 0;              // leading dim of the W parts (n rounded up to 64)
+    void* E = nullptr;            // F32: float [n][Tpad] dt exp(U); 16-bit: the same, bin-blocked
     double* part_e = nullptr;     // [n][ntile_t]  per-(row, bin tile) sums of exp(U)
+    double* part_s = nullptr;     // 16-bit: [n][ntile_t] per-(row, bin tile) sums of U - b over the spike bins
     float* part_g = nullptr;      // [nsplit][n][n] FP32 partial sums of E X^T
     void* Wsplit = nullptr;       // 16-bit: hi and lo parts of W, [2][n][ldn]
     int* flags = nullptr;         // [4] device error flags
@@ -64,11 +62,7 @@ struct Buffers {
     double* eb = nullptr;         // [n] exp(b_i) in FP64 (plain FP32 form)
     void* fit_mem = nullptr;      // optimiser state of glm_fit (allocated by its first call)
     // derivative in tau (allocated by the first request for it)
-    double* dpow_seg = nullptr;   // [SEG + 1]  k a^(k-1)
-    double* seg_carry_y = nullptr;  // [n][nseg] Y = dX/da at segment starts
-    double* seg_tmp = nullptr;    // [n][nseg]
-    double* D = nullptr;          // [n][n]  sum_{t in sp(i)} Y_j[t]
-    double* part_tau = nullptr;   // [3][n][ntile]
+    double* part_tau = nullptr;   // [5][n][ntile]
     double* tau_rows = nullptr;   // [n]
     int fit_m = 0;
 };
@@ -85,9 +79,9 @@ struct glm_ctx {
     glm::Problem pb;
     glm::Buffers buf;
     glm::ScanConsts sc;
-    CUtensorMap tmap[6];  // tensor-core path: W_hi, W_lo, X_hi^T, X_lo^T, E, X_hi
+    CUtensorMap tmap[7];  // tensor-core path: W_hi, W_lo, X_hi, X_lo (N-major), E, X_hi, X_lo (K-major)
     bool has_problem = false;
-    bool dtau_ready = false;  // D and the Y carries are current
+    bool c_ready = false;  // C holds the spike term of the current problem and tau
     std::string last_error;
     // tracing: event pairs per launched kernel group while profiling is on
     bool prof_on = false;
@@ -115,9 +109,10 @@ namespace glm {
 cudaError_t launch_carry(glm_ctx* c);
 cudaError_t launch_filter_cache(glm_ctx* c);
 cudaError_t launch_filter_range(glm_ctx* c, int64_t t0, int64_t t_len, void* out, int64_t ldx, glm_dtype_t dtype);
-cudaError_t launch_spike_term(glm_ctx* c, bool dy, double* out);
-cudaError_t launch_carry_y(glm_ctx* c);
-cudaError_t launch_tau_rows(glm_ctx* c, const float* W, double* rows);
+cudaError_t launch_spike_term(glm_ctx* c, double* out);
+cudaError_t launch_tau_rows(glm_ctx* c, double* rows);
+cudaError_t launch_sum_splits(glm_ctx* c, int nsplit, double* C, bool accumulate);
+cudaError_t launch_tc_spike_term(glm_ctx* c);
 cudaError_t launch_simt_u_epilogue(glm_ctx* c, const float* W, const float* b);
 cudaError_t launch_simt_grad(glm_ctx* c);
 cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_rows, double* G, double* gb,

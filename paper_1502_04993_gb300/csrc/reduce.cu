@@ -1,5 +1,6 @@
 // Step a7: FP64 reductions in a fixed order (bitwise reproducible).
-//   L_i   = q_i b_i + sum_j W_ij C_ij - dt sum_t exp(U_i[t])     (Eq. 7 with the spike term from C)
+//   L_i   = sum_{t in sp(i)} U_i[t] - dt sum_t exp(U_i[t])        (Eq. 7), with the spike part
+//           q_i b_i + sum_j W_ij C_ij (plain FP32 form) or q_i b_i + sum_tiles (sum of U - b at spike bins)
 //   dL/db_i = q_i - dt sum_t exp(U_i[t])                         (Eq. 12, j = 0)
 //   dL/dW_ij = C_ij - sum_s P_s[i][j],  P_s = sum_{t in split s} dt exp(U_i[t]) X_j[t]   (Eq. 12)
 //   L = sum_i L_i                                                (Eq. 1)
@@ -21,7 +22,8 @@ struct ReduceArgs {
     double dt;
     const float* W;
     const float* b;
-    const double* C;
+    const double* C;       // spike term (the plain form's spike part of L; dL/dW in both forms)
+    const double* part_s;  // tensor-core forms: [n][ntile] sums of U - b at the spike bins
     const double* qd;
     const double* part_e;  // [n][ntile]
     double* L_rows;
@@ -34,7 +36,12 @@ __global__ void reduce_rows_kernel(const __grid_constant__ ReduceArgs A) {
     const int lane = threadIdx.x & 31;
     if (i >= A.n) return;
     double spk = 0.0;
-    for (int32_t j = lane; j < A.n; j += 32) spk += (double)A.W[(int64_t)i * A.n + j] * A.C[(int64_t)i * A.n + j];
+    if (A.part_s) {
+        const double* ps = A.part_s + (int64_t)i * A.ntile;
+        for (int64_t t = lane; t < A.ntile; t += 32) spk += ps[t];
+    } else {
+        for (int32_t j = lane; j < A.n; j += 32) spk += (double)A.W[(int64_t)i * A.n + j] * A.C[(int64_t)i * A.n + j];
+    }
     double integ = 0.0;
     const double* pe = A.part_e + (int64_t)i * A.ntile;
     for (int64_t t = lane; t < A.ntile; t += 32) integ += pe[t];
@@ -56,6 +63,22 @@ __global__ void reduce_grad_kernel(int64_t nn, int nsplit, const double* __restr
     G[e] = C[e] - s;
 }
 
+// C[e] (+)= sum over splits of part_g, in split order.
+__global__ void sum_splits_kernel(int64_t nn, int nsplit, const float* __restrict__ part_g, double* __restrict__ C,
+                                  bool accumulate) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nn) return;
+    double s = 0.0;
+    for (int p = 0; p < nsplit; ++p) s += (double)part_g[p * nn + e];
+    C[e] = accumulate ? C[e] + s : s;
+}
+
+cudaError_t launch_sum_splits(glm_ctx* c, int nsplit, double* C, bool accumulate) {
+    const int64_t nn = (int64_t)c->pb.n * c->pb.n;
+    sum_splits_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(nn, nsplit, c->buf.part_g, C, accumulate);
+    return cudaGetLastError();
+}
+
 __global__ void total_kernel(int32_t n, const double* __restrict__ L_rows, double* __restrict__ out) {
     __shared__ double sh[32];
     double s = 0.0;
@@ -71,13 +94,13 @@ __global__ void total_kernel(int32_t n, const double* __restrict__ L_rows, doubl
 }
 
 // Row i's share of dL/dtau, up to the factor da/dtau = a dt / tau^2 (applied on the host):
-//   r_i = sum_j W_ij D_ij - dt e^{b_i} sum_t e^{v_i[t]} Z_i[t],
-// D_ij = sum_{t in sp(i)} Y_j[t] (the spike part), Z_i = W_i Y_i on the grid.  The epilogue left per tile k:
-// P1 = sum e^v a^(t-t0), P2 = sum e^v Z_loc, Zend = Z_loc at the next tile; with Z_start(0) = 0 and
-// Z_start(k+1) = A Z_start(k) + Zend(k) (A = a^256) the integral part is sum_k Z_start(k) P1(k) + P2(k).
+//   r_i = sum_t R_i[t] Z_i[t] = sum_{t in sp(i)} Z_i[t] - dt e^{b_i} sum_t e^{v_i[t]} Z_i[t],
+// with Z_i = W_i Y, Y = dX/da on the grid, i.e. Z_i[t] = a Z_i[t-1] + v_i[t-1] (v = U - b).  The epilogue
+// left per tile k: P1 = sum e^v a^(t-t0), P2 = sum e^v Z_loc, Zend = Z_loc at the next tile, P3 = sum over
+// the spike bins of a^(t-t0), P4 = sum over the spike bins of Z_loc; with Z_start(0) = 0 and
+// Z_start(k+1) = A Z_start(k) + Zend(k) (A = a^256) a weight family contributes sum_k Z_start(k) P(k) + P'(k).
 // Warp per row: lanes own contiguous tile ranges, a shuffle scan supplies each range's Z_start.
-__global__ void tau_rows_kernel(int32_t n, int64_t ntile, double dt, double A256, const float* __restrict__ W,
-                                const double* __restrict__ D, const double* __restrict__ eb,
+__global__ void tau_rows_kernel(int32_t n, int64_t ntile, double dt, double A256, const double* __restrict__ eb,
                                 const double* __restrict__ part_tau, double* __restrict__ rows) {
     const int32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -86,12 +109,17 @@ __global__ void tau_rows_kernel(int32_t n, int64_t ntile, double dt, double A256
     const double* p1 = part_tau + (int64_t)i * ntile;
     const double* p2 = p1 + plane;
     const double* ze = p1 + 2 * plane;
+    const double* p3 = p1 + 3 * plane;
+    const double* p4 = p1 + 4 * plane;
     const int64_t len = (ntile + 31) / 32;
     const int64_t k0 = min((int64_t)lane * len, ntile), k1 = min(k0 + len, ntile);
-    double z = 0.0, w = 1.0, Q = 0.0, S = 0.0;
+    // with z = Z_start relative to the range start (0) and w = A^(k - k0):
+    double z = 0.0, w = 1.0, Qe = 0.0, Se = 0.0, Qs = 0.0, Ss = 0.0;
     for (int64_t k = k0; k < k1; ++k) {
-        Q = fma(w, p1[k], Q);
-        S += fma(z, p1[k], p2[k]);
+        Qe = fma(w, p1[k], Qe);
+        Se += fma(z, p1[k], p2[k]);
+        Qs = fma(w, p3[k], Qs);
+        Ss += fma(z, p3[k], p4[k]);
         z = fma(A256, z, ze[k]);
         w *= A256;
     }
@@ -105,19 +133,18 @@ __global__ void tau_rows_kernel(int32_t n, int64_t ntile, double dt, double A256
     }
     double zin = __shfl_up_sync(0xffffffffu, v, 1);
     if (lane == 0) zin = 0.0;
-    double integ = fma(zin, Q, S);
-    double spk = 0.0;
-    for (int32_t j = lane; j < n; j += 32) spk += (double)W[(int64_t)i * n + j] * D[(int64_t)i * n + j];
+    double integ = fma(zin, Qe, Se);
+    double spk = fma(zin, Qs, Ss);
     integ = warp_sum(integ);
     spk = warp_sum(spk);
     if (lane == 0) rows[i] = spk - dt * eb[i] * integ;
 }
 
-cudaError_t launch_tau_rows(glm_ctx* c, const float* W, double* rows) {
+cudaError_t launch_tau_rows(glm_ctx* c, double* rows) {
     const Problem& P = c->pb;
     const double A256 = std::exp(-(double)SEG * P.dt / P.tau);
-    tau_rows_kernel<<<(P.n + 7) / 8, 256, 0, c->stream>>>(P.n, P.Tpad / tc_tile_t(), P.dt, A256, W, c->buf.D,
-                                                          c->buf.eb, c->buf.part_tau, rows);
+    tau_rows_kernel<<<(P.n + 7) / 8, 256, 0, c->stream>>>(P.n, P.Tpad / tc_tile_t(), P.dt, A256, c->buf.eb,
+                                                          c->buf.part_tau, rows);
     return cudaGetLastError();
 }
 
@@ -130,7 +157,9 @@ cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_
     A.dt = P.dt;
     A.W = W;
     A.b = b;
+    const bool tensor = P.prec != GLM_PREC_F32;
     A.C = c->buf.C;
+    A.part_s = tensor ? c->buf.part_s : nullptr;  // tensor-core forms: spike part of L from U itself
     A.qd = c->buf.qd;
     A.part_e = c->buf.part_e;
     A.L_rows = L_rows;
@@ -138,8 +167,7 @@ cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_
     reduce_rows_kernel<<<(P.n + 7) / 8, 256, 0, c->stream>>>(A);
     if (want_grad && G) {
         const int64_t nn = (int64_t)P.n * P.n;
-        reduce_grad_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(nn, nsplit, c->buf.C,
-                                                                              c->buf.part_g, G);
+        reduce_grad_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(nn, nsplit, A.C, c->buf.part_g, G);
     }
     return cudaGetLastError();
 }

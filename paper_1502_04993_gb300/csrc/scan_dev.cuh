@@ -71,44 +71,4 @@ __device__ __forceinline__ float seg_scan(const ScanConsts& K, float x_seg, uint
     return __shfl_sync(FULL, xend, 31);
 }
 
-// Joint scan of X and Y = dX/da over one segment, for the derivative in tau.  The pair obeys
-//   X[t+1] = a X[t] + S[t],   Y[t+1] = a Y[t] + X[t],
-// so a block of m bins maps (X, Y) to (a^m X + bx, a^m Y + m a^(m-1) X + by).  (xs, ys) = (X, Y)[t0];
-// out_y[m] = Y[t0 + 8 lane + m]; returns (X, Y)[t0 + 256] through *xe, *ye (all lanes).
-__device__ __forceinline__ void seg_scan_xy(const ScanConsts& K, float xs, float ys, uint32_t bits8, int lane,
-                                            float pl_hi, float pl_lo, float pld_hi, float pld_lo, float out_y[8],
-                                            float* xe, float* ye) {
-    float zy[8];
-    float ax = 0.f, ay = 0.f;
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-        zy[m] = ay;
-        ay = mul2(K.a_hi, K.a_lo, ay, ax);
-        ax = mul2(K.a_hi, K.a_lo, ax, (float)((bits8 >> m) & 1u));
-    }
-    // inclusive Kogge-Stone scan of (vx, vy) with block maps of 8 * 2^d bins
-    float vx = ax, vy = ay;
-#pragma unroll
-    for (int d = 0; d < 5; ++d) {
-        const float ox = __shfl_up_sync(FULL, vx, 1 << d);
-        const float oy = __shfl_up_sync(FULL, vy, 1 << d);
-        if (lane >= (1 << d)) {
-            vy = mul2(K.ps_hi[d], K.ps_lo[d], oy, mul2(K.psd_hi[d], K.psd_lo[d], ox, vy));
-            vx = mul2(K.ps_hi[d], K.ps_lo[d], ox, vx);
-        }
-    }
-    float ex = __shfl_up_sync(FULL, vx, 1), ey = __shfl_up_sync(FULL, vy, 1);
-    if (lane == 0) ex = ey = 0.f;
-    // lane start: X_l = a^(8l) xs + ex,  Y_l = a^(8l) ys + 8l a^(8l-1) xs + ey
-    const float xl = mul2(pl_hi, pl_lo, xs, ex);
-    const float yl = mul2(pl_hi, pl_lo, ys, mul2(pld_hi, pld_lo, xs, ey));
-#pragma unroll
-    for (int m = 0; m < 8; ++m)
-        out_y[m] = mul2(K.pm_hi[m], K.pm_lo[m], yl, mul2(K.pmd_hi[m], K.pmd_lo[m], xl, zy[m]));
-    const float xend = mul2(K.pm_hi[8], K.pm_lo[8], xl, ax);
-    const float yend = mul2(K.pm_hi[8], K.pm_lo[8], yl, mul2(K.pmd_hi[8], K.pmd_lo[8], xl, ay));
-    *xe = __shfl_sync(FULL, xend, 31);
-    *ye = __shfl_sync(FULL, yend, 31);
-}
-
 }  // namespace glm

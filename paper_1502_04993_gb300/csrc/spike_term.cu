@@ -82,14 +82,10 @@ struct SpikeTermArgs {
     const int64_t* offs;
     const int32_t* bins;
     const double* seg_carry;
-    const double* seg_carry_y;  // Y = dX/da at segment starts (DY only)
     const int32_t* seg_first;
     double* C_part;  // [parts][n][n]
 };
 
-// DY = false: C_ij = sum_{t in sp(i)} X_j[t].  DY = true: D_ij = sum_{t in sp(i)} Y_j[t] with Y = dX/da, the
-// spike part of the derivative in tau (same gather, the joint (X, Y) scan in phase A).
-template <bool DY>
 __global__ void __launch_bounds__(ST_THREADS, 1) spike_term_kernel(const __grid_constant__ ScanConsts K,
                                                                    const __grid_constant__ SpikeTermArgs A) {
     extern __shared__ float4 Xs[];  // [XS_CHUNKS], then the staged spike bins
@@ -100,7 +96,6 @@ __global__ void __launch_bounds__(ST_THREADS, 1) spike_term_kernel(const __grid_
     const int64_t part = blockIdx.y;
     const int32_t i_base = blockIdx.z * ST_ROWS_PER_SLICE;
     const float pl_hi = K.pl_hi[lane], pl_lo = K.pl_lo[lane];
-    const float pld_hi = K.pld_hi[lane], pld_lo = K.pld_lo[lane];
     const int64_t sp0 = part * A.segs_per_part;
     const int64_t sp1 = min(sp0 + A.segs_per_part, A.nseg);
     const int seg_w = warp & (ST_SUBSEGS - 1);   // phase A: this warp's segment
@@ -149,16 +144,15 @@ __global__ void __launch_bounds__(ST_THREADS, 1) spike_term_kernel(const __grid_
         const int64_t s = sc + seg_w;
         if (s < sp1) {
             const int64_t t0 = s * SEG;
-            float xs[4], ys[4];
+            float xs[4];
             int64_t rc[4], re[4], sv[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int32_t r = j0 + grp_w * 4 + k;
-                xs[k] = ys[k] = 0.f;
+                xs[k] = 0.f;
                 rc[k] = re[k] = 0;
                 if (r < A.n) {
                     xs[k] = (float)A.seg_carry[(int64_t)r * A.nseg + s];
-                    if (DY) ys[k] = (float)A.seg_carry_y[(int64_t)r * A.nseg + s];
                     rc[k] = A.offs[r] + A.seg_first[(int64_t)r * A.nseg + s];
                     re[k] = A.offs[r + 1];
                 }
@@ -172,12 +166,7 @@ __global__ void __launch_bounds__(ST_THREADS, 1) spike_term_kernel(const __grid_
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const uint32_t bits = seg_bits_pre(A.bins, rc[k], re[k], t0, lane, sv[k]);
-                if (DY) {
-                    float xe, ye;
-                    seg_scan_xy(K, xs[k], ys[k], bits, lane, pl_hi, pl_lo, pld_hi, pld_lo, v[k], &xe, &ye);
-                } else {
-                    seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v[k]);
-                }
+                seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v[k]);
             }
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
@@ -259,7 +248,7 @@ int spike_term_parts(const glm_ctx* c) {
     return (int)p;
 }
 
-cudaError_t launch_spike_term(glm_ctx* c, bool dy, double* out) {
+cudaError_t launch_spike_term(glm_ctx* c, double* out) {
     const Problem& P = c->pb;
     const int parts = spike_term_parts(c);
     const int64_t nsub = (P.nseg + ST_SUBSEGS - 1) / ST_SUBSEGS;
@@ -271,21 +260,13 @@ cudaError_t launch_spike_term(glm_ctx* c, bool dy, double* out) {
     A.offs = c->buf.offs;
     A.bins = c->buf.bins;
     A.seg_carry = c->buf.seg_carry;
-    A.seg_carry_y = c->buf.seg_carry_y;
     A.seg_first = c->buf.seg_first;
     A.C_part = c->buf.C_part;
     const size_t smem = ST_SMEM;
     dim3 grid((P.n + ST_JB - 1) / ST_JB, parts, (P.n + ST_ROWS_PER_SLICE - 1) / ST_ROWS_PER_SLICE);
-    cudaError_t e;
-    if (dy) {
-        e = cudaFuncSetAttribute(spike_term_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        spike_term_kernel<true><<<grid, ST_THREADS, smem, c->stream>>>(c->sc, A);
-    } else {
-        e = cudaFuncSetAttribute(spike_term_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        spike_term_kernel<false><<<grid, ST_THREADS, smem, c->stream>>>(c->sc, A);
-    }
+    cudaError_t e = cudaFuncSetAttribute(spike_term_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    spike_term_kernel<<<grid, ST_THREADS, smem, c->stream>>>(c->sc, A);
     const int64_t nn = (int64_t)P.n * P.n;
     spike_term_reduce_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(nn, parts, c->buf.C_part, out);
     return cudaGetLastError();

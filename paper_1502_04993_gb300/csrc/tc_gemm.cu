@@ -2,13 +2,16 @@
 //
 //   MODE 0, steps a3/a4:  U = b 1^T + W X  (Eq. 3) from split operands W = W_hi + W_lo, X = X_hi + X_lo:
 //                         U ~ W_hi X_hi + W_lo X_hi + W_hi X_lo (the dropped W_lo X_lo is ~2^-16 of U - b),
-//                         with the link in the epilogue (Eq. 5): E[i][t] = dt exp(U_i[t]) stored 16-bit,
-//                         FP64 per-(row, 256-bin tile) sums of exp(U).
+//                         with the link and the spike-time term in the epilogue (Eq. 5, Eq. 7): per
+//                         (row, 256-bin tile) FP64 sums of exp(U) and of U - b over the row's spike bins,
+//                         and E[i][t] = dt exp(U_i[t]) stored 16-bit.
 //                         Tile 128 x 256, K step 32, 4 stages of (W_hi, W_lo, X_hi, X_lo).  W is K-major (64-byte
 //                         swizzle); X is an N-major operand: one 3-D box of 4 bin blocks x 32 neurons x 64 bins
 //                         (128-byte swizzle) per stage.  3 MMAs per 16-wide k slice, 2 TMEM accumulators
 //                         (epilogue overlaps the next tile).
-//   MODE 1, step a5:      P_s = E X^T over a split s of the bins.  Tile 256 x 256 per block as two 128 x 256
+//   MODE 1, step a5:      P_s = E X^T over a split s of the bins (dL/dW = C - sum_s P_s, Eq. 12).  The same
+//                         kernel forms the spike term C = S X^T once per problem (S, the spike raster, in
+//                         the place of E; X_hi and X_lo in turn).  Tile 256 x 256 per block as two 128 x 256
 //                         accumulators that share every X tile (A0 = E rows m0.., A1 = E rows m0+128..),
 //                         K step 64 (128-byte swizzle), 3 stages, FP32 partials per split.
 //
@@ -34,8 +37,10 @@ namespace glm {
 namespace {
 
 constexpr int NUM_THREADS = 192;
+constexpr int SP_REG = 12;  // spike bins per (row, 256-bin tile) held in registers by the epilogue
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int BN = 256;
+static_assert(BN == SEG, "a U-product tile is one 256-bin segment of the spike index");
 
 template <int MODE>
 struct Cfg;
@@ -95,7 +100,13 @@ struct TcArgs {
     const float* b;
     const double* eb;  // exp(b_i) in FP64
     float a;           // exp(-dt / tau), for the tau partials
-    double* part_tau;  // TAU: [3][n][ntile] = sum_t e^v a^(t-t0), sum_t e^v Z_loc[t], Z_loc[t0 + 256]
+    double* part_tau;  // TAU: [5][n][ntile] = sum_t e^v a^(t-t0), sum_t e^v Z_loc[t], Z_loc[t0 + 256],
+                       //      and over the spike bins sum a^(t-t0), sum Z_loc[t]
+    double* part_s;    // MODE 0: [n][ntile] sum of U - b over the row's spike bins in the tile
+    const int64_t* offs;      // spikes (CSR) and the index of each row's first spike per 256-bin segment
+    const int32_t* bins;
+    const int32_t* seg_first;
+    int64_t nseg;
     void* E;
     double* part_e;
     int64_t ntile;
@@ -160,8 +171,7 @@ __device__ __forceinline__ uint32_t pack16<__half>(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// TAU (MODE 0 only): the epilogue also emits, per (row, tile), the partial sums that give the integral
-// part of dL/dtau.  With v = (W X)_i[t] = U_i[t] - b_i, Z_i[t] = a Z_i[t-1] + v[t-1] (Z = W dX/da), the
+// TAU (MODE 0 only): the epilogue also emits, per (row, tile), the partial sums that give dL/dtau.  With v = (W X)_i[t] = U_i[t] - b_i, Z_i[t] = a Z_i[t-1] + v[t-1] (Z = W dX/da), the
 // tile's local Z_loc starts at 0 at its first bin t0, and Z[t] = a^(t-t0) Z[t0] + Z_loc[t]; a per-row
 // combine (reduce.cu) chains the tiles.
 template <int MODE, typename T16, bool TAU>
@@ -339,7 +349,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const float dteb = (float)(A.dt * ebi);
                 double rsum = 0.0;
                 bool bad = false;
-                float zl = 0.f, pw = 1.f, p1 = 0.f, p2 = 0.f;
+                float zl = 0.f, pw = 1.f, p1 = 0.f, p2 = 0.f, p3 = 0.f, p4 = 0.f, spv = 0.f;
+                // the row's spike bins in this tile (tile = 256-bin segment n0 / 256): the first ST_REG in
+                // registers, relative to the tile start; any further ones are read per chunk
+                int64_t kb = 0, ke = 0;
+                if (i < A.n) {
+                    const int64_t sgi = (int64_t)i * A.nseg + w.n0 / BN, o0 = A.offs[i];
+                    kb = o0 + A.seg_first[sgi];
+                    ke = (w.n0 / BN + 1 < A.nseg) ? o0 + A.seg_first[sgi + 1] : A.offs[i + 1];
+                }
+                int sb[SP_REG];
+#pragma unroll
+                for (int u = 0; u < SP_REG; ++u) sb[u] = (kb + u < ke) ? A.bins[kb + u] - w.n0 : BN;
                 // E is bin-blocked: bins [64 b, 64 b + 64) of row i at (b n + i) 64
                 T16* erow = reinterpret_cast<T16*>(A.E) + ((int64_t)(w.n0 / 64) * A.n + i) * 64;
 #pragma unroll 1
@@ -347,15 +368,28 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     uint32_t r[32];
                     tc::tmem_ld32(taddr + c * 32, r);
                     tc::tmem_ld_wait();
+                    // spike mask of the chunk: bit m <-> bin n0 + 32 c + m
+                    uint32_t sm = 0;
+#pragma unroll
+                    for (int u = 0; u < SP_REG; ++u) {
+                        const uint32_t d = (uint32_t)(sb[u] - c * 32);
+                        sm |= (d < 32u) ? (1u << d) : 0u;
+                    }
+                    for (int64_t k = kb + SP_REG; k < ke; ++k) {
+                        const uint32_t d = (uint32_t)(A.bins[k] - w.n0 - c * 32);
+                        sm |= (d < 32u) ? (1u << d) : 0u;
+                    }
                     float s = 0.f;
                     int cnt = 0;
                     uint32_t pk[16];
 #pragma unroll
                     for (int e = 0; e < 32; e += 2) {
                         const int64_t t = (int64_t)w.n0 + c * 32 + e;
-                        float e0 = __expf(__uint_as_float(r[e]));
-                        float e1 = __expf(__uint_as_float(r[e + 1]));
+                        const float v0f = __uint_as_float(r[e]), v1f = __uint_as_float(r[e + 1]);
+                        float e0 = __expf(v0f);
+                        float e1 = __expf(v1f);
                         const bool v0 = t < A.T, v1 = t + 1 < A.T;
+                        const bool s0 = (sm >> e) & 1u, s1 = (sm >> (e + 1)) & 1u;
                         bad |= (v0 && !(e0 <= 3.0e38f)) || (v1 && !(e1 <= 3.0e38f));
                         if (v0) {
                             s += e0 - 1.f;
@@ -369,15 +403,25 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         } else {
                             e1 = 0.f;
                         }
+                        if (s0) spv += v0f;
+                        if (s1) spv += v1f;
                         pk[e >> 1] = pack16<T16>(dteb * e0, dteb * e1);
                         if (TAU) {
                             p1 = fmaf(e0, pw, p1);
                             p2 = fmaf(e0, zl, p2);
-                            zl = fmaf(A.a, zl, __uint_as_float(r[e]));
+                            if (s0) {
+                                p3 += pw;
+                                p4 += zl;
+                            }
+                            zl = fmaf(A.a, zl, v0f);
                             pw *= A.a;
                             p1 = fmaf(e1, pw, p1);
                             p2 = fmaf(e1, zl, p2);
-                            zl = fmaf(A.a, zl, __uint_as_float(r[e + 1]));
+                            if (s1) {
+                                p3 += pw;
+                                p4 += zl;
+                            }
+                            zl = fmaf(A.a, zl, v1f);
                             pw *= A.a;
                         }
                     }
@@ -390,12 +434,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     }
                 }
                 bad |= !(dteb <= 3.0e38f);
-                if (i < A.n) A.part_e[(int64_t)i * A.ntile + w.n0 / BN] = ebi * rsum;
+                if (i < A.n) {
+                    A.part_e[(int64_t)i * A.ntile + w.n0 / BN] = ebi * rsum;
+                    A.part_s[(int64_t)i * A.ntile + w.n0 / BN] = (double)spv;
+                }
                 if (TAU && i < A.n) {
                     const int64_t o = (int64_t)i * A.ntile + w.n0 / BN, plane = (int64_t)A.n * A.ntile;
                     A.part_tau[o] = p1;
                     A.part_tau[plane + o] = p2;
                     A.part_tau[2 * plane + o] = zl;
+                    A.part_tau[3 * plane + o] = p3;
+                    A.part_tau[4 * plane + o] = p4;
                 }
                 if (bad) atomicOr(A.flags, 1);
             } else {
@@ -511,8 +560,8 @@ int tc_nsplit(const glm_ctx* c) {
 int tc_tile_t() { return BN; }
 
 // Maps: 0 W_hi, 1 W_lo (U = W X, K-major, 64-byte swizzle), 2 X_hi, 3 X_lo (U = W X, N-major boxes of 4 x 32 x 64),
-// 4 E, 5 X_hi (E X^T, K-major boxes of 1 x 128 (E) or 1 x 256 (X) x 64).  The last four are 3-D maps over the
-// bin-blocked arrays (bin in block, neuron, bin block), all with the 128-byte swizzle.
+// 4 E, 5 X_hi, 6 X_lo (E X^T and S X^T, K-major boxes of 1 x 128 (E) or 1 x 256 (X) x 64).  Maps 2-6 are 3-D
+// maps over the bin-blocked arrays (bin in block, neuron, bin block), all with the 128-byte swizzle.
 cudaError_t tc_prepare_maps(glm_ctx* c) {
     const Problem& P = c->pb;
     const bool bf = P.prec == GLM_PREC_BF16;
@@ -525,7 +574,8 @@ cudaError_t tc_prepare_maps(glm_ctx* c) {
               encode_blocked(&c->tmap[2], bf, c->buf.X, P.n, P.Tpad, Cfg<0>::BK, BN / 64) &&
               encode_blocked(&c->tmap[3], bf, c->buf.Xlo, P.n, P.Tpad, Cfg<0>::BK, BN / 64) &&
               encode_blocked(&c->tmap[4], bf, c->buf.E, P.n, P.Tpad, 128, 1) &&
-              encode_blocked(&c->tmap[5], bf, c->buf.X, P.n, P.Tpad, BN, 1);
+              encode_blocked(&c->tmap[5], bf, c->buf.X, P.n, P.Tpad, BN, 1) &&
+              encode_blocked(&c->tmap[6], bf, c->buf.Xlo, P.n, P.Tpad, BN, 1);
     return ok ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -555,6 +605,11 @@ static TcArgs base_args(glm_ctx* c) {
     A.eb = c->buf.eb;
     A.a = (float)P.a;
     A.part_tau = nullptr;
+    A.part_s = nullptr;
+    A.offs = c->buf.offs;
+    A.bins = c->buf.bins;
+    A.seg_first = c->buf.seg_first;
+    A.nseg = P.nseg;
     A.E = nullptr;
     A.part_e = nullptr;
     A.part_g = nullptr;
@@ -588,6 +643,7 @@ cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, boo
     A.E = c->buf.E;
     A.part_e = c->buf.part_e;
     A.part_tau = c->buf.part_tau;
+    A.part_s = c->buf.part_s;
     A.idesc |= 1u << 16;  // B (X) is N-major
     if (tau) {
         if (P.prec == GLM_PREC_BF16)
@@ -599,7 +655,7 @@ cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, boo
     return run<0, __half>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
 }
 
-cudaError_t launch_tc_grad(glm_ctx* c) {
+static cudaError_t run_products(glm_ctx* c, const CUtensorMap& mapB) {
     const Problem& P = c->pb;
     TcArgs A = base_args(c);
     A.mt = (P.n + 255) / 256;
@@ -610,9 +666,36 @@ cudaError_t launch_tc_grad(glm_ctx* c) {
     A.units = (int64_t)A.mt * A.nt * ns;
     A.nsplit = ns;
     A.part_g = c->buf.part_g;
-    if (P.prec == GLM_PREC_BF16)
-        return run<1, __nv_bfloat16>(c, c->tmap[4], c->tmap[4], c->tmap[5], c->tmap[5], A);
-    return run<1, __half>(c, c->tmap[4], c->tmap[4], c->tmap[5], c->tmap[5], A);
+    if (P.prec == GLM_PREC_BF16) return run<1, __nv_bfloat16>(c, c->tmap[4], c->tmap[4], mapB, mapB, A);
+    return run<1, __half>(c, c->tmap[4], c->tmap[4], mapB, mapB, A);
+}
+
+cudaError_t launch_tc_grad(glm_ctx* c) { return run_products(c, c->tmap[5]); }
+
+// S[i][t] = 1 at every spike, written into the (zeroed) bin-blocked E buffer; block per row.
+__global__ void spike_raster_kernel(int32_t n, const int64_t* __restrict__ offs, const int32_t* __restrict__ bins,
+                                    uint16_t one, uint16_t* __restrict__ S) {
+    const int32_t i = blockIdx.x;
+    for (int64_t k = offs[i] + threadIdx.x; k < offs[i + 1]; k += blockDim.x) {
+        const int64_t t = bins[k];
+        S[((t >> 6) * n + i) * 64 + (t & 63)] = one;
+    }
+}
+
+// C = S (X_hi + X_lo)^T with S, the spike raster, exact in 16 bits: two passes of the E X^T kernel, the
+// second adding to the first.  The E buffer holds S until the first evaluation overwrites it.
+cudaError_t launch_tc_spike_term(glm_ctx* c) {
+    const Problem& P = c->pb;
+    cudaError_t e = cudaMemsetAsync(c->buf.E, 0, (size_t)P.n * P.Tpad * 2, c->stream);
+    if (e != cudaSuccess) return e;
+    const uint16_t one = (P.prec == GLM_PREC_BF16) ? 0x3F80u : 0x3C00u;
+    spike_raster_kernel<<<P.n, 256, 0, c->stream>>>(P.n, c->buf.offs, c->buf.bins, one,
+                                                    reinterpret_cast<uint16_t*>(c->buf.E));
+    const int ns = tc_nsplit(c);
+    if ((e = run_products(c, c->tmap[5])) != cudaSuccess) return e;
+    if ((e = launch_sum_splits(c, ns, c->buf.C, false)) != cudaSuccess) return e;
+    if ((e = run_products(c, c->tmap[6])) != cudaSuccess) return e;
+    return launch_sum_splits(c, ns, c->buf.C, true);
 }
 
 }  // namespace glm
