@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--fit", default="", help="comma list of precisions to also run glm_fit with (e.g. bf16,f32)")
     ap.add_argument("--fit-eta", type=float, default=1e-9)
     ap.add_argument("--fit-max-iter", type=int, default=400)
+    ap.add_argument("--batch", type=int, default=0,
+                    help="also fit this many uneven recordings with glm_fit_batch and one after another")
+    ap.add_argument("--batch-t-scale", type=float, default=0.1, help="recording-length scale of --batch")
     return ap.parse_args()
 
 
@@ -181,6 +184,40 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_batch(args, glm, device, prec):
+    """Uneven recordings (N ~ U{100..1500}, T ~ U(300, 3600) s x t_scale, 3-12 Hz) fitted one after another
+    and then together with glm_fit_batch; aggregate neuron*bins/s counts N T per evaluation of each fit."""
+    import torch
+    import synth
+    specs = synth.batch_workloads(args.batch, t_scale=args.batch_t_scale)
+    recs = [synth.make_workload(None, **sp) for sp in specs]
+    ctxs = [glm.GLM(device) for _ in recs]
+    try:
+        for c, w in zip(ctxs, recs):
+            c.set_problem(w["offs"], w["bins"], w["n_bins"], w["dt"], w["tau"], prec=prec)
+        kw = dict(eta=args.fit_eta, max_iter=args.fit_max_iter)
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        seq = [c.fit(**kw)["report"] for c in ctxs]
+        torch.cuda.synchronize(device)
+        t_seq = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        res, rc = glm.fit_batch(ctxs, **kw)
+        torch.cuda.synchronize(device)
+        t_bat = time.perf_counter() - t0
+        units_seq = sum(w["n"] * w["n_bins"] * r["evaluations"] for w, r in zip(recs, seq))
+        units_bat = sum(w["n"] * w["n_bins"] * r["report"]["evaluations"] for w, r in zip(recs, res))
+        return {"recordings": len(recs), "t_scale": args.batch_t_scale,
+                "n": [w["n"] for w in recs], "n_bins": [w["n_bins"] for w in recs],
+                "sequential_s": t_seq, "batched_s": t_bat, "speedup": t_seq / t_bat, "status": rc,
+                "sequential_neuron_bins_per_s": units_seq / t_seq, "batched_neuron_bins_per_s": units_bat / t_bat,
+                "iterations_max": max(r["report"]["iterations"] for r in res),
+                "L_sequential": sum(r["L"] for r in seq), "L_batched": sum(r["report"]["L"] for r in res)}
+    finally:
+        for c in ctxs:
+            c.close()
 
 
 def main():
@@ -334,6 +371,8 @@ def main():
             for p, v in fits.items():
                 v["speedup_vs_f32"] = fits["f32"]["seconds"] / v["seconds"]
         line["fit"] = {"eta": args.fit_eta, "max_iter": args.fit_max_iter, "by_precision": fits}
+    if args.batch:
+        line["batch"] = run_batch(args, glm, device, prec)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, os.cpu_count() or 1)
         line["cpu_baseline"].pop("seconds", None)

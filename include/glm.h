@@ -200,6 +200,37 @@ void glm_fit_default_opts(glm_fit_opts_t* opts);
 int glm_fit(glm_ctx* ctx, const glm_fit_opts_t* opts, float* W_dev, float* b_dev, int8_t* row_status_host,
             glm_fit_report_t* report);
 
+/* Fit several independent recordings together (the batched form of glm_fit).  ctxs[p] holds problem p
+ * (set with glm_set_problem; uneven n and n_bins are fine); all contexts are on the same device and use
+ * the same tensor-core precision (GLM_PREC_BF16 or GLM_PREC_F16).  Every evaluation is one launch of each
+ * contraction over the tiles of all problems, and one optimiser iteration for all of them (directions,
+ * line-search rounds, gradient, update) is recorded once as a CUDA graph and replayed; a line search that
+ * is still open after an iteration's rounds continues in the next iteration.  All work runs on ctxs[0]'s
+ * stream.  W_dev[p], b_dev[p]: as for glm_fit; row_status_host and reports: optional arrays of n_prob
+ * (row_status_host[p] may be NULL).  n_prob: 1..32.  Returns the worst of the per-problem glm_fit
+ * statuses or a negative GLM_ERR_* (INVALID_ARG for mixed devices or precisions, UNSUPPORTED for
+ * GLM_PREC_F32).  Synchronises ctxs[0]'s stream. */
+#define GLM_FIT_BATCH_MAX 32
+int glm_fit_batch(glm_ctx* const* ctxs, int32_t n_prob, const glm_fit_opts_t* opts, float* const* W_dev,
+                  float* const* b_dev, int8_t* const* row_status_host, glm_fit_report_t* reports);
+
+/* ---- autotuner of the gradient product's tile shape ----
+ * (no counterpart in the paper.)  Times the gradient product E X^T of the current problem for row tiles of
+ * 256 and 128 neurons and 1, 2, 4 and 8 bin splits per SM (the K extent of a tile), and keeps the fastest
+ * for the context's later evaluations and fits.  The choice is cached for the process per precision, n,
+ * n_bins and GPU, so later contexts of the same shape reuse it without timing.  Results of later calls are
+ * reproducible for a given choice; another choice changes the FP32 summation order of the gradient.
+ * glm_fit_batch tunes its batched launch the same way, for all its problems at once.  Tensor-core
+ * precisions only (GLM_ERR_UNSUPPORTED for GLM_PREC_F32).  Synchronises the context's stream. */
+typedef struct {
+    int32_t mode;       /* 1: 256-row tiles, 2: 128-row tiles */
+    int32_t nsplit;     /* bin splits */
+    int32_t cached;     /* 1 if taken from the process cache without timing */
+    int32_t candidates; /* candidates timed */
+    float best_ms;      /* time of one gradient product with the choice */
+} glm_tune_report_t;
+int glm_autotune(glm_ctx* ctx, glm_tune_report_t* report);
+
 /* ---- classification of reconstructed weights (Sec. 3.1 GMM, Sec. 3.3 k-means, Table 2, Eq. 20) ---- */
 #define GLM_CLASSIFY_GMM 0    /* 3-component Gaussian mixture by EM, started from 3-means (default) */
 #define GLM_CLASSIFY_KMEANS 1 /* 3-means (Lloyd) */

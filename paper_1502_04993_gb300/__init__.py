@@ -69,11 +69,18 @@ class FitReport(ctypes.Structure):
                 ("seconds", ctypes.c_double)]
 
 
+class TuneReport(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("nsplit", ctypes.c_int32), ("cached", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_float)]
+
+
 ROW_STATUS = {0: "converged", 1: "maxiter", 2: "stalled", 3: "degenerate", 4: "at_floor"}
 ERRORS[-11] = "GLM_ERR_SCRATCH_TOO_SMALL"
 SIGNATURES["glm_loglik_noalloc"] = ([_i32, _i64, _f64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int)
 SIGNATURES["glm_fit_default_opts"] = ([ctypes.POINTER(FitOpts)], None)
 SIGNATURES["glm_fit"] = ([_vp, ctypes.POINTER(FitOpts), _vp, _vp, _vp, ctypes.POINTER(FitReport)], ctypes.c_int)
+SIGNATURES["glm_fit_batch"] = ([_vp, _i32, ctypes.POINTER(FitOpts), _vp, _vp, _vp, ctypes.POINTER(FitReport)], ctypes.c_int)
+SIGNATURES["glm_autotune"] = ([_vp, _vp], ctypes.c_int)
 SIGNATURES["glm_classify"] =([_vp, _i32, ctypes.POINTER(ClassifyOpts), _vp, _vp, _vp, ctypes.POINTER(ClassifyReport)],
                               ctypes.c_int)
 
@@ -112,6 +119,37 @@ def load_library(path: str = LIB_PATH):
 
 def _ptr(t) -> int | None:
     return None if t is None else t.data_ptr()
+
+
+def fit_batch(contexts, *, method: str = "lbfgs", m: int = 10, max_iter: int = 500, eta: float = 1e-10,
+              c1: float = 1e-4, max_halvings: int = 40, gain_floor: float = -1.0):
+    """Fit the problems of several contexts together (glm_fit_batch): one launch per contraction over all
+    problems, one CUDA graph per optimiser iteration.  Returns a list of dict(W, b, status, report), one per
+    context, and the call's status code."""
+    lib = load_library()
+    k = len(contexts)
+    if k == 0:
+        raise ValueError("no contexts")
+    torch = contexts[0].torch
+    Ws, bs, sts = [], [], []
+    for g in contexts:
+        dev = f"cuda:{g.device}"
+        Ws.append(torch.zeros((g.n, g.n), dtype=torch.float32, device=dev))
+        bs.append(torch.zeros(g.n, dtype=torch.float32, device=dev))
+        sts.append(np.zeros(g.n, dtype=np.int8))
+    arr = ctypes.c_void_p * k
+    hs = arr(*[g.h for g in contexts])
+    wp = arr(*[w.data_ptr() for w in Ws])
+    bp = arr(*[b.data_ptr() for b in bs])
+    sp = arr(*[s.ctypes.data for s in sts])
+    reps = (FitReport * k)()
+    o = FitOpts({"lbfgs": 0, "ga": 1}[method], m, max_iter, eta, c1, max_halvings, 0, gain_floor)
+    rc = lib.glm_fit_batch(hs, k, ctypes.byref(o), wp, bp, sp, reps)
+    if rc < 0:
+        contexts[0]._check(rc, "glm_fit_batch")
+    out = [dict(W=Ws[p], b=bs[p], status=sts[p], report={f: getattr(reps[p], f) for f, _ in FitReport._fields_})
+           for p in range(k)]
+    return out, rc
 
 
 def classify(W, method: str = "gmm", truth=None, types=None, max_iter: int = 1000, tol: float = 1e-12):
@@ -256,6 +294,12 @@ class GLM:
             self._check(rc, "glm_fit")
         report = {f: getattr(rep, f) for f, _ in FitReport._fields_}
         return dict(W=Wd, b=bd, status=status, report=report, rc=rc)
+
+    def autotune(self) -> dict:
+        """Time the gradient product's tile shapes for this problem and keep the fastest (glm_autotune)."""
+        rep = TuneReport()
+        self._check(self.lib.glm_autotune(self.h, ctypes.byref(rep)), "glm_autotune")
+        return {f: getattr(rep, f) for f, _ in TuneReport._fields_}
 
     def loglik_grad(self, W, b, *, grad: bool = True, total: bool = True, tau_grad: bool = False, out=None):
         """L_i, L, dL/dW, dL/db (and with tau_grad dL/dtau) at (W, b).  W: (n, n) float32, b: (n,) float32."""

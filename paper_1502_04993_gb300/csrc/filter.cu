@@ -28,7 +28,7 @@ void fill_scan_consts(double a, ScanConsts* sc) {
     for (int m = 0; m <= 8; ++m) split(std::pow(a, (double)m), &sc->pm_hi[m], &sc->pm_lo[m]);
     for (int d = 0; d < 5; ++d) split(std::pow(a, 8.0 * (1 << d)), &sc->ps_hi[d], &sc->ps_lo[d]);
     for (int l = 0; l < 32; ++l) split(std::pow(a, 8.0 * l), &sc->pl_hi[l], &sc->pl_lo[l]);
-    // d/da of the same powers: k a^(k-1)
+    for (int k = 0; k < 8; ++k) sc->pr[k] = (float)std::pow(a, (double)k);
 }
 
 // Block per row: segment-first indices and, in seg_carry, the contribution of each segment's own

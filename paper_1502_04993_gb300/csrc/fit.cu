@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -64,7 +65,7 @@ struct FitState {
     int32_t* hn;     // [n]  stored curvature pairs
     int32_t* hs;     // [n]  ring start
     int32_t* iters;  // [n]
-    int* counters;   // [3]  active rows, open line searches, rows stopped in this round
+    int* counters;   // [4]  active rows, open line searches, rows stopped in this round, rows to evaluate
     const double* qd; // [n]  spike counts
     double floor;     // smallest predicted gain s |g.d| worth testing, relative to |L_i| + q_i
 };
@@ -217,6 +218,10 @@ __global__ void fit_direction_kernel(FitState F) {
     __shared__ double alpha[32];
     const int32_t i = blockIdx.x;
     if (F.status[i] != ACTIVE) return;
+    if (F.pend[i]) {  // a search still open (batched fits): it keeps its direction and step
+        if (threadIdx.x == 0) atomicAdd(F.counters + 0, 1);
+        return;
+    }
     const double* g = F.g + (int64_t)i * F.d;
     double* q = F.dir + (int64_t)i * F.d;
     const int hn = (F.method == GLM_FIT_LBFGS) ? F.hn[i] : 0;
@@ -295,6 +300,27 @@ __global__ void fit_direction_kernel(FitState F) {
     }
 }
 
+// The rows with an open line search, in increasing order (one block; chunked block scan).
+__global__ void fit_compact_kernel(FitState F, int32_t* __restrict__ rows) {
+    __shared__ int32_t sh[1024];
+    const int32_t per = (F.n + blockDim.x - 1) / blockDim.x;
+    const int32_t r0 = min((int32_t)threadIdx.x * per, F.n), r1 = min(r0 + per, F.n);
+    int32_t cnt = 0;
+    for (int32_t i = r0; i < r1; ++i) cnt += (F.status[i] == ACTIVE && F.pend[i]) ? 1 : 0;
+    sh[threadIdx.x] = cnt;
+    __syncthreads();
+    for (int d = 1; d < (int)blockDim.x; d <<= 1) {  // inclusive Hillis-Steele scan
+        const int32_t v = (threadIdx.x >= (unsigned)d) ? sh[threadIdx.x - d] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int32_t pos = sh[threadIdx.x] - cnt;
+    for (int32_t i = r0; i < r1; ++i)
+        if (F.status[i] == ACTIVE && F.pend[i]) rows[pos++] = i;
+    if (threadIdx.x == blockDim.x - 1) F.counters[3] = sh[threadIdx.x];  // rows to evaluate
+}
+
 __global__ void fit_write_kernel(FitState F, float* __restrict__ W, float* __restrict__ b) {
     const int32_t i = blockIdx.x;
     const double* th = F.theta + (int64_t)i * F.d;
@@ -313,8 +339,20 @@ __global__ void fit_finish_kernel(FitState F) {
 
 }  // namespace
 
-int fit_run(glm_ctx* c, const glm_fit_opts_t* o, float* W, float* b, int8_t* row_status, glm_fit_report_t* rep) {
-    const auto t_start = std::chrono::steady_clock::now();
+namespace {
+
+// One problem's optimiser state: device pointers into its fit_mem.
+struct FitProb {
+    glm_ctx* c = nullptr;
+    FitState F;
+    double *G = nullptr, *gb = nullptr, *Lr = nullptr;
+    int32_t* eval_rows = nullptr;  // rows of the current line-search round
+    float *W32 = nullptr, *b32 = nullptr;
+    float *W = nullptr, *b = nullptr;  // caller's output (and warm start)
+    int iters = 0, evals = 0, grads = 0;
+};
+
+int fit_setup(glm_ctx* c, const glm_fit_opts_t* o, float* W, float* b, FitProb* fp) {
     const Problem& P = c->pb;
     Buffers& B = c->buf;
     const int32_t n = P.n, d = n + 1, m = o->m;
@@ -323,12 +361,12 @@ int fit_run(glm_ctx* c, const glm_fit_opts_t* o, float* W, float* b, int8_t* row
         if (B.fit_mem) return set_error(c, GLM_ERR_UNSUPPORTED, "glm_fit: the L-BFGS memory cannot change within a problem");
         const size_t nd = (size_t)n * d;
         const size_t bytes = sizeof(double) * (nd * (3 + 2 * (size_t)m) + (size_t)m * n + 4 * (size_t)n + (size_t)n * n + n + n) +
-                             sizeof(int32_t) * 7 * (size_t)n + sizeof(float) * ((size_t)n * n + n) + 64;
+                             sizeof(int32_t) * 8 * (size_t)n + sizeof(float) * ((size_t)n * n + n) + 64;
         int rc = ws_alloc_bytes(c, &B.fit_mem, bytes);
         if (rc) return rc;
         B.fit_m = m;
     }
-    FitState F;
+    FitState& F = fp->F;
     F.n = n;
     F.d = d;
     F.m = m;
@@ -337,147 +375,408 @@ int fit_run(glm_ctx* c, const glm_fit_opts_t* o, float* W, float* b, int8_t* row
     // gains below this fraction of |L_i| + q_i are not resolved by the evaluation (the 16-bit forms carry
     // a gradient error of ~1e-4 of its terms, the plain FP32 form ~1e-9 of L)
     F.floor = o->gain_floor >= 0.0 ? o->gain_floor : (P.prec == GLM_PREC_F32) ? 1e-13 : 1e-10;
-    {
-        uint8_t* p = reinterpret_cast<uint8_t*>(B.fit_mem);
-        const size_t nd = (size_t)n * d;
-        double* dp = reinterpret_cast<double*>(p);
-        F.theta = dp;
-        dp += nd;
-        F.g = dp;
-        dp += nd;
-        F.dir = dp;
-        dp += nd;
-        F.S = dp;
-        dp += (size_t)m * nd;
-        F.Y = dp;
-        dp += (size_t)m * nd;
-        F.rho = dp;
-        dp += (size_t)m * n;
-        F.Lcur = dp;
-        dp += n;
-        F.step = dp;
-        dp += n;
-        F.gd = dp;
-        dp += n;
-        F.gastep = dp;
-        dp += n;
-        double* G = dp;
-        dp += (size_t)n * n;
-        double* gb = dp;
-        dp += n;
-        double* Lr = dp;
-        dp += n;
-        int32_t* ip = reinterpret_cast<int32_t*>(dp);
-        F.status = ip;
-        ip += n;
-        F.pend = ip;
-        ip += n;
-        F.acc = ip;
-        ip += n;
-        F.halv = ip;
-        ip += n;
-        F.hn = ip;
-        ip += n;
-        F.hs = ip;
-        ip += n;
-        F.iters = ip;
-        ip += n;
-        float* fp = reinterpret_cast<float*>(ip);
-        float* W32 = fp;
-        fp += (size_t)n * n;
-        float* b32 = fp;
-        fp += n;
-        F.counters = reinterpret_cast<int*>((reinterpret_cast<uintptr_t>(fp) + 15) & ~(uintptr_t)15);
+    const size_t nd = (size_t)n * d;
+    double* dp = reinterpret_cast<double*>(B.fit_mem);
+    F.theta = dp;
+    dp += nd;
+    F.g = dp;
+    dp += nd;
+    F.dir = dp;
+    dp += nd;
+    F.S = dp;
+    dp += (size_t)m * nd;
+    F.Y = dp;
+    dp += (size_t)m * nd;
+    F.rho = dp;
+    dp += (size_t)m * n;
+    F.Lcur = dp;
+    dp += n;
+    F.step = dp;
+    dp += n;
+    F.gd = dp;
+    dp += n;
+    F.gastep = dp;
+    dp += n;
+    fp->G = dp;
+    dp += (size_t)n * n;
+    fp->gb = dp;
+    dp += n;
+    fp->Lr = dp;
+    dp += n;
+    int32_t* ip = reinterpret_cast<int32_t*>(dp);
+    F.status = ip;
+    ip += n;
+    F.pend = ip;
+    ip += n;
+    F.acc = ip;
+    ip += n;
+    F.halv = ip;
+    ip += n;
+    F.hn = ip;
+    ip += n;
+    F.hs = ip;
+    ip += n;
+    F.iters = ip;
+    ip += n;
+    fp->eval_rows = ip;
+    ip += n;
+    float* flp = reinterpret_cast<float*>(ip);
+    fp->W32 = flp;
+    flp += (size_t)n * n;
+    fp->b32 = flp;
+    flp += n;
+    F.counters = reinterpret_cast<int*>((reinterpret_cast<uintptr_t>(flp) + 15) & ~(uintptr_t)15);
+    fp->c = c;
+    fp->W = W;
+    fp->b = b;
+    return GLM_OK;
+}
 
-        cudaStream_t st = c->stream;
-        int evals = 0, grads = 0, iters = 0;
-        auto ck = [&](cudaError_t e) { return e == cudaSuccess ? GLM_OK : set_error(c, GLM_ERR_CUDA, cudaGetErrorString(e)); };
-        int rc;
-        fit_init_kernel<<<n, FT, 0, st>>>(F, P.T, P.dt, B.qd, o->warm_start, W, b);
-        fit_trial_kernel<<<n, FT, 0, st>>>(F, W32, b32);
-        c->launches += 2;
-        if ((rc = ck(reset_flags(c)))) return rc;
-        if ((rc = eval_enqueue(c, W32, b32, Lr, G, gb, true, false))) return rc;
-        evals++;
-        grads++;
-        fit_grad0_kernel<<<n, FT, 0, st>>>(F, Lr, G, gb);
-        c->launches += 1;
-        int host_cnt[3] = {0, 0, 0};
-        while (true) {
-            if ((rc = ck(cudaMemsetAsync(F.counters, 0, 3 * sizeof(int), st)))) return rc;
-            fit_direction_kernel<<<n, FT, 0, st>>>(F);
-            c->launches += 1;
-            if ((rc = ck(cudaMemcpyAsync(host_cnt, F.counters, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)))) return rc;
-            if ((rc = eval_status(c))) return rc;
-            if (host_cnt[0] == 0 || iters >= o->max_iter) break;
-            // line search: every round evaluates all rows' trial points in one batched product
-            int rounds = 0;
-            while (true) {
-                fit_trial_kernel<<<n, FT, 0, st>>>(F, W32, b32);
-                c->launches += 1;
-                if ((rc = eval_enqueue(c, W32, b32, Lr, nullptr, nullptr, false, false))) return rc;
-                evals++;
-                if ((rc = ck(cudaMemsetAsync(F.counters + 1, 0, 2 * sizeof(int), st)))) return rc;
-                fit_armijo_kernel<<<(n + 255) / 256, 256, 0, st>>>(F, Lr, o->c1, o->max_halvings);
-                c->launches += 1;
-                rounds++;
-                if ((rc = ck(cudaMemcpyAsync(host_cnt + 1, F.counters + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, st))))
-                    return rc;
-                // a non-finite trial only fails the Armijo test; clear the flag before it is read
-                if ((rc = ck(cudaStreamSynchronize(st)))) return rc;
-                if ((rc = ck(reset_flags(c)))) return rc;
-                if (host_cnt[1] == 0) break;
-            }
-            // accepted points: gradient there.  Every accepted row was evaluated at its accepted point in
-            // each round since its acceptance, the last one included, so that round's U product and
-            // per-tile sums serve the gradient.  Rows not accepted (stalled, restarting) take nothing
-            // from this evaluation.
-            fit_commit_kernel<<<n, FT, 0, st>>>(F);
-            c->launches += 1;
-            if ((rc = eval_enqueue(c, W32, b32, Lr, G, gb, true, true))) return rc;
-            grads++;
-            (void)rounds;
-            fit_update_kernel<<<n, FT, 0, st>>>(F, Lr, G, gb, o->eta, o->max_iter);
-            c->launches += 1;
-            iters++;
-        }
-        fit_finish_kernel<<<(n + 255) / 256, 256, 0, st>>>(F);
-        fit_write_kernel<<<n, FT, 0, st>>>(F, W, b);
-        c->launches += 2;
-        // final log-likelihood at the returned point
-        fit_trial_kernel<<<n, FT, 0, st>>>(F, W32, b32);
-        c->launches += 1;
-        if ((rc = eval_enqueue(c, W32, b32, Lr, nullptr, nullptr, false, false))) return rc;
-        evals++;
-        std::vector<int32_t> stat(n);
-        std::vector<double> Lh(n);
-        if ((rc = ck(cudaMemcpyAsync(stat.data(), F.status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st)))) return rc;
-        if ((rc = ck(cudaMemcpyAsync(Lh.data(), Lr, sizeof(double) * n, cudaMemcpyDeviceToHost, st)))) return rc;
-        if ((rc = eval_status(c))) return rc;
-        int cnt[5] = {0, 0, 0, 0, 0};
-        double Ltot = 0.0;
-        for (int32_t i = 0; i < n; ++i) {
-            const int s = stat[i];
-            if (s >= 0 && s < 5) cnt[s]++;
-            if (row_status) row_status[i] = (int8_t)s;
-            Ltot += Lh[i];
-        }
-        if (rep) {
-            rep->iterations = iters;
-            rep->evaluations = evals;
-            rep->gradients = grads;
-            rep->converged = cnt[GLM_ROW_CONVERGED];
-            rep->maxiter = cnt[GLM_ROW_MAXITER];
-            rep->stalled = cnt[GLM_ROW_STALLED];
-            rep->degenerate = cnt[GLM_ROW_DEGENERATE];
-            rep->at_floor = cnt[GLM_ROW_AT_FLOOR];
-            rep->L = Ltot;
-            rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-        }
-        if (cnt[GLM_ROW_MAXITER]) return GLM_STATUS_NOT_CONVERGED;
-        if (cnt[GLM_ROW_STALLED]) return GLM_STATUS_STALLED;
-        return GLM_OK;
+int ck(glm_ctx* c, cudaError_t e) { return e == cudaSuccess ? GLM_OK : set_error(c, GLM_ERR_CUDA, cudaGetErrorString(e)); }
+
+// Start point, its log-likelihood and gradient.
+int fit_start(FitProb& fp, const glm_fit_opts_t* o) {
+    glm_ctx* c = fp.c;
+    const Problem& P = c->pb;
+    const int32_t n = P.n;
+    cudaStream_t st = c->stream;
+    int rc;
+    fit_init_kernel<<<n, FT, 0, st>>>(fp.F, P.T, P.dt, c->buf.qd, o->warm_start, fp.W, fp.b);
+    fit_trial_kernel<<<n, FT, 0, st>>>(fp.F, fp.W32, fp.b32);
+    c->launches += 2;
+    if ((rc = ck(c, reset_flags(c)))) return rc;
+    if ((rc = eval_enqueue(c, fp.W32, fp.b32, fp.Lr, fp.G, fp.gb, true, false))) return rc;
+    fp.evals++;
+    fp.grads++;
+    fit_grad0_kernel<<<n, FT, 0, st>>>(fp.F, fp.Lr, fp.G, fp.gb);
+    c->launches += 1;
+    return GLM_OK;
+}
+
+// Returned point, final log-likelihood, row states and report.
+int fit_end(FitProb& fp, int8_t* row_status, glm_fit_report_t* rep, double seconds) {
+    glm_ctx* c = fp.c;
+    const int32_t n = c->pb.n;
+    cudaStream_t st = c->stream;
+    int rc;
+    fit_finish_kernel<<<(n + 255) / 256, 256, 0, st>>>(fp.F);
+    fit_write_kernel<<<n, FT, 0, st>>>(fp.F, fp.W, fp.b);
+    fit_trial_kernel<<<n, FT, 0, st>>>(fp.F, fp.W32, fp.b32);
+    c->launches += 3;
+    if ((rc = eval_enqueue(c, fp.W32, fp.b32, fp.Lr, nullptr, nullptr, false, false))) return rc;
+    fp.evals++;
+    std::vector<int32_t> stat(n);
+    std::vector<double> Lh(n);
+    if ((rc = ck(c, cudaMemcpyAsync(stat.data(), fp.F.status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st))))
+        return rc;
+    if ((rc = ck(c, cudaMemcpyAsync(Lh.data(), fp.Lr, sizeof(double) * n, cudaMemcpyDeviceToHost, st)))) return rc;
+    if ((rc = eval_status(c))) return rc;
+    int cnt[5] = {0, 0, 0, 0, 0};
+    double Ltot = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+        const int s = stat[i];
+        if (s >= 0 && s < 5) cnt[s]++;
+        if (row_status) row_status[i] = (int8_t)s;
+        Ltot += Lh[i];
     }
+    if (rep) {
+        rep->iterations = fp.iters;
+        rep->evaluations = fp.evals;
+        rep->gradients = fp.grads;
+        rep->converged = cnt[GLM_ROW_CONVERGED];
+        rep->maxiter = cnt[GLM_ROW_MAXITER];
+        rep->stalled = cnt[GLM_ROW_STALLED];
+        rep->degenerate = cnt[GLM_ROW_DEGENERATE];
+        rep->at_floor = cnt[GLM_ROW_AT_FLOOR];
+        rep->L = Ltot;
+        rep->seconds = seconds;
+    }
+    if (cnt[GLM_ROW_MAXITER]) return GLM_STATUS_NOT_CONVERGED;
+    if (cnt[GLM_ROW_STALLED]) return GLM_STATUS_STALLED;
+    return GLM_OK;
+}
+
+}  // namespace
+
+int fit_run(glm_ctx* c, const glm_fit_opts_t* o, float* W, float* b, int8_t* row_status, glm_fit_report_t* rep) {
+    const auto t_start = std::chrono::steady_clock::now();
+    const int32_t n = c->pb.n;
+    FitProb fp;
+    int rc;
+    if ((rc = fit_setup(c, o, W, b, &fp))) return rc;
+    FitState& F = fp.F;
+    cudaStream_t st = c->stream;
+    if ((rc = fit_start(fp, o))) return rc;
+    int host_cnt[3] = {0, 0, 0};
+    while (true) {
+        if ((rc = ck(c, cudaMemsetAsync(F.counters, 0, 4 * sizeof(int), st)))) return rc;
+        fit_direction_kernel<<<n, FT, 0, st>>>(F);
+        c->launches += 1;
+        if ((rc = ck(c, cudaMemcpyAsync(host_cnt, F.counters, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)))) return rc;
+        if ((rc = eval_status(c))) return rc;
+        if (host_cnt[0] == 0 || fp.iters >= o->max_iter) break;
+        // line search: every round evaluates the trial points of the rows whose search is still open, in
+        // one batched product over just those rows; their rates and per-tile sums land at their own row
+        // positions, so an accepted row keeps the values of its accepted point until the gradient.
+        int32_t open = host_cnt[0];
+        while (true) {
+            fit_trial_kernel<<<n, FT, 0, st>>>(F, fp.W32, fp.b32);
+            fit_compact_kernel<<<1, 1024, 0, st>>>(F, fp.eval_rows);
+            c->launches += 2;
+            if ((rc = eval_enqueue(c, fp.W32, fp.b32, fp.Lr, nullptr, nullptr, false, false, false, fp.eval_rows, open)))
+                return rc;
+            fp.evals++;
+            if ((rc = ck(c, cudaMemsetAsync(F.counters + 1, 0, 2 * sizeof(int), st)))) return rc;
+            fit_armijo_kernel<<<(n + 255) / 256, 256, 0, st>>>(F, fp.Lr, o->c1, o->max_halvings);
+            c->launches += 1;
+            if ((rc = ck(c, cudaMemcpyAsync(host_cnt + 1, F.counters + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, st))))
+                return rc;
+            // a non-finite trial only fails the Armijo test; clear the flag before it is read
+            if ((rc = ck(c, cudaStreamSynchronize(st)))) return rc;
+            if ((rc = ck(c, reset_flags(c)))) return rc;
+            if (host_cnt[1] == 0) break;
+            open = host_cnt[1];
+        }
+        // accepted points: gradient there, from the rates and per-tile sums each accepted row left in
+        // its acceptance round.  Rows not accepted (stopped, restarting) take nothing from it.
+        fit_commit_kernel<<<n, FT, 0, st>>>(F);
+        c->launches += 1;
+        if ((rc = eval_enqueue(c, fp.W32, fp.b32, fp.Lr, fp.G, fp.gb, true, true))) return rc;
+        fp.grads++;
+        fit_update_kernel<<<n, FT, 0, st>>>(F, fp.Lr, fp.G, fp.gb, o->eta, o->max_iter);
+        c->launches += 1;
+        fp.iters++;
+    }
+    return fit_end(fp, row_status, rep,
+                   std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
+}
+
+// ---- several problems at once ----
+//
+// Every problem keeps its own optimiser state; the two contractions of each evaluation are one launch
+// over all problems (tensor-core forms).  One iteration - directions, GRAPH_ROUNDS line-search rounds,
+// gradient, update - is recorded once as a CUDA graph and replayed; the host reads one count per
+// problem after each replay.  A row whose search is still open after the rounds of an iteration keeps
+// its direction and step and goes on searching in the next one.
+
+namespace {
+
+constexpr int GRAPH_ROUNDS = 3;
+
+// rows still active in each problem (block per problem)
+__global__ void count_active_kernel(const int32_t* const* __restrict__ status, const int32_t* __restrict__ nrows,
+                                    int* __restrict__ dst) {
+    __shared__ int sh[32];
+    const int p = blockIdx.x;
+    const int32_t* st = status[p];
+    int c = 0;
+    for (int32_t i = threadIdx.x; i < nrows[p]; i += blockDim.x) c += st[i] == ACTIVE ? 1 : 0;
+    for (int off = 16; off >= 1; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        dst[p] = t;
+    }
+}
+
+}  // namespace
+
+int fit_run_batch(glm_ctx* const* cs, int np, const glm_fit_opts_t* o, float* const* W, float* const* b,
+                  int8_t* const* row_status, glm_fit_report_t* reps) {
+    const auto t_start = std::chrono::steady_clock::now();
+    glm_ctx* c0 = cs[0];
+    // the batch runs on a private stream (a CUDA graph cannot be recorded on the legacy default stream),
+    // ordered after the work already queued on the first context's stream
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+        return set_error(c0, GLM_ERR_CUDA, "cudaStreamCreateWithFlags");
+    {
+        cudaEvent_t ev;
+        cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, c0->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+        cudaEventDestroy(ev);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(st);
+            return set_error(c0, GLM_ERR_CUDA, cudaGetErrorString(e));
+        }
+    }
+    std::vector<cudaStream_t> saved(np);
+    std::vector<bool> saved_prof(np);
+    for (int p = 0; p < np; ++p) {  // all work of the batch goes to the first context's stream
+        saved[p] = cs[p]->stream;
+        saved_prof[p] = cs[p]->prof_on;
+        cs[p]->stream = st;
+    }
+    std::vector<FitProb> fp(np);
+    void *host_u = nullptr, *host_g = nullptr, *dev_u = nullptr, *dev_g = nullptr, *dev_aux = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int rc = GLM_OK;
+    auto done = [&](int r) {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cudaFree(dev_u);
+        cudaFree(dev_g);
+        cudaFree(dev_aux);
+        std::free(host_u);
+        std::free(host_g);
+        cudaStreamSynchronize(st);
+        for (int p = 0; p < np; ++p) {
+            cs[p]->stream = saved[p];
+            cs[p]->prof_on = saved_prof[p];
+        }
+        cudaStreamDestroy(st);
+        return r;
+    };
+    for (int p = 0; p < np && !rc; ++p) rc = fit_setup(cs[p], o, W[p], b[p], &fp[p]);
+    if (rc) return done(rc);
+    // batch descriptors, the per-problem count pointers and the gathered counts
+    std::vector<float*> W32(np), b32(np);
+    std::vector<int32_t*> rows(np);
+    std::vector<const int32_t*> mdev(np);
+    std::vector<const int32_t*> st_src(np);
+    std::vector<int32_t> nrows(np);
+    for (int p = 0; p < np; ++p) {
+        W32[p] = fp[p].W32;
+        b32[p] = fp[p].b32;
+        rows[p] = fp[p].eval_rows;
+        mdev[p] = fp[p].F.counters + 3;  // set by fit_compact_kernel
+        st_src[p] = fp[p].F.status;
+        nrows[p] = fp[p].F.n;
+    }
+    const size_t bb = tc_batch_bytes();
+    host_u = std::malloc(bb);
+    host_g = std::malloc(bb);
+    if (!host_u || !host_g) return done(set_error(c0, GLM_ERR_OOM, "host memory"));
+    if ((rc = tc_batch_fill(cs, np, W32.data(), b32.data(), rows.data(), mdev.data(), host_u, host_g)))
+        return done(set_error(c0, rc, "bad batch"));
+    const size_t aux = sizeof(int32_t*) * np + 2 * sizeof(int) * np;
+    if ((rc = ck(c0, cudaMalloc(&dev_u, bb))) || (rc = ck(c0, cudaMalloc(&dev_g, bb))) ||
+        (rc = ck(c0, cudaMalloc(&dev_aux, aux))))
+        return done(rc);
+    const int32_t** d_src = static_cast<const int32_t**>(dev_aux);
+    int32_t* d_n = reinterpret_cast<int32_t*>(d_src + np);
+    int* d_cnt = d_n + np;
+    if ((rc = ck(c0, cudaMemcpy(dev_u, host_u, bb, cudaMemcpyHostToDevice))) ||
+        (rc = ck(c0, cudaMemcpy(dev_g, host_g, bb, cudaMemcpyHostToDevice))) ||
+        (rc = ck(c0, cudaMemcpy(d_src, st_src.data(), sizeof(int32_t*) * np, cudaMemcpyHostToDevice))) ||
+        (rc = ck(c0, cudaMemcpy(d_n, nrows.data(), sizeof(int32_t) * np, cudaMemcpyHostToDevice))))
+        return done(rc);
+    // the batched E X^T launch is tuned as a whole (row tile and splits), then the problems start
+    if ((rc = tc_autotune_batch(cs, np, dev_g, host_g))) return done(set_error(c0, rc, "batch autotune failed"));
+    for (int p = 0; p < np && !rc; ++p) rc = fit_start(fp[p], o);
+    if (rc) return done(rc);
+    if ((rc = ck(c0, cudaStreamSynchronize(st)))) return done(rc);
+    for (int p = 0; p < np && !rc; ++p) rc = eval_status(cs[p]);
+    if (rc) return done(rc);
+
+    // one iteration, recorded once
+    int64_t launches = 0;
+    auto enqueue_iteration = [&]() -> int {
+        int r;
+        for (int p = 0; p < np; ++p) {
+            FitState& F = fp[p].F;
+            if ((r = ck(c0, cudaMemsetAsync(F.counters, 0, 3 * sizeof(int), st)))) return r;
+            fit_direction_kernel<<<F.n, FT, 0, st>>>(F);
+            ++launches;
+        }
+        for (int round = 0; round < GRAPH_ROUNDS; ++round) {
+            for (int p = 0; p < np; ++p) {
+                FitState& F = fp[p].F;
+                fit_trial_kernel<<<F.n, FT, 0, st>>>(F, fp[p].W32, fp[p].b32);
+                fit_compact_kernel<<<1, 1024, 0, st>>>(F, fp[p].eval_rows);
+                launches += 2;
+            }
+            if ((r = ck(c0, launch_tc_u_batch(cs, np, dev_u, W32.data(), b32.data(), rows.data(), mdev.data()))))
+                return r;
+            launches += 2 * np + 1;
+            for (int p = 0; p < np; ++p) {
+                glm_ctx* c = cs[p];
+                FitState& F = fp[p].F;
+                if ((r = ck(c, launch_reduce(c, fp[p].W32, fp[p].b32, fp[p].Lr, nullptr, nullptr, false,
+                                             c->pb.Tpad / tc_tile_t(), tc_nsplit(c)))))
+                    return r;
+                fit_armijo_kernel<<<(F.n + 255) / 256, 256, 0, st>>>(F, fp[p].Lr, o->c1, o->max_halvings);
+                launches += 2;
+                // a non-finite trial only fails the Armijo test
+                if ((r = ck(c, reset_flags(c)))) return r;
+                fp[p].evals++;
+            }
+        }
+        for (int p = 0; p < np; ++p) {
+            fit_commit_kernel<<<fp[p].F.n, FT, 0, st>>>(fp[p].F);
+            ++launches;
+        }
+        if ((r = ck(c0, launch_tc_grad_batch(c0, dev_g)))) return r;
+        ++launches;
+        for (int p = 0; p < np; ++p) {
+            glm_ctx* c = cs[p];
+            if ((r = ck(c, launch_reduce(c, fp[p].W32, fp[p].b32, fp[p].Lr, fp[p].G, fp[p].gb, true,
+                                         c->pb.Tpad / tc_tile_t(), tc_nsplit(c)))))
+                return r;
+            fit_update_kernel<<<fp[p].F.n, FT, 0, st>>>(fp[p].F, fp[p].Lr, fp[p].G, fp[p].gb, o->eta, o->max_iter);
+            launches += 3;
+            fp[p].grads++;
+            fp[p].iters++;
+        }
+        count_active_kernel<<<np, 256, 0, st>>>(d_src, d_n, d_cnt);
+        ++launches;
+        return GLM_OK;
+    };
+    for (int p = 0; p < np; ++p) cs[p]->prof_on = false;  // no event records inside the graph
+    // attributes and a first pass outside capture
+    if ((rc = enqueue_iteration())) return done(rc);
+    const int64_t per_iteration = launches;
+    std::vector<int> host_cnt(np, 0);
+    auto read_counts = [&]() -> int {
+        int r;
+        if ((r = ck(c0, cudaMemcpyAsync(host_cnt.data(), d_cnt, sizeof(int) * np, cudaMemcpyDeviceToHost, st))))
+            return r;
+        if ((r = ck(c0, cudaStreamSynchronize(st)))) return r;
+        for (int p = 0; p < np; ++p)
+            if ((r = eval_status(cs[p]))) return r;
+        return GLM_OK;
+    };
+    if ((rc = read_counts())) return done(rc);
+    if ((rc = ck(c0, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)))) return done(rc);
+    const int cap_rc = enqueue_iteration();
+    cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    if (cap_rc) return done(cap_rc);
+    if ((rc = ck(c0, ce)) || (rc = ck(c0, cudaGraphInstantiate(&exec, graph, 0)))) return done(rc);
+    // the recorded iteration also counted itself once: undo that
+    for (int p = 0; p < np; ++p) {
+        fp[p].iters--;
+        fp[p].grads--;
+        fp[p].evals -= GRAPH_ROUNDS;
+    }
+    int iter = 1;
+    const int max_iter = o->max_iter + o->max_halvings;  // searches may run across iterations
+    while (iter < max_iter) {
+        bool any = false;
+        for (int p = 0; p < np; ++p) any |= host_cnt[p] > 0;
+        if (!any) break;
+        if ((rc = ck(c0, cudaGraphLaunch(exec, st)))) return done(rc);
+        for (int p = 0; p < np; ++p) {
+            fp[p].iters++;
+            fp[p].grads++;
+            fp[p].evals += GRAPH_ROUNDS;
+        }
+        c0->launches += per_iteration;
+        ++iter;
+        if ((rc = read_counts())) return done(rc);
+    }
+    for (int p = 0; p < np; ++p) cs[p]->prof_on = saved_prof[p];
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    int worst = GLM_OK;
+    for (int p = 0; p < np; ++p) {
+        const int r = fit_end(fp[p], row_status ? row_status[p] : nullptr, reps ? &reps[p] : nullptr, secs);
+        if (r < 0) return done(r);
+        if (r > worst) worst = r;
+    }
+    return done(worst);
 }
 
 }  // namespace glm

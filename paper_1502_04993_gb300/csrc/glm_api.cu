@@ -50,6 +50,8 @@ void free_all(glm_ctx* c) {
     c->buf = Buffers();
     c->has_problem = false;
     c->c_ready = false;
+    c->g_mode = 1;
+    c->g_nsplit = 0;
 }
 
 // Device allocation charged against the workspace cap.
@@ -177,8 +179,9 @@ int do_prepare(glm_ctx* c) {
     GLM_RUN("carry", 2, launch_carry(c));
     GLM_RUN("filter_scan", 1, launch_filter_cache(c));
     // The spike term C (the W-independent part of dL/dW, Eq. 12): a gather of X at the spike bins for the
-    // plain FP32 form, S (X_hi + X_lo)^T on the tensor cores for the 16-bit forms.  The plain form also
-    // takes the spike part of L from it; the 16-bit forms take that from U at the spike bins.
+    // plain FP32 form, S (X_hi + X_lo)^T on the tensor cores for the 16-bit forms.  The spike part of L
+    // comes from U at the spike bins in the U-product epilogue instead (its rounding then cancels against
+    // that of the integral part).
     int rc = ensure_spike_term(c);
     if (rc) return rc;
     // pw is a pageable host buffer: the copy above has been staged before cudaMemcpyAsync returned
@@ -222,13 +225,13 @@ int set_error(glm_ctx* c, int code, const char* msg) { return fail(c, code, msg)
 // Queue one evaluation at (W, b) on the context's stream; no synchronisation.  With reuse_u the U
 // product is skipped: E and the per-tile sums must already hold the values at this (W, b).
 int eval_enqueue(glm_ctx* c, const float* W, const float* b, double* L_rows, double* G, double* gb, bool want_grad,
-                 bool reuse_u, bool tau) {
+                 bool reuse_u, bool tau, const int32_t* rows, int32_t m) {
     const bool tensor = c->pb.prec != GLM_PREC_F32;
     if (!reuse_u) {
         if (tensor)
-            GLM_RUN("u_epilogue", 3, launch_tc_u_epilogue(c, W, b, tau));
+            GLM_RUN("u_epilogue", 3, launch_tc_u_epilogue(c, W, b, tau, rows, m));
         else
-            GLM_RUN("u_epilogue", 2, launch_simt_u_epilogue(c, W, b));
+            GLM_RUN("u_epilogue", 2, launch_simt_u_epilogue(c, W, b, rows, m));
     }
     if (want_grad) {
         if (tensor)
@@ -394,10 +397,10 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
         (rc = ws_alloc(c, &B.X, (size_t)n * P.Tpad * esz)) ||
         (rc = ws_alloc(c, &B.E, (size_t)n * P.Tpad * esz)) ||
         (rc = ws_alloc_t(c, &B.part_e, (size_t)n * (P.Tpad / (tensor ? tc_tile_t() : simt_tile_t())))) ||
-        (rc = ws_alloc_t(c, &B.part_g, nn * (tensor ? tc_nsplit(c) : grad_nsplit(c)))) ||
+        (rc = ws_alloc_t(c, &B.part_g, nn * (tensor ? tc_nsplit_max(c) : grad_nsplit(c)))) ||
         (rc = ws_alloc_t(c, &B.flags, 4)) || (rc = ws_alloc_t(c, &B.Lrows, n)) || (rc = ws_alloc_t(c, &B.scal, 8)) || (rc = ws_alloc_t(c, &B.eb, n)) ||
         (tensor && (rc = ws_alloc(c, &B.Xlo, (size_t)P.n * P.Tpad * 2))) ||
-        (tensor && (rc = ws_alloc_t(c, &B.part_s, (size_t)n * (P.Tpad / tc_tile_t())))) ||
+        (rc = ws_alloc_t(c, &B.part_s, (size_t)n * (P.Tpad / (tensor ? tc_tile_t() : simt_tile_t())))) ||
         (tensor && (rc = ws_alloc(c, &B.Wsplit, 2 * (size_t)n * B.ldn * 2)))) {
         free_all(c);
         return rc;
@@ -530,6 +533,42 @@ int glm_fit(glm_ctx* c, const glm_fit_opts_t* opts, float* W, float* b, int8_t* 
         return fail(c, GLM_ERR_INVALID_ARG, "bad fit options");
     DeviceGuard g(c->device);
     return glm::fit_run(c, &o, W, b, row_status, rep);
+}
+
+int glm_autotune(glm_ctx* c, glm_tune_report_t* rep) {
+    if (!c) return GLM_ERR_INVALID_ARG;
+    if (!c->has_problem) return fail(c, GLM_ERR_NO_PROBLEM, "no problem set");
+    if (c->pb.prec == GLM_PREC_F32) return fail(c, GLM_ERR_UNSUPPORTED, "the autotuner covers the tensor-core products");
+    if (rep) std::memset(rep, 0, sizeof(*rep));
+    DeviceGuard g(c->device);
+    const int rc = glm::tc_autotune(c, rep);
+    return rc ? fail(c, rc, "autotune failed") : GLM_OK;
+}
+
+int glm_fit_batch(glm_ctx* const* cs, int32_t np, const glm_fit_opts_t* opts, float* const* W, float* const* b,
+                  int8_t* const* row_status, glm_fit_report_t* reps) {
+    if (!cs || np < 1 || np > GLM_FIT_BATCH_MAX || !W || !b) return GLM_ERR_INVALID_ARG;
+    glm_ctx* c0 = cs[0];
+    if (!c0) return GLM_ERR_INVALID_ARG;
+    for (int32_t p = 0; p < np; ++p) {
+        glm_ctx* c = cs[p];
+        if (!c || !W[p] || !b[p]) return fail(c0, GLM_ERR_INVALID_ARG, "null context or output");
+        if (!c->has_problem) return fail(c0, GLM_ERR_NO_PROBLEM, "a context has no problem set");
+        if (c->device != c0->device) return fail(c0, GLM_ERR_INVALID_ARG, "contexts on different devices");
+        if (c->pb.prec != c0->pb.prec) return fail(c0, GLM_ERR_INVALID_ARG, "contexts with different precisions");
+        for (int32_t q = 0; q < p; ++q)
+            if (cs[q] == c) return fail(c0, GLM_ERR_INVALID_ARG, "a context appears twice");
+    }
+    if (c0->pb.prec == GLM_PREC_F32)
+        return fail(c0, GLM_ERR_UNSUPPORTED, "glm_fit_batch needs a tensor-core precision (fit FP32 problems one by one)");
+    glm_fit_opts_t o;
+    glm_fit_default_opts(&o);
+    if (opts) o = *opts;
+    if ((o.method != GLM_FIT_LBFGS && o.method != GLM_FIT_GA) || o.m < 1 || o.m > 32 || o.max_iter < 0 ||
+        !(o.eta >= 0) || !(o.c1 > 0 && o.c1 < 1) || o.max_halvings < 1 || std::isnan(o.gain_floor))
+        return fail(c0, GLM_ERR_INVALID_ARG, "bad fit options");
+    DeviceGuard g(c0->device);
+    return glm::fit_run_batch(cs, np, &o, W, b, row_status, reps);
 }
 
 }  // extern "C"

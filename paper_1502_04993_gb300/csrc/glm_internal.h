@@ -25,7 +25,7 @@ struct ScanConsts {
     float pm_hi[9], pm_lo[9];    // a^m,          m = 0..8
     float ps_hi[5], ps_lo[5];    // a^(8*2^d),    d = 0..4   (warp scan strides)
     float pl_hi[32], pl_lo[32];  // a^(8*l),      l = 0..31  (lane offsets)
-    // derivatives in a, for the joint scan of X and Y = dX/da (the tau derivative)
+    float pr[8];                 // a^k rounded once to FP32, k = 0..7 (a lane's own spikes)
 };
 
 struct Problem {
@@ -53,7 +53,7 @@ struct Buffers {
     int64_t ldn = 0;              // leading dim of the W parts (n rounded up to 64)
     void* E = nullptr;            // F32: float [n][Tpad] dt exp(U); 16-bit: the same, bin-blocked
     double* part_e = nullptr;     // [n][ntile_t]  per-(row, bin tile) sums of exp(U)
-    double* part_s = nullptr;     // 16-bit: [n][ntile_t] per-(row, bin tile) sums of U - b over the spike bins
+    double* part_s = nullptr;     // [n][ntile_t] per-(row, bin tile) sums of U - b over the spike bins
     float* part_g = nullptr;      // [nsplit][n][n] FP32 partial sums of E X^T
     void* Wsplit = nullptr;       // 16-bit: hi and lo parts of W, [2][n][ldn]
     int* flags = nullptr;         // [4] device error flags
@@ -82,6 +82,8 @@ struct glm_ctx {
     CUtensorMap tmap[7];  // tensor-core path: W_hi, W_lo, X_hi, X_lo (N-major), E, X_hi, X_lo (K-major)
     bool has_problem = false;
     bool c_ready = false;  // C holds the spike term of the current problem and tau
+    int g_mode = 1;        // E X^T row tile: 1 = 256 rows, 2 = 128 rows (autotuner)
+    int g_nsplit = 0;      // E X^T bin splits (0: the default for g_mode)
     std::string last_error;
     // tracing: event pairs per launched kernel group while profiling is on
     bool prof_on = false;
@@ -113,22 +115,39 @@ cudaError_t launch_spike_term(glm_ctx* c, double* out);
 cudaError_t launch_tau_rows(glm_ctx* c, double* rows);
 cudaError_t launch_sum_splits(glm_ctx* c, int nsplit, double* C, bool accumulate);
 cudaError_t launch_tc_spike_term(glm_ctx* c);
-cudaError_t launch_simt_u_epilogue(glm_ctx* c, const float* W, const float* b);
+// rows: evaluated rows (null: all n), m of them; outputs land at the rows' own positions
+cudaError_t launch_simt_u_epilogue(glm_ctx* c, const float* W, const float* b, const int32_t* rows = nullptr,
+                                   int32_t m = 0);
 cudaError_t launch_simt_grad(glm_ctx* c);
 cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_rows, double* G, double* gb,
                           bool want_grad, int64_t ntile, int nsplit);
 void launch_exp_bias(glm_ctx* c, const float* b);
 int set_error(glm_ctx* c, int code, const char* msg);
+// One evaluation at (W, b).  With rows (m of them) only those rows' U product, rates and per-tile sums
+// are formed (their L_rows entries are valid; other rows' entries are not).
 int eval_enqueue(glm_ctx* c, const float* W, const float* b, double* L_rows, double* G, double* gb, bool want_grad,
-                 bool reuse_u, bool tau = false);
+                 bool reuse_u, bool tau = false, const int32_t* rows = nullptr, int32_t m = 0);
 int eval_status(glm_ctx* c);
 cudaError_t reset_flags(glm_ctx* c);
 int ws_alloc_bytes(glm_ctx* c, void** p, size_t bytes);
 int fit_run(glm_ctx* c, const glm_fit_opts_t* o, float* W, float* b, int8_t* row_status, glm_fit_report_t* rep);
+int fit_run_batch(glm_ctx* const* cs, int np, const glm_fit_opts_t* o, float* const* W, float* const* b,
+                  int8_t* const* row_status, glm_fit_report_t* reps);
 cudaError_t tc_prepare_maps(glm_ctx* c);
-cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, bool tau);
+cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, bool tau, const int32_t* rows = nullptr,
+                                 int32_t m = 0);
 cudaError_t launch_tc_grad(glm_ctx* c);
 int tc_nsplit(const glm_ctx* c);
+int tc_nsplit_max(const glm_ctx* c);
+int tc_autotune(glm_ctx* c, glm_tune_report_t* rep);
+int tc_autotune_batch(glm_ctx* const* cs, int np, void* dev_g, void* host_g);
+// several problems per launch (glm_fit_batch)
+size_t tc_batch_bytes();
+int tc_batch_fill(glm_ctx* const* cs, int np, float* const* W32, float* const* b32, int32_t* const* rows,
+                  const int32_t* const* m_dev, void* host_u, void* host_g);
+cudaError_t launch_tc_u_batch(glm_ctx* const* cs, int np, const void* dev_u, float* const* W32, float* const* b32,
+                              int32_t* const* rows, const int32_t* const* m_dev);
+cudaError_t launch_tc_grad_batch(glm_ctx* c0, const void* dev_g);
 int tc_tile_t();
 cudaError_t launch_total(glm_ctx* c, const double* L_rows, double* out1);
 

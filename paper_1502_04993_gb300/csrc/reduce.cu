@@ -1,6 +1,6 @@
 // Step a7: FP64 reductions in a fixed order (bitwise reproducible).
-//   L_i   = sum_{t in sp(i)} U_i[t] - dt sum_t exp(U_i[t])        (Eq. 7), with the spike part
-//           q_i b_i + sum_j W_ij C_ij (plain FP32 form) or q_i b_i + sum_tiles (sum of U - b at spike bins)
+//   L_i   = sum_{t in sp(i)} U_i[t] - dt sum_t exp(U_i[t])        (Eq. 7), the spike part as
+//           q_i b_i + sum over tiles of (sum of U - b at the row's spike bins), from the U-product epilogue
 //   dL/db_i = q_i - dt sum_t exp(U_i[t])                         (Eq. 12, j = 0)
 //   dL/dW_ij = C_ij - sum_s P_s[i][j],  P_s = sum_{t in split s} dt exp(U_i[t]) X_j[t]   (Eq. 12)
 //   L = sum_i L_i                                                (Eq. 1)
@@ -22,8 +22,8 @@ struct ReduceArgs {
     double dt;
     const float* W;
     const float* b;
-    const double* C;       // spike term (the plain form's spike part of L; dL/dW in both forms)
-    const double* part_s;  // tensor-core forms: [n][ntile] sums of U - b at the spike bins
+    const double* C;       // spike term (dL/dW)
+    const double* part_s;  // [n][ntile] sums of U - b at the spike bins
     const double* qd;
     const double* part_e;  // [n][ntile]
     double* L_rows;
@@ -36,12 +36,8 @@ __global__ void reduce_rows_kernel(const __grid_constant__ ReduceArgs A) {
     const int lane = threadIdx.x & 31;
     if (i >= A.n) return;
     double spk = 0.0;
-    if (A.part_s) {
-        const double* ps = A.part_s + (int64_t)i * A.ntile;
-        for (int64_t t = lane; t < A.ntile; t += 32) spk += ps[t];
-    } else {
-        for (int32_t j = lane; j < A.n; j += 32) spk += (double)A.W[(int64_t)i * A.n + j] * A.C[(int64_t)i * A.n + j];
-    }
+    const double* ps = A.part_s + (int64_t)i * A.ntile;
+    for (int64_t t = lane; t < A.ntile; t += 32) spk += ps[t];
     double integ = 0.0;
     const double* pe = A.part_e + (int64_t)i * A.ntile;
     for (int64_t t = lane; t < A.ntile; t += 32) integ += pe[t];
@@ -157,9 +153,8 @@ cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_
     A.dt = P.dt;
     A.W = W;
     A.b = b;
-    const bool tensor = P.prec != GLM_PREC_F32;
     A.C = c->buf.C;
-    A.part_s = tensor ? c->buf.part_s : nullptr;  // tensor-core forms: spike part of L from U itself
+    A.part_s = c->buf.part_s;
     A.qd = c->buf.qd;
     A.part_e = c->buf.part_e;
     A.L_rows = L_rows;

@@ -43,7 +43,9 @@ __device__ __forceinline__ uint32_t seg_bits(const int32_t* __restrict__ bins, i
 
 // Scan of one segment.  x_seg = X[t0] (all lanes), bits8 = this lane's spike bits, (pl_hi, pl_lo) =
 // a^(8 lane).  On return out[m] = X[t0 + 8 lane + m]; the result is X[t0 + 256] (all lanes).
-//   local part:   z_0 = 0, z_{m+1} = a z_m + S[t_lane + m]   (this lane's own spikes)
+//   local part:   z_m = sum over this lane's spikes j < m of a^(m-1-j), each power rounded once.  (The
+//                 recursion z_{m+1} = a z_m + S rounds the same chain 1, a, a^2, ... after every spike
+//                 and so biases X by ~0.6 ulp; the direct powers do not.)
 //   lane start:   X[t_lane] = a^(8 lane) x_seg + sum_{k < lane} a^(8 (lane - 1 - k)) z_8(k)
 //                 (Kogge-Stone scan of the affine recurrence with constant multiplier a^8)
 //   values:       X[t_lane + m] = a^m X[t_lane] + z_m
@@ -52,9 +54,15 @@ __device__ __forceinline__ float seg_scan(const ScanConsts& K, float x_seg, uint
     float z[8];
     float zz = 0.f;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
-        z[m] = zz;
-        zz = mul2(K.a_hi, K.a_lo, zz, (float)((bits8 >> m) & 1u));
+    for (int m = 0; m < 8; ++m) z[m] = 0.f;
+    uint32_t bb = bits8;
+    while (bb) {  // usually no spike, rarely more than one, in a lane's 8 bins
+        const int j = __ffs(bb) - 1;
+        bb &= bb - 1;
+#pragma unroll
+        for (int m = 1; m < 8; ++m)
+            if (m > j) z[m] += K.pr[m - 1 - j];
+        zz += K.pr[7 - j];
     }
     float v = zz;
 #pragma unroll

@@ -1,6 +1,7 @@
 // The plain FP32 form of the two contractions (CUDA cores, no tensor cores):
 //   step a3/a4:  U = b 1^T + W X (Eq. 3) with the link applied in the epilogue (Eq. 5):
-//                E[i][t] = dt exp(U_i[t]) stored FP32, per (bin tile, row) FP64 sums of exp(U)
+//                E[i][t] = dt exp(U_i[t]) stored FP32, per (bin tile, row) FP64 sums of exp(U) and of
+//                U - b over the row's spike bins (the spike-time term of Eq. 7)
 //   step a5:     P_s = E X^T over a split s of the bins (FP32, two-level accumulation)
 // 128 x 128 output tiles, 256 threads, 8 x 8 outputs per thread, operands staged in shared memory.
 #include <cmath>
@@ -27,9 +28,20 @@ struct SimtUArgs {
     float* E;         // [n][Tpad]
     double* part_e;   // [n][ntile]
     int* flags;
+    const int32_t* rows;  // evaluated rows (null: all n); tile row l is row rows[l] for l < m
+    int32_t m;
+    const int64_t* offs;  // spikes (CSR) and each row's first spike index per 256-bin segment
+    const int32_t* bins;
+    const int32_t* seg_first;
+    int64_t nseg;
+    double* part_s;       // [n][ntile] sum of U - b over the row's spike bins in the tile
 };
 
-// U tile rows i0..i0+127, bins t0..t0+127.  A = W (row-major, K contiguous), B = X (K x N, N contiguous).
+__device__ __forceinline__ int32_t row_of(const SimtUArgs& A, int32_t l) {
+    return l < A.m ? (A.rows ? A.rows[l] : l) : A.n;
+}
+
+// U tile rows i0..i0+127 (of the evaluated rows), bins t0..t0+127.  A = W (row-major, K contiguous), B = X (K x N, N contiguous).
 __global__ void __launch_bounds__(ST) simt_u_kernel(const __grid_constant__ SimtUArgs A) {
     __shared__ __align__(16) float As[2][SK][SB];
     __shared__ __align__(16) float Bs[2][SK][SB];
@@ -50,7 +62,7 @@ __global__ void __launch_bounds__(ST) simt_u_kernel(const __grid_constant__ Simt
     auto load = [&](int k0) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int32_t i = i0 + a_row + 64 * h;
+            const int32_t i = row_of(A, i0 + a_row + 64 * h);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int32_t k = k0 + a_col + q;
@@ -99,7 +111,7 @@ __global__ void __launch_bounds__(ST) simt_u_kernel(const __grid_constant__ Simt
     bool bad = false;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-        const int32_t i = i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4));
+        const int32_t i = row_of(A, i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4)));
         const double ebi = (i < n) ? A.eb[i] : 0.0;
         const float dteb = (float)(A.dt * ebi);
         float msum = 0.f;
@@ -118,14 +130,35 @@ __global__ void __launch_bounds__(ST) simt_u_kernel(const __grid_constant__ Simt
             ev[c] = valid ? fmaf(dteb, m, dteb) : 0.f;
         }
         double rs = ebi * ((double)cnt + (double)msum);
+        // spike bins of row i in this tile (half of a 256-bin segment): this thread's share of sum (U - b)
+        float spv = 0.f;
+        if (i < n) {
+            const int64_t s = t0 / SEG, o0 = A.offs[i];
+            const int64_t ke = (s + 1 < A.nseg) ? o0 + A.seg_first[(int64_t)i * A.nseg + s + 1] : A.offs[i + 1];
+            for (int64_t k = o0 + A.seg_first[(int64_t)i * A.nseg + s]; k < ke; ++k) {
+                const int col = (int)(A.bins[k] - t0);
+                if (col < 0) continue;
+                if (col >= SB) break;
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (col == (c < 4 ? tx * 4 + c : 64 + tx * 4 + (c - 4))) spv += acc[r][c];
+            }
+        }
+        double sp = (double)spv;
         // the 16 threads with the same ty share these rows
 #pragma unroll
-        for (int off = 8; off >= 1; off >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, off);
+        for (int off = 8; off >= 1; off >>= 1) {
+            rs += __shfl_xor_sync(0xffffffffu, rs, off);
+            sp += __shfl_xor_sync(0xffffffffu, sp, off);
+        }
         if (i < n) {
             float* dst = A.E + (int64_t)i * A.Tpad + t0;
             *reinterpret_cast<float4*>(dst + tx * 4) = make_float4(ev[0], ev[1], ev[2], ev[3]);
             *reinterpret_cast<float4*>(dst + 64 + tx * 4) = make_float4(ev[4], ev[5], ev[6], ev[7]);
-            if (tx == 0) A.part_e[(int64_t)i * gridDim.x + blockIdx.x] = rs;
+            if (tx == 0) {
+                A.part_e[(int64_t)i * gridDim.x + blockIdx.x] = rs;
+                A.part_s[(int64_t)i * gridDim.x + blockIdx.x] = sp;
+            }
         }
     }
     if (bad) atomicOr(A.flags, 1);
@@ -253,7 +286,7 @@ void launch_exp_bias(glm_ctx* c, const float* b) {
     exp_bias_kernel<<<(c->pb.n + 255) / 256, 256, 0, c->stream>>>(c->pb.n, b, c->buf.eb, c->buf.flags);
 }
 
-cudaError_t launch_simt_u_epilogue(glm_ctx* c, const float* W, const float* b) {
+cudaError_t launch_simt_u_epilogue(glm_ctx* c, const float* W, const float* b, const int32_t* rows, int32_t m) {
     const Problem& P = c->pb;
     launch_exp_bias(c, b);
     SimtUArgs A;
@@ -268,7 +301,14 @@ cudaError_t launch_simt_u_epilogue(glm_ctx* c, const float* W, const float* b) {
     A.E = reinterpret_cast<float*>(c->buf.E);
     A.part_e = c->buf.part_e;
     A.flags = c->buf.flags;
-    dim3 grid((unsigned)(P.Tpad / SB), (P.n + SB - 1) / SB);
+    A.rows = rows;
+    A.m = rows ? m : P.n;
+    A.offs = c->buf.offs;
+    A.bins = c->buf.bins;
+    A.seg_first = c->buf.seg_first;
+    A.nseg = P.nseg;
+    A.part_s = c->buf.part_s;
+    dim3 grid((unsigned)(P.Tpad / SB), (A.m + SB - 1) / SB);
     simt_u_kernel<<<grid, ST, 0, c->stream>>>(A);
     return cudaGetLastError();
 }

@@ -27,6 +27,10 @@
 #include <cudaTypedefs.h>
 
 #include <cmath>
+#include <cstring>
+#include <mutex>
+#include <utility>
+#include <vector>
 #include <type_traits>
 
 #include "glm_internal.h"
@@ -38,6 +42,7 @@ namespace {
 
 constexpr int NUM_THREADS = 192;
 constexpr int SP_REG = 12;  // spike bins per (row, 256-bin tile) held in registers by the epilogue
+constexpr int TUNE_UPM_MAX = 8;  // most units per SM the autotuner tries for E X^T
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int BN = 256;
 static_assert(BN == SEG, "a U-product tile is one 256-bin segment of the spike index");
@@ -80,6 +85,24 @@ struct Cfg<1> {
     static constexpr uint32_t B_BYTES = BN * BK * 2;
 };
 
+template <>
+struct Cfg<2> {                               // E X^T with 128-row tiles (small N), double-buffered accumulators
+    static constexpr int BM = 128;
+    static constexpr int BK = 64;
+    static constexpr int NA = 1, NB = 1;      // E rows m0.. ; X
+    static constexpr int STAGES = 4;
+    static constexpr int NBUF = 2;
+    static constexpr uint32_t SWZ = 2;
+    static constexpr uint32_t SBO = 8 * 128;
+    static constexpr uint32_t A_KSTEP = 2;
+    static constexpr uint32_t B_SWZ = SWZ;
+    static constexpr uint32_t B_SBO = SBO;
+    static constexpr uint32_t B_LBO = 16;
+    static constexpr uint32_t B_KSTEP = 2;
+    static constexpr uint32_t A_BYTES = 128 * BK * 2;
+    static constexpr uint32_t B_BYTES = BN * BK * 2;
+};
+
 template <int MODE>
 struct Layout {
     using C = Cfg<MODE>;
@@ -107,6 +130,8 @@ struct TcArgs {
     const int32_t* bins;
     const int32_t* seg_first;
     int64_t nseg;
+    const int32_t* rows;  // MODE 0: evaluated rows (null: all n); tile row l is row rows[l] for l < m_rows
+    int32_t m_rows;
     void* E;
     double* part_e;
     int64_t ntile;
@@ -120,12 +145,23 @@ struct Unit {
     int64_t kb0, kb1, kstep, split;
 };
 
+// Several independent problems in one launch (glm_fit_batch): their units are laid end to end.  MODE 0
+// takes each problem's count of evaluated rows from m_dev when given (set on the device by the fit).
+constexpr int MAX_BATCH = 32;
+struct TcBatch {
+    int32_t nprob;
+    const int32_t* m_dev[MAX_BATCH];
+    TcArgs args[MAX_BATCH];
+    CUtensorMap maps[MAX_BATCH][4];  // A0, A1, B0, B1 of each problem
+};
+
+// unit u of a problem with mt row tiles
 template <int MODE>
-__device__ __forceinline__ Unit decode(const TcArgs& A, int64_t u) {
+__device__ __forceinline__ Unit decode(const TcArgs& A, int64_t u, int32_t mt) {
     Unit r;
     if (MODE == 0) {
-        r.m0 = (int32_t)(u % A.mt) * Cfg<0>::BM;
-        r.n0 = (int32_t)(u / A.mt) * BN;
+        r.m0 = (int32_t)(u % mt) * Cfg<0>::BM;
+        r.n0 = (int32_t)(u / mt) * BN;
         r.kb0 = 0;
         r.kb1 = A.kb_per_unit;
         r.kstep = 1;
@@ -134,7 +170,7 @@ __device__ __forceinline__ Unit decode(const TcArgs& A, int64_t u) {
         const int64_t tiles = (int64_t)A.mt * A.nt;
         const int64_t tile = u % tiles;
         r.split = u / tiles;
-        r.m0 = (int32_t)(tile % A.mt) * Cfg<1>::BM;
+        r.m0 = (int32_t)(tile % A.mt) * (MODE == 2 ? 128 : 256);
         r.n0 = (int32_t)(tile / A.mt) * BN;
         // the splits interleave: split s takes k-steps s, s + nsplit, s + 2 nsplit, ...  All blocks then
         // stream the same narrow band of bins, which stays in L2 while the 16 tiles of each split reuse it.
@@ -174,11 +210,11 @@ __device__ __forceinline__ uint32_t pack16<__half>(float lo, float hi) {
 // TAU (MODE 0 only): the epilogue also emits, per (row, tile), the partial sums that give dL/dtau.  With v = (W X)_i[t] = U_i[t] - b_i, Z_i[t] = a Z_i[t-1] + v[t-1] (Z = W dX/da), the
 // tile's local Z_loc starts at 0 at its first bin t0, and Z[t] = a^(t-t0) Z[t0] + Z_loc[t]; a per-row
 // combine (reduce.cu) chains the tiles.
-template <int MODE, typename T16, bool TAU>
+template <int MODE, typename T16, bool TAU, bool BATCH>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
                    const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1,
-                   const __grid_constant__ TcArgs A) {
+                   const __grid_constant__ TcArgs Ag, const TcBatch* __restrict__ batch) {
     using C = Cfg<MODE>;
     using L = Layout<MODE>;
     extern __shared__ uint8_t smem_raw[];
@@ -190,9 +226,31 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     uint64_t* done = tempty + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    // per problem: first unit, row tiles, evaluated rows (one problem unless BATCH)
+    __shared__ int64_t s_ubeg[MAX_BATCH + 1];
+    __shared__ int32_t s_mt[MAX_BATCH], s_m[MAX_BATCH];
+    __shared__ int s_np;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
+        const int np = BATCH ? batch->nprob : 1;
+        int64_t acc_units = 0;
+        for (int p = 0; p < np; ++p) {
+            const TcArgs& a = BATCH ? batch->args[p] : Ag;
+            int32_t m = a.m_rows, mt = a.mt;
+            int64_t units = a.units;
+            if (MODE == 0) {
+                if (BATCH && batch->m_dev[p]) m = *batch->m_dev[p];
+                mt = (m + Cfg<0>::BM - 1) / Cfg<0>::BM;
+                units = (int64_t)mt * a.nt;
+            }
+            s_ubeg[p] = acc_units;
+            s_mt[p] = mt;
+            s_m[p] = m;
+            acc_units += units;
+        }
+        s_ubeg[np] = acc_units;
+        s_np = np;
         for (int s = 0; s < C::STAGES; ++s) {
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
@@ -205,7 +263,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
-    if (warp == 0 && lane == 0) {
+    if (!BATCH && warp == 0 && lane == 0) {
         tc::prefetch_tensormap(&mapA0);
         tc::prefetch_tensormap(&mapA1);
         tc::prefetch_tensormap(&mapB0);
@@ -219,10 +277,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    const int64_t total_units = s_ubeg[s_np];
+    auto prob_of = [&](int64_t u) {
+        int p = 0;
+        while (u >= s_ubeg[p + 1]) ++p;
+        return p;
+    };
+    auto args_of = [&](int p) -> const TcArgs& { return BATCH ? batch->args[p] : Ag; };
+    auto map_of = [&](int p, int k) -> const CUtensorMap* {
+        if (BATCH) return &batch->maps[p][k];
+        return k == 0 ? &mapA0 : k == 1 ? &mapA1 : k == 2 ? &mapB0 : &mapB1;
+    };
 
     auto raise = [&]() {
         *abort_flag = 1;
-        atomicOr(A.flags + 1, 1);
+        atomicOr(Ag.flags + 1, 1);
     };
 
     if (warp == 0) {
@@ -233,10 +302,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             int issued_phase[C::STAGES];
             for (int s = 0; s < C::STAGES; ++s) issued_phase[s] = -1;
             bool ok = true;
-            for (int64_t u = blockIdx.x; u < A.units && ok; u += gridDim.x) {
-                const Unit w = decode<MODE>(A, u);
+            for (int64_t u = blockIdx.x; u < total_units && ok; u += gridDim.x) {
+                const int p = prob_of(u);
+                const TcArgs& A = args_of(p);
+                const Unit w = decode<MODE>(A, u - s_ubeg[p], s_mt[p]);
+                const CUtensorMap *mA0 = map_of(p, 0), *mA1 = map_of(p, 1), *mB0 = map_of(p, 2), *mB1 = map_of(p, 3);
                 for (int64_t kb = w.kb0; kb < w.kb1; kb += w.kstep) {
-                    if (!tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag, A.limit_ns)) {
+                    if (!tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag, Ag.limit_ns)) {
                         raise();
                         ok = false;
                         break;
@@ -245,16 +317,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     tc::mbar_arrive_expect_tx(&full[stage], L::STAGE_BYTES);
                     const int32_t kx = (int32_t)(kb * C::BK);
                     if (MODE == 0) {
-                        tc::tma_load_2d(sa, &mapA0, kx, w.m0, &full[stage]);
-                        tc::tma_load_2d(sa + C::A_BYTES, &mapA1, kx, w.m0, &full[stage]);
+                        tc::tma_load_2d(sa, mA0, kx, w.m0, &full[stage]);
+                        tc::tma_load_2d(sa + C::A_BYTES, mA1, kx, w.m0, &full[stage]);
                         // (bin in block, neuron = k, bin block): 4 blocks of 32 x 64
-                        tc::tma_load_3d(sa + 2 * C::A_BYTES, &mapB0, 0, kx, w.n0 / 64, &full[stage]);
-                        tc::tma_load_3d(sa + 2 * C::A_BYTES + C::B_BYTES, &mapB1, 0, kx, w.n0 / 64, &full[stage]);
+                        tc::tma_load_3d(sa + 2 * C::A_BYTES, mB0, 0, kx, w.n0 / 64, &full[stage]);
+                        tc::tma_load_3d(sa + 2 * C::A_BYTES + C::B_BYTES, mB1, 0, kx, w.n0 / 64, &full[stage]);
                     } else {
                         // (bin in block, neuron, bin block = k-step)
-                        tc::tma_load_3d(sa, &mapA0, 0, w.m0, (int32_t)kb, &full[stage]);
-                        tc::tma_load_3d(sa + C::A_BYTES, &mapA0, 0, w.m0 + 128, (int32_t)kb, &full[stage]);
-                        tc::tma_load_3d(sa + 2 * C::A_BYTES, &mapB0, 0, w.n0, (int32_t)kb, &full[stage]);
+                        tc::tma_load_3d(sa, mA0, 0, w.m0, (int32_t)kb, &full[stage]);
+                        if (C::NA == 2) tc::tma_load_3d(sa + C::A_BYTES, mA0, 0, w.m0 + 128, (int32_t)kb, &full[stage]);
+                        tc::tma_load_3d(sa + C::NA * C::A_BYTES, mB0, 0, w.n0, (int32_t)kb, &full[stage]);
                     }
                     issued_phase[stage] = (int)phase;
                     if (++stage == C::STAGES) {
@@ -266,7 +338,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             // drain: every issued copy has landed before the block may exit
             volatile int never = 0;
             for (int s = 0; s < C::STAGES; ++s)
-                if (issued_phase[s] >= 0) tc::mbar_wait(&full[s], (uint32_t)issued_phase[s], &never, A.limit_ns);
+                if (issued_phase[s] >= 0) tc::mbar_wait(&full[s], (uint32_t)issued_phase[s], &never, Ag.limit_ns);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -275,11 +347,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             uint32_t phase = 0;
             int it = 0;
             bool ok = true;
-            for (int64_t u = blockIdx.x; u < A.units && ok; u += gridDim.x, ++it) {
-                const Unit w = decode<MODE>(A, u);
+            for (int64_t u = blockIdx.x; u < total_units && ok; u += gridDim.x, ++it) {
+                const int p = prob_of(u);
+                const Unit w = decode<MODE>(args_of(p), u - s_ubeg[p], s_mt[p]);
                 const int buf = (C::NBUF == 2) ? (it & 1) : 0;
                 const uint32_t buf_phase = (uint32_t)((C::NBUF == 2 ? (it >> 1) : it) & 1);
-                if (!tc::mbar_wait(&tempty[buf], buf_phase ^ 1, abort_flag, A.limit_ns)) {
+                if (!tc::mbar_wait(&tempty[buf], buf_phase ^ 1, abort_flag, Ag.limit_ns)) {
                     raise();
                     break;
                 }
@@ -287,7 +360,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const uint32_t d0 = tmem_base + (uint32_t)(buf * BN);
                 const uint32_t d1 = tmem_base + (uint32_t)BN;  // MODE 1: second row half
                 for (int64_t kb = w.kb0; kb < w.kb1; kb += w.kstep) {
-                    if (!tc::mbar_wait(&full[stage], phase, abort_flag, A.limit_ns)) {
+                    if (!tc::mbar_wait(&full[stage], phase, abort_flag, Ag.limit_ns)) {
                         raise();
                         ok = false;
                         break;
@@ -296,19 +369,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     const uint32_t sa = tc::smem_u32(smem + stage * L::STAGE_BYTES);
                     const uint64_t da0 = smem_desc(sa, C::SWZ, C::SBO);
                     const uint64_t da1 = smem_desc(sa + C::A_BYTES, C::SWZ, C::SBO);
-                    const uint64_t db0 = smem_desc(sa + 2 * C::A_BYTES, C::B_SWZ, C::B_SBO, C::B_LBO);
-                    const uint64_t db1 = smem_desc(sa + 2 * C::A_BYTES + C::B_BYTES, C::B_SWZ, C::B_SBO, C::B_LBO);
+                    const uint64_t db0 = smem_desc(sa + C::NA * C::A_BYTES, C::B_SWZ, C::B_SBO, C::B_LBO);
+                    const uint64_t db1 = smem_desc(sa + C::NA * C::A_BYTES + C::B_BYTES, C::B_SWZ, C::B_SBO, C::B_LBO);
 #pragma unroll
                     for (int k = 0; k < C::BK / 16; ++k) {
                         const uint32_t acc = (kb == w.kb0 && k == 0) ? 0u : 1u;
                         const uint64_t ka = C::A_KSTEP * k, kb16 = C::B_KSTEP * k;
                         if (MODE == 0) {
-                            tc::mma_f16(d0, da0 + ka, db0 + kb16, A.idesc, acc);   // W_hi X_hi
-                            tc::mma_f16(d0, da1 + ka, db0 + kb16, A.idesc, 1u);    // W_lo X_hi
-                            tc::mma_f16(d0, da0 + ka, db1 + kb16, A.idesc, 1u);    // W_hi X_lo
+                            tc::mma_f16(d0, da0 + ka, db0 + kb16, Ag.idesc, acc);   // W_hi X_hi
+                            tc::mma_f16(d0, da1 + ka, db0 + kb16, Ag.idesc, 1u);    // W_lo X_hi
+                            tc::mma_f16(d0, da0 + ka, db1 + kb16, Ag.idesc, 1u);    // W_hi X_lo
                         } else {
-                            tc::mma_f16(d0, da0 + ka, db0 + kb16, A.idesc, acc);   // rows m0..
-                            tc::mma_f16(d1, da1 + ka, db0 + kb16, A.idesc, acc);   // rows m0+128..
+                            tc::mma_f16(d0, da0 + ka, db0 + kb16, Ag.idesc, acc);   // rows m0..
+                            if (C::NA == 2) tc::mma_f16(d1, da1 + ka, db0 + kb16, Ag.idesc, acc);  // rows m0+128..
                         }
                     }
                     tc::mma_commit(&empty[stage]);
@@ -323,18 +396,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             // drain: all issued MMAs have completed before TMEM is released
             tc::mma_commit(done);
             volatile int never = 0;
-            tc::mbar_wait(done, 0, &never, A.limit_ns);
+            tc::mbar_wait(done, 0, &never, Ag.limit_ns);
         }
     } else {
         // ---------------- epilogue ----------------
         const int q = warp & 3;
         const int row = q * 32 + lane;
         int it = 0;
-        for (int64_t u = blockIdx.x; u < A.units; u += gridDim.x, ++it) {
-            const Unit w = decode<MODE>(A, u);
+        for (int64_t u = blockIdx.x; u < total_units; u += gridDim.x, ++it) {
+            const int p = prob_of(u);
+            const TcArgs& A = args_of(p);
+            const Unit w = decode<MODE>(A, u - s_ubeg[p], s_mt[p]);
             const int buf = (C::NBUF == 2) ? (it & 1) : 0;
             const uint32_t buf_phase = (uint32_t)((C::NBUF == 2 ? (it >> 1) : it) & 1);
-            if (!tc::mbar_wait(&tfull[buf], buf_phase, abort_flag, A.limit_ns)) {
+            if (!tc::mbar_wait(&tfull[buf], buf_phase, abort_flag, Ag.limit_ns)) {
                 raise();
                 break;
             }
@@ -344,7 +419,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 // e^{U} = e^{b_i} e^{v}, v = (W X)_i[t]: e^{b_i} in FP64, and the row sum is kept as
                 // e^{b_i} (count + sum (e^{v} - 1)), so quiet bins (v ~ 0) add no FP32 rounding of b + v.
                 const uint32_t taddr = lane_base + (uint32_t)(buf * BN);
-                const int32_t i = w.m0 + row;
+                const int32_t il = w.m0 + row;
+                const int32_t i = il < s_m[p] ? (A.rows ? A.rows[il] : il) : A.n;
                 const double ebi = (i < A.n) ? A.eb[i] : 0.0;
                 const float dteb = (float)(A.dt * ebi);
                 double rsum = 0.0;
@@ -446,11 +522,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     A.part_tau[3 * plane + o] = p3;
                     A.part_tau[4 * plane + o] = p4;
                 }
-                if (bad) atomicOr(A.flags, 1);
+                if (bad && i < A.n) atomicOr(A.flags, 1);  // rows past the evaluated set hold stale W parts
             } else {
 #pragma unroll 1
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t taddr = lane_base + (uint32_t)(h * BN);
+                for (int h = 0; h < C::NA; ++h) {
+                    const uint32_t taddr = lane_base + (uint32_t)((buf + h) * BN);
                     const int32_t i = w.m0 + h * 128 + row;
                     float* grow = A.part_g + ((int64_t)w.split * A.n + i) * A.n;
 #pragma unroll 1
@@ -481,11 +557,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 }
 
 template <typename T16>
-__global__ void split_w_kernel(int32_t n, int64_t ldk, const float* __restrict__ W, T16* __restrict__ hi,
-                               T16* __restrict__ lo, int* flags) {
+// hi + lo parts of the evaluated rows of W, packed: part row l holds row rows[l] (all rows when rows is null);
+// m rows, or *m_dev when given
+__global__ void split_w_kernel(int32_t n, int64_t ldk, const float* __restrict__ W, const int32_t* __restrict__ rows,
+                               int32_t m, const int32_t* __restrict__ m_dev, T16* __restrict__ hi, T16* __restrict__ lo,
+                               int* flags) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)n * ldk) return;
-    const int64_t i = e / ldk, k = e % ldk;
+    if (m_dev) m = *m_dev;
+    if (e >= (int64_t)m * ldk) return;
+    const int64_t pr = e / ldk, k = e % ldk;
+    const int64_t i = rows ? rows[pr] : pr;
     float w = 0.f;
     if (k < n) w = W[i * n + k];
     if (!isfinite(w)) atomicOr(flags, 1);
@@ -547,15 +628,22 @@ bool encode_blocked(CUtensorMap* m, bool bf16, const void* base, uint64_t n, uin
 
 }  // namespace
 
-int tc_nsplit(const glm_ctx* c) {
-    const int64_t tiles = (int64_t)((c->pb.n + 255) / 256) * ((c->pb.n + BN - 1) / BN);
+// Splits of the bins for E X^T with row tiles of 256 (mode 1) or 128 (mode 2) so that the launch has about
+// units_per_sm units per SM.
+int tc_nsplit_for(const glm_ctx* c, int mode, int units_per_sm) {
+    const int64_t bm = mode == 2 ? 128 : 256;
+    const int64_t tiles = (int64_t)((c->pb.n + bm - 1) / bm) * ((c->pb.n + BN - 1) / BN);
     const int64_t kb_total = (c->pb.T + Cfg<1>::BK - 1) / Cfg<1>::BK;
-    int64_t s = (4 * (int64_t)c->sm_count + tiles - 1) / tiles;
+    int64_t s = ((int64_t)units_per_sm * c->sm_count + tiles - 1) / tiles;
     if (s > kb_total) s = kb_total;
     if (s < 1) s = 1;
     const int64_t kps = (kb_total + s - 1) / s;
     return (int)((kb_total + kps - 1) / kps);  // no empty split
 }
+
+int tc_nsplit(const glm_ctx* c) { return c->g_nsplit > 0 ? c->g_nsplit : tc_nsplit_for(c, c->g_mode, 4); }
+
+int tc_nsplit_max(const glm_ctx* c) { return tc_nsplit_for(c, 1, TUNE_UPM_MAX); }
 
 int tc_tile_t() { return BN; }
 
@@ -579,15 +667,20 @@ cudaError_t tc_prepare_maps(glm_ctx* c) {
     return ok ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int MODE, typename T16, bool TAU = false>
+template <int MODE, typename T16, bool TAU = false, bool BATCH = false>
 static cudaError_t run(glm_ctx* c, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0,
-                       const CUtensorMap& b1, const TcArgs& A) {
+                       const CUtensorMap& b1, const TcArgs& A, const TcBatch* batch = nullptr, int64_t grid = 0) {
     const size_t smem = Layout<MODE>::SMEM;
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<MODE, T16, TAU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(c->stream, &cap);
     if (e != cudaSuccess) return e;
-    const int64_t grid = A.units < c->sm_count ? A.units : c->sm_count;
-    tc_gemm_kernel<MODE, T16, TAU><<<(unsigned)grid, NUM_THREADS, smem, c->stream>>>(a0, a1, b0, b1, A);
+    if (cap == cudaStreamCaptureStatusNone) {  // set before the first launch; not during graph capture
+        e = cudaFuncSetAttribute(tc_gemm_kernel<MODE, T16, TAU, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (grid <= 0) grid = A.units < c->sm_count ? A.units : c->sm_count;
+    tc_gemm_kernel<MODE, T16, TAU, BATCH><<<(unsigned)grid, NUM_THREADS, smem, c->stream>>>(a0, a1, b0, b1, A, batch);
     return cudaGetLastError();
 }
 
@@ -606,6 +699,8 @@ static TcArgs base_args(glm_ctx* c) {
     A.a = (float)P.a;
     A.part_tau = nullptr;
     A.part_s = nullptr;
+    A.rows = nullptr;
+    A.m_rows = P.n;
     A.offs = c->buf.offs;
     A.bins = c->buf.bins;
     A.seg_first = c->buf.seg_first;
@@ -619,23 +714,27 @@ static TcArgs base_args(glm_ctx* c) {
     return A;
 }
 
-cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, bool tau) {
+cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, bool tau, const int32_t* rows,
+                                 int32_t m) {
     const Problem& P = c->pb;
     const int64_t ldk = c->buf.ldn;
-    const int64_t total = (int64_t)P.n * ldk;
+    const int32_t mr = rows ? m : P.n;
+    const int64_t total = (int64_t)mr * ldk;
     const size_t wsz = (size_t)P.n * ldk;
     if (P.prec == GLM_PREC_BF16) {
         auto* hi = reinterpret_cast<__nv_bfloat16*>(c->buf.Wsplit);
-        split_w_kernel<__nv_bfloat16><<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(P.n, ldk, W, hi,
-                                                                                             hi + wsz, c->buf.flags);
+        split_w_kernel<__nv_bfloat16><<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(
+            P.n, ldk, W, rows, mr, nullptr, hi, hi + wsz, c->buf.flags);
     } else {
         auto* hi = reinterpret_cast<__half*>(c->buf.Wsplit);
-        split_w_kernel<__half><<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(P.n, ldk, W, hi, hi + wsz,
-                                                                                      c->buf.flags);
+        split_w_kernel<__half><<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(P.n, ldk, W, rows, mr, nullptr,
+                                                                                      hi, hi + wsz, c->buf.flags);
     }
     launch_exp_bias(c, b);
     TcArgs A = base_args(c);
-    A.mt = (P.n + 127) / 128;
+    A.rows = rows;
+    A.m_rows = mr;
+    A.mt = (mr + 127) / 128;
     A.nt = (int32_t)(P.Tpad / BN);
     A.units = (int64_t)A.mt * A.nt;
     A.kb_per_unit = (P.n + Cfg<0>::BK - 1) / Cfg<0>::BK;
@@ -655,19 +754,33 @@ cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, boo
     return run<0, __half>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
 }
 
-static cudaError_t run_products(glm_ctx* c, const CUtensorMap& mapB) {
+// E X^T arguments of context c with its tile mode and split count
+static TcArgs grad_args(glm_ctx* c, int mode, int ns) {
     const Problem& P = c->pb;
     TcArgs A = base_args(c);
-    A.mt = (P.n + 255) / 256;
+    A.mt = (P.n + (mode == 2 ? 127 : 255)) / (mode == 2 ? 128 : 256);
     A.nt = (P.n + BN - 1) / BN;
-    const int ns = tc_nsplit(c);
     A.kb_total = (P.T + Cfg<1>::BK - 1) / Cfg<1>::BK;
     A.kb_per_unit = (int32_t)((A.kb_total + ns - 1) / ns);
     A.units = (int64_t)A.mt * A.nt * ns;
     A.nsplit = ns;
     A.part_g = c->buf.part_g;
-    if (P.prec == GLM_PREC_BF16) return run<1, __nv_bfloat16>(c, c->tmap[4], c->tmap[4], mapB, mapB, A);
+    return A;
+}
+
+static cudaError_t run_products_as(glm_ctx* c, const CUtensorMap& mapB, int mode, int ns) {
+    const TcArgs A = grad_args(c, mode, ns);
+    const bool bf = c->pb.prec == GLM_PREC_BF16;
+    if (mode == 2) {
+        if (bf) return run<2, __nv_bfloat16>(c, c->tmap[4], c->tmap[4], mapB, mapB, A);
+        return run<2, __half>(c, c->tmap[4], c->tmap[4], mapB, mapB, A);
+    }
+    if (bf) return run<1, __nv_bfloat16>(c, c->tmap[4], c->tmap[4], mapB, mapB, A);
     return run<1, __half>(c, c->tmap[4], c->tmap[4], mapB, mapB, A);
+}
+
+static cudaError_t run_products(glm_ctx* c, const CUtensorMap& mapB) {
+    return run_products_as(c, mapB, c->g_mode, tc_nsplit(c));
 }
 
 cudaError_t launch_tc_grad(glm_ctx* c) { return run_products(c, c->tmap[5]); }
@@ -696,6 +809,219 @@ cudaError_t launch_tc_spike_term(glm_ctx* c) {
     if ((e = launch_sum_splits(c, ns, c->buf.C, false)) != cudaSuccess) return e;
     if ((e = run_products(c, c->tmap[6])) != cudaSuccess) return e;
     return launch_sum_splits(c, ns, c->buf.C, true);
+}
+
+// ---- several problems per launch (glm_fit_batch) ----
+
+size_t tc_batch_bytes() { return sizeof(TcBatch); }
+
+// Host images of the two batch descriptors: U products of the rows rows[p] (m_dev[p] of them) at
+// (W32[p], b32[p]), and E X^T.  All problems share one precision.
+int tc_batch_fill(glm_ctx* const* cs, int np, float* const* W32, float* const* b32, int32_t* const* rows,
+                  const int32_t* const* m_dev, void* host_u, void* host_g) {
+    if (np < 1 || np > MAX_BATCH) return GLM_ERR_INVALID_ARG;
+    TcBatch* bu = static_cast<TcBatch*>(host_u);
+    TcBatch* bg = static_cast<TcBatch*>(host_g);
+    std::memset(static_cast<void*>(bu), 0, sizeof(TcBatch));
+    std::memset(static_cast<void*>(bg), 0, sizeof(TcBatch));
+    bu->nprob = bg->nprob = np;
+    for (int p = 0; p < np; ++p) {
+        glm_ctx* c = cs[p];
+        const Problem& P = c->pb;
+        TcArgs A = base_args(c);
+        A.rows = rows[p];
+        A.m_rows = P.n;
+        A.mt = (P.n + 127) / 128;
+        A.nt = (int32_t)(P.Tpad / BN);
+        A.units = (int64_t)A.mt * A.nt;
+        A.kb_per_unit = (P.n + Cfg<0>::BK - 1) / Cfg<0>::BK;
+        A.b = b32[p];
+        A.E = c->buf.E;
+        A.part_e = c->buf.part_e;
+        A.part_tau = c->buf.part_tau;
+        A.part_s = c->buf.part_s;
+        bu->args[p] = A;
+        bu->m_dev[p] = m_dev[p];
+        for (int k = 0; k < 4; ++k) bu->maps[p][k] = c->tmap[k];
+        bg->args[p] = grad_args(c, c->g_mode, tc_nsplit(c));
+        bg->maps[p][0] = bg->maps[p][1] = c->tmap[4];
+        bg->maps[p][2] = bg->maps[p][3] = c->tmap[5];
+    }
+    (void)W32;
+    return GLM_OK;
+}
+
+// One launch of the U product over every problem's evaluated rows (their count read on the device),
+// after each problem's W split and exp(b).
+cudaError_t launch_tc_u_batch(glm_ctx* const* cs, int np, const void* dev_u, float* const* W32, float* const* b32,
+                              int32_t* const* rows, const int32_t* const* m_dev) {
+    glm_ctx* c0 = cs[0];
+    for (int p = 0; p < np; ++p) {
+        glm_ctx* c = cs[p];
+        const Problem& P = c->pb;
+        const int64_t ldk = c->buf.ldn;
+        const int64_t total = (int64_t)P.n * ldk;
+        const size_t wsz = (size_t)P.n * ldk;
+        if (P.prec == GLM_PREC_BF16) {
+            auto* hi = reinterpret_cast<__nv_bfloat16*>(c->buf.Wsplit);
+            split_w_kernel<__nv_bfloat16><<<(unsigned)((total + 255) / 256), 256, 0, c0->stream>>>(
+                P.n, ldk, W32[p], rows[p], P.n, m_dev[p], hi, hi + wsz, c->buf.flags);
+        } else {
+            auto* hi = reinterpret_cast<__half*>(c->buf.Wsplit);
+            split_w_kernel<__half><<<(unsigned)((total + 255) / 256), 256, 0, c0->stream>>>(
+                P.n, ldk, W32[p], rows[p], P.n, m_dev[p], hi, hi + wsz, c->buf.flags);
+        }
+        launch_exp_bias(c, b32[p]);
+    }
+    TcArgs Ag = base_args(c0);
+    Ag.idesc |= 1u << 16;  // B (X) is N-major
+    const TcBatch* b = static_cast<const TcBatch*>(dev_u);
+    const CUtensorMap* m = c0->tmap;
+    if (c0->pb.prec == GLM_PREC_BF16)
+        return run<0, __nv_bfloat16, false, true>(c0, m[0], m[1], m[2], m[3], Ag, b, c0->sm_count);
+    return run<0, __half, false, true>(c0, m[0], m[1], m[2], m[3], Ag, b, c0->sm_count);
+}
+
+// One launch of E X^T over every problem (all in c0's tile mode).
+cudaError_t launch_tc_grad_batch(glm_ctx* c0, const void* dev_g) {
+    TcArgs Ag = base_args(c0);
+    const TcBatch* b = static_cast<const TcBatch*>(dev_g);
+    const CUtensorMap* m = c0->tmap;
+    const bool bf = c0->pb.prec == GLM_PREC_BF16;
+    if (c0->g_mode == 2) {
+        if (bf) return run<2, __nv_bfloat16, false, true>(c0, m[4], m[4], m[5], m[5], Ag, b, c0->sm_count);
+        return run<2, __half, false, true>(c0, m[4], m[4], m[5], m[5], Ag, b, c0->sm_count);
+    }
+    if (bf) return run<1, __nv_bfloat16, false, true>(c0, m[4], m[4], m[5], m[5], Ag, b, c0->sm_count);
+    return run<1, __half, false, true>(c0, m[4], m[4], m[5], m[5], Ag, b, c0->sm_count);
+}
+
+// ---- autotuner of the E X^T tile shape: row tile (256 or 128) x bin split (units per SM) ----
+//
+// Candidates are timed with CUDA events on the context's stream, on its current E and X; the choice is
+// cached per (precision, n, n_bins, SM count) for the process.
+namespace {
+struct TuneKey {
+    int prec, n, sms;
+    int64_t T;
+    bool operator==(const TuneKey& o) const { return prec == o.prec && n == o.n && sms == o.sms && T == o.T; }
+};
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, std::pair<int, int>>> g_tune_cache;  // key -> (mode, nsplit)
+}  // namespace
+
+int tc_autotune(glm_ctx* c, glm_tune_report_t* rep) {
+    const TuneKey key{(int)c->pb.prec, c->pb.n, c->sm_count, c->pb.T};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (auto& kv : g_tune_cache)
+            if (kv.first == key) {
+                c->g_mode = kv.second.first;
+                c->g_nsplit = kv.second.second;
+                if (rep) {
+                    rep->mode = c->g_mode;
+                    rep->nsplit = c->g_nsplit;
+                    rep->cached = 1;
+                }
+                return GLM_OK;
+            }
+    }
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return GLM_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return GLM_ERR_CUDA;
+    }
+    int best_mode = 1, best_ns = tc_nsplit_for(c, 1, 4), n_cand = 0;
+    float best_ms = 3.0e38f;
+    const int upms[] = {1, 2, 4, TUNE_UPM_MAX};
+    int rc = GLM_OK;
+    for (int mode = 1; mode <= 2 && !rc; ++mode)
+        for (int upm : upms) {
+            const int ns = tc_nsplit_for(c, mode, upm);
+            cudaError_t e = run_products_as(c, c->tmap[5], mode, ns);  // warm-up
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+            for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = run_products_as(c, c->tmap[5], mode, ns);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                rc = GLM_ERR_CUDA;
+                break;
+            }
+            ++n_cand;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_mode = mode;
+                best_ns = ns;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    c->g_mode = best_mode;
+    c->g_nsplit = best_ns;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (g_tune_cache.size() > 4096) g_tune_cache.clear();
+        g_tune_cache.push_back({key, {best_mode, best_ns}});
+    }
+    if (rep) {
+        rep->mode = best_mode;
+        rep->nsplit = best_ns;
+        rep->cached = 0;
+        rep->candidates = n_cand;
+        rep->best_ms = best_ms / 2.0f;
+    }
+    return GLM_OK;
+}
+
+// The batched E X^T launch tuned as a whole: one row-tile mode for all problems (one kernel), each problem's
+// splits for a common units-per-SM target.  dev_g / host_g: the batch descriptor (device / host image),
+// left holding the choice.
+int tc_autotune_batch(glm_ctx* const* cs, int np, void* dev_g, void* host_g) {
+    glm_ctx* c0 = cs[0];
+    TcBatch* bg = static_cast<TcBatch*>(host_g);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return GLM_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return GLM_ERR_CUDA;
+    }
+    auto set = [&](int mode, int upm) -> cudaError_t {
+        for (int p = 0; p < np; ++p) {
+            cs[p]->g_mode = mode;
+            cs[p]->g_nsplit = tc_nsplit_for(cs[p], mode, upm);
+            bg->args[p] = grad_args(cs[p], mode, cs[p]->g_nsplit);
+        }
+        return cudaMemcpy(dev_g, host_g, sizeof(TcBatch), cudaMemcpyHostToDevice);
+    };
+    int best_mode = 1, best_upm = 4;
+    float best_ms = 3.0e38f;
+    const int upms[] = {1, 2, 4, TUNE_UPM_MAX};
+    cudaError_t e = cudaSuccess;
+    for (int mode = 1; mode <= 2 && e == cudaSuccess; ++mode)
+        for (int upm : upms) {
+            float ms = 0.f;
+            e = set(mode, upm);
+            if (e == cudaSuccess) e = launch_tc_grad_batch(c0, dev_g);  // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, c0->stream);
+            for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = launch_tc_grad_batch(c0, dev_g);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c0->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_mode = mode;
+                best_upm = upm;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e == cudaSuccess) e = set(best_mode, best_upm);
+    return e == cudaSuccess ? GLM_OK : GLM_ERR_CUDA;
 }
 
 }  // namespace glm

@@ -145,16 +145,17 @@ def make_workload(name: str | None = None, *, threads: int = 0, **overrides) -> 
     return out
 
 
-def batch_workloads(n_rec: int = 24, *, scale: float = 1.0):
+def batch_workloads(n_rec: int = 24, *, scale: float = 1.0, t_scale: float | None = None):
     """Uneven recordings for batched fitting: N ~ U{100..1500}, T ~ U(300, 3600) s, rate ~ U(3, 12) Hz,
-    80/20 E/I, p = 0.1, +0.2 / -0.8, seeds 1..n_rec.  ``scale`` shrinks N and T for tests."""
+    80/20 E/I, p = 0.1, +0.2 / -0.8, seeds 1..n_rec.  ``scale`` shrinks N and T for tests; ``t_scale``, when
+    given, shrinks T alone."""
     out = []
     for s in range(1, n_rec + 1):
         w = philox4x32_10((s, 0, 0, 0x42415443), (s, 0))
         n = max(8, int(round((100 + w[0] % 1401) * scale)))
         t_sec = 300.0 + (w[1] / 4294967296.0) * 3300.0
         rate = 3.0 + (w[2] / 4294967296.0) * 9.0
-        n_bins = max(64, int(round(t_sec * 1000 * scale)))
+        n_bins = max(64, int(round(t_sec * 1000 * (scale if t_scale is None else t_scale))))
         out.append(dict(n=n, n_exc=int(round(0.8 * n)), p=0.1, w_exc=0.2, w_inh=0.8, w_self=-6.25, rate=rate,
                         tau=0.010, dt=0.001, n_bins=n_bins, seed=s))
     return out

@@ -3,11 +3,11 @@ inputs that span several tiles and ragged tails, plus edge cases, error paths an
 full N = 1000, 1.8M-bin size.
 
 Tolerances.  Plain FP32 form: filtered trains within a few FP32 ulps; spike term relative 5e-7 (a sum
-of FP32 X values, each rounded once or twice); log-likelihood relative 2e-9 (total) and, per row, 5e-8 of
-(|L_i| + q_i), the size of its terms (L_i itself can cross zero).
-The total-L bound is set by the FP32 storage of X itself: the rounding of the kernel values
-e^{-k dt/tau} (Eq. 13) repeats identically after every spike, so it does not average out over bins; its
-effect on the integral term is about 2^-24 E|U - b| ~ 1e-9 relative.
+of FP32 X values, each rounded once or twice); log-likelihood relative 1e-9 (total) and, per row, 5e-8 of
+(|L_i| + q_i), the size of its terms (L_i itself can cross zero).  The total-L bound needs X without a
+systematic rounding error: the kernel values e^{-k dt/tau} (Eq. 13) recur after every spike, so a scan
+that rounds the chain 1, a, a^2, ... repeatedly biases X by ~0.6 ulp (about 2e-9 in L); the scan
+takes each power rounded once, and the spike and integral parts of L come from the same U.
 gradient componentwise relative 1e-5 against the size of its two terms, |dG_ij| / (C_ij + dt sum_t
 e^{U_i} X_j).  Tensor-core forms (X and the rates in BF16 or FP16, W as hi + lo): total log-likelihood
 relative 1e-6, gradient 2e-3 in the same componentwise measure.  Per row, the X rounding error
@@ -135,7 +135,8 @@ def test_loglik_grad_f32_matches_oracle(ctx, n, T, seed, scale):
     ctx.set_problem(w["offs"], w["bins"], T, w["dt"], w["tau"], prec="f32")
     r = ctx.loglik_grad(to_dev(W), to_dev(b))
     ref = oracle.loglik_grad(w["offs"], w["bins"], T, w["dt"], w["tau"], W.astype(np.float64), b.astype(np.float64))
-    assert abs(r["L_total"] - ref["L_total"]) <= 2e-9 * abs(ref["L_total"])
+    print(f"f32 n={n} T={T}: L total rel {abs(r['L_total'] - ref['L_total']) / abs(ref['L_total']):.2e}")
+    assert abs(r["L_total"] - ref["L_total"]) <= 1e-9 * abs(ref["L_total"])
     Lr = r["L_rows"].cpu().numpy()
     assert np.all(np.abs(Lr - ref["L"]) <= 5e-8 * (np.abs(ref["L"]) + np.diff(w["offs"])))
     gb = r["gb"].cpu().numpy()
