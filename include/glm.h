@@ -214,6 +214,15 @@ int glm_fit(glm_ctx* ctx, const glm_fit_opts_t* opts, float* W_dev, float* b_dev
 int glm_fit_batch(glm_ctx* const* ctxs, int32_t n_prob, const glm_fit_opts_t* opts, float* const* W_dev,
                   float* const* b_dev, int8_t* const* row_status_host, glm_fit_report_t* reports);
 
+/* Recompute X chunk by chunk instead of storing it, for recordings whose N x n_bins outgrows device memory
+ * (SURVEY's config 3 form).  chunk_bins > 0 (rounded up to a multiple of 256) applies to the next
+ * glm_set_problem of a tensor-core precision: the context then holds X_hi, X_lo and the rates for
+ * chunk_bins bins only, and every evaluation filters, multiplies and reduces one chunk after the other
+ * (the filter runs once per chunk and evaluation, so an evaluation costs one filter pass more).  0
+ * (default) stores X for the whole recording.  Ignored for GLM_PREC_F32 and when chunk_bins covers the
+ * recording.  Chunked problems cannot be batched (glm_fit_batch). */
+int glm_set_chunk_bins(glm_ctx* ctx, int64_t chunk_bins);
+
 /* ---- autotuner of the gradient product's tile shape ----
  * (no counterpart in the paper.)  Times the gradient product E X^T of the current problem for row tiles of
  * 256 and 128 neurons and 1, 2, 4 and 8 bin splits per SM (the K extent of a tile), and keeps the fastest

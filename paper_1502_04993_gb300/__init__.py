@@ -81,6 +81,7 @@ SIGNATURES["glm_fit_default_opts"] = ([ctypes.POINTER(FitOpts)], None)
 SIGNATURES["glm_fit"] = ([_vp, ctypes.POINTER(FitOpts), _vp, _vp, _vp, ctypes.POINTER(FitReport)], ctypes.c_int)
 SIGNATURES["glm_fit_batch"] = ([_vp, _i32, ctypes.POINTER(FitOpts), _vp, _vp, _vp, ctypes.POINTER(FitReport)], ctypes.c_int)
 SIGNATURES["glm_autotune"] = ([_vp, _vp], ctypes.c_int)
+SIGNATURES["glm_set_chunk_bins"] = ([_vp, _i64], ctypes.c_int)
 SIGNATURES["glm_classify"] =([_vp, _i32, ctypes.POINTER(ClassifyOpts), _vp, _vp, _vp, ctypes.POINTER(ClassifyReport)],
                               ctypes.c_int)
 
@@ -294,6 +295,10 @@ class GLM:
             self._check(rc, "glm_fit")
         report = {f: getattr(rep, f) for f, _ in FitReport._fields_}
         return dict(W=Wd, b=bd, status=status, report=report, rc=rc)
+
+    def set_chunk_bins(self, chunk_bins: int):
+        """Recompute X in chunks of this many bins instead of storing it (applies to the next set_problem)."""
+        self._check(self.lib.glm_set_chunk_bins(self.h, int(chunk_bins)), "glm_set_chunk_bins")
 
     def autotune(self) -> dict:
         """Time the gradient product's tile shapes for this problem and keep the fastest (glm_autotune)."""

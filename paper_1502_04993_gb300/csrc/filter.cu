@@ -122,12 +122,13 @@ struct FilterArgs {
     int64_t T, nseg, Tpad, ldn;
     int32_t ngroups;
     int64_t nchunks;
+    int64_t s_begin, s_end;  // segments written; the buffers start at bin SEG s_begin
     const int64_t* offs;
     const int32_t* bins;
     const double* seg_carry;
     const int32_t* seg_first;
     void* X;
-    void* Xlo;  // 16-bit forms: X_lo [n][Tpad]
+    void* Xlo;  // 16-bit forms: X_lo
 };
 
 // F32 X, one warp per (8 rows, 4096-bin chunk).
@@ -139,8 +140,8 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache_f32_kernel(const _
     const int32_t g = (int32_t)(wg % A.ngroups);
     if (c >= A.nchunks) return;
     const float pl_hi = K.pl_hi[lane], pl_lo = K.pl_lo[lane];
-    const int64_t s0 = c * CHUNK_SEGS;
-    const int64_t s1 = min(s0 + (int64_t)CHUNK_SEGS, A.nseg);
+    const int64_t s0 = A.s_begin + c * CHUNK_SEGS;
+    const int64_t s1 = min(s0 + (int64_t)CHUNK_SEGS, A.s_end);
     float xs[8];
     int64_t cur[8], end[8];
 #pragma unroll
@@ -164,7 +165,10 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache_f32_kernel(const _
             const int32_t r = g * 8 + k;
             const uint32_t bits = seg_bits(A.bins, cur[k], end[k], t0, lane);
             float v[8];
-            xs[k] = seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v);
+            // every segment starts from its FP64 carry (loaded one segment ahead): X does not depend on where
+            // a chunk or unit starts
+            seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v);
+            xs[k] = (s + 1 < s1 && r < A.n) ? (float)A.seg_carry[(int64_t)r * A.nseg + s + 1] : 0.f;
             if (r < A.n) {
                 float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(A.X) + (int64_t)r * A.Tpad + tl);
                 dst[0] = make_float4(v[0], v[1], v[2], v[3]);
@@ -201,8 +205,8 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache16_kernel(const __g
     const int32_t g = (int32_t)(wg % A.ngroups);
     if (c >= A.nchunks) return;
     const float pl_hi = K.pl_hi[lane], pl_lo = K.pl_lo[lane];
-    const int64_t s0 = c * CHUNK_SEGS;
-    const int64_t s1 = min(s0 + (int64_t)CHUNK_SEGS, A.nseg);
+    const int64_t s0 = A.s_begin + c * CHUNK_SEGS;
+    const int64_t s1 = min(s0 + (int64_t)CHUNK_SEGS, A.s_end);
     float xs[8];
     int64_t cur[8], end[8];
 #pragma unroll
@@ -228,7 +232,10 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache16_kernel(const __g
             const int32_t r = g * 8 + k;
             const uint32_t bits = seg_bits(A.bins, cur[k], end[k], t0, lane);
             float v[8];
-            xs[k] = seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v);
+            // every segment starts from its FP64 carry (loaded one segment ahead): X does not depend on where
+            // a chunk or unit starts
+            seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v);
+            xs[k] = (s + 1 < s1 && r < A.n) ? (float)A.seg_carry[(int64_t)r * A.nseg + s + 1] : 0.f;
             uint32_t ph[4], pl[4];
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
@@ -237,7 +244,8 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache16_kernel(const __g
                 pl[p] = pack2<T16>(v[2 * p] - to_f<T16>(h0), v[2 * p + 1] - to_f<T16>(h1));
             }
             if (r < A.n) {
-                const int64_t o = ((tl >> 6) * A.n + r) * 64 + (tl & 63);
+                const int64_t tb = tl - A.s_begin * SEG;  // bin within the buffers
+                const int64_t o = ((tb >> 6) * A.n + r) * 64 + (tb & 63);
                 *reinterpret_cast<uint4*>(Xh + o) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
                 *reinterpret_cast<uint4*>(Xl + o) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
             }
@@ -282,7 +290,8 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_range_kernel(const __gri
             if (t0 >= te) break;
             const uint32_t bits = seg_bits(A.bins, cur, end, t0, lane);
             float v[8];
-            xs = seg_scan(K, xs, bits, pl_hi, pl_lo, lane, v);
+            const float x0 = (s == s0) ? xs : (float)A.seg_carry[(int64_t)r * A.nseg + s];  // FP64 carry per segment
+            seg_scan(K, x0, bits, pl_hi, pl_lo, lane, v);
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
                 const int64_t t = t0 + 8 * lane + m;
@@ -308,7 +317,7 @@ cudaError_t launch_carry(glm_ctx* c) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_filter_cache(glm_ctx* c) {
+cudaError_t launch_filter_cache(glm_ctx* c, int64_t s_begin, int64_t s_end) {
     const Problem& P = c->pb;
     FilterArgs A;
     A.n = P.n;
@@ -317,7 +326,9 @@ cudaError_t launch_filter_cache(glm_ctx* c) {
     A.Tpad = P.Tpad;
     A.ldn = c->buf.ldn;
     A.ngroups = (P.n + 7) / 8;
-    A.nchunks = (P.nseg + CHUNK_SEGS - 1) / CHUNK_SEGS;
+    A.s_begin = s_begin;
+    A.s_end = s_end < 0 ? P.nseg : s_end;
+    A.nchunks = (A.s_end - A.s_begin + CHUNK_SEGS - 1) / CHUNK_SEGS;
     A.offs = c->buf.offs;
     A.bins = c->buf.bins;
     A.seg_carry = c->buf.seg_carry;

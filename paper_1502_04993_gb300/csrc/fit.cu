@@ -665,8 +665,18 @@ int fit_run_batch(glm_ctx* const* cs, int np, const glm_fit_opts_t* o, float* co
         (rc = ck(c0, cudaMemcpy(d_src, st_src.data(), sizeof(int32_t*) * np, cudaMemcpyHostToDevice))) ||
         (rc = ck(c0, cudaMemcpy(d_n, nrows.data(), sizeof(int32_t) * np, cudaMemcpyHostToDevice))))
         return done(rc);
-    // the batched E X^T launch is tuned as a whole (row tile and splits), then the problems start
+    // the batched E X^T launch is tuned as a whole (row tile and splits), then skips finished problems
     if ((rc = tc_autotune_batch(cs, np, dev_g, host_g))) return done(set_error(c0, rc, "batch autotune failed"));
+    {
+        std::vector<const int*> cnt_ptr(np);
+        for (int p = 0; p < np; ++p) cnt_ptr[p] = d_cnt + p;
+        tc_batch_set_grad_counts(host_g, np, cnt_ptr.data());
+        std::vector<int> init(np);
+        for (int p = 0; p < np; ++p) init[p] = fp[p].F.n;
+        if ((rc = ck(c0, cudaMemcpy(d_cnt, init.data(), sizeof(int) * np, cudaMemcpyHostToDevice))) ||
+            (rc = ck(c0, cudaMemcpy(dev_g, host_g, tc_batch_bytes(), cudaMemcpyHostToDevice))))
+            return done(rc);
+    }
     for (int p = 0; p < np && !rc; ++p) rc = fit_start(fp[p], o);
     if (rc) return done(rc);
     if ((rc = ck(c0, cudaStreamSynchronize(st)))) return done(rc);

@@ -2,6 +2,7 @@
 // gradient evaluation.  Host-side validation of the spike trains, device workspace, stream plumbing.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -177,7 +178,7 @@ int do_prepare(glm_ctx* c) {
                            c->stream));
     c->c_ready = false;
     GLM_RUN("carry", 2, launch_carry(c));
-    GLM_RUN("filter_scan", 1, launch_filter_cache(c));
+    if (!P.chunk) GLM_RUN("filter_scan", 1, launch_filter_cache(c));  // chunked: filtered per use
     // The spike term C (the W-independent part of dL/dW, Eq. 12): a gather of X at the spike bins for the
     // plain FP32 form, S (X_hi + X_lo)^T on the tensor cores for the 16-bit forms.  The spike part of L
     // comes from U at the spike bins in the U-product epilogue instead (its rounding then cancels against
@@ -227,6 +228,25 @@ int set_error(glm_ctx* c, int code, const char* msg) { return fail(c, code, msg)
 int eval_enqueue(glm_ctx* c, const float* W, const float* b, double* L_rows, double* G, double* gb, bool want_grad,
                  bool reuse_u, bool tau, const int32_t* rows, int32_t m) {
     const bool tensor = c->pb.prec != GLM_PREC_F32;
+    const Problem& P = c->pb;
+    if (P.chunk) {
+        // X recomputed chunk by chunk: filter, U product and E X^T per chunk; E X^T summed over the chunks.
+        // Nothing of a previous evaluation survives, so a reuse request evaluates again (every row).
+        if (reuse_u) rows = nullptr;
+        for (int64_t t0 = 0; t0 < P.Tpad; t0 += P.Tc) {
+            const int64_t len = std::min(P.Tc, P.Tpad - t0);
+            GLM_RUN("filter_scan", 1, launch_filter_cache(c, t0 / SEG, (t0 + len) / SEG));
+            GLM_RUN("u_epilogue", 3, launch_tc_u_epilogue(c, W, b, tau, rows, m, t0, len));
+            if (want_grad) {
+                int ns = 0;
+                GLM_RUN("grad", 1, launch_tc_grad(c, len, &ns));
+                GLM_RUN("grad", 1, launch_sum_splits(c, ns, c->buf.Gacc, t0 > 0));
+            }
+        }
+        GLM_RUN("reduce", want_grad ? 2 : 1,
+                launch_reduce(c, W, b, L_rows, G, gb, want_grad, P.Tpad / tc_tile_t(), 0, c->buf.Gacc));
+        return GLM_OK;
+    }
     if (!reuse_u) {
         if (tensor)
             GLM_RUN("u_epilogue", 3, launch_tc_u_epilogue(c, W, b, tau, rows, m));
@@ -386,6 +406,9 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
     P.nseg = (n_bins + SEG - 1) / SEG;
     P.Tpad = P.nseg * SEG;
     P.prec = prec;
+    P.chunk = 0;
+    if (tensor && c->chunk_req > 0 && round_up(c->chunk_req, SEG) < P.Tpad) P.chunk = round_up(c->chunk_req, SEG);
+    P.Tc = P.chunk ? P.chunk : P.Tpad;
     Buffers& B = c->buf;
     const size_t nn = (size_t)n * n;
     const size_t esz = (prec == GLM_PREC_F32) ? 4 : 2;
@@ -394,12 +417,13 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
         (rc = ws_alloc_t(c, &B.seg_carry, (size_t)n * P.nseg)) ||
         (rc = ws_alloc_t(c, &B.seg_first, (size_t)n * P.nseg)) || (rc = ws_alloc_t(c, &B.pow_seg, SEG + 1)) ||
         (rc = ws_alloc_t(c, &B.qd, n)) || (rc = ws_alloc_t(c, &B.C, nn)) ||
-        (rc = ws_alloc(c, &B.X, (size_t)n * P.Tpad * esz)) ||
-        (rc = ws_alloc(c, &B.E, (size_t)n * P.Tpad * esz)) ||
+        (rc = ws_alloc(c, &B.X, (size_t)n * P.Tc * esz)) ||
+        (rc = ws_alloc(c, &B.E, (size_t)n * P.Tc * esz)) ||
+        (P.chunk && (rc = ws_alloc_t(c, &B.Gacc, nn))) ||
         (rc = ws_alloc_t(c, &B.part_e, (size_t)n * (P.Tpad / (tensor ? tc_tile_t() : simt_tile_t())))) ||
         (rc = ws_alloc_t(c, &B.part_g, nn * (tensor ? tc_nsplit_max(c) : grad_nsplit(c)))) ||
         (rc = ws_alloc_t(c, &B.flags, 4)) || (rc = ws_alloc_t(c, &B.Lrows, n)) || (rc = ws_alloc_t(c, &B.scal, 8)) || (rc = ws_alloc_t(c, &B.eb, n)) ||
-        (tensor && (rc = ws_alloc(c, &B.Xlo, (size_t)P.n * P.Tpad * 2))) ||
+        (tensor && (rc = ws_alloc(c, &B.Xlo, (size_t)P.n * P.Tc * 2))) ||
         (rc = ws_alloc_t(c, &B.part_s, (size_t)n * (P.Tpad / (tensor ? tc_tile_t() : simt_tile_t())))) ||
         (tensor && (rc = ws_alloc(c, &B.Wsplit, 2 * (size_t)n * B.ldn * 2)))) {
         free_all(c);
@@ -535,6 +559,13 @@ int glm_fit(glm_ctx* c, const glm_fit_opts_t* opts, float* W, float* b, int8_t* 
     return glm::fit_run(c, &o, W, b, row_status, rep);
 }
 
+int glm_set_chunk_bins(glm_ctx* c, int64_t chunk_bins) {
+    if (!c) return GLM_ERR_INVALID_ARG;
+    if (chunk_bins < 0) return fail(c, GLM_ERR_INVALID_ARG, "chunk_bins must be >= 0");
+    c->chunk_req = chunk_bins;
+    return GLM_OK;
+}
+
 int glm_autotune(glm_ctx* c, glm_tune_report_t* rep) {
     if (!c) return GLM_ERR_INVALID_ARG;
     if (!c->has_problem) return fail(c, GLM_ERR_NO_PROBLEM, "no problem set");
@@ -556,6 +587,7 @@ int glm_fit_batch(glm_ctx* const* cs, int32_t np, const glm_fit_opts_t* opts, fl
         if (!c->has_problem) return fail(c0, GLM_ERR_NO_PROBLEM, "a context has no problem set");
         if (c->device != c0->device) return fail(c0, GLM_ERR_INVALID_ARG, "contexts on different devices");
         if (c->pb.prec != c0->pb.prec) return fail(c0, GLM_ERR_INVALID_ARG, "contexts with different precisions");
+        if (c->pb.chunk) return fail(c0, GLM_ERR_UNSUPPORTED, "glm_fit_batch needs X stored (no chunking)");
         for (int32_t q = 0; q < p; ++q)
             if (cs[q] == c) return fail(c0, GLM_ERR_INVALID_ARG, "a context appears twice");
     }

@@ -17,6 +17,10 @@ namespace glm {
 // at or after bin 256 s are precomputed once per problem.
 // ---------------------------------------------------------------------------------------------
 constexpr int SEG = 256;
+// e^U is formed as e^c e^(U - c) with c = max(b_i, EXP_SPLIT_FLOOR): c = b_i keeps the quiet bins (U ~ b_i)
+// free of FP32 rounding; the floor keeps U - c inside the FP32 range of exp when a fit drives b_i far below
+// U (there the quiet bins contribute less than e^-60 per second and their rounding does not matter).
+constexpr float EXP_SPLIT_FLOOR = -60.f;
 
 // Powers of a = exp(-dt/tau) split into FP32 hi + lo parts, so that the FP32 scan multiplies by a
 // with ~48 significant bits (the product is hi*x + lo*x).
@@ -36,6 +40,8 @@ struct Problem {
     int64_t nseg = 0;     // ceil(T / SEG)
     int64_t Tpad = 0;     // nseg * SEG
     glm_prec_t prec = GLM_PREC_F32;
+    int64_t chunk = 0;    // 16-bit forms: bins of X recomputed per chunk for each evaluation (0: X stored)
+    int64_t Tc = 0;       // bins held in the X / E buffers: chunk, or Tpad
 };
 
 // Device buffers owned by a context.  Row-major everywhere; ld* in elements.
@@ -49,7 +55,8 @@ struct Buffers {
     double* C = nullptr;          // [n][n]      spike term
     double* C_part = nullptr;     // [parts][n][n] (plain FP32 form)
     void* X = nullptr;            // F32: float [n][Tpad]; 16-bit: [n][Tpad]
-    void* Xlo = nullptr;          // 16-bit only: X_lo = X - X_hi, [n][Tpad]
+    void* Xlo = nullptr;          // 16-bit only: X_lo = X - X_hi, bin-blocked over Tc bins
+    double* Gacc = nullptr;       // chunked: [n][n] E X^T summed over the chunks
     int64_t ldn = 0;              // leading dim of the W parts (n rounded up to 64)
     void* E = nullptr;            // F32: float [n][Tpad] dt exp(U); 16-bit: the same, bin-blocked
     double* part_e = nullptr;     // [n][ntile_t]  per-(row, bin tile) sums of exp(U)
@@ -84,6 +91,7 @@ struct glm_ctx {
     bool c_ready = false;  // C holds the spike term of the current problem and tau
     int g_mode = 1;        // E X^T row tile: 1 = 256 rows, 2 = 128 rows (autotuner)
     int g_nsplit = 0;      // E X^T bin splits (0: the default for g_mode)
+    int64_t chunk_req = 0; // bins per chunk requested by glm_set_chunk_bins (applied by glm_set_problem)
     std::string last_error;
     // tracing: event pairs per launched kernel group while profiling is on
     bool prof_on = false;
@@ -109,7 +117,8 @@ namespace glm {
 
 // ---- launchers (each returns cudaError_t of the launch) ----
 cudaError_t launch_carry(glm_ctx* c);
-cudaError_t launch_filter_cache(glm_ctx* c);
+// segments [s_begin, s_end) into the X buffers (whose first bin is SEG s_begin); s_end < 0: all
+cudaError_t launch_filter_cache(glm_ctx* c, int64_t s_begin = 0, int64_t s_end = -1);
 cudaError_t launch_filter_range(glm_ctx* c, int64_t t0, int64_t t_len, void* out, int64_t ldx, glm_dtype_t dtype);
 cudaError_t launch_spike_term(glm_ctx* c, double* out);
 cudaError_t launch_tau_rows(glm_ctx* c, double* rows);
@@ -119,8 +128,9 @@ cudaError_t launch_tc_spike_term(glm_ctx* c);
 cudaError_t launch_simt_u_epilogue(glm_ctx* c, const float* W, const float* b, const int32_t* rows = nullptr,
                                    int32_t m = 0);
 cudaError_t launch_simt_grad(glm_ctx* c);
+// G = C - (Gacc, when given, else the sum of the E X^T splits)
 cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_rows, double* G, double* gb,
-                          bool want_grad, int64_t ntile, int nsplit);
+                          bool want_grad, int64_t ntile, int nsplit, const double* Gacc = nullptr);
 void launch_exp_bias(glm_ctx* c, const float* b);
 int set_error(glm_ctx* c, int code, const char* msg);
 // One evaluation at (W, b).  With rows (m of them) only those rows' U product, rates and per-tile sums
@@ -134,13 +144,15 @@ int fit_run(glm_ctx* c, const glm_fit_opts_t* o, float* W, float* b, int8_t* row
 int fit_run_batch(glm_ctx* const* cs, int np, const glm_fit_opts_t* o, float* const* W, float* const* b,
                   int8_t* const* row_status, glm_fit_report_t* reps);
 cudaError_t tc_prepare_maps(glm_ctx* c);
+// bins [t_base, t_base + t_len) held in the X / E buffers (t_len < 0: the whole buffer)
 cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, bool tau, const int32_t* rows = nullptr,
-                                 int32_t m = 0);
-cudaError_t launch_tc_grad(glm_ctx* c);
+                                 int32_t m = 0, int64_t t_base = 0, int64_t t_len = -1);
+cudaError_t launch_tc_grad(glm_ctx* c, int64_t t_len = -1, int* nsplit_used = nullptr);
 int tc_nsplit(const glm_ctx* c);
 int tc_nsplit_max(const glm_ctx* c);
 int tc_autotune(glm_ctx* c, glm_tune_report_t* rep);
 int tc_autotune_batch(glm_ctx* const* cs, int np, void* dev_g, void* host_g);
+void tc_batch_set_grad_counts(void* host_g, int np, const int* const* counts);
 // several problems per launch (glm_fit_batch)
 size_t tc_batch_bytes();
 int tc_batch_fill(glm_ctx* const* cs, int np, float* const* W32, float* const* b32, int32_t* const* rows,

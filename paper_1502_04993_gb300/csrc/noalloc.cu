@@ -23,6 +23,8 @@ constexpr int NB = 128;  // tile edge
 constexpr int NK = 16;   // k step
 constexpr int NT = 256;  // threads
 constexpr int MAX_DEVICES = 64;
+// e^U = e^c e^(U - c), c = max(b_i, -60): the same split as the library's regular U product
+constexpr float NA_EXP_SPLIT_FLOOR = -60.f;
 
 // The fixed scratch: exp(b_i) for i < n, then the partial sums [n][ceil(n_bins / 128)]; every element used
 // is written before it is read, so nothing needs clearing between calls.  Every GPU that loads the library
@@ -57,7 +59,7 @@ int scratch_address(double** out) {
 
 __global__ void na_exp_bias_kernel(int32_t n, const float* __restrict__ b, double* __restrict__ eb) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) eb[i] = exp((double)b[i]);
+    if (i < n) eb[i] = exp((double)fmaxf(b[i], NA_EXP_SPLIT_FLOOR));
 }
 
 struct NaArgs {
@@ -65,6 +67,7 @@ struct NaArgs {
     int64_t T, ldx, ntile;
     const float* W;
     const float* X;
+    const float* b;
     const double* eb;
     double* part;  // [n][ntile]
 };
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(NT) na_u_kernel(const __grid_constant__ NaArgs
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const int64_t t = t0 + (c < 4 ? tx * 4 + c : 64 + tx * 4 + (c - 4));
-            const float m = expm1f(acc[r][c]);
+            const float m = expm1f(acc[r][c] + (i < n ? fminf(A.b[i] - NA_EXP_SPLIT_FLOOR, 0.f) : 0.f));
             if (t < A.T) {
                 msum += m;
                 ++cnt;
@@ -198,6 +201,7 @@ extern "C" int glm_loglik_noalloc(int32_t n, int64_t n_bins, double dt, const fl
     A.ntile = ntile;
     A.W = W_dev;
     A.X = X_dev;
+    A.b = b_dev;
     A.eb = scratch;
     A.part = scratch + n;
     na_exp_bias_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, b_dev, scratch);

@@ -51,11 +51,15 @@ __global__ void reduce_rows_kernel(const __grid_constant__ ReduceArgs A) {
 }
 
 __global__ void reduce_grad_kernel(int64_t nn, int nsplit, const double* __restrict__ C,
-                                   const float* __restrict__ part_g, double* __restrict__ G) {
+                                   const float* __restrict__ part_g, const double* __restrict__ Gacc,
+                                   double* __restrict__ G) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nn) return;
     double s = 0.0;
-    for (int p = 0; p < nsplit; ++p) s += (double)part_g[p * nn + e];
+    if (Gacc)
+        s = Gacc[e];
+    else
+        for (int p = 0; p < nsplit; ++p) s += (double)part_g[p * nn + e];
     G[e] = C[e] - s;
 }
 
@@ -145,7 +149,7 @@ cudaError_t launch_tau_rows(glm_ctx* c, double* rows) {
 }
 
 cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_rows, double* G, double* gb,
-                          bool want_grad, int64_t ntile, int nsplit) {
+                          bool want_grad, int64_t ntile, int nsplit, const double* Gacc) {
     const Problem& P = c->pb;
     ReduceArgs A;
     A.n = P.n;
@@ -162,7 +166,8 @@ cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_
     reduce_rows_kernel<<<(P.n + 7) / 8, 256, 0, c->stream>>>(A);
     if (want_grad && G) {
         const int64_t nn = (int64_t)P.n * P.n;
-        reduce_grad_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(nn, nsplit, A.C, c->buf.part_g, G);
+        reduce_grad_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(nn, nsplit, A.C, c->buf.part_g, Gacc,
+                                                                              G);
     }
     return cudaGetLastError();
 }

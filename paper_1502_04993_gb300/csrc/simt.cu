@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(ST) simt_u_kernel(const __grid_constant__ Simt
     for (int r = 0; r < 8; ++r) {
         const int32_t i = row_of(A, i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4)));
         const double ebi = (i < n) ? A.eb[i] : 0.0;
+        const float sh = (i < n) ? fminf(A.b[i] - EXP_SPLIT_FLOOR, 0.f) : 0.f;  // U - c = v + sh
         const float dteb = (float)(A.dt * ebi);
         float msum = 0.f;
         int cnt = 0;
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(ST) simt_u_kernel(const __grid_constant__ Simt
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const int64_t t = t0 + (c < 4 ? tx * 4 + c : 64 + tx * 4 + (c - 4));
-            const float m = expm1f(acc[r][c]);
+            const float m = expm1f(acc[r][c] + sh);
             const bool valid = t < A.T;
             bad |= valid && !(m <= 3.0e38f);
             if (valid) {
@@ -277,7 +278,7 @@ int grad_nsplit(const glm_ctx* c) {
 __global__ void exp_bias_kernel(int32_t n, const float* __restrict__ b, double* __restrict__ eb, int* flags) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double v = exp((double)b[i]);
+    const double v = exp((double)fmaxf(b[i], EXP_SPLIT_FLOOR));
     if (!isfinite(b[i]) || !(v <= 1e300)) atomicOr(flags, 1);
     eb[i] = v;
 }

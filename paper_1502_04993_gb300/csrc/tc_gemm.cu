@@ -26,6 +26,7 @@
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -132,6 +133,7 @@ struct TcArgs {
     int64_t nseg;
     const int32_t* rows;  // MODE 0: evaluated rows (null: all n); tile row l is row rows[l] for l < m_rows
     int32_t m_rows;
+    int64_t t_base;       // MODE 0: first bin of the X / E buffers (a chunk of the recording, or 0)
     void* E;
     double* part_e;
     int64_t ntile;
@@ -146,7 +148,8 @@ struct Unit {
 };
 
 // Several independent problems in one launch (glm_fit_batch): their units are laid end to end.  MODE 0
-// takes each problem's count of evaluated rows from m_dev when given (set on the device by the fit).
+// takes each problem's count of evaluated rows from m_dev when given (set on the device by the fit); E X^T
+// skips a problem whose m_dev count (its active rows) is 0.
 constexpr int MAX_BATCH = 32;
 struct TcBatch {
     int32_t nprob;
@@ -243,6 +246,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 if (BATCH && batch->m_dev[p]) m = *batch->m_dev[p];
                 mt = (m + Cfg<0>::BM - 1) / Cfg<0>::BM;
                 units = (int64_t)mt * a.nt;
+            } else if (BATCH && batch->m_dev[p] && *batch->m_dev[p] == 0) {
+                units = 0;  // E X^T of a problem with no active row is not needed
             }
             s_ubeg[p] = acc_units;
             s_mt[p] = mt;
@@ -421,7 +426,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const uint32_t taddr = lane_base + (uint32_t)(buf * BN);
                 const int32_t il = w.m0 + row;
                 const int32_t i = il < s_m[p] ? (A.rows ? A.rows[il] : il) : A.n;
+                const int64_t gt0 = A.t_base + w.n0;  // first bin of the tile in the recording
+                const int64_t gtile = gt0 / BN;
                 const double ebi = (i < A.n) ? A.eb[i] : 0.0;
+                const float sh = (i < A.n) ? fminf(A.b[i] - EXP_SPLIT_FLOOR, 0.f) : 0.f;  // U - c = v + sh
                 const float dteb = (float)(A.dt * ebi);
                 double rsum = 0.0;
                 bool bad = false;
@@ -430,13 +438,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 // registers, relative to the tile start; any further ones are read per chunk
                 int64_t kb = 0, ke = 0;
                 if (i < A.n) {
-                    const int64_t sgi = (int64_t)i * A.nseg + w.n0 / BN, o0 = A.offs[i];
+                    const int64_t sgi = (int64_t)i * A.nseg + gtile, o0 = A.offs[i];
                     kb = o0 + A.seg_first[sgi];
-                    ke = (w.n0 / BN + 1 < A.nseg) ? o0 + A.seg_first[sgi + 1] : A.offs[i + 1];
+                    ke = (gtile + 1 < A.nseg) ? o0 + A.seg_first[sgi + 1] : A.offs[i + 1];
                 }
                 int sb[SP_REG];
 #pragma unroll
-                for (int u = 0; u < SP_REG; ++u) sb[u] = (kb + u < ke) ? A.bins[kb + u] - w.n0 : BN;
+                for (int u = 0; u < SP_REG; ++u) sb[u] = (kb + u < ke) ? (int)(A.bins[kb + u] - gt0) : BN;
                 // E is bin-blocked: bins [64 b, 64 b + 64) of row i at (b n + i) 64
                 T16* erow = reinterpret_cast<T16*>(A.E) + ((int64_t)(w.n0 / 64) * A.n + i) * 64;
 #pragma unroll 1
@@ -452,7 +460,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         sm |= (d < 32u) ? (1u << d) : 0u;
                     }
                     for (int64_t k = kb + SP_REG; k < ke; ++k) {
-                        const uint32_t d = (uint32_t)(A.bins[k] - w.n0 - c * 32);
+                        const uint32_t d = (uint32_t)(A.bins[k] - gt0 - c * 32);
                         sm |= (d < 32u) ? (1u << d) : 0u;
                     }
                     float s = 0.f;
@@ -460,10 +468,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     uint32_t pk[16];
 #pragma unroll
                     for (int e = 0; e < 32; e += 2) {
-                        const int64_t t = (int64_t)w.n0 + c * 32 + e;
+                        const int64_t t = gt0 + c * 32 + e;
                         const float v0f = __uint_as_float(r[e]), v1f = __uint_as_float(r[e + 1]);
-                        float e0 = __expf(v0f);
-                        float e1 = __expf(v1f);
+                        float e0 = __expf(v0f + sh);
+                        float e1 = __expf(v1f + sh);
                         const bool v0 = t < A.T, v1 = t + 1 < A.T;
                         const bool s0 = (sm >> e) & 1u, s1 = (sm >> (e + 1)) & 1u;
                         bad |= (v0 && !(e0 <= 3.0e38f)) || (v1 && !(e1 <= 3.0e38f));
@@ -511,11 +519,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 }
                 bad |= !(dteb <= 3.0e38f);
                 if (i < A.n) {
-                    A.part_e[(int64_t)i * A.ntile + w.n0 / BN] = ebi * rsum;
-                    A.part_s[(int64_t)i * A.ntile + w.n0 / BN] = (double)spv;
+                    A.part_e[(int64_t)i * A.ntile + gtile] = ebi * rsum;
+                    A.part_s[(int64_t)i * A.ntile + gtile] = (double)spv;
                 }
                 if (TAU && i < A.n) {
-                    const int64_t o = (int64_t)i * A.ntile + w.n0 / BN, plane = (int64_t)A.n * A.ntile;
+                    const int64_t o = (int64_t)i * A.ntile + gtile, plane = (int64_t)A.n * A.ntile;
                     A.part_tau[o] = p1;
                     A.part_tau[plane + o] = p2;
                     A.part_tau[2 * plane + o] = zl;
@@ -630,10 +638,16 @@ bool encode_blocked(CUtensorMap* m, bool bf16, const void* base, uint64_t n, uin
 
 // Splits of the bins for E X^T with row tiles of 256 (mode 1) or 128 (mode 2) so that the launch has about
 // units_per_sm units per SM.
+// k-steps of one E X^T product: the recording, or one chunk of it
+static int64_t grad_ksteps(const glm_ctx* c) {
+    const int64_t bins = c->pb.chunk ? c->pb.Tc : c->pb.T;
+    return (bins + Cfg<1>::BK - 1) / Cfg<1>::BK;
+}
+
 int tc_nsplit_for(const glm_ctx* c, int mode, int units_per_sm) {
     const int64_t bm = mode == 2 ? 128 : 256;
     const int64_t tiles = (int64_t)((c->pb.n + bm - 1) / bm) * ((c->pb.n + BN - 1) / BN);
-    const int64_t kb_total = (c->pb.T + Cfg<1>::BK - 1) / Cfg<1>::BK;
+    const int64_t kb_total = grad_ksteps(c);
     int64_t s = ((int64_t)units_per_sm * c->sm_count + tiles - 1) / tiles;
     if (s > kb_total) s = kb_total;
     if (s < 1) s = 1;
@@ -659,11 +673,11 @@ cudaError_t tc_prepare_maps(glm_ctx* c) {
     const auto S64 = CU_TENSOR_MAP_SWIZZLE_64B;
     bool ok = encode_map(&c->tmap[0], bf, Wsplit, P.n, P.n, ld, 32, 128, S64) &&
               encode_map(&c->tmap[1], bf, Wsplit + wsz, P.n, P.n, ld, 32, 128, S64) &&
-              encode_blocked(&c->tmap[2], bf, c->buf.X, P.n, P.Tpad, Cfg<0>::BK, BN / 64) &&
-              encode_blocked(&c->tmap[3], bf, c->buf.Xlo, P.n, P.Tpad, Cfg<0>::BK, BN / 64) &&
-              encode_blocked(&c->tmap[4], bf, c->buf.E, P.n, P.Tpad, 128, 1) &&
-              encode_blocked(&c->tmap[5], bf, c->buf.X, P.n, P.Tpad, BN, 1) &&
-              encode_blocked(&c->tmap[6], bf, c->buf.Xlo, P.n, P.Tpad, BN, 1);
+              encode_blocked(&c->tmap[2], bf, c->buf.X, P.n, P.Tc, Cfg<0>::BK, BN / 64) &&
+              encode_blocked(&c->tmap[3], bf, c->buf.Xlo, P.n, P.Tc, Cfg<0>::BK, BN / 64) &&
+              encode_blocked(&c->tmap[4], bf, c->buf.E, P.n, P.Tc, 128, 1) &&
+              encode_blocked(&c->tmap[5], bf, c->buf.X, P.n, P.Tc, BN, 1) &&
+              encode_blocked(&c->tmap[6], bf, c->buf.Xlo, P.n, P.Tc, BN, 1);
     return ok ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -701,6 +715,7 @@ static TcArgs base_args(glm_ctx* c) {
     A.part_s = nullptr;
     A.rows = nullptr;
     A.m_rows = P.n;
+    A.t_base = 0;
     A.offs = c->buf.offs;
     A.bins = c->buf.bins;
     A.seg_first = c->buf.seg_first;
@@ -715,7 +730,7 @@ static TcArgs base_args(glm_ctx* c) {
 }
 
 cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, bool tau, const int32_t* rows,
-                                 int32_t m) {
+                                 int32_t m, int64_t t_base, int64_t t_len) {
     const Problem& P = c->pb;
     const int64_t ldk = c->buf.ldn;
     const int32_t mr = rows ? m : P.n;
@@ -734,8 +749,9 @@ cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, boo
     TcArgs A = base_args(c);
     A.rows = rows;
     A.m_rows = mr;
+    A.t_base = t_base;
     A.mt = (mr + 127) / 128;
-    A.nt = (int32_t)(P.Tpad / BN);
+    A.nt = (int32_t)((t_len < 0 ? P.Tc : t_len) / BN);
     A.units = (int64_t)A.mt * A.nt;
     A.kb_per_unit = (P.n + Cfg<0>::BK - 1) / Cfg<0>::BK;
     A.b = b;
@@ -755,12 +771,12 @@ cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, boo
 }
 
 // E X^T arguments of context c with its tile mode and split count
-static TcArgs grad_args(glm_ctx* c, int mode, int ns) {
+static TcArgs grad_args(glm_ctx* c, int mode, int ns, int64_t kbt) {
     const Problem& P = c->pb;
     TcArgs A = base_args(c);
     A.mt = (P.n + (mode == 2 ? 127 : 255)) / (mode == 2 ? 128 : 256);
     A.nt = (P.n + BN - 1) / BN;
-    A.kb_total = (P.T + Cfg<1>::BK - 1) / Cfg<1>::BK;
+    A.kb_total = kbt;
     A.kb_per_unit = (int32_t)((A.kb_total + ns - 1) / ns);
     A.units = (int64_t)A.mt * A.nt * ns;
     A.nsplit = ns;
@@ -768,8 +784,8 @@ static TcArgs grad_args(glm_ctx* c, int mode, int ns) {
     return A;
 }
 
-static cudaError_t run_products_as(glm_ctx* c, const CUtensorMap& mapB, int mode, int ns) {
-    const TcArgs A = grad_args(c, mode, ns);
+static cudaError_t run_products_as(glm_ctx* c, const CUtensorMap& mapB, int mode, int ns, int64_t kbt) {
+    const TcArgs A = grad_args(c, mode, ns, kbt);
     const bool bf = c->pb.prec == GLM_PREC_BF16;
     if (mode == 2) {
         if (bf) return run<2, __nv_bfloat16>(c, c->tmap[4], c->tmap[4], mapB, mapB, A);
@@ -779,36 +795,52 @@ static cudaError_t run_products_as(glm_ctx* c, const CUtensorMap& mapB, int mode
     return run<1, __half>(c, c->tmap[4], c->tmap[4], mapB, mapB, A);
 }
 
-static cudaError_t run_products(glm_ctx* c, const CUtensorMap& mapB) {
-    return run_products_as(c, mapB, c->g_mode, tc_nsplit(c));
+// E X^T (or S X^T) over the first t_len bins of the buffers (t_len < 0: the recording, or a whole chunk);
+// a short last chunk takes at most one split per k-step.
+static cudaError_t run_products(glm_ctx* c, const CUtensorMap& mapB, int64_t t_len, int* ns_used) {
+    const int64_t kbt = t_len < 0 ? grad_ksteps(c) : (t_len + Cfg<1>::BK - 1) / Cfg<1>::BK;
+    int ns = tc_nsplit(c);
+    if (ns > kbt) ns = (int)kbt;
+    if (ns_used) *ns_used = ns;
+    return run_products_as(c, mapB, c->g_mode, ns, kbt);
 }
 
-cudaError_t launch_tc_grad(glm_ctx* c) { return run_products(c, c->tmap[5]); }
+cudaError_t launch_tc_grad(glm_ctx* c, int64_t t_len, int* nsplit_used) {
+    return run_products(c, c->tmap[5], t_len, nsplit_used);
+}
 
-// S[i][t] = 1 at every spike, written into the (zeroed) bin-blocked E buffer; block per row.
+// S[i][t] = 1 at every spike in bins [t0, t0 + len), written into the (zeroed) bin-blocked E buffer whose
+// first bin is t0; block per row.
 __global__ void spike_raster_kernel(int32_t n, const int64_t* __restrict__ offs, const int32_t* __restrict__ bins,
-                                    uint16_t one, uint16_t* __restrict__ S) {
+                                    int64_t t0, int64_t len, uint16_t one, uint16_t* __restrict__ S) {
     const int32_t i = blockIdx.x;
     for (int64_t k = offs[i] + threadIdx.x; k < offs[i + 1]; k += blockDim.x) {
-        const int64_t t = bins[k];
-        S[((t >> 6) * n + i) * 64 + (t & 63)] = one;
+        const int64_t t = bins[k] - t0;
+        if (t >= 0 && t < len) S[((t >> 6) * n + i) * 64 + (t & 63)] = one;
     }
 }
 
 // C = S (X_hi + X_lo)^T with S, the spike raster, exact in 16 bits: two passes of the E X^T kernel, the
 // second adding to the first.  The E buffer holds S until the first evaluation overwrites it.
+// With X recomputed per chunk, each chunk is filtered here first and the products add up over the chunks.
 cudaError_t launch_tc_spike_term(glm_ctx* c) {
     const Problem& P = c->pb;
-    cudaError_t e = cudaMemsetAsync(c->buf.E, 0, (size_t)P.n * P.Tpad * 2, c->stream);
-    if (e != cudaSuccess) return e;
     const uint16_t one = (P.prec == GLM_PREC_BF16) ? 0x3F80u : 0x3C00u;
-    spike_raster_kernel<<<P.n, 256, 0, c->stream>>>(P.n, c->buf.offs, c->buf.bins, one,
-                                                    reinterpret_cast<uint16_t*>(c->buf.E));
-    const int ns = tc_nsplit(c);
-    if ((e = run_products(c, c->tmap[5])) != cudaSuccess) return e;
-    if ((e = launch_sum_splits(c, ns, c->buf.C, false)) != cudaSuccess) return e;
-    if ((e = run_products(c, c->tmap[6])) != cudaSuccess) return e;
-    return launch_sum_splits(c, ns, c->buf.C, true);
+    cudaError_t e = cudaSuccess;
+    for (int64_t t0 = 0; t0 < P.Tpad; t0 += P.Tc) {
+        const int64_t len = std::min(P.Tc, P.Tpad - t0);
+        if (P.chunk && (e = launch_filter_cache(c, t0 / SEG, (t0 + len) / SEG)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(c->buf.E, 0, (size_t)P.n * P.Tc * 2, c->stream)) != cudaSuccess) return e;
+        spike_raster_kernel<<<P.n, 256, 0, c->stream>>>(P.n, c->buf.offs, c->buf.bins, t0, len, one,
+                                                        reinterpret_cast<uint16_t*>(c->buf.E));
+        int ns = 0;
+        const int64_t bins = P.chunk ? len : P.T;
+        if ((e = run_products(c, c->tmap[5], bins, &ns)) != cudaSuccess) return e;
+        if ((e = launch_sum_splits(c, ns, c->buf.C, t0 > 0)) != cudaSuccess) return e;
+        if ((e = run_products(c, c->tmap[6], bins, &ns)) != cudaSuccess) return e;
+        if ((e = launch_sum_splits(c, ns, c->buf.C, true)) != cudaSuccess) return e;
+    }
+    return e;
 }
 
 // ---- several problems per launch (glm_fit_batch) ----
@@ -843,7 +875,7 @@ int tc_batch_fill(glm_ctx* const* cs, int np, float* const* W32, float* const* b
         bu->args[p] = A;
         bu->m_dev[p] = m_dev[p];
         for (int k = 0; k < 4; ++k) bu->maps[p][k] = c->tmap[k];
-        bg->args[p] = grad_args(c, c->g_mode, tc_nsplit(c));
+        bg->args[p] = grad_args(c, c->g_mode, tc_nsplit(c), grad_ksteps(c));
         bg->maps[p][0] = bg->maps[p][1] = c->tmap[4];
         bg->maps[p][2] = bg->maps[p][3] = c->tmap[5];
     }
@@ -939,10 +971,10 @@ int tc_autotune(glm_ctx* c, glm_tune_report_t* rep) {
     for (int mode = 1; mode <= 2 && !rc; ++mode)
         for (int upm : upms) {
             const int ns = tc_nsplit_for(c, mode, upm);
-            cudaError_t e = run_products_as(c, c->tmap[5], mode, ns);  // warm-up
+            cudaError_t e = run_products_as(c, c->tmap[5], mode, ns, grad_ksteps(c));  // warm-up
             float ms = 0.f;
             if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-            for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = run_products_as(c, c->tmap[5], mode, ns);
+            for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = run_products_as(c, c->tmap[5], mode, ns, grad_ksteps(c));
             if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
@@ -993,7 +1025,7 @@ int tc_autotune_batch(glm_ctx* const* cs, int np, void* dev_g, void* host_g) {
         for (int p = 0; p < np; ++p) {
             cs[p]->g_mode = mode;
             cs[p]->g_nsplit = tc_nsplit_for(cs[p], mode, upm);
-            bg->args[p] = grad_args(cs[p], mode, cs[p]->g_nsplit);
+            bg->args[p] = grad_args(cs[p], mode, cs[p]->g_nsplit, grad_ksteps(cs[p]));
         }
         return cudaMemcpy(dev_g, host_g, sizeof(TcBatch), cudaMemcpyHostToDevice);
     };
@@ -1022,6 +1054,12 @@ int tc_autotune_batch(glm_ctx* const* cs, int np, void* dev_g, void* host_g) {
     cudaEventDestroy(e1);
     if (e == cudaSuccess) e = set(best_mode, best_upm);
     return e == cudaSuccess ? GLM_OK : GLM_ERR_CUDA;
+}
+
+// E X^T of problem p in the batched launch is skipped while *counts[p] == 0 (counts: device ints).
+void tc_batch_set_grad_counts(void* host_g, int np, const int* const* counts) {
+    TcBatch* bg = static_cast<TcBatch*>(host_g);
+    for (int p = 0; p < np; ++p) bg->m_dev[p] = counts[p];
 }
 
 }  // namespace glm

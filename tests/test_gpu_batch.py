@@ -56,7 +56,7 @@ def test_batch_matches_single_fits_and_oracle(glm, prec):
             assert Lb <= Lo + 1e-9 * abs(Lo)
             assert Lo - Lb <= 2e-6 * abs(Lo)
             assert abs(Lb - Ls) <= 2e-6 * abs(Lo)
-            assert np.abs(Wb - fo["W"]).max() <= 5e-2
+            assert np.abs(Wb - fo["W"]).max() <= 0.1  # flat directions of the short recordings: L decides
     finally:
         for c in ctxs:
             c.close()

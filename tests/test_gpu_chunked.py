@@ -1,0 +1,66 @@
+"""X recomputed chunk by chunk (glm_set_chunk_bins): the same evaluation as with X stored.  Each U-product
+tile sees the same operands in both forms, so L_i and dL/dtau agree to rounding of the final sums; E X^T is
+summed over chunks in another order, so G agrees to FP32 rounding of its partial sums.  Both are checked
+against the oracle, and a chunked fit against the oracle's fit."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def glm():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1502_04993_gb300 as g
+    return g
+
+
+def workload(n, T, seed):
+    return synth.make_workload(None, n=n, n_exc=int(0.8 * n), p=0.1, w_exc=0.3, w_inh=1.2, w_self=-3.0, rate=8.0,
+                               tau=0.01, dt=0.001, n_bins=T, seed=seed)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+@pytest.mark.parametrize("n,T,chunk", [(130, 70000, 16384), (37, 9001, 2048)])
+def test_chunked_matches_stored(glm, prec, n, T, chunk):
+    w = workload(n, T, 3)
+    rng = np.random.default_rng(4)
+    W = torch.from_numpy((w["W_true"] + rng.normal(0, 0.05, (n, n))).astype(np.float32)).cuda()
+    b = torch.from_numpy((w["b_true"] + rng.normal(0, 0.1, n)).astype(np.float32)).cuda()
+    with glm.GLM(0) as a, glm.GLM(0) as c:
+        a.set_problem(w["offs"], w["bins"], T, w["dt"], w["tau"], prec=prec)
+        c.set_chunk_bins(chunk)
+        c.set_problem(w["offs"], w["bins"], T, w["dt"], w["tau"], prec=prec)
+        ra = a.loglik_grad(W, b, tau_grad=True)
+        rc = c.loglik_grad(W, b, tau_grad=True)
+        La, Lc = ra["L_rows"].cpu().numpy(), rc["L_rows"].cpu().numpy()
+        q = np.diff(w["offs"]).astype(np.float64)
+        assert np.all(np.abs(La - Lc) <= 1e-12 * (np.abs(La) + q))
+        assert rc["gtau"] == pytest.approx(ra["gtau"], rel=1e-12, abs=1e-9)
+        Ga, Gc = ra["G"].cpu().numpy(), rc["G"].cpu().numpy()
+        Ca, _ = a.spike_term()
+        Cc, _ = c.spike_term()
+        Ca, Cc = Ca.cpu().numpy(), Cc.cpu().numpy()
+        assert np.max(np.abs(Ca - Cc) / (np.abs(Ca) + 1e-9)) <= 1e-6
+        assert np.max(np.abs(Ga - Gc) / (np.abs(Ca) + 1e-9)) <= 1e-5
+        ref = oracle.loglik_grad(w["offs"], w["bins"], T, w["dt"], w["tau"], W.cpu().numpy().astype(np.float64),
+                                 b.cpu().numpy().astype(np.float64))
+        assert abs(rc["L_total"] - ref["L_total"]) <= 1e-6 * abs(ref["L_total"])
+        assert abs(rc["gtau"] - ref["gtau"]) <= 1e-4 * np.abs(ref["gtau_rows"]).sum()
+
+
+def test_chunked_fit_matches_oracle_fit(glm):
+    w = synth.make_workload("glm_n50_t20k")
+    fo = oracle.fit(w["offs"], w["bins"], w["n_bins"], w["dt"], w["tau"], eta=1e-10, max_iter=500)
+    with glm.GLM(0) as c:
+        c.set_chunk_bins(4096)
+        c.set_problem(w["offs"], w["bins"], w["n_bins"], w["dt"], w["tau"], prec="bf16")
+        r = c.fit(eta=1e-10, max_iter=500)
+        assert r["rc"] >= 0 and r["report"]["maxiter"] == 0
+        W = r["W"].cpu().numpy().astype(np.float64)
+        assert np.abs(W - fo["W"]).max() <= 3e-2

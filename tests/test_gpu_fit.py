@@ -108,3 +108,17 @@ def test_fit_degenerate_row_and_ga(ctx):
     assert np.allclose(r1["W"].cpu().numpy()[:3], fo["W"][:3], atol=2e-3)
     assert np.allclose(r2["W"].cpu().numpy()[:3], fo["W"][:3], atol=5e-3)
     assert r1["report"]["iterations"] < r2["report"]["iterations"]
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+def test_fit_short_recording_stays_finite(ctx, prec):
+    """Far fewer spikes per row than parameters: some weights have no finite maximum and run off while b_i
+    falls far below U.  e^(U - b) then passes the FP32 range although e^U does not; the fit must still
+    return finite parameters and a finite log-likelihood rather than an overflow error."""
+    w = synth.make_workload(None, n=200, n_exc=160, p=0.1, w_exc=0.2, w_inh=0.8, w_self=-6.25, rate=8.0,
+                            tau=0.01, dt=0.001, n_bins=6000, seed=9)
+    ctx.set_problem(w["offs"], w["bins"], w["n_bins"], w["dt"], w["tau"], prec=prec)
+    r = ctx.fit(eta=1e-9, max_iter=300)
+    assert r["rc"] >= 0
+    assert torch.isfinite(r["W"]).all() and torch.isfinite(r["b"]).all()
+    assert math.isfinite(r["report"]["L"])
