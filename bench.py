@@ -188,7 +188,7 @@ def run_reference(args):
 
 def run_batch(args, glm, device, prec):
     """Uneven recordings (N ~ U{100..1500}, T ~ U(300, 3600) s x t_scale, 3-12 Hz) fitted one after another
-    and then together with glm_fit_batch; aggregate neuron*bins/s counts N T per evaluation of each fit."""
+    and then together with glm_fit_batch, to the same stopping rule; the speedup is the ratio of wall times."""
     import torch
     import synth
     specs = synth.batch_workloads(args.batch, t_scale=args.batch_t_scale)
@@ -207,12 +207,10 @@ def run_batch(args, glm, device, prec):
         res, rc = glm.fit_batch(ctxs, **kw)
         torch.cuda.synchronize(device)
         t_bat = time.perf_counter() - t0
-        units_seq = sum(w["n"] * w["n_bins"] * r["evaluations"] for w, r in zip(recs, seq))
-        units_bat = sum(w["n"] * w["n_bins"] * r["report"]["evaluations"] for w, r in zip(recs, res))
         return {"recordings": len(recs), "t_scale": args.batch_t_scale,
                 "n": [w["n"] for w in recs], "n_bins": [w["n_bins"] for w in recs],
                 "sequential_s": t_seq, "batched_s": t_bat, "speedup": t_seq / t_bat, "status": rc,
-                "sequential_neuron_bins_per_s": units_seq / t_seq, "batched_neuron_bins_per_s": units_bat / t_bat,
+                "neuron_bins": sum(w["n"] * w["n_bins"] for w in recs),
                 "iterations_max": max(r["report"]["iterations"] for r in res),
                 "L_sequential": sum(r["L"] for r in seq), "L_batched": sum(r["report"]["L"] for r in res)}
     finally:
@@ -281,6 +279,16 @@ def main():
         dist.barrier()
     value = job_throughput(n, T, args.steps, ws, ms / 1000.0)
 
+    # ---- the evaluation alone, X already filtered (what every fit iteration repeats) ----
+    torch.cuda.synchronize(device)
+    ev2, ev3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev2.record(stream)
+    for _ in range(args.steps):
+        ctx.loglik_grad(W, b, total=False, out=out)
+    ev3.record(stream)
+    torch.cuda.synchronize(device)
+    ms_eval = max_over_ranks(ev2.elapsed_time(ev3), device)
+
     # ---- end to end through the public API from host buffers ----
     k2 = args.e2e_steps or max(1, min(args.steps, 5))
     W_h = torch.from_numpy(w["W_true"].astype(np.float32)).pin_memory()
@@ -334,7 +342,12 @@ def main():
         roof = {"bound": "hbm", "achieved": nbytes / per_launch_s / 1e9, "peak": peak, "unit": "GB/s",
                 "peak_source": f"{peak_src} hbm_gbs"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    # DRAM bytes per launch of the dominant kernel from one ncu capture (dram__bytes_read.sum +
+    # dram__bytes_write.sum), N = 1000 x 200 000 bins, scaled to the launch by its neuron-bins (the traffic
+    # of these kernels grows in proportion: X read once, the rates written once); None for kernels not captured
+    traffic_per_unit = {("u_epilogue", "bf16"): (815.832576e6 + 378.606336e6) / (1000 * 200000)}
+    tpu = traffic_per_unit.get((name, prec))
+    roof["traffic"] = tpu * n * T if tpu is not None else None
     roof["kernel"] = name
     roof["ms_per_launch"] = tot_ms / cnt
 
@@ -348,6 +361,9 @@ def main():
         "e2e": {"value": job_throughput(n, T, k2, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "steps": k2},
         "gpu_launches": int(launches),
+        "x_cached": {"value": job_throughput(n, T, args.steps, ws, ms_eval / 1000.0), "unit": UNIT,
+                     "ms_per_eval": ms_eval / args.steps,
+                     "what": "glm_loglik_grad with gradient on the filtered X already in HBM (one fit evaluation)"},
         "kernel_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
         "roofline": roof,
         "clocks": clk,

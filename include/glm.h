@@ -175,6 +175,10 @@ typedef struct {
                              its line search is declared stalled: smaller gains are not resolved by the
                              evaluation.  < 0 (default): 1e-13 for GLM_PREC_F32, 1e-10 for BF16/F16;
                              0 disables the test. */
+    double alpha;         /* smooth l1 penalty (Sec. 2.5, Eq. 16-17): maximise L_i - alpha sum_{j != i}
+                             sqrt(W_ij^2 + eps); the bias and the self weight are not penalised.  0 (default):
+                             plain maximum likelihood */
+    double eps;           /* epsilon of the smooth l1 form, > 0 (default 1e-6) */
 } glm_fit_opts_t;
 
 typedef struct {
@@ -214,8 +218,22 @@ int glm_fit(glm_ctx* ctx, const glm_fit_opts_t* opts, float* W_dev, float* b_dev
 int glm_fit_batch(glm_ctx* const* ctxs, int32_t n_prob, const glm_fit_opts_t* opts, float* const* W_dev,
                   float* const* b_dev, int8_t* const* row_status_host, glm_fit_report_t* reports);
 
+/* Cross-validation of the l1 penalty (Sec. 2.5) and of the kernel time constant (Sec. 3.2): for every tau in
+ * taus and every alpha in alphas, fit W, b on ctx_train (glm_fit with opts and that alpha) and evaluate the
+ * log-likelihood of the fit on ctx_valid, a recording of the same neurons over other bins (e.g. the second
+ * half of one recording).  taus: n_tau values (> 0), or NULL with n_tau = 1 to keep both problems' tau;
+ * alphas: n_alpha values >= 0, fitted in the order given, each fit starting from the previous one (an
+ * ascending list keeps every start close).  L_valid_host: optional double[n_tau * n_alpha], index
+ * k_tau * n_alpha + k_alpha; best_host: optional int32[2] receiving (k_tau, k_alpha) of the largest
+ * validation log-likelihood; W_best_dev (float[n*n]) and b_best_dev (float[n]) receive the fit there.  Both
+ * contexts hold problems of the same n and precision on the same device; their tau is left at the last
+ * value tried.  Errors: as glm_fit and glm_loglik_grad, INVALID_ARG for mismatched problems. */
+int glm_cross_validate(glm_ctx* ctx_train, glm_ctx* ctx_valid, const glm_fit_opts_t* opts, const double* alphas,
+                       int32_t n_alpha, const double* taus, int32_t n_tau, double* L_valid_host, int32_t* best_host,
+                       float* W_best_dev, float* b_best_dev);
+
 /* Recompute X chunk by chunk instead of storing it, for recordings whose N x n_bins outgrows device memory
- * (SURVEY's config 3 form).  chunk_bins > 0 (rounded up to a multiple of 256) applies to the next
+ * (hour-long recordings of thousands of neurons).  chunk_bins > 0 (rounded up to a multiple of 4096) applies to the next
  * glm_set_problem of a tensor-core precision: the context then holds X_hi, X_lo and the rates for
  * chunk_bins bins only, and every evaluation filters, multiplies and reduces one chunk after the other
  * (the filter runs once per chunk and evaluation, so an evaluation costs one filter pass more).  0

@@ -194,7 +194,9 @@ int oracle_eval_rows(int32_t n, int64_t T, double dt, double tau, const int64_t*
 
 /* ----------------------------------------------------------------------------
  * Per-row fit.  theta = (b_i, W_i1..W_in).  The objective handed to the
- * minimiser is f = -L_i.
+ * minimiser is f = -L_i, or with the smooth l1 penalty of Sec. 2.5 (Eq. 16
+ * with the epsilon-l1 form of Eq. 17) f = -L_i + alpha sum_{j != i}
+ * sqrt(W_ij^2 + eps); the bias and the self weight are not penalised.
  * -------------------------------------------------------------------------- */
 typedef struct {
     int32_t n;
@@ -204,9 +206,11 @@ typedef struct {
     const int32_t* sp; /* spike bins of this row */
     int64_t q;
     double* U;        /* scratch, T */
+    int32_t row;      /* i, for the self weight */
+    double alpha, eps;
 } row_ctx;
 
-/* f = -L_i(theta); if g != NULL also g = -grad L_i */
+/* f = -L_i(theta) (+ penalty); if g != NULL also g = grad f */
 static double row_eval(const row_ctx* c, const double* theta, double* g) {
     const int32_t n = c->n;
     const int64_t T = c->T;
@@ -238,7 +242,16 @@ static double row_eval(const row_ctx* c, const double* theta, double* g) {
             g[1 + j] = -s;
         }
     }
-    return -L;
+    double pen = 0.0;
+    if (c->alpha > 0.0) {
+        for (int32_t j = 0; j < n; ++j) {
+            if (j == c->row) continue;
+            const double w = theta[1 + j], r = sqrt(w * w + c->eps);
+            pen += r;
+            if (g) g[1 + j] += c->alpha * w / r;
+        }
+    }
+    return -L + c->alpha * pen;
 }
 
 static double dot(const double* a, const double* b, int32_t d) {
@@ -256,8 +269,9 @@ static double dot(const double* a, const double* b, int32_t d) {
  */
 int oracle_fit(int32_t n, int64_t T, double dt, double tau, const int64_t* offs, const int32_t* bins,
                int32_t method, int32_t m, int32_t max_iter, double eta, double c1, int32_t max_halvings,
-               double* W, double* b, int32_t* iters, int32_t* status, int32_t n_threads) {
+               double alpha, double eps, double* W, double* b, int32_t* iters, int32_t* status, int32_t n_threads) {
     if (check_spikes(n, T, offs, bins) || !(dt > 0) || !(tau > 0) || !W || !b || !iters || !status) return OR_EINVAL;
+    if (!(alpha >= 0) || !(eps > 0)) return OR_EINVAL;
     if (m < 1 || m > 64 || max_iter < 0 || !(eta >= 0) || !(c1 > 0 && c1 < 1) || max_halvings < 1)
         return OR_EINVAL;
     double* X = (double*)malloc(sizeof(double) * (size_t)n * (size_t)T);
@@ -282,7 +296,7 @@ int oracle_fit(int32_t n, int64_t T, double dt, double tau, const int64_t* offs,
             failed = 1;
             continue;
         }
-        row_ctx c = {n, T, dt, X, bins + offs[i], q, mem};
+        row_ctx c = {n, T, dt, X, bins + offs[i], q, mem, i, alpha, eps};
         double* x = mem + T;
         double* g = x + d;
         double* dir = g + d;

@@ -59,7 +59,8 @@ class ClassifyReport(ctypes.Structure):
 class FitOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int32), ("m", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("eta", ctypes.c_double), ("c1", ctypes.c_double), ("max_halvings", ctypes.c_int32),
-                ("warm_start", ctypes.c_int32), ("gain_floor", ctypes.c_double)]
+                ("warm_start", ctypes.c_int32), ("gain_floor", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("eps", ctypes.c_double)]
 
 
 class FitReport(ctypes.Structure):
@@ -82,6 +83,8 @@ SIGNATURES["glm_fit"] = ([_vp, ctypes.POINTER(FitOpts), _vp, _vp, _vp, ctypes.PO
 SIGNATURES["glm_fit_batch"] = ([_vp, _i32, ctypes.POINTER(FitOpts), _vp, _vp, _vp, ctypes.POINTER(FitReport)], ctypes.c_int)
 SIGNATURES["glm_autotune"] = ([_vp, _vp], ctypes.c_int)
 SIGNATURES["glm_set_chunk_bins"] = ([_vp, _i64], ctypes.c_int)
+SIGNATURES["glm_cross_validate"] = ([_vp, _vp, ctypes.POINTER(FitOpts), _vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp],
+                                     ctypes.c_int)
 SIGNATURES["glm_classify"] =([_vp, _i32, ctypes.POINTER(ClassifyOpts), _vp, _vp, _vp, ctypes.POINTER(ClassifyReport)],
                               ctypes.c_int)
 
@@ -123,7 +126,8 @@ def _ptr(t) -> int | None:
 
 
 def fit_batch(contexts, *, method: str = "lbfgs", m: int = 10, max_iter: int = 500, eta: float = 1e-10,
-              c1: float = 1e-4, max_halvings: int = 40, gain_floor: float = -1.0):
+              c1: float = 1e-4, max_halvings: int = 40, gain_floor: float = -1.0, alpha: float = 0.0,
+              eps: float = 1e-6):
     """Fit the problems of several contexts together (glm_fit_batch): one launch per contraction over all
     problems, one CUDA graph per optimiser iteration.  Returns a list of dict(W, b, status, report), one per
     context, and the call's status code."""
@@ -144,13 +148,56 @@ def fit_batch(contexts, *, method: str = "lbfgs", m: int = 10, max_iter: int = 5
     bp = arr(*[b.data_ptr() for b in bs])
     sp = arr(*[s.ctypes.data for s in sts])
     reps = (FitReport * k)()
-    o = FitOpts({"lbfgs": 0, "ga": 1}[method], m, max_iter, eta, c1, max_halvings, 0, gain_floor)
+    o = FitOpts({"lbfgs": 0, "ga": 1}[method], m, max_iter, eta, c1, max_halvings, 0, gain_floor, alpha, eps)
     rc = lib.glm_fit_batch(hs, k, ctypes.byref(o), wp, bp, sp, reps)
     if rc < 0:
         contexts[0]._check(rc, "glm_fit_batch")
     out = [dict(W=Ws[p], b=bs[p], status=sts[p], report={f: getattr(reps[p], f) for f, _ in FitReport._fields_})
            for p in range(k)]
     return out, rc
+
+
+def split_recording(offs, bins, n_bins: int, t_split: int):
+    """Split a CSR recording at bin t_split into a training part [0, t_split) and a validation part
+    [t_split, n_bins) whose bins are counted from t_split (for glm_cross_validate).  Returns
+    ((offs, bins, t_split), (offs, bins, n_bins - t_split))."""
+    offs = np.ascontiguousarray(offs, dtype=np.int64)
+    bins = np.ascontiguousarray(bins, dtype=np.int32)
+    if not 0 < t_split < n_bins:
+        raise ValueError("t_split must lie inside the recording")
+    n = offs.size - 1
+    rows = np.repeat(np.arange(n), np.diff(offs))
+    early = bins < t_split
+    parts = []
+    for keep, base, length in ((early, 0, t_split), (~early, t_split, n_bins - t_split)):
+        o = np.zeros(n + 1, dtype=np.int64)
+        np.cumsum(np.bincount(rows[keep], minlength=n), out=o[1:])
+        parts.append((o, (bins[keep] - base).astype(np.int32), int(length)))
+    return tuple(parts)
+
+
+def cross_validate(train, valid, alphas, taus=None, **fit_kw):
+    """glm_cross_validate: fit on context `train` for every alpha (and tau), score on context `valid`.
+    Returns dict(L_valid [n_tau x n_alpha], best (k_tau, k_alpha), W, b at the best point)."""
+    lib = load_library()
+    torch = train.torch
+    alphas = np.ascontiguousarray(alphas, dtype=np.float64)
+    tau_arr = None if taus is None else np.ascontiguousarray(taus, dtype=np.float64)
+    n_tau = 1 if tau_arr is None else tau_arr.size
+    L = np.zeros((n_tau, alphas.size))
+    best = np.zeros(2, dtype=np.int32)
+    dev = f"cuda:{train.device}"
+    W = torch.zeros((train.n, train.n), dtype=torch.float32, device=dev)
+    b = torch.zeros(train.n, dtype=torch.float32, device=dev)
+    kw = dict(method="lbfgs", m=10, max_iter=500, eta=1e-10, c1=1e-4, max_halvings=40, gain_floor=-1.0, eps=1e-6)
+    kw.update(fit_kw)
+    o = FitOpts({"lbfgs": 0, "ga": 1}[kw["method"]], kw["m"], kw["max_iter"], kw["eta"], kw["c1"],
+                kw["max_halvings"], 0, kw["gain_floor"], 0.0, kw["eps"])
+    rc = lib.glm_cross_validate(train.h, valid.h, ctypes.byref(o), alphas.ctypes.data, alphas.size,
+                                None if tau_arr is None else tau_arr.ctypes.data, n_tau, L.ctypes.data,
+                                best.ctypes.data, _ptr(W), _ptr(b))
+    train._check(rc, "glm_cross_validate")
+    return dict(L_valid=L, best=(int(best[0]), int(best[1])), W=W, b=b)
 
 
 def classify(W, method: str = "gmm", truth=None, types=None, max_iter: int = 1000, tol: float = 1e-12):
@@ -277,7 +324,8 @@ class GLM:
         return int(self.lib.glm_launch_count(self.h))
 
     def fit(self, W=None, b=None, *, method: str = "lbfgs", m: int = 10, max_iter: int = 500, eta: float = 1e-10,
-            c1: float = 1e-4, max_halvings: int = 40, gain_floor: float = -1.0):
+            c1: float = 1e-4, max_halvings: int = 40, gain_floor: float = -1.0, alpha: float = 0.0,
+            eps: float = 1e-6):
         """Maximum-likelihood W, b of the current problem (glm_fit).  Starts at W = 0, b = log(q / T dt) unless
         W and b are given (warm start).  Returns dict(W, b, status per row, report, rc)."""
         torch = self.torch
@@ -287,7 +335,8 @@ class GLM:
               else torch.zeros((self.n, self.n), dtype=torch.float32, device=dev)).contiguous()
         bd = (b.to(device=dev, dtype=torch.float32).clone() if warm
               else torch.zeros(self.n, dtype=torch.float32, device=dev)).contiguous()
-        o = FitOpts({"lbfgs": 0, "ga": 1}[method], m, max_iter, eta, c1, max_halvings, int(warm), gain_floor)
+        o = FitOpts({"lbfgs": 0, "ga": 1}[method], m, max_iter, eta, c1, max_halvings, int(warm), gain_floor, alpha,
+                    eps)
         rep = FitReport()
         status = np.zeros(self.n, dtype=np.int8)
         rc = self.lib.glm_fit(self.h, ctypes.byref(o), _ptr(Wd), _ptr(bd), status.ctypes.data, ctypes.byref(rep))

@@ -101,7 +101,8 @@ __global__ void seg_carry_kernel(int32_t n, int64_t nseg, double a_seg, double* 
     }
 }
 
-constexpr int CHUNK_SEGS = 16;  // 4096 bins per warp unit
+constexpr int CHUNK_SEGS = 16;  // 4096 bins per warp unit: X is chained in FP32 within a unit and restarted
+                                // from the FP64 carry at every unit start (chunks of X start on unit bounds)
 constexpr int FW_WARPS = 4;
 
 template <typename T16>
@@ -165,10 +166,7 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache_f32_kernel(const _
             const int32_t r = g * 8 + k;
             const uint32_t bits = seg_bits(A.bins, cur[k], end[k], t0, lane);
             float v[8];
-            // every segment starts from its FP64 carry (loaded one segment ahead): X does not depend on where
-            // a chunk or unit starts
-            seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v);
-            xs[k] = (s + 1 < s1 && r < A.n) ? (float)A.seg_carry[(int64_t)r * A.nseg + s + 1] : 0.f;
+            xs[k] = seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v);
             if (r < A.n) {
                 float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(A.X) + (int64_t)r * A.Tpad + tl);
                 dst[0] = make_float4(v[0], v[1], v[2], v[3]);
@@ -232,10 +230,7 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache16_kernel(const __g
             const int32_t r = g * 8 + k;
             const uint32_t bits = seg_bits(A.bins, cur[k], end[k], t0, lane);
             float v[8];
-            // every segment starts from its FP64 carry (loaded one segment ahead): X does not depend on where
-            // a chunk or unit starts
-            seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v);
-            xs[k] = (s + 1 < s1 && r < A.n) ? (float)A.seg_carry[(int64_t)r * A.nseg + s + 1] : 0.f;
+            xs[k] = seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v);
             uint32_t ph[4], pl[4];
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
@@ -290,8 +285,7 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_range_kernel(const __gri
             if (t0 >= te) break;
             const uint32_t bits = seg_bits(A.bins, cur, end, t0, lane);
             float v[8];
-            const float x0 = (s == s0) ? xs : (float)A.seg_carry[(int64_t)r * A.nseg + s];  // FP64 carry per segment
-            seg_scan(K, x0, bits, pl_hi, pl_lo, lane, v);
+            xs = seg_scan(K, xs, bits, pl_hi, pl_lo, lane, v);
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
                 const int64_t t = t0 + 8 * lane + m;
@@ -306,6 +300,63 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_range_kernel(const __gri
             }
         }
     }
+}
+
+// The spike raster S (1 at every spike, 0 elsewhere) in 16 bits, bin-blocked like X, for the tensor-core
+// spike term C = S X^T: one warp per (8 rows, 4096-bin unit), each lane writing its 8 bins of a row as one
+// 16-byte word, so every bin of the buffers is written once (no separate clearing pass).
+__global__ void __launch_bounds__(FW_WARPS * 32) spike_raster16_kernel(const __grid_constant__ FilterArgs A,
+                                                                       uint16_t one) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wg = (int64_t)blockIdx.x * FW_WARPS + (threadIdx.x >> 5);
+    const int64_t c = wg / A.ngroups;
+    const int32_t g = (int32_t)(wg % A.ngroups);
+    if (c >= A.nchunks) return;
+    const int64_t s0 = A.s_begin + c * CHUNK_SEGS;
+    const int64_t s1 = min(s0 + (int64_t)CHUNK_SEGS, A.s_end);
+    uint16_t* S = reinterpret_cast<uint16_t*>(A.X);
+#pragma unroll 1
+    for (int k = 0; k < 8; ++k) {
+        const int32_t r = g * 8 + k;
+        if (r >= A.n) break;
+        int64_t cur = A.offs[r] + A.seg_first[(int64_t)r * A.nseg + s0];
+        const int64_t end = A.offs[r + 1];
+        for (int64_t s = s0; s < s1; ++s) {
+            const int64_t t0 = s * SEG;
+            const uint32_t bits = seg_bits(A.bins, cur, end, t0, lane);
+            uint32_t w[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+                w[p] = (((bits >> (2 * p)) & 1u) ? (uint32_t)one : 0u) |
+                       (((bits >> (2 * p + 1)) & 1u) ? ((uint32_t)one << 16) : 0u);
+            const int64_t tb = t0 + 8 * lane - A.s_begin * SEG;  // bin within the buffer
+            *reinterpret_cast<uint4*>(S + ((tb >> 6) * A.n + r) * 64 + (tb & 63)) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+cudaError_t launch_spike_raster(glm_ctx* c, void* out, int64_t s_begin, int64_t s_end) {
+    const Problem& P = c->pb;
+    FilterArgs A;
+    A.n = P.n;
+    A.T = P.T;
+    A.nseg = P.nseg;
+    A.Tpad = P.Tpad;
+    A.ldn = c->buf.ldn;
+    A.ngroups = (P.n + 7) / 8;
+    A.s_begin = s_begin;
+    A.s_end = s_end;
+    A.nchunks = (s_end - s_begin + CHUNK_SEGS - 1) / CHUNK_SEGS;
+    A.offs = c->buf.offs;
+    A.bins = c->buf.bins;
+    A.seg_carry = c->buf.seg_carry;
+    A.seg_first = c->buf.seg_first;
+    A.X = out;
+    A.Xlo = nullptr;
+    const uint16_t one = (P.prec == GLM_PREC_BF16) ? 0x3F80u : 0x3C00u;
+    const int64_t warps = (int64_t)A.ngroups * A.nchunks;
+    spike_raster16_kernel<<<(unsigned)((warps + FW_WARPS - 1) / FW_WARPS), FW_WARPS * 32, 0, c->stream>>>(A, one);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_carry(glm_ctx* c) {

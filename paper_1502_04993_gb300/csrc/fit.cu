@@ -18,6 +18,9 @@
 //               one, and is stalled otherwise.
 //   stop        |L_i(new) - L_i(old)| / |L_i(old)| < eta
 #include <cuda_runtime.h>
+#include <type_traits>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
 
 #include <chrono>
 #include <cstdlib>
@@ -68,7 +71,14 @@ struct FitState {
     int* counters;   // [4]  active rows, open line searches, rows stopped in this round, rows to evaluate
     const double* qd; // [n]  spike counts
     double floor;     // smallest predicted gain s |g.d| worth testing, relative to |L_i| + q_i
+    double alpha, eps; // smooth l1 penalty alpha sum_{j != i} sqrt(W_ij^2 + eps) (Sec. 2.5); alpha = 0: none
+    double* pen;       // [n]  penalty sum at each row's last trial point
 };
+
+// d/dW of the penalty for theta index k >= 1 (W_i,k-1); the self weight is not penalised
+__device__ __forceinline__ double pen_grad(const FitState& F, int32_t i, int k, double w) {
+    return (F.alpha > 0.0 && k - 1 != i) ? F.alpha * w / sqrt(w * w + F.eps) : 0.0;
+}
 
 __global__ void fit_init_kernel(FitState F, int64_t T, double dt, const double* __restrict__ qd, int warm,
                                 const float* __restrict__ W, const float* __restrict__ b) {
@@ -96,26 +106,37 @@ __global__ void fit_init_kernel(FitState F, int64_t T, double dt, const double* 
 }
 
 // trial point in FP32 for the evaluator: theta + s d for rows with an open or accepted step, theta otherwise
-__global__ void fit_trial_kernel(FitState F, float* __restrict__ W, float* __restrict__ b) {
-    const int32_t i = blockIdx.x;
+__device__ __forceinline__ void fit_trial_body(const FitState& F, int32_t i, float* __restrict__ W,
+                                               float* __restrict__ b) {
+    __shared__ double shp[32];
     const bool move = F.status[i] == ACTIVE && (F.pend[i] || F.acc[i]);
     const double s = move ? F.step[i] : 0.0;
     const double* th = F.theta + (int64_t)i * F.d;
     const double* dr = F.dir + (int64_t)i * F.d;
+    double pen = 0.0;
     for (int k = threadIdx.x; k < F.d; k += blockDim.x) {
-        const float v = (float)(th[k] + s * dr[k]);
+        const double x = th[k] + s * dr[k];
+        const float v = (float)x;
         if (k == 0)
             b[i] = v;
         else
             W[(int64_t)i * F.n + (k - 1)] = v;
+        if (F.alpha > 0.0 && k >= 1 && k - 1 != i) pen += sqrt(x * x + F.eps);
     }
+    if (F.alpha > 0.0) {
+        pen = block_sum(pen, shp);
+        if (threadIdx.x == 0) F.pen[i] = pen;
+    }
+}
+__global__ void fit_trial_kernel(FitState F, float* __restrict__ W, float* __restrict__ b) {
+    fit_trial_body(F, blockIdx.x, W, b);
 }
 
 // Armijo test of every open line search against the rows' trial log-likelihoods
-__global__ void fit_armijo_kernel(FitState F, const double* __restrict__ Ltrial, double c1, int max_halvings) {
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void fit_armijo_body(const FitState& F, int32_t i, const double* __restrict__ Ltrial,
+                                                double c1, int max_halvings) {
     if (i >= F.n || F.status[i] != ACTIVE || !F.pend[i]) return;
-    const double Lt = Ltrial[i];
+    const double Lt = Ltrial[i] - F.alpha * (F.alpha > 0.0 ? F.pen[i] : 0.0);  // penalised (Eq. 16)
     const double s = F.step[i], gd = F.gd[i];
     // f(trial) <= f + c1 s g.d   with f = -L
     if (isfinite(Lt) && -Lt <= -F.Lcur[i] + c1 * s * gd) {
@@ -148,22 +169,25 @@ __global__ void fit_armijo_kernel(FitState F, const double* __restrict__ Ltrial,
     }
     atomicAdd(F.counters + 1, 1);
 }
+__global__ void fit_armijo_kernel(FitState F, const double* __restrict__ Ltrial, double c1, int max_halvings) {
+    fit_armijo_body(F, blockIdx.x * blockDim.x + threadIdx.x, Ltrial, c1, max_halvings);
+}
 
 // accept the steps: theta += s d for accepted rows (block per row)
-__global__ void fit_commit_kernel(FitState F) {
-    const int32_t i = blockIdx.x;
+__device__ __forceinline__ void fit_commit_body(const FitState& F, int32_t i) {
     if (F.status[i] != ACTIVE || !F.acc[i]) return;
     const double s = F.step[i];
     double* th = F.theta + (int64_t)i * F.d;
     const double* dr = F.dir + (int64_t)i * F.d;
     for (int k = threadIdx.x; k < F.d; k += blockDim.x) th[k] += s * dr[k];
 }
+__global__ void fit_commit_kernel(FitState F) { fit_commit_body(F, blockIdx.x); }
 
 // new gradient, curvature pair, stopping rule (block per row)
-__global__ void fit_update_kernel(FitState F, const double* __restrict__ Lnew, const double* __restrict__ G,
-                                  const double* __restrict__ gb, double eta, int max_iter) {
+__device__ __forceinline__ void fit_update_body(const FitState& F, int32_t i, const double* __restrict__ Lnew,
+                                                const double* __restrict__ G, const double* __restrict__ gb,
+                                                double eta, int max_iter) {
     __shared__ double sh[32];
-    const int32_t i = blockIdx.x;
     if (F.status[i] != ACTIVE || !F.acc[i]) return;
     double* g = F.g + (int64_t)i * F.d;
     const double s = F.step[i];
@@ -172,8 +196,9 @@ __global__ void fit_update_kernel(FitState F, const double* __restrict__ Lnew, c
     double* Sv = F.S + ((int64_t)slot * F.n + i) * F.d;
     double* Yv = F.Y + ((int64_t)slot * F.n + i) * F.d;
     double sy = 0.0;
+    const double* th = F.theta + (int64_t)i * F.d;
     for (int k = threadIdx.x; k < F.d; k += blockDim.x) {
-        const double gn = (k == 0) ? -gb[i] : -G[(int64_t)i * F.n + (k - 1)];
+        const double gn = (k == 0) ? -gb[i] : -G[(int64_t)i * F.n + (k - 1)] + pen_grad(F, i, k, th[k]);
         const double y = gn - g[k];
         const double sv = s * dr[k];
         if (F.method == GLM_FIT_LBFGS) {
@@ -192,7 +217,7 @@ __global__ void fit_update_kernel(FitState F, const double* __restrict__ Lnew, c
             else
                 F.hs[i] = (F.hs[i] + 1) % F.m;
         }
-        const double Lold = F.Lcur[i], Ln = Lnew[i];
+        const double Lold = F.Lcur[i], Ln = Lnew[i] - (F.alpha > 0.0 ? F.alpha * F.pen[i] : 0.0);
         F.Lcur[i] = Ln;
         F.gastep[i] = s;
         F.iters[i]++;
@@ -202,21 +227,26 @@ __global__ void fit_update_kernel(FitState F, const double* __restrict__ Lnew, c
             F.status[i] = GLM_ROW_MAXITER;
     }
 }
+__global__ void fit_update_kernel(FitState F, const double* __restrict__ Lnew, const double* __restrict__ G,
+                                  const double* __restrict__ gb, double eta, int max_iter) {
+    fit_update_body(F, blockIdx.x, Lnew, G, gb, eta, max_iter);
+}
 
 // gradient of -L at the start point
 __global__ void fit_grad0_kernel(FitState F, const double* __restrict__ L, const double* __restrict__ G,
                                  const double* __restrict__ gb) {
     const int32_t i = blockIdx.x;
     double* g = F.g + (int64_t)i * F.d;
-    for (int k = threadIdx.x; k < F.d; k += blockDim.x) g[k] = (k == 0) ? -gb[i] : -G[(int64_t)i * F.n + (k - 1)];
-    if (threadIdx.x == 0) F.Lcur[i] = L[i];
+    const double* th = F.theta + (int64_t)i * F.d;
+    for (int k = threadIdx.x; k < F.d; k += blockDim.x)
+        g[k] = (k == 0) ? -gb[i] : -G[(int64_t)i * F.n + (k - 1)] + pen_grad(F, i, k, th[k]);
+    if (threadIdx.x == 0) F.Lcur[i] = L[i] - (F.alpha > 0.0 ? F.alpha * F.pen[i] : 0.0);
 }
 
 // search direction and initial step of every active row (block per row)
-__global__ void fit_direction_kernel(FitState F) {
+__device__ __forceinline__ void fit_direction_body(const FitState& F, int32_t i) {
     __shared__ double sh[32];
     __shared__ double alpha[32];
-    const int32_t i = blockIdx.x;
     if (F.status[i] != ACTIVE) return;
     if (F.pend[i]) {  // a search still open (batched fits): it keeps its direction and step
         if (threadIdx.x == 0) atomicAdd(F.counters + 0, 1);
@@ -300,8 +330,10 @@ __global__ void fit_direction_kernel(FitState F) {
     }
 }
 
+__global__ void fit_direction_kernel(FitState F) { fit_direction_body(F, blockIdx.x); }
+
 // The rows with an open line search, in increasing order (one block; chunked block scan).
-__global__ void fit_compact_kernel(FitState F, int32_t* __restrict__ rows) {
+__device__ __forceinline__ void fit_compact_body(const FitState& F, int32_t* __restrict__ rows) {
     __shared__ int32_t sh[1024];
     const int32_t per = (F.n + blockDim.x - 1) / blockDim.x;
     const int32_t r0 = min((int32_t)threadIdx.x * per, F.n), r1 = min(r0 + per, F.n);
@@ -320,6 +352,7 @@ __global__ void fit_compact_kernel(FitState F, int32_t* __restrict__ rows) {
         if (F.status[i] == ACTIVE && F.pend[i]) rows[pos++] = i;
     if (threadIdx.x == blockDim.x - 1) F.counters[3] = sh[threadIdx.x];  // rows to evaluate
 }
+__global__ void fit_compact_kernel(FitState F, int32_t* __restrict__ rows) { fit_compact_body(F, rows); }
 
 __global__ void fit_write_kernel(FitState F, float* __restrict__ W, float* __restrict__ b) {
     const int32_t i = blockIdx.x;
@@ -360,7 +393,7 @@ int fit_setup(glm_ctx* c, const glm_fit_opts_t* o, float* W, float* b, FitProb* 
     if (!B.fit_mem || B.fit_m != m) {
         if (B.fit_mem) return set_error(c, GLM_ERR_UNSUPPORTED, "glm_fit: the L-BFGS memory cannot change within a problem");
         const size_t nd = (size_t)n * d;
-        const size_t bytes = sizeof(double) * (nd * (3 + 2 * (size_t)m) + (size_t)m * n + 4 * (size_t)n + (size_t)n * n + n + n) +
+        const size_t bytes = sizeof(double) * (nd * (3 + 2 * (size_t)m) + (size_t)m * n + 5 * (size_t)n + (size_t)n * n + n + n) +
                              sizeof(int32_t) * 8 * (size_t)n + sizeof(float) * ((size_t)n * n + n) + 64;
         int rc = ws_alloc_bytes(c, &B.fit_mem, bytes);
         if (rc) return rc;
@@ -375,6 +408,8 @@ int fit_setup(glm_ctx* c, const glm_fit_opts_t* o, float* W, float* b, FitProb* 
     // gains below this fraction of |L_i| + q_i are not resolved by the evaluation (the 16-bit forms carry
     // a gradient error of ~1e-4 of its terms, the plain FP32 form ~1e-9 of L)
     F.floor = o->gain_floor >= 0.0 ? o->gain_floor : (P.prec == GLM_PREC_F32) ? 1e-13 : 1e-10;
+    F.alpha = o->alpha;
+    F.eps = o->eps;
     const size_t nd = (size_t)n * d;
     double* dp = reinterpret_cast<double*>(B.fit_mem);
     F.theta = dp;
@@ -396,6 +431,8 @@ int fit_setup(glm_ctx* c, const glm_fit_opts_t* o, float* W, float* b, FitProb* 
     F.gd = dp;
     dp += n;
     F.gastep = dp;
+    dp += n;
+    F.pen = dp;
     dp += n;
     fp->G = dp;
     dp += (size_t)n * n;
@@ -562,6 +599,160 @@ int fit_run(glm_ctx* c, const glm_fit_opts_t* o, float* W, float* b, int8_t* row
 namespace {
 
 constexpr int GRAPH_ROUNDS = 3;
+constexpr int FB_MAX = 32;
+
+// Every problem of a batched fit, for kernels that run over the rows of all problems at once (device
+// memory).  Global row r belongs to problem p with rbeg[p] <= r < rbeg[p + 1].
+struct FitBatch {
+    int32_t np;
+    int32_t rbeg[FB_MAX + 1];  // rows
+    int64_t ebeg[FB_MAX + 1];  // n x n elements
+    int64_t wbeg[FB_MAX + 1];  // W-split elements (n x ldk)
+    FitState F[FB_MAX];
+    float* W32[FB_MAX];
+    float* b32[FB_MAX];
+    double* Lr[FB_MAX];
+    double* G[FB_MAX];
+    double* gb[FB_MAX];
+    int32_t* rows[FB_MAX];
+    const double* part_e[FB_MAX];
+    const double* part_s[FB_MAX];
+    const double* qd[FB_MAX];
+    const double* C[FB_MAX];
+    const float* part_g[FB_MAX];
+    int64_t ntile[FB_MAX];
+    int32_t nsplit[FB_MAX];
+    double dt[FB_MAX];
+    int* flags[FB_MAX];
+    double* eb[FB_MAX];
+    void* Wsplit[FB_MAX];
+    int64_t ldk[FB_MAX];
+};
+
+__device__ __forceinline__ int fb_prob(const int32_t* beg, int np, int64_t r) {
+    int p = 0;
+    while (p + 1 < np && r >= beg[p + 1]) ++p;
+    return p;
+}
+__device__ __forceinline__ int fb_prob64(const int64_t* beg, int np, int64_t r) {
+    int p = 0;
+    while (p + 1 < np && r >= beg[p + 1]) ++p;
+    return p;
+}
+
+// iteration start: counters of every problem
+__global__ void fb_start_kernel(const FitBatch* __restrict__ B) {
+    const int p = threadIdx.x;
+    if (p < B->np) {
+        int* c = B->F[p].counters;
+        c[0] = c[1] = c[2] = 0;
+    }
+}
+// after a round: the open-search counts and the error flags (a non-finite trial only fails its Armijo test)
+__global__ void fb_round_reset_kernel(const FitBatch* __restrict__ B) {
+    const int p = threadIdx.x;
+    if (p < B->np) {
+        B->F[p].counters[1] = B->F[p].counters[2] = 0;
+        B->flags[p][0] = B->flags[p][1] = 0;
+    }
+}
+__global__ void fb_direction_kernel(const FitBatch* __restrict__ B) {
+    const int p = fb_prob(B->rbeg, B->np, blockIdx.x);
+    fit_direction_body(B->F[p], blockIdx.x - B->rbeg[p]);
+}
+__global__ void fb_trial_kernel(const FitBatch* __restrict__ B) {
+    const int p = fb_prob(B->rbeg, B->np, blockIdx.x);
+    fit_trial_body(B->F[p], blockIdx.x - B->rbeg[p], B->W32[p], B->b32[p]);
+}
+__global__ void fb_compact_kernel(const FitBatch* __restrict__ B) {
+    fit_compact_body(B->F[blockIdx.x], B->rows[blockIdx.x]);
+}
+__global__ void fb_commit_kernel(const FitBatch* __restrict__ B) {
+    const int p = fb_prob(B->rbeg, B->np, blockIdx.x);
+    fit_commit_body(B->F[p], blockIdx.x - B->rbeg[p]);
+}
+__global__ void fb_armijo_kernel(const FitBatch* __restrict__ B, int32_t nrows, double c1, int max_halvings) {
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    const int p = fb_prob(B->rbeg, B->np, r);
+    fit_armijo_body(B->F[p], r - B->rbeg[p], B->Lr[p], c1, max_halvings);
+}
+__global__ void fb_update_kernel(const FitBatch* __restrict__ B, double eta, int max_iter) {
+    const int p = fb_prob(B->rbeg, B->np, blockIdx.x);
+    fit_update_body(B->F[p], blockIdx.x - B->rbeg[p], B->Lr[p], B->G[p], B->gb[p], eta, max_iter);
+}
+// exp(c), c = max(b_i, floor), of every row of every problem (the U product's e^U = e^c e^(U - c))
+__global__ void fb_exp_bias_kernel(const FitBatch* __restrict__ B, int32_t nrows) {
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    const int p = fb_prob(B->rbeg, B->np, r);
+    const int32_t i = r - B->rbeg[p];
+    const float bi = B->b32[p][i];
+    const double v = exp((double)fmaxf(bi, EXP_SPLIT_FLOOR));
+    if (!isfinite(bi) || !(v <= 1e300)) atomicOr(B->flags[p], 1);
+    B->eb[p][i] = v;
+}
+// hi + lo parts of the rows to evaluate (rows[p][l], l < counters[3]) of every problem, packed per problem
+template <typename T16>
+__global__ void fb_split_w_kernel(const FitBatch* __restrict__ B, int64_t total) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int p = fb_prob64(B->wbeg, B->np, e);
+    const FitState& F = B->F[p];
+    const int64_t ldk = B->ldk[p], el = e - B->wbeg[p];
+    const int64_t l = el / ldk, k = el % ldk;
+    if (l >= F.counters[3]) return;
+    const int32_t i = B->rows[p][l];
+    float w = (k < F.n) ? B->W32[p][(int64_t)i * F.n + k] : 0.f;
+    if (!isfinite(w)) atomicOr(B->flags[p], 1);
+    T16* hi = static_cast<T16*>(B->Wsplit[p]);
+    T16* lo = hi + (int64_t)F.n * ldk;
+    T16 h, lw;
+    if constexpr (std::is_same<T16, __nv_bfloat16>::value) {
+        h = __float2bfloat16_rn(w);
+        lw = __float2bfloat16_rn(w - __bfloat162float(h));
+    } else {
+        h = __float2half_rn(w);
+        lw = __float2half_rn(w - __half2float(h));
+    }
+    hi[el] = h;
+    lo[el] = lw;
+}
+// L_i (and with gb the bias gradient) of every row of every problem from the per-tile partials (warp per row)
+__global__ void fb_reduce_rows_kernel(const FitBatch* __restrict__ B, int32_t nrows, bool with_gb) {
+    const int32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= nrows) return;
+    const int p = fb_prob(B->rbeg, B->np, r);
+    const int32_t i = r - B->rbeg[p];
+    const int64_t nt = B->ntile[p];
+    const double* pe = B->part_e[p] + (int64_t)i * nt;
+    const double* ps = B->part_s[p] + (int64_t)i * nt;
+    double integ = 0.0, spk = 0.0;
+    for (int64_t t = lane; t < nt; t += 32) {
+        integ += pe[t];
+        spk += ps[t];
+    }
+    for (int off = 16; off >= 1; off >>= 1) {
+        integ += __shfl_xor_sync(0xffffffffu, integ, off);
+        spk += __shfl_xor_sync(0xffffffffu, spk, off);
+    }
+    if (lane == 0) {
+        const double q = B->qd[p][i];
+        B->Lr[p][i] = q * (double)B->b32[p][i] + spk - B->dt[p] * integ;
+        if (with_gb) B->gb[p][i] = q - B->dt[p] * integ;
+    }
+}
+// G = C - sum over splits of E X^T, every element of every problem
+__global__ void fb_reduce_grad_kernel(const FitBatch* __restrict__ B, int64_t total) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int p = fb_prob64(B->ebeg, B->np, e);
+    const int64_t el = e - B->ebeg[p], nn = B->ebeg[p + 1] - B->ebeg[p];
+    double sum = 0.0;
+    for (int k = 0; k < B->nsplit[p]; ++k) sum += (double)B->part_g[p][k * nn + el];
+    B->G[p][el] = B->C[p][el] - sum;
+}
 
 // rows still active in each problem (block per problem)
 __global__ void count_active_kernel(const int32_t* const* __restrict__ status, const int32_t* __restrict__ nrows,
@@ -611,7 +802,7 @@ int fit_run_batch(glm_ctx* const* cs, int np, const glm_fit_opts_t* o, float* co
         cs[p]->stream = st;
     }
     std::vector<FitProb> fp(np);
-    void *host_u = nullptr, *host_g = nullptr, *dev_u = nullptr, *dev_g = nullptr, *dev_aux = nullptr;
+    void *host_u = nullptr, *host_g = nullptr, *dev_u = nullptr, *dev_g = nullptr, *dev_aux = nullptr, *fb_mem = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int rc = GLM_OK;
@@ -621,6 +812,7 @@ int fit_run_batch(glm_ctx* const* cs, int np, const glm_fit_opts_t* o, float* co
         cudaFree(dev_u);
         cudaFree(dev_g);
         cudaFree(dev_aux);
+        cudaFree(fb_mem);
         std::free(host_u);
         std::free(host_g);
         cudaStreamSynchronize(st);
@@ -683,57 +875,77 @@ int fit_run_batch(glm_ctx* const* cs, int np, const glm_fit_opts_t* o, float* co
     for (int p = 0; p < np && !rc; ++p) rc = eval_status(cs[p]);
     if (rc) return done(rc);
 
-    // one iteration, recorded once
+    // the batch-wide view of every problem, for the kernels that run over all rows at once
+    FitBatch hb;
+    std::memset(static_cast<void*>(&hb), 0, sizeof(hb));
+    hb.np = np;
+    for (int p = 0; p < np; ++p) {
+        glm_ctx* c = cs[p];
+        const int64_t n = c->pb.n;
+        hb.rbeg[p + 1] = hb.rbeg[p] + (int32_t)n;
+        hb.ebeg[p + 1] = hb.ebeg[p] + n * n;
+        hb.wbeg[p + 1] = hb.wbeg[p] + n * c->buf.ldn;
+        hb.F[p] = fp[p].F;
+        hb.W32[p] = fp[p].W32;
+        hb.b32[p] = fp[p].b32;
+        hb.Lr[p] = fp[p].Lr;
+        hb.G[p] = fp[p].G;
+        hb.gb[p] = fp[p].gb;
+        hb.rows[p] = fp[p].eval_rows;
+        hb.part_e[p] = c->buf.part_e;
+        hb.part_s[p] = c->buf.part_s;
+        hb.qd[p] = c->buf.qd;
+        hb.C[p] = c->buf.C;
+        hb.part_g[p] = c->buf.part_g;
+        hb.ntile[p] = c->pb.Tpad / tc_tile_t();
+        hb.nsplit[p] = tc_nsplit(c);
+        hb.dt[p] = c->pb.dt;
+        hb.flags[p] = c->buf.flags;
+        hb.eb[p] = c->buf.eb;
+        hb.Wsplit[p] = c->buf.Wsplit;
+        hb.ldk[p] = c->buf.ldn;
+    }
+    FitBatch* d_fb = nullptr;
+    if ((rc = ck(c0, cudaMalloc(&d_fb, sizeof(FitBatch))))) return done(rc);
+    fb_mem = d_fb;
+    if ((rc = ck(c0, cudaMemcpy(d_fb, &hb, sizeof(FitBatch), cudaMemcpyHostToDevice)))) return done(rc);
+    const int32_t rows_all = hb.rbeg[np];
+    const int64_t nelem = hb.ebeg[np], nw = hb.wbeg[np];
+    const bool bf = c0->pb.prec == GLM_PREC_BF16;
+
+    // one iteration, recorded once: every kernel runs over all problems
     int64_t launches = 0;
     auto enqueue_iteration = [&]() -> int {
         int r;
-        for (int p = 0; p < np; ++p) {
-            FitState& F = fp[p].F;
-            if ((r = ck(c0, cudaMemsetAsync(F.counters, 0, 3 * sizeof(int), st)))) return r;
-            fit_direction_kernel<<<F.n, FT, 0, st>>>(F);
-            ++launches;
-        }
+        fb_start_kernel<<<1, FB_MAX, 0, st>>>(d_fb);
+        fb_direction_kernel<<<rows_all, FT, 0, st>>>(d_fb);
+        launches += 2;
         for (int round = 0; round < GRAPH_ROUNDS; ++round) {
-            for (int p = 0; p < np; ++p) {
-                FitState& F = fp[p].F;
-                fit_trial_kernel<<<F.n, FT, 0, st>>>(F, fp[p].W32, fp[p].b32);
-                fit_compact_kernel<<<1, 1024, 0, st>>>(F, fp[p].eval_rows);
-                launches += 2;
-            }
-            if ((r = ck(c0, launch_tc_u_batch(cs, np, dev_u, W32.data(), b32.data(), rows.data(), mdev.data()))))
-                return r;
-            launches += 2 * np + 1;
-            for (int p = 0; p < np; ++p) {
-                glm_ctx* c = cs[p];
-                FitState& F = fp[p].F;
-                if ((r = ck(c, launch_reduce(c, fp[p].W32, fp[p].b32, fp[p].Lr, nullptr, nullptr, false,
-                                             c->pb.Tpad / tc_tile_t(), tc_nsplit(c)))))
-                    return r;
-                fit_armijo_kernel<<<(F.n + 255) / 256, 256, 0, st>>>(F, fp[p].Lr, o->c1, o->max_halvings);
-                launches += 2;
-                // a non-finite trial only fails the Armijo test
-                if ((r = ck(c, reset_flags(c)))) return r;
-                fp[p].evals++;
-            }
+            fb_trial_kernel<<<rows_all, FT, 0, st>>>(d_fb);
+            fb_compact_kernel<<<np, 1024, 0, st>>>(d_fb);
+            fb_exp_bias_kernel<<<(rows_all + 255) / 256, 256, 0, st>>>(d_fb, rows_all);
+            if (bf)
+                fb_split_w_kernel<__nv_bfloat16><<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(d_fb, nw);
+            else
+                fb_split_w_kernel<__half><<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(d_fb, nw);
+            if ((r = ck(c0, launch_tc_u_batch(c0, dev_u)))) return r;
+            fb_reduce_rows_kernel<<<(rows_all + 7) / 8, 256, 0, st>>>(d_fb, rows_all, false);
+            fb_armijo_kernel<<<(rows_all + 255) / 256, 256, 0, st>>>(d_fb, rows_all, o->c1, o->max_halvings);
+            fb_round_reset_kernel<<<1, FB_MAX, 0, st>>>(d_fb);
+            launches += 8;
+            for (int p = 0; p < np; ++p) fp[p].evals++;
         }
-        for (int p = 0; p < np; ++p) {
-            fit_commit_kernel<<<fp[p].F.n, FT, 0, st>>>(fp[p].F);
-            ++launches;
-        }
+        fb_commit_kernel<<<rows_all, FT, 0, st>>>(d_fb);
         if ((r = ck(c0, launch_tc_grad_batch(c0, dev_g)))) return r;
-        ++launches;
+        fb_reduce_rows_kernel<<<(rows_all + 7) / 8, 256, 0, st>>>(d_fb, rows_all, true);
+        fb_reduce_grad_kernel<<<(unsigned)((nelem + 255) / 256), 256, 0, st>>>(d_fb, nelem);
+        fb_update_kernel<<<rows_all, FT, 0, st>>>(d_fb, o->eta, o->max_iter);
+        count_active_kernel<<<np, 256, 0, st>>>(d_src, d_n, d_cnt);
+        launches += 6;
         for (int p = 0; p < np; ++p) {
-            glm_ctx* c = cs[p];
-            if ((r = ck(c, launch_reduce(c, fp[p].W32, fp[p].b32, fp[p].Lr, fp[p].G, fp[p].gb, true,
-                                         c->pb.Tpad / tc_tile_t(), tc_nsplit(c)))))
-                return r;
-            fit_update_kernel<<<fp[p].F.n, FT, 0, st>>>(fp[p].F, fp[p].Lr, fp[p].G, fp[p].gb, o->eta, o->max_iter);
-            launches += 3;
             fp[p].grads++;
             fp[p].iters++;
         }
-        count_active_kernel<<<np, 256, 0, st>>>(d_src, d_n, d_cnt);
-        ++launches;
         return GLM_OK;
     };
     for (int p = 0; p < np; ++p) cs[p]->prof_on = false;  // no event records inside the graph

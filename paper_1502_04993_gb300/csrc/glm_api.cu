@@ -407,7 +407,8 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
     P.Tpad = P.nseg * SEG;
     P.prec = prec;
     P.chunk = 0;
-    if (tensor && c->chunk_req > 0 && round_up(c->chunk_req, SEG) < P.Tpad) P.chunk = round_up(c->chunk_req, SEG);
+    // chunks start on the filter's 4096-bin units, so X does not depend on the chunking
+    if (tensor && c->chunk_req > 0 && round_up(c->chunk_req, 16 * SEG) < P.Tpad) P.chunk = round_up(c->chunk_req, 16 * SEG);
     P.Tc = P.chunk ? P.chunk : P.Tpad;
     Buffers& B = c->buf;
     const size_t nn = (size_t)n * n;
@@ -542,6 +543,8 @@ void glm_fit_default_opts(glm_fit_opts_t* o) {
     o->max_halvings = 40;
     o->warm_start = 0;
     o->gain_floor = -1.0;
+    o->alpha = 0.0;
+    o->eps = 1e-6;
 }
 
 int glm_fit(glm_ctx* c, const glm_fit_opts_t* opts, float* W, float* b, int8_t* row_status, glm_fit_report_t* rep) {
@@ -553,10 +556,76 @@ int glm_fit(glm_ctx* c, const glm_fit_opts_t* opts, float* W, float* b, int8_t* 
     if (opts) o = *opts;
     if ((o.method != GLM_FIT_LBFGS && o.method != GLM_FIT_GA) || o.m < 1 || o.m > 32 || o.max_iter < 0 ||
         !(o.eta >= 0) || !(o.c1 > 0 && o.c1 < 1) || o.max_halvings < 1 ||
-        std::isnan(o.gain_floor))
+        std::isnan(o.gain_floor) || !(o.alpha >= 0) || !(o.eps > 0))
         return fail(c, GLM_ERR_INVALID_ARG, "bad fit options");
     DeviceGuard g(c->device);
     return glm::fit_run(c, &o, W, b, row_status, rep);
+}
+
+int glm_cross_validate(glm_ctx* tr, glm_ctx* va, const glm_fit_opts_t* opts, const double* alphas, int32_t n_alpha,
+                       const double* taus, int32_t n_tau, double* L_valid, int32_t* best, float* W_best,
+                       float* b_best) {
+    if (!tr || !va || !alphas || n_alpha < 1 || n_tau < 1 || (!taus && n_tau != 1)) return GLM_ERR_INVALID_ARG;
+    if (!tr->has_problem || !va->has_problem) return fail(tr, GLM_ERR_NO_PROBLEM, "no problem set");
+    if (tr->pb.n != va->pb.n || tr->pb.prec != va->pb.prec || tr->device != va->device)
+        return fail(tr, GLM_ERR_INVALID_ARG, "training and validation problems differ in n, precision or device");
+    for (int32_t k = 0; k < n_alpha; ++k)
+        if (!(alphas[k] >= 0)) return fail(tr, GLM_ERR_INVALID_ARG, "alpha must be >= 0");
+    for (int32_t k = 0; taus && k < n_tau; ++k)
+        if (!(taus[k] > 0) || !std::isfinite(taus[k])) return fail(tr, GLM_ERR_INVALID_ARG, "tau must be > 0");
+    glm_fit_opts_t o;
+    glm_fit_default_opts(&o);
+    if (opts) o = *opts;
+    DeviceGuard g(tr->device);
+    const int32_t n = tr->pb.n;
+    float *W = nullptr, *b = nullptr, *Wv = nullptr, *bv = nullptr;
+    double* Lr = nullptr;
+    auto cleanup = [&](int rc) {
+        cudaFree(W);
+        cudaFree(b);
+        cudaFree(Lr);
+        return rc;
+    };
+    if (cudaMalloc(&W, sizeof(float) * (size_t)n * n) != cudaSuccess || cudaMalloc(&b, sizeof(float) * n) != cudaSuccess ||
+        cudaMalloc(&Lr, sizeof(double) * n) != cudaSuccess)
+        return cleanup(fail(tr, GLM_ERR_OOM, "cross-validation work buffers"));
+    Wv = W;
+    bv = b;
+    double best_L = -INFINITY;
+    int32_t bt = -1, ba = -1;
+    for (int32_t kt = 0; kt < n_tau; ++kt) {
+        if (taus) {
+            int rc;
+            if ((rc = glm_prepare(tr, taus[kt])) || (rc = glm_prepare(va, taus[kt]))) return cleanup(rc);
+        }
+        for (int32_t ka = 0; ka < n_alpha; ++ka) {
+            o.alpha = alphas[ka];
+            o.warm_start = ka > 0 ? 1 : 0;  // each alpha starts from the previous fit at this tau
+            const int rf = glm_fit(tr, &o, Wv, bv, nullptr, nullptr);
+            if (rf < 0) return cleanup(rf);
+            double Lt = 0.0;
+            const int re = glm_loglik_grad(va, Wv, bv, Lr, &Lt, nullptr, nullptr, nullptr);
+            if (re < 0) return cleanup(re);
+            if (L_valid) L_valid[(int64_t)kt * n_alpha + ka] = Lt;
+            if (Lt > best_L || bt < 0) {
+                best_L = Lt;
+                bt = kt;
+                ba = ka;
+                if (W_best && cudaMemcpyAsync(W_best, Wv, sizeof(float) * (size_t)n * n, cudaMemcpyDeviceToDevice,
+                                              tr->stream) != cudaSuccess)
+                    return cleanup(fail(tr, GLM_ERR_CUDA, "copy of the best W"));
+                if (b_best && cudaMemcpyAsync(b_best, bv, sizeof(float) * n, cudaMemcpyDeviceToDevice, tr->stream) !=
+                                  cudaSuccess)
+                    return cleanup(fail(tr, GLM_ERR_CUDA, "copy of the best b"));
+            }
+        }
+    }
+    if (best) {
+        best[0] = bt;
+        best[1] = ba;
+    }
+    if (cudaStreamSynchronize(tr->stream) != cudaSuccess) return cleanup(fail(tr, GLM_ERR_CUDA, "synchronise"));
+    return cleanup(GLM_OK);
 }
 
 int glm_set_chunk_bins(glm_ctx* c, int64_t chunk_bins) {
@@ -597,7 +666,8 @@ int glm_fit_batch(glm_ctx* const* cs, int32_t np, const glm_fit_opts_t* opts, fl
     glm_fit_default_opts(&o);
     if (opts) o = *opts;
     if ((o.method != GLM_FIT_LBFGS && o.method != GLM_FIT_GA) || o.m < 1 || o.m > 32 || o.max_iter < 0 ||
-        !(o.eta >= 0) || !(o.c1 > 0 && o.c1 < 1) || o.max_halvings < 1 || std::isnan(o.gain_floor))
+        !(o.eta >= 0) || !(o.c1 > 0 && o.c1 < 1) || o.max_halvings < 1 || std::isnan(o.gain_floor) ||
+        !(o.alpha >= 0) || !(o.eps > 0))
         return fail(c0, GLM_ERR_INVALID_ARG, "bad fit options");
     DeviceGuard g(c0->device);
     return glm::fit_run_batch(cs, np, &o, W, b, row_status, reps);

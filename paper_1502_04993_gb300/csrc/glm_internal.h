@@ -119,6 +119,8 @@ namespace glm {
 cudaError_t launch_carry(glm_ctx* c);
 // segments [s_begin, s_end) into the X buffers (whose first bin is SEG s_begin); s_end < 0: all
 cudaError_t launch_filter_cache(glm_ctx* c, int64_t s_begin = 0, int64_t s_end = -1);
+// the 16-bit spike raster of segments [s_begin, s_end) into a bin-blocked buffer starting at bin SEG s_begin
+cudaError_t launch_spike_raster(glm_ctx* c, void* out, int64_t s_begin, int64_t s_end);
 cudaError_t launch_filter_range(glm_ctx* c, int64_t t0, int64_t t_len, void* out, int64_t ldx, glm_dtype_t dtype);
 cudaError_t launch_spike_term(glm_ctx* c, double* out);
 cudaError_t launch_tau_rows(glm_ctx* c, double* rows);
@@ -157,8 +159,7 @@ void tc_batch_set_grad_counts(void* host_g, int np, const int* const* counts);
 size_t tc_batch_bytes();
 int tc_batch_fill(glm_ctx* const* cs, int np, float* const* W32, float* const* b32, int32_t* const* rows,
                   const int32_t* const* m_dev, void* host_u, void* host_g);
-cudaError_t launch_tc_u_batch(glm_ctx* const* cs, int np, const void* dev_u, float* const* W32, float* const* b32,
-                              int32_t* const* rows, const int32_t* const* m_dev);
+cudaError_t launch_tc_u_batch(glm_ctx* c0, const void* dev_u);
 cudaError_t launch_tc_grad_batch(glm_ctx* c0, const void* dev_g);
 int tc_tile_t();
 cudaError_t launch_total(glm_ctx* c, const double* L_rows, double* out1);

@@ -53,16 +53,16 @@ __device__ __forceinline__ float seg_scan(const ScanConsts& K, float x_seg, uint
                                           float pl_lo, int lane, float out[8]) {
     float z[8];
     float zz = 0.f;
+    z[0] = 0.f;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) z[m] = 0.f;
-    uint32_t bb = bits8;
-    while (bb) {  // usually no spike, rarely more than one, in a lane's 8 bins
-        const int j = __ffs(bb) - 1;
-        bb &= bb - 1;
+    for (int m = 1; m <= 8; ++m) {  // static indices only: the powers stay in the constant bank
+        float acc = 0.f;
 #pragma unroll
-        for (int m = 1; m < 8; ++m)
-            if (m > j) z[m] += K.pr[m - 1 - j];
-        zz += K.pr[7 - j];
+        for (int j = 0; j < m; ++j) acc = fmaf((float)((bits8 >> j) & 1u), K.pr[m - 1 - j], acc);
+        if (m < 8)
+            z[m] = acc;
+        else
+            zz = acc;
     }
     float v = zz;
 #pragma unroll

@@ -809,30 +809,14 @@ cudaError_t launch_tc_grad(glm_ctx* c, int64_t t_len, int* nsplit_used) {
     return run_products(c, c->tmap[5], t_len, nsplit_used);
 }
 
-// S[i][t] = 1 at every spike in bins [t0, t0 + len), written into the (zeroed) bin-blocked E buffer whose
-// first bin is t0; block per row.
-__global__ void spike_raster_kernel(int32_t n, const int64_t* __restrict__ offs, const int32_t* __restrict__ bins,
-                                    int64_t t0, int64_t len, uint16_t one, uint16_t* __restrict__ S) {
-    const int32_t i = blockIdx.x;
-    for (int64_t k = offs[i] + threadIdx.x; k < offs[i + 1]; k += blockDim.x) {
-        const int64_t t = bins[k] - t0;
-        if (t >= 0 && t < len) S[((t >> 6) * n + i) * 64 + (t & 63)] = one;
-    }
-}
-
-// C = S (X_hi + X_lo)^T with S, the spike raster, exact in 16 bits: two passes of the E X^T kernel, the
-// second adding to the first.  The E buffer holds S until the first evaluation overwrites it.
 // With X recomputed per chunk, each chunk is filtered here first and the products add up over the chunks.
 cudaError_t launch_tc_spike_term(glm_ctx* c) {
     const Problem& P = c->pb;
-    const uint16_t one = (P.prec == GLM_PREC_BF16) ? 0x3F80u : 0x3C00u;
     cudaError_t e = cudaSuccess;
     for (int64_t t0 = 0; t0 < P.Tpad; t0 += P.Tc) {
         const int64_t len = std::min(P.Tc, P.Tpad - t0);
         if (P.chunk && (e = launch_filter_cache(c, t0 / SEG, (t0 + len) / SEG)) != cudaSuccess) return e;
-        if ((e = cudaMemsetAsync(c->buf.E, 0, (size_t)P.n * P.Tc * 2, c->stream)) != cudaSuccess) return e;
-        spike_raster_kernel<<<P.n, 256, 0, c->stream>>>(P.n, c->buf.offs, c->buf.bins, t0, len, one,
-                                                        reinterpret_cast<uint16_t*>(c->buf.E));
+        if ((e = launch_spike_raster(c, c->buf.E, t0 / SEG, (t0 + len) / SEG)) != cudaSuccess) return e;
         int ns = 0;
         const int64_t bins = P.chunk ? len : P.T;
         if ((e = run_products(c, c->tmap[5], bins, &ns)) != cudaSuccess) return e;
@@ -883,28 +867,9 @@ int tc_batch_fill(glm_ctx* const* cs, int np, float* const* W32, float* const* b
     return GLM_OK;
 }
 
-// One launch of the U product over every problem's evaluated rows (their count read on the device),
-// after each problem's W split and exp(b).
-cudaError_t launch_tc_u_batch(glm_ctx* const* cs, int np, const void* dev_u, float* const* W32, float* const* b32,
-                              int32_t* const* rows, const int32_t* const* m_dev) {
-    glm_ctx* c0 = cs[0];
-    for (int p = 0; p < np; ++p) {
-        glm_ctx* c = cs[p];
-        const Problem& P = c->pb;
-        const int64_t ldk = c->buf.ldn;
-        const int64_t total = (int64_t)P.n * ldk;
-        const size_t wsz = (size_t)P.n * ldk;
-        if (P.prec == GLM_PREC_BF16) {
-            auto* hi = reinterpret_cast<__nv_bfloat16*>(c->buf.Wsplit);
-            split_w_kernel<__nv_bfloat16><<<(unsigned)((total + 255) / 256), 256, 0, c0->stream>>>(
-                P.n, ldk, W32[p], rows[p], P.n, m_dev[p], hi, hi + wsz, c->buf.flags);
-        } else {
-            auto* hi = reinterpret_cast<__half*>(c->buf.Wsplit);
-            split_w_kernel<__half><<<(unsigned)((total + 255) / 256), 256, 0, c0->stream>>>(
-                P.n, ldk, W32[p], rows[p], P.n, m_dev[p], hi, hi + wsz, c->buf.flags);
-        }
-        launch_exp_bias(c, b32[p]);
-    }
+// One launch of the U product over every problem's evaluated rows (their count read on the device); the
+// W splits and exp(b) of the problems are formed before it (by the caller).
+cudaError_t launch_tc_u_batch(glm_ctx* c0, const void* dev_u) {
     TcArgs Ag = base_args(c0);
     Ag.idesc |= 1u << 16;  // B (X) is N-major
     const TcBatch* b = static_cast<const TcBatch*>(dev_u);

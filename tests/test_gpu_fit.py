@@ -122,3 +122,45 @@ def test_fit_short_recording_stays_finite(ctx, prec):
     assert r["rc"] >= 0
     assert torch.isfinite(r["W"]).all() and torch.isfinite(r["b"]).all()
     assert math.isfinite(r["report"]["L"])
+
+
+@pytest.mark.parametrize("prec,wtol", [("f32", 5e-3), ("bf16", 3e-2)])
+def test_l1_penalised_fit_matches_oracle(ctx, prec, wtol):
+    """Sec. 2.5: the smooth l1 MAP fit (Eq. 16-17) against the oracle's; at the GPU's point the oracle's own
+    gradient balances the penalty, alpha W / sqrt(W^2 + eps), off the diagonal."""
+    w = synth.make_workload("glm_n50_t20k", n_bins=8000)
+    alpha, eps = 2.0, 1e-4
+    fo = oracle.fit(w["offs"], w["bins"], 8000, w["dt"], w["tau"], eta=1e-12, max_iter=1000, alpha=alpha, eps=eps)
+    ctx.set_problem(w["offs"], w["bins"], 8000, w["dt"], w["tau"], prec=prec)
+    r = ctx.fit(eta=1e-12, max_iter=1000, alpha=alpha, eps=eps)
+    assert r["rc"] >= 0 and r["report"]["maxiter"] == 0
+    W = r["W"].cpu().numpy().astype(np.float64)
+    b = r["b"].cpu().numpy().astype(np.float64)
+    assert np.abs(W - fo["W"]).max() <= wtol
+    g = oracle.loglik_grad(w["offs"], w["bins"], 8000, w["dt"], w["tau"], W, b)
+    off = ~np.eye(W.shape[0], dtype=bool)
+    resid = (g["G"] - alpha * W / np.sqrt(W ** 2 + eps))[off]
+    scale = np.abs(g["G"]).max() + alpha
+    assert np.abs(resid).max() <= (2e-3 if prec == "f32" else 5e-2) * scale
+
+
+def test_cross_validation_recovers_tau(glm):
+    """Sec. 3.2 / 2.5: fit on the first 60 % of a recording, score on the rest, over a grid of tau and alpha.
+    The data were generated with tau = 10 ms, which must win; every grid value must equal the oracle's
+    validation log-likelihood at the GPU fit."""
+    w = synth.make_workload("glm_n50_t20k")
+    (tr, va) = glm.split_recording(w["offs"], w["bins"], w["n_bins"], 12000)
+    taus = [0.005, 0.01, 0.02]
+    alphas = [0.0, 0.5, 2.0]
+    with glm.GLM(0) as a, glm.GLM(0) as v:
+        a.set_problem(tr[0], tr[1], tr[2], w["dt"], w["tau"], prec="bf16")
+        v.set_problem(va[0], va[1], va[2], w["dt"], w["tau"], prec="bf16")
+        res = glm.cross_validate(a, v, alphas, taus, eta=1e-10, max_iter=500)
+        L = res["L_valid"]
+        print(L)
+        kt, ka = res["best"]
+        assert taus[kt] == 0.01
+        assert L[kt, ka] == L.max()
+        Lo = oracle.loglik_grad(va[0], va[1], va[2], w["dt"], taus[kt], res["W"].cpu().numpy().astype(np.float64),
+                                res["b"].cpu().numpy().astype(np.float64))["L_total"]
+        assert abs(L[kt, ka] - Lo) <= 1e-6 * abs(Lo)

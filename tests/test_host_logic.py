@@ -1,0 +1,19 @@
+"""Host-side helpers that need no GPU: splitting a recording for cross-validation."""
+import numpy as np
+
+import synth
+
+
+def test_split_recording_conserves_and_rebases():
+    import paper_1502_04993_gb300 as glm
+    w = synth.make_workload("glm_n50_t20k")
+    (a, b) = glm.split_recording(w["offs"], w["bins"], w["n_bins"], 12000)
+    assert a[2] == 12000 and b[2] == w["n_bins"] - 12000
+    assert a[0][-1] + b[0][-1] == w["offs"][-1]
+    n = w["offs"].size - 1
+    for i in range(n):
+        row = w["bins"][w["offs"][i]:w["offs"][i + 1]]
+        ra = a[1][a[0][i]:a[0][i + 1]]
+        rb = b[1][b[0][i]:b[0][i + 1]]
+        assert np.array_equal(np.concatenate([ra, rb + 12000]), row)
+        assert np.all(ra < 12000) and np.all(rb >= 0) and np.all(rb < b[2])

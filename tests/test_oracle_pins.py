@@ -345,3 +345,29 @@ def test_mer_breakdown_counts_by_hand():
     assert (r["exc"]["fp"], r["exc"]["fn"], r["exc"]["nd"]) == (2, 1, 1)
     assert (r["inh"]["fp"], r["inh"]["fn"], r["inh"]["nd"]) == (1, 1, 1)
     assert (r["absent"]["fp"], r["absent"]["fn"]) == (1, 2)
+
+
+def test_l1_penalised_fit_stationarity_and_shrinkage():
+    """Eq. 16-17: at the penalised optimum dL/dW_ij = alpha W_ij / sqrt(W_ij^2 + eps) for j != i, while the
+    self weight and the bias are not penalised (dL/dW_ii = dL/db_i = 0); alpha = 0 is the plain fit; and the
+    off-diagonal weights shrink as alpha grows.  The gradient comes from the evaluation routine, not from
+    the fit's own objective."""
+    w = synth.make_workload("glm_n50_t20k", n_bins=8000)
+    args = (w["offs"], w["bins"], 8000, w["dt"], w["tau"])
+    plain = oracle.fit(*args, eta=1e-13, max_iter=800)
+    zero = oracle.fit(*args, eta=1e-13, max_iter=800, alpha=0.0)
+    assert np.array_equal(plain["W"], zero["W"]) and np.array_equal(plain["b"], zero["b"])
+    eps = 1e-4
+    sums = []
+    for alpha in (0.5, 2.0, 8.0):
+        f = oracle.fit(*args, eta=1e-14, max_iter=2000, alpha=alpha, eps=eps)
+        r = oracle.loglik_grad(*args, f["W"], f["b"])
+        n = f["W"].shape[0]
+        off = ~np.eye(n, dtype=bool)
+        resid = r["G"] - alpha * f["W"] / np.sqrt(f["W"] ** 2 + eps)
+        q = np.diff(w["offs"]).astype(np.float64)
+        assert np.max(np.abs(resid[off])) <= 1e-3 * alpha + 1e-4
+        assert np.max(np.abs(np.diag(r["G"]))) <= 1e-3
+        assert np.all(np.abs(r["gb"]) <= 1e-4 * q + 1e-6)
+        sums.append(np.abs(f["W"][off]).sum())
+    assert sums[0] > sums[1] > sums[2]
