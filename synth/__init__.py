@@ -159,3 +159,23 @@ def batch_workloads(n_rec: int = 24, *, scale: float = 1.0, t_scale: float | Non
         out.append(dict(n=n, n_exc=int(round(0.8 * n)), p=0.1, w_exc=0.2, w_inh=0.8, w_self=-6.25, rate=rate,
                         tau=0.010, dt=0.001, n_bins=n_bins, seed=s))
     return out
+
+
+def continuous_times(offs, bins, dt: float, seed: int) -> np.ndarray:
+    """Off-grid spike times for the continuous-time form: spike k at (bins[k] + u_k) dt with u_k uniform in
+    [0, 1) from a Philox stream keyed by ``seed``.  Rows stay strictly increasing (one spike per bin)."""
+    bins = np.asarray(bins, dtype=np.int64)
+    u = np.random.Generator(np.random.Philox(key=int(seed))).random(len(bins))
+    return (bins.astype(np.float64) + u) * dt
+
+
+def make_ct_workload(name: str | None = None, *, jitter_seed: int = 7, delay: float | None = None,
+                     threads: int = 0, **overrides) -> dict:
+    """A grid workload (``make_workload``) with its spikes moved off the grid (``continuous_times``), on the
+    recording window [0, n_bins dt).  ``delay`` (default one bin, dt) is the uniform transmission delay."""
+    w = make_workload(name, threads=threads, **overrides)
+    w["times"] = continuous_times(w["offs"], w["bins"], w["dt"], jitter_seed)
+    w["t_begin"] = 0.0
+    w["t_end"] = w["n_bins"] * w["dt"]
+    w["delay"] = w["dt"] if delay is None else float(delay)
+    return w
