@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=0,
                     help="also fit this many uneven recordings with glm_fit_batch and one after another")
     ap.add_argument("--batch-t-scale", type=float, default=0.1, help="recording-length scale of --batch")
+    ap.add_argument("--ct-seconds", type=float, default=180.0,
+                    help="also evaluate and fit the continuous-time form on this much of the recording, its spikes "
+                         "moved off the grid (0: off)")
     return ap.parse_args()
 
 
@@ -216,6 +219,87 @@ def run_batch(args, glm, device, prec):
     finally:
         for c in ctxs:
             c.close()
+
+
+def run_ct(args, glm, w, device, stream, prec):
+    """The continuous-time form (event columns, exact interval integrals) on the first args.ct_seconds of the
+    recording with its spikes moved off the grid, against the grid form on the same window: evaluation time,
+    set-up time, U-product roofline, and a fit of each with its misclassification rate."""
+    import numpy as np
+    import torch
+    import synth
+    from oracle.classify import truth_labels  # ground-truth labels from the generating W (no fitting)
+    n, dt, tau = w["n"], w["dt"], w["tau"]
+    nb = min(w["n_bins"], int(round(args.ct_seconds / dt)))
+    offs, bins = w["offs"], w["bins"]
+    cnt = np.array([np.searchsorted(bins[offs[i]:offs[i + 1]], nb) for i in range(n)], dtype=np.int64)
+    offs2 = np.zeros(n + 1, dtype=np.int64)
+    offs2[1:] = np.cumsum(cnt)
+    bins2 = np.concatenate([bins[offs[i]:offs[i] + cnt[i]] for i in range(n)]).astype(np.int32)
+    times = synth.continuous_times(offs2, bins2, dt, 7)
+    W = torch.from_numpy(w["W_true"].astype(np.float32)).cuda(device)
+    b = torch.from_numpy(w["b_true"].astype(np.float32)).cuda(device)
+    out = {"L_rows": torch.empty(n, dtype=torch.float64, device=device),
+           "G": torch.empty((n, n), dtype=torch.float64, device=device),
+           "gb": torch.empty(n, dtype=torch.float64, device=device)}
+    res = {"workload": f"{args.workload}: first {nb * dt:g} s, spikes moved uniformly inside their bins, delay {dt:g} s",
+           "spikes": int(offs2[-1])}
+    k = max(3, args.steps)
+
+    def timed(c):
+        for _ in range(2):
+            c.loglik_grad(W, b, total=False, out=out)
+        torch.cuda.synchronize(device)
+        c.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            c.loglik_grad(W, b, total=False, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        prof = c.profile_read()
+        c.profile(False)
+        return e0.elapsed_time(e1) / k, {kk: v[1] / k for kk, v in prof.items()}
+
+    truth = truth_labels(w["W_true"])
+    ct = glm.GLM(device, stream=stream)
+    gr = glm.GLM(device, stream=stream)
+    try:
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        ct.set_problem_ct(offs2, times, 0.0, nb * dt, tau, dt, prec=prec)
+        torch.cuda.synchronize(device)
+        res["setup_s"] = time.perf_counter() - t0
+        M = ct.columns()
+        ms, kern = timed(ct)
+        peaks, src = measured_peaks()
+        u_ms = kern.get("u_epilogue", float("nan"))
+        ach = 6.0 * n * n * M / (u_ms / 1000.0) / 1e12
+        res.update({"columns": M, "ms_per_eval": ms, "kernel_ms_per_eval": kern,
+                    "neuron_columns_per_s": n * M / (ms / 1000.0),
+                    "recording_seconds_per_s": nb * dt / (ms / 1000.0),
+                    "u_product_roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"],
+                                           "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops"],
+                                           "peak_source": f"{src} bf16_tflops (burst)"}})
+        gr.set_problem(offs2, bins2, nb, dt, tau, prec=prec)
+        gms, _ = timed(gr)
+        res["grid_same_window"] = {"bins": nb, "ms_per_eval": gms}
+        fits = {}
+        Ws = {}
+        for name, c in (("continuous", ct), ("grid", gr)):
+            r = c.fit(eta=args.fit_eta, max_iter=args.fit_max_iter)
+            _, rep = glm.classify(r["W"].cpu().numpy().astype(np.float64), "gmm", truth=truth, types=w["types"])
+            fits[name] = {"seconds": r["report"]["seconds"], "iterations": r["report"]["iterations"],
+                          "evaluations": r["report"]["evaluations"], "mer": rep["mer"]}
+            Ws[name] = r["W"]
+        dW = (Ws["continuous"] - Ws["grid"]).abs()
+        fits["max_abs_W_difference"] = float(dW.max())
+        fits["mean_abs_W_difference"] = float(dW.mean())
+        res["fit"] = fits
+    finally:
+        ct.close()
+        gr.close()
+    return res
 
 
 def main():
@@ -389,6 +473,8 @@ def main():
         line["fit"] = {"eta": args.fit_eta, "max_iter": args.fit_max_iter, "by_precision": fits}
     if args.batch:
         line["batch"] = run_batch(args, glm, device, prec)
+    if args.ct_seconds > 0 and prec != "f32":
+        line["continuous_time"] = run_ct(args, glm, w, device, stream, prec)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, os.cpu_count() or 1)
         line["cpu_baseline"].pop("seconds", None)

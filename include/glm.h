@@ -113,6 +113,42 @@ void glm_destroy(glm_ctx* ctx);
 int glm_set_problem(glm_ctx* ctx, int32_t n, int64_t n_bins, double dt, double tau, const int64_t* offs_host,
                     const int32_t* bins_host, glm_prec_t prec);
 
+/* Continuous-time form of the same model (Sec. 2.3, Eq. 7-14): spike times in seconds, off any grid.
+ * Every spike reaches every neuron after one uniform delay (Sec. 2.4, Eq. 15 with D_ij = delay), so the
+ * potential is U_i(t) = b_i + sum_j W_ij v_j(t), v_j(t) = sum over arrivals e <= t of exp(-(t - e) / tau)
+ * (Eq. 3, 11; an arrival counts at its own time), and L_i = sum_k U_i(t_ik) - int exp(U_i) dt over
+ * [t_begin, t_end) (Eq. 2, 7).  The library cuts the recording at every distinct arrival and spike time
+ * into event columns; the U product runs over the columns, and the integral over each column is the
+ * exact one of Eq. 9-10 (its Ei closed form is evaluated by Gauss-Legendre quadrature in exp(-s/tau),
+ * see glm_ct_interval), with the matching interval weights of Eq. 14 in the gradient.
+ *   n:                 neurons, n >= 1.
+ *   t_begin, t_end:    the recording window in seconds, finite, t_begin < t_end.
+ *   tau:               kernel time constant in seconds, finite and > 0.
+ *   delay:             transmission delay in seconds, finite and >= 0 (0: a spike counts in its own U).
+ *   offs_host:         int64[n + 1] CSR offsets, offs[0] = 0, non-decreasing; offs[n] < 2^30.
+ *   times_host:        double[offs[n]] spike times; row i strictly increasing, each in [t_begin, t_end).
+ *   prec:              GLM_PREC_BF16 or GLM_PREC_F16 (the FP32 form covers the grid only: UNSUPPORTED).
+ * Afterwards glm_prepare, glm_spike_term, glm_loglik_grad (without dL/dtau), glm_fit and
+ * glm_cross_validate work on the columns as they do on bins; glm_filter, glm_fit_batch, the chunked form
+ * and dL/dtau return UNSUPPORTED.  The host arrays may be freed on return.
+ * Errors: INVALID_ARG, UNSORTED_SPIKES, SPIKE_OUT_OF_RANGE, OOM, CUDA, UNSUPPORTED, UNSUPPORTED_ARCH. */
+int glm_set_problem_ct(glm_ctx* ctx, int32_t n, double t_begin, double t_end, double tau, double delay,
+                       const int64_t* offs_host, const double* times_host, glm_prec_t prec);
+
+/* Number of time columns of the current problem: n_bins on the grid, the event columns (distinct
+ * arrival and spike times, plus the column starting at t_begin) in continuous time.
+ * Errors: INVALID_ARG, NO_PROBLEM. */
+int glm_problem_columns(const glm_ctx* ctx, int64_t* n_columns);
+
+/* The two interval integrals of the continuous-time form over one column of length D, for a potential
+ * that relaxes as U(s) = b + u exp(-s / tau) (Eq. 8 between events), with b = 0, computed by the same
+ * FP32 code as the U-product epilogue:
+ *   F = int_0^D exp(u exp(-s / tau)) ds              (= tau (Ei(u) - Ei(u a)), a = exp(-D / tau), Eq. 10)
+ *   G = int_0^D exp(-s / tau) exp(u exp(-s / tau)) ds (= tau (e^u - e^{u a}) / u, Eq. 14)
+ * Host function, needs no GPU.  Errors: INVALID_ARG (D < 0, tau <= 0, non-finite u, D or tau, NULL
+ * outputs). */
+int glm_ct_interval(double u, double D, double tau, double* F_host, double* G_host);
+
 /* Recompute the per-problem caches (filter scan, spike term) from the device-resident spikes, for a new
  * tau (tau > 0) or, with tau <= 0, the current one.  Errors: NO_PROBLEM, INVALID_ARG, CUDA. */
 int glm_prepare(glm_ctx* ctx, double tau);

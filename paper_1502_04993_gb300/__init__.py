@@ -83,6 +83,9 @@ SIGNATURES["glm_fit"] = ([_vp, ctypes.POINTER(FitOpts), _vp, _vp, _vp, ctypes.PO
 SIGNATURES["glm_fit_batch"] = ([_vp, _i32, ctypes.POINTER(FitOpts), _vp, _vp, _vp, ctypes.POINTER(FitReport)], ctypes.c_int)
 SIGNATURES["glm_autotune"] = ([_vp, _vp], ctypes.c_int)
 SIGNATURES["glm_set_chunk_bins"] = ([_vp, _i64], ctypes.c_int)
+SIGNATURES["glm_set_problem_ct"] = ([_vp, _i32, _f64, _f64, _f64, _f64, _vp, _vp, ctypes.c_int], ctypes.c_int)
+SIGNATURES["glm_problem_columns"] = ([_vp, ctypes.POINTER(_i64)], ctypes.c_int)
+SIGNATURES["glm_ct_interval"] = ([_f64, _f64, _f64, ctypes.POINTER(_f64), ctypes.POINTER(_f64)], ctypes.c_int)
 SIGNATURES["glm_cross_validate"] = ([_vp, _vp, ctypes.POINTER(FitOpts), _vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp],
                                      ctypes.c_int)
 SIGNATURES["glm_classify"] =([_vp, _i32, ctypes.POINTER(ClassifyOpts), _vp, _vp, _vp, ctypes.POINTER(ClassifyReport)],
@@ -155,6 +158,16 @@ def fit_batch(contexts, *, method: str = "lbfgs", m: int = 10, max_iter: int = 5
     out = [dict(W=Ws[p], b=bs[p], status=sts[p], report={f: getattr(reps[p], f) for f, _ in FitReport._fields_})
            for p in range(k)]
     return out, rc
+
+
+def ct_interval(u: float, D: float, tau: float):
+    """(F, G) of one continuous-time column (glm_ct_interval; host code, no GPU needed)."""
+    lib = load_library()
+    F, G = ctypes.c_double(), ctypes.c_double()
+    rc = lib.glm_ct_interval(float(u), float(D), float(tau), ctypes.byref(F), ctypes.byref(G))
+    if rc != GLM_OK:
+        raise GLMError(rc, "glm_ct_interval")
+    return F.value, G.value
 
 
 def split_recording(offs, bins, n_bins: int, t_split: int):
@@ -278,6 +291,24 @@ class GLM:
                                       bins.ctypes.data if bins.size else None, PREC[prec])
         self._check(rc, "glm_set_problem")
         self.n, self.n_bins, self.dt, self.tau, self.prec = n, int(n_bins), dt, tau, prec
+
+    def set_problem_ct(self, offs, times, t_begin: float, t_end: float, tau: float, delay: float,
+                       prec: str = "bf16"):
+        """Continuous-time problem (glm_set_problem_ct): spike times in seconds, one uniform delay."""
+        offs = np.ascontiguousarray(offs, dtype=np.int64)
+        times = np.ascontiguousarray(times, dtype=np.float64)
+        n = offs.size - 1
+        rc = self.lib.glm_set_problem_ct(self.h, n, float(t_begin), float(t_end), float(tau), float(delay),
+                                         offs.ctypes.data, times.ctypes.data if times.size else None, PREC[prec])
+        self._check(rc, "glm_set_problem_ct")
+        self.n, self.tau, self.prec = n, tau, prec
+        self.n_bins, self.dt = self.columns(), None
+
+    def columns(self) -> int:
+        """Time columns of the current problem (bins, or event columns in continuous time)."""
+        m = ctypes.c_int64()
+        self._check(self.lib.glm_problem_columns(self.h, ctypes.byref(m)), "glm_problem_columns")
+        return int(m.value)
 
     def prepare(self, tau: float | None = None):
         self._check(self.lib.glm_prepare(self.h, float(tau) if tau else -1.0), "glm_prepare")

@@ -31,18 +31,21 @@ void fill_scan_consts(double a, ScanConsts* sc) {
     for (int k = 0; k < 8; ++k) sc->pr[k] = (float)std::pow(a, (double)k);
 }
 
-// Block per row: segment-first indices and, in seg_carry, the contribution of each segment's own
-// spikes to X at the next segment start: sum_{t in seg s} a^(256 (s+1) - 1 - t).
+// Block per row: segment-first indices and, in seg_local (when given), the contribution of each segment's
+// own spikes to X at the next segment start: sum_{t in seg s} a^(256 (s+1) - 1 - t) on the grid; with
+// continuous-time columns (ctime given) sum exp(-(c_end - c_{t+1}) / tau), a source t arriving at column t+1.
 __global__ void seg_local_kernel(int32_t n, int64_t nseg, const int64_t* __restrict__ offs,
                                  const int32_t* __restrict__ bins, const double* __restrict__ pow_seg,
-                                 double* __restrict__ seg_local, int32_t* __restrict__ seg_first) {
+                                 const double* __restrict__ ctime, double inv_tau, double* __restrict__ seg_local,
+                                 int32_t* __restrict__ seg_first) {
     const int32_t j = blockIdx.x;
     if (j >= n) return;
     const int64_t o0 = offs[j], q = offs[j + 1] - o0;
     const int32_t* b = bins + o0;
-    double* loc = seg_local + (int64_t)j * nseg;
+    double* loc = seg_local ? seg_local + (int64_t)j * nseg : nullptr;
     int32_t* first = seg_first + (int64_t)j * nseg;
-    for (int64_t s = threadIdx.x; s < nseg; s += blockDim.x) loc[s] = 0.0;
+    if (loc)
+        for (int64_t s = threadIdx.x; s < nseg; s += blockDim.x) loc[s] = 0.0;
     if (q == 0) {
         for (int64_t s = threadIdx.x; s < nseg; s += blockDim.x) first[s] = 0;
         return;
@@ -53,10 +56,13 @@ __global__ void seg_local_kernel(int32_t n, int64_t nseg, const int64_t* __restr
         const int64_t ps = (k > 0) ? (int64_t)(b[k - 1] / SEG) : -1;
         if (s != ps) {
             for (int64_t ss = ps + 1; ss <= s; ++ss) first[ss] = (int32_t)k;
-            double acc = 0.0;
-            const int64_t end = (s + 1) * SEG;
-            for (int64_t kk = k; kk < q && b[kk] < end; ++kk) acc += pow_seg[end - 1 - b[kk]];
-            loc[s] = acc;
+            if (loc) {
+                double acc = 0.0;
+                const int64_t end = (s + 1) * SEG;
+                for (int64_t kk = k; kk < q && b[kk] < end; ++kk)
+                    acc += ctime ? exp(-(ctime[end] - ctime[b[kk] + 1]) * inv_tau) : pow_seg[end - 1 - b[kk]];
+                loc[s] = acc;
+            }
         }
         if (k == q - 1)
             for (int64_t ss = s + 1; ss < nseg; ++ss) first[ss] = (int32_t)q;
@@ -66,21 +72,30 @@ __global__ void seg_local_kernel(int32_t n, int64_t nseg, const int64_t* __restr
 // Warp per row, in place: seg_carry[s] <- X_j[256 s] = a^256 X_j[256 (s-1)] + local[s-1].
 // The segments of a row are split into 32 contiguous parts, one per lane: each lane runs the recursion
 // over its part from zero, a shuffle scan over the lanes supplies every part's true carry-in
-// (multiplier a^(256 * part length) per lane step), and each lane then rewrites its part.
-__global__ void seg_carry_kernel(int32_t n, int64_t nseg, double a_seg, double* __restrict__ seg) {
+// (multiplier a^(256 * part length) per lane step), and each lane then rewrites its part.  With mul_seg
+// (continuous-time columns) segment s decays by mul_seg[s] instead of a_seg.
+__global__ void seg_carry_kernel(int32_t n, int64_t nseg, double a_seg, const double* __restrict__ mul_seg,
+                                 double* __restrict__ seg) {
     const int32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (j >= n) return;
     double* p = seg + (int64_t)j * nseg;
     const int64_t len = (nseg + 31) / 32;
     const int64_t s0 = min((int64_t)lane * len, nseg), s1 = min(s0 + len, nseg);
-    double c = 0.0;
-    for (int64_t s = s0; s < s1; ++s) c = fma(a_seg, c, p[s]);  // this part's contribution at its end
-    // multiplier across one full part: a_seg^len (parts shorter than len only occur at the end)
-    double mul = 1.0, base = a_seg;
-    for (int64_t e = len; e > 0; e >>= 1) {
-        if (e & 1) mul *= base;
-        base *= base;
+    double c = 0.0, mul = 1.0;
+    if (mul_seg) {
+        for (int64_t s = s0; s < s1; ++s) {
+            c = fma(mul_seg[s], c, p[s]);
+            mul *= mul_seg[s];
+        }
+    } else {
+        for (int64_t s = s0; s < s1; ++s) c = fma(a_seg, c, p[s]);  // this part's contribution at its end
+        // multiplier across one full part: a_seg^len (parts shorter than len only occur at the end)
+        double base = a_seg;
+        for (int64_t e = len; e > 0; e >>= 1) {
+            if (e & 1) mul *= base;
+            base *= base;
+        }
     }
     // inclusive scan over lanes of carry_out(l) = mul * carry_out(l-1) + c(l)
     double v = c, m = mul;
@@ -97,7 +112,7 @@ __global__ void seg_carry_kernel(int32_t n, int64_t nseg, double a_seg, double* 
     for (int64_t s = s0; s < s1; ++s) {
         const double l = p[s];
         p[s] = cin;
-        cin = fma(a_seg, cin, l);
+        cin = fma(mul_seg ? mul_seg[s] : a_seg, cin, l);
     }
 }
 
@@ -130,6 +145,7 @@ struct FilterArgs {
     const int32_t* seg_first;
     void* X;
     void* Xlo;  // 16-bit forms: X_lo
+    const float* col_a;  // continuous-time columns: decay of each column
 };
 
 // F32 X, one warp per (8 rows, 4096-bin chunk).
@@ -248,6 +264,62 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache16_kernel(const __g
     }
 }
 
+// Continuous-time columns: as filter_cache16_kernel with the decay of each column (seg_scan_ct); the
+// multipliers of a segment are formed once for the 8 rows of the warp.
+template <typename T16>
+__global__ void __launch_bounds__(FW_WARPS * 32) filter_cache16_ct_kernel(const __grid_constant__ FilterArgs A) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wg = (int64_t)blockIdx.x * FW_WARPS + (threadIdx.x >> 5);
+    const int64_t c = wg / A.ngroups;
+    const int32_t g = (int32_t)(wg % A.ngroups);
+    if (c >= A.nchunks) return;
+    const int64_t s0 = A.s_begin + c * CHUNK_SEGS;
+    const int64_t s1 = min(s0 + (int64_t)CHUNK_SEGS, A.s_end);
+    float xs[8];
+    int64_t cur[8], end[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int32_t r = g * 8 + k;
+        if (r < A.n) {
+            xs[k] = (float)A.seg_carry[(int64_t)r * A.nseg + s0];
+            cur[k] = A.offs[r] + A.seg_first[(int64_t)r * A.nseg + s0];
+            end[k] = A.offs[r + 1];
+        } else {
+            xs[k] = 0.f;
+            cur[k] = 0;
+            end[k] = 0;
+        }
+    }
+    T16* Xh = reinterpret_cast<T16*>(A.X);
+    T16* Xl = reinterpret_cast<T16*>(A.Xlo);
+    for (int64_t s = s0; s < s1; ++s) {
+        const int64_t t0 = s * SEG;
+        const int64_t tl = t0 + 8 * lane;
+        CtSegMul S;
+        ct_seg_setup(A.col_a, t0, lane, S);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int32_t r = g * 8 + k;
+            const uint32_t bits = seg_bits(A.bins, cur[k], end[k], t0, lane);
+            float v[8];
+            xs[k] = seg_scan_ct(S, xs[k], bits, lane, v);
+            uint32_t ph[4], pl[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const T16 h0 = from_f<T16>(v[2 * p]), h1 = from_f<T16>(v[2 * p + 1]);
+                ph[p] = pack2<T16>(to_f<T16>(h0), to_f<T16>(h1));
+                pl[p] = pack2<T16>(v[2 * p] - to_f<T16>(h0), v[2 * p + 1] - to_f<T16>(h1));
+            }
+            if (r < A.n) {
+                const int64_t tb = tl - A.s_begin * SEG;
+                const int64_t o = ((tb >> 6) * A.n + r) * 64 + (tb & 63);
+                *reinterpret_cast<uint4*>(Xh + o) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+                *reinterpret_cast<uint4*>(Xl + o) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+            }
+        }
+    }
+}
+
 struct RangeArgs {
     int32_t n;
     int64_t T, nseg;
@@ -353,6 +425,7 @@ cudaError_t launch_spike_raster(glm_ctx* c, void* out, int64_t s_begin, int64_t 
     A.seg_first = c->buf.seg_first;
     A.X = out;
     A.Xlo = nullptr;
+    A.col_a = nullptr;
     const uint16_t one = (P.prec == GLM_PREC_BF16) ? 0x3F80u : 0x3C00u;
     const int64_t warps = (int64_t)A.ngroups * A.nchunks;
     spike_raster16_kernel<<<(unsigned)((warps + FW_WARPS - 1) / FW_WARPS), FW_WARPS * 32, 0, c->stream>>>(A, one);
@@ -361,10 +434,20 @@ cudaError_t launch_spike_raster(glm_ctx* c, void* out, int64_t s_begin, int64_t 
 
 cudaError_t launch_carry(glm_ctx* c) {
     const Problem& P = c->pb;
-    seg_local_kernel<<<P.n, 256, 0, c->stream>>>(P.n, P.nseg, c->buf.offs, c->buf.bins, c->buf.pow_seg,
-                                                 c->buf.seg_carry, c->buf.seg_first);
+    const Buffers& B = c->buf;
+    if (P.ct) {
+        // first spike per segment of the spike columns; carries of the arrival sources
+        seg_local_kernel<<<P.n, 256, 0, c->stream>>>(P.n, P.nseg, B.offs, B.bins, nullptr, nullptr, 0.0, nullptr,
+                                                     B.seg_first);
+        seg_local_kernel<<<P.n, 256, 0, c->stream>>>(P.n, P.nseg, B.aoffs, B.abins, nullptr, B.ctime, 1.0 / P.tau,
+                                                     B.seg_carry, B.aseg_first);
+        seg_carry_kernel<<<(P.n + 3) / 4, 128, 0, c->stream>>>(P.n, P.nseg, 0.0, B.seg_mul, B.seg_carry);
+        return cudaGetLastError();
+    }
+    seg_local_kernel<<<P.n, 256, 0, c->stream>>>(P.n, P.nseg, B.offs, B.bins, B.pow_seg, nullptr, 0.0, B.seg_carry,
+                                                 B.seg_first);
     const double a_seg = std::exp(-(double)SEG * P.dt / P.tau);
-    seg_carry_kernel<<<(P.n + 3) / 4, 128, 0, c->stream>>>(P.n, P.nseg, a_seg, c->buf.seg_carry);
+    seg_carry_kernel<<<(P.n + 3) / 4, 128, 0, c->stream>>>(P.n, P.nseg, a_seg, nullptr, B.seg_carry);
     return cudaGetLastError();
 }
 
@@ -386,6 +469,19 @@ cudaError_t launch_filter_cache(glm_ctx* c, int64_t s_begin, int64_t s_end) {
     A.seg_first = c->buf.seg_first;
     A.X = c->buf.X;
     A.Xlo = c->buf.Xlo;
+    A.col_a = c->buf.col_a;
+    if (P.ct) {
+        A.offs = c->buf.aoffs;
+        A.bins = c->buf.abins;
+        A.seg_first = c->buf.aseg_first;
+        const int64_t warps = (int64_t)A.ngroups * A.nchunks;
+        const int64_t blocks = (warps + FW_WARPS - 1) / FW_WARPS;
+        if (P.prec == GLM_PREC_BF16)
+            filter_cache16_ct_kernel<__nv_bfloat16><<<(unsigned)blocks, FW_WARPS * 32, 0, c->stream>>>(A);
+        else
+            filter_cache16_ct_kernel<__half><<<(unsigned)blocks, FW_WARPS * 32, 0, c->stream>>>(A);
+        return cudaGetLastError();
+    }
     if (P.prec == GLM_PREC_F32) {
         const int64_t warps = (int64_t)A.ngroups * A.nchunks;
         const int64_t blocks = (warps + FW_WARPS - 1) / FW_WARPS;

@@ -80,7 +80,7 @@ __device__ __forceinline__ double pen_grad(const FitState& F, int32_t i, int k, 
     return (F.alpha > 0.0 && k - 1 != i) ? F.alpha * w / sqrt(w * w + F.eps) : 0.0;
 }
 
-__global__ void fit_init_kernel(FitState F, int64_t T, double dt, const double* __restrict__ qd, int warm,
+__global__ void fit_init_kernel(FitState F, double span, const double* __restrict__ qd, int warm,
                                 const float* __restrict__ W, const float* __restrict__ b) {
     const int32_t i = blockIdx.x;
     double* th = F.theta + (int64_t)i * F.d;
@@ -89,7 +89,7 @@ __global__ void fit_init_kernel(FitState F, int64_t T, double dt, const double* 
     for (int k = threadIdx.x; k < F.d; k += blockDim.x) {
         double v;
         if (k == 0)
-            v = degen ? log(1e-3) : (warm ? (double)b[i] : log(q / ((double)T * dt)));
+            v = degen ? log(1e-3) : (warm ? (double)b[i] : log(q / span));
         else
             v = (degen || !warm) ? 0.0 : (double)W[(int64_t)i * F.n + (k - 1)];
         th[k] = v;
@@ -478,7 +478,7 @@ int fit_start(FitProb& fp, const glm_fit_opts_t* o) {
     const int32_t n = P.n;
     cudaStream_t st = c->stream;
     int rc;
-    fit_init_kernel<<<n, FT, 0, st>>>(fp.F, P.T, P.dt, c->buf.qd, o->warm_start, fp.W, fp.b);
+    fit_init_kernel<<<n, FT, 0, st>>>(fp.F, P.span, c->buf.qd, o->warm_start, fp.W, fp.b);
     fit_trial_kernel<<<n, FT, 0, st>>>(fp.F, fp.W32, fp.b32);
     c->launches += 2;
     if ((rc = ck(c, reset_flags(c)))) return rc;
@@ -899,7 +899,7 @@ int fit_run_batch(glm_ctx* const* cs, int np, const glm_fit_opts_t* o, float* co
         hb.part_g[p] = c->buf.part_g;
         hb.ntile[p] = c->pb.Tpad / tc_tile_t();
         hb.nsplit[p] = tc_nsplit(c);
-        hb.dt[p] = c->pb.dt;
+        hb.dt[p] = c->pb.dt_int;
         hb.flags[p] = c->buf.flags;
         hb.eb[p] = c->buf.eb;
         hb.Wsplit[p] = c->buf.Wsplit;

@@ -166,10 +166,66 @@ int validate_spikes(glm_ctx* c, int32_t n, int64_t T, const int64_t* offs, const
     return GLM_OK;
 }
 
+// Device buffers of the problem described by c->pb (frees everything on failure).
+int alloc_problem(glm_ctx* c) {
+    const Problem& P = c->pb;
+    const int32_t n = P.n;
+    const bool tensor = P.prec != GLM_PREC_F32;
+    Buffers& B = c->buf;
+    const size_t nn = (size_t)n * n;
+    const size_t esz = tensor ? 2 : 4;
+    const int64_t ntile = P.Tpad / (tensor ? tc_tile_t() : simt_tile_t());
+    int rc;
+    B.ldn = round_up(n, 64);
+    if ((rc = ws_alloc_t(c, &B.offs, n + 1)) || (rc = ws_alloc_t(c, &B.bins, P.q > 0 ? P.q : 1)) ||
+        (rc = ws_alloc_t(c, &B.seg_carry, (size_t)n * P.nseg)) ||
+        (rc = ws_alloc_t(c, &B.seg_first, (size_t)n * P.nseg)) || (rc = ws_alloc_t(c, &B.pow_seg, SEG + 1)) ||
+        (rc = ws_alloc_t(c, &B.qd, n)) || (rc = ws_alloc_t(c, &B.C, nn)) ||
+        (rc = ws_alloc(c, &B.X, (size_t)n * P.Tc * esz)) || (rc = ws_alloc(c, &B.E, (size_t)n * P.Tc * esz)) ||
+        (P.chunk && (rc = ws_alloc_t(c, &B.Gacc, nn))) || (rc = ws_alloc_t(c, &B.part_e, (size_t)n * ntile)) ||
+        (rc = ws_alloc_t(c, &B.part_g, nn * (tensor ? tc_nsplit_max(c) : grad_nsplit(c)))) ||
+        (rc = ws_alloc_t(c, &B.flags, 4)) || (rc = ws_alloc_t(c, &B.Lrows, n)) || (rc = ws_alloc_t(c, &B.scal, 8)) ||
+        (rc = ws_alloc_t(c, &B.eb, n)) || (tensor && (rc = ws_alloc(c, &B.Xlo, (size_t)P.n * P.Tc * 2))) ||
+        (rc = ws_alloc_t(c, &B.part_s, (size_t)n * ntile)) ||
+        (tensor && (rc = ws_alloc(c, &B.Wsplit, 2 * (size_t)n * B.ldn * 2)))) {
+        free_all(c);
+        return rc;
+    }
+    if (P.ct) {
+        if ((rc = ws_alloc_t(c, &B.aoffs, n + 1)) || (rc = ws_alloc_t(c, &B.abins, P.qa > 0 ? P.qa : 1)) ||
+            (rc = ws_alloc_t(c, &B.aseg_first, (size_t)n * P.nseg)) || (rc = ws_alloc_t(c, &B.ctime, P.Tpad + 1)) ||
+            (rc = ws_alloc_t(c, &B.col_a, P.Tpad)) || (rc = ws_alloc_t(c, &B.colc, 8 * (size_t)P.Tpad)) ||
+            (rc = ws_alloc_t(c, &B.seg_mul, P.nseg)) || (rc = ws_alloc_t(c, &B.tile_span, P.nseg))) {
+            free_all(c);
+            return rc;
+        }
+    } else {
+        B.aoffs = B.offs;
+        B.abins = B.bins;
+        B.aseg_first = B.seg_first;
+    }
+    if (tensor) {
+        cudaError_t e = tc_prepare_maps(c);
+        if (e != cudaSuccess) {
+            free_all(c);
+            return cuda_fail(c, e, "cuTensorMapEncodeTiled");
+        }
+    }
+    return GLM_OK;
+}
+
 int ensure_spike_term(glm_ctx* c);
 
 int do_prepare(glm_ctx* c) {
     Problem& P = c->pb;
+    if (P.ct) {
+        // column decays for this tau, then carries, filter and spike term as on the grid
+        c->c_ready = false;
+        GLM_RUN("ct_consts", 1, launch_ct_consts(c));
+        GLM_RUN("carry", 3, launch_carry(c));
+        GLM_RUN("filter_scan", 1, launch_filter_cache(c));
+        return ensure_spike_term(c);
+    }
     P.a = std::exp(-P.dt / P.tau);
     fill_scan_consts(P.a, &c->sc);
     std::vector<double> pw(SEG + 1);
@@ -410,33 +466,10 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
     // chunks start on the filter's 4096-bin units, so X does not depend on the chunking
     if (tensor && c->chunk_req > 0 && round_up(c->chunk_req, 16 * SEG) < P.Tpad) P.chunk = round_up(c->chunk_req, 16 * SEG);
     P.Tc = P.chunk ? P.chunk : P.Tpad;
+    P.span = (double)n_bins * dt;
+    P.dt_int = dt;
+    if ((rc = alloc_problem(c))) return rc;
     Buffers& B = c->buf;
-    const size_t nn = (size_t)n * n;
-    const size_t esz = (prec == GLM_PREC_F32) ? 4 : 2;
-    B.ldn = round_up(n, 64);
-    if ((rc = ws_alloc_t(c, &B.offs, n + 1)) || (rc = ws_alloc_t(c, &B.bins, P.q > 0 ? P.q : 1)) ||
-        (rc = ws_alloc_t(c, &B.seg_carry, (size_t)n * P.nseg)) ||
-        (rc = ws_alloc_t(c, &B.seg_first, (size_t)n * P.nseg)) || (rc = ws_alloc_t(c, &B.pow_seg, SEG + 1)) ||
-        (rc = ws_alloc_t(c, &B.qd, n)) || (rc = ws_alloc_t(c, &B.C, nn)) ||
-        (rc = ws_alloc(c, &B.X, (size_t)n * P.Tc * esz)) ||
-        (rc = ws_alloc(c, &B.E, (size_t)n * P.Tc * esz)) ||
-        (P.chunk && (rc = ws_alloc_t(c, &B.Gacc, nn))) ||
-        (rc = ws_alloc_t(c, &B.part_e, (size_t)n * (P.Tpad / (tensor ? tc_tile_t() : simt_tile_t())))) ||
-        (rc = ws_alloc_t(c, &B.part_g, nn * (tensor ? tc_nsplit_max(c) : grad_nsplit(c)))) ||
-        (rc = ws_alloc_t(c, &B.flags, 4)) || (rc = ws_alloc_t(c, &B.Lrows, n)) || (rc = ws_alloc_t(c, &B.scal, 8)) || (rc = ws_alloc_t(c, &B.eb, n)) ||
-        (tensor && (rc = ws_alloc(c, &B.Xlo, (size_t)P.n * P.Tc * 2))) ||
-        (rc = ws_alloc_t(c, &B.part_s, (size_t)n * (P.Tpad / (tensor ? tc_tile_t() : simt_tile_t())))) ||
-        (tensor && (rc = ws_alloc(c, &B.Wsplit, 2 * (size_t)n * B.ldn * 2)))) {
-        free_all(c);
-        return rc;
-    }
-    if (tensor) {
-        cudaError_t e = tc_prepare_maps(c);
-        if (e != cudaSuccess) {
-            free_all(c);
-            return cuda_fail(c, e, "cuTensorMapEncodeTiled");
-        }
-    }
     std::vector<double> qd(n);
     for (int32_t i = 0; i < n; ++i) qd[i] = (double)(offs[i + 1] - offs[i]);
     GLM_CK(cudaMemcpyAsync(B.offs, offs, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, c->stream));
@@ -455,6 +488,116 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
     return GLM_OK;
 }
 
+int glm_set_problem_ct(glm_ctx* c, int32_t n, double t_begin, double t_end, double tau, double delay,
+                       const int64_t* offs, const double* times, glm_prec_t prec) {
+    if (!c) return GLM_ERR_INVALID_ARG;
+    if (n < 1 || !offs) return fail(c, GLM_ERR_INVALID_ARG, "need n >= 1 and offs");
+    if (!(std::isfinite(t_begin) && std::isfinite(t_end) && t_end > t_begin))
+        return fail(c, GLM_ERR_INVALID_ARG, "need finite t_begin < t_end");
+    if (!(std::isfinite(tau) && tau > 0) || !(std::isfinite(delay) && delay >= 0))
+        return fail(c, GLM_ERR_INVALID_ARG, "tau must be finite and > 0, delay finite and >= 0");
+    if (prec != GLM_PREC_BF16 && prec != GLM_PREC_F16)
+        return fail(c, GLM_ERR_UNSUPPORTED, "the continuous-time form runs on the tensor-core precisions (bf16, f16)");
+    if (!(c->cc_major == 10 && c->cc_minor == 3))
+        return fail(c, GLM_ERR_UNSUPPORTED_ARCH, "BF16/F16 tensor-core paths need an sm_103 GPU (found sm_" +
+                                                     std::to_string(c->cc_major) + std::to_string(c->cc_minor) + ")");
+    if (offs[0] != 0) return fail(c, GLM_ERR_SPIKE_OUT_OF_RANGE, "offs[0] must be 0");
+    for (int32_t i = 0; i < n; ++i)
+        if (offs[i + 1] < offs[i]) return fail(c, GLM_ERR_SPIKE_OUT_OF_RANGE, "offs must be non-decreasing");
+    const int64_t q = offs[n];
+    if (q > 0 && !times) return fail(c, GLM_ERR_INVALID_ARG, "times is NULL but offs[n] > 0");
+    if (q >= ((int64_t)1 << 30)) return fail(c, GLM_ERR_INVALID_ARG, "at most 2^30 - 1 spikes");
+    // row j's arrivals are its spikes with t + delay < t_end: a prefix of the row
+    std::vector<int64_t> aoffs(n + 1, 0);
+    for (int32_t i = 0; i < n; ++i) {
+        double prev = -INFINITY;
+        int64_t na = 0;
+        for (int64_t k = offs[i]; k < offs[i + 1]; ++k) {
+            const double t = times[k];
+            if (!(t >= t_begin && t < t_end))
+                return fail(c, GLM_ERR_SPIKE_OUT_OF_RANGE, "spike time of row " + std::to_string(i) +
+                                                               " outside [t_begin, t_end) or not finite");
+            if (!(t > prev))
+                return fail(c, GLM_ERR_UNSORTED_SPIKES,
+                            "row " + std::to_string(i) + ": times not strictly increasing at index " + std::to_string(k));
+            prev = t;
+            if (t + delay < t_end) ++na;
+        }
+        aoffs[i + 1] = aoffs[i] + na;
+    }
+    const int64_t qa = aoffs[n];
+    DeviceGuard g(c->device);
+    GLM_CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+    free_all(c);
+    Problem& P = c->pb;
+    P = Problem();
+    P.n = n;
+    P.tau = tau;
+    P.q = q;
+    P.qa = qa;
+    P.prec = prec;
+    P.ct = true;
+    P.t_begin = t_begin;
+    P.t_end = t_end;
+    P.delay = delay;
+    P.span = t_end - t_begin;
+    P.dt_int = 1.0;
+    P.dt = P.span;  // not used by the continuous-time path
+    // columns: the distinct event times (device sort), then the buffers sized by them
+    int64_t* d_offs = nullptr;
+    double* d_times = nullptr;
+    void* items = nullptr;
+    int32_t *excl = nullptr, *flag = nullptr;
+    auto cleanup = [&](int rc) {
+        cudaFree(d_offs);
+        cudaFree(d_times);
+        cudaFree(items);
+        cudaFree(excl);
+        cudaFree(flag);
+        if (rc) free_all(c);
+        return rc;
+    };
+    if (cudaMalloc(&d_offs, sizeof(int64_t) * (n + 1)) != cudaSuccess ||
+        cudaMalloc(&d_times, sizeof(double) * (q > 0 ? q : 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(fail(c, GLM_ERR_OOM, "continuous-time set-up buffers"));
+    }
+    if (cudaMemcpyAsync(d_offs, offs, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        (q > 0 && cudaMemcpyAsync(d_times, times, sizeof(double) * q, cudaMemcpyHostToDevice, c->stream) != cudaSuccess))
+        return cleanup(fail(c, GLM_ERR_CUDA, "copy of the spike times"));
+    int64_t M = 0;
+    int rc = ct_build_columns(c, n, q, qa, t_begin, t_end, delay, d_offs, d_times, &M, &items, &excl, &flag);
+    if (rc) return cleanup(rc);
+    if (M >= ((int64_t)1 << 31) - SEG) return cleanup(fail(c, GLM_ERR_INVALID_ARG, "too many event columns"));
+    P.T = M;
+    P.nseg = (M + SEG - 1) / SEG;
+    P.Tpad = P.nseg * SEG;
+    P.Tc = P.Tpad;
+    if ((rc = alloc_problem(c))) return cleanup(rc);
+    Buffers& B = c->buf;
+    std::vector<double> qd(n);
+    for (int32_t i = 0; i < n; ++i) qd[i] = (double)(offs[i + 1] - offs[i]);
+    if (cudaMemcpyAsync(B.offs, offs, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(B.aoffs, aoffs.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(B.qd, qd.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(B.flags, 0, 4 * sizeof(int), c->stream) != cudaSuccess ||
+        ct_finish_columns(c, items, excl, flag, q + qa) != cudaSuccess)
+        return cleanup(fail(c, GLM_ERR_CUDA, "continuous-time columns"));
+    if ((rc = do_prepare(c))) return cleanup(rc);
+    if ((c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize()) != cudaSuccess)
+        return cleanup(fail(c, GLM_ERR_CUDA, "synchronise"));
+    c->has_problem = true;
+    return cleanup(GLM_OK);
+}
+
+int glm_problem_columns(const glm_ctx* c, int64_t* n_columns) {
+    if (!c || !n_columns) return GLM_ERR_INVALID_ARG;
+    if (!c->has_problem) return GLM_ERR_NO_PROBLEM;
+    *n_columns = c->pb.T;
+    return GLM_OK;
+}
+
 int glm_prepare(glm_ctx* c, double tau) {
     if (!c) return GLM_ERR_INVALID_ARG;
     if (!c->has_problem) return fail(c, GLM_ERR_NO_PROBLEM, "no problem set");
@@ -469,6 +612,7 @@ int glm_prepare(glm_ctx* c, double tau) {
 int glm_filter(glm_ctx* c, int64_t t0, int64_t t_len, void* X_dev, int64_t ldx, glm_dtype_t dtype) {
     if (!c) return GLM_ERR_INVALID_ARG;
     if (!c->has_problem) return fail(c, GLM_ERR_NO_PROBLEM, "no problem set");
+    if (c->pb.ct) return fail(c, GLM_ERR_UNSUPPORTED, "glm_filter serves the grid form");
     if (!X_dev || t0 < 0 || t_len < 1 || t0 + t_len > c->pb.T || ldx < t_len)
         return fail(c, GLM_ERR_INVALID_ARG, "bad range, buffer or leading dimension");
     if (dtype != GLM_DTYPE_F32 && dtype != GLM_DTYPE_BF16 && dtype != GLM_DTYPE_F16)
@@ -500,6 +644,8 @@ int glm_loglik_grad(glm_ctx* c, const float* W, const float* b, double* L_rows, 
     if (!W || !b) return fail(c, GLM_ERR_INVALID_ARG, "W and b are required");
     if (gtau_host && c->pb.prec == GLM_PREC_F32)
         return fail(c, GLM_ERR_UNSUPPORTED, "dL/dtau is computed by the tensor-core precisions only");
+    if (gtau_host && c->pb.ct)
+        return fail(c, GLM_ERR_UNSUPPORTED, "dL/dtau is computed for the grid form only");
     DeviceGuard g(c->device);
     double* Lr = L_rows ? L_rows : c->buf.Lrows;
     if (gtau_host) {
@@ -657,6 +803,7 @@ int glm_fit_batch(glm_ctx* const* cs, int32_t np, const glm_fit_opts_t* opts, fl
         if (c->device != c0->device) return fail(c0, GLM_ERR_INVALID_ARG, "contexts on different devices");
         if (c->pb.prec != c0->pb.prec) return fail(c0, GLM_ERR_INVALID_ARG, "contexts with different precisions");
         if (c->pb.chunk) return fail(c0, GLM_ERR_UNSUPPORTED, "glm_fit_batch needs X stored (no chunking)");
+        if (c->pb.ct) return fail(c0, GLM_ERR_UNSUPPORTED, "glm_fit_batch serves the grid form");
         for (int32_t q = 0; q < p; ++q)
             if (cs[q] == c) return fail(c0, GLM_ERR_INVALID_ARG, "a context appears twice");
     }

@@ -42,6 +42,13 @@ struct Problem {
     glm_prec_t prec = GLM_PREC_F32;
     int64_t chunk = 0;    // 16-bit forms: bins of X recomputed per chunk for each evaluation (0: X stored)
     int64_t Tc = 0;       // bins held in the X / E buffers: chunk, or Tpad
+    double span = 0;      // duration of the recording in seconds: T dt, or t_end - t_begin
+    double dt_int = 0;    // factor of the per-tile integral sums in L: dt (grid) or 1 (sums already in seconds)
+    // continuous-time form: the "bins" are event columns (T of them), spike times in [t_begin, t_end),
+    // every spike arriving everywhere after `delay`
+    bool ct = false;
+    double t_begin = 0, t_end = 0, delay = 0;
+    int64_t qa = 0;       // arrivals inside the recording
 };
 
 // Device buffers owned by a context.  Row-major everywhere; ld* in elements.
@@ -72,6 +79,17 @@ struct Buffers {
     double* part_tau = nullptr;   // [5][n][ntile]
     double* tau_rows = nullptr;   // [n]
     int fit_m = 0;
+    // sources of the filter recursion: the spikes (grid: aliases of offs, bins, seg_first) or, in continuous
+    // time, the column before each arrival
+    int64_t* aoffs = nullptr;     // [n+1]
+    int32_t* abins = nullptr;     // [qa]
+    int32_t* aseg_first = nullptr;// [n][nseg]
+    // continuous-time columns
+    double* ctime = nullptr;      // [Tpad + 1] column start times; t_end from column T on
+    float* col_a = nullptr;       // [Tpad] exp(-(column length) / tau)
+    float* colc = nullptr;        // [Tpad][8] a, 1 - a and the one-panel quadrature factors (ct_link.cuh)
+    double* seg_mul = nullptr;    // [nseg] decay over each 256-column segment
+    double* tile_span = nullptr;  // [nseg] duration of each 256-column segment
 };
 
 }  // namespace glm
@@ -163,6 +181,12 @@ cudaError_t launch_tc_u_batch(glm_ctx* c0, const void* dev_u);
 cudaError_t launch_tc_grad_batch(glm_ctx* c0, const void* dev_g);
 int tc_tile_t();
 cudaError_t launch_total(glm_ctx* c, const double* L_rows, double* out1);
+// continuous-time columns (ct.cu)
+int ct_build_columns(glm_ctx* c, int32_t n, int64_t q, int64_t qa, double t_begin, double t_end, double delay,
+                     const int64_t* offs, const double* times, int64_t* M, void** items, int32_t** excl,
+                     int32_t** flag);
+cudaError_t ct_finish_columns(glm_ctx* c, const void* items, const int32_t* excl, const int32_t* flag, int64_t m);
+cudaError_t launch_ct_consts(glm_ctx* c);
 
 // ---- sizes shared between the launchers and the allocator ----
 int simt_tile_t();          // bins per SIMT GEMM1 tile

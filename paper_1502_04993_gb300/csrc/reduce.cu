@@ -154,7 +154,7 @@ cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_
     ReduceArgs A;
     A.n = P.n;
     A.ntile = ntile;
-    A.dt = P.dt;
+    A.dt = P.dt_int;
     A.W = W;
     A.b = b;
     A.C = c->buf.C;

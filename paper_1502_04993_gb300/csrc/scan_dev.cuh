@@ -79,4 +79,61 @@ __device__ __forceinline__ float seg_scan(const ScanConsts& K, float x_seg, uint
     return __shfl_sync(FULL, xend, 31);
 }
 
+// Continuous-time columns: the multiplier differs per column, so the powers of a become running products
+// of the column decays.  They depend on the columns only and are formed once per segment for all the rows
+// a warp scans.  Lane l owns columns t_l = t0 + 8 l .. t_l + 7; al[k] = a_{t_l + k} carries X from column
+// t_l + k to t_l + k + 1.
+struct CtSegMul {
+    float al[8];
+    float pk[9];  // pk[k] = al[0] ... al[k-1]
+    float ks[5];  // multiplier of this lane's running span at Kogge-Stone step d
+    float lp;     // product over all earlier lanes (the a^(8 l) of the constant form)
+};
+
+__device__ __forceinline__ void ct_seg_setup(const float* __restrict__ col_a, int64_t t0, int lane, CtSegMul& S) {
+    const float4 v0 = __ldg(reinterpret_cast<const float4*>(col_a + t0 + 8 * lane));
+    const float4 v1 = __ldg(reinterpret_cast<const float4*>(col_a + t0 + 8 * lane + 4));
+    S.al[0] = v0.x;
+    S.al[1] = v0.y;
+    S.al[2] = v0.z;
+    S.al[3] = v0.w;
+    S.al[4] = v1.x;
+    S.al[5] = v1.y;
+    S.al[6] = v1.z;
+    S.al[7] = v1.w;
+    S.pk[0] = 1.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) S.pk[k + 1] = S.pk[k] * S.al[k];
+    float P = S.pk[8];
+#pragma unroll
+    for (int d = 0; d < 5; ++d) {
+        const float o = __shfl_up_sync(FULL, P, 1 << d);
+        S.ks[d] = P;
+        if (lane >= (1 << d)) P *= o;
+    }
+    S.lp = __shfl_up_sync(FULL, P, 1);
+    if (lane == 0) S.lp = 1.f;
+}
+
+// Scan of one segment of columns: as seg_scan, with the lane's own recursion z_{k+1} = al[k] z_k + S and
+// the multipliers of CtSegMul.
+__device__ __forceinline__ float seg_scan_ct(const CtSegMul& S, float x_seg, uint32_t bits8, int lane, float out[8]) {
+    float z[9];
+    z[0] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) z[k + 1] = fmaf(S.al[k], z[k], (float)((bits8 >> k) & 1u));
+    float v = z[8];
+#pragma unroll
+    for (int d = 0; d < 5; ++d) {
+        const float o = __shfl_up_sync(FULL, v, 1 << d);
+        if (lane >= (1 << d)) v = fmaf(S.ks[d], o, v);
+    }
+    float ex = __shfl_up_sync(FULL, v, 1);
+    if (lane == 0) ex = 0.f;
+    const float xl = fmaf(S.lp, x_seg, ex);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) out[k] = fmaf(S.pk[k], xl, z[k]);
+    return __shfl_sync(FULL, fmaf(S.pk[8], xl, z[8]), 31);
+}
+
 }  // namespace glm

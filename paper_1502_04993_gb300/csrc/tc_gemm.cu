@@ -34,6 +34,7 @@
 #include <vector>
 #include <type_traits>
 
+#include "ct_link.cuh"
 #include "glm_internal.h"
 #include "tc_ptx.cuh"
 
@@ -140,6 +141,9 @@ struct TcArgs {
     float* part_g;
     int* flags;
     uint64_t limit_ns;
+    const float* colc;         // CT: [Tpad][8] column constants (ct_link.cuh)
+    const double* tile_span;   // CT: [ntile] seconds covered by each 256-column tile
+    float ct_tau;
 };
 
 struct Unit {
@@ -210,16 +214,20 @@ __device__ __forceinline__ uint32_t pack16<__half>(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// CT (MODE 0 only): continuous-time columns.  The epilogue takes, per column m of length D_m, the exact
+// interval integral e^{b} F(u, D_m) of the rate and the interval weight E'_m = e^{b} G(u, D_m) of Eq. 14
+// (ct_link.cuh) in place of dt e^U; the per-tile sums hold e^{b} (duration + sum (F - D)) in seconds.
 // TAU (MODE 0 only): the epilogue also emits, per (row, tile), the partial sums that give dL/dtau.  With v = (W X)_i[t] = U_i[t] - b_i, Z_i[t] = a Z_i[t-1] + v[t-1] (Z = W dX/da), the
 // tile's local Z_loc starts at 0 at its first bin t0, and Z[t] = a^(t-t0) Z[t0] + Z_loc[t]; a per-row
 // combine (reduce.cu) chains the tiles.
-template <int MODE, typename T16, bool TAU, bool BATCH>
+template <int MODE, typename T16, bool TAU, bool BATCH, bool CT = false>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
                    const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1,
                    const __grid_constant__ TcArgs Ag, const TcBatch* __restrict__ batch) {
     using C = Cfg<MODE>;
     using L = Layout<MODE>;
+    static_assert(!CT || (MODE == 0 && !TAU), "the continuous-time epilogue is a U-product epilogue without tau partials");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * L::STAGE_BYTES);
@@ -431,6 +439,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const double ebi = (i < A.n) ? A.eb[i] : 0.0;
                 const float sh = (i < A.n) ? fminf(A.b[i] - EXP_SPLIT_FLOOR, 0.f) : 0.f;  // U - c = v + sh
                 const float dteb = (float)(A.dt * ebi);
+                // continuous time: E' = e^{b} G = e^{c} e^{sh} tau (1 - a) gm
+                const float esh = CT ? __expf(sh) : 1.f;
+                const float tgeb = CT ? (float)(ebi * (double)A.ct_tau) * esh : 0.f;
                 double rsum = 0.0;
                 bool bad = false;
                 float zl = 0.f, pw = 1.f, p1 = 0.f, p2 = 0.f, p3 = 0.f, p4 = 0.f, spv = 0.f;
@@ -470,26 +481,47 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     for (int e = 0; e < 32; e += 2) {
                         const int64_t t = gt0 + c * 32 + e;
                         const float v0f = __uint_as_float(r[e]), v1f = __uint_as_float(r[e + 1]);
-                        float e0 = __expf(v0f + sh);
-                        float e1 = __expf(v1f + sh);
                         const bool v0 = t < A.T, v1 = t + 1 < A.T;
                         const bool s0 = (sm >> e) & 1u, s1 = (sm >> (e + 1)) & 1u;
-                        bad |= (v0 && !(e0 <= 3.0e38f)) || (v1 && !(e1 <= 3.0e38f));
-                        if (v0) {
-                            s += e0 - 1.f;
-                            ++cnt;
+                        float e0, e1;
+                        if constexpr (CT) {
+                            // columns t, t + 1: F - D and G / (tau oma) from the column constants
+                            const float4* cp = reinterpret_cast<const float4*>(A.colc) + 2 * t;
+                            const float4 c0 = __ldg(cp), c1 = __ldg(cp + 1), c2 = __ldg(cp + 2), c3 = __ldg(cp + 3);
+                            const float k0[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+                            const float k1[8] = {c2.x, c2.y, c2.z, c2.w, c3.x, c3.y, c3.z, c3.w};
+                            float f0, g0, f1, g1;
+                            ct_link(v0f, k0, A.ct_tau, &f0, &g0);
+                            ct_link(v1f, k1, A.ct_tau, &f1, &g1);
+                            e0 = tgeb * k0[1] * g0;
+                            e1 = tgeb * k1[1] * g1;
+                            bad |= (v0 && !(fabsf(f0) <= 3.0e38f && e0 <= 3.0e38f)) ||
+                                   (v1 && !(fabsf(f1) <= 3.0e38f && e1 <= 3.0e38f));
+                            if (v0) s += f0; else e0 = 0.f;
+                            if (v1) s += f1; else e1 = 0.f;
                         } else {
-                            e0 = 0.f;
-                        }
-                        if (v1) {
-                            s += e1 - 1.f;
-                            ++cnt;
-                        } else {
-                            e1 = 0.f;
+                            e0 = __expf(v0f + sh);
+                            e1 = __expf(v1f + sh);
+                            bad |= (v0 && !(e0 <= 3.0e38f)) || (v1 && !(e1 <= 3.0e38f));
+                            if (v0) {
+                                s += e0 - 1.f;
+                                ++cnt;
+                            } else {
+                                e0 = 0.f;
+                            }
+                            if (v1) {
+                                s += e1 - 1.f;
+                                ++cnt;
+                            } else {
+                                e1 = 0.f;
+                            }
                         }
                         if (s0) spv += v0f;
                         if (s1) spv += v1f;
-                        pk[e >> 1] = pack16<T16>(dteb * e0, dteb * e1);
+                        if constexpr (CT)
+                            pk[e >> 1] = pack16<T16>(e0, e1);
+                        else
+                            pk[e >> 1] = pack16<T16>(dteb * e0, dteb * e1);
                         if (TAU) {
                             p1 = fmaf(e0, pw, p1);
                             p2 = fmaf(e0, zl, p2);
@@ -518,6 +550,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     }
                 }
                 bad |= !(dteb <= 3.0e38f);
+                if (CT) {
+                    rsum = (double)esh * (A.tile_span[gtile] + rsum);  // e^{sh} sum_m F_m
+                    bad |= !(tgeb <= 3.0e38f);
+                }
                 if (i < A.n) {
                     A.part_e[(int64_t)i * A.ntile + gtile] = ebi * rsum;
                     A.part_s[(int64_t)i * A.ntile + gtile] = (double)spv;
@@ -681,7 +717,7 @@ cudaError_t tc_prepare_maps(glm_ctx* c) {
     return ok ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int MODE, typename T16, bool TAU = false, bool BATCH = false>
+template <int MODE, typename T16, bool TAU = false, bool BATCH = false, bool CT = false>
 static cudaError_t run(glm_ctx* c, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0,
                        const CUtensorMap& b1, const TcArgs& A, const TcBatch* batch = nullptr, int64_t grid = 0) {
     const size_t smem = Layout<MODE>::SMEM;
@@ -689,12 +725,13 @@ static cudaError_t run(glm_ctx* c, const CUtensorMap& a0, const CUtensorMap& a1,
     cudaError_t e = cudaStreamIsCapturing(c->stream, &cap);
     if (e != cudaSuccess) return e;
     if (cap == cudaStreamCaptureStatusNone) {  // set before the first launch; not during graph capture
-        e = cudaFuncSetAttribute(tc_gemm_kernel<MODE, T16, TAU, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+        e = cudaFuncSetAttribute(tc_gemm_kernel<MODE, T16, TAU, BATCH, CT>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     if (grid <= 0) grid = A.units < c->sm_count ? A.units : c->sm_count;
-    tc_gemm_kernel<MODE, T16, TAU, BATCH><<<(unsigned)grid, NUM_THREADS, smem, c->stream>>>(a0, a1, b0, b1, A, batch);
+    tc_gemm_kernel<MODE, T16, TAU, BATCH, CT><<<(unsigned)grid, NUM_THREADS, smem, c->stream>>>(a0, a1, b0, b1, A,
+                                                                                               batch);
     return cudaGetLastError();
 }
 
@@ -726,6 +763,9 @@ static TcArgs base_args(glm_ctx* c) {
     A.ntile = P.Tpad / BN;
     A.kb_total = 0;
     A.nsplit = 1;
+    A.colc = c->buf.colc;
+    A.tile_span = c->buf.tile_span;
+    A.ct_tau = (float)P.tau;
     return A;
 }
 
@@ -760,6 +800,12 @@ cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, boo
     A.part_tau = c->buf.part_tau;
     A.part_s = c->buf.part_s;
     A.idesc |= 1u << 16;  // B (X) is N-major
+    if (P.ct) {
+        if (tau) return cudaErrorNotSupported;
+        if (P.prec == GLM_PREC_BF16)
+            return run<0, __nv_bfloat16, false, false, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
+        return run<0, __half, false, false, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
+    }
     if (tau) {
         if (P.prec == GLM_PREC_BF16)
             return run<0, __nv_bfloat16, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);

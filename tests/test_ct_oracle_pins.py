@@ -124,7 +124,7 @@ def test_no_spikes_closed_form():
 
 def grid_case(n_bins, dt, seed=5, n=6):
     rng = np.random.default_rng(seed)
-    rows = [np.sort(rng.choice(n_bins - 1, size=rng.integers(3, 12), replace=False)) for _ in range(n)]
+    rows = [np.sort(rng.choice(n_bins - 1, size=rng.integers(20, 60), replace=False)) for _ in range(n)]
     offs = np.zeros(n + 1, dtype=np.int64)
     offs[1:] = np.cumsum([len(r) for r in rows])
     bins = np.concatenate(rows).astype(np.int32)
@@ -134,7 +134,9 @@ def grid_case(n_bins, dt, seed=5, n=6):
 
 
 def test_grid_aligned_times_reduce_to_the_grid_form():
-    dt, tau, n_bins = 0.002, 0.02, 400
+    # a power-of-two bin width: bin * dt + dt is exactly (bin + 1) * dt, so an arrival one bin after a
+    # spike lands on the next bin's spike time exactly, as on the grid
+    dt, tau, n_bins = 2.0 ** -9, 0.02, 400
     offs, bins, W, b = grid_case(n_bins, dt)
     times = bins.astype(np.float64) * dt
     n = len(b)
