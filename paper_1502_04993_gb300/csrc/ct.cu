@@ -364,9 +364,9 @@ extern "C" int glm_ct_interval(double u, double D, double tau, double* F, double
         return GLM_ERR_INVALID_ARG;
     float col[8];
     glm::ct_column(D, tau, col);
-    float dF = 0.f, gm = 0.f;
-    glm::ct_link((float)u, col, (float)tau, &dF, &gm);
+    float dF = 0.f, eg = 0.f;
+    glm::ct_link((float)u, col, (float)tau, &dF, &eg);
     *F = D + (double)dF;
-    *G = tau * (double)col[1] * (double)gm;
+    *G = tau * (double)eg;
     return GLM_OK;
 }

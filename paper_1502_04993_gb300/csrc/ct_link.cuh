@@ -44,24 +44,52 @@ __host__ __device__ __forceinline__ void ct_column(double D, double tau, float* 
     col[7] = (float)(h * GL4_W0D / (a + oma * GL4_E3D));
 }
 
-// e^x and e^x - 1 of one node: expm1 keeps e^x - 1 exact near 0; below x = -1 e^x comes from exp itself,
-// where 1 + expm1 would keep none of its digits.
-__host__ __device__ __forceinline__ void ct_node(float x, float* y, float* e) {
-    *y = expm1f(x);
-    *e = (x < -1.f) ? expf(x) : 1.f + *y;
+// e^x on the device's exp unit (ex2 of x log2 e, a few ulp), the C library's expf on the host.
+__host__ __device__ __forceinline__ float ct_exp(float x) {
+#ifdef __CUDA_ARCH__
+    return __expf(x);
+#else
+    return expf(x);
+#endif
 }
 
-// One element: dF = F(u, D) - D and gm = G(u, D) / (tau oma) = (1/oma) int_a^1 e^{u rho} d rho, from the
-// column constants col = {a, oma, q2[2], q4[4]}.
-__host__ __device__ __forceinline__ void ct_link(float u, const float* col, float tau, float* dF, float* gm) {
+// e^x and e^x - 1 of one node, branch-free: for |x| < 1/2 the Taylor series of e^x - 1 to x^8 (remainder
+// below x^9 / 9!, i.e. 1.4e-8 relative), which keeps e^x - 1 exact near 0; otherwise e^x itself.
+__host__ __device__ __forceinline__ void ct_node(float x, float* y, float* e) {
+    const float p = x * fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, 1.f / 40320.f, 1.f / 5040.f),
+                                                                        1.f / 720.f), 1.f / 120.f), 1.f / 24.f),
+                                              1.f / 6.f), 0.5f), 1.f);
+    const float ex = ct_exp(x);
+    const bool small = fabsf(x) < 0.5f;
+    *y = small ? p : ex - 1.f;
+    *e = small ? 1.f + p : ex;
+}
+
+// The usual case (w = |u| oma <= 0.1), branch-free: dF = F(u, D) - D and eg = G(u, D) / tau by the
+// 2-node rule, from the first four column constants {a, oma, q2[0], q2[1]}.  The nodes sit at m -+ z / u
+// around the column midpoint m = a + oma / 2 (z = u oma / (2 sqrt 3), |z| <= 0.029), so one exponential
+// at m and the series of e^{-+z} - 1 (even part z^2/2 (1 + z^2/12), odd part z (1 + z^2/6); remainder
+// below z^5 / 120) give both: e^{u rho} - 1 = (e^{u m} - 1) + e^{u m} (e^{-+z} - 1).
+__host__ __device__ __forceinline__ void ct_link2(float u, float a, float oma, float q0, float q1, float* dF,
+                                                 float* eg) {
+    float em1, em;
+    ct_node(u * fmaf(oma, 0.5f, a), &em1, &em);
+    const float z = u * oma * 0.28867513459481288f;
+    const float z2 = z * z;
+    const float ev = 0.5f * z2 * fmaf(z2, 1.f / 12.f, 1.f);
+    const float od = z * fmaf(z2, 1.f / 6.f, 1.f);
+    const float y0 = fmaf(em, ev - od, em1), y1 = fmaf(em, ev + od, em1);
+    *dF = fmaf(q0, y0, q1 * y1);
+    *eg = oma * em * (1.f + ev);
+}
+
+// Any element: dF = F(u, D) - D and eg = G(u, D) / tau = int_a^1 e^{u rho} d rho, from the column
+// constants col = {a, oma, q2[2], q4[4]}.
+__host__ __device__ __forceinline__ void ct_link(float u, const float* col, float tau, float* dF, float* eg) {
     const float a = col[0], oma = col[1];
     const float w = fabsf(u) * oma;
     if (w <= CT_W2_MAX) {
-        float y0, y1, e0, e1;
-        ct_node(u * fmaf(oma, GL2_E0, a), &y0, &e0);
-        ct_node(u * fmaf(oma, GL2_E1, a), &y1, &e1);
-        *dF = fmaf(col[2], y0, col[3] * y1);
-        *gm = 0.5f * (e0 + e1);
+        ct_link2(u, a, oma, col[2], col[3], dF, eg);
     } else if (w <= 1.f) {
         float y0, y1, y2, y3, e0, e1, e2, e3;
         ct_node(u * fmaf(oma, GL4_E0, a), &y0, &e0);
@@ -69,7 +97,7 @@ __host__ __device__ __forceinline__ void ct_link(float u, const float* col, floa
         ct_node(u * fmaf(oma, GL4_E2, a), &y2, &e2);
         ct_node(u * fmaf(oma, GL4_E3, a), &y3, &e3);
         *dF = fmaf(col[4], y0, fmaf(col[5], y1, fmaf(col[6], y2, col[7] * y3)));
-        *gm = 0.5f * fmaf(GL4_W0, e0 + e3, GL4_W1 * (e1 + e2));
+        *eg = 0.5f * oma * fmaf(GL4_W0, e0 + e3, GL4_W1 * (e1 + e2));
     } else {
         int P = (int)ceilf(w);
         if (P > CT_PANELS_MAX) P = CT_PANELS_MAX;
@@ -88,7 +116,7 @@ __host__ __device__ __forceinline__ void ct_link(float u, const float* col, floa
             sg += GL4_W0 * (e0 + e3) + GL4_W1 * (e1 + e2);
         }
         *dF = 0.5f * tau * h * sf;
-        *gm = 0.5f * sg / (float)P;
+        *eg = 0.5f * h * sg;
     }
 }
 

@@ -66,8 +66,9 @@ struct Buffers {
     double* Gacc = nullptr;       // chunked: [n][n] E X^T summed over the chunks
     int64_t ldn = 0;              // leading dim of the W parts (n rounded up to 64)
     void* E = nullptr;            // F32: float [n][Tpad] dt exp(U); 16-bit: the same, bin-blocked
-    double* part_e = nullptr;     // [n][ntile_t]  per-(row, bin tile) sums of exp(U)
-    double* part_s = nullptr;     // [n][ntile_t] per-(row, bin tile) sums of U - b over the spike bins
+    double* part_e = nullptr;     // [n][ntile_t]  per-(row, bin tile) sums of exp(U); continuous time: two
+                                  // such planes, one per half of each tile's columns
+    double* part_s = nullptr;     // [n][ntile_t] per-(row, bin tile) sums of U - b over the spike bins (idem)
     float* part_g = nullptr;      // [nsplit][n][n] FP32 partial sums of E X^T
     void* Wsplit = nullptr;       // 16-bit: hi and lo parts of W, [2][n][ldn]
     int* flags = nullptr;         // [4] device error flags

@@ -26,6 +26,8 @@ struct ReduceArgs {
     const double* part_s;  // [n][ntile] sums of U - b at the spike bins
     const double* qd;
     const double* part_e;  // [n][ntile]
+    const double* part_s2; // second planes of part_s and part_e (continuous time), or null
+    const double* part_e2;
     double* L_rows;
     double* gb;
 };
@@ -41,6 +43,14 @@ __global__ void reduce_rows_kernel(const __grid_constant__ ReduceArgs A) {
     double integ = 0.0;
     const double* pe = A.part_e + (int64_t)i * A.ntile;
     for (int64_t t = lane; t < A.ntile; t += 32) integ += pe[t];
+    if (A.part_e2) {
+        const double* ps2 = A.part_s2 + (int64_t)i * A.ntile;
+        const double* pe2 = A.part_e2 + (int64_t)i * A.ntile;
+        for (int64_t t = lane; t < A.ntile; t += 32) {
+            spk += ps2[t];
+            integ += pe2[t];
+        }
+    }
     spk = warp_sum(spk);
     integ = warp_sum(integ);
     if (lane == 0) {
@@ -161,6 +171,8 @@ cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_
     A.part_s = c->buf.part_s;
     A.qd = c->buf.qd;
     A.part_e = c->buf.part_e;
+    A.part_s2 = P.ct ? c->buf.part_s + (int64_t)P.n * ntile : nullptr;
+    A.part_e2 = P.ct ? c->buf.part_e + (int64_t)P.n * ntile : nullptr;
     A.L_rows = L_rows;
     A.gb = gb;
     reduce_rows_kernel<<<(P.n + 7) / 8, 256, 0, c->stream>>>(A);

@@ -42,7 +42,13 @@ namespace glm {
 
 namespace {
 
-constexpr int NUM_THREADS = 192;
+// warp 0 TMA, warp 1 MMA, then the epilogue warps: 4 (one per TMEM lane quarter), or 8 for the
+// continuous-time U product, whose epilogue does several times the grid's arithmetic per element (two
+// warps per lane quarter, each taking half of the tile's columns)
+template <int MODE, bool CT>
+constexpr int epi_warps() { return (MODE == 0 && CT) ? 8 : 4; }
+template <int MODE, bool CT>
+constexpr int kthreads() { return 64 + 32 * epi_warps<MODE, CT>(); }
 constexpr int SP_REG = 12;  // spike bins per (row, 256-bin tile) held in registers by the epilogue
 constexpr int TUNE_UPM_MAX = 8;  // most units per SM the autotuner tries for E X^T
 constexpr uint32_t TMEM_COLS = 512;
@@ -221,7 +227,7 @@ __device__ __forceinline__ uint32_t pack16<__half>(float lo, float hi) {
 // tile's local Z_loc starts at 0 at its first bin t0, and Z[t] = a^(t-t0) Z[t0] + Z_loc[t]; a per-row
 // combine (reduce.cu) chains the tiles.
 template <int MODE, typename T16, bool TAU, bool BATCH, bool CT = false>
-__global__ void __launch_bounds__(NUM_THREADS, 1)
+__global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
                    const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1,
                    const __grid_constant__ TcArgs Ag, const TcBatch* __restrict__ batch) {
@@ -270,7 +276,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         for (int a = 0; a < 2; ++a) {
             tc::mbar_init(&tfull[a], 1);
-            tc::mbar_init(&tempty[a], 4);
+            tc::mbar_init(&tempty[a], epi_warps<MODE, CT>());
         }
         tc::mbar_init(done, 1);
         *abort_flag = 0;
@@ -428,7 +434,96 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             }
             tc::tc_fence_after();
             const uint32_t lane_base = tmem_base + ((uint32_t)(q * 32) << 16);
-            if (MODE == 0) {
+            if constexpr (MODE == 0 && CT) {
+                // Continuous-time columns.  Per column m of length D_m: the exact integral of the rate,
+                // e^{b} F(u, D_m) with u = (W V)_i at the column start, and the gradient weight
+                // E'_m = e^{b} G(u, D_m) of Eq. 14 (ct_link.cuh).  With e^{b} = e^{c} e^{sh} as on the grid,
+                // each half-warp pair writes its share of the tile's sums: e^{c} e^{sh} (duration + sum (F - D)),
+                // the duration counted by the first half.  Columns go 8 at a time (one 16-byte word of E').
+                const int half = (warp - 2) >> 2;
+                const uint32_t taddr = lane_base + (uint32_t)(buf * BN);
+                const int32_t il = w.m0 + row;
+                const int32_t i = il < s_m[p] ? (A.rows ? A.rows[il] : il) : A.n;
+                const int64_t gt0 = A.t_base + w.n0;
+                const int64_t gtile = gt0 / BN;
+                const double ebi = (i < A.n) ? A.eb[i] : 0.0;
+                const float sh = (i < A.n) ? fminf(A.b[i] - EXP_SPLIT_FLOOR, 0.f) : 0.f;
+                const float esh = __expf(sh);
+                const float tgeb = (float)(ebi * (double)A.ct_tau) * esh;
+                bool bad = !(tgeb <= 3.0e38f);
+                float s = 0.f, spv = 0.f;
+                int64_t kb = 0, ke = 0;
+                if (i < A.n) {
+                    const int64_t sgi = (int64_t)i * A.nseg + gtile, o0 = A.offs[i];
+                    kb = o0 + A.seg_first[sgi];
+                    ke = (gtile + 1 < A.nseg) ? o0 + A.seg_first[sgi + 1] : A.offs[i + 1];
+                }
+                int sb[SP_REG];
+#pragma unroll
+                for (int u = 0; u < SP_REG; ++u) sb[u] = (kb + u < ke) ? (int)(A.bins[kb + u] - gt0) : BN;
+                T16* erow = reinterpret_cast<T16*>(A.E) + ((int64_t)(w.n0 / 64) * A.n + i) * 64;
+                const float4* colq = reinterpret_cast<const float4*>(A.colc) + 2 * gt0;
+#pragma unroll 1
+                for (int g = half * (BN / 16); g < (half + 1) * (BN / 16); ++g) {
+                    const int c0 = g * 8;  // first column of the group within the tile
+                    uint32_t r[8];
+                    tc::tmem_ld8(taddr + c0, r);
+                    tc::tmem_ld_wait();
+                    uint32_t sm = 0;  // spike mask: bit e <-> column c0 + e
+#pragma unroll
+                    for (int u = 0; u < SP_REG; ++u) {
+                        const uint32_t d = (uint32_t)(sb[u] - c0);
+                        sm |= (d < 8u) ? (1u << d) : 0u;
+                    }
+                    for (int64_t k = kb + SP_REG; k < ke; ++k) {
+                        const uint32_t d = (uint32_t)(A.bins[k] - gt0 - c0);
+                        sm |= (d < 8u) ? (1u << d) : 0u;
+                    }
+                    float fv[8], gv[8];
+                    uint32_t slow = 0;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const float4 k = __ldg(colq + 2 * (c0 + e));  // a, 1 - a, 2-node factors
+                        const float u = __uint_as_float(r[e]);
+                        ct_link2(u, k.x, k.y, k.z, k.w, &fv[e], &gv[e]);
+                        slow |= (fabsf(u) * k.y > CT_W2_MAX) ? (1u << e) : 0u;
+                    }
+                    if (__any_sync(0xffffffffu, slow != 0u)) {  // columns where the exponent moves by > 0.1
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            if ((slow >> e) & 1u) {
+                                const float4 k0 = __ldg(colq + 2 * (c0 + e)), k1 = __ldg(colq + 2 * (c0 + e) + 1);
+                                const float col[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
+                                ct_link(__uint_as_float(r[e]), col, A.ct_tau, &fv[e], &gv[e]);
+                            }
+                        }
+                    }
+                    uint32_t pk[4];
+#pragma unroll
+                    for (int e = 0; e < 8; e += 2) {
+                        const int64_t t = gt0 + c0 + e;
+                        const bool v0 = t < A.T, v1 = t + 1 < A.T;
+                        float e0 = tgeb * gv[e], e1 = tgeb * gv[e + 1];
+                        bad |= (v0 && !(fabsf(fv[e]) <= 3.0e38f && e0 <= 3.0e38f)) ||
+                               (v1 && !(fabsf(fv[e + 1]) <= 3.0e38f && e1 <= 3.0e38f));
+                        if (v0) s += fv[e]; else e0 = 0.f;
+                        if (v1) s += fv[e + 1]; else e1 = 0.f;
+                        if ((sm >> e) & 1u) spv += __uint_as_float(r[e]);
+                        if ((sm >> (e + 1)) & 1u) spv += __uint_as_float(r[e + 1]);
+                        pk[e >> 1] = pack16<T16>(e0, e1);
+                    }
+                    if (i < A.n)
+                        *reinterpret_cast<uint4*>(erow + (int64_t)(c0 >> 6) * A.n * 64 + (c0 & 63)) =
+                            make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                }
+                if (i < A.n) {
+                    const double rsum = (double)esh * ((half == 0 ? A.tile_span[gtile] : 0.0) + (double)s);
+                    const int64_t o = (int64_t)half * A.n * A.ntile + (int64_t)i * A.ntile + gtile;
+                    A.part_e[o] = ebi * rsum;
+                    A.part_s[o] = (double)spv;
+                }
+                if (bad && i < A.n) atomicOr(A.flags, 1);
+            } else if constexpr (MODE == 0) {
                 // e^{U} = e^{b_i} e^{v}, v = (W X)_i[t]: e^{b_i} in FP64, and the row sum is kept as
                 // e^{b_i} (count + sum (e^{v} - 1)), so quiet bins (v ~ 0) add no FP32 rounding of b + v.
                 const uint32_t taddr = lane_base + (uint32_t)(buf * BN);
@@ -439,9 +534,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const double ebi = (i < A.n) ? A.eb[i] : 0.0;
                 const float sh = (i < A.n) ? fminf(A.b[i] - EXP_SPLIT_FLOOR, 0.f) : 0.f;  // U - c = v + sh
                 const float dteb = (float)(A.dt * ebi);
-                // continuous time: E' = e^{b} G = e^{c} e^{sh} tau (1 - a) gm
-                const float esh = CT ? __expf(sh) : 1.f;
-                const float tgeb = CT ? (float)(ebi * (double)A.ct_tau) * esh : 0.f;
                 double rsum = 0.0;
                 bool bad = false;
                 float zl = 0.f, pw = 1.f, p1 = 0.f, p2 = 0.f, p3 = 0.f, p4 = 0.f, spv = 0.f;
@@ -483,45 +575,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         const float v0f = __uint_as_float(r[e]), v1f = __uint_as_float(r[e + 1]);
                         const bool v0 = t < A.T, v1 = t + 1 < A.T;
                         const bool s0 = (sm >> e) & 1u, s1 = (sm >> (e + 1)) & 1u;
-                        float e0, e1;
-                        if constexpr (CT) {
-                            // columns t, t + 1: F - D and G / (tau oma) from the column constants
-                            const float4* cp = reinterpret_cast<const float4*>(A.colc) + 2 * t;
-                            const float4 c0 = __ldg(cp), c1 = __ldg(cp + 1), c2 = __ldg(cp + 2), c3 = __ldg(cp + 3);
-                            const float k0[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-                            const float k1[8] = {c2.x, c2.y, c2.z, c2.w, c3.x, c3.y, c3.z, c3.w};
-                            float f0, g0, f1, g1;
-                            ct_link(v0f, k0, A.ct_tau, &f0, &g0);
-                            ct_link(v1f, k1, A.ct_tau, &f1, &g1);
-                            e0 = tgeb * k0[1] * g0;
-                            e1 = tgeb * k1[1] * g1;
-                            bad |= (v0 && !(fabsf(f0) <= 3.0e38f && e0 <= 3.0e38f)) ||
-                                   (v1 && !(fabsf(f1) <= 3.0e38f && e1 <= 3.0e38f));
-                            if (v0) s += f0; else e0 = 0.f;
-                            if (v1) s += f1; else e1 = 0.f;
+                        float e0 = __expf(v0f + sh);
+                        float e1 = __expf(v1f + sh);
+                        bad |= (v0 && !(e0 <= 3.0e38f)) || (v1 && !(e1 <= 3.0e38f));
+                        if (v0) {
+                            s += e0 - 1.f;
+                            ++cnt;
                         } else {
-                            e0 = __expf(v0f + sh);
-                            e1 = __expf(v1f + sh);
-                            bad |= (v0 && !(e0 <= 3.0e38f)) || (v1 && !(e1 <= 3.0e38f));
-                            if (v0) {
-                                s += e0 - 1.f;
-                                ++cnt;
-                            } else {
-                                e0 = 0.f;
-                            }
-                            if (v1) {
-                                s += e1 - 1.f;
-                                ++cnt;
-                            } else {
-                                e1 = 0.f;
-                            }
+                            e0 = 0.f;
+                        }
+                        if (v1) {
+                            s += e1 - 1.f;
+                            ++cnt;
+                        } else {
+                            e1 = 0.f;
                         }
                         if (s0) spv += v0f;
                         if (s1) spv += v1f;
-                        if constexpr (CT)
-                            pk[e >> 1] = pack16<T16>(e0, e1);
-                        else
-                            pk[e >> 1] = pack16<T16>(dteb * e0, dteb * e1);
+                        pk[e >> 1] = pack16<T16>(dteb * e0, dteb * e1);
                         if (TAU) {
                             p1 = fmaf(e0, pw, p1);
                             p2 = fmaf(e0, zl, p2);
@@ -550,10 +621,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     }
                 }
                 bad |= !(dteb <= 3.0e38f);
-                if (CT) {
-                    rsum = (double)esh * (A.tile_span[gtile] + rsum);  // e^{sh} sum_m F_m
-                    bad |= !(tgeb <= 3.0e38f);
-                }
                 if (i < A.n) {
                     A.part_e[(int64_t)i * A.ntile + gtile] = ebi * rsum;
                     A.part_s[(int64_t)i * A.ntile + gtile] = (double)spv;
@@ -730,8 +797,8 @@ static cudaError_t run(glm_ctx* c, const CUtensorMap& a0, const CUtensorMap& a1,
         if (e != cudaSuccess) return e;
     }
     if (grid <= 0) grid = A.units < c->sm_count ? A.units : c->sm_count;
-    tc_gemm_kernel<MODE, T16, TAU, BATCH, CT><<<(unsigned)grid, NUM_THREADS, smem, c->stream>>>(a0, a1, b0, b1, A,
-                                                                                               batch);
+    tc_gemm_kernel<MODE, T16, TAU, BATCH, CT><<<(unsigned)grid, kthreads<MODE, CT>(), smem, c->stream>>>(
+        a0, a1, b0, b1, A, batch);
     return cudaGetLastError();
 }
 
