@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--ct-seconds", type=float, default=180.0,
                     help="also evaluate and fit the continuous-time form on this much of the recording, its spikes "
                          "moved off the grid (0: off)")
+    ap.add_argument("--no-ct-fit", action="store_true", help="continuous-time leg without its fits (profiling)")
+    ap.add_argument("--synfire", action="store_true",
+                    help="also fit the N = 2000 synfire-chain recording and find its links by Ward clustering")
+    ap.add_argument("--synfire-seconds", type=float, default=3600.0)
     return ap.parse_args()
 
 
@@ -286,20 +290,91 @@ def run_ct(args, glm, w, device, stream, prec):
         res["grid_same_window"] = {"bins": nb, "ms_per_eval": gms}
         fits = {}
         Ws = {}
-        for name, c in (("continuous", ct), ("grid", gr)):
+        for name, c in (() if args.no_ct_fit else (("continuous", ct), ("grid", gr))):
             r = c.fit(eta=args.fit_eta, max_iter=args.fit_max_iter)
             _, rep = glm.classify(r["W"].cpu().numpy().astype(np.float64), "gmm", truth=truth, types=w["types"])
             fits[name] = {"seconds": r["report"]["seconds"], "iterations": r["report"]["iterations"],
                           "evaluations": r["report"]["evaluations"], "mer": rep["mer"]}
             Ws[name] = r["W"]
-        dW = (Ws["continuous"] - Ws["grid"]).abs()
-        fits["max_abs_W_difference"] = float(dW.max())
-        fits["mean_abs_W_difference"] = float(dW.mean())
-        res["fit"] = fits
+        if Ws:
+            dW = (Ws["continuous"] - Ws["grid"]).abs()
+            fits["max_abs_W_difference"] = float(dW.max())
+            fits["mean_abs_W_difference"] = float(dW.mean())
+            res["fit"] = fits
     finally:
         ct.close()
         gr.close()
     return res
+
+
+def chain_links(W_true, w_syn):
+    """The links of the planted synfire chain, in chain order, from the generating weights: every neuron of
+    link g + 1 receives exactly w_syn from every neuron of link g (no other weight has that value)."""
+    import numpy as np
+    hit = np.isclose(W_true, w_syn)
+    targets = {}
+    for j in np.nonzero(hit.any(axis=0))[0]:
+        targets.setdefault(tuple(np.nonzero(hit[:, j])[0]), []).append(int(j))
+    groups = {frozenset(v): frozenset(k) for k, v in targets.items()}  # link -> next link
+    heads = [g for g in groups if not any(g <= nxt for nxt in groups.values())]
+    links = [heads[0]] if heads else []
+    while links and links[-1] in groups:
+        links.append(groups[links[-1]])
+    return [sorted(l) for l in links]
+
+
+def links_found(Z, links, m):
+    """Links that some subtree of the dendrogram holds >= 90 % of while being >= 90 % pure."""
+    work = {k: {k} for k in range(m)}
+    subtrees = []
+    for q, (a, b, _, _) in enumerate(Z):
+        c = work.pop(int(a)) | work.pop(int(b))
+        work[m + q] = c
+        if len(c) <= 4 * max(len(l) for l in links):
+            subtrees.append(c)
+    found = []
+    for l in links:
+        L = set(l)
+        ok = any(len(c & L) >= 0.9 * len(L) and len(c & L) >= 0.9 * len(c) for c in subtrees)
+        found.append(bool(ok))
+    return found
+
+
+def run_synfire(args, glm, device, stream, prec):
+    """The synfire recording (N = 2000 with a 10 x 50 chain, ids shuffled, as in Sec. 3.4): fit, classify,
+    and find the chain's links by Ward clustering of the fitted weights, by outgoing connections (links
+    that project to a next link) and by incoming ones (links that receive from a previous link)."""
+    import numpy as np
+    import torch
+    import synth
+    from oracle.classify import truth_labels  # ground-truth labels from the generating W (no fitting)
+    cfg = synth.WORKLOADS["glm_n2000_synfire_t3600s"]
+    nb = int(round(args.synfire_seconds / cfg["dt"]))
+    t0 = time.perf_counter()
+    w = synth.make_workload("glm_n2000_synfire_t3600s", n_bins=nb)
+    gen_s = time.perf_counter() - t0
+    links = chain_links(w["W_true"], cfg["w_syn"])
+    c = glm.GLM(device, stream=stream)
+    try:
+        c.set_problem(w["offs"], w["bins"], nb, w["dt"], w["tau"], prec=prec)
+        r = c.fit(eta=args.fit_eta, max_iter=args.fit_max_iter)
+        Wf = r["W"]
+        _, rep = glm.classify(Wf.cpu().numpy().astype(np.float64), "gmm", truth=truth_labels(w["W_true"]),
+                              types=w["types"])
+        torch.cuda.synchronize(device)
+        t1 = time.perf_counter()
+        Zo = c.ward(Wf, by="out")
+        Zi = c.ward(Wf, by="in")
+        ward_s = time.perf_counter() - t1
+    finally:
+        c.close()
+    fo, fi = links_found(Zo, links, w["n"]), links_found(Zi, links, w["n"])
+    return {"workload": f"glm_n2000_synfire: N = 2000, {nb * cfg['dt']:g} s, 10 x 50 synfire links, ids shuffled",
+            "generation_s": gen_s, "fit": {"seconds": r["report"]["seconds"], "iterations": r["report"]["iterations"],
+                                           "evaluations": r["report"]["evaluations"], "mer": rep["mer"]},
+            "ward_seconds_two_linkages": ward_s,
+            "links": len(links), "found_by_outgoing": fo, "found_by_incoming": fi,
+            "found_by_either": int(sum(a or b for a, b in zip(fo, fi)))}
 
 
 def main():
@@ -475,6 +550,8 @@ def main():
         line["batch"] = run_batch(args, glm, device, prec)
     if args.ct_seconds > 0 and prec != "f32":
         line["continuous_time"] = run_ct(args, glm, w, device, stream, prec)
+    if args.synfire:
+        line["synfire"] = run_synfire(args, glm, device, stream, prec)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, os.cpu_count() or 1)
         line["cpu_baseline"].pop("seconds", None)

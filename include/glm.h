@@ -149,6 +149,49 @@ int glm_problem_columns(const glm_ctx* ctx, int64_t* n_columns);
  * outputs). */
 int glm_ct_interval(double u, double D, double tau, double* F_host, double* G_host);
 
+/* ---- per-neuron time constants and delays (Sec. 2.2, Sec. 2.4 Eq. 15) ----
+ * The paper's kernel h_i(t) = H(t) exp(-t / tau_i) belongs to the target neuron i, and Eq. 15 shifts every
+ * source train S_j by the delay D_ij of the target that receives it.  The rows (targets) are grouped into
+ * classes of equal (tau, delay); one context per class holds that class's filtered trains (all N sources,
+ * filtered with the class's tau and shifted by its delay) and evaluates and fits only the class's rows.
+ * Number the neurons so that each class is a contiguous block of rows. */
+
+/* Delay in bins with which every source train reaches the rows (delay_bins >= 1; 1, the default, is the
+ * one-bin delay of the grid recursion X[t] = a X[t-1] + S[t-1]).  Above 1 the filter reads each spike
+ * delay_bins - 1 bins later (spikes pushed past the recording drop out); the rows' own spikes, for the
+ * spike-time term, stay where they are.  Takes effect at the next glm_set_problem (grid form).
+ * Errors: INVALID_ARG (delay_bins < 1). */
+int glm_set_source_delay(glm_ctx* ctx, int32_t delay_bins);
+
+/* Restrict evaluations and fits of the current problem to rows [r0, r1) (0 <= r0 < r1 <= n; r0 = 0 with
+ * r1 = 0 or n restores all rows).  glm_loglik_grad then forms U, the rates and the gradient for those rows
+ * only and returns L_i = 0, dL/dW_i. = 0 and dL/db_i = 0 for the others (L_total sums the range);
+ * glm_fit leaves the other rows' W and b as given, with state GLM_ROW_EXCLUDED.  Not with glm_fit_batch.
+ * Errors: INVALID_ARG, NO_PROBLEM. */
+int glm_set_row_range(glm_ctx* ctx, int32_t r0, int32_t r1);
+
+
+/* Ward's minimum-variance hierarchical clustering of neurons by their weights (Sec. 3.4.2, Ward 1963): the
+ * paper clusters the reconstructed connectivity by outgoing weights (columns of W) and, inside clusters,
+ * by incoming weights (rows) to expose the links of a synfire chain.
+ *   W_dev:        float[n * n] weights (device, row-major, W[i, j] = weight of j -> i).
+ *   by:           0: point k is the column W[:, subset[k]] (outgoing); 1: the row W[subset[k], :] (incoming).
+ *   subset_host:  int32[m] neuron indices to cluster, or NULL for all n (m is then n).
+ *   Z_host:       double[(m - 1) * 4] the linkage in SciPy's layout: row q = (id_a, id_b, height, size),
+ *                 ids < m are the points (positions in the subset), m + q the cluster made by row q,
+ *                 id_a < id_b, heights non-decreasing; height = sqrt(2 x the rise in within-cluster sum of
+ *                 squares) = the Ward distance.
+ * Squared distances in FP64 on the device, then a nearest-neighbour-chain walk with the Lance-Williams
+ * update in one block; uses O(m^2 + m n) doubles of temporary device memory and the context's stream
+ * (the context needs no problem).  Errors: INVALID_ARG, OOM, CUDA, NONFINITE (the walk did not complete:
+ * non-finite weights). */
+int glm_ward(glm_ctx* ctx, const float* W_dev, int32_t n, int32_t by, const int32_t* subset_host, int32_t m,
+             double* Z_host);
+
+/* Labels 0 .. k-1 of the k clusters left after the first m - k merges of a linkage (clusters numbered by
+ * their smallest member).  Host function.  Errors: INVALID_ARG. */
+int glm_ward_cut(const double* Z_host, int32_t m, int32_t k, int32_t* labels_host);
+
 /* Recompute the per-problem caches (filter scan, spike term) from the device-resident spikes, for a new
  * tau (tau > 0) or, with tau <= 0, the current one.  Errors: NO_PROBLEM, INVALID_ARG, CUDA. */
 int glm_prepare(glm_ctx* ctx, double tau);
@@ -194,6 +237,8 @@ int glm_loglik_grad(glm_ctx* ctx, const float* W_dev, const float* b_dev, double
                               gain below gain_floor (|L_i| + q_i), so no further increase can be told apart
                               from the evaluation's rounding (typical of the 16-bit precisions near the
                               optimum, whose L_i carry a relative error of ~1e-7) */
+#define GLM_ROW_EXCLUDED 5 /* outside the context's row range (glm_set_row_range): not fitted, W_i and b_i
+                              returned as given */
 
 #define GLM_STATUS_NOT_CONVERGED 1 /* some row reached max_iter */
 #define GLM_STATUS_STALLED 2       /* some row's line search failed (no increase found) */
@@ -222,6 +267,7 @@ typedef struct {
     int32_t evaluations; /* log-likelihood evaluations (U products), trials included */
     int32_t gradients;   /* gradient products */
     int32_t converged, maxiter, stalled, degenerate, at_floor; /* rows in each final state */
+    int32_t excluded;    /* rows outside the row range */
     double L;            /* final log-likelihood sum_i L_i */
     double seconds;      /* wall time of the call */
 } glm_fit_report_t;
@@ -253,6 +299,15 @@ int glm_fit(glm_ctx* ctx, const glm_fit_opts_t* opts, float* W_dev, float* b_dev
 #define GLM_FIT_BATCH_MAX 32
 int glm_fit_batch(glm_ctx* const* ctxs, int32_t n_prob, const glm_fit_opts_t* opts, float* const* W_dev,
                   float* const* b_dev, int8_t* const* row_status_host, glm_fit_report_t* reports);
+
+/* Fit every class: glm_fit on each context in turn (each with its own tau, delay and row range; the row
+ * ranges must not overlap), all writing into the one W_dev (n x n) and b_dev (n).  row_status_host
+ * (optional, int8[n]) receives each row's state from the context that owns it (GLM_ROW_EXCLUDED for rows
+ * in no range); the report sums the classes' counts and times (iterations: the largest).  Returns the
+ * most severe status of the classes' fits.  Errors: INVALID_ARG (overlapping ranges, differing n or
+ * device), NO_PROBLEM, and those of glm_fit. */
+int glm_fit_classes(glm_ctx* const* ctxs, int32_t n_class, const glm_fit_opts_t* opts, float* W_dev, float* b_dev,
+                    int8_t* row_status_host, glm_fit_report_t* report);
 
 /* Cross-validation of the l1 penalty (Sec. 2.5) and of the kernel time constant (Sec. 3.2): for every tau in
  * taus and every alpha in alphas, fit W, b on ctx_train (glm_fit with opts and that alpha) and evaluate the

@@ -66,7 +66,8 @@ class FitOpts(ctypes.Structure):
 class FitReport(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("evaluations", ctypes.c_int32), ("gradients", ctypes.c_int32),
                 ("converged", ctypes.c_int32), ("maxiter", ctypes.c_int32), ("stalled", ctypes.c_int32),
-                ("degenerate", ctypes.c_int32), ("at_floor", ctypes.c_int32), ("L", ctypes.c_double),
+                ("degenerate", ctypes.c_int32), ("at_floor", ctypes.c_int32), ("excluded", ctypes.c_int32),
+                ("L", ctypes.c_double),
                 ("seconds", ctypes.c_double)]
 
 
@@ -75,7 +76,7 @@ class TuneReport(ctypes.Structure):
                 ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_float)]
 
 
-ROW_STATUS = {0: "converged", 1: "maxiter", 2: "stalled", 3: "degenerate", 4: "at_floor"}
+ROW_STATUS = {0: "converged", 1: "maxiter", 2: "stalled", 3: "degenerate", 4: "at_floor", 5: "excluded"}
 ERRORS[-11] = "GLM_ERR_SCRATCH_TOO_SMALL"
 SIGNATURES["glm_loglik_noalloc"] = ([_i32, _i64, _f64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int)
 SIGNATURES["glm_fit_default_opts"] = ([ctypes.POINTER(FitOpts)], None)
@@ -83,6 +84,12 @@ SIGNATURES["glm_fit"] = ([_vp, ctypes.POINTER(FitOpts), _vp, _vp, _vp, ctypes.PO
 SIGNATURES["glm_fit_batch"] = ([_vp, _i32, ctypes.POINTER(FitOpts), _vp, _vp, _vp, ctypes.POINTER(FitReport)], ctypes.c_int)
 SIGNATURES["glm_autotune"] = ([_vp, _vp], ctypes.c_int)
 SIGNATURES["glm_set_chunk_bins"] = ([_vp, _i64], ctypes.c_int)
+SIGNATURES["glm_set_source_delay"] = ([_vp, _i32], ctypes.c_int)
+SIGNATURES["glm_set_row_range"] = ([_vp, _i32, _i32], ctypes.c_int)
+SIGNATURES["glm_fit_classes"] = ([_vp, _i32, ctypes.POINTER(FitOpts), _vp, _vp, _vp, ctypes.POINTER(FitReport)],
+                                 ctypes.c_int)
+SIGNATURES["glm_ward"] = ([_vp, _vp, _i32, _i32, _vp, _i32, _vp], ctypes.c_int)
+SIGNATURES["glm_ward_cut"] = ([_vp, _i32, _i32, _vp], ctypes.c_int)
 SIGNATURES["glm_set_problem_ct"] = ([_vp, _i32, _f64, _f64, _f64, _f64, _vp, _vp, ctypes.c_int], ctypes.c_int)
 SIGNATURES["glm_problem_columns"] = ([_vp, ctypes.POINTER(_i64)], ctypes.c_int)
 SIGNATURES["glm_ct_interval"] = ([_f64, _f64, _f64, ctypes.POINTER(_f64), ctypes.POINTER(_f64)], ctypes.c_int)
@@ -158,6 +165,47 @@ def fit_batch(contexts, *, method: str = "lbfgs", m: int = 10, max_iter: int = 5
     out = [dict(W=Ws[p], b=bs[p], status=sts[p], report={f: getattr(reps[p], f) for f, _ in FitReport._fields_})
            for p in range(k)]
     return out, rc
+
+
+def fit_classes(contexts, W=None, b=None, *, method: str = "lbfgs", m: int = 10, max_iter: int = 500,
+                eta: float = 1e-10, c1: float = 1e-4, max_halvings: int = 40, gain_floor: float = -1.0,
+                alpha: float = 0.0, eps: float = 1e-6):
+    """Fit the row classes held by several contexts (glm_fit_classes): each context has its own tau, source
+    delay and row range, and all of them write into one W (n x n) and b (n).  W and b, when given, are the
+    warm start (and the values kept for rows in no range).  Returns dict(W, b, status, report, rc)."""
+    lib = load_library()
+    k = len(contexts)
+    if k == 0:
+        raise ValueError("no contexts")
+    g0 = contexts[0]
+    torch = g0.torch
+    dev = f"cuda:{g0.device}"
+    warm = W is not None
+    Wd = (W.to(device=dev, dtype=torch.float32).clone() if warm
+          else torch.zeros((g0.n, g0.n), dtype=torch.float32, device=dev)).contiguous()
+    bd = (b.to(device=dev, dtype=torch.float32).clone() if warm
+          else torch.zeros(g0.n, dtype=torch.float32, device=dev)).contiguous()
+    status = np.zeros(g0.n, dtype=np.int8)
+    hs = (ctypes.c_void_p * k)(*[g.h for g in contexts])
+    o = FitOpts({"lbfgs": 0, "ga": 1}[method], m, max_iter, eta, c1, max_halvings, int(warm), gain_floor, alpha,
+                eps)
+    rep_ = FitReport()
+    rc = lib.glm_fit_classes(hs, k, ctypes.byref(o), _ptr(Wd), _ptr(bd), status.ctypes.data, ctypes.byref(rep_))
+    if rc < 0:
+        g0._check(rc, "glm_fit_classes")
+    return dict(W=Wd, b=bd, status=status, report={f: getattr(rep_, f) for f, _ in FitReport._fields_}, rc=rc)
+
+
+def ward_cut(Z, k: int) -> np.ndarray:
+    """Labels of the k clusters of a linkage (glm_ward_cut)."""
+    lib = load_library()
+    Z = np.ascontiguousarray(Z, dtype=np.float64)
+    m = Z.shape[0] + 1
+    lab = np.zeros(m, dtype=np.int32)
+    rc = lib.glm_ward_cut(Z.ctypes.data, m, int(k), lab.ctypes.data)
+    if rc != GLM_OK:
+        raise GLMError(rc, "glm_ward_cut")
+    return lab
 
 
 def ct_interval(u: float, D: float, tau: float):
@@ -303,6 +351,27 @@ class GLM:
         self._check(rc, "glm_set_problem_ct")
         self.n, self.tau, self.prec = n, tau, prec
         self.n_bins, self.dt = self.columns(), None
+
+    def set_source_delay(self, delay_bins: int):
+        """Delay of the source trains in bins (>= 1), applied at the next set_problem (glm_set_source_delay)."""
+        self._check(self.lib.glm_set_source_delay(self.h, int(delay_bins)), "glm_set_source_delay")
+
+    def set_row_range(self, r0: int, r1: int):
+        """Evaluate and fit rows [r0, r1) only (glm_set_row_range); (0, 0) restores all rows."""
+        self._check(self.lib.glm_set_row_range(self.h, int(r0), int(r1)), "glm_set_row_range")
+
+    def ward(self, W, by: str = "out", subset=None) -> np.ndarray:
+        """Ward linkage of neurons by their outgoing (by='out') or incoming ('in') weights (glm_ward)."""
+        torch = self.torch
+        Wd = W.to(device=f"cuda:{self.device}", dtype=torch.float32).contiguous()
+        n = Wd.shape[0]
+        sub = None if subset is None else np.ascontiguousarray(subset, dtype=np.int32)
+        m = n if sub is None else sub.size
+        Z = np.zeros((max(m - 1, 0), 4), dtype=np.float64)
+        rc = self.lib.glm_ward(self.h, _ptr(Wd), n, {"out": 0, "in": 1}[by], None if sub is None else sub.ctypes.data,
+                               m, Z.ctypes.data)
+        self._check(rc, "glm_ward")
+        return Z
 
     def columns(self) -> int:
         """Time columns of the current problem (bins, or event columns in continuous time)."""

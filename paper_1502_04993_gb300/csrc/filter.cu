@@ -444,8 +444,16 @@ cudaError_t launch_carry(glm_ctx* c) {
         seg_carry_kernel<<<(P.n + 3) / 4, 128, 0, c->stream>>>(P.n, P.nseg, 0.0, B.seg_mul, B.seg_carry);
         return cudaGetLastError();
     }
-    seg_local_kernel<<<P.n, 256, 0, c->stream>>>(P.n, P.nseg, B.offs, B.bins, B.pow_seg, nullptr, 0.0, B.seg_carry,
-                                                 B.seg_first);
+    if (P.delay_bins > 1) {
+        // delayed sources: first spike per segment of the rows' own spikes; carries of the shifted trains
+        seg_local_kernel<<<P.n, 256, 0, c->stream>>>(P.n, P.nseg, B.offs, B.bins, nullptr, nullptr, 0.0, nullptr,
+                                                     B.seg_first);
+        seg_local_kernel<<<P.n, 256, 0, c->stream>>>(P.n, P.nseg, B.aoffs, B.abins, B.pow_seg, nullptr, 0.0,
+                                                     B.seg_carry, B.aseg_first);
+    } else {
+        seg_local_kernel<<<P.n, 256, 0, c->stream>>>(P.n, P.nseg, B.offs, B.bins, B.pow_seg, nullptr, 0.0,
+                                                     B.seg_carry, B.seg_first);
+    }
     const double a_seg = std::exp(-(double)SEG * P.dt / P.tau);
     seg_carry_kernel<<<(P.n + 3) / 4, 128, 0, c->stream>>>(P.n, P.nseg, a_seg, nullptr, B.seg_carry);
     return cudaGetLastError();
@@ -463,10 +471,10 @@ cudaError_t launch_filter_cache(glm_ctx* c, int64_t s_begin, int64_t s_end) {
     A.s_begin = s_begin;
     A.s_end = s_end < 0 ? P.nseg : s_end;
     A.nchunks = (A.s_end - A.s_begin + CHUNK_SEGS - 1) / CHUNK_SEGS;
-    A.offs = c->buf.offs;
-    A.bins = c->buf.bins;
+    A.offs = c->buf.aoffs;  // the source trains (the spikes, or the spikes shifted by a delay)
+    A.bins = c->buf.abins;
     A.seg_carry = c->buf.seg_carry;
-    A.seg_first = c->buf.seg_first;
+    A.seg_first = c->buf.aseg_first;
     A.X = c->buf.X;
     A.Xlo = c->buf.Xlo;
     A.col_a = c->buf.col_a;
@@ -512,10 +520,10 @@ cudaError_t launch_filter_range(glm_ctx* c, int64_t t0, int64_t t_len, void* out
     A.t_len = t_len;
     A.ldx = ldx;
     A.dtype = (int)dtype;
-    A.offs = c->buf.offs;
-    A.bins = c->buf.bins;
+    A.offs = c->buf.aoffs;
+    A.bins = c->buf.abins;
     A.seg_carry = c->buf.seg_carry;
-    A.seg_first = c->buf.seg_first;
+    A.seg_first = c->buf.aseg_first;
     A.out = out;
     const int64_t warps = (int64_t)A.ngroups * A.nchunks;
     const int64_t blocks = (warps + FW_WARPS - 1) / FW_WARPS;

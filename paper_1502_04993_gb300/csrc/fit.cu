@@ -80,22 +80,25 @@ __device__ __forceinline__ double pen_grad(const FitState& F, int32_t i, int k, 
     return (F.alpha > 0.0 && k - 1 != i) ? F.alpha * w / sqrt(w * w + F.eps) : 0.0;
 }
 
+// Rows outside [r0, r1) (a row range) keep the caller's W_i and b_i and are not fitted.
 __global__ void fit_init_kernel(FitState F, double span, const double* __restrict__ qd, int warm,
-                                const float* __restrict__ W, const float* __restrict__ b) {
+                                const float* __restrict__ W, const float* __restrict__ b, int32_t r0, int32_t r1) {
     const int32_t i = blockIdx.x;
     double* th = F.theta + (int64_t)i * F.d;
     const double q = qd[i];
-    const bool degen = q == 0.0;
+    const bool excl = i < r0 || i >= r1;
+    const bool degen = !excl && q == 0.0;
+    const bool keep = warm || excl;
     for (int k = threadIdx.x; k < F.d; k += blockDim.x) {
         double v;
         if (k == 0)
-            v = degen ? log(1e-3) : (warm ? (double)b[i] : log(q / span));
+            v = degen ? log(1e-3) : (keep ? (double)b[i] : log(q / span));
         else
-            v = (degen || !warm) ? 0.0 : (double)W[(int64_t)i * F.n + (k - 1)];
+            v = (degen || !keep) ? 0.0 : (double)W[(int64_t)i * F.n + (k - 1)];
         th[k] = v;
     }
     if (threadIdx.x == 0) {
-        F.status[i] = degen ? GLM_ROW_DEGENERATE : ACTIVE;
+        F.status[i] = excl ? GLM_ROW_EXCLUDED : degen ? GLM_ROW_DEGENERATE : ACTIVE;
         F.hn[i] = 0;
         F.hs[i] = 0;
         F.iters[i] = 0;
@@ -478,7 +481,8 @@ int fit_start(FitProb& fp, const glm_fit_opts_t* o) {
     const int32_t n = P.n;
     cudaStream_t st = c->stream;
     int rc;
-    fit_init_kernel<<<n, FT, 0, st>>>(fp.F, P.span, c->buf.qd, o->warm_start, fp.W, fp.b);
+    fit_init_kernel<<<n, FT, 0, st>>>(fp.F, P.span, c->buf.qd, o->warm_start, fp.W, fp.b, c->row_r0,
+                                      c->row_r1 < 0 ? n : c->row_r1);
     fit_trial_kernel<<<n, FT, 0, st>>>(fp.F, fp.W32, fp.b32);
     c->launches += 2;
     if ((rc = ck(c, reset_flags(c)))) return rc;
@@ -508,11 +512,11 @@ int fit_end(FitProb& fp, int8_t* row_status, glm_fit_report_t* rep, double secon
         return rc;
     if ((rc = ck(c, cudaMemcpyAsync(Lh.data(), fp.Lr, sizeof(double) * n, cudaMemcpyDeviceToHost, st)))) return rc;
     if ((rc = eval_status(c))) return rc;
-    int cnt[5] = {0, 0, 0, 0, 0};
+    int cnt[6] = {0, 0, 0, 0, 0, 0};
     double Ltot = 0.0;
     for (int32_t i = 0; i < n; ++i) {
         const int s = stat[i];
-        if (s >= 0 && s < 5) cnt[s]++;
+        if (s >= 0 && s < 6) cnt[s]++;
         if (row_status) row_status[i] = (int8_t)s;
         Ltot += Lh[i];
     }
@@ -525,6 +529,7 @@ int fit_end(FitProb& fp, int8_t* row_status, glm_fit_report_t* rep, double secon
         rep->stalled = cnt[GLM_ROW_STALLED];
         rep->degenerate = cnt[GLM_ROW_DEGENERATE];
         rep->at_floor = cnt[GLM_ROW_AT_FLOOR];
+        rep->excluded = cnt[GLM_ROW_EXCLUDED];
         rep->L = Ltot;
         rep->seconds = seconds;
     }

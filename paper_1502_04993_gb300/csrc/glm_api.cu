@@ -192,15 +192,21 @@ int alloc_problem(glm_ctx* c) {
         free_all(c);
         return rc;
     }
-    if (P.ct) {
+    if (P.ct || P.delay_bins > 1) {
         if ((rc = ws_alloc_t(c, &B.aoffs, n + 1)) || (rc = ws_alloc_t(c, &B.abins, P.qa > 0 ? P.qa : 1)) ||
-            (rc = ws_alloc_t(c, &B.aseg_first, (size_t)n * P.nseg)) || (rc = ws_alloc_t(c, &B.ctime, P.Tpad + 1)) ||
-            (rc = ws_alloc_t(c, &B.col_a, P.Tpad)) || (rc = ws_alloc_t(c, &B.colc, 8 * (size_t)P.Tpad)) ||
-            (rc = ws_alloc_t(c, &B.seg_mul, P.nseg)) || (rc = ws_alloc_t(c, &B.tile_span, P.nseg))) {
+            (rc = ws_alloc_t(c, &B.aseg_first, (size_t)n * P.nseg))) {
             free_all(c);
             return rc;
         }
-    } else {
+    }
+    if (P.ct) {
+        if ((rc = ws_alloc_t(c, &B.ctime, P.Tpad + 1)) || (rc = ws_alloc_t(c, &B.col_a, P.Tpad)) ||
+            (rc = ws_alloc_t(c, &B.colc, 8 * (size_t)P.Tpad)) || (rc = ws_alloc_t(c, &B.seg_mul, P.nseg)) ||
+            (rc = ws_alloc_t(c, &B.tile_span, P.nseg))) {
+            free_all(c);
+            return rc;
+        }
+    } else if (P.delay_bins <= 1) {
         B.aoffs = B.offs;
         B.abins = B.bins;
         B.aseg_first = B.seg_first;
@@ -280,12 +286,32 @@ namespace glm {
 
 int set_error(glm_ctx* c, int code, const char* msg) { return fail(c, code, msg); }
 
+// Device list of the rows of the context's row range (allocated with the problem's workspace).
+int ensure_range_rows(glm_ctx* c) {
+    if (c->buf.range_rows) return GLM_OK;
+    const int32_t m = c->row_r1 - c->row_r0;
+    int rc = ws_alloc_t(c, &c->buf.range_rows, m > 0 ? m : 1);
+    if (rc) return rc;
+    std::vector<int32_t> r(m > 0 ? m : 1);
+    for (int32_t k = 0; k < m; ++k) r[k] = c->row_r0 + k;
+    GLM_CK(cudaMemcpyAsync(c->buf.range_rows, r.data(), sizeof(int32_t) * r.size(), cudaMemcpyHostToDevice, c->stream));
+    GLM_CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());  // r is a host temporary
+    return GLM_OK;
+}
+
 // Queue one evaluation at (W, b) on the context's stream; no synchronisation.  With reuse_u the U
 // product is skipped: E and the per-tile sums must already hold the values at this (W, b).
 int eval_enqueue(glm_ctx* c, const float* W, const float* b, double* L_rows, double* G, double* gb, bool want_grad,
                  bool reuse_u, bool tau, const int32_t* rows, int32_t m) {
     const bool tensor = c->pb.prec != GLM_PREC_F32;
     const Problem& P = c->pb;
+    if (!rows && c->row_r1 >= 0) {
+        // a row range: only its rows are evaluated (the others' outputs are set to zero)
+        int rc = ensure_range_rows(c);
+        if (rc) return rc;
+        rows = c->buf.range_rows;
+        m = c->row_r1 - c->row_r0;
+    }
     if (P.chunk) {
         // X recomputed chunk by chunk: filter, U product and E X^T per chunk; E X^T summed over the chunks.
         // Nothing of a previous evaluation survives, so a reuse request evaluates again (every row).
@@ -469,8 +495,30 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
     P.Tc = P.chunk ? P.chunk : P.Tpad;
     P.span = (double)n_bins * dt;
     P.dt_int = dt;
+    // delayed sources: each spike at bin s reaches the rows at s + delay, i.e. the filter reads it at
+    // s + delay - 1 (its recursion adds S[t - 1] at t); spikes pushed past the recording drop out
+    P.delay_bins = c->delay_req;
+    std::vector<int64_t> aoffs;
+    std::vector<int32_t> abins;
+    if (P.delay_bins > 1) {
+        aoffs.assign(n + 1, 0);
+        abins.reserve(P.q);
+        for (int32_t i = 0; i < n; ++i) {
+            for (int64_t k = offs[i]; k < offs[i + 1]; ++k) {
+                const int64_t s2 = (int64_t)bins[k] + P.delay_bins - 1;
+                if (s2 < n_bins) abins.push_back((int32_t)s2);
+            }
+            aoffs[i + 1] = (int64_t)abins.size();
+        }
+        P.qa = aoffs[n];
+    }
     if ((rc = alloc_problem(c))) return rc;
     Buffers& B = c->buf;
+    if (P.delay_bins > 1) {
+        GLM_CK(cudaMemcpyAsync(B.aoffs, aoffs.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, c->stream));
+        if (P.qa > 0)
+            GLM_CK(cudaMemcpyAsync(B.abins, abins.data(), sizeof(int32_t) * P.qa, cudaMemcpyHostToDevice, c->stream));
+    }
     std::vector<double> qd(n);
     for (int32_t i = 0; i < n; ++i) qd[i] = (double)(offs[i + 1] - offs[i]);
     GLM_CK(cudaMemcpyAsync(B.offs, offs, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, c->stream));
@@ -775,6 +823,79 @@ int glm_cross_validate(glm_ctx* tr, glm_ctx* va, const glm_fit_opts_t* opts, con
     return cleanup(GLM_OK);
 }
 
+int glm_set_source_delay(glm_ctx* c, int32_t delay_bins) {
+    if (!c) return GLM_ERR_INVALID_ARG;
+    if (delay_bins < 1) return fail(c, GLM_ERR_INVALID_ARG, "delay_bins must be >= 1");
+    c->delay_req = delay_bins;
+    return GLM_OK;
+}
+
+int glm_set_row_range(glm_ctx* c, int32_t r0, int32_t r1) {
+    if (!c) return GLM_ERR_INVALID_ARG;
+    if (!c->has_problem) return fail(c, GLM_ERR_NO_PROBLEM, "no problem set");
+    const int32_t n = c->pb.n;
+    if (r0 == 0 && (r1 == 0 || r1 == n)) {
+        c->row_r0 = 0;
+        c->row_r1 = -1;
+    } else {
+        if (r0 < 0 || r1 <= r0 || r1 > n) return fail(c, GLM_ERR_INVALID_ARG, "need 0 <= r0 < r1 <= n");
+        c->row_r0 = r0;
+        c->row_r1 = r1;
+    }
+    c->buf.range_rows = nullptr;  // rebuilt on first use (the old list stays in the workspace until the next problem)
+    return GLM_OK;
+}
+
+int glm_fit_classes(glm_ctx* const* cs, int32_t n_class, const glm_fit_opts_t* opts, float* W, float* b,
+                    int8_t* row_status, glm_fit_report_t* rep) {
+    if (!cs || n_class < 1 || !W || !b) return GLM_ERR_INVALID_ARG;
+    glm_ctx* c0 = cs[0];
+    if (!c0 || !c0->has_problem) return c0 ? fail(c0, GLM_ERR_NO_PROBLEM, "no problem set") : GLM_ERR_INVALID_ARG;
+    const int32_t n = c0->pb.n;
+    std::vector<int> owner(n, -1);
+    for (int32_t k = 0; k < n_class; ++k) {
+        glm_ctx* c = cs[k];
+        if (!c || !c->has_problem) return fail(c0, GLM_ERR_NO_PROBLEM, "a class context has no problem set");
+        if (c->pb.n != n || c->device != c0->device)
+            return fail(c0, GLM_ERR_INVALID_ARG, "class contexts differ in n or device");
+        const int32_t r0 = c->row_r0, r1 = c->row_r1 < 0 ? n : c->row_r1;
+        for (int32_t i = r0; i < r1; ++i) {
+            if (owner[i] >= 0) return fail(c0, GLM_ERR_INVALID_ARG, "the row ranges of the classes overlap");
+            owner[i] = k;
+        }
+    }
+    std::vector<int8_t> st((size_t)n * n_class, (int8_t)GLM_ROW_EXCLUDED);
+    glm_fit_report_t tot;
+    std::memset(&tot, 0, sizeof(tot));
+    int worst = GLM_OK;
+    for (int32_t k = 0; k < n_class; ++k) {
+        glm_fit_report_t r;
+        const int rc = glm_fit(cs[k], opts, W, b, st.data() + (size_t)k * n, &r);
+        if (rc < 0) return rc;
+        if (rc > worst) worst = rc;
+        tot.iterations = std::max(tot.iterations, r.iterations);
+        tot.evaluations += r.evaluations;
+        tot.gradients += r.gradients;
+        tot.converged += r.converged;
+        tot.maxiter += r.maxiter;
+        tot.stalled += r.stalled;
+        tot.degenerate += r.degenerate;
+        tot.at_floor += r.at_floor;
+        tot.L += r.L;
+        tot.seconds += r.seconds;
+        // each class's fit runs on its context's stream; W and b are shared between them
+        DeviceGuard g(cs[k]->device);
+        if (cudaStreamSynchronize(cs[k]->stream) != cudaSuccess) return fail(cs[k], GLM_ERR_CUDA, "synchronise");
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        const int k = owner[i];
+        if (k < 0) tot.excluded++;
+        if (row_status) row_status[i] = k < 0 ? (int8_t)GLM_ROW_EXCLUDED : st[(size_t)k * n + i];
+    }
+    if (rep) *rep = tot;
+    return worst;
+}
+
 int glm_set_chunk_bins(glm_ctx* c, int64_t chunk_bins) {
     if (!c) return GLM_ERR_INVALID_ARG;
     if (chunk_bins < 0) return fail(c, GLM_ERR_INVALID_ARG, "chunk_bins must be >= 0");
@@ -805,6 +926,7 @@ int glm_fit_batch(glm_ctx* const* cs, int32_t np, const glm_fit_opts_t* opts, fl
         if (c->pb.prec != c0->pb.prec) return fail(c0, GLM_ERR_INVALID_ARG, "contexts with different precisions");
         if (c->pb.chunk) return fail(c0, GLM_ERR_UNSUPPORTED, "glm_fit_batch needs X stored (no chunking)");
         if (c->pb.ct) return fail(c0, GLM_ERR_UNSUPPORTED, "glm_fit_batch serves the grid form");
+        if (c->row_r1 >= 0) return fail(c0, GLM_ERR_UNSUPPORTED, "glm_fit_batch fits whole problems (no row range)");
         for (int32_t q = 0; q < p; ++q)
             if (cs[q] == c) return fail(c0, GLM_ERR_INVALID_ARG, "a context appears twice");
     }

@@ -48,6 +48,9 @@ struct Problem {
     // every spike arriving everywhere after `delay`
     bool ct = false;
     double t_begin = 0, t_end = 0, delay = 0;
+    // grid form: every source train reaches the rows after delay_bins bins (1: the one-bin delay of the
+    // filter recursion); above 1 the filter reads the spikes shifted by delay_bins - 1
+    int32_t delay_bins = 1;
     int64_t qa = 0;       // arrivals inside the recording
 };
 
@@ -91,6 +94,7 @@ struct Buffers {
     float* colc = nullptr;        // [Tpad][8] a, 1 - a and the one-panel quadrature factors (ct_link.cuh)
     double* seg_mul = nullptr;    // [nseg] decay over each 256-column segment
     double* tile_span = nullptr;  // [nseg] duration of each 256-column segment
+    int32_t* range_rows = nullptr;// [r1 - r0] the rows r0 .. r1 - 1 of a row range (glm_set_row_range)
 };
 
 }  // namespace glm
@@ -111,6 +115,8 @@ struct glm_ctx {
     int g_mode = 1;        // E X^T row tile: 1 = 256 rows, 2 = 128 rows (autotuner)
     int g_nsplit = 0;      // E X^T bin splits (0: the default for g_mode)
     int64_t chunk_req = 0; // bins per chunk requested by glm_set_chunk_bins (applied by glm_set_problem)
+    int32_t delay_req = 1; // source delay in bins requested by glm_set_source_delay (applied by glm_set_problem)
+    int32_t row_r0 = 0, row_r1 = -1;  // evaluated and fitted rows (glm_set_row_range); r1 < 0: all rows
     std::string last_error;
     // tracing: event pairs per launched kernel group while profiling is on
     bool prof_on = false;
@@ -154,6 +160,7 @@ cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_
                           bool want_grad, int64_t ntile, int nsplit, const double* Gacc = nullptr);
 void launch_exp_bias(glm_ctx* c, const float* b);
 int set_error(glm_ctx* c, int code, const char* msg);
+int ensure_range_rows(glm_ctx* c);
 // One evaluation at (W, b).  With rows (m of them) only those rows' U product, rates and per-tile sums
 // are formed (their L_rows entries are valid; other rows' entries are not).
 int eval_enqueue(glm_ctx* c, const float* W, const float* b, double* L_rows, double* G, double* gb, bool want_grad,

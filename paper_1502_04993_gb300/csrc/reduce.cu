@@ -28,6 +28,7 @@ struct ReduceArgs {
     const double* part_e;  // [n][ntile]
     const double* part_s2; // second planes of part_s and part_e (continuous time), or null
     const double* part_e2;
+    int32_t r0, r1;        // rows outside [r0, r1) (a row range) get L_i = 0 and dL/db_i = 0
     double* L_rows;
     double* gb;
 };
@@ -55,16 +56,22 @@ __global__ void reduce_rows_kernel(const __grid_constant__ ReduceArgs A) {
     integ = warp_sum(integ);
     if (lane == 0) {
         const double q = A.qd[i];
-        A.L_rows[i] = q * (double)A.b[i] + spk - A.dt * integ;
-        if (A.gb) A.gb[i] = q - A.dt * integ;
+        const bool in = i >= A.r0 && i < A.r1;
+        A.L_rows[i] = in ? q * (double)A.b[i] + spk - A.dt * integ : 0.0;
+        if (A.gb) A.gb[i] = in ? q - A.dt * integ : 0.0;
     }
 }
 
+// G rows outside [e0, e1) (element range of a row range) are set to zero
 __global__ void reduce_grad_kernel(int64_t nn, int nsplit, const double* __restrict__ C,
                                    const float* __restrict__ part_g, const double* __restrict__ Gacc,
-                                   double* __restrict__ G) {
+                                   double* __restrict__ G, int64_t e0, int64_t e1) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nn) return;
+    if (e < e0 || e >= e1) {
+        G[e] = 0.0;
+        return;
+    }
     double s = 0.0;
     if (Gacc)
         s = Gacc[e];
@@ -173,13 +180,15 @@ cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_
     A.part_e = c->buf.part_e;
     A.part_s2 = P.ct ? c->buf.part_s + (int64_t)P.n * ntile : nullptr;
     A.part_e2 = P.ct ? c->buf.part_e + (int64_t)P.n * ntile : nullptr;
+    A.r0 = c->row_r0;
+    A.r1 = c->row_r1 < 0 ? P.n : c->row_r1;
     A.L_rows = L_rows;
     A.gb = gb;
     reduce_rows_kernel<<<(P.n + 7) / 8, 256, 0, c->stream>>>(A);
     if (want_grad && G) {
         const int64_t nn = (int64_t)P.n * P.n;
-        reduce_grad_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(nn, nsplit, A.C, c->buf.part_g, Gacc,
-                                                                              G);
+        reduce_grad_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(
+            nn, nsplit, A.C, c->buf.part_g, Gacc, G, (int64_t)A.r0 * P.n, (int64_t)A.r1 * P.n);
     }
     return cudaGetLastError();
 }

@@ -83,6 +83,10 @@ struct SpikeTermArgs {
     const int32_t* bins;
     const double* seg_carry;
     const int32_t* seg_first;
+    // the source trains scanned into X (the spikes, or the spikes shifted by a source delay)
+    const int64_t* aoffs;
+    const int32_t* abins;
+    const int32_t* aseg_first;
     double* C_part;  // [parts][n][n]
 };
 
@@ -153,19 +157,19 @@ __global__ void __launch_bounds__(ST_THREADS, 1) spike_term_kernel(const __grid_
                 rc[k] = re[k] = 0;
                 if (r < A.n) {
                     xs[k] = (float)A.seg_carry[(int64_t)r * A.nseg + s];
-                    rc[k] = A.offs[r] + A.seg_first[(int64_t)r * A.nseg + s];
-                    re[k] = A.offs[r + 1];
+                    rc[k] = A.aoffs[r] + A.aseg_first[(int64_t)r * A.nseg + s];
+                    re[k] = A.aoffs[r + 1];
                 }
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int64_t kk = rc[k] + lane;
-                sv[k] = (kk < re[k]) ? (int64_t)__ldg(A.bins + kk) : INT64_MAX;
+                sv[k] = (kk < re[k]) ? (int64_t)__ldg(A.abins + kk) : INT64_MAX;
             }
             float v[4][8];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const uint32_t bits = seg_bits_pre(A.bins, rc[k], re[k], t0, lane, sv[k]);
+                const uint32_t bits = seg_bits_pre(A.abins, rc[k], re[k], t0, lane, sv[k]);
                 seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v[k]);
             }
 #pragma unroll
@@ -261,6 +265,9 @@ cudaError_t launch_spike_term(glm_ctx* c, double* out) {
     A.bins = c->buf.bins;
     A.seg_carry = c->buf.seg_carry;
     A.seg_first = c->buf.seg_first;
+    A.aoffs = c->buf.aoffs;
+    A.abins = c->buf.abins;
+    A.aseg_first = c->buf.aseg_first;
     A.C_part = c->buf.C_part;
     const size_t smem = ST_SMEM;
     dim3 grid((P.n + ST_JB - 1) / ST_JB, parts, (P.n + ST_ROWS_PER_SLICE - 1) / ST_ROWS_PER_SLICE);

@@ -140,6 +140,7 @@ struct TcArgs {
     int64_t nseg;
     const int32_t* rows;  // MODE 0: evaluated rows (null: all n); tile row l is row rows[l] for l < m_rows
     int32_t m_rows;
+    int32_t m_base;       // MODE 1, 2: first row of the row tiles (a row range starts there)
     int64_t t_base;       // MODE 0: first bin of the X / E buffers (a chunk of the recording, or 0)
     void* E;
     double* part_e;
@@ -183,7 +184,7 @@ __device__ __forceinline__ Unit decode(const TcArgs& A, int64_t u, int32_t mt) {
         const int64_t tiles = (int64_t)A.mt * A.nt;
         const int64_t tile = u % tiles;
         r.split = u / tiles;
-        r.m0 = (int32_t)(tile % A.mt) * (MODE == 2 ? 128 : 256);
+        r.m0 = A.m_base + (int32_t)(tile % A.mt) * (MODE == 2 ? 128 : 256);
         r.n0 = (int32_t)(tile / A.mt) * BN;
         // the splits interleave: split s takes k-steps s, s + nsplit, s + 2 nsplit, ...  All blocks then
         // stream the same narrow band of bins, which stays in L2 while the 16 tiles of each split reuse it.
@@ -819,6 +820,7 @@ static TcArgs base_args(glm_ctx* c) {
     A.part_s = nullptr;
     A.rows = nullptr;
     A.m_rows = P.n;
+    A.m_base = 0;
     A.t_base = 0;
     A.offs = c->buf.offs;
     A.bins = c->buf.bins;
@@ -884,10 +886,13 @@ cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, boo
 }
 
 // E X^T arguments of context c with its tile mode and split count
-static TcArgs grad_args(glm_ctx* c, int mode, int ns, int64_t kbt) {
+static TcArgs grad_args(glm_ctx* c, int mode, int ns, int64_t kbt, bool ranged = false) {
     const Problem& P = c->pb;
     TcArgs A = base_args(c);
-    A.mt = (P.n + (mode == 2 ? 127 : 255)) / (mode == 2 ? 128 : 256);
+    // a row range needs only the row tiles that cover it
+    const int32_t r0 = ranged ? c->row_r0 : 0, r1 = (ranged && c->row_r1 >= 0) ? c->row_r1 : P.n;
+    A.m_base = r0;
+    A.mt = (r1 - r0 + (mode == 2 ? 127 : 255)) / (mode == 2 ? 128 : 256);
     A.nt = (P.n + BN - 1) / BN;
     A.kb_total = kbt;
     A.kb_per_unit = (int32_t)((A.kb_total + ns - 1) / ns);
@@ -897,8 +902,9 @@ static TcArgs grad_args(glm_ctx* c, int mode, int ns, int64_t kbt) {
     return A;
 }
 
-static cudaError_t run_products_as(glm_ctx* c, const CUtensorMap& mapB, int mode, int ns, int64_t kbt) {
-    const TcArgs A = grad_args(c, mode, ns, kbt);
+static cudaError_t run_products_as(glm_ctx* c, const CUtensorMap& mapB, int mode, int ns, int64_t kbt,
+                                   bool ranged = false) {
+    const TcArgs A = grad_args(c, mode, ns, kbt, ranged);
     const bool bf = c->pb.prec == GLM_PREC_BF16;
     if (mode == 2) {
         if (bf) return run<2, __nv_bfloat16>(c, c->tmap[4], c->tmap[4], mapB, mapB, A);
@@ -910,16 +916,17 @@ static cudaError_t run_products_as(glm_ctx* c, const CUtensorMap& mapB, int mode
 
 // E X^T (or S X^T) over the first t_len bins of the buffers (t_len < 0: the recording, or a whole chunk);
 // a short last chunk takes at most one split per k-step.
-static cudaError_t run_products(glm_ctx* c, const CUtensorMap& mapB, int64_t t_len, int* ns_used) {
+// ranged: only the row tiles of the context's row range (the gradient); the spike term takes every row
+static cudaError_t run_products(glm_ctx* c, const CUtensorMap& mapB, int64_t t_len, int* ns_used, bool ranged = false) {
     const int64_t kbt = t_len < 0 ? grad_ksteps(c) : (t_len + Cfg<1>::BK - 1) / Cfg<1>::BK;
     int ns = tc_nsplit(c);
     if (ns > kbt) ns = (int)kbt;
     if (ns_used) *ns_used = ns;
-    return run_products_as(c, mapB, c->g_mode, ns, kbt);
+    return run_products_as(c, mapB, c->g_mode, ns, kbt, ranged);
 }
 
 cudaError_t launch_tc_grad(glm_ctx* c, int64_t t_len, int* nsplit_used) {
-    return run_products(c, c->tmap[5], t_len, nsplit_used);
+    return run_products(c, c->tmap[5], t_len, nsplit_used, true);
 }
 
 // With X recomputed per chunk, each chunk is filtered here first and the products add up over the chunks.
