@@ -464,11 +464,19 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                 for (int u = 0; u < SP_REG; ++u) sb[u] = (kb + u < ke) ? (int)(A.bins[kb + u] - gt0) : BN;
                 T16* erow = reinterpret_cast<T16*>(A.E) + ((int64_t)(w.n0 / 64) * A.n + i) * 64;
                 const float4* colq = reinterpret_cast<const float4*>(A.colc) + 2 * gt0;
+                const int g_begin = half * (BN / 16), g_end = (half + 1) * (BN / 16);
+                // column constants of the next group are loaded while this one is computed
+                float4 kc[8], kn[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) kc[e] = __ldg(colq + 2 * (g_begin * 8 + e));
 #pragma unroll 1
-                for (int g = half * (BN / 16); g < (half + 1) * (BN / 16); ++g) {
+                for (int g = g_begin; g < g_end; ++g) {
                     const int c0 = g * 8;  // first column of the group within the tile
                     uint32_t r[8];
                     tc::tmem_ld8(taddr + c0, r);
+                    const int cn = (g + 1 < g_end ? g + 1 : g) * 8;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) kn[e] = __ldg(colq + 2 * (cn + e));
                     tc::tmem_ld_wait();
                     uint32_t sm = 0;  // spike mask: bit e <-> column c0 + e
 #pragma unroll
@@ -484,7 +492,7 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                     uint32_t slow = 0;
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
-                        const float4 k = __ldg(colq + 2 * (c0 + e));  // a, 1 - a, 2-node factors
+                        const float4 k = kc[e];  // a, 1 - a, 2-node factors
                         const float u = __uint_as_float(r[e]);
                         ct_link2(u, k.x, k.y, k.z, k.w, &fv[e], &gv[e]);
                         slow |= (fabsf(u) * k.y > CT_W2_MAX) ? (1u << e) : 0u;
@@ -516,6 +524,8 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                     if (i < A.n)
                         *reinterpret_cast<uint4*>(erow + (int64_t)(c0 >> 6) * A.n * 64 + (c0 & 63)) =
                             make_uint4(pk[0], pk[1], pk[2], pk[3]);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) kc[e] = kn[e];
                 }
                 if (i < A.n) {
                     const double rsum = (double)esh * ((half == 0 ? A.tile_span[gtile] : 0.0) + (double)s);

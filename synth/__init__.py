@@ -123,10 +123,13 @@ WORKLOADS = {
     # low-rate state and settles near 80 Hz.
     "glm_n1000_t1800s": dict(n=1000, n_exc=800, p=0.1, w_exc=0.2, w_inh=0.8, w_self=-6.25, rate=8.0,
                              tau=0.010, dt=0.001, n_bins=1_800_000, seed=0),
-    # N=2000 (1600 E / 400 I) with a 10 x 50 synfire chain, 3600 s
+    # N=2000 (1600 E / 400 I) with a 10 x 50 synfire chain, 3600 s.  In this exponential-rate model the
+    # +0.3 chain drives the network into saturation (mean rate 97 Hz) unless each chain neuron's baseline
+    # is lowered; syn_b_comp = 2 lowers it by twice its expected input from the previous link,
+    # 50 x 0.3 x rate x tau (mean rate then 5.2 Hz: chain neurons 1.5 Hz, background 6.5 Hz).
     "glm_n2000_synfire_t3600s": dict(n=2000, n_exc=1600, p=0.05, w_exc=0.2, w_inh=0.8, w_self=-6.25,
                                      rate=8.0, tau=0.010, dt=0.001, n_bins=3_600_000, seed=0, syn_groups=10,
-                                     syn_size=50, w_syn=0.3, shuffle=True),
+                                     syn_size=50, w_syn=0.3, shuffle=True, syn_b_comp=2.0),
 }
 
 
@@ -139,6 +142,11 @@ def make_workload(name: str | None = None, *, threads: int = 0, **overrides) -> 
                        syn_size=cfg.get("syn_size", 0), w_syn=cfg.get("w_syn", 0.0),
                        shuffle=cfg.get("shuffle", False))
     b = np.full(cfg["n"], math.log(cfg["rate"]), dtype=np.float64)
+    if cfg.get("syn_groups", 0) and cfg.get("syn_b_comp", 0.0):
+        # chain neurons: baseline lowered by syn_b_comp x their expected input from the previous link
+        w_syn = cfg["w_syn"]
+        n_in = np.isclose(W, w_syn).sum(axis=1)
+        b -= cfg["syn_b_comp"] * n_in * w_syn * cfg["rate"] * cfg["tau"]
     offs, bins = simulate(W, b, cfg["tau"], cfg["dt"], cfg["n_bins"], cfg["seed"], threads=threads)
     out = dict(cfg)
     out.update(W_true=W, b_true=b, types=types, offs=offs, bins=bins)
