@@ -69,50 +69,74 @@ __global__ void seg_local_kernel(int32_t n, int64_t nseg, const int64_t* __restr
     }
 }
 
-// Warp per row, in place: seg_carry[s] <- X_j[256 s] = a^256 X_j[256 (s-1)] + local[s-1].
-// The segments of a row are split into 32 contiguous parts, one per lane: each lane runs the recursion
-// over its part from zero, a shuffle scan over the lanes supplies every part's true carry-in
-// (multiplier a^(256 * part length) per lane step), and each lane then rewrites its part.  With mul_seg
-// (continuous-time columns) segment s decays by mul_seg[s] instead of a_seg.
-__global__ void seg_carry_kernel(int32_t n, int64_t nseg, double a_seg, const double* __restrict__ mul_seg,
-                                 double* __restrict__ seg) {
-    const int32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
+// Block per row, in place: seg_carry[s] <- X_j[256 s], with X_j[256 (s+1)] = A_s X_j[256 s] + local[s]
+// (A_s = a^256, or mul_seg[s] for continuous-time columns).  The row goes through shared memory in chunks of
+// CS segments, read and written with coalesced accesses: each thread composes the affine maps of its 8
+// consecutive segments (multiplier M, offset V), a block scan over the threads composes them in order,
+// and each thread then rewrites its segments from its carry-in.  The chunk's carry-out starts the next
+// chunk.  The order of the FP64 operations is fixed: the result is reproducible.
+constexpr int SC_T = 256, SC_E = 8, SC_CS = SC_T * SC_E;
+
+__device__ __forceinline__ int sc_pad(int k) { return k + (k >> 3); }  // one pad per 8 doubles: no bank conflicts
+
+__global__ void __launch_bounds__(SC_T) seg_carry_kernel(int32_t n, int64_t nseg, double a_seg,
+                                                         const double* __restrict__ mul_seg, double* __restrict__ seg) {
+    __shared__ double sl[SC_CS + SC_CS / 8], sa[SC_CS + SC_CS / 8];
+    __shared__ double wm[SC_T / 32], wv[SC_T / 32];
+    __shared__ double s_cin;
+    const int32_t j = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (j >= n) return;
     double* p = seg + (int64_t)j * nseg;
-    const int64_t len = (nseg + 31) / 32;
-    const int64_t s0 = min((int64_t)lane * len, nseg), s1 = min(s0 + len, nseg);
-    double c = 0.0, mul = 1.0;
-    if (mul_seg) {
-        for (int64_t s = s0; s < s1; ++s) {
-            c = fma(mul_seg[s], c, p[s]);
-            mul *= mul_seg[s];
+    if (tid == 0) s_cin = 0.0;
+    for (int64_t c0 = 0; c0 < nseg; c0 += SC_CS) {
+        const int len = (int)min((int64_t)SC_CS, nseg - c0);
+        __syncthreads();  // s_cin of the previous chunk is written; the buffers are free
+        for (int k = tid; k < SC_CS; k += SC_T) {
+            sl[sc_pad(k)] = k < len ? p[c0 + k] : 0.0;
+            sa[sc_pad(k)] = k < len ? (mul_seg ? mul_seg[c0 + k] : a_seg) : 1.0;
         }
-    } else {
-        for (int64_t s = s0; s < s1; ++s) c = fma(a_seg, c, p[s]);  // this part's contribution at its end
-        // multiplier across one full part: a_seg^len (parts shorter than len only occur at the end)
-        double base = a_seg;
-        for (int64_t e = len; e > 0; e >>= 1) {
-            if (e & 1) mul *= base;
-            base *= base;
+        __syncthreads();
+        // this thread's map over segments [tid E, tid E + E)
+        double M = 1.0, V = 0.0;
+#pragma unroll
+        for (int e = 0; e < SC_E; ++e) {
+            const int k = sc_pad(tid * SC_E + e);
+            V = fma(sa[k], V, sl[k]);
+            M *= sa[k];
         }
-    }
-    // inclusive scan over lanes of carry_out(l) = mul * carry_out(l-1) + c(l)
-    double v = c, m = mul;
-    for (int d = 1; d < 32; d <<= 1) {
-        const double o = __shfl_up_sync(0xffffffffu, v, d);
-        const double om = __shfl_up_sync(0xffffffffu, m, d);
-        if (lane >= d) {
-            v = fma(m, o, v);
-            m = m * om;
+        // inclusive scan of the maps over the threads: (M, V) after (M', V') is (M M', M V' + V)
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const double oM = __shfl_up_sync(0xffffffffu, M, d), oV = __shfl_up_sync(0xffffffffu, V, d);
+            if (lane >= d) {
+                V = fma(M, oV, V);
+                M *= oM;
+            }
         }
-    }
-    double cin = __shfl_up_sync(0xffffffffu, v, 1);
-    if (lane == 0) cin = 0.0;
-    for (int64_t s = s0; s < s1; ++s) {
-        const double l = p[s];
-        p[s] = cin;
-        cin = fma(mul_seg ? mul_seg[s] : a_seg, cin, l);
+        if (lane == 31) {
+            wm[wid] = M;
+            wv[wid] = V;
+        }
+        __syncthreads();
+        // carry into this thread's first segment: chunk carry-in through the earlier warps, then the
+        // earlier lanes of this warp
+        double cin = s_cin;
+        for (int w = 0; w < wid; ++w) cin = fma(wm[w], cin, wv[w]);
+        {
+            double pM = __shfl_up_sync(0xffffffffu, M, 1), pV = __shfl_up_sync(0xffffffffu, V, 1);
+            if (lane > 0) cin = fma(pM, cin, pV);
+        }
+#pragma unroll
+        for (int e = 0; e < SC_E; ++e) {
+            const int k = sc_pad(tid * SC_E + e);
+            const double l = sl[k];
+            sl[k] = cin;
+            cin = fma(sa[k], cin, l);
+        }
+        if (tid == SC_T - 1) s_cin = cin;
+        __syncthreads();
+        for (int k = tid; k < len; k += SC_T) p[c0 + k] = sl[sc_pad(k)];
     }
 }
 
@@ -441,7 +465,7 @@ cudaError_t launch_carry(glm_ctx* c) {
                                                      B.seg_first);
         seg_local_kernel<<<P.n, 256, 0, c->stream>>>(P.n, P.nseg, B.aoffs, B.abins, nullptr, B.ctime, 1.0 / P.tau,
                                                      B.seg_carry, B.aseg_first);
-        seg_carry_kernel<<<(P.n + 3) / 4, 128, 0, c->stream>>>(P.n, P.nseg, 0.0, B.seg_mul, B.seg_carry);
+        seg_carry_kernel<<<P.n, SC_T, 0, c->stream>>>(P.n, P.nseg, 0.0, B.seg_mul, B.seg_carry);
         return cudaGetLastError();
     }
     if (P.delay_bins > 1) {
@@ -455,7 +479,7 @@ cudaError_t launch_carry(glm_ctx* c) {
                                                      B.seg_carry, B.seg_first);
     }
     const double a_seg = std::exp(-(double)SEG * P.dt / P.tau);
-    seg_carry_kernel<<<(P.n + 3) / 4, 128, 0, c->stream>>>(P.n, P.nseg, a_seg, nullptr, B.seg_carry);
+    seg_carry_kernel<<<P.n, SC_T, 0, c->stream>>>(P.n, P.nseg, a_seg, nullptr, B.seg_carry);
     return cudaGetLastError();
 }
 
