@@ -453,12 +453,14 @@ def main():
     W_h = torch.from_numpy(w["W_true"].astype(np.float32)).pin_memory()
     b_h = torch.from_numpy(w["b_true"].astype(np.float32)).pin_memory()
     G_h = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    offs_h = torch.from_numpy(w["offs"]).pin_memory().numpy()  # the step's inputs in pinned host memory
+    bins_h = torch.from_numpy(w["bins"]).pin_memory().numpy()
     torch.cuda.synchronize(device)
     if ws > 1:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(k2):
-        ctx.set_problem(w["offs"], w["bins"], T, w["dt"], w["tau"], prec=prec)
+        ctx.set_problem(offs_h, bins_h, T, w["dt"], w["tau"], prec=prec)
         Wd = W_h.to(device, non_blocking=True)
         bd = b_h.to(device, non_blocking=True)
         r = ctx.loglik_grad(Wd, bd, total=True, out=out)

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "glm_internal.h"
@@ -144,12 +145,41 @@ void prof_fold(glm_ctx* c) {
         c->launches += (nkernels);                     \
     } while (0)
 
+// rows [i0, i1) sorted and inside [0, T)
+bool rows_valid(int32_t i0, int32_t i1, int64_t T, const int64_t* offs, const int32_t* bins) {
+    for (int32_t i = i0; i < i1; ++i) {
+        int64_t prev = -1;
+        for (int64_t k = offs[i]; k < offs[i + 1]; ++k) {
+            const int64_t s = bins[k];
+            if (s < 0 || s >= T || s <= prev) return false;
+            prev = s;
+        }
+    }
+    return true;
+}
+
 int validate_spikes(glm_ctx* c, int32_t n, int64_t T, const int64_t* offs, const int32_t* bins) {
     if (offs[0] != 0) return fail(c, GLM_ERR_SPIKE_OUT_OF_RANGE, "offs[0] must be 0");
     for (int32_t i = 0; i < n; ++i)
         if (offs[i + 1] < offs[i]) return fail(c, GLM_ERR_SPIKE_OUT_OF_RANGE, "offs must be non-decreasing");
     const int64_t q = offs[n];
     if (q > 0 && !bins) return fail(c, GLM_ERR_INVALID_ARG, "bins is NULL but offs[n] > 0");
+    // large recordings: the rows are checked on several host threads, split by spike count; only when
+    // one of them finds a fault does the single pass below run, to name the first one
+    const int nt = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+    if (q >= ((int64_t)1 << 20) && nt > 1 && n >= nt) {
+        std::vector<int32_t> cut(nt + 1, n);
+        cut[0] = 0;
+        for (int t = 1; t < nt; ++t)
+            cut[t] = (int32_t)(std::upper_bound(offs, offs + n + 1, q * t / nt) - offs - 1);
+        for (int t = 1; t <= nt; ++t) cut[t] = std::max(cut[t], cut[t - 1]);
+        std::vector<char> ok(nt, 1);
+        std::vector<std::thread> th;
+        for (int t = 0; t < nt; ++t)
+            th.emplace_back([&, t]() { ok[t] = rows_valid(cut[t], cut[t + 1], T, offs, bins) ? 1 : 0; });
+        for (auto& x : th) x.join();
+        if (std::all_of(ok.begin(), ok.end(), [](char v) { return v != 0; })) return GLM_OK;
+    }
     for (int32_t i = 0; i < n; ++i) {
         int64_t prev = -1;
         for (int64_t k = offs[i]; k < offs[i + 1]; ++k) {
@@ -241,7 +271,12 @@ int do_prepare(glm_ctx* c) {
                            c->stream));
     c->c_ready = false;
     GLM_RUN("carry", 2, launch_carry(c));
-    if (!P.chunk) GLM_RUN("filter_scan", 1, launch_filter_cache(c));  // chunked: filtered per use
+    if (!P.chunk) {  // chunked: filtered per use
+        // the 16-bit forms' spike term reads the raster from E: the filter writes it on the way
+        const bool raster = P.prec != GLM_PREC_F32 && P.delay_bins <= 1;
+        GLM_RUN("filter_scan", 1, launch_filter_cache(c, 0, -1, raster ? c->buf.E : nullptr));
+        c->raster_in_E = raster;
+    }
     // The spike term C (the W-independent part of dL/dW, Eq. 12): a gather of X at the spike bins for the
     // plain FP32 form, S (X_hi + X_lo)^T on the tensor cores for the 16-bit forms.  The spike part of L
     // comes from U at the spike bins in the U-product epilogue instead (its rounding then cancels against
@@ -258,7 +293,7 @@ int ensure_spike_term(glm_ctx* c) {
     Buffers& B = c->buf;
     const size_t nn = (size_t)c->pb.n * c->pb.n;
     if (c->pb.prec != GLM_PREC_F32) {
-        GLM_RUN("spike_term", 5, launch_tc_spike_term(c));
+        GLM_RUN("spike_term", 0, launch_tc_spike_term(c));  // counts its own launches
     } else {
         int rc;
         if (!B.C_part && (rc = ws_alloc_t(c, &B.C_part, nn * spike_term_parts(c)))) return rc;
@@ -478,6 +513,36 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
     if (rc) return rc;
     DeviceGuard g(c->device);
     GLM_CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+    {
+        // a recording of the same shape (neurons, bins, spike count, precision, chunking, delay) reuses
+        // the context's buffers: only the spikes and the caches are renewed
+        const Problem& O = c->pb;
+        const int64_t chunk = (tensor && c->chunk_req > 0 && round_up(c->chunk_req, 16 * SEG) < round_up(n_bins, SEG))
+                                  ? round_up(c->chunk_req, 16 * SEG) : 0;
+        if (c->has_problem && !O.ct && O.n == n && O.T == n_bins && O.q == offs[n] && O.prec == prec &&
+            O.chunk == chunk && O.delay_bins == c->delay_req && c->delay_req <= 1) {
+            c->has_problem = false;
+            Problem& P = c->pb;
+            P.dt = dt;
+            P.tau = tau;
+            P.span = (double)n_bins * dt;
+            P.dt_int = dt;
+            Buffers& B = c->buf;
+            std::vector<double> qd(n);
+            for (int32_t i = 0; i < n; ++i) qd[i] = (double)(offs[i + 1] - offs[i]);
+            GLM_CK(cudaMemcpyAsync(B.offs, offs, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, c->stream));
+            if (P.q > 0) GLM_CK(cudaMemcpyAsync(B.bins, bins, sizeof(int32_t) * P.q, cudaMemcpyHostToDevice, c->stream));
+            GLM_CK(cudaMemcpyAsync(B.qd, qd.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+            GLM_CK(cudaMemsetAsync(B.flags, 0, 4 * sizeof(int), c->stream));
+            if ((rc = do_prepare(c))) {
+                free_all(c);
+                return rc;
+            }
+            GLM_CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+            c->has_problem = true;
+            return GLM_OK;
+        }
+    }
     free_all(c);
     Problem& P = c->pb;
     P = Problem();

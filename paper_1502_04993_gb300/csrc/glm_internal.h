@@ -112,6 +112,7 @@ struct glm_ctx {
     CUtensorMap tmap[7];  // tensor-core path: W_hi, W_lo, X_hi, X_lo (N-major), E, X_hi, X_lo (K-major)
     bool has_problem = false;
     bool c_ready = false;  // C holds the spike term of the current problem and tau
+    bool raster_in_E = false;  // the E buffer holds the spike raster written by the last filter pass
     int g_mode = 1;        // E X^T row tile: 1 = 256 rows, 2 = 128 rows (autotuner)
     int g_nsplit = 0;      // E X^T bin splits (0: the default for g_mode)
     int64_t chunk_req = 0; // bins per chunk requested by glm_set_chunk_bins (applied by glm_set_problem)
@@ -143,7 +144,9 @@ namespace glm {
 // ---- launchers (each returns cudaError_t of the launch) ----
 cudaError_t launch_carry(glm_ctx* c);
 // segments [s_begin, s_end) into the X buffers (whose first bin is SEG s_begin); s_end < 0: all
-cudaError_t launch_filter_cache(glm_ctx* c, int64_t s_begin = 0, int64_t s_end = -1);
+// raster: also write the rows' spike raster (16-bit 0 / 1) there; only where the filter's sources are the
+// rows' own spikes (grid form, one-bin delay)
+cudaError_t launch_filter_cache(glm_ctx* c, int64_t s_begin = 0, int64_t s_end = -1, void* raster = nullptr);
 // the 16-bit spike raster of segments [s_begin, s_end) into a bin-blocked buffer starting at bin SEG s_begin
 cudaError_t launch_spike_raster(glm_ctx* c, void* out, int64_t s_begin, int64_t s_end);
 cudaError_t launch_filter_range(glm_ctx* c, int64_t t0, int64_t t_len, void* out, int64_t ldx, glm_dtype_t dtype);

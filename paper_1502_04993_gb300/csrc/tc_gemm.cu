@@ -945,8 +945,13 @@ cudaError_t launch_tc_spike_term(glm_ctx* c) {
     cudaError_t e = cudaSuccess;
     for (int64_t t0 = 0; t0 < P.Tpad; t0 += P.Tc) {
         const int64_t len = std::min(P.Tc, P.Tpad - t0);
-        if (P.chunk && (e = launch_filter_cache(c, t0 / SEG, (t0 + len) / SEG)) != cudaSuccess) return e;
-        if ((e = launch_spike_raster(c, c->buf.E, t0 / SEG, (t0 + len) / SEG)) != cudaSuccess) return e;
+        const bool fused = P.delay_bins <= 1 && !P.ct;  // the filter's sources are the rows' own spikes
+        if (P.chunk && (e = launch_filter_cache(c, t0 / SEG, (t0 + len) / SEG, fused ? c->buf.E : nullptr)) != cudaSuccess)
+            return e;
+        const bool raster = !(fused && (P.chunk || c->raster_in_E));
+        if (raster && (e = launch_spike_raster(c, c->buf.E, t0 / SEG, (t0 + len) / SEG)) != cudaSuccess) return e;
+        c->launches += (P.chunk ? 1 : 0) + (raster ? 1 : 0) + 4;  // filter, raster, two products, two sums
+        c->raster_in_E = false;  // consumed below; the next U product overwrites E
         int ns = 0;
         const int64_t bins = P.chunk ? len : P.T;
         if ((e = run_products(c, c->tmap[5], bins, &ns)) != cudaSuccess) return e;

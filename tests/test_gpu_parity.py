@@ -291,3 +291,25 @@ def test_full_size_sampled_rows_f32(ctx, full_size):
     Cr = C.cpu().numpy()[rows]
     assert metric10(r["G"].cpu().numpy()[rows], ref["G"], Cr) <= 1e-5
     assert np.all(np.abs(r["gb"].cpu().numpy()[rows] - ref["gb"]) <= 1e-7 * np.diff(w["offs"])[rows])
+
+
+def test_same_shape_problem_reuses_buffers(glm, ctx):
+    """A second recording of the same shape (neurons, bins, total spikes) renews only the spikes and the
+    caches of the context; its results are those of a fresh context, bit for bit."""
+    w = workload(60, 7000, 6)
+    n, T = w["n"], 7000
+    rows = [w["bins"][w["offs"][i]:w["offs"][i + 1]] for i in range(n)][::-1]  # same total, other rows
+    offs2 = np.zeros(n + 1, dtype=np.int64)
+    offs2[1:] = np.cumsum([len(r) for r in rows])
+    bins2 = np.concatenate(rows).astype(np.int32)
+    W, b = params(w, 9)
+    for prec in ("bf16", "f32"):
+        ctx.set_problem(w["offs"], w["bins"], T, w["dt"], w["tau"], prec=prec)
+        ctx.loglik_grad(to_dev(W), to_dev(b))
+        ctx.set_problem(offs2, bins2, T, w["dt"], 0.015, prec=prec)
+        a = ctx.loglik_grad(to_dev(W), to_dev(b))
+        with glm.GLM(0) as fresh:
+            fresh.set_problem(offs2, bins2, T, w["dt"], 0.015, prec=prec)
+            f = fresh.loglik_grad(to_dev(W), to_dev(b))
+            assert a["L_total"] == f["L_total"]
+            assert torch.equal(a["G"], f["G"]) and torch.equal(a["gb"], f["gb"])
