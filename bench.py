@@ -359,8 +359,10 @@ def run_synfire(args, glm, device, stream, prec):
         c.set_problem(w["offs"], w["bins"], nb, w["dt"], w["tau"], prec=prec)
         r = c.fit(eta=args.fit_eta, max_iter=args.fit_max_iter)
         Wf = r["W"]
-        _, rep = glm.classify(Wf.cpu().numpy().astype(np.float64), "gmm", truth=truth_labels(w["W_true"]),
-                              types=w["types"])
+        Wn = Wf.cpu().numpy().astype(np.float64)
+        truth = truth_labels(w["W_true"])
+        _, rep = glm.classify(Wn, "gmm", truth=truth, types=w["types"])
+        _, rep_k = glm.classify(Wn, "kmeans", truth=truth, types=w["types"])
         torch.cuda.synchronize(device)
         t1 = time.perf_counter()
         Zo = c.ward(Wf, by="out")
@@ -371,7 +373,10 @@ def run_synfire(args, glm, device, stream, prec):
     fo, fi = links_found(Zo, links, w["n"]), links_found(Zi, links, w["n"])
     return {"workload": f"glm_n2000_synfire: N = 2000, {nb * cfg['dt']:g} s, 10 x 50 synfire links, ids shuffled",
             "generation_s": gen_s, "fit": {"seconds": r["report"]["seconds"], "iterations": r["report"]["iterations"],
-                                           "evaluations": r["report"]["evaluations"], "mer": rep["mer"]},
+                                           "evaluations": r["report"]["evaluations"], "mer": rep["mer"],
+                                           "mer_kmeans": rep_k["mer"], "converged": r["report"]["converged"],
+                                           "at_floor": r["report"]["at_floor"], "maxiter": r["report"]["maxiter"],
+                                           "centers_gmm": list(rep["centers"])},
             "ward_seconds_two_linkages": ward_s,
             "links": len(links), "found_by_outgoing": fo, "found_by_incoming": fi,
             "found_by_either": int(sum(a or b for a, b in zip(fo, fi)))}

@@ -237,6 +237,25 @@ def split_recording(offs, bins, n_bins: int, t_split: int):
     return tuple(parts)
 
 
+def split_recording_ct(offs, times, t_begin: float, t_end: float, t_split: float):
+    """Split a continuous-time recording at t_split into a training window [t_begin, t_split) and a
+    validation window [t_split, t_end), times kept as they are.  Returns
+    ((offs, times, t_begin, t_split), (offs, times, t_split, t_end))."""
+    offs = np.ascontiguousarray(offs, dtype=np.int64)
+    times = np.ascontiguousarray(times, dtype=np.float64)
+    if not t_begin < t_split < t_end:
+        raise ValueError("t_split must lie inside the recording")
+    n = offs.size - 1
+    rows = np.repeat(np.arange(n), np.diff(offs))
+    early = times < t_split
+    parts = []
+    for keep, lo, hi in ((early, t_begin, t_split), (~early, t_split, t_end)):
+        o = np.zeros(n + 1, dtype=np.int64)
+        o[1:] = np.cumsum(np.bincount(rows[keep], minlength=n))
+        parts.append((o, times[keep].copy(), lo, hi))
+    return parts[0], parts[1]
+
+
 def cross_validate(train, valid, alphas, taus=None, **fit_kw):
     """glm_cross_validate: fit on context `train` for every alpha (and tau), score on context `valid`.
     Returns dict(L_valid [n_tau x n_alpha], best (k_tau, k_alpha), W, b at the best point)."""

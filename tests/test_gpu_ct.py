@@ -196,3 +196,24 @@ def test_ct_fit_reaches_the_oracle_optimum(ctx):
     L0 = oc.loglik_grad(w["offs"], w["times"], w["t_begin"], w["t_end"], w["tau"], w["delay"], w["W_true"],
                         w["b_true"], grad=False)["L_total"]
     assert ref["L_total"] >= L0
+
+
+def test_ct_cross_validation_recovers_tau(glm):
+    """Cross-validation (Sec. 3.2 / 2.5) on off-grid times: fit on the first 60 % of the window, score on
+    the rest, over tau; the data were generated with tau = 10 ms, which must win, and the best validation
+    L must be the oracle's at the GPU fit."""
+    w = workload(50, 40000, 31, 0.001)
+    (tr, va) = glm.split_recording_ct(w["offs"], w["times"], w["t_begin"], w["t_end"], 24.0)
+    taus = [0.005, 0.01, 0.02]
+    with glm.GLM(0) as a, glm.GLM(0) as v:
+        a.set_problem_ct(tr[0], tr[1], tr[2], tr[3], w["tau"], w["delay"], prec="bf16")
+        v.set_problem_ct(va[0], va[1], va[2], va[3], w["tau"], w["delay"], prec="bf16")
+        res = glm.cross_validate(a, v, [0.0], taus, eta=1e-10, max_iter=500)
+        L = res["L_valid"]
+        print("ct cross-validation", L.ravel())
+        kt, ka = res["best"]
+        assert taus[kt] == 0.01
+        Lo = oc.loglik_grad(va[0], va[1], va[2], va[3], taus[kt], w["delay"],
+                            res["W"].cpu().numpy().astype(np.float64), res["b"].cpu().numpy().astype(np.float64),
+                            grad=False)["L_total"]
+        assert abs(L[kt, ka] - Lo) <= 1e-6 * abs(Lo)

@@ -17,3 +17,12 @@ def test_split_recording_conserves_and_rebases():
         rb = b[1][b[0][i]:b[0][i + 1]]
         assert np.array_equal(np.concatenate([ra, rb + 12000]), row)
         assert np.all(ra < 12000) and np.all(rb >= 0) and np.all(rb < b[2])
+
+
+def test_split_recording_ct():
+    import paper_1502_04993_gb300 as glm
+    offs = np.array([0, 3, 3, 5], dtype=np.int64)
+    times = np.array([0.1, 0.5, 0.9, 0.45, 0.7])
+    (o1, t1, a1, b1), (o2, t2, a2, b2) = glm.split_recording_ct(offs, times, 0.0, 1.0, 0.5)
+    assert o1.tolist() == [0, 1, 1, 2] and t1.tolist() == [0.1, 0.45] and (a1, b1) == (0.0, 0.5)
+    assert o2.tolist() == [0, 2, 2, 3] and t2.tolist() == [0.5, 0.9, 0.7] and (a2, b2) == (0.5, 1.0)
