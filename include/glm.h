@@ -192,6 +192,19 @@ int glm_ward(glm_ctx* ctx, const float* W_dev, int32_t n, int32_t by, const int3
  * their smallest member).  Host function.  Errors: INVALID_ARG. */
 int glm_ward_cut(const double* Z_host, int32_t m, int32_t k, int32_t* labels_host);
 
+/* ---- checks of the library itself (the paper has no counterpart) ----
+ * glm_poison_caches: fill every buffer that glm_prepare and glm_loglik_grad recompute (filtered trains,
+ * rates, partial sums, spike term, segment carries, column constants) with the byte 0xFF, i.e. NaN in
+ * every floating type, and mark the spike term stale.  After glm_prepare the results must be those of a
+ * fresh context bit for bit: no kernel reads a value it did not write (padding bins and rows included).
+ * Errors: INVALID_ARG, NO_PROBLEM, CUDA.
+ * glm_check_wait_limit: run the bounded mbarrier wait of the tensor-core kernels on a barrier nobody
+ * arrives on, with limit_seconds in [1e-4, 2].  Returns GLM_ERR_TIMEOUT when the wait gave up and
+ * reported it (the expected outcome; the context stays usable), GLM_ERR_CUDA if it did not.  The context
+ * needs no problem. */
+int glm_poison_caches(glm_ctx* ctx);
+int glm_check_wait_limit(glm_ctx* ctx, double limit_seconds);
+
 /* Recompute the per-problem caches (filter scan, spike term) from the device-resident spikes, for a new
  * tau (tau > 0) or, with tau <= 0, the current one.  Errors: NO_PROBLEM, INVALID_ARG, CUDA. */
 int glm_prepare(glm_ctx* ctx, double tau);

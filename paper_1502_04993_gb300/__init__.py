@@ -90,6 +90,8 @@ SIGNATURES["glm_fit_classes"] = ([_vp, _i32, ctypes.POINTER(FitOpts), _vp, _vp, 
                                  ctypes.c_int)
 SIGNATURES["glm_ward"] = ([_vp, _vp, _i32, _i32, _vp, _i32, _vp], ctypes.c_int)
 SIGNATURES["glm_ward_cut"] = ([_vp, _i32, _i32, _vp], ctypes.c_int)
+SIGNATURES["glm_poison_caches"] = ([_vp], ctypes.c_int)
+SIGNATURES["glm_check_wait_limit"] = ([_vp, _f64], ctypes.c_int)
 SIGNATURES["glm_set_problem_ct"] = ([_vp, _i32, _f64, _f64, _f64, _f64, _vp, _vp, ctypes.c_int], ctypes.c_int)
 SIGNATURES["glm_problem_columns"] = ([_vp, ctypes.POINTER(_i64)], ctypes.c_int)
 SIGNATURES["glm_ct_interval"] = ([_f64, _f64, _f64, ctypes.POINTER(_f64), ctypes.POINTER(_f64)], ctypes.c_int)
@@ -391,6 +393,14 @@ class GLM:
                                m, Z.ctypes.data)
         self._check(rc, "glm_ward")
         return Z
+
+    def poison_caches(self):
+        """Fill every recomputed buffer with NaN bytes (glm_poison_caches); glm_prepare restores them."""
+        self._check(self.lib.glm_poison_caches(self.h), "glm_poison_caches")
+
+    def check_wait_limit(self, limit_seconds: float = 0.05) -> int:
+        """Status of a bounded wait that nobody satisfies (glm_check_wait_limit): GLM_ERR_TIMEOUT expected."""
+        return int(self.lib.glm_check_wait_limit(self.h, float(limit_seconds)))
 
     def columns(self) -> int:
         """Time columns of the current problem (bins, or event columns in continuous time)."""

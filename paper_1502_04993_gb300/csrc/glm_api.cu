@@ -961,6 +961,52 @@ int glm_fit_classes(glm_ctx* const* cs, int32_t n_class, const glm_fit_opts_t* o
     return worst;
 }
 
+int glm_check_wait_limit(glm_ctx* c, double limit_seconds) {
+    if (!c) return GLM_ERR_INVALID_ARG;
+    if (!(limit_seconds >= 1e-4 && limit_seconds <= 2.0))
+        return fail(c, GLM_ERR_INVALID_ARG, "limit_seconds must lie in [1e-4, 2]");
+    DeviceGuard g(c->device);
+    int* d = nullptr;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, GLM_ERR_OOM, "wait check flag");
+    }
+    int h = 0;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = launch_wait_check(c, (uint64_t)(limit_seconds * 1e9), d);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
+    cudaFree(d);
+    c->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(c, e, "wait check");
+    if (h == 2) return fail(c, GLM_ERR_TIMEOUT, "the bounded wait gave up, as it should");
+    return fail(c, GLM_ERR_CUDA, "the wait on an mbarrier nobody arrives on did not time out");
+}
+
+int glm_poison_caches(glm_ctx* c) {
+    if (!c) return GLM_ERR_INVALID_ARG;
+    if (!c->has_problem) return fail(c, GLM_ERR_NO_PROBLEM, "no problem set");
+    DeviceGuard g(c->device);
+    Buffers& B = c->buf;
+    // everything glm_prepare and glm_loglik_grad recompute; not the spikes, the continuous-time column
+    // times and durations (set-up data) or the optimiser state
+    void* derived[] = {B.seg_carry, B.seg_first, B.pow_seg, B.C, B.C_part, B.X, B.Xlo, B.Gacc, B.E, B.part_e,
+                       B.part_s, B.part_g, B.Wsplit, B.Lrows, B.scal, B.eb, B.part_tau, B.tau_rows,
+                       B.col_a, B.colc, B.seg_mul};
+    for (void* p : derived) {
+        if (!p) continue;
+        for (int k = 0; k < c->n_allocs; ++k)
+            if (c->allocs[k] == p) GLM_CK(cudaMemsetAsync(p, 0xFF, c->alloc_bytes[k], c->stream));
+    }
+    if (B.aseg_first != B.seg_first)
+        for (int k = 0; k < c->n_allocs; ++k)
+            if (c->allocs[k] == B.aseg_first) GLM_CK(cudaMemsetAsync(B.aseg_first, 0xFF, c->alloc_bytes[k], c->stream));
+    c->c_ready = false;
+    c->raster_in_E = false;
+    GLM_CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+    return GLM_OK;
+}
+
 int glm_set_chunk_bins(glm_ctx* c, int64_t chunk_bins) {
     if (!c) return GLM_ERR_INVALID_ARG;
     if (chunk_bins < 0) return fail(c, GLM_ERR_INVALID_ARG, "chunk_bins must be >= 0");

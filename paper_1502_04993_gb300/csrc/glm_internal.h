@@ -164,6 +164,7 @@ cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_
 void launch_exp_bias(glm_ctx* c, const float* b);
 int set_error(glm_ctx* c, int code, const char* msg);
 int ensure_range_rows(glm_ctx* c);
+cudaError_t launch_wait_check(glm_ctx* c, uint64_t limit_ns, int* out);
 // One evaluation at (W, b).  With rows (m of them) only those rows' U product, rates and per-tile sums
 // are formed (their L_rows entries are valid; other rows' entries are not).
 int eval_enqueue(glm_ctx* c, const float* W, const float* b, double* L_rows, double* G, double* gb, bool want_grad,

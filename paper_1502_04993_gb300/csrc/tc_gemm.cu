@@ -962,6 +962,25 @@ cudaError_t launch_tc_spike_term(glm_ctx* c) {
     return e;
 }
 
+// One thread waits, with the bounded wait of the kernels above, on an mbarrier that expects an arrival
+// nobody makes; it must give up after limit_ns and report it (out = 2).
+__global__ void wait_check_kernel(uint64_t limit_ns, int* out) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) out[0] = tc::mbar_wait(&bar, 0, &abort_flag, limit_ns) ? 1 : 2;
+}
+
+cudaError_t launch_wait_check(glm_ctx* c, uint64_t limit_ns, int* out) {
+    wait_check_kernel<<<1, 32, 0, c->stream>>>(limit_ns, out);
+    return cudaGetLastError();
+}
+
 // ---- several problems per launch (glm_fit_batch) ----
 
 size_t tc_batch_bytes() { return sizeof(TcBatch); }
