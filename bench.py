@@ -51,6 +51,8 @@ def parse():
                     help="also evaluate and fit the continuous-time form on this much of the recording, its spikes "
                          "moved off the grid (0: off)")
     ap.add_argument("--no-ct-fit", action="store_true", help="continuous-time leg without its fits (profiling)")
+    ap.add_argument("--classes", type=int, default=4,
+                    help="also evaluate the recording as this many row classes with their own tau and delay (0: off)")
     ap.add_argument("--synfire", action="store_true",
                     help="also fit the N = 2000 synfire-chain recording and find its links by Ward clustering")
     ap.add_argument("--synfire-seconds", type=float, default=3600.0)
@@ -307,6 +309,55 @@ def run_ct(args, glm, w, device, stream, prec):
     return res
 
 
+def run_classes(args, glm, w, device, stream, prec, single_ms):
+    """Per-neuron time constants and delays: the recording's rows split into args.classes classes of
+    equal size, class k with tau = 8 + 2k ms and a delay of k + 1 bins, one context per class evaluating
+    only its rows.  Times one evaluation of all classes (U products over each class's rows, E X^T over
+    its row tiles, reductions) against the single-tau evaluation of the same recording."""
+    import numpy as np
+    import torch
+    n, T = w["n"], w["n_bins"]
+    K = args.classes
+    cuts = [round(k * n / K) for k in range(K + 1)]
+    W = torch.from_numpy(w["W_true"].astype(np.float32)).cuda(device)
+    b = torch.from_numpy(w["b_true"].astype(np.float32)).cuda(device)
+    outs = [{"L_rows": torch.empty(n, dtype=torch.float64, device=device),
+             "G": torch.empty((n, n), dtype=torch.float64, device=device),
+             "gb": torch.empty(n, dtype=torch.float64, device=device)} for _ in range(K)]
+    ctxs = []
+    try:
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        for k in range(K):
+            c = glm.GLM(device, stream=stream)
+            ctxs.append(c)
+            c.set_source_delay(k + 1)
+            c.set_problem(w["offs"], w["bins"], T, w["dt"], 0.008 + 0.002 * k, prec=prec)
+            c.set_row_range(cuts[k], cuts[k + 1])
+        torch.cuda.synchronize(device)
+        setup_s = time.perf_counter() - t0
+        for _ in range(2):
+            for c, o in zip(ctxs, outs):
+                c.loglik_grad(W, b, total=False, out=o)
+        steps = max(3, args.steps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(device)
+        e0.record(stream)
+        for _ in range(steps):
+            for c, o in zip(ctxs, outs):
+                c.loglik_grad(W, b, total=False, out=o)
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        ms = e0.elapsed_time(e1) / steps
+    finally:
+        for c in ctxs:
+            c.close()
+    return {"classes": K, "rows": [cuts[k + 1] - cuts[k] for k in range(K)],
+            "tau_ms": [8 + 2 * k for k in range(K)], "delay_bins": [k + 1 for k in range(K)],
+            "setup_s": setup_s, "ms_per_eval_all_classes": ms, "single_tau_ms_per_eval": single_ms,
+            "neuron_bins_per_s": n * T / (ms / 1000.0)}
+
+
 def chain_links(W_true, w_syn):
     """The links of the planted synfire chain, in chain order, from the generating weights: every neuron of
     link g + 1 receives exactly w_syn from every neuron of link g (no other weight has that value)."""
@@ -557,6 +608,8 @@ def main():
         line["batch"] = run_batch(args, glm, device, prec)
     if args.ct_seconds > 0 and prec != "f32":
         line["continuous_time"] = run_ct(args, glm, w, device, stream, prec)
+    if args.classes > 0 and prec != "f32":
+        line["row_classes"] = run_classes(args, glm, w, device, stream, prec, ms_eval / args.steps)
     if args.synfire:
         line["synfire"] = run_synfire(args, glm, device, stream, prec)
     if ws == 1 and not args.no_cpu_baseline:

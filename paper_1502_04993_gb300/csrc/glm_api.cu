@@ -213,11 +213,11 @@ int alloc_problem(glm_ctx* c) {
         (rc = ws_alloc_t(c, &B.qd, n)) || (rc = ws_alloc_t(c, &B.C, nn)) ||
         (rc = ws_alloc(c, &B.X, (size_t)n * P.Tc * esz)) || (rc = ws_alloc(c, &B.E, (size_t)n * P.Tc * esz)) ||
         (P.chunk && (rc = ws_alloc_t(c, &B.Gacc, nn))) ||
-        (rc = ws_alloc_t(c, &B.part_e, (size_t)n * ntile * (P.ct ? 2 : 1))) ||
+        (rc = ws_alloc_t(c, &B.part_e, (size_t)n * ntile * (P.ct ? CT_PARTS : 1))) ||
         (rc = ws_alloc_t(c, &B.part_g, nn * (tensor ? tc_nsplit_max(c) : grad_nsplit(c)))) ||
         (rc = ws_alloc_t(c, &B.flags, 4)) || (rc = ws_alloc_t(c, &B.Lrows, n)) || (rc = ws_alloc_t(c, &B.scal, 8)) ||
         (rc = ws_alloc_t(c, &B.eb, n)) || (tensor && (rc = ws_alloc(c, &B.Xlo, (size_t)P.n * P.Tc * 2))) ||
-        (rc = ws_alloc_t(c, &B.part_s, (size_t)n * ntile * (P.ct ? 2 : 1))) ||
+        (rc = ws_alloc_t(c, &B.part_s, (size_t)n * ntile * (P.ct ? CT_PARTS : 1))) ||
         (tensor && (rc = ws_alloc(c, &B.Wsplit, 2 * (size_t)n * B.ldn * 2)))) {
         free_all(c);
         return rc;

@@ -21,6 +21,9 @@ constexpr int SEG = 256;
 // free of FP32 rounding; the floor keeps U - c inside the FP32 range of exp when a fit drives b_i far below
 // U (there the quiet bins contribute less than e^-60 per second and their rounding does not matter).
 constexpr float EXP_SPLIT_FLOOR = -60.f;
+// continuous-time U product: epilogue warps per TMEM lane quarter, each with a part of a tile's columns
+// and its own plane of per-tile partial sums
+constexpr int CT_PARTS = 3;
 
 // Powers of a = exp(-dt/tau) split into FP32 hi + lo parts, so that the FP32 scan multiplies by a
 // with ~48 significant bits (the product is hi*x + lo*x).
@@ -69,8 +72,8 @@ struct Buffers {
     double* Gacc = nullptr;       // chunked: [n][n] E X^T summed over the chunks
     int64_t ldn = 0;              // leading dim of the W parts (n rounded up to 64)
     void* E = nullptr;            // F32: float [n][Tpad] dt exp(U); 16-bit: the same, bin-blocked
-    double* part_e = nullptr;     // [n][ntile_t]  per-(row, bin tile) sums of exp(U); continuous time: two
-                                  // such planes, one per half of each tile's columns
+    double* part_e = nullptr;     // [n][ntile_t]  per-(row, bin tile) sums of exp(U); continuous time:
+                                  // CT_PARTS such planes, one per part of each tile's columns
     double* part_s = nullptr;     // [n][ntile_t] per-(row, bin tile) sums of U - b over the spike bins (idem)
     float* part_g = nullptr;      // [nsplit][n][n] FP32 partial sums of E X^T
     void* Wsplit = nullptr;       // 16-bit: hi and lo parts of W, [2][n][ldn]

@@ -26,8 +26,7 @@ struct ReduceArgs {
     const double* part_s;  // [n][ntile] sums of U - b at the spike bins
     const double* qd;
     const double* part_e;  // [n][ntile]
-    const double* part_s2; // second planes of part_s and part_e (continuous time), or null
-    const double* part_e2;
+    int32_t planes;        // planes of part_s and part_e, [planes][n][ntile] (continuous time: CT_PARTS)
     int32_t r0, r1;        // rows outside [r0, r1) (a row range) get L_i = 0 and dL/db_i = 0
     double* L_rows;
     double* gb;
@@ -44,9 +43,9 @@ __global__ void reduce_rows_kernel(const __grid_constant__ ReduceArgs A) {
     double integ = 0.0;
     const double* pe = A.part_e + (int64_t)i * A.ntile;
     for (int64_t t = lane; t < A.ntile; t += 32) integ += pe[t];
-    if (A.part_e2) {
-        const double* ps2 = A.part_s2 + (int64_t)i * A.ntile;
-        const double* pe2 = A.part_e2 + (int64_t)i * A.ntile;
+    for (int32_t pl = 1; pl < A.planes; ++pl) {
+        const double* ps2 = A.part_s + ((int64_t)pl * A.n + i) * A.ntile;
+        const double* pe2 = A.part_e + ((int64_t)pl * A.n + i) * A.ntile;
         for (int64_t t = lane; t < A.ntile; t += 32) {
             spk += ps2[t];
             integ += pe2[t];
@@ -178,8 +177,7 @@ cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_
     A.part_s = c->buf.part_s;
     A.qd = c->buf.qd;
     A.part_e = c->buf.part_e;
-    A.part_s2 = P.ct ? c->buf.part_s + (int64_t)P.n * ntile : nullptr;
-    A.part_e2 = P.ct ? c->buf.part_e + (int64_t)P.n * ntile : nullptr;
+    A.planes = P.ct ? CT_PARTS : 1;
     A.r0 = c->row_r0;
     A.r1 = c->row_r1 < 0 ? P.n : c->row_r1;
     A.L_rows = L_rows;

@@ -42,11 +42,11 @@ namespace glm {
 
 namespace {
 
-// warp 0 TMA, warp 1 MMA, then the epilogue warps: 4 (one per TMEM lane quarter), or 8 for the
-// continuous-time U product, whose epilogue does several times the grid's arithmetic per element (two
-// warps per lane quarter, each taking half of the tile's columns)
+// warp 0 TMA, warp 1 MMA, then the epilogue warps: 4 (one per TMEM lane quarter), or 4 CT_PARTS for the
+// continuous-time U product, whose epilogue does several times the grid's arithmetic per element
+// (CT_PARTS warps per lane quarter, each taking a part of the tile's columns)
 template <int MODE, bool CT>
-constexpr int epi_warps() { return (MODE == 0 && CT) ? 8 : 4; }
+constexpr int epi_warps() { return (MODE == 0 && CT) ? 4 * CT_PARTS : 4; }
 template <int MODE, bool CT>
 constexpr int kthreads() { return 64 + 32 * epi_warps<MODE, CT>(); }
 constexpr int SP_REG = 12;  // spike bins per (row, 256-bin tile) held in registers by the epilogue
@@ -439,9 +439,10 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                 // Continuous-time columns.  Per column m of length D_m: the exact integral of the rate,
                 // e^{b} F(u, D_m) with u = (W V)_i at the column start, and the gradient weight
                 // E'_m = e^{b} G(u, D_m) of Eq. 14 (ct_link.cuh).  With e^{b} = e^{c} e^{sh} as on the grid,
-                // each half-warp pair writes its share of the tile's sums: e^{c} e^{sh} (duration + sum (F - D)),
-                // the duration counted by the first half.  Columns go 8 at a time (one 16-byte word of E').
-                const int half = (warp - 2) >> 2;
+                // each of the CT_PARTS warps of a lane quarter takes a part of the tile's columns and writes its
+                // share of the tile's sums, e^{c} e^{sh} (duration + sum (F - D)), to its own plane (the duration
+                // counted by the first part).  Columns go 8 at a time (one 16-byte word of E').
+                const int part = (warp - 2) >> 2;  // 0 .. CT_PARTS - 1
                 const uint32_t taddr = lane_base + (uint32_t)(buf * BN);
                 const int32_t il = w.m0 + row;
                 const int32_t i = il < s_m[p] ? (A.rows ? A.rows[il] : il) : A.n;
@@ -464,19 +465,15 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                 for (int u = 0; u < SP_REG; ++u) sb[u] = (kb + u < ke) ? (int)(A.bins[kb + u] - gt0) : BN;
                 T16* erow = reinterpret_cast<T16*>(A.E) + ((int64_t)(w.n0 / 64) * A.n + i) * 64;
                 const float4* colq = reinterpret_cast<const float4*>(A.colc) + 2 * gt0;
-                const int g_begin = half * (BN / 16), g_end = (half + 1) * (BN / 16);
-                // column constants of the next group are loaded while this one is computed
-                float4 kc[8], kn[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) kc[e] = __ldg(colq + 2 * (g_begin * 8 + e));
+                const int g_begin = part * (BN / 8) / CT_PARTS, g_end = (part + 1) * (BN / 8) / CT_PARTS;
 #pragma unroll 1
                 for (int g = g_begin; g < g_end; ++g) {
                     const int c0 = g * 8;  // first column of the group within the tile
                     uint32_t r[8];
                     tc::tmem_ld8(taddr + c0, r);
-                    const int cn = (g + 1 < g_end ? g + 1 : g) * 8;
+                    float4 kc[8];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) kn[e] = __ldg(colq + 2 * (cn + e));
+                    for (int e = 0; e < 8; ++e) kc[e] = __ldg(colq + 2 * (c0 + e));
                     tc::tmem_ld_wait();
                     uint32_t sm = 0;  // spike mask: bit e <-> column c0 + e
 #pragma unroll
@@ -524,12 +521,10 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                     if (i < A.n)
                         *reinterpret_cast<uint4*>(erow + (int64_t)(c0 >> 6) * A.n * 64 + (c0 & 63)) =
                             make_uint4(pk[0], pk[1], pk[2], pk[3]);
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) kc[e] = kn[e];
                 }
                 if (i < A.n) {
-                    const double rsum = (double)esh * ((half == 0 ? A.tile_span[gtile] : 0.0) + (double)s);
-                    const int64_t o = (int64_t)half * A.n * A.ntile + (int64_t)i * A.ntile + gtile;
+                    const double rsum = (double)esh * ((part == 0 ? A.tile_span[gtile] : 0.0) + (double)s);
+                    const int64_t o = (int64_t)part * A.n * A.ntile + (int64_t)i * A.ntile + gtile;
                     A.part_e[o] = ebi * rsum;
                     A.part_s[o] = (double)spv;
                 }
