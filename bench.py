@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-ct-fit", action="store_true", help="continuous-time leg without its fits (profiling)")
     ap.add_argument("--classes", type=int, default=4,
                     help="also evaluate the recording as this many row classes with their own tau and delay (0: off)")
+    ap.add_argument("--undersampling", default="",
+                    help="comma list of sampled fractions (e.g. 0.25,0.5,0.75,1): refit on random neuron subsets "
+                         "with the E:I ratio kept and report the misclassification rate (k-means and GMM)")
     ap.add_argument("--synfire", action="store_true",
                     help="also fit the N = 2000 synfire-chain recording and find its links by Ward clustering")
     ap.add_argument("--synfire-seconds", type=float, default=3600.0)
@@ -358,6 +361,36 @@ def run_classes(args, glm, w, device, stream, prec, single_ms):
             "neuron_bins_per_s": n * T / (ms / 1000.0)}
 
 
+def run_undersampling(args, glm, w, device, stream, prec):
+    """Undersampling (App. C.2): fit only the spike trains of a random subset of the neurons (excitatory
+    and inhibitory in their full proportion), classify the subset's weights against the generating ones."""
+    import numpy as np
+    from oracle.classify import truth_labels  # ground-truth labels from the generating W (no fitting)
+    rng = np.random.default_rng(17)
+    exc = np.nonzero(w["types"] > 0)[0]
+    inh = np.nonzero(w["types"] < 0)[0]
+    out = []
+    for f in [float(x) for x in args.undersampling.split(",") if x]:
+        sub = np.sort(np.concatenate([rng.choice(exc, int(round(f * len(exc))), replace=False),
+                                      rng.choice(inh, int(round(f * len(inh))), replace=False)]))
+        offs = np.zeros(len(sub) + 1, dtype=np.int64)
+        offs[1:] = np.cumsum([w["offs"][i + 1] - w["offs"][i] for i in sub])
+        bins = np.concatenate([w["bins"][w["offs"][i]:w["offs"][i + 1]] for i in sub]).astype(np.int32)
+        c = glm.GLM(device, stream=stream)
+        try:
+            c.set_problem(offs, bins, w["n_bins"], w["dt"], w["tau"], prec=prec)
+            r = c.fit(eta=args.fit_eta, max_iter=args.fit_max_iter)
+        finally:
+            c.close()
+        Wf = r["W"].cpu().numpy().astype(np.float64)
+        truth = truth_labels(w["W_true"][np.ix_(sub, sub)])
+        _, rg = glm.classify(Wf, "gmm", truth=truth, types=w["types"][sub])
+        _, rk = glm.classify(Wf, "kmeans", truth=truth, types=w["types"][sub])
+        out.append({"fraction": f, "neurons": int(len(sub)), "fit_seconds": r["report"]["seconds"],
+                    "mer_gmm": rg["mer"], "mer_kmeans": rk["mer"]})
+    return out
+
+
 def chain_links(W_true, w_syn):
     """The links of the planted synfire chain, in chain order, from the generating weights: every neuron of
     link g + 1 receives exactly w_syn from every neuron of link g (no other weight has that value)."""
@@ -610,6 +643,8 @@ def main():
         line["continuous_time"] = run_ct(args, glm, w, device, stream, prec)
     if args.classes > 0 and prec != "f32":
         line["row_classes"] = run_classes(args, glm, w, device, stream, prec, ms_eval / args.steps)
+    if args.undersampling:
+        line["undersampling"] = run_undersampling(args, glm, w, device, stream, prec)
     if args.synfire:
         line["synfire"] = run_synfire(args, glm, device, stream, prec)
     if ws == 1 and not args.no_cpu_baseline:
