@@ -237,7 +237,7 @@ def run_ct(args, glm, w, device, stream, prec):
     import numpy as np
     import torch
     import synth
-    from oracle.classify import truth_labels  # ground-truth labels from the generating W (no fitting)
+    from synth import truth_labels
     n, dt, tau = w["n"], w["dt"], w["tau"]
     nb = min(w["n_bins"], int(round(args.ct_seconds / dt)))
     offs, bins = w["offs"], w["bins"]
@@ -365,7 +365,7 @@ def run_undersampling(args, glm, w, device, stream, prec):
     """Undersampling (App. C.2): fit only the spike trains of a random subset of the neurons (excitatory
     and inhibitory in their full proportion), classify the subset's weights against the generating ones."""
     import numpy as np
-    from oracle.classify import truth_labels  # ground-truth labels from the generating W (no fitting)
+    from synth import truth_labels
     rng = np.random.default_rng(17)
     exc = np.nonzero(w["types"] > 0)[0]
     inh = np.nonzero(w["types"] < 0)[0]
@@ -431,7 +431,7 @@ def run_synfire(args, glm, device, stream, prec):
     import numpy as np
     import torch
     import synth
-    from oracle.classify import truth_labels  # ground-truth labels from the generating W (no fitting)
+    from synth import truth_labels
     cfg = synth.WORKLOADS["glm_n2000_synfire_t3600s"]
     nb = int(round(args.synfire_seconds / cfg["dt"]))
     t0 = time.perf_counter()
@@ -620,7 +620,7 @@ def main():
     }
     if args.fit:
         # full fits: wall time of glm_fit per precision, and the classification against the ground truth
-        from oracle.classify import truth_labels  # ground-truth labels from the generating W (no fitting)
+        from synth import truth_labels
         truth = truth_labels(w["W_true"])
         fits = {}
         for p in [s for s in args.fit.split(",") if s]:

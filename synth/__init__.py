@@ -133,6 +133,15 @@ WORKLOADS = {
 }
 
 
+def truth_labels(W_true: np.ndarray) -> np.ndarray:
+    """Ground-truth connection classes of a generated network: +1 excitatory, -1 inhibitory, 0 absent
+    (W_true[i, j] is the weight from j onto i; the diagonal, the self-coupling, is no connection)."""
+    W_true = np.asarray(W_true)
+    lab = np.sign(W_true).astype(np.int8)
+    np.fill_diagonal(lab, 0)
+    return lab
+
+
 def make_workload(name: str | None = None, *, threads: int = 0, **overrides) -> dict:
     """Generate a named workload (ground truth + spikes).  Any field may be overridden."""
     cfg = dict(WORKLOADS[name]) if name else {}

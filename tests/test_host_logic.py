@@ -26,3 +26,13 @@ def test_split_recording_ct():
     (o1, t1, a1, b1), (o2, t2, a2, b2) = glm.split_recording_ct(offs, times, 0.0, 1.0, 0.5)
     assert o1.tolist() == [0, 1, 1, 2] and t1.tolist() == [0.1, 0.45] and (a1, b1) == (0.0, 0.5)
     assert o2.tolist() == [0, 2, 2, 3] and t2.tolist() == [0.5, 0.9, 0.7] and (a2, b2) == (0.5, 1.0)
+
+
+def test_synth_truth_labels_match_the_oracle_definition():
+    """The bench's ground-truth labels (from the generator) agree with the oracle's classification truth."""
+    import synth
+    from oracle.classify import truth_labels
+    rng = np.random.default_rng(0)
+    W = rng.choice([-1.2, 0.0, 0.3], size=(37, 37), p=[0.1, 0.8, 0.1])
+    np.fill_diagonal(W, -3.0)
+    assert np.array_equal(synth.truth_labels(W), truth_labels(W))
