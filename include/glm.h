@@ -109,7 +109,11 @@ void glm_destroy(glm_ctx* ctx);
  *               each in [0, n_bins).  At most one spike per neuron and bin.
  *   prec:       precision of the contractions (glm_prec_t).
  * The spikes are copied to the device; the host arrays may be freed on return.  Replaces any previous
- * problem.  Errors: INVALID_ARG, UNSORTED_SPIKES, SPIKE_OUT_OF_RANGE, OOM, CUDA, UNSUPPORTED_ARCH. */
+ * problem.  A recording with the current problem's n, n_bins, spike count, precision, chunking and delay
+ * reuses its buffers: its spikes are copied to a second device buffer (allocated by the first such call) and
+ * checked there, and replace the current ones only when they pass; otherwise the host checks them.  Either
+ * way a recording that fails the check changes nothing and gets the same error and message.
+ * Errors: INVALID_ARG, UNSORTED_SPIKES, SPIKE_OUT_OF_RANGE, OOM, CUDA, UNSUPPORTED_ARCH. */
 int glm_set_problem(glm_ctx* ctx, int32_t n, int64_t n_bins, double dt, double tau, const int64_t* offs_host,
                     const int32_t* bins_host, glm_prec_t prec);
 

@@ -468,6 +468,42 @@ cudaError_t launch_spike_raster(glm_ctx* c, void* out, int64_t s_begin, int64_t 
     return cudaGetLastError();
 }
 
+// Spike ingest check on the device, for a CSR whose offsets the host has checked (offs[0] = 0, non-decreasing,
+// offs[n] = q): every bin inside [0, T) and the bins of each row strictly increasing.  A fault at index k has
+// the key 2k (bin out of range) or 2k + 1 (not above the row's previous bin); the smallest key is kept, so the
+// host names the same first fault as a pass over the rows in order.  Index k starts a row when some offs[i]
+// equals k (binary search; needed only where bins[k] <= bins[k - 1]).
+__global__ void __launch_bounds__(256) check_bins_kernel(int32_t n, int64_t q, int64_t T,
+                                                         const int64_t* __restrict__ offs,
+                                                         const int32_t* __restrict__ bins,
+                                                         unsigned long long* __restrict__ first_bad) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < q; k += stride) {
+        const int32_t s = __ldg(bins + k);
+        unsigned long long key = ~0ull;
+        if (s < 0 || (int64_t)s >= T) {
+            key = 2ull * (unsigned long long)k;
+        } else if (k > 0 && s <= __ldg(bins + k - 1)) {
+            int32_t lo = 0, hi = n;  // offs[lo] <= k < offs[hi] is kept; offs[0] = 0 <= k and offs[n] = q > k
+            while (hi - lo > 1) {
+                const int32_t mid = lo + (hi - lo) / 2;
+                if (__ldg(offs + mid) <= k) lo = mid; else hi = mid;
+            }
+            if (__ldg(offs + lo) != k) key = 2ull * (unsigned long long)k + 1ull;
+        }
+        if (key != ~0ull) atomicMin(first_bad, key);
+    }
+}
+
+cudaError_t launch_check_bins(glm_ctx* c, int32_t n, int64_t q, int64_t T, const int64_t* offs, const int32_t* bins,
+                              unsigned long long* first_bad) {
+    cudaError_t e = cudaMemsetAsync(first_bad, 0xFF, sizeof(unsigned long long), c->stream);
+    if (e != cudaSuccess || q <= 0) return e;
+    const int64_t blocks = std::min<int64_t>((q + 255) / 256, (int64_t)c->sm_count * 8);
+    check_bins_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(n, q, T, offs, bins, first_bad);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_carry(glm_ctx* c) {
     const Problem& P = c->pb;
     const Buffers& B = c->buf;

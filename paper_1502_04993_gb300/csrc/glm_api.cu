@@ -158,12 +158,29 @@ bool rows_valid(int32_t i0, int32_t i1, int64_t T, const int64_t* offs, const in
     return true;
 }
 
-int validate_spikes(glm_ctx* c, int32_t n, int64_t T, const int64_t* offs, const int32_t* bins) {
+// offsets of a CSR spike list: offs[0] = 0, non-decreasing, and bins given when there are spikes
+int validate_offs(glm_ctx* c, int32_t n, const int64_t* offs, const int32_t* bins) {
     if (offs[0] != 0) return fail(c, GLM_ERR_SPIKE_OUT_OF_RANGE, "offs[0] must be 0");
     for (int32_t i = 0; i < n; ++i)
         if (offs[i + 1] < offs[i]) return fail(c, GLM_ERR_SPIKE_OUT_OF_RANGE, "offs must be non-decreasing");
+    if (offs[n] > 0 && !bins) return fail(c, GLM_ERR_INVALID_ARG, "bins is NULL but offs[n] > 0");
+    return GLM_OK;
+}
+
+// the error for the first fault, at spike index k: bin out of range (range) or not above the previous bin
+int bins_fault(glm_ctx* c, int32_t n, const int64_t* offs, const int32_t* bins, int64_t k, bool range) {
+    const int32_t i = (int32_t)(std::upper_bound(offs, offs + n + 1, k) - offs - 1);
+    if (range)
+        return fail(c, GLM_ERR_SPIKE_OUT_OF_RANGE,
+                    "spike bin " + std::to_string(bins[k]) + " of row " + std::to_string(i) + " outside [0, n_bins)");
+    return fail(c, GLM_ERR_UNSORTED_SPIKES,
+                "row " + std::to_string(i) + ": bins not strictly increasing at index " + std::to_string(k));
+}
+
+int validate_spikes(glm_ctx* c, int32_t n, int64_t T, const int64_t* offs, const int32_t* bins) {
+    int rc = validate_offs(c, n, offs, bins);
+    if (rc) return rc;
     const int64_t q = offs[n];
-    if (q > 0 && !bins) return fail(c, GLM_ERR_INVALID_ARG, "bins is NULL but offs[n] > 0");
     // large recordings: the rows are checked on several host threads, split by spike count; only when
     // one of them finds a fault does the single pass below run, to name the first one
     const int nt = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
@@ -184,15 +201,47 @@ int validate_spikes(glm_ctx* c, int32_t n, int64_t T, const int64_t* offs, const
         int64_t prev = -1;
         for (int64_t k = offs[i]; k < offs[i + 1]; ++k) {
             const int64_t s = bins[k];
-            if (s < 0 || s >= T)
-                return fail(c, GLM_ERR_SPIKE_OUT_OF_RANGE,
-                            "spike bin " + std::to_string(s) + " of row " + std::to_string(i) + " outside [0, n_bins)");
-            if (s <= prev)
-                return fail(c, GLM_ERR_UNSORTED_SPIKES,
-                            "row " + std::to_string(i) + ": bins not strictly increasing at index " + std::to_string(k));
+            if (s < 0 || s >= T) return bins_fault(c, n, offs, bins, k, true);
+            if (s <= prev) return bins_fault(c, n, offs, bins, k, false);
             prev = s;
         }
     }
+    return GLM_OK;
+}
+
+// The spikes of a recording with the shape of the current problem into its offs / bins.  They are copied to
+// staging buffers and checked there on the device (bins in range, rows strictly increasing), so a recording
+// that fails leaves the current problem as it was; then the staging and current buffers swap.  Without room
+// for the staging buffers the host checks the bins and they are copied in place.
+int stage_spikes(glm_ctx* c, int32_t n, int64_t T, const int64_t* offs, const int32_t* bins) {
+    Buffers& B = c->buf;
+    const int64_t q = offs[n];
+    if (!(B.offs_next && B.bins_next && B.bad)) {
+        const std::string keep = c->last_error;
+        if (!B.offs_next) ws_alloc_t(c, &B.offs_next, n + 1);
+        if (!B.bins_next) ws_alloc_t(c, &B.bins_next, q > 0 ? q : 1);
+        if (!B.bad) ws_alloc_t(c, &B.bad, 1);
+        c->last_error = keep;
+    }
+    if (!(B.offs_next && B.bins_next && B.bad)) {
+        int rc = validate_spikes(c, n, T, offs, bins);
+        if (rc) return rc;
+        GLM_CK(cudaMemcpyAsync(B.offs, offs, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, c->stream));
+        if (q > 0) GLM_CK(cudaMemcpyAsync(B.bins, bins, sizeof(int32_t) * q, cudaMemcpyHostToDevice, c->stream));
+        return GLM_OK;
+    }
+    GLM_CK(cudaMemcpyAsync(B.offs_next, offs, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, c->stream));
+    if (q > 0) GLM_CK(cudaMemcpyAsync(B.bins_next, bins, sizeof(int32_t) * q, cudaMemcpyHostToDevice, c->stream));
+    GLM_CK(launch_check_bins(c, n, q, T, B.offs_next, B.bins_next, B.bad));
+    c->launches += q > 0 ? 1 : 0;
+    unsigned long long key = ~0ull;
+    GLM_CK(cudaMemcpyAsync(&key, B.bad, sizeof(key), cudaMemcpyDeviceToHost, c->stream));
+    GLM_CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+    if (key != ~0ull) return bins_fault(c, n, offs, bins, (int64_t)(key >> 1), (key & 1ull) == 0);
+    std::swap(B.offs, B.offs_next);
+    std::swap(B.bins, B.bins_next);
+    B.aoffs = B.offs;  // one-bin delay: the filter's sources are the spikes themselves
+    B.abins = B.bins;
     return GLM_OK;
 }
 
@@ -509,7 +558,7 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
     if (tensor && !(c->cc_major == 10 && c->cc_minor == 3))
         return fail(c, GLM_ERR_UNSUPPORTED_ARCH, "BF16/F16 tensor-core paths need an sm_103 GPU (found sm_" +
                                                      std::to_string(c->cc_major) + std::to_string(c->cc_minor) + ")");
-    int rc = validate_spikes(c, n, n_bins, offs, bins);
+    int rc = validate_offs(c, n, offs, bins);
     if (rc) return rc;
     DeviceGuard g(c->device);
     GLM_CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
@@ -521,6 +570,7 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
                                   ? round_up(c->chunk_req, 16 * SEG) : 0;
         if (c->has_problem && !O.ct && O.n == n && O.T == n_bins && O.q == offs[n] && O.prec == prec &&
             O.chunk == chunk && O.delay_bins == c->delay_req && c->delay_req <= 1) {
+            if ((rc = stage_spikes(c, n, n_bins, offs, bins))) return rc;
             c->has_problem = false;
             Problem& P = c->pb;
             P.dt = dt;
@@ -530,8 +580,6 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
             Buffers& B = c->buf;
             std::vector<double> qd(n);
             for (int32_t i = 0; i < n; ++i) qd[i] = (double)(offs[i + 1] - offs[i]);
-            GLM_CK(cudaMemcpyAsync(B.offs, offs, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, c->stream));
-            if (P.q > 0) GLM_CK(cudaMemcpyAsync(B.bins, bins, sizeof(int32_t) * P.q, cudaMemcpyHostToDevice, c->stream));
             GLM_CK(cudaMemcpyAsync(B.qd, qd.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
             GLM_CK(cudaMemsetAsync(B.flags, 0, 4 * sizeof(int), c->stream));
             if ((rc = do_prepare(c))) {
@@ -543,6 +591,7 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
             return GLM_OK;
         }
     }
+    if ((rc = validate_spikes(c, n, n_bins, offs, bins))) return rc;
     free_all(c);
     Problem& P = c->pb;
     P = Problem();

@@ -98,6 +98,11 @@ struct Buffers {
     double* seg_mul = nullptr;    // [nseg] decay over each 256-column segment
     double* tile_span = nullptr;  // [nseg] duration of each 256-column segment
     int32_t* range_rows = nullptr;// [r1 - r0] the rows r0 .. r1 - 1 of a row range (glm_set_row_range)
+    // a recording of the same shape is copied here and checked on the device before it replaces offs / bins
+    // (allocated by the first such recording)
+    int64_t* offs_next = nullptr; // [n+1]
+    int32_t* bins_next = nullptr; // [q]
+    unsigned long long* bad = nullptr; // [1] first fault found by the check (launch_check_bins)
 };
 
 }  // namespace glm
@@ -146,6 +151,10 @@ namespace glm {
 
 // ---- launchers (each returns cudaError_t of the launch) ----
 cudaError_t launch_carry(glm_ctx* c);
+// device check of a CSR spike list whose offsets are valid: *first_bad = smallest 2k (bin k outside [0, T)) or
+// 2k + 1 (bin k not above the previous bin of its row), all ones when there is none
+cudaError_t launch_check_bins(glm_ctx* c, int32_t n, int64_t q, int64_t T, const int64_t* offs, const int32_t* bins,
+                              unsigned long long* first_bad);
 // segments [s_begin, s_end) into the X buffers (whose first bin is SEG s_begin); s_end < 0: all
 // raster: also write the rows' spike raster (16-bit 0 / 1) there; only where the filter's sources are the
 // rows' own spikes (grid form, one-bin delay)

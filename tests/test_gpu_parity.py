@@ -313,3 +313,37 @@ def test_same_shape_problem_reuses_buffers(glm, ctx):
             f = fresh.loglik_grad(to_dev(W), to_dev(b))
             assert a["L_total"] == f["L_total"]
             assert torch.equal(a["G"], f["G"]) and torch.equal(a["gb"], f["gb"])
+
+
+def test_same_shape_recording_checked_on_device(glm, ctx):
+    """A recording of the current problem's shape is checked on the device: a bin out of range or rows not
+    strictly increasing give the errors (and messages) of the host check, and the problem stays as it was."""
+    w = workload(40, 5000, 8)
+    n, T = w["n"], 5000
+    W, b = params(w, 4)
+    ctx.set_problem(w["offs"], w["bins"], T, w["dt"], w["tau"], prec="bf16")
+    before = ctx.loglik_grad(to_dev(W), to_dev(b))
+    offs = w["offs"]
+    r = int(np.argmax(np.diff(offs)))  # a row with several spikes
+    k0 = int(offs[r])
+    cases = []
+    bad = w["bins"].copy(); bad[k0 + 1] = T                      # out of range
+    cases.append((bad, glm.GLMError, "outside"))
+    bad = w["bins"].copy(); bad[k0 + 1] = bad[k0]                # two spikes in one bin
+    cases.append((bad, glm.GLMError, "strictly increasing"))
+    bad = w["bins"].copy(); bad[k0 + 2] = -1                     # negative
+    cases.append((bad, glm.GLMError, "outside"))
+    for bins, exc, text in cases:
+        with pytest.raises(exc) as e_dev:
+            ctx.set_problem(offs, bins, T, w["dt"], w["tau"], prec="bf16")
+        with glm.GLM(0) as fresh, pytest.raises(exc) as e_host:
+            fresh.set_problem(offs, bins, T, w["dt"], w["tau"], prec="bf16")
+        assert text in str(e_dev.value) and str(e_dev.value) == str(e_host.value)
+        after = ctx.loglik_grad(to_dev(W), to_dev(b))
+        assert after["L_total"] == before["L_total"] and torch.equal(after["G"], before["G"])
+    # a row that starts lower than the previous row ends is valid (rows are checked separately)
+    rows = [w["bins"][offs[i]:offs[i + 1]] for i in range(n)]
+    assert any(len(rows[i]) and len(rows[i - 1]) and rows[i][0] <= rows[i - 1][-1] for i in range(1, n))
+    ctx.set_problem(offs, w["bins"], T, w["dt"], w["tau"], prec="bf16")
+    again = ctx.loglik_grad(to_dev(W), to_dev(b))
+    assert again["L_total"] == before["L_total"]
