@@ -61,6 +61,22 @@ __global__ void reduce_rows_kernel(const __grid_constant__ ReduceArgs A) {
     }
 }
 
+// sum over the splits p = 0 .. nsplit-1 of part_g[p nn + e], added in split order; the loads of 8 splits are
+// issued before their adds, so a thread keeps 8 reads in flight (the splits are tens to hundreds of MB)
+__device__ __forceinline__ double sum_parts(const float* __restrict__ part_g, int64_t nn, int64_t e, int nsplit) {
+    double s = 0.0;
+    int p = 0;
+    for (; p + 8 <= nsplit; p += 8) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldcs(part_g + (int64_t)(p + u) * nn + e);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += (double)v[u];
+    }
+    for (; p < nsplit; ++p) s += (double)__ldcs(part_g + (int64_t)p * nn + e);
+    return s;
+}
+
 // G rows outside [e0, e1) (element range of a row range) are set to zero
 __global__ void reduce_grad_kernel(int64_t nn, int nsplit, const double* __restrict__ C,
                                    const float* __restrict__ part_g, const double* __restrict__ Gacc,
@@ -75,7 +91,7 @@ __global__ void reduce_grad_kernel(int64_t nn, int nsplit, const double* __restr
     if (Gacc)
         s = Gacc[e];
     else
-        for (int p = 0; p < nsplit; ++p) s += (double)part_g[p * nn + e];
+        s = sum_parts(part_g, nn, e, nsplit);
     G[e] = C[e] - s;
 }
 
@@ -84,8 +100,7 @@ __global__ void sum_splits_kernel(int64_t nn, int nsplit, const float* __restric
                                   bool accumulate) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nn) return;
-    double s = 0.0;
-    for (int p = 0; p < nsplit; ++p) s += (double)part_g[p * nn + e];
+    const double s = sum_parts(part_g, nn, e, nsplit);
     C[e] = accumulate ? C[e] + s : s;
 }
 
