@@ -34,20 +34,30 @@ void fill_scan_consts(double a, ScanConsts* sc) {
 // Segment-first indices and, in seg_local (when given), the contribution of each segment's own spikes to X
 // at the next segment start: sum_{t in seg s} a^(256 (s+1) - 1 - t) on the grid; with continuous-time
 // columns (ctime given) sum exp(-(c_end - c_{t+1}) / tau), a source t arriving at column t+1.
-// Block per row, SL_W warps; warp w owns a contiguous range of segments and finds its spikes by binary
-// search in the row's sorted bins.  It walks them 32 at a time with coalesced loads: the spikes of one
+// Block per row, SL_W warps; warp w owns a contiguous range of segments and finds its spikes by a search in
+// the row's sorted bins.  It walks them 32 at a time (the loads of four such steps issued together): the spikes of one
 // segment are adjacent lanes, their terms are summed by a shuffle tree over the run, and a run that goes on
 // past the 32 lanes is carried to the next step (its partial sum first).  The order of the FP64 additions
 // depends only on the data: the result is reproducible.
 constexpr int SL_W = 8;
 
-__device__ __forceinline__ int64_t lower_bound_bins(const int32_t* __restrict__ b, int64_t q, int64_t x) {
-    int64_t lo = 0, hi = q;  // first k with b[k] >= x
-    while (lo < hi) {
-        const int64_t mid = lo + (hi - lo) / 2;
-        if ((int64_t)__ldg(b + mid) < x) lo = mid + 1; else hi = mid;
+// First k in [lo0, q) with b[k] >= x (q if none) in the sorted bins of a row, found by the whole warp: each
+// round probes 32 points that split the interval in 33 parts, so a row of 10^4 spikes takes 4 dependent
+// loads.  Every probe lies inside [lo, hi) and the interval shrinks every round.
+__device__ __forceinline__ int64_t warp_lower_bound(const int32_t* __restrict__ b, int64_t lo0, int64_t q, int64_t x,
+                                                    int lane) {
+    int64_t lo = lo0, hi = q;  // b[k] < x for k < lo, b[k] >= x for hi <= k < q
+    while (hi - lo > 32) {
+        const int64_t p = lo + (hi - lo) * (lane + 1) / 33;
+        const uint32_t below = __ballot_sync(FULL, (int64_t)__ldg(b + p) < x);
+        const int c = __popc(below);  // the lanes below x are a prefix
+        const int64_t plo = __shfl_sync(FULL, p, c > 0 ? c - 1 : 0);
+        const int64_t phi = __shfl_sync(FULL, p, c < 32 ? c : 31);
+        if (c > 0) lo = plo + 1;
+        if (c < 32) hi = phi;
     }
-    return lo;
+    const int64_t p = lo + lane;
+    return lo + __popc(__ballot_sync(FULL, p < hi && (int64_t)__ldg(b + p) < x));
 }
 
 __global__ void __launch_bounds__(SL_W * 32) seg_local_kernel(int32_t n, int64_t nseg, const int64_t* __restrict__ offs,
@@ -65,41 +75,50 @@ __global__ void __launch_bounds__(SL_W * 32) seg_local_kernel(int32_t n, int64_t
     if (sb >= se) return;
     if (loc)
         for (int64_t s = sb + lane; s < se; s += 32) loc[s] = 0.0;
-    const int64_t k_lo = lower_bound_bins(b, q, sb * SEG), k_hi = lower_bound_bins(b, q, se * SEG);
+    const int64_t k_lo = warp_lower_bound(b, 0, q, sb * SEG, lane);
+    const int64_t k_hi = warp_lower_bound(b, k_lo, q, se * SEG, lane);
     __syncwarp();
     int64_t last_s = sb - 1;   // segment of the previous spike of the range
     int64_t open_s = -1;       // segment of the run still open at the end of the previous step
     double open_acc = 0.0;     // its partial sum
-    for (int64_t base = k_lo; base < k_hi; base += 32) {
-        const int64_t k = base + lane;
-        const bool valid = k < k_hi;
-        const int64_t bk = valid ? (int64_t)__ldg(b + k) : 0;
-        const int64_t s = valid ? bk / SEG : INT64_MAX;
-        int64_t prev_s = __shfl_up_sync(FULL, s, 1);
-        if (lane == 0) prev_s = last_s;
-        const bool head = valid && s != prev_s;
-        if (head)
-            for (int64_t ss = prev_s + 1; ss <= s; ++ss) first[ss] = (int32_t)k;
-        const int last_lane = (k_hi - 1 - base < 31) ? (int)(k_hi - 1 - base) : 31;
-        if (loc) {
-            const int64_t end = (s + 1) * SEG;
-            double v = 0.0;
-            if (valid) v = ctime ? exp(-(ctime[end] - ctime[bk + 1]) * inv_tau) : pow_seg[end - 1 - bk];
+    for (int64_t base0 = k_lo; base0 < k_hi; base0 += 4 * 32) {
+        int32_t pre[4];  // the bins of four steps, loaded together
 #pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {  // lane l: sum over [l, min(l + 2 off, end of its run))
-                const double t = __shfl_down_sync(FULL, v, off);
-                const int64_t ts = __shfl_down_sync(FULL, s, off);
-                if (lane + off < 32 && ts == s) v += t;
+        for (int u = 0; u < 4; ++u) pre[u] = (base0 + 32 * u + lane < k_hi) ? __ldg(b + base0 + 32 * u + lane) : 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t base = base0 + 32 * u;
+            if (base >= k_hi) break;
+            const int64_t k = base + lane;
+            const bool valid = k < k_hi;
+            const int64_t bk = valid ? (int64_t)pre[u] : 0;
+            const int64_t s = valid ? bk / SEG : INT64_MAX;
+            int64_t prev_s = __shfl_up_sync(FULL, s, 1);
+            if (lane == 0) prev_s = last_s;
+            const bool head = valid && s != prev_s;
+            if (head)
+                for (int64_t ss = prev_s + 1; ss <= s; ++ss) first[ss] = (int32_t)k;
+            const int last_lane = (k_hi - 1 - base < 31) ? (int)(k_hi - 1 - base) : 31;
+            if (loc) {
+                const int64_t end = (s + 1) * SEG;
+                double v = 0.0;
+                if (valid) v = ctime ? exp(-(ctime[end] - ctime[bk + 1]) * inv_tau) : pow_seg[end - 1 - bk];
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {  // lane l: sum over [l, min(l + 2 off, end of its run))
+                    const double t = __shfl_down_sync(FULL, v, off);
+                    const int64_t ts = __shfl_down_sync(FULL, s, off);
+                    if (lane + off < 32 && ts == s) v += t;
+                }
+                const bool lead = head || (lane == 0 && valid);  // first lane of a run in this step
+                if (lane == 0 && valid && s == open_s) v = open_acc + v;
+                if (lead) loc[s] = v;  // a run carried on to the next step is written again there
+                const uint32_t leads = __ballot_sync(FULL, lead) & (0xffffffffu >> (31 - last_lane));
+                const int hl = 31 - __clz(leads);
+                open_acc = __shfl_sync(FULL, v, hl);
+                open_s = __shfl_sync(FULL, s, hl);
             }
-            const bool lead = head || (lane == 0 && valid);  // first lane of a run in this step
-            if (lane == 0 && valid && s == open_s) v = open_acc + v;
-            if (lead) loc[s] = v;  // a run carried on to the next step is written again there
-            const uint32_t leads = __ballot_sync(FULL, lead) & (0xffffffffu >> (31 - last_lane));
-            const int hl = 31 - __clz(leads);
-            open_acc = __shfl_sync(FULL, v, hl);
-            open_s = __shfl_sync(FULL, s, hl);
+            last_s = __shfl_sync(FULL, s, last_lane);
         }
-        last_s = __shfl_sync(FULL, s, last_lane);
     }
     for (int64_t ss = last_s + 1 + lane; ss < se; ss += 32) first[ss] = (int32_t)k_hi;
 }

@@ -126,6 +126,8 @@ struct TcArgs {
     int32_t kb_per_unit;  // MODE 0: k-steps over the neurons; MODE 1: k-steps per split
     int64_t kb_total;     // MODE 1: k-steps over the bins
     int64_t nsplit;       // MODE 1: number of interleaved splits
+    int64_t kb_half;      // MODE 1, 2: k-steps from kb_half on read the second B operand at kb - kb_half (the
+                          // two products S X_hi^T + S X_lo^T in one accumulator); 0: one B operand
     uint32_t idesc;
     double dt;
     const float* b;
@@ -344,9 +346,11 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                         tc::tma_load_3d(sa + 2 * C::A_BYTES + C::B_BYTES, mB1, 0, kx, w.n0 / 64, &full[stage]);
                     } else {
                         // (bin in block, neuron, bin block = k-step)
-                        tc::tma_load_3d(sa, mA0, 0, w.m0, (int32_t)kb, &full[stage]);
-                        if (C::NA == 2) tc::tma_load_3d(sa + C::A_BYTES, mA0, 0, w.m0 + 128, (int32_t)kb, &full[stage]);
-                        tc::tma_load_3d(sa + C::NA * C::A_BYTES, mB0, 0, w.n0, (int32_t)kb, &full[stage]);
+                        const bool second = A.kb_half > 0 && kb >= A.kb_half;
+                        const int32_t kbx = (int32_t)(second ? kb - A.kb_half : kb);
+                        tc::tma_load_3d(sa, mA0, 0, w.m0, kbx, &full[stage]);
+                        if (C::NA == 2) tc::tma_load_3d(sa + C::A_BYTES, mA0, 0, w.m0 + 128, kbx, &full[stage]);
+                        tc::tma_load_3d(sa + C::NA * C::A_BYTES, second ? mB1 : mB0, 0, w.n0, kbx, &full[stage]);
                     }
                     issued_phase[stage] = (int)phase;
                     if (++stage == C::STAGES) {
@@ -817,6 +821,7 @@ static TcArgs base_args(glm_ctx* c) {
     A.dt = P.dt;
     A.flags = c->buf.flags;
     A.limit_ns = 4000000000ull;  // 4 s per wait
+    A.kb_half = 0;
     A.idesc = tc::idesc_f16(P.prec == GLM_PREC_BF16 ? 1u : 0u, 128, BN);  // both operands K-major
     A.b = nullptr;
     A.eb = c->buf.eb;
@@ -907,27 +912,31 @@ static TcArgs grad_args(glm_ctx* c, int mode, int ns, int64_t kbt, bool ranged =
     return A;
 }
 
+// mapB2 (when given): a second B operand over the same kbt k-steps, summed into the same accumulators
 static cudaError_t run_products_as(glm_ctx* c, const CUtensorMap& mapB, int mode, int ns, int64_t kbt,
-                                   bool ranged = false) {
-    const TcArgs A = grad_args(c, mode, ns, kbt, ranged);
+                                   bool ranged = false, const CUtensorMap* mapB2 = nullptr) {
+    TcArgs A = grad_args(c, mode, ns, mapB2 ? 2 * kbt : kbt, ranged);
+    if (mapB2) A.kb_half = kbt;
+    const CUtensorMap& mB1 = mapB2 ? *mapB2 : mapB;
     const bool bf = c->pb.prec == GLM_PREC_BF16;
     if (mode == 2) {
-        if (bf) return run<2, __nv_bfloat16>(c, c->tmap[4], c->tmap[4], mapB, mapB, A);
-        return run<2, __half>(c, c->tmap[4], c->tmap[4], mapB, mapB, A);
+        if (bf) return run<2, __nv_bfloat16>(c, c->tmap[4], c->tmap[4], mapB, mB1, A);
+        return run<2, __half>(c, c->tmap[4], c->tmap[4], mapB, mB1, A);
     }
-    if (bf) return run<1, __nv_bfloat16>(c, c->tmap[4], c->tmap[4], mapB, mapB, A);
-    return run<1, __half>(c, c->tmap[4], c->tmap[4], mapB, mapB, A);
+    if (bf) return run<1, __nv_bfloat16>(c, c->tmap[4], c->tmap[4], mapB, mB1, A);
+    return run<1, __half>(c, c->tmap[4], c->tmap[4], mapB, mB1, A);
 }
 
 // E X^T (or S X^T) over the first t_len bins of the buffers (t_len < 0: the recording, or a whole chunk);
 // a short last chunk takes at most one split per k-step.
 // ranged: only the row tiles of the context's row range (the gradient); the spike term takes every row
-static cudaError_t run_products(glm_ctx* c, const CUtensorMap& mapB, int64_t t_len, int* ns_used, bool ranged = false) {
+static cudaError_t run_products(glm_ctx* c, const CUtensorMap& mapB, int64_t t_len, int* ns_used, bool ranged = false,
+                                const CUtensorMap* mapB2 = nullptr) {
     const int64_t kbt = t_len < 0 ? grad_ksteps(c) : (t_len + Cfg<1>::BK - 1) / Cfg<1>::BK;
     int ns = tc_nsplit(c);
     if (ns > kbt) ns = (int)kbt;
     if (ns_used) *ns_used = ns;
-    return run_products_as(c, mapB, c->g_mode, ns, kbt, ranged);
+    return run_products_as(c, mapB, c->g_mode, ns, kbt, ranged, mapB2);
 }
 
 cudaError_t launch_tc_grad(glm_ctx* c, int64_t t_len, int* nsplit_used) {
@@ -945,14 +954,13 @@ cudaError_t launch_tc_spike_term(glm_ctx* c) {
             return e;
         const bool raster = !(fused && (P.chunk || c->raster_in_E));
         if (raster && (e = launch_spike_raster(c, c->buf.E, t0 / SEG, (t0 + len) / SEG)) != cudaSuccess) return e;
-        c->launches += (P.chunk ? 1 : 0) + (raster ? 1 : 0) + 4;  // filter, raster, two products, two sums
+        c->launches += (P.chunk ? 1 : 0) + (raster ? 1 : 0) + 2;  // filter, raster, the products, the sum
         c->raster_in_E = false;  // consumed below; the next U product overwrites E
         int ns = 0;
         const int64_t bins = P.chunk ? len : P.T;
-        if ((e = run_products(c, c->tmap[5], bins, &ns)) != cudaSuccess) return e;
+        // S X_hi^T and S X_lo^T in one launch: each split runs over its bins of X_hi, then of X_lo
+        if ((e = run_products(c, c->tmap[5], bins, &ns, false, &c->tmap[6])) != cudaSuccess) return e;
         if ((e = launch_sum_splits(c, ns, c->buf.C, t0 > 0)) != cudaSuccess) return e;
-        if ((e = run_products(c, c->tmap[6], bins, &ns)) != cudaSuccess) return e;
-        if ((e = launch_sum_splits(c, ns, c->buf.C, true)) != cudaSuccess) return e;
     }
     return e;
 }
