@@ -225,19 +225,9 @@ struct FilterArgs {
     void* X;
     void* Xlo;  // 16-bit forms: X_lo
     const float* col_a;  // continuous-time columns: decay of each column
-    uint64_t* smask;     // 16-bit filter: also the spike raster as bit masks, [bin block of 64][n] (bit k: a
-                         // spike at bin 64 block + k), or null
+    void* S;             // 16-bit filter: also the spike raster (0 / 1), bin-blocked like X, or null
+    uint16_t one;        // the 16-bit word of 1
 };
-
-// The spike bits of lanes 8 m .. 8 m + 7 (lane l holds bins 8 l .. 8 l + 7 of a 256-bin segment) as the
-// 64-bit mask of the segment's 64-bin block m, in every lane of the group.
-__device__ __forceinline__ uint64_t block_mask(uint32_t bits, int lane) {
-    uint64_t m = (uint64_t)(bits & 0xFFu) << (8 * (lane & 7));
-    m |= __shfl_xor_sync(FULL, m, 1);
-    m |= __shfl_xor_sync(FULL, m, 2);
-    m |= __shfl_xor_sync(FULL, m, 4);
-    return m;
-}
 
 // F32 X, one warp per (8 rows, 4096-bin chunk).
 __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache_f32_kernel(const __grid_constant__ ScanConsts K,
@@ -345,15 +335,19 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache16_kernel(const __g
                 ph[p] = pack2<T16>(to_f<T16>(h0), to_f<T16>(h1));
                 pl[p] = pack2<T16>(v[2 * p] - to_f<T16>(h0), v[2 * p + 1] - to_f<T16>(h1));
             }
-            const int64_t tb = tl - A.s_begin * SEG;  // bin within the buffers
             if (r < A.n) {
+                const int64_t tb = tl - A.s_begin * SEG;  // bin within the buffers
                 const int64_t o = ((tb >> 6) * A.n + r) * 64 + (tb & 63);
                 *reinterpret_cast<uint4*>(Xh + o) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
                 *reinterpret_cast<uint4*>(Xl + o) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
-            }
-            if (A.smask) {  // the sources are the rows' own spikes: bits is also row r's raster here
-                const uint64_t m = block_mask(bits, lane);
-                if ((lane & 7) == 0 && r < A.n) A.smask[(tb >> 6) * A.n + r] = m;
+                if (A.S) {  // the sources are the rows' own spikes: bits is also row r's raster here
+                    uint32_t sw[4];
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+                        sw[p] = (((bits >> (2 * p)) & 1u) ? (uint32_t)A.one : 0u) |
+                                (((bits >> (2 * p + 1)) & 1u) ? ((uint32_t)A.one << 16) : 0u);
+                    *reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(A.S) + o) = make_uint4(sw[0], sw[1], sw[2], sw[3]);
+                }
             }
         }
     }
@@ -469,10 +463,11 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_range_kernel(const __gri
     }
 }
 
-// The spike raster S (1 at every spike, 0 elsewhere) of the tensor-core spike term C = S X^T, as 64-bit masks
-// [bin block of 64][n] (bit k: a spike at bin 64 block + k); the product expands them into its operand tiles.
-// One warp per (8 rows, 4096-bin unit); every block of the buffer is written once (no clearing pass).
-__global__ void __launch_bounds__(FW_WARPS * 32) spike_mask_kernel(const __grid_constant__ FilterArgs A) {
+// The spike raster S (1 at every spike, 0 elsewhere) in 16 bits, bin-blocked like X, for the tensor-core
+// spike term C = S X^T: one warp per (8 rows, 4096-bin unit), each lane writing its 8 bins of a row as one
+// 16-byte word, so every bin of the buffers is written once (no separate clearing pass).
+__global__ void __launch_bounds__(FW_WARPS * 32) spike_raster16_kernel(const __grid_constant__ FilterArgs A,
+                                                                       uint16_t one) {
     const int lane = threadIdx.x & 31;
     const int64_t wg = (int64_t)blockIdx.x * FW_WARPS + (threadIdx.x >> 5);
     const int64_t c = wg / A.ngroups;
@@ -480,6 +475,7 @@ __global__ void __launch_bounds__(FW_WARPS * 32) spike_mask_kernel(const __grid_
     if (c >= A.nchunks) return;
     const int64_t s0 = A.s_begin + c * CHUNK_SEGS;
     const int64_t s1 = min(s0 + (int64_t)CHUNK_SEGS, A.s_end);
+    uint16_t* S = reinterpret_cast<uint16_t*>(A.X);
 #pragma unroll 1
     for (int k = 0; k < 8; ++k) {
         const int32_t r = g * 8 + k;
@@ -488,14 +484,19 @@ __global__ void __launch_bounds__(FW_WARPS * 32) spike_mask_kernel(const __grid_
         const int64_t end = A.offs[r + 1];
         for (int64_t s = s0; s < s1; ++s) {
             const int64_t t0 = s * SEG;
-            const uint64_t m = block_mask(seg_bits(A.bins, cur, end, t0, lane), lane);
+            const uint32_t bits = seg_bits(A.bins, cur, end, t0, lane);
+            uint32_t w[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+                w[p] = (((bits >> (2 * p)) & 1u) ? (uint32_t)one : 0u) |
+                       (((bits >> (2 * p + 1)) & 1u) ? ((uint32_t)one << 16) : 0u);
             const int64_t tb = t0 + 8 * lane - A.s_begin * SEG;  // bin within the buffer
-            if ((lane & 7) == 0) A.smask[(tb >> 6) * A.n + r] = m;
+            *reinterpret_cast<uint4*>(S + ((tb >> 6) * A.n + r) * 64 + (tb & 63)) = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
 }
 
-cudaError_t launch_spike_mask(glm_ctx* c, uint64_t* out, int64_t s_begin, int64_t s_end) {
+cudaError_t launch_spike_raster(glm_ctx* c, void* out, int64_t s_begin, int64_t s_end) {
     const Problem& P = c->pb;
     FilterArgs A;
     A.n = P.n;
@@ -511,12 +512,13 @@ cudaError_t launch_spike_mask(glm_ctx* c, uint64_t* out, int64_t s_begin, int64_
     A.bins = c->buf.bins;
     A.seg_carry = c->buf.seg_carry;
     A.seg_first = c->buf.seg_first;
-    A.X = nullptr;
+    A.X = out;
     A.Xlo = nullptr;
     A.col_a = nullptr;
-    A.smask = out;
+    A.S = nullptr;
+    const uint16_t one = (P.prec == GLM_PREC_BF16) ? 0x3F80u : 0x3C00u;
     const int64_t warps = (int64_t)A.ngroups * A.nchunks;
-    spike_mask_kernel<<<(unsigned)((warps + FW_WARPS - 1) / FW_WARPS), FW_WARPS * 32, 0, c->stream>>>(A);
+    spike_raster16_kernel<<<(unsigned)((warps + FW_WARPS - 1) / FW_WARPS), FW_WARPS * 32, 0, c->stream>>>(A, one);
     return cudaGetLastError();
 }
 
@@ -583,7 +585,7 @@ cudaError_t launch_carry(glm_ctx* c) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_filter_cache(glm_ctx* c, int64_t s_begin, int64_t s_end, uint64_t* smask) {
+cudaError_t launch_filter_cache(glm_ctx* c, int64_t s_begin, int64_t s_end, void* raster) {
     const Problem& P = c->pb;
     FilterArgs A;
     A.n = P.n;
@@ -602,7 +604,8 @@ cudaError_t launch_filter_cache(glm_ctx* c, int64_t s_begin, int64_t s_end, uint
     A.X = c->buf.X;
     A.Xlo = c->buf.Xlo;
     A.col_a = c->buf.col_a;
-    A.smask = smask;
+    A.S = raster;
+    A.one = (P.prec == GLM_PREC_BF16) ? 0x3F80u : 0x3C00u;
     if (P.ct) {
         A.offs = c->buf.aoffs;
         A.bins = c->buf.abins;

@@ -323,7 +323,7 @@ int do_prepare(glm_ctx* c) {
     if (!P.chunk) {  // chunked: filtered per use
         // the 16-bit forms' spike term reads the raster from E: the filter writes it on the way
         const bool raster = P.prec != GLM_PREC_F32 && P.delay_bins <= 1;
-        GLM_RUN("filter_scan", 1, launch_filter_cache(c, 0, -1, raster ? static_cast<uint64_t*>(c->buf.E) : nullptr));
+        GLM_RUN("filter_scan", 1, launch_filter_cache(c, 0, -1, raster ? c->buf.E : nullptr));
         c->raster_in_E = raster;
     }
     // The spike term C (the W-independent part of dL/dW, Eq. 12): a gather of X at the spike bins for the

@@ -156,11 +156,11 @@ cudaError_t launch_carry(glm_ctx* c);
 cudaError_t launch_check_bins(glm_ctx* c, int32_t n, int64_t q, int64_t T, const int64_t* offs, const int32_t* bins,
                               unsigned long long* first_bad);
 // segments [s_begin, s_end) into the X buffers (whose first bin is SEG s_begin); s_end < 0: all
-// smask: also write the rows' spike raster there as 64-bit masks [bin block of 64][n]; only where the filter's
-// sources are the rows' own spikes (grid form, one-bin delay)
-cudaError_t launch_filter_cache(glm_ctx* c, int64_t s_begin = 0, int64_t s_end = -1, uint64_t* smask = nullptr);
-// the spike raster masks of segments [s_begin, s_end) into [bin block of 64][n], block 0 at bin SEG s_begin
-cudaError_t launch_spike_mask(glm_ctx* c, uint64_t* out, int64_t s_begin, int64_t s_end);
+// raster: also write the rows' spike raster (16-bit 0 / 1) there; only where the filter's sources are the
+// rows' own spikes (grid form, one-bin delay)
+cudaError_t launch_filter_cache(glm_ctx* c, int64_t s_begin = 0, int64_t s_end = -1, void* raster = nullptr);
+// the 16-bit spike raster of segments [s_begin, s_end) into a bin-blocked buffer starting at bin SEG s_begin
+cudaError_t launch_spike_raster(glm_ctx* c, void* out, int64_t s_begin, int64_t s_end);
 cudaError_t launch_filter_range(glm_ctx* c, int64_t t0, int64_t t_len, void* out, int64_t ldx, glm_dtype_t dtype);
 cudaError_t launch_spike_term(glm_ctx* c, double* out);
 cudaError_t launch_tau_rows(glm_ctx* c, double* rows);

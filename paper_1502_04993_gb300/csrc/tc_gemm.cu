@@ -10,10 +10,8 @@
 //                         (128-byte swizzle) per stage.  3 MMAs per 16-wide k slice, 2 TMEM accumulators
 //                         (epilogue overlaps the next tile).
 //   MODE 1, step a5:      P_s = E X^T over a split s of the bins (dL/dW = C - sum_s P_s, Eq. 12).  The same
-//                         kernel forms the spike term C = S X^T once per problem: S, the spike raster, in
-//                         the place of E, written into the stages by the epilogue warps from 64-bit masks
-//                         (one per neuron and 64 bins) instead of loaded; each split runs over its bins of
-//                         X_hi, then of X_lo, into one accumulator.  Tile 256 x 256 per block as two 128 x 256
+//                         kernel forms the spike term C = S X^T once per problem (S, the spike raster, in
+//                         the place of E; X_hi and X_lo in turn).  Tile 256 x 256 per block as two 128 x 256
 //                         accumulators that share every X tile (A0 = E rows m0.., A1 = E rows m0+128..),
 //                         K step 64 (128-byte swizzle), 3 stages, FP32 partials per split.
 //
@@ -32,7 +30,6 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
-#include <type_traits>
 #include <utility>
 #include <vector>
 #include <type_traits>
@@ -129,8 +126,6 @@ struct TcArgs {
     int32_t kb_per_unit;  // MODE 0: k-steps over the neurons; MODE 1: k-steps per split
     int64_t kb_total;     // MODE 1: k-steps over the bins
     int64_t nsplit;       // MODE 1: number of interleaved splits
-    const uint64_t* smask;  // MODE 1, 2: A is the spike raster, expanded in shared memory from these masks
-                            // [bin block of 64][n] by the epilogue warps (null: A loaded by TMA)
     int64_t kb_half;      // MODE 1, 2: k-steps from kb_half on read the second B operand at kb - kb_half (the
                           // two products S X_hi^T + S X_lo^T in one accumulator); 0: one B operand
     uint32_t idesc;
@@ -234,66 +229,6 @@ __device__ __forceinline__ uint32_t pack16<__half>(float lo, float hi) {
 // TAU (MODE 0 only): the epilogue also emits, per (row, tile), the partial sums that give dL/dtau.  With v = (W X)_i[t] = U_i[t] - b_i, Z_i[t] = a Z_i[t-1] + v[t-1] (Z = W dX/da), the
 // tile's local Z_loc starts at 0 at its first bin t0, and Z[t] = a^(t-t0) Z[t0] + Z_loc[t]; a per-row
 // combine (reduce.cu) chains the tiles.
-// The A operand of S X^T for one unit, written by the 4 epilogue warps instead of TMA: for every k-step, row t
-// of each 128-row half of the tile is the spike raster of neuron m0 + 128 h + t over the k-step's 64 bins,
-// expanded from its 64-bit mask into the layout TMA gives a K-major box with the 128-byte swizzle (row t at
-// 128 t, its 16-byte chunk c at chunk c ^ (t mod 8); bit k of the mask is element k).  The masks of the
-// next PF k-steps are in flight while a stage is written; each warp arrives on the stage's full barrier
-// after a proxy fence.  False when a wait gave up.
-template <typename C, typename T16>
-__device__ __forceinline__ bool expand_raster(const TcArgs& A, const Unit& w, uint8_t* smem, uint64_t* full,
-                                              uint64_t* empty, int& stage, uint32_t& phase, int warp, int lane,
-                                              volatile int* abort_flag) {
-    constexpr int PF = 4;
-    const uint32_t one = std::is_same<T16, __nv_bfloat16>::value ? 0x3F80u : 0x3C00u;  // 1 in T16
-    const int t = (warp - 2) * 32 + lane;
-    auto mask_at = [&](int64_t kb, int h) -> uint64_t {
-        if (kb >= w.kb1) return 0ull;
-        const int64_t kbx = (A.kb_half > 0 && kb >= A.kb_half) ? kb - A.kb_half : kb;
-        const int32_t r = w.m0 + 128 * h + t;
-        return r < A.n ? __ldg(A.smask + kbx * A.n + r) : 0ull;
-    };
-    uint64_t mk[PF][C::NA];
-#pragma unroll
-    for (int j = 0; j < PF; ++j)
-#pragma unroll
-        for (int h = 0; h < C::NA; ++h) mk[j][h] = mask_at(w.kb0 + j * w.kstep, h);
-    for (int64_t kb = w.kb0; kb < w.kb1; kb += w.kstep) {
-        uint64_t nx[C::NA];
-#pragma unroll
-        for (int h = 0; h < C::NA; ++h) nx[h] = mask_at(kb + PF * w.kstep, h);
-        if (!tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag, A.limit_ns)) return false;
-        uint8_t* sa = smem + stage * (C::NA * C::A_BYTES + C::NB * C::B_BYTES);  // Layout<MODE>::STAGE_BYTES
-#pragma unroll
-        for (int h = 0; h < C::NA; ++h) {
-            uint8_t* rowp = sa + h * C::A_BYTES + t * 128;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const uint32_t byte = (uint32_t)(mk[0][h] >> (8 * c)) & 0xFFu;
-                uint32_t v[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    v[e] = ((byte >> (2 * e)) & 1u) * one + ((byte >> (2 * e + 1)) & 1u) * (one << 16);
-                *reinterpret_cast<uint4*>(rowp + ((c ^ (t & 7)) << 4)) = make_uint4(v[0], v[1], v[2], v[3]);
-            }
-        }
-        tc::fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&full[stage]);
-#pragma unroll
-        for (int j = 0; j + 1 < PF; ++j)
-#pragma unroll
-            for (int h = 0; h < C::NA; ++h) mk[j][h] = mk[j + 1][h];
-#pragma unroll
-        for (int h = 0; h < C::NA; ++h) mk[PF - 1][h] = nx[h];
-        if (++stage == C::STAGES) {
-            stage = 0;
-            phase ^= 1;
-        }
-    }
-    return true;
-}
-
 template <int MODE, typename T16, bool TAU, bool BATCH, bool CT = false>
 __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
@@ -338,10 +273,8 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
         }
         s_ubeg[np] = acc_units;
         s_np = np;
-        // a raster expanded in shared memory: each of the epilogue warps also arrives on full[]
-        const uint32_t full_count = (MODE != 0 && !BATCH && Ag.smask) ? 1u + (uint32_t)epi_warps<MODE, CT>() : 1u;
         for (int s = 0; s < C::STAGES; ++s) {
-            tc::mbar_init(&full[s], full_count);
+            tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
         for (int a = 0; a < 2; ++a) {
@@ -403,8 +336,7 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                         break;
                     }
                     uint8_t* sa = smem + stage * L::STAGE_BYTES;
-                    const bool gen_a = MODE != 0 && !BATCH && A.smask;  // A written by the epilogue warps
-                    tc::mbar_arrive_expect_tx(&full[stage], gen_a ? C::NB * C::B_BYTES : L::STAGE_BYTES);
+                    tc::mbar_arrive_expect_tx(&full[stage], L::STAGE_BYTES);
                     const int32_t kx = (int32_t)(kb * C::BK);
                     if (MODE == 0) {
                         tc::tma_load_2d(sa, mA0, kx, w.m0, &full[stage]);
@@ -416,10 +348,8 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                         // (bin in block, neuron, bin block = k-step)
                         const bool second = A.kb_half > 0 && kb >= A.kb_half;
                         const int32_t kbx = (int32_t)(second ? kb - A.kb_half : kb);
-                        if (!gen_a) {
-                            tc::tma_load_3d(sa, mA0, 0, w.m0, kbx, &full[stage]);
-                            if (C::NA == 2) tc::tma_load_3d(sa + C::A_BYTES, mA0, 0, w.m0 + 128, kbx, &full[stage]);
-                        }
+                        tc::tma_load_3d(sa, mA0, 0, w.m0, kbx, &full[stage]);
+                        if (C::NA == 2) tc::tma_load_3d(sa + C::A_BYTES, mA0, 0, w.m0 + 128, kbx, &full[stage]);
                         tc::tma_load_3d(sa + C::NA * C::A_BYTES, second ? mB1 : mB0, 0, w.n0, kbx, &full[stage]);
                     }
                     issued_phase[stage] = (int)phase;
@@ -497,20 +427,12 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
         const int q = warp & 3;
         const int row = q * 32 + lane;
         int it = 0;
-        int gstage = 0;       // raster expansion: the producer's stage and phase sequence
-        uint32_t gphase = 0;
         for (int64_t u = blockIdx.x; u < total_units; u += gridDim.x, ++it) {
             const int p = prob_of(u);
             const TcArgs& A = args_of(p);
             const Unit w = decode<MODE>(A, u - s_ubeg[p], s_mt[p]);
             const int buf = (C::NBUF == 2) ? (it & 1) : 0;
             const uint32_t buf_phase = (uint32_t)((C::NBUF == 2 ? (it >> 1) : it) & 1);
-            if constexpr (MODE != 0 && !BATCH) {
-                if (A.smask && !expand_raster<C, T16>(A, w, smem, full, empty, gstage, gphase, warp, lane, abort_flag)) {
-                    raise();
-                    break;
-                }
-            }
             if (!tc::mbar_wait(&tfull[buf], buf_phase, abort_flag, Ag.limit_ns)) {
                 raise();
                 break;
@@ -900,7 +822,6 @@ static TcArgs base_args(glm_ctx* c) {
     A.flags = c->buf.flags;
     A.limit_ns = 4000000000ull;  // 4 s per wait
     A.kb_half = 0;
-    A.smask = nullptr;
     A.idesc = tc::idesc_f16(P.prec == GLM_PREC_BF16 ? 1u : 0u, 128, BN);  // both operands K-major
     A.b = nullptr;
     A.eb = c->buf.eb;
@@ -992,13 +913,10 @@ static TcArgs grad_args(glm_ctx* c, int mode, int ns, int64_t kbt, bool ranged =
 }
 
 // mapB2 (when given): a second B operand over the same kbt k-steps, summed into the same accumulators
-// smask (when given): A is the spike raster, expanded from these masks in shared memory
 static cudaError_t run_products_as(glm_ctx* c, const CUtensorMap& mapB, int mode, int ns, int64_t kbt,
-                                   bool ranged = false, const CUtensorMap* mapB2 = nullptr,
-                                   const uint64_t* smask = nullptr) {
+                                   bool ranged = false, const CUtensorMap* mapB2 = nullptr) {
     TcArgs A = grad_args(c, mode, ns, mapB2 ? 2 * kbt : kbt, ranged);
     if (mapB2) A.kb_half = kbt;
-    A.smask = smask;
     const CUtensorMap& mB1 = mapB2 ? *mapB2 : mapB;
     const bool bf = c->pb.prec == GLM_PREC_BF16;
     if (mode == 2) {
@@ -1013,12 +931,12 @@ static cudaError_t run_products_as(glm_ctx* c, const CUtensorMap& mapB, int mode
 // a short last chunk takes at most one split per k-step.
 // ranged: only the row tiles of the context's row range (the gradient); the spike term takes every row
 static cudaError_t run_products(glm_ctx* c, const CUtensorMap& mapB, int64_t t_len, int* ns_used, bool ranged = false,
-                                const CUtensorMap* mapB2 = nullptr, const uint64_t* smask = nullptr) {
+                                const CUtensorMap* mapB2 = nullptr) {
     const int64_t kbt = t_len < 0 ? grad_ksteps(c) : (t_len + Cfg<1>::BK - 1) / Cfg<1>::BK;
     int ns = tc_nsplit(c);
     if (ns > kbt) ns = (int)kbt;
     if (ns_used) *ns_used = ns;
-    return run_products_as(c, mapB, c->g_mode, ns, kbt, ranged, mapB2, smask);
+    return run_products_as(c, mapB, c->g_mode, ns, kbt, ranged, mapB2);
 }
 
 cudaError_t launch_tc_grad(glm_ctx* c, int64_t t_len, int* nsplit_used) {
@@ -1032,19 +950,16 @@ cudaError_t launch_tc_spike_term(glm_ctx* c) {
     for (int64_t t0 = 0; t0 < P.Tpad; t0 += P.Tc) {
         const int64_t len = std::min(P.Tc, P.Tpad - t0);
         const bool fused = P.delay_bins <= 1 && !P.ct;  // the filter's sources are the rows' own spikes
-        // the spike raster as 64-bit masks [bin block][n] in the E buffer (free until the first U product)
-        uint64_t* smask = static_cast<uint64_t*>(c->buf.E);
-        if (P.chunk && (e = launch_filter_cache(c, t0 / SEG, (t0 + len) / SEG, fused ? smask : nullptr)) != cudaSuccess)
+        if (P.chunk && (e = launch_filter_cache(c, t0 / SEG, (t0 + len) / SEG, fused ? c->buf.E : nullptr)) != cudaSuccess)
             return e;
         const bool raster = !(fused && (P.chunk || c->raster_in_E));
-        if (raster && (e = launch_spike_mask(c, smask, t0 / SEG, (t0 + len) / SEG)) != cudaSuccess) return e;
+        if (raster && (e = launch_spike_raster(c, c->buf.E, t0 / SEG, (t0 + len) / SEG)) != cudaSuccess) return e;
         c->launches += (P.chunk ? 1 : 0) + (raster ? 1 : 0) + 2;  // filter, raster, the products, the sum
         c->raster_in_E = false;  // consumed below; the next U product overwrites E
         int ns = 0;
         const int64_t bins = P.chunk ? len : P.T;
-        // S X_hi^T and S X_lo^T in one launch: each split runs over its bins of X_hi, then of X_lo; the epilogue
-        // warps expand S from the masks into the operand tiles
-        if ((e = run_products(c, c->tmap[5], bins, &ns, false, &c->tmap[6], smask)) != cudaSuccess) return e;
+        // S X_hi^T and S X_lo^T in one launch: each split runs over its bins of X_hi, then of X_lo
+        if ((e = run_products(c, c->tmap[5], bins, &ns, false, &c->tmap[6])) != cudaSuccess) return e;
         if ((e = launch_sum_splits(c, ns, c->buf.C, t0 > 0)) != cudaSuccess) return e;
     }
     return e;
