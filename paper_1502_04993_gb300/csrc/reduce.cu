@@ -61,52 +61,88 @@ __global__ void reduce_rows_kernel(const __grid_constant__ ReduceArgs A) {
     }
 }
 
-// sum over the splits p = 0 .. nsplit-1 of part_g[p nn + e], added in split order; the loads of 8 splits are
-// issued before their adds, so a thread keeps 8 reads in flight (the splits are tens to hundreds of MB)
-__device__ __forceinline__ double sum_parts(const float* __restrict__ part_g, int64_t nn, int64_t e, int nsplit) {
-    double s = 0.0;
-    int p = 0;
-    for (; p + 8 <= nsplit; p += 8) {
-        float v[8];
+// Sums over the splits p = 0 .. nsplit-1 of part_g[p nn + e], added in split order.  A thread takes 4
+// consecutive elements (one 16-byte load per split when nn is a multiple of 4, so every split plane starts
+// 16-byte aligned), and the loads of 4 splits are issued before their adds: a warp reads 512 contiguous bytes
+// of each plane and keeps 16 such reads in flight.
+constexpr int SPLIT_EPT = 4;
+
+__device__ __forceinline__ void sum_parts4(const float* __restrict__ part_g, int64_t nn, int64_t e0, int nsplit,
+                                           bool vec, double (&s)[SPLIT_EPT]) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = __ldcs(part_g + (int64_t)(p + u) * nn + e);
+    for (int i = 0; i < SPLIT_EPT; ++i) s[i] = 0.0;
+    if (vec) {
+        int p = 0;
+        for (; p + 4 <= nsplit; p += 4) {
+            float4 v[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) s += (double)v[u];
+            for (int u = 0; u < 4; ++u) v[u] = __ldcs(reinterpret_cast<const float4*>(part_g + (int64_t)(p + u) * nn + e0));
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                s[0] += (double)v[u].x;
+                s[1] += (double)v[u].y;
+                s[2] += (double)v[u].z;
+                s[3] += (double)v[u].w;
+            }
+        }
+        for (; p < nsplit; ++p) {
+            const float4 v = __ldcs(reinterpret_cast<const float4*>(part_g + (int64_t)p * nn + e0));
+            s[0] += (double)v.x;
+            s[1] += (double)v.y;
+            s[2] += (double)v.z;
+            s[3] += (double)v.w;
+        }
+        return;
     }
-    for (; p < nsplit; ++p) s += (double)__ldcs(part_g + (int64_t)p * nn + e);
-    return s;
+    for (int p = 0; p < nsplit; ++p)
+#pragma unroll
+        for (int i = 0; i < SPLIT_EPT; ++i)
+            if (e0 + i < nn) s[i] += (double)__ldcs(part_g + (int64_t)p * nn + e0 + i);
 }
 
 // G rows outside [e0, e1) (element range of a row range) are set to zero
 __global__ void reduce_grad_kernel(int64_t nn, int nsplit, const double* __restrict__ C,
                                    const float* __restrict__ part_g, const double* __restrict__ Gacc,
                                    double* __restrict__ G, int64_t e0, int64_t e1) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nn) return;
-    if (e < e0 || e >= e1) {
-        G[e] = 0.0;
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * SPLIT_EPT;
+    if (b >= nn) return;
+    const bool vec = (nn % SPLIT_EPT) == 0;
+    double s[SPLIT_EPT];
+    if (b + SPLIT_EPT <= e0 || b >= e1) {  // all outside the row range: no partial sums there
+#pragma unroll
+        for (int i = 0; i < SPLIT_EPT; ++i)
+            if (b + i < nn) G[b + i] = 0.0;
         return;
     }
-    double s = 0.0;
-    if (Gacc)
-        s = Gacc[e];
-    else
-        s = sum_parts(part_g, nn, e, nsplit);
-    G[e] = C[e] - s;
+    if (Gacc) {
+#pragma unroll
+        for (int i = 0; i < SPLIT_EPT; ++i) s[i] = (b + i < nn) ? Gacc[b + i] : 0.0;
+    } else {
+        sum_parts4(part_g, nn, b, nsplit, vec, s);
+    }
+#pragma unroll
+    for (int i = 0; i < SPLIT_EPT; ++i) {
+        const int64_t e = b + i;
+        if (e < nn) G[e] = (e < e0 || e >= e1) ? 0.0 : C[e] - s[i];
+    }
 }
 
 // C[e] (+)= sum over splits of part_g, in split order.
 __global__ void sum_splits_kernel(int64_t nn, int nsplit, const float* __restrict__ part_g, double* __restrict__ C,
                                   bool accumulate) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nn) return;
-    const double s = sum_parts(part_g, nn, e, nsplit);
-    C[e] = accumulate ? C[e] + s : s;
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * SPLIT_EPT;
+    if (b >= nn) return;
+    double s[SPLIT_EPT];
+    sum_parts4(part_g, nn, b, nsplit, (nn % SPLIT_EPT) == 0, s);
+#pragma unroll
+    for (int i = 0; i < SPLIT_EPT; ++i)
+        if (b + i < nn) C[b + i] = accumulate ? C[b + i] + s[i] : s[i];
 }
 
 cudaError_t launch_sum_splits(glm_ctx* c, int nsplit, double* C, bool accumulate) {
     const int64_t nn = (int64_t)c->pb.n * c->pb.n;
-    sum_splits_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(nn, nsplit, c->buf.part_g, C, accumulate);
+    const int64_t threads = (nn + SPLIT_EPT - 1) / SPLIT_EPT;
+    sum_splits_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(nn, nsplit, c->buf.part_g, C, accumulate);
     return cudaGetLastError();
 }
 
@@ -200,7 +236,8 @@ cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_
     reduce_rows_kernel<<<(P.n + 7) / 8, 256, 0, c->stream>>>(A);
     if (want_grad && G) {
         const int64_t nn = (int64_t)P.n * P.n;
-        reduce_grad_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(
+        const int64_t threads = (nn + SPLIT_EPT - 1) / SPLIT_EPT;
+        reduce_grad_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(
             nn, nsplit, A.C, c->buf.part_g, Gacc, G, (int64_t)A.r0 * P.n, (int64_t)A.r1 * P.n);
     }
     return cudaGetLastError();
