@@ -754,9 +754,15 @@ __global__ void fb_reduce_grad_kernel(const FitBatch* __restrict__ B, int64_t to
     if (e >= total) return;
     const int p = fb_prob64(B->ebeg, B->np, e);
     const int64_t el = e - B->ebeg[p], nn = B->ebeg[p + 1] - B->ebeg[p];
-    double sum = 0.0;
-    for (int k = 0; k < B->nsplit[p]; ++k) sum += (double)B->part_g[p][k * nn + el];
-    B->G[p][el] = B->C[p][el] - sum;
+    // FP32 pair summed with TwoSum, one FP64 value at the end (as reduce_grad_kernel: FP64 adds are scarce)
+    float hi = 0.f, lo = 0.f;
+    for (int k = 0; k < B->nsplit[p]; ++k) {
+        const float v = B->part_g[p][k * nn + el];
+        const float s = hi + v, bp = s - hi;
+        lo += (hi - (s - bp)) + (v - bp);
+        hi = s;
+    }
+    B->G[p][el] = B->C[p][el] - ((double)hi + (double)lo);
 }
 
 // rows still active in each problem (block per problem)

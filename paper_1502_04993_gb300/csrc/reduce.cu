@@ -61,16 +61,26 @@ __global__ void reduce_rows_kernel(const __grid_constant__ ReduceArgs A) {
     }
 }
 
-// Sums over the splits p = 0 .. nsplit-1 of part_g[p nn + e], added in split order.  A thread takes 4
-// consecutive elements (one 16-byte load per split when nn is a multiple of 4, so every split plane starts
-// 16-byte aligned), and the loads of 4 splits are issued before their adds: a warp reads 512 contiguous bytes
-// of each plane and keeps 16 such reads in flight.
+// Sums over the splits p = 0 .. nsplit-1 of part_g[p nn + e], added in split order.  The FP32 partials are
+// accumulated as an unevaluated FP32 pair hi + lo with TwoSum (Knuth: hi + err = hi_old + v exactly), which
+// keeps ~48 significant bits, and the pair becomes one FP64 value at the end: FP64 arithmetic is a scarce
+// pipe on this GPU, and summing the partials in FP64 made these kernels pipe-bound at a tenth of the memory
+// bandwidth.  A thread takes 4 consecutive elements (one 16-byte load per split when nn is a multiple of 4,
+// so every split plane starts 16-byte aligned), and the loads of 4 splits are issued before their adds.
 constexpr int SPLIT_EPT = 4;
 
+__device__ __forceinline__ void two_sum_f(float& hi, float& lo, float v) {
+    const float s = hi + v;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (v - bp);
+    hi = s;
+}
+
 __device__ __forceinline__ void sum_parts4(const float* __restrict__ part_g, int64_t nn, int64_t e0, int nsplit,
-                                           bool vec, double (&s)[SPLIT_EPT]) {
+                                           bool vec, double (&out)[SPLIT_EPT]) {
+    float hi[SPLIT_EPT], lo[SPLIT_EPT];
 #pragma unroll
-    for (int i = 0; i < SPLIT_EPT; ++i) s[i] = 0.0;
+    for (int i = 0; i < SPLIT_EPT; ++i) hi[i] = lo[i] = 0.f;
     if (vec) {
         int p = 0;
         for (; p + 4 <= nsplit; p += 4) {
@@ -79,25 +89,27 @@ __device__ __forceinline__ void sum_parts4(const float* __restrict__ part_g, int
             for (int u = 0; u < 4; ++u) v[u] = __ldcs(reinterpret_cast<const float4*>(part_g + (int64_t)(p + u) * nn + e0));
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                s[0] += (double)v[u].x;
-                s[1] += (double)v[u].y;
-                s[2] += (double)v[u].z;
-                s[3] += (double)v[u].w;
+                two_sum_f(hi[0], lo[0], v[u].x);
+                two_sum_f(hi[1], lo[1], v[u].y);
+                two_sum_f(hi[2], lo[2], v[u].z);
+                two_sum_f(hi[3], lo[3], v[u].w);
             }
         }
         for (; p < nsplit; ++p) {
             const float4 v = __ldcs(reinterpret_cast<const float4*>(part_g + (int64_t)p * nn + e0));
-            s[0] += (double)v.x;
-            s[1] += (double)v.y;
-            s[2] += (double)v.z;
-            s[3] += (double)v.w;
+            two_sum_f(hi[0], lo[0], v.x);
+            two_sum_f(hi[1], lo[1], v.y);
+            two_sum_f(hi[2], lo[2], v.z);
+            two_sum_f(hi[3], lo[3], v.w);
         }
-        return;
-    }
-    for (int p = 0; p < nsplit; ++p)
+    } else {
+        for (int p = 0; p < nsplit; ++p)
 #pragma unroll
-        for (int i = 0; i < SPLIT_EPT; ++i)
-            if (e0 + i < nn) s[i] += (double)__ldcs(part_g + (int64_t)p * nn + e0 + i);
+            for (int i = 0; i < SPLIT_EPT; ++i)
+                if (e0 + i < nn) two_sum_f(hi[i], lo[i], __ldcs(part_g + (int64_t)p * nn + e0 + i));
+    }
+#pragma unroll
+    for (int i = 0; i < SPLIT_EPT; ++i) out[i] = (double)hi[i] + (double)lo[i];
 }
 
 // G rows outside [e0, e1) (element range of a row range) are set to zero
