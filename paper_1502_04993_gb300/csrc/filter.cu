@@ -34,22 +34,27 @@ void fill_scan_consts(double a, ScanConsts* sc) {
 // Block per row: segment-first indices and, in seg_local (when given), the contribution of each segment's
 // own spikes to X at the next segment start: sum_{t in seg s} a^(256 (s+1) - 1 - t) on the grid; with
 // continuous-time columns (ctime given) sum exp(-(c_end - c_{t+1}) / tau), a source t arriving at column t+1.
+// The sums are double-float pairs; on the grid the powers a^k come from a shared table of pairs and are
+// added with TwoSum, so the grid path uses no FP64 arithmetic after the table.
 __global__ void seg_local_kernel(int32_t n, int64_t nseg, const int64_t* __restrict__ offs,
                                  const int32_t* __restrict__ bins, const double* __restrict__ pow_seg,
-                                 const double* __restrict__ ctime, double inv_tau, double* __restrict__ seg_local,
+                                 const double* __restrict__ ctime, double inv_tau, float2* __restrict__ seg_local,
                                  int32_t* __restrict__ seg_first) {
+    __shared__ float2 pw[SEG];
     const int32_t j = blockIdx.x;
     if (j >= n) return;
     const int64_t o0 = offs[j], q = offs[j + 1] - o0;
     const int32_t* b = bins + o0;
-    double* loc = seg_local ? seg_local + (int64_t)j * nseg : nullptr;
+    float2* loc = seg_local ? seg_local + (int64_t)j * nseg : nullptr;
     int32_t* first = seg_first + (int64_t)j * nseg;
     if (loc)
-        for (int64_t s = threadIdx.x; s < nseg; s += blockDim.x) loc[s] = 0.0;
+        for (int64_t s = threadIdx.x; s < nseg; s += blockDim.x) loc[s] = make_float2(0.f, 0.f);
     if (q == 0) {
         for (int64_t s = threadIdx.x; s < nseg; s += blockDim.x) first[s] = 0;
         return;
     }
+    if (pow_seg)
+        for (int k = threadIdx.x; k < SEG; k += blockDim.x) pw[k] = df_from(pow_seg[k]);
     __syncthreads();
     for (int64_t k = threadIdx.x; k < q; k += blockDim.x) {
         const int64_t s = b[k] / SEG;
@@ -57,11 +62,23 @@ __global__ void seg_local_kernel(int32_t n, int64_t nseg, const int64_t* __restr
         if (s != ps) {
             for (int64_t ss = ps + 1; ss <= s; ++ss) first[ss] = (int32_t)k;
             if (loc) {
-                double acc = 0.0;
                 const int64_t end = (s + 1) * SEG;
-                for (int64_t kk = k; kk < q && b[kk] < end; ++kk)
-                    acc += ctime ? exp(-(ctime[end] - ctime[b[kk] + 1]) * inv_tau) : pow_seg[end - 1 - b[kk]];
-                loc[s] = acc;
+                if (ctime) {
+                    double acc = 0.0;
+                    for (int64_t kk = k; kk < q && b[kk] < end; ++kk)
+                        acc += exp(-(ctime[end] - ctime[b[kk] + 1]) * inv_tau);
+                    loc[s] = df_from(acc);
+                } else {
+                    float h = 0.f, l = 0.f;
+                    for (int64_t kk = k; kk < q && b[kk] < end; ++kk) {
+                        const float2 v = pw[end - 1 - b[kk]];
+                        const float t = h + v.x, bp = t - h;
+                        l += ((h - (t - bp)) + (v.x - bp)) + v.y;
+                        h = t;
+                    }
+                    const float hh = h + l;
+                    loc[s] = make_float2(hh, l - (hh - h));
+                }
             }
         }
         if (k == q - 1)
@@ -74,44 +91,50 @@ __global__ void seg_local_kernel(int32_t n, int64_t nseg, const int64_t* __restr
 // CS segments, read and written with coalesced accesses: each thread composes the affine maps of its 8
 // consecutive segments (multiplier M, offset V), a block scan over the threads composes them in order,
 // and each thread then rewrites its segments from its carry-in.  The chunk's carry-out starts the next
-// chunk.  The order of the FP64 operations is fixed: the result is reproducible.
+// chunk.  All values are double-float pairs (~44 bits; the readers round the carries to FP32); the order of
+// the operations is fixed: the result is reproducible.
 constexpr int SC_T = 256, SC_E = 8, SC_CS = SC_T * SC_E;
 
-__device__ __forceinline__ int sc_pad(int k) { return k + (k >> 3); }  // one pad per 8 doubles: no bank conflicts
+__device__ __forceinline__ int sc_pad(int k) { return k + (k >> 3); }  // one pad per 8 pairs: no bank conflicts
+
+__device__ __forceinline__ float2 shfl_up_f2(float2 v, int d) {
+    return make_float2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
 
 __global__ void __launch_bounds__(SC_T) seg_carry_kernel(int32_t n, int64_t nseg, double a_seg,
-                                                         const double* __restrict__ mul_seg, double* __restrict__ seg) {
-    __shared__ double sl[SC_CS + SC_CS / 8], sa[SC_CS + SC_CS / 8];
-    __shared__ double wm[SC_T / 32], wv[SC_T / 32];
-    __shared__ double s_cin;
+                                                         const double* __restrict__ mul_seg, float2* __restrict__ seg) {
+    __shared__ float2 sl[SC_CS + SC_CS / 8], sa[SC_CS + SC_CS / 8];
+    __shared__ float2 wm[SC_T / 32], wv[SC_T / 32];
+    __shared__ float2 s_cin;
     const int32_t j = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (j >= n) return;
-    double* p = seg + (int64_t)j * nseg;
-    if (tid == 0) s_cin = 0.0;
+    float2* p = seg + (int64_t)j * nseg;
+    const float2 a2 = df_from(a_seg), one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
+    if (tid == 0) s_cin = zero;
     for (int64_t c0 = 0; c0 < nseg; c0 += SC_CS) {
         const int len = (int)min((int64_t)SC_CS, nseg - c0);
         __syncthreads();  // s_cin of the previous chunk is written; the buffers are free
         for (int k = tid; k < SC_CS; k += SC_T) {
-            sl[sc_pad(k)] = k < len ? p[c0 + k] : 0.0;
-            sa[sc_pad(k)] = k < len ? (mul_seg ? mul_seg[c0 + k] : a_seg) : 1.0;
+            sl[sc_pad(k)] = k < len ? p[c0 + k] : zero;
+            sa[sc_pad(k)] = k < len ? (mul_seg ? df_from(mul_seg[c0 + k]) : a2) : one;
         }
         __syncthreads();
         // this thread's map over segments [tid E, tid E + E)
-        double M = 1.0, V = 0.0;
+        float2 M = one, V = zero;
 #pragma unroll
         for (int e = 0; e < SC_E; ++e) {
             const int k = sc_pad(tid * SC_E + e);
-            V = fma(sa[k], V, sl[k]);
-            M *= sa[k];
+            V = df_fma(sa[k], V, sl[k]);
+            M = df_mul(M, sa[k]);
         }
         // inclusive scan of the maps over the threads: (M, V) after (M', V') is (M M', M V' + V)
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const double oM = __shfl_up_sync(0xffffffffu, M, d), oV = __shfl_up_sync(0xffffffffu, V, d);
+            const float2 oM = shfl_up_f2(M, d), oV = shfl_up_f2(V, d);
             if (lane >= d) {
-                V = fma(M, oV, V);
-                M *= oM;
+                V = df_fma(M, oV, V);
+                M = df_mul(M, oM);
             }
         }
         if (lane == 31) {
@@ -121,18 +144,18 @@ __global__ void __launch_bounds__(SC_T) seg_carry_kernel(int32_t n, int64_t nseg
         __syncthreads();
         // carry into this thread's first segment: chunk carry-in through the earlier warps, then the
         // earlier lanes of this warp
-        double cin = s_cin;
-        for (int w = 0; w < wid; ++w) cin = fma(wm[w], cin, wv[w]);
+        float2 cin = s_cin;
+        for (int w = 0; w < wid; ++w) cin = df_fma(wm[w], cin, wv[w]);
         {
-            double pM = __shfl_up_sync(0xffffffffu, M, 1), pV = __shfl_up_sync(0xffffffffu, V, 1);
-            if (lane > 0) cin = fma(pM, cin, pV);
+            const float2 pM = shfl_up_f2(M, 1), pV = shfl_up_f2(V, 1);
+            if (lane > 0) cin = df_fma(pM, cin, pV);
         }
 #pragma unroll
         for (int e = 0; e < SC_E; ++e) {
             const int k = sc_pad(tid * SC_E + e);
-            const double l = sl[k];
+            const float2 l = sl[k];
             sl[k] = cin;
-            cin = fma(sa[k], cin, l);
+            cin = df_fma(sa[k], cin, l);
         }
         if (tid == SC_T - 1) s_cin = cin;
         __syncthreads();
@@ -166,7 +189,7 @@ struct FilterArgs {
     int64_t s_begin, s_end;  // segments written; the buffers start at bin SEG s_begin
     const int64_t* offs;
     const int32_t* bins;
-    const double* seg_carry;
+    const float2* seg_carry;  // [n][nseg] X at each segment start, double-float pairs
     const int32_t* seg_first;
     void* X;
     void* Xlo;  // 16-bit forms: X_lo
@@ -192,7 +215,7 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache_f32_kernel(const _
     for (int k = 0; k < 8; ++k) {
         const int32_t r = g * 8 + k;
         if (r < A.n) {
-            xs[k] = (float)A.seg_carry[(int64_t)r * A.nseg + s0];
+            xs[k] = df_f(A.seg_carry[(int64_t)r * A.nseg + s0]);
             cur[k] = A.offs[r] + A.seg_first[(int64_t)r * A.nseg + s0];
             end[k] = A.offs[r + 1];
         } else {
@@ -254,7 +277,7 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache16_kernel(const __g
     for (int k = 0; k < RPW; ++k) {
         const int32_t r = g * RPW + k;
         if (r < A.n) {
-            xs[k] = (float)A.seg_carry[(int64_t)r * A.nseg + s0];
+            xs[k] = df_f(A.seg_carry[(int64_t)r * A.nseg + s0]);
             cur[k] = A.offs[r] + A.seg_first[(int64_t)r * A.nseg + s0];
             end[k] = A.offs[r + 1];
         } else {
@@ -316,7 +339,7 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache16_ct_kernel(const 
     for (int k = 0; k < 8; ++k) {
         const int32_t r = g * 8 + k;
         if (r < A.n) {
-            xs[k] = (float)A.seg_carry[(int64_t)r * A.nseg + s0];
+            xs[k] = df_f(A.seg_carry[(int64_t)r * A.nseg + s0]);
             cur[k] = A.offs[r] + A.seg_first[(int64_t)r * A.nseg + s0];
             end[k] = A.offs[r + 1];
         } else {
@@ -364,7 +387,7 @@ struct RangeArgs {
     int dtype;
     const int64_t* offs;
     const int32_t* bins;
-    const double* seg_carry;
+    const float2* seg_carry;  // [n][nseg] X at each segment start, double-float pairs
     const int32_t* seg_first;
     void* out;
 };
@@ -384,7 +407,7 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_range_kernel(const __gri
     for (int k = 0; k < 8; ++k) {
         const int32_t r = g * 8 + k;
         if (r >= A.n) break;
-        float xs = (float)A.seg_carry[(int64_t)r * A.nseg + s0];
+        float xs = df_f(A.seg_carry[(int64_t)r * A.nseg + s0]);
         int64_t cur = A.offs[r] + A.seg_first[(int64_t)r * A.nseg + s0];
         const int64_t end = A.offs[r + 1];
         for (int64_t s = s0; s < s1; ++s) {

@@ -61,7 +61,7 @@ struct Problem {
 struct Buffers {
     int64_t* offs = nullptr;      // [n+1]
     int32_t* bins = nullptr;      // [q]
-    double* seg_carry = nullptr;  // [n][nseg]   X_j[256 s]
+    float2* seg_carry = nullptr;  // [n][nseg]   X_j[256 s] as a double-float pair (hi, lo)
     int32_t* seg_first = nullptr; // [n][nseg]   first spike index (relative to offs[j]) at bin >= 256 s
     double* pow_seg = nullptr;    // [SEG + 1]   a^k, k = 0..SEG
     double* qd = nullptr;         // [n]         spike counts

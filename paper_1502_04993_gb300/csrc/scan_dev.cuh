@@ -11,6 +11,31 @@ namespace glm {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Double-float arithmetic: a value is an unevaluated FP32 pair (x = hi, y = lo), ~44-48 significant bits
+// (Dekker 1971; Knuth's TwoSum).  The segment carries use it instead of FP64, a scarce pipe on this GPU.
+__device__ __forceinline__ float2 df_from(double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    const float s = a.x + b.x;
+    const float bp = s - a.x;
+    float e = (a.x - (s - bp)) + (b.x - bp);  // a.x + b.x = s + e exactly
+    e += a.y + b.y;
+    const float h = s + e;
+    return make_float2(h, e - (h - s));
+}
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);  // a.x b.x = p + e exactly
+    e = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
+    const float h = p + e;
+    return make_float2(h, e - (h - p));
+}
+__device__ __forceinline__ float2 df_fma(float2 a, float2 x, float2 y) { return df_add(df_mul(a, x), y); }
+// the pair rounded to FP32
+__device__ __forceinline__ float df_f(float2 v) { return v.x + v.y; }
+
 // Split product (hi + lo) * x + add in FP32: the multiplier keeps ~48 significant bits.
 __device__ __forceinline__ float mul2(float hi, float lo, float x, float add) {
     return fmaf(hi, x, fmaf(lo, x, add));

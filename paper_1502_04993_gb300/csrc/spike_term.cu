@@ -81,7 +81,7 @@ struct SpikeTermArgs {
     int64_t segs_per_part;
     const int64_t* offs;
     const int32_t* bins;
-    const double* seg_carry;
+    const float2* seg_carry;  // double-float pairs
     const int32_t* seg_first;
     // the source trains scanned into X (the spikes, or the spikes shifted by a source delay)
     const int64_t* aoffs;
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(ST_THREADS, 1) spike_term_kernel(const __grid_
                 xs[k] = 0.f;
                 rc[k] = re[k] = 0;
                 if (r < A.n) {
-                    xs[k] = (float)A.seg_carry[(int64_t)r * A.nseg + s];
+                    xs[k] = df_f(A.seg_carry[(int64_t)r * A.nseg + s]);
                     rc[k] = A.aoffs[r] + A.aseg_first[(int64_t)r * A.nseg + s];
                     re[k] = A.aoffs[r + 1];
                 }
