@@ -31,59 +31,102 @@ void fill_scan_consts(double a, ScanConsts* sc) {
     for (int k = 0; k < 8; ++k) sc->pr[k] = (float)std::pow(a, (double)k);
 }
 
-// Block per row: segment-first indices and, in seg_local (when given), the contribution of each segment's
-// own spikes to X at the next segment start: sum_{t in seg s} a^(256 (s+1) - 1 - t) on the grid; with
-// continuous-time columns (ctime given) sum exp(-(c_end - c_{t+1}) / tau), a source t arriving at column t+1.
-// The sums are double-float pairs; on the grid the powers a^k come from a shared table of pairs and are
-// added with TwoSum, so the grid path uses no FP64 arithmetic after the table.
-__global__ void seg_local_kernel(int32_t n, int64_t nseg, const int64_t* __restrict__ offs,
+// Segment-first indices and, in seg_local (when given), the contribution of each segment's own spikes to X
+// at the next segment start: sum_{t in seg s} a^(256 (s+1) - 1 - t) on the grid; with continuous-time
+// columns (ctime given) sum exp(-(c_end - c_{t+1}) / tau), a source t arriving at column t+1.
+// Block per row, SL_W warps; warp w owns a contiguous range of segments and finds its spikes by a search in
+// the row's sorted bins.  It walks them 32 at a time (the loads of four such steps issued together): the spikes of one
+// segment are adjacent lanes, their terms are summed by a shuffle tree over the run, and a run that goes on
+// past the 32 lanes is carried to the next step (its partial sum first).  The sums are double-float pairs
+// (on the grid the powers a^k come from a shared table of pairs), and the order of the additions depends
+// only on the data: the result is reproducible.
+constexpr int SL_W = 8;
+
+// First k in [lo0, q) with b[k] >= x (q if none) in the sorted bins of a row, found by the whole warp: each
+// round probes 32 points that split the interval in 33 parts, so a row of 10^4 spikes takes 4 dependent
+// loads.  Every probe lies inside [lo, hi) and the interval shrinks every round.
+__device__ __forceinline__ int64_t warp_lower_bound(const int32_t* __restrict__ b, int64_t lo0, int64_t q, int64_t x,
+                                                    int lane) {
+    int64_t lo = lo0, hi = q;  // b[k] < x for k < lo, b[k] >= x for hi <= k < q
+    while (hi - lo > 32) {
+        const int64_t p = lo + (hi - lo) * (lane + 1) / 33;
+        const uint32_t below = __ballot_sync(FULL, (int64_t)__ldg(b + p) < x);
+        const int c = __popc(below);  // the lanes below x are a prefix
+        const int64_t plo = __shfl_sync(FULL, p, c > 0 ? c - 1 : 0);
+        const int64_t phi = __shfl_sync(FULL, p, c < 32 ? c : 31);
+        if (c > 0) lo = plo + 1;
+        if (c < 32) hi = phi;
+    }
+    const int64_t p = lo + lane;
+    return lo + __popc(__ballot_sync(FULL, p < hi && (int64_t)__ldg(b + p) < x));
+}
+
+__global__ void __launch_bounds__(SL_W * 32) seg_local_kernel(int32_t n, int64_t nseg, const int64_t* __restrict__ offs,
                                  const int32_t* __restrict__ bins, const double* __restrict__ pow_seg,
                                  const double* __restrict__ ctime, double inv_tau, float2* __restrict__ seg_local,
                                  int32_t* __restrict__ seg_first) {
     __shared__ float2 pw[SEG];
     const int32_t j = blockIdx.x;
     if (j >= n) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t o0 = offs[j], q = offs[j + 1] - o0;
     const int32_t* b = bins + o0;
     float2* loc = seg_local ? seg_local + (int64_t)j * nseg : nullptr;
     int32_t* first = seg_first + (int64_t)j * nseg;
-    if (loc)
-        for (int64_t s = threadIdx.x; s < nseg; s += blockDim.x) loc[s] = make_float2(0.f, 0.f);
-    if (q == 0) {
-        for (int64_t s = threadIdx.x; s < nseg; s += blockDim.x) first[s] = 0;
-        return;
-    }
     if (pow_seg)
         for (int k = threadIdx.x; k < SEG; k += blockDim.x) pw[k] = df_from(pow_seg[k]);
     __syncthreads();
-    for (int64_t k = threadIdx.x; k < q; k += blockDim.x) {
-        const int64_t s = b[k] / SEG;
-        const int64_t ps = (k > 0) ? (int64_t)(b[k - 1] / SEG) : -1;
-        if (s != ps) {
-            for (int64_t ss = ps + 1; ss <= s; ++ss) first[ss] = (int32_t)k;
+    const int64_t sb = nseg * warp / SL_W, se = nseg * (warp + 1) / SL_W;
+    if (sb >= se) return;
+    if (loc)
+        for (int64_t s = sb + lane; s < se; s += 32) loc[s] = make_float2(0.f, 0.f);
+    const int64_t k_lo = warp_lower_bound(b, 0, q, sb * SEG, lane);
+    const int64_t k_hi = warp_lower_bound(b, k_lo, q, se * SEG, lane);
+    __syncwarp();
+    int64_t last_s = sb - 1;   // segment of the previous spike of the range
+    int64_t open_s = -1;       // segment of the run still open at the end of the previous step
+    float2 open_acc = make_float2(0.f, 0.f);  // its partial sum
+    for (int64_t base0 = k_lo; base0 < k_hi; base0 += 4 * 32) {
+        int32_t pre[4];  // the bins of four steps, loaded together
+#pragma unroll
+        for (int u = 0; u < 4; ++u) pre[u] = (base0 + 32 * u + lane < k_hi) ? __ldg(b + base0 + 32 * u + lane) : 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t base = base0 + 32 * u;
+            if (base >= k_hi) break;
+            const int64_t k = base + lane;
+            const bool valid = k < k_hi;
+            const int64_t bk = valid ? (int64_t)pre[u] : 0;
+            const int64_t s = valid ? bk / SEG : INT64_MAX;
+            int64_t prev_s = __shfl_up_sync(FULL, s, 1);
+            if (lane == 0) prev_s = last_s;
+            const bool head = valid && s != prev_s;
+            if (head)
+                for (int64_t ss = prev_s + 1; ss <= s; ++ss) first[ss] = (int32_t)k;
+            const int last_lane = (k_hi - 1 - base < 31) ? (int)(k_hi - 1 - base) : 31;
             if (loc) {
-                const int64_t end = (s + 1) * SEG;
-                if (ctime) {
-                    double acc = 0.0;
-                    for (int64_t kk = k; kk < q && b[kk] < end; ++kk)
-                        acc += exp(-(ctime[end] - ctime[b[kk] + 1]) * inv_tau);
-                    loc[s] = df_from(acc);
-                } else {
-                    float h = 0.f, l = 0.f;
-                    for (int64_t kk = k; kk < q && b[kk] < end; ++kk) {
-                        const float2 v = pw[end - 1 - b[kk]];
-                        const float t = h + v.x, bp = t - h;
-                        l += ((h - (t - bp)) + (v.x - bp)) + v.y;
-                        h = t;
-                    }
-                    const float hh = h + l;
-                    loc[s] = make_float2(hh, l - (hh - h));
+                const int64_t end = valid ? (s + 1) * SEG : 0;
+                float2 v = make_float2(0.f, 0.f);
+                if (valid) v = ctime ? df_from(exp(-(ctime[end] - ctime[bk + 1]) * inv_tau)) : pw[end - 1 - bk];
+                const int32_t s32 = valid ? (int32_t)s : -1;  // segment index (< 2^23) for the shuffles
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {  // lane l: sum over [l, min(l + 2 off, end of its run))
+                    const float2 t = make_float2(__shfl_down_sync(FULL, v.x, off), __shfl_down_sync(FULL, v.y, off));
+                    const int32_t ts = __shfl_down_sync(FULL, s32, off);
+                    if (lane + off < 32 && ts == s32) v = df_add(v, t);
                 }
+                const bool lead = head || (lane == 0 && valid);  // first lane of a run in this step
+                if (lane == 0 && valid && s == open_s) v = df_add(open_acc, v);
+                if (lead) loc[s] = v;  // a run carried on to the next step is written again there
+                const uint32_t leads = __ballot_sync(FULL, lead) & (0xffffffffu >> (31 - last_lane));
+                const int hl = 31 - __clz(leads);
+                open_acc = make_float2(__shfl_sync(FULL, v.x, hl), __shfl_sync(FULL, v.y, hl));
+                open_s = __shfl_sync(FULL, s, hl);
             }
+            last_s = __shfl_sync(FULL, s, last_lane);
         }
-        if (k == q - 1)
-            for (int64_t ss = s + 1; ss < nseg; ++ss) first[ss] = (int32_t)q;
     }
+    for (int64_t ss = last_s + 1 + lane; ss < se; ss += 32) first[ss] = (int32_t)k_hi;
 }
 
 // Block per row, in place: seg_carry[s] <- X_j[256 s], with X_j[256 (s+1)] = A_s X_j[256 s] + local[s]
@@ -532,21 +575,21 @@ cudaError_t launch_carry(glm_ctx* c) {
     const Buffers& B = c->buf;
     if (P.ct) {
         // first spike per segment of the spike columns; carries of the arrival sources
-        seg_local_kernel<<<P.n, 256, 0, c->stream>>>(P.n, P.nseg, B.offs, B.bins, nullptr, nullptr, 0.0, nullptr,
+        seg_local_kernel<<<P.n, SL_W * 32, 0, c->stream>>>(P.n, P.nseg, B.offs, B.bins, nullptr, nullptr, 0.0, nullptr,
                                                      B.seg_first);
-        seg_local_kernel<<<P.n, 256, 0, c->stream>>>(P.n, P.nseg, B.aoffs, B.abins, nullptr, B.ctime, 1.0 / P.tau,
+        seg_local_kernel<<<P.n, SL_W * 32, 0, c->stream>>>(P.n, P.nseg, B.aoffs, B.abins, nullptr, B.ctime, 1.0 / P.tau,
                                                      B.seg_carry, B.aseg_first);
         seg_carry_kernel<<<P.n, SC_T, 0, c->stream>>>(P.n, P.nseg, 0.0, B.seg_mul, B.seg_carry);
         return cudaGetLastError();
     }
     if (P.delay_bins > 1) {
         // delayed sources: first spike per segment of the rows' own spikes; carries of the shifted trains
-        seg_local_kernel<<<P.n, 256, 0, c->stream>>>(P.n, P.nseg, B.offs, B.bins, nullptr, nullptr, 0.0, nullptr,
+        seg_local_kernel<<<P.n, SL_W * 32, 0, c->stream>>>(P.n, P.nseg, B.offs, B.bins, nullptr, nullptr, 0.0, nullptr,
                                                      B.seg_first);
-        seg_local_kernel<<<P.n, 256, 0, c->stream>>>(P.n, P.nseg, B.aoffs, B.abins, B.pow_seg, nullptr, 0.0,
+        seg_local_kernel<<<P.n, SL_W * 32, 0, c->stream>>>(P.n, P.nseg, B.aoffs, B.abins, B.pow_seg, nullptr, 0.0,
                                                      B.seg_carry, B.aseg_first);
     } else {
-        seg_local_kernel<<<P.n, 256, 0, c->stream>>>(P.n, P.nseg, B.offs, B.bins, B.pow_seg, nullptr, 0.0,
+        seg_local_kernel<<<P.n, SL_W * 32, 0, c->stream>>>(P.n, P.nseg, B.offs, B.bins, B.pow_seg, nullptr, 0.0,
                                                      B.seg_carry, B.seg_first);
     }
     const double a_seg = std::exp(-(double)SEG * P.dt / P.tau);
