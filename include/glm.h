@@ -61,7 +61,7 @@ extern "C" {
 #define GLM_ERR_TIMEOUT (-7)            /* a bounded device-side wait gave up */
 #define GLM_ERR_UNSUPPORTED_ARCH (-8)   /* a tensor-core precision was asked for on a GPU other than sm_103 */
 #define GLM_ERR_NO_PROBLEM (-9)         /* the call needs glm_set_problem() first */
-#define GLM_ERR_UNSUPPORTED (-10)       /* valid request outside what this build implements */
+#define GLM_ERR_UNSUPPORTED (-10)       /* valid request outside what the library implements */
 
 /* ---- precision of the contractions U = b + W X and G = R X^T ----
  * GLM_PREC_F32:  the plain FP32 form.  X and exp-rates stored in FP32,

@@ -100,7 +100,7 @@ SIGNATURES["glm_cross_validate"] = ([_vp, _vp, ctypes.POINTER(FitOpts), _vp, _i3
 SIGNATURES["glm_classify"] =([_vp, _i32, ctypes.POINTER(ClassifyOpts), _vp, _vp, _vp, ctypes.POINTER(ClassifyReport)],
                               ctypes.c_int)
 
-# precisions this build implements
+# precisions the library implements
 AVAILABLE_PRECISIONS = ("f32", "bf16", "f16")
 
 

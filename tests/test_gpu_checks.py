@@ -1,6 +1,6 @@
-"""Checks of the library itself (SURVEY's plan for race detection and failure detection, with the
-compute sanitizer closed): no kernel reads a value it did not write, and a bounded device-side wait gives
-up, reports it and leaves the context usable.
+"""Checks of the library itself, standing in for race detection and failure detection by a sanitizer: no
+kernel reads a value it did not write, and a bounded device-side wait gives up, reports it and leaves the
+context usable.
 
 * Poisoned caches: every recomputed buffer filled with NaN bytes, then glm_prepare and an evaluation give
   the results of a fresh context bit for bit (grid BF16 and FP32, the chunked form, continuous time, a
