@@ -224,6 +224,25 @@ __device__ __forceinline__ uint32_t pack2<__half>(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// X_hi and X_lo words of two adjacent values: one paired conversion each, the hi word kept as converted
+// (the same rounding as two separate conversions, in fewer instructions; the filter is issue-bound)
+template <typename T16>
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo);
+template <>
+__device__ __forceinline__ void split_pair<__nv_bfloat16>(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = pack2<__nv_bfloat16>(a - hf.x, b - hf.y);
+}
+template <>
+__device__ __forceinline__ void split_pair<__half>(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = pack2<__half>(a - hf.x, b - hf.y);
+}
+
 struct FilterArgs {
     int32_t n;
     int64_t T, nseg, Tpad, ldn;
@@ -289,20 +308,6 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache_f32_kernel(const _
 // [64 b, 64 b + 64) of row r at (b n + r) 64), the layout the tensor-core products read.  One warp per
 // (RPW rows, 4096-bin chunk): each lane stores its 8 bins of a row as one 16-byte word of X_hi and one of
 // X_lo, so every warp store covers four whole 128-byte lines.
-template <typename T16>
-__device__ __forceinline__ float to_f(T16 v);
-template <>
-__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-template <>
-__device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
-
-template <typename T16>
-__device__ __forceinline__ T16 from_f(float v);
-template <>
-__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
-template <>
-__device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
-
 template <typename T16, int RPW>
 __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache16_kernel(const __grid_constant__ ScanConsts K,
                                                                        const __grid_constant__ FilterArgs A) {
@@ -342,11 +347,7 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache16_kernel(const __g
             xs[k] = seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v);
             uint32_t ph[4], pl[4];
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                const T16 h0 = from_f<T16>(v[2 * p]), h1 = from_f<T16>(v[2 * p + 1]);
-                ph[p] = pack2<T16>(to_f<T16>(h0), to_f<T16>(h1));
-                pl[p] = pack2<T16>(v[2 * p] - to_f<T16>(h0), v[2 * p + 1] - to_f<T16>(h1));
-            }
+            for (int p = 0; p < 4; ++p) split_pair<T16>(v[2 * p], v[2 * p + 1], ph[p], pl[p]);
             if (r < A.n) {
                 const int64_t tb = tl - A.s_begin * SEG;  // bin within the buffers
                 const int64_t o = ((tb >> 6) * A.n + r) * 64 + (tb & 63);
@@ -406,11 +407,7 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache16_ct_kernel(const 
             xs[k] = seg_scan_ct(S, xs[k], bits, lane, v);
             uint32_t ph[4], pl[4];
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                const T16 h0 = from_f<T16>(v[2 * p]), h1 = from_f<T16>(v[2 * p + 1]);
-                ph[p] = pack2<T16>(to_f<T16>(h0), to_f<T16>(h1));
-                pl[p] = pack2<T16>(v[2 * p] - to_f<T16>(h0), v[2 * p + 1] - to_f<T16>(h1));
-            }
+            for (int p = 0; p < 4; ++p) split_pair<T16>(v[2 * p], v[2 * p + 1], ph[p], pl[p]);
             if (r < A.n) {
                 const int64_t tb = tl - A.s_begin * SEG;
                 const int64_t o = ((tb >> 6) * A.n + r) * 64 + (tb & 63);
