@@ -6,7 +6,10 @@ One step = the whole hot path once: filter scan and spike term from the device-r
 (steps a0-a2), then U = b + W X with the fused link epilogue, the gradient product and the FP64
 reductions (a3-a5, a7).  `value` times K such steps with the inputs already in HBM; `e2e` times the
 same through the public API from host buffers (spike upload and validation, W/b upload, L and G read
-back).  Prints one JSON line (rank 0).
+back).  After the timed steps, untimed legs add to the same line: the full fit in BF16 and in the plain
+FP32 form (wall time, iterations, misclassification rate, speed-up over FP32), the continuous-time
+form on the first 180 s, the recording as four row classes with their own tau and delay, and the FP64
+oracle on a bounded sample of the host cores.  Prints one JSON line (rank 0).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--prec f32|bf16|f16] [--impl ours|reference]
 """
