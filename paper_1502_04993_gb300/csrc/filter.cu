@@ -1,13 +1,14 @@
 // Step a0/a1: spike ingest and the filter scan X_j[t] = a X_j[t-1] + S_j[t-1] (Eq. 13 on the grid; the
 // exponential kernel h(t) = H(t) exp(-t/tau) of Sec. 2.2 with a one-bin delay).
 //
-//   carry pass  (FP64, O(q + n * nseg)):  per row and 256-bin segment, X at the segment start and the
+//   carry pass  (double-float, O(q + n * nseg)):  per row and 256-bin segment, X at the segment start and the
 //               index of the first spike in or after the segment.
-//   write pass  (FP32 scan, HBM-write bound):  the segments of a 4096-bin chunk are scanned in order,
-//               starting from the FP64 carry, and stored as
+//   write pass  (FP32 scan; writes at ~80 % of the copy bandwidth, bound by instruction issue):  the
+//               segments of a 4096-bin chunk are scanned in order, starting from the carry (rounded to
+//               FP32), and stored as
 //                 F32:    X row-major [n][Tpad]
-//                 16-bit: X_hi row-major [n][Tpad] (operand of E X^T) and X_hi^T, X_lo^T [Tpad][ldn]
-//                         (K-major operands of U = W X; X_lo = X - X_hi rounded once more)
+//                 16-bit: X_hi and X_lo = X - X_hi rounded once more, both bin-blocked [Tpad / 64][n][64],
+//                         the layout both tensor-core products read (and, on the grid, the spike raster)
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(SC_T) seg_carry_kernel(int32_t n, int64_t nseg
 }
 
 constexpr int CHUNK_SEGS = 16;  // 4096 bins per warp unit: X is chained in FP32 within a unit and restarted
-                                // from the FP64 carry at every unit start (chunks of X start on unit bounds)
+                                // from the segment carry at every unit start (chunks of X start on unit bounds)
 constexpr int FW_WARPS = 4;
 constexpr int FW16_RPW = 4;  // rows per warp of the 16-bit filter
 

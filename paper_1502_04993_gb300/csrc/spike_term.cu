@@ -9,7 +9,7 @@
 //            (up to 24 per row) into shared memory, laid out [spike][row slot][thread] so that the later
 //            reads of a warp are conflict-free;
 //   phase A  meanwhile the warps scan X_j for the 16 rows into shared memory (warp = one 256-bin segment x
-//            4 rows, started from the FP64 segment carries);
+//            4 rows, started from the segment carries);
 //   phase B  every thread walks the staged spikes of its rows and accumulates X_j[t] for the 16 rows (spikes
 //            beyond the staged 24 are read from global memory).
 // Each row's spikes in a sub-chunk are summed in plain FP32, and these partial sums enter an FP32 hi + lo
