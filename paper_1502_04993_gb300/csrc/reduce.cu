@@ -1,4 +1,5 @@
-// Step a7: FP64 reductions in a fixed order (bitwise reproducible).
+// Step a7: reductions in a fixed order (bitwise reproducible): the per-tile sums in FP64, the FP32 partials of
+// the split products as FP32 TwoSum pairs (~48 bits) converted once to FP64.
 //   L_i   = sum_{t in sp(i)} U_i[t] - dt sum_t exp(U_i[t])        (Eq. 7), the spike part as
 //           q_i b_i + sum over tiles of (sum of U - b at the row's spike bins), from the U-product epilogue
 //   dL/db_i = q_i - dt sum_t exp(U_i[t])                         (Eq. 12, j = 0)
