@@ -1,5 +1,7 @@
-"""Host-side helpers that need no GPU: splitting a recording for cross-validation."""
+"""Host-side logic that needs no GPU: splitting a recording for cross-validation, the generator's ground-truth
+labels, and the double-float arithmetic of the segment carries."""
 import numpy as np
+import pytest
 
 import synth
 
@@ -36,3 +38,53 @@ def test_synth_truth_labels_match_the_oracle_definition():
     W = rng.choice([-1.2, 0.0, 0.3], size=(37, 37), p=[0.1, 0.8, 0.1])
     np.fill_diagonal(W, -3.0)
     assert np.array_equal(synth.truth_labels(W), truth_labels(W))
+
+
+def _df_add(a, b):
+    """Double-float sum of FP32 pairs, the steps of df_add in the CUDA scan header (TwoSum, then a renormalising
+    fast two-sum), evaluated in numpy float32."""
+    f = np.float32
+    s = f(a[0] + b[0])
+    bp = f(s - a[0])
+    e = f(f(a[0] - f(s - bp)) + f(b[0] - bp))
+    e = f(e + f(a[1] + b[1]))
+    h = f(s + e)
+    return (h, f(e - f(h - s)))
+
+
+def _df_mul(a, b):
+    """Double-float product (Dekker): the exact error of the FP32 product by an FMA, evaluated exactly in FP64
+    and rounded once, as fmaf does."""
+    f = np.float32
+    p = f(a[0] * b[0])
+    e = f(float(a[0]) * float(b[0]) - float(p))          # fmaf(a.x, b.x, -p): exact product minus p, rounded
+    e = f(float(a[1]) * float(b[0]) + float(e))          # fmaf(a.y, b.x, e)
+    e = f(float(a[0]) * float(b[1]) + float(e))          # fmaf(a.x, b.y, ...)
+    h = f(p + e)
+    return (h, f(e - f(h - p)))
+
+
+def _df(v):
+    h = np.float32(v)
+    return (h, np.float32(v - float(h)))
+
+
+@pytest.mark.parametrize("tau_over_dt", [10.0, 1000.0, 100000.0])
+def test_double_float_segment_carries_track_fp64(tau_over_dt):
+    """The segment carries X[256 (s+1)] = A X[256 s] + local[s] run in double-float pairs on the device; over a
+    few thousand segments, even with A close to 1 (tau of 10^5 bins, where errors accumulate), the pair stays
+    within a small multiple of 2^-44 of the FP64 recursion (relative, for values in FP32's normal range), far
+    below the FP32 rounding its readers apply."""
+    rng = np.random.default_rng(1)
+    a_seg = np.exp(-256.0 / tau_over_dt)
+    A = _df(a_seg)
+    x64, x = 0.0, (np.float32(0), np.float32(0))
+    worst = 0.0
+    for s in range(3000):
+        loc = float(rng.exponential(1.0)) * float(rng.random() < 0.9)
+        x64 = a_seg * x64 + loc
+        x = _df_add(_df_mul(A, x), _df(loc))
+        # relative to the value, above FP32's normal range (a run of empty segments with a tiny A takes the pair
+        # into FP32's subnormals, where it keeps an absolute accuracy of ~1e-45 that no reader can see)
+        worst = max(worst, abs((float(x[0]) + float(x[1])) - x64) / (x64 + 2.0 ** -100))
+    assert worst < 2.0 ** -40, worst
