@@ -62,11 +62,12 @@ def kmeans1d(x: np.ndarray, max_iter: int = 1000):
     return c[order], rank[assign]
 
 
-def gmm1d(x: np.ndarray, max_iter: int = 1000, tol: float = 1e-12, var_floor: float = 1e-12):
+def gmm1d(x: np.ndarray, max_iter: int = 1000, tol: float = 1e-12, var_floor: float = 1e-12, trace=None):
     """3-component 1-D Gaussian mixture by EM, initialised from k-means.
 
     Returns (weights, means, variances) sorted by mean, the posterior-argmax assignment and the final
-    mixture log-likelihood."""
+    mixture log-likelihood.  ``trace``, when a list, receives the mixture log-likelihood of every EM
+    iterate (each before its M step)."""
     x = np.asarray(x, dtype=np.float64).ravel()
     c, a = kmeans1d(x)
     pi = np.array([(a == k).mean() for k in range(3)])
@@ -83,6 +84,8 @@ def gmm1d(x: np.ndarray, max_iter: int = 1000, tol: float = 1e-12, var_floor: fl
         mx = logp.max(axis=1, keepdims=True)
         lse = mx[:, 0] + np.log(np.exp(logp - mx).sum(axis=1))
         ll = lse.sum()
+        if trace is not None:
+            trace.append(float(ll))
         resp = np.exp(logp - lse[:, None])
         # M step
         nk = resp.sum(axis=0)
@@ -94,13 +97,18 @@ def gmm1d(x: np.ndarray, max_iter: int = 1000, tol: float = 1e-12, var_floor: fl
         prev = ll
     order = np.argsort(mu, kind="stable")
     pi, mu, var = pi[order], mu[order], var[order]
+    return (pi, mu, var), gmm_assign(x, pi, mu, var), ll
+
+
+def gmm_assign(x: np.ndarray, pi: np.ndarray, mu: np.ndarray, var: np.ndarray) -> np.ndarray:
+    """Component of largest posterior for each point; a tie goes to the component whose mean is nearer 0."""
+    x = np.asarray(x, dtype=np.float64).ravel()
     logp = (np.log(pi)[None, :] - 0.5 * np.log(2 * math.pi * var)[None, :]
             - 0.5 * (x[:, None] - mu[None, :]) ** 2 / var[None, :])
     best = logp.max(axis=1, keepdims=True)
     tie = logp == best
     pref = np.where(tie, np.abs(mu)[None, :], np.inf)
-    assign = pref.argmin(axis=1)
-    return (pi, mu, var), assign, ll
+    return pref.argmin(axis=1)
 
 
 def classify(W: np.ndarray, method: str = "gmm"):
