@@ -405,8 +405,15 @@ int glm_classify(const double* W_host, int32_t n, const glm_classify_opts_t* opt
  * The paper has no counterpart to this call; it exists for callers that may not allocate device memory:
  * processes whose device memory belongs to another allocator (a framework's caching pool, a pre-reserved
  * arena) and loops that must not call cudaMalloc after start-up.  It needs no context and allocates
- * nothing: its temporary storage is one fixed array of GLM_NOALLOC_SCRATCH_BYTES in device memory, part
- * of the library image, which every GPU that loads the library holds until the process exits.
+ * nothing itself: its temporary storage is one fixed array of GLM_NOALLOC_SCRATCH_BYTES in device memory,
+ * part of the library's device code, which a GPU holds from the moment that code is loaded on it until the
+ * process exits.  With CUDA's default lazy module loading that moment is the first call of this function
+ * on the device (not the loading of the library): the first call commits the 16 MiB and fails with
+ * GLM_ERR_CUDA if the device has no room left.  Make that first call at start-up, before another allocator
+ * reserves the device's memory, or run the process with CUDA_MODULE_LOADING=EAGER; later calls commit
+ * nothing.  The array's device address is looked up on that first call and kept for the process: it stays
+ * valid for the life of the device's primary context (after cudaDeviceReset, do not call this function
+ * again in the same process).
  *
  * Computes the per-row log-likelihood of the plain FP32 form (the same quantity as glm_loglik_grad's
  * L_rows for a GLM_PREC_F32 problem) from caller buffers, all device pointers on the current device:
