@@ -3,9 +3,9 @@
 //
 //   carry pass  (double-float, O(q + n * nseg)):  per row and 256-bin segment, X at the segment start and the
 //               index of the first spike in or after the segment.
-//   write pass  (FP32 scan; writes at ~80 % of the copy bandwidth, bound by instruction issue):  the
-//               segments of a 4096-bin chunk are scanned in order, starting from the carry (rounded to
-//               FP32), and stored as
+//   write pass  (FP32 scan for the 16-bit forms, writing at ~80 % of the copy bandwidth, bound by
+//               instruction issue; double-float scan for the FP32 form):  the segments of a 4096-bin chunk
+//               are scanned in order, starting from the carry, and stored as
 //                 F32:    X row-major [n][Tpad]
 //                 16-bit: X_hi and X_lo = X - X_hi rounded once more, both bin-blocked [Tpad / 64][n][64],
 //                         the layout both tensor-core products read (and, on the grid, the spike raster)
@@ -261,7 +261,10 @@ struct FilterArgs {
     uint16_t one;        // the 16-bit word of 1
 };
 
-// F32 X, one warp per (8 rows, 4096-bin chunk).
+// F32 X, one warp per (8 rows, 4096-bin chunk).  The scan runs in double-float and each stored value is
+// rounded once from it: the stored X is the correctly rounded X (the plain FP32 form's L needs X free of
+// systematic rounding to reach ~1e-9 relative).  The filter runs once per problem, so the extra arithmetic
+// does not recur in the fit.
 __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache_f32_kernel(const __grid_constant__ ScanConsts K,
                                                                          const __grid_constant__ FilterArgs A) {
     const int lane = threadIdx.x & 31;
@@ -269,38 +272,23 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache_f32_kernel(const _
     const int64_t c = wg / A.ngroups;
     const int32_t g = (int32_t)(wg % A.ngroups);
     if (c >= A.nchunks) return;
-    const float pl_hi = K.pl_hi[lane], pl_lo = K.pl_lo[lane];
+    const float2 pl = make_float2(K.pl_hi[lane], K.pl_lo[lane]);
     const int64_t s0 = A.s_begin + c * CHUNK_SEGS;
     const int64_t s1 = min(s0 + (int64_t)CHUNK_SEGS, A.s_end);
-    float xs[8];
-    int64_t cur[8], end[8];
-#pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int32_t r = g * 8 + k;
-        if (r < A.n) {
-            xs[k] = df_f(A.seg_carry[(int64_t)r * A.nseg + s0]);
-            cur[k] = A.offs[r] + A.seg_first[(int64_t)r * A.nseg + s0];
-            end[k] = A.offs[r + 1];
-        } else {
-            xs[k] = 0.f;
-            cur[k] = 0;
-            end[k] = 0;
-        }
-    }
-    for (int64_t s = s0; s < s1; ++s) {
-        const int64_t t0 = s * SEG;
-        const int64_t tl = t0 + 8 * lane;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int32_t r = g * 8 + k;
-            const uint32_t bits = seg_bits(A.bins, cur[k], end[k], t0, lane);
-            float v[8];
-            xs[k] = seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v);
-            if (r < A.n) {
-                float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(A.X) + (int64_t)r * A.Tpad + tl);
-                dst[0] = make_float4(v[0], v[1], v[2], v[3]);
-                dst[1] = make_float4(v[4], v[5], v[6], v[7]);
-            }
+        if (r >= A.n) break;
+        float2 xs = A.seg_carry[(int64_t)r * A.nseg + s0];
+        int64_t cur = A.offs[r] + A.seg_first[(int64_t)r * A.nseg + s0];
+        const int64_t end = A.offs[r + 1];
+        for (int64_t s = s0; s < s1; ++s) {
+            const int64_t t0 = s * SEG;
+            const uint32_t bits = seg_bits(A.bins, cur, end, t0, lane);
+            float2 v[8];
+            xs = seg_scan_df(K, xs, bits, pl, lane, v);
+            float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(A.X) + (int64_t)r * A.Tpad + t0 + 8 * lane);
+            dst[0] = make_float4(df_f(v[0]), df_f(v[1]), df_f(v[2]), df_f(v[3]));
+            dst[1] = make_float4(df_f(v[4]), df_f(v[5]), df_f(v[6]), df_f(v[7]));
         }
     }
 }
@@ -441,33 +429,34 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_range_kernel(const __gri
     const int64_t c = wg / A.ngroups;
     const int32_t g = (int32_t)(wg % A.ngroups);
     if (c >= A.nchunks) return;
-    const float pl_hi = K.pl_hi[lane], pl_lo = K.pl_lo[lane];
+    const float2 pl = make_float2(K.pl_hi[lane], K.pl_lo[lane]);
     const int64_t s0 = A.s_begin + c * CHUNK_SEGS;
     const int64_t s1 = min(s0 + (int64_t)CHUNK_SEGS, A.nseg);
     const int64_t te = A.t0 + A.t_len;
     for (int k = 0; k < 8; ++k) {
         const int32_t r = g * 8 + k;
         if (r >= A.n) break;
-        float xs = df_f(A.seg_carry[(int64_t)r * A.nseg + s0]);
+        float2 xs = A.seg_carry[(int64_t)r * A.nseg + s0];
         int64_t cur = A.offs[r] + A.seg_first[(int64_t)r * A.nseg + s0];
         const int64_t end = A.offs[r + 1];
         for (int64_t s = s0; s < s1; ++s) {
             const int64_t t0 = s * SEG;
             if (t0 >= te) break;
             const uint32_t bits = seg_bits(A.bins, cur, end, t0, lane);
-            float v[8];
-            xs = seg_scan(K, xs, bits, pl_hi, pl_lo, lane, v);
+            float2 v[8];
+            xs = seg_scan_df(K, xs, bits, pl, lane, v);  // as the FP32 cache: X rounded once
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
                 const int64_t t = t0 + 8 * lane + m;
                 if (t < A.t0 || t >= te) continue;
                 const int64_t o = (int64_t)r * A.ldx + (t - A.t0);
+                const float x = df_f(v[m]);
                 if (A.dtype == GLM_DTYPE_F32)
-                    reinterpret_cast<float*>(A.out)[o] = v[m];
+                    reinterpret_cast<float*>(A.out)[o] = x;
                 else if (A.dtype == GLM_DTYPE_BF16)
-                    reinterpret_cast<__nv_bfloat16*>(A.out)[o] = __float2bfloat16_rn(v[m]);
+                    reinterpret_cast<__nv_bfloat16*>(A.out)[o] = __float2bfloat16_rn(x);
                 else
-                    reinterpret_cast<__half*>(A.out)[o] = __float2half_rn(v[m]);
+                    reinterpret_cast<__half*>(A.out)[o] = __float2half_rn(x);
             }
         }
     }

@@ -104,6 +104,38 @@ __device__ __forceinline__ float seg_scan(const ScanConsts& K, float x_seg, uint
     return __shfl_sync(FULL, xend, 31);
 }
 
+__device__ __forceinline__ float2 shfl_up_df(float2 v, int d) {
+    return make_float2(__shfl_up_sync(FULL, v.x, d), __shfl_up_sync(FULL, v.y, d));
+}
+
+// seg_scan in double-float arithmetic (~44 significant bits, every multiplier a hi + lo pair): out[m] and
+// the result carry X to well below FP32 resolution, so the plain FP32 form rounds each stored value once
+// from it (correctly rounded X: no rounding error from the scan itself, whose systematic part, repeated
+// after every spike of a train, would otherwise reach ~1e-10 of L).  Same structure as seg_scan; the
+// lane's local sums follow the recursion z_{m+1} = a z_m + S_m, whose double-float roundings are
+// ~2^-44 and so negligible.
+__device__ __forceinline__ float2 seg_scan_df(const ScanConsts& K, float2 x_seg, uint32_t bits8, float2 pl, int lane,
+                                              float2 out[8]) {
+    const float2 A = make_float2(K.a_hi, K.a_lo);
+    float2 z[9];
+    z[0] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) z[m + 1] = df_add(df_mul(A, z[m]), make_float2((float)((bits8 >> m) & 1u), 0.f));
+    float2 v = z[8];
+#pragma unroll
+    for (int d = 0; d < 5; ++d) {
+        const float2 o = shfl_up_df(v, 1 << d);
+        if (lane >= (1 << d)) v = df_fma(make_float2(K.ps_hi[d], K.ps_lo[d]), o, v);
+    }
+    float2 ex = shfl_up_df(v, 1);
+    if (lane == 0) ex = make_float2(0.f, 0.f);
+    const float2 xl = df_fma(pl, x_seg, ex);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) out[m] = df_fma(make_float2(K.pm_hi[m], K.pm_lo[m]), xl, z[m]);
+    const float2 xend = df_fma(make_float2(K.pm_hi[8], K.pm_lo[8]), xl, z[8]);
+    return make_float2(__shfl_sync(FULL, xend.x, 31), __shfl_sync(FULL, xend.y, 31));
+}
+
 // Continuous-time columns: the multiplier differs per column, so the powers of a become running products
 // of the column decays.  They depend on the columns only and are formed once per segment for all the rows
 // a warp scans.  Lane l owns columns t_l = t0 + 8 l .. t_l + 7; al[k] = a_{t_l + k} carries X from column

@@ -1,11 +1,14 @@
 // The plain FP32 form of the two contractions (CUDA cores, no tensor cores):
 //   step a3/a4:  U = b 1^T + W X (Eq. 3) with the link applied in the epilogue (Eq. 5):
-//                E[i][t] = dt exp(U_i[t]) stored FP32, per (bin tile, row) FP64 sums of exp(U) and of
-//                U - b over the row's spike bins (the spike-time term of Eq. 7)
+//                E[i][t] = dt exp(U_i[t]) stored FP32, per (bin tile, row) FP64 sums of exp(U).  The
+//                spike-time term of Eq. 7 is not taken from this U: the FP32 form forms it in the row
+//                reduction as q_i b_i + sum_j W_ij C_ij from the FP64 spike term C, because the rounding of
+//                U's FP32 accumulation, summed over the spike bins, alone comes to ~1e-9 of L
 //   step a5:     P_s = E X^T over a split s of the bins (FP32, two-level accumulation)
 // 128 x 128 output tiles, 256 threads, 8 x 8 outputs per thread, operands staged in shared memory.
 #include <cmath>
 
+#include "expm1_acc.cuh"
 #include "glm_internal.h"
 
 namespace glm {
@@ -30,11 +33,6 @@ struct SimtUArgs {
     int* flags;
     const int32_t* rows;  // evaluated rows (null: all n); tile row l is row rows[l] for l < m
     int32_t m;
-    const int64_t* offs;  // spikes (CSR) and each row's first spike index per 256-bin segment
-    const int32_t* bins;
-    const int32_t* seg_first;
-    int64_t nseg;
-    double* part_s;       // [n][ntile] sum of U - b over the row's spike bins in the tile
 };
 
 __device__ __forceinline__ int32_t row_of(const SimtUArgs& A, int32_t l) {
@@ -106,7 +104,8 @@ __global__ void __launch_bounds__(ST) simt_u_kernel(const __grid_constant__ Simt
     }
     // epilogue.  With v = (W X)_i[t]:  e^{U} = e^{b_i} (1 + expm1(v)).  e^{b_i} comes in FP64 and the
     // integer count of bins is kept apart from the FP32 sum of expm1(v), so the part of the integral that
-    // repeats over quiet bins (U ~ b_i) carries no FP32 rounding of exp or of b + v.
+    // repeats over quiet bins (U ~ b_i) carries no FP32 rounding of exp or of b + v; expm1 is correctly
+    // rounded (expm1_acc.cuh), so its rounding carries no bias into the sum either.
     // E = dt e (0 beyond T) in FP32; FP64 row sums of e per tile.
     bool bad = false;
 #pragma unroll
@@ -121,7 +120,7 @@ __global__ void __launch_bounds__(ST) simt_u_kernel(const __grid_constant__ Simt
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const int64_t t = t0 + (c < 4 ? tx * 4 + c : 64 + tx * 4 + (c - 4));
-            const float m = expm1f(acc[r][c] + sh);
+            const float m = expm1_acc(acc[r][c] + sh);
             const bool valid = t < A.T;
             bad |= valid && !(m <= 3.0e38f);
             if (valid) {
@@ -131,35 +130,14 @@ __global__ void __launch_bounds__(ST) simt_u_kernel(const __grid_constant__ Simt
             ev[c] = valid ? fmaf(dteb, m, dteb) : 0.f;
         }
         double rs = ebi * ((double)cnt + (double)msum);
-        // spike bins of row i in this tile (half of a 256-bin segment): this thread's share of sum (U - b)
-        float spv = 0.f;
-        if (i < n) {
-            const int64_t s = t0 / SEG, o0 = A.offs[i];
-            const int64_t ke = (s + 1 < A.nseg) ? o0 + A.seg_first[(int64_t)i * A.nseg + s + 1] : A.offs[i + 1];
-            for (int64_t k = o0 + A.seg_first[(int64_t)i * A.nseg + s]; k < ke; ++k) {
-                const int col = (int)(A.bins[k] - t0);
-                if (col < 0) continue;
-                if (col >= SB) break;
-#pragma unroll
-                for (int c = 0; c < 8; ++c)
-                    if (col == (c < 4 ? tx * 4 + c : 64 + tx * 4 + (c - 4))) spv += acc[r][c];
-            }
-        }
-        double sp = (double)spv;
         // the 16 threads with the same ty share these rows
 #pragma unroll
-        for (int off = 8; off >= 1; off >>= 1) {
-            rs += __shfl_xor_sync(0xffffffffu, rs, off);
-            sp += __shfl_xor_sync(0xffffffffu, sp, off);
-        }
+        for (int off = 8; off >= 1; off >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, off);
         if (i < n) {
             float* dst = A.E + (int64_t)i * A.Tpad + t0;
             *reinterpret_cast<float4*>(dst + tx * 4) = make_float4(ev[0], ev[1], ev[2], ev[3]);
             *reinterpret_cast<float4*>(dst + 64 + tx * 4) = make_float4(ev[4], ev[5], ev[6], ev[7]);
-            if (tx == 0) {
-                A.part_e[(int64_t)i * gridDim.x + blockIdx.x] = rs;
-                A.part_s[(int64_t)i * gridDim.x + blockIdx.x] = sp;
-            }
+            if (tx == 0) A.part_e[(int64_t)i * gridDim.x + blockIdx.x] = rs;
         }
     }
     if (bad) atomicOr(A.flags, 1);
@@ -304,11 +282,6 @@ cudaError_t launch_simt_u_epilogue(glm_ctx* c, const float* W, const float* b, c
     A.flags = c->buf.flags;
     A.rows = rows;
     A.m = rows ? m : P.n;
-    A.offs = c->buf.offs;
-    A.bins = c->buf.bins;
-    A.seg_first = c->buf.seg_first;
-    A.nseg = P.nseg;
-    A.part_s = c->buf.part_s;
     dim3 grid((unsigned)(P.Tpad / SB), (A.m + SB - 1) / SB);
     simt_u_kernel<<<grid, ST, 0, c->stream>>>(A);
     return cudaGetLastError();
@@ -332,3 +305,10 @@ cudaError_t launch_simt_grad(glm_ctx* c) {
 }
 
 }  // namespace glm
+
+// The FP32 form's e^v - 1 (expm1_acc.cuh), evaluated on the host by the same code as the epilogue's.
+extern "C" int glm_expm1(const float* v_host, int64_t n, float* out_host) {
+    if (n < 0 || (n > 0 && (!v_host || !out_host))) return GLM_ERR_INVALID_ARG;
+    for (int64_t k = 0; k < n; ++k) out_host[k] = glm::expm1_acc(v_host[k]);
+    return GLM_OK;
+}

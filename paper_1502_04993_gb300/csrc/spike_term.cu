@@ -12,8 +12,10 @@
 //            4 rows, started from the segment carries);
 //   phase B  every thread walks the staged spikes of its rows and accumulates X_j[t] for the 16 rows (spikes
 //            beyond the staged 24 are read from global memory).
-// Each row's spikes in a sub-chunk are summed in plain FP32, and these partial sums enter an FP32 hi + lo
-// pair (TwoSum) that carries ~44 significant bits; the order is fixed and the result deterministic.
+// X is scanned in double-float (seg_scan_df) and kept in shared memory as hi + lo pairs; every spike's pair
+// enters the row's double-float sum (TwoSum on the hi parts, the lo parts added alongside), ~44 significant
+// bits in a fixed order: C is exact to far below the FP32 rounding of X, which the log-likelihood of the
+// plain FP32 form needs (its spike part is sum_j W_ij C_ij).
 #include <cmath>
 
 #include "glm_internal.h"
@@ -27,15 +29,15 @@ constexpr int ST_SUBSEGS = 4;                 // 1024 bins per sub-chunk
 constexpr int ST_SUB = ST_SUBSEGS * SEG;
 constexpr int ST_KI = 2;                      // postsynaptic rows per thread
 constexpr int ST_ROWS_PER_SLICE = ST_THREADS * ST_KI;
-constexpr int ST_CAP = 24;                    // spike bins per row and sub-chunk staged in shared memory
+constexpr int ST_CAP = 20;                    // spike bins per row and sub-chunk staged in shared memory
 static_assert(ST_THREADS / 32 == ST_SUBSEGS * (ST_JB / 4), "phase A: one warp per (segment, 4 rows)");
 
-// Xs layout: [bin][16 floats] = 4 chunks of 16 bytes per bin, plus one 16-byte pad after every 8 bins.  The
-// phase-A stores (lane l writes bin 8 l + m) then fall 33 chunks apart, i.e. on 8 different bank groups per
-// quarter warp, and the phase-B loads of one bin are 4 consecutive chunks (one base, immediate offsets).
-constexpr int XS_CHUNKS = ST_SUB * 4 + ST_SUB / 8;
+// Xs layout: [bin][16 hi floats, 16 lo floats] = 8 chunks of 16 bytes per bin, plus one 16-byte pad after
+// every 8 bins; the phase-B loads of one bin are 8 consecutive chunks (one base, immediate offsets).
+constexpr int XS_CHUNKS = ST_SUB * 8 + ST_SUB / 8;
 constexpr size_t ST_SMEM = (size_t)XS_CHUNKS * 16 + (size_t)ST_CAP * ST_KI * ST_THREADS * 4;
-__device__ __forceinline__ int xs_base(int bin) { return bin * 4 + (bin >> 3); }
+static_assert(ST_SMEM <= 227 * 1024, "shared memory of one block");
+__device__ __forceinline__ int xs_base(int bin) { return bin * 8 + (bin >> 3); }
 
 __device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(ST_THREADS, 1) spike_term_kernel(const __grid_
     const int32_t j0 = blockIdx.x * ST_JB;
     const int64_t part = blockIdx.y;
     const int32_t i_base = blockIdx.z * ST_ROWS_PER_SLICE;
-    const float pl_hi = K.pl_hi[lane], pl_lo = K.pl_lo[lane];
+    const float2 pl = make_float2(K.pl_hi[lane], K.pl_lo[lane]);
     const int64_t sp0 = part * A.segs_per_part;
     const int64_t sp1 = min(sp0 + A.segs_per_part, A.nseg);
     const int seg_w = warp & (ST_SUBSEGS - 1);   // phase A: this warp's segment
@@ -148,15 +150,15 @@ __global__ void __launch_bounds__(ST_THREADS, 1) spike_term_kernel(const __grid_
         const int64_t s = sc + seg_w;
         if (s < sp1) {
             const int64_t t0 = s * SEG;
-            float xs[4];
+            float2 xs[4];
             int64_t rc[4], re[4], sv[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int32_t r = j0 + grp_w * 4 + k;
-                xs[k] = 0.f;
+                xs[k] = make_float2(0.f, 0.f);
                 rc[k] = re[k] = 0;
                 if (r < A.n) {
-                    xs[k] = df_f(A.seg_carry[(int64_t)r * A.nseg + s]);
+                    xs[k] = A.seg_carry[(int64_t)r * A.nseg + s];
                     rc[k] = A.aoffs[r] + A.aseg_first[(int64_t)r * A.nseg + s];
                     re[k] = A.aoffs[r + 1];
                 }
@@ -166,55 +168,46 @@ __global__ void __launch_bounds__(ST_THREADS, 1) spike_term_kernel(const __grid_
                 const int64_t kk = rc[k] + lane;
                 sv[k] = (kk < re[k]) ? (int64_t)__ldg(A.abins + kk) : INT64_MAX;
             }
-            float v[4][8];
+            float* xf = reinterpret_cast<float*>(Xs);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const uint32_t bits = seg_bits_pre(A.abins, rc[k], re[k], t0, lane, sv[k]);
-                seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v[k]);
-            }
+                float2 v[8];
+                seg_scan_df(K, xs[k], bits, pl, lane, v);
 #pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                const int bin = seg_w * SEG + 8 * lane + m;
-                Xs[xs_base(bin) + grp_w] = make_float4(v[0][m], v[1][m], v[2][m], v[3][m]);
+                for (int m = 0; m < 8; ++m) {
+                    const int bin = seg_w * SEG + 8 * lane + m;
+                    xf[4 * xs_base(bin) + grp_w * 4 + k] = v[m].x;
+                    xf[4 * xs_base(bin) + 16 + grp_w * 4 + k] = v[m].y;
+                }
             }
         }
         cp_async_wait_all();
         __syncthreads();
         // ---- phase B: the spikes of this thread's postsynaptic rows in the sub-chunk ----
+        auto add_bin = [&](int k, int t) {
+            const float4* xp = Xs + xs_base(t);
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) {
+                const float4 h = xp[ch], l = xp[4 + ch];
+                two_sum(acc_hi[k][4 * ch + 0], acc_lo[k][4 * ch + 0], h.x);
+                two_sum(acc_hi[k][4 * ch + 1], acc_lo[k][4 * ch + 1], h.y);
+                two_sum(acc_hi[k][4 * ch + 2], acc_lo[k][4 * ch + 2], h.z);
+                two_sum(acc_hi[k][4 * ch + 3], acc_lo[k][4 * ch + 3], h.w);
+                acc_lo[k][4 * ch + 0] += l.x;
+                acc_lo[k][4 * ch + 1] += l.y;
+                acc_lo[k][4 * ch + 2] += l.z;
+                acc_lo[k][4 * ch + 3] += l.w;
+            }
+        };
 #pragma unroll
         for (int k = 0; k < ST_KI; ++k) {
-            float sh[ST_JB];
-#pragma unroll
-            for (int jj = 0; jj < ST_JB; ++jj) sh[jj] = 0.f;
             const int c = min(cnt[k], ST_CAP);
             const int32_t* sk = Sp + k * ST_THREADS + threadIdx.x;
 #pragma unroll 2
-            for (int u = 0; u < c; ++u) {
-                const int t = sk[u * ST_KI * ST_THREADS] - (int)tb;
-                const float4* xp = Xs + xs_base(t);
-#pragma unroll
-                for (int ch = 0; ch < 4; ++ch) {
-                    const float4 x = xp[ch];
-                    sh[4 * ch + 0] += x.x;
-                    sh[4 * ch + 1] += x.y;
-                    sh[4 * ch + 2] += x.z;
-                    sh[4 * ch + 3] += x.w;
-                }
-            }
-            for (int u = ST_CAP; u < cnt[k]; ++u) {  // beyond the staged spikes (rows firing fast)
-                const int t = (int)(__ldg(A.bins + cur[k] + u) - tb);
-                const float4* xp = Xs + xs_base(t);
-#pragma unroll
-                for (int ch = 0; ch < 4; ++ch) {
-                    const float4 x = xp[ch];
-                    sh[4 * ch + 0] += x.x;
-                    sh[4 * ch + 1] += x.y;
-                    sh[4 * ch + 2] += x.z;
-                    sh[4 * ch + 3] += x.w;
-                }
-            }
-#pragma unroll
-            for (int jj = 0; jj < ST_JB; ++jj) two_sum(acc_hi[k][jj], acc_lo[k][jj], sh[jj]);
+            for (int u = 0; u < c; ++u) add_bin(k, sk[u * ST_KI * ST_THREADS] - (int)tb);
+            for (int u = ST_CAP; u < cnt[k]; ++u)  // beyond the staged spikes (rows firing fast)
+                add_bin(k, (int)(__ldg(A.bins + cur[k] + u) - tb));
             cur[k] = k1[k];
         }
         __syncthreads();

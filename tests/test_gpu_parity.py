@@ -7,7 +7,8 @@ of FP32 X values, each rounded once or twice); log-likelihood relative 1e-9 (tot
 (|L_i| + q_i), the size of its terms (L_i itself can cross zero).  The total-L bound needs X without a
 systematic rounding error: the kernel values e^{-k dt/tau} (Eq. 13) recur after every spike, so a scan
 that rounds the chain 1, a, a^2, ... repeatedly biases X by ~0.6 ulp (about 2e-9 in L); the scan
-takes each power rounded once, and the spike and integral parts of L come from the same U.
+takes each power rounded once.  It also needs the spike part of L in FP64 from the spike term C
+(q_i b_i + sum_j W_ij C_ij): summing the FP32-accumulated U over the spike bins instead adds ~1e-9.
 gradient componentwise relative 1e-5 against the size of its two terms, |dG_ij| / (C_ij + dt sum_t
 e^{U_i} X_j).  Tensor-core forms (X and the rates in BF16 or FP16, W as hi + lo): total log-likelihood
 relative 1e-6, gradient 2e-3 in the same componentwise measure.  Per row, the X rounding error

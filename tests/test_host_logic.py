@@ -88,3 +88,26 @@ def test_double_float_segment_carries_track_fp64(tau_over_dt):
         # into FP32's subnormals, where it keeps an absolute accuracy of ~1e-45 that no reader can see)
         worst = max(worst, abs((float(x[0]) + float(x[1])) - x64) / (x64 + 2.0 ** -100))
     assert worst < 2.0 ** -40, worst
+
+
+def test_fp32_form_expm1_is_correctly_rounded():
+    """The plain FP32 form's e^v - 1 (glm_expm1, the epilogue's own source run on the host) against e^v - 1 in
+    FP64 rounded once to FP32: equal but for rare near-ties (never more than one ulp away), and unbiased (mean
+    signed error ~0 ulp; CUDA's expm1f measured -0.035 ulp on this range, enough to bias L by ~5e-10)."""
+    import numpy as np
+    from paper_1502_04993_gb300 import build as b
+    import paper_1502_04993_gb300 as glm
+    glm.load_library(b.build())
+    rng = np.random.default_rng(5)
+    v = np.concatenate([np.linspace(-0.6, 1.5, 400_001), rng.uniform(-19.9, 88.0, 200_000),
+                        rng.normal(0, 1e-3, 50_000), [0.0, -0.0, 1e-30, -1e-30, 0.34657, -0.34658, 88.0, -20.0]])
+    v = v.astype(np.float32)
+    got = glm.expm1(v).astype(np.float64)
+    ref32 = np.expm1(v.astype(np.float64)).astype(np.float32).astype(np.float64)
+    ulp = np.spacing(np.abs(ref32).astype(np.float32)).astype(np.float64)
+    ex = np.expm1(v.astype(np.float64))
+    d = (got - ex) / ulp
+    assert np.mean(got != ref32) < 1e-3
+    assert np.max(np.abs(got - ref32) / ulp) <= 1.0
+    assert abs(np.mean(d)) < 2e-3
+    assert glm.expm1(np.array([np.nan, 100.0, -50.0], np.float32)).tolist()[1:] == [np.inf, -1.0]
