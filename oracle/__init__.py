@@ -58,7 +58,7 @@ def _load():
             lib.oracle_eval_rows.argtypes = [i32, i64, f64, f64, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, i32]
             lib.oracle_eval_rows.restype = ctypes.c_int
             lib.oracle_fit.argtypes = [i32, i64, f64, f64, vp, vp, i32, i32, i32, f64, f64, i32, f64, f64, vp, vp,
-                                       vp, vp, i32]
+                                       vp, vp, i32, i32, vp]
             lib.oracle_fit.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -114,20 +114,24 @@ def loglik_grad(offs, bins, n_bins: int, dt: float, tau: float, W, b, threads: i
 
 def fit(offs, bins, n_bins: int, dt: float, tau: float, *, method: str = "lbfgs", m: int = 10,
         max_iter: int = 500, eta: float = 1e-10, c1: float = 1e-4, max_halvings: int = 60,
-        alpha: float = 0.0, eps: float = 1e-6, threads: int = 0) -> dict:
+        alpha: float = 0.0, eps: float = 1e-6, threads: int = 0, rows=None) -> dict:
     """Maximum-likelihood W, b, one independent row at a time (Sec. 2.2 separability, Sec. 2.6.3); with
     alpha > 0 the maximum a posteriori estimate under the smooth l1 penalty alpha sum_{j != i}
-    sqrt(W_ij^2 + eps) (Sec. 2.5, Eq. 16-17)."""
+    sqrt(W_ij^2 + eps) (Sec. 2.5, Eq. 16-17).  ``rows``: fit only these rows (W, b, iters and status then
+    follow the order of the list)."""
     offs, bins = _spikes(offs, bins)
     n = offs.size - 1
-    W = np.zeros((n, n))
-    b = np.zeros(n)
-    iters = np.zeros(n, dtype=np.int32)
-    status = np.zeros(n, dtype=np.int32)
+    rl = None if rows is None else np.ascontiguousarray(rows, dtype=np.int32)
+    nr = n if rl is None else rl.size
+    W = np.zeros((nr, n))
+    b = np.zeros(nr)
+    iters = np.zeros(nr, dtype=np.int32)
+    status = np.zeros(nr, dtype=np.int32)
     meth = {"lbfgs": 0, "ga": 1}[method]
     rc = _load().oracle_fit(n, int(n_bins), dt, tau, offs.ctypes.data, bins.ctypes.data, meth, m, max_iter, eta,
                             c1, max_halvings, float(alpha), float(eps), W.ctypes.data, b.ctypes.data,
-                            iters.ctypes.data, status.ctypes.data, threads)
+                            iters.ctypes.data, status.ctypes.data, threads, nr if rl is not None else 0,
+                            rl.ctypes.data if rl is not None else None)
     if rc != 0:
         raise ValueError(f"oracle_fit failed ({rc})")
     return dict(W=W, b=b, iters=iters, status=status)

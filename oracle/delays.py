@@ -11,8 +11,13 @@ Row i has (tau_i, d_i), d_i >= 1 bins.  A spike of neuron j in bin s reaches i i
   L_i        = sum_{t in sp(i)} U_i[t] - dt sum_t exp(U_i[t])                   (Eq. 7 on the grid)
   dL/dW_ij   = sum_t R_i[t] X^(i)_j[t],  dL/db_i = sum_t R_i[t],  R = S - dt e^U (Eq. 12)
 With d_i = 1 this is the grid model of ``oracle.loglik_grad``.  Rows of equal (tau, d) share X: it is the
-grid filter (Eq. 13, ``oracle.filter``) of the trains shifted by d - 1 bins.  Pins:
-``tests/test_delay_oracle_pins.py``.
+grid filter (Eq. 13, ``oracle.filter``) of the trains shifted by d - 1 bins.
+
+Self-delay (Sec. 2.4 and Sec. 3.1: the paper's own network has one transmission delay d for every
+connection and a separate self-delay d_s for each neuron's action on itself): with ``self_delay_rows``
+row i's own train reaches it after s_i bins while every other train arrives after d_i, so the diagonal
+term of U_i uses X^(i,self)_i[t] = sum over spikes s of i with s + s_i <= t of a_i^(t - s_i - s), and
+dL/dW_ii = sum_t R_i[t] X^(i,self)_i[t].  Pins: ``tests/test_delay_oracle_pins.py``.
 """
 from __future__ import annotations
 
@@ -33,8 +38,10 @@ def shift_trains(offs, bins, n_bins: int, shift: int):
     return new_offs, (np.concatenate(rows) if rows else np.zeros(0)).astype(np.int32)
 
 
-def loglik_grad_classes(offs, bins, n_bins: int, dt: float, tau_rows, delay_rows, W, b) -> dict:
-    """L_i, L, dL/dW, dL/db with row i's own tau_i and delay d_i (FP64)."""
+def loglik_grad_classes(offs, bins, n_bins: int, dt: float, tau_rows, delay_rows, W, b,
+                        self_delay_rows=None) -> dict:
+    """L_i, L, dL/dW, dL/db with row i's own tau_i and delay d_i, and (when given) its self-delay s_i for
+    the diagonal term (FP64)."""
     from . import filter as grid_filter
     offs = np.asarray(offs, dtype=np.int64)
     bins = np.asarray(bins, dtype=np.int64)
@@ -43,6 +50,7 @@ def loglik_grad_classes(offs, bins, n_bins: int, dt: float, tau_rows, delay_rows
     tau_rows = np.asarray(tau_rows, dtype=np.float64)
     delay_rows = np.asarray(delay_rows, dtype=np.int64)
     n = len(offs) - 1
+    self_rows = delay_rows if self_delay_rows is None else np.asarray(self_delay_rows, dtype=np.int64)
     L = np.zeros(n)
     G = np.zeros((n, n))
     gb = np.zeros(n)
@@ -50,13 +58,19 @@ def loglik_grad_classes(offs, bins, n_bins: int, dt: float, tau_rows, delay_rows
         rows = np.nonzero((tau_rows == tau) & (delay_rows == d))[0]
         so, sb = shift_trains(offs, bins, n_bins, int(d) - 1)
         X = grid_filter(so, sb, n_bins, dt, tau)
-        U = b[rows, None] + W[rows] @ X
-        S = np.zeros((len(rows), n_bins))
-        for k, i in enumerate(rows):
-            S[k, bins[offs[i]:offs[i + 1]]] = 1.0
-        E = dt * np.exp(U)
-        L[rows] = (S * U).sum(axis=1) - E.sum(axis=1)
-        R = S - E
-        G[rows] = R @ X.T
-        gb[rows] = R.sum(axis=1)
+        for i in rows:
+            # row i's own train, as it reaches row i: shifted by its self-delay instead of d
+            own_o = np.array([0, offs[i + 1] - offs[i]], dtype=np.int64)
+            oo, ob = shift_trains(own_o, bins[offs[i]:offs[i + 1]], n_bins, int(self_rows[i]) - 1)
+            Xi = X.copy() if self_rows[i] != d else X
+            if self_rows[i] != d:
+                Xi[i] = grid_filter(oo, ob, n_bins, dt, tau)[0]
+            U = b[i] + W[i] @ Xi
+            S = np.zeros(n_bins)
+            S[bins[offs[i]:offs[i + 1]]] = 1.0
+            E = dt * np.exp(U)
+            L[i] = (S * U).sum() - E.sum()
+            R = S - E
+            G[i] = Xi @ R
+            gb[i] = R.sum()
     return dict(L=L, L_total=float(L.sum()), G=G, gb=gb)

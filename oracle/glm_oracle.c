@@ -269,8 +269,18 @@ static double dot(const double* a, const double* b, int32_t d) {
  */
 int oracle_fit(int32_t n, int64_t T, double dt, double tau, const int64_t* offs, const int32_t* bins,
                int32_t method, int32_t m, int32_t max_iter, double eta, double c1, int32_t max_halvings,
-               double alpha, double eps, double* W, double* b, int32_t* iters, int32_t* status, int32_t n_threads) {
+               double alpha, double eps, double* W, double* b, int32_t* iters, int32_t* status, int32_t n_threads,
+               int32_t n_rows, const int32_t* rows) {
+    /* rows (n_rows of them), when given: fit only these rows (each row is its own problem, Sec. 2.2);
+       W, b, iters and status are then indexed by position in the list */
     if (check_spikes(n, T, offs, bins) || !(dt > 0) || !(tau > 0) || !W || !b || !iters || !status) return OR_EINVAL;
+    if (rows) {
+        if (n_rows < 1) return OR_EINVAL;
+        for (int32_t r = 0; r < n_rows; ++r)
+            if (rows[r] < 0 || rows[r] >= n) return OR_EINVAL;
+    } else {
+        n_rows = n;
+    }
     if (!(alpha >= 0) || !(eps > 0)) return OR_EINVAL;
     if (m < 1 || m > 64 || max_iter < 0 || !(eta >= 0) || !(c1 > 0 && c1 < 1) || max_halvings < 1)
         return OR_EINVAL;
@@ -281,13 +291,14 @@ int oracle_fit(int32_t n, int64_t T, double dt, double tau, const int64_t* offs,
     const int32_t d = n + 1;
     int failed = 0;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
-    for (int32_t i = 0; i < n; ++i) {
+    for (int32_t r = 0; r < n_rows; ++r) {
+        const int32_t i = rows ? rows[r] : r;
         const int64_t q = offs[i + 1] - offs[i];
         if (q == 0) {
-            b[i] = log(1e-3);
-            for (int32_t j = 0; j < n; ++j) W[(size_t)i * n + j] = 0.0;
-            iters[i] = 0;
-            status[i] = FIT_DEGENERATE;
+            b[r] = log(1e-3);
+            for (int32_t j = 0; j < n; ++j) W[(size_t)r * n + j] = 0.0;
+            iters[r] = 0;
+            status[r] = FIT_DEGENERATE;
             continue;
         }
         double* mem = (double*)malloc(sizeof(double) * ((size_t)T + (size_t)d * (6 + 2 * (size_t)m) + (size_t)m));
@@ -398,10 +409,10 @@ int oracle_fit(int32_t n, int64_t T, double dt, double tau, const int64_t* offs,
                 break;
             }
         }
-        b[i] = x[0];
-        for (int32_t j = 0; j < n; ++j) W[(size_t)i * n + j] = x[1 + j];
-        iters[i] = it;
-        status[i] = st;
+        b[r] = x[0];
+        for (int32_t j = 0; j < n; ++j) W[(size_t)r * n + j] = x[1 + j];
+        iters[r] = it;
+        status[r] = st;
         free(mem);
     }
     free(X);

@@ -24,16 +24,19 @@ def tiny(seed, n=3, T=80):
     return offs, bins, W, b
 
 
-def direct(offs, bins, T, dt, taus, ds, W, b):
-    """Definition: U_i[t] = b_i + sum_j W_ij sum_{s: s + d_i <= t} exp(-(t - d_i - s) dt / tau_i)."""
+def direct(offs, bins, T, dt, taus, ds, W, b, selfd=None):
+    """Definition: U_i[t] = b_i + sum_j W_ij sum_{s: s + D_ij <= t} exp(-(t - D_ij - s) dt / tau_i), with
+    D_ij = d_i for j != i and D_ii = the self-delay (d_i unless given)."""
     n = len(offs) - 1
+    selfd = ds if selfd is None else selfd
     L, G, gb = np.zeros(n), np.zeros((n, n)), np.zeros(n)
     for i in range(n):
         X = np.zeros((n, T))
         for j in range(n):
+            dij = selfd[i] if j == i else ds[i]
             for s in bins[offs[j]:offs[j + 1]]:
-                for t in range(s + ds[i], T):
-                    X[j, t] += np.exp(-(t - ds[i] - s) * dt / taus[i])
+                for t in range(s + dij, T):
+                    X[j, t] += np.exp(-(t - dij - s) * dt / taus[i])
         U = b[i] + W[i] @ X
         S = np.zeros(T)
         S[bins[offs[i]:offs[i + 1]]] = 1.0
@@ -97,3 +100,36 @@ def test_delay_past_the_recording():
     r = od.loglik_grad_classes(offs, bins, 50, 0.001, [0.01, 0.01], [5, 5], W, b)
     L, G, gb = direct(offs, bins, 50, 0.001, [0.01, 0.01], [5, 5], W, b)
     assert np.allclose(r["L"], L, rtol=1e-12) and np.allclose(r["G"], G, rtol=1e-11, atol=1e-14)
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_self_delay_matches_the_definition(seed):
+    """The paper's separate self-delay (Sec. 2.4, Sec. 3.1): the diagonal term acts after s_i bins, every other
+    source after d_i; against the per-pair definition, including s_i = d_i rows (no change)."""
+    T, dt = 90, 0.001
+    offs, bins, W, b = tiny(seed, n=4, T=T)
+    taus, ds, selfd = [0.01, 0.01, 0.015, 0.02], [3, 3, 2, 4], [1, 3, 1, 2]
+    r = od.loglik_grad_classes(offs, bins, T, dt, taus, ds, W, b, self_delay_rows=selfd)
+    L, G, gb = direct(offs, bins, T, dt, taus, ds, W, b, selfd=selfd)
+    assert np.allclose(r["L"], L, rtol=1e-12, atol=1e-12)
+    assert np.allclose(r["G"], G, rtol=1e-11, atol=1e-12)
+    assert np.allclose(r["gb"], gb, rtol=1e-12, atol=1e-12)
+    # and it differs from the uniform-delay model exactly where a self-delay differs
+    u = od.loglik_grad_classes(offs, bins, T, dt, taus, ds, W, b)
+    differ = np.array(selfd) != np.array(ds)
+    assert np.all(np.abs(r["L"] - u["L"])[differ] > 1e-9) and np.array_equal(r["L"][~differ], u["L"][~differ])
+
+
+def test_self_delay_gradient_is_the_derivative():
+    T, dt = 100, 0.001
+    offs, bins, W, b = tiny(6, n=3, T=T)
+    taus, ds, selfd = [0.01, 0.012, 0.01], [2, 4, 3], [1, 1, 3]
+    r = od.loglik_grad_classes(offs, bins, T, dt, taus, ds, W, b, self_delay_rows=selfd)
+    h = 1e-6
+    for i in range(3):
+        Wp, Wm = W.copy(), W.copy()
+        Wp[i, i] += h
+        Wm[i, i] -= h
+        fd = (od.loglik_grad_classes(offs, bins, T, dt, taus, ds, Wp, b, self_delay_rows=selfd)["L"][i]
+              - od.loglik_grad_classes(offs, bins, T, dt, taus, ds, Wm, b, self_delay_rows=selfd)["L"][i]) / (2 * h)
+        assert r["G"][i, i] == pytest.approx(fd, rel=1e-6, abs=1e-8)
