@@ -154,6 +154,24 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu; /proc/cpuinfo as a fallback)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(w, cores: int, n_rows: int | None = None, t_frac: float = 0.25):
     """The FP64 oracle as it stands, on a bounded sample: `cores` rows over the first t_frac of the bins."""
     import numpy as np
@@ -177,6 +195,58 @@ def cpu_baseline(w, cores: int, n_rows: int | None = None, t_frac: float = 0.25)
             "seconds": el}
 
 
+def cpu_baseline_report(w, cores: int, glm, device, stream, gpu_fit: dict | None):
+    """The CPU baseline of the bench line: the FP64 oracle timed on this host's cores, all cores and one
+    thread, on bounded samples of the N = 1000 workload; the oracle's whole fit of the N = 50, 20 000-bin
+    recording beside the GPU's fits of it (FP32 and BF16); and the N = 1000 evaluation and fit times
+    extrapolated from the sampled rate (labelled as such: a full oracle evaluation takes minutes)."""
+    import numpy as np
+    import oracle
+    import synth
+    from synth import truth_labels
+    allc = cpu_baseline(w, cores)
+    one = cpu_baseline(w, 1, n_rows=1, t_frac=0.25)
+    rep = {k: allc[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    rep["cpu_model"] = cpu_model()
+    rep["single_thread"] = {"value": one["value"], "unit": UNIT, "cores": 1, "sample": one["sample"]}
+    rep["all_core_over_single"] = allc["value"] / one["value"]
+    # config 0: the whole fit, oracle (all cores and one thread) against the GPU
+    w0 = synth.make_workload("glm_n50_t20k")
+    truth0 = truth_labels(w0["W_true"])
+    c0 = {"workload": "glm_n50_t20k (N = 50, 20 000 bins)", "eta": 1e-10}
+    for label, th in (("oracle_all_cores", cores), ("oracle_one_thread", 1)):
+        t0 = time.perf_counter()
+        f = oracle.fit(w0["offs"], w0["bins"], w0["n_bins"], w0["dt"], w0["tau"], eta=1e-10, max_iter=500,
+                       threads=th)
+        el = time.perf_counter() - t0
+        lab, _ = oracle.classify(f["W"], "gmm")
+        c0[label] = {"seconds": el, "iterations_max": int(f["iters"].max()),
+                     "mer": oracle.mer_breakdown(lab, truth0)["mer"]}
+    oracle_labels = oracle.classify(f["W"], "gmm")[0]
+    g = glm.GLM(device, stream=stream)
+    try:
+        for p in ("f32", "bf16"):
+            g.set_problem(w0["offs"], w0["bins"], w0["n_bins"], w0["dt"], w0["tau"], prec=p)
+            r = g.fit(eta=1e-10, max_iter=500)
+            Wf = r["W"].cpu().numpy().astype(np.float64)
+            lab, rr = glm.classify(Wf, "gmm", truth=truth0)
+            c0[f"gpu_{p}"] = {"seconds": r["report"]["seconds"], "iterations": r["report"]["iterations"],
+                              "mer": rr["mer"], "labels_equal_oracle": bool(np.array_equal(lab, oracle_labels))}
+    finally:
+        g.close()
+    for p in ("f32", "bf16"):
+        c0[f"oracle_all_cores_over_gpu_{p}"] = c0["oracle_all_cores"]["seconds"] / c0[f"gpu_{p}"]["seconds"]
+    rep["config0_fit"] = c0
+    # config 1 (N = 1000, 1.8 M bins): extrapolated from the sampled all-core rate
+    s_eval = w["n"] * w["n_bins"] / allc["value"]
+    ext = {"label": "extrapolated from the sampled all-core rate (not run)", "seconds_per_evaluation": s_eval}
+    if gpu_fit and "bf16" in gpu_fit:
+        ext["fit_seconds_at_gpu_bf16_evaluation_count"] = s_eval * gpu_fit["bf16"]["evaluations"]
+        ext["gpu_bf16_fit_seconds"] = gpu_fit["bf16"]["seconds"]
+    rep["config1_extrapolated"] = ext
+    return rep
+
+
 def run_reference(args):
     ws, rank, _ = dist_info()
     if rank != 0:
@@ -197,7 +267,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "n": w["n"], "n_bins": w["n_bins"]},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": r["sample"]},
+                             "sample": r["sample"], "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -302,9 +372,13 @@ def run_ct(args, glm, w, device, stream, prec):
         Ws = {}
         for name, c in (() if args.no_ct_fit else (("continuous", ct), ("grid", gr))):
             r = c.fit(eta=args.fit_eta, max_iter=args.fit_max_iter)
-            _, rep = glm.classify(r["W"].cpu().numpy().astype(np.float64), "gmm", truth=truth, types=w["types"])
+            Wf = r["W"].cpu().numpy().astype(np.float64)
+            _, rep = glm.classify(Wf, "gmm", truth=truth, types=w["types"])
+            _, repk = glm.classify(Wf, "kmeans", truth=truth, types=w["types"])
             fits[name] = {"seconds": r["report"]["seconds"], "iterations": r["report"]["iterations"],
-                          "evaluations": r["report"]["evaluations"], "mer": rep["mer"]}
+                          "evaluations": r["report"]["evaluations"], "mer_percent_gmm": 100.0 * rep["mer"],
+                          "mer_percent_kmeans": 100.0 * repk["mer"], "centers_gmm": list(rep["centers"]),
+                          "centers_kmeans": list(repk["centers"])}
             Ws[name] = r["W"]
         if Ws:
             dW = (Ws["continuous"] - Ws["grid"]).abs()
@@ -576,19 +650,35 @@ def main():
     name, (cnt, tot_ms) = top
     per_launch_s = tot_ms / cnt / 1000.0
     if name in ("u_epilogue", "grad"):
-        # 2 N flop per neuron-bin per product; the 16-bit U product executes 3 of them (W_hi X_hi, W_lo X_hi,
-        # W_hi X_lo), the precision split of the operands
-        flops = 2.0 * n * n * T * (3 if (name == "u_epilogue" and prec != "f32") else 1)
         if prec == "f32":
+            flops = 2.0 * n * n * T
             # FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x max SM clock
             sm_mhz = peaks.get("sm_max_mhz", 2070.0)
             peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
             roof = {"bound": "alu", "achieved": flops / per_launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
         else:
+            # algorithmic work per neuron-bin: 2N for the plain product; the U product with W as hi + lo
+            # (W_hi X + W_lo X) is 4N.  The kernel also executes W_hi X_lo (the rounding correction of X):
+            # 6N executed.
+            alg = 4.0 if name == "u_epilogue" else 2.0
+            executed = 6.0 if name == "u_epilogue" else 2.0
             peak = peaks["bf16_tflops"]
-            roof = {"bound": "tensor", "achieved": flops / per_launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                    "peak_source": f"{peak_src} bf16_tflops (burst)"}
+            ach = alg * n * n * T / per_launch_s / 1e12
+            roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "peak_source": f"{peak_src} bf16_tflops (burst)",
+                    "flop_count": (f"{alg:g}N per neuron-bin (W_hi X + W_lo X)" if name == "u_epilogue"
+                                   else "2N per neuron-bin")}
+            ex = executed * n * n * T / per_launch_s / 1e12
+            roof["executed"] = {"achieved": ex, "frac": ex / peak,
+                                "flop_count": f"{executed:g}N per neuron-bin, every product the kernel issues"}
+            if name == "u_epilogue":
+                roof["plain_2N_frac"] = 2.0 * n * n * T / per_launch_s / 1e12 / peak
+            pk = peaks.get("clocks_under_load", {}).get("sm_mhz_median")
+            if pk and clk.get("sm_mhz"):
+                # the peak was measured at its own clock: scaled to this run's median SM clock
+                roof["clock_normalised"] = {"peak_run_sm_mhz": pk, "this_run_sm_mhz": clk["sm_mhz"],
+                                            "frac": ach / (peak * clk["sm_mhz"] / pk)}
     else:
         esz = 4 if prec == "f32" else 2
         nbytes = {"filter_scan": n * T * esz * (1 if prec == "f32" else 2) + w["bins"].nbytes,
@@ -637,7 +727,8 @@ def main():
             fr = r["report"]
             fits[p] = {"seconds": fr["seconds"], "iterations": fr["iterations"], "evaluations": fr["evaluations"],
                        "gradients": fr["gradients"], "converged": fr["converged"], "at_floor": fr["at_floor"], "stalled": fr["stalled"],
-                       "maxiter": fr["maxiter"], "L": fr["L"], "mer": rep["mer"], "mer_n2": rep["mer_n2"]}
+                       "maxiter": fr["maxiter"], "L": fr["L"], "mer": rep["mer"], "mer_percent": 100.0 * rep["mer"],
+                       "mer_n2": rep["mer_n2"]}
         if "f32" in fits:
             for p, v in fits.items():
                 v["speedup_vs_f32"] = fits["f32"]["seconds"] / v["seconds"]
@@ -653,8 +744,8 @@ def main():
     if args.synfire:
         line["synfire"] = run_synfire(args, glm, device, stream, prec)
     if ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, os.cpu_count() or 1)
-        line["cpu_baseline"].pop("seconds", None)
+        line["cpu_baseline"] = cpu_baseline_report(w, os.cpu_count() or 1, glm, device, stream,
+                                                   line.get("fit", {}).get("by_precision"))
     print(json.dumps(line), flush=True)
     ctx.close()
     if ws > 1:

@@ -153,6 +153,13 @@ int glm_problem_columns(const glm_ctx* ctx, int64_t* n_columns);
  * outputs). */
 int glm_ct_interval(double u, double D, double tau, double* F_host, double* G_host);
 
+/* e^v - 1 for each of n FP32 values, as the plain FP32 form's link epilogue evaluates it (the rate of Eq. 5
+ * is e^b (1 + (e^v - 1)) with v = sum_j W_ij X_j): Cody-Waite reduction and a Taylor series in double-float,
+ * rounded once, i.e. correctly rounded but for rare near-ties, so that its rounding does not bias the
+ * integral of Eq. 7.  Host function, needs no GPU; the device code is the same source.
+ * Errors: INVALID_ARG (n < 0, NULL arrays with n > 0). */
+int glm_expm1(const float* v_host, int64_t n, float* out_host);
+
 /* ---- per-neuron time constants and delays (Sec. 2.2, Sec. 2.4 Eq. 15) ----
  * The paper's kernel h_i(t) = H(t) exp(-t / tau_i) belongs to the target neuron i, and Eq. 15 shifts every
  * source train S_j by the delay D_ij of the target that receives it.  The rows (targets) are grouped into
@@ -166,6 +173,17 @@ int glm_ct_interval(double u, double D, double tau, double* F_host, double* G_ho
  * spike-time term, stay where they are.  Takes effect at the next glm_set_problem (grid form).
  * Errors: INVALID_ARG (delay_bins < 1). */
 int glm_set_source_delay(glm_ctx* ctx, int32_t delay_bins);
+
+/* Self-delay (Sec. 2.4, Eq. 15 with D_ii != D_ij; the paper's own network uses one delay d for every
+ * connection and a separate self-delay d_s, Sec. 3.1): each row's own train reaches it after self_bins bins
+ * while every other train arrives after the source delay (glm_set_source_delay).  1 <= self_bins <= the
+ * source delay (a self-delay equal to it, or 0, the default, leaves the model as it is).  U_i then has the
+ * diagonal term W_ii X_i[t + d - d_s], X filtered with the source delay d: the filtered trains extend d - d_s
+ * bins past the recording, and the U product, the spike term's diagonal and dL/dW_ii use that shifted row.
+ * Takes effect at the next glm_set_problem of a tensor-core grid problem with X stored; glm_set_problem
+ * returns UNSUPPORTED for the plain FP32 form or a chunked problem with a self-delay, and glm_loglik_grad
+ * does for dL/dtau, as do glm_set_problem_ct and glm_fit_batch.  Errors: INVALID_ARG (self_bins < 0). */
+int glm_set_self_delay(glm_ctx* ctx, int32_t self_bins);
 
 /* Restrict evaluations and fits of the current problem to rows [r0, r1) (0 <= r0 < r1 <= n; r0 = 0 with
  * r1 = 0 or n restores all rows).  glm_loglik_grad then forms U, the rates and the gradient for those rows
@@ -365,6 +383,13 @@ typedef struct {
     float best_ms;      /* time of one gradient product with the choice */
 } glm_tune_report_t;
 int glm_autotune(glm_ctx* ctx, glm_tune_report_t* report);
+
+/* Set the gradient product's tile shape by hand, as one of the autotuner's candidates: mode 1 (256-row
+ * tiles) or 2 (128-row tiles), and units_per_sm in {1, 2, 4, 8}, from which the bin splits follow
+ * (written to *nsplit_out when not NULL).  Applies to the context's later evaluations and fits until the next
+ * glm_set_problem or glm_autotune.  Every candidate computes the same product; they differ in the FP32
+ * summation order of the gradient only.  Errors: INVALID_ARG, NO_PROBLEM, UNSUPPORTED (GLM_PREC_F32). */
+int glm_set_grad_tile(glm_ctx* ctx, int32_t mode, int32_t units_per_sm, int32_t* nsplit_out);
 
 /* ---- classification of reconstructed weights (Sec. 3.1 GMM, Sec. 3.3 k-means, Table 2, Eq. 20) ---- */
 #define GLM_CLASSIFY_GMM 0    /* 3-component Gaussian mixture by EM, started from 3-means (default) */

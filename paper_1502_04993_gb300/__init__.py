@@ -83,8 +83,10 @@ SIGNATURES["glm_fit_default_opts"] = ([ctypes.POINTER(FitOpts)], None)
 SIGNATURES["glm_fit"] = ([_vp, ctypes.POINTER(FitOpts), _vp, _vp, _vp, ctypes.POINTER(FitReport)], ctypes.c_int)
 SIGNATURES["glm_fit_batch"] = ([_vp, _i32, ctypes.POINTER(FitOpts), _vp, _vp, _vp, ctypes.POINTER(FitReport)], ctypes.c_int)
 SIGNATURES["glm_autotune"] = ([_vp, _vp], ctypes.c_int)
+SIGNATURES["glm_set_grad_tile"] = ([_vp, _i32, _i32, ctypes.POINTER(_i32)], ctypes.c_int)
 SIGNATURES["glm_set_chunk_bins"] = ([_vp, _i64], ctypes.c_int)
 SIGNATURES["glm_set_source_delay"] = ([_vp, _i32], ctypes.c_int)
+SIGNATURES["glm_set_self_delay"] = ([_vp, _i32], ctypes.c_int)
 SIGNATURES["glm_set_row_range"] = ([_vp, _i32, _i32], ctypes.c_int)
 SIGNATURES["glm_fit_classes"] = ([_vp, _i32, ctypes.POINTER(FitOpts), _vp, _vp, _vp, ctypes.POINTER(FitReport)],
                                  ctypes.c_int)
@@ -95,6 +97,7 @@ SIGNATURES["glm_check_wait_limit"] = ([_vp, _f64], ctypes.c_int)
 SIGNATURES["glm_set_problem_ct"] = ([_vp, _i32, _f64, _f64, _f64, _f64, _vp, _vp, ctypes.c_int], ctypes.c_int)
 SIGNATURES["glm_problem_columns"] = ([_vp, ctypes.POINTER(_i64)], ctypes.c_int)
 SIGNATURES["glm_ct_interval"] = ([_f64, _f64, _f64, ctypes.POINTER(_f64), ctypes.POINTER(_f64)], ctypes.c_int)
+SIGNATURES["glm_expm1"] = ([_vp, _i64, _vp], ctypes.c_int)
 SIGNATURES["glm_cross_validate"] = ([_vp, _vp, ctypes.POINTER(FitOpts), _vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp],
                                      ctypes.c_int)
 SIGNATURES["glm_classify"] =([_vp, _i32, ctypes.POINTER(ClassifyOpts), _vp, _vp, _vp, ctypes.POINTER(ClassifyReport)],
@@ -208,6 +211,17 @@ def ward_cut(Z, k: int) -> np.ndarray:
     if rc != GLM_OK:
         raise GLMError(rc, "glm_ward_cut")
     return lab
+
+
+def expm1(v) -> np.ndarray:
+    """e^v - 1 of float32 values as the plain FP32 form's epilogue computes it (host code of libglm)."""
+    lib = load_library()
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    out = np.empty_like(v)
+    rc = lib.glm_expm1(v.ctypes.data, v.size, out.ctypes.data)
+    if rc != GLM_OK:
+        raise GLMError(rc, "glm_expm1")
+    return out
 
 
 def ct_interval(u: float, D: float, tau: float):
@@ -377,6 +391,11 @@ class GLM:
         """Delay of the source trains in bins (>= 1), applied at the next set_problem (glm_set_source_delay)."""
         self._check(self.lib.glm_set_source_delay(self.h, int(delay_bins)), "glm_set_source_delay")
 
+    def set_self_delay(self, self_bins: int):
+        """Each row's own train reaches it after self_bins bins, the others after the source delay
+        (glm_set_self_delay; applies at the next set_problem)."""
+        self._check(self.lib.glm_set_self_delay(self.h, int(self_bins)), "glm_set_self_delay")
+
     def set_row_range(self, r0: int, r1: int):
         """Evaluate and fit rows [r0, r1) only (glm_set_row_range); (0, 0) restores all rows."""
         self._check(self.lib.glm_set_row_range(self.h, int(r0), int(r1)), "glm_set_row_range")
@@ -477,6 +496,13 @@ class GLM:
     def set_chunk_bins(self, chunk_bins: int):
         """Recompute X in chunks of this many bins instead of storing it (applies to the next set_problem)."""
         self._check(self.lib.glm_set_chunk_bins(self.h, int(chunk_bins)), "glm_set_chunk_bins")
+
+    def set_grad_tile(self, mode: int, units_per_sm: int) -> int:
+        """Force one of the autotuner's gradient-product tile shapes; returns the resulting bin splits."""
+        ns = ctypes.c_int32(0)
+        self._check(self.lib.glm_set_grad_tile(self.h, int(mode), int(units_per_sm), ctypes.byref(ns)),
+                    "glm_set_grad_tile")
+        return ns.value
 
     def autotune(self) -> dict:
         """Time the gradient product's tile shapes for this problem and keep the fastest (glm_autotune)."""

@@ -278,6 +278,11 @@ int alloc_problem(glm_ctx* c) {
             return rc;
         }
     }
+    if (P.self_shift > 0 &&
+        ((rc = ws_alloc_t(c, &B.part_self, (size_t)n * ntile)) || (rc = ws_alloc_t(c, &B.gself, n)))) {
+        free_all(c);
+        return rc;
+    }
     if (P.ct) {
         if ((rc = ws_alloc_t(c, &B.ctime, P.Tpad + 1)) || (rc = ws_alloc_t(c, &B.col_a, P.Tpad)) ||
             (rc = ws_alloc_t(c, &B.colc, 8 * (size_t)P.Tpad)) || (rc = ws_alloc_t(c, &B.seg_mul, P.nseg)) ||
@@ -600,7 +605,11 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
     P.dt = dt;
     P.tau = tau;
     P.q = offs[n];
-    P.nseg = (n_bins + SEG - 1) / SEG;
+    // a self-delay shorter than the source delay reads X_i that many bins ahead: the buffers extend past T
+    P.self_shift = (c->self_req > 0 && c->self_req < c->delay_req) ? c->delay_req - c->self_req : 0;
+    if (P.self_shift > 0 && (!tensor || (c->chunk_req > 0 && round_up(c->chunk_req, 16 * SEG) < round_up(n_bins, SEG))))
+        return fail(c, GLM_ERR_UNSUPPORTED, "a self-delay needs a tensor-core precision with X stored (no chunks)");
+    P.nseg = (n_bins + P.self_shift + SEG - 1) / SEG;
     P.Tpad = P.nseg * SEG;
     P.prec = prec;
     P.chunk = 0;
@@ -610,17 +619,19 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
     P.span = (double)n_bins * dt;
     P.dt_int = dt;
     // delayed sources: each spike at bin s reaches the rows at s + delay, i.e. the filter reads it at
-    // s + delay - 1 (its recursion adds S[t - 1] at t); spikes pushed past the recording drop out
+    // s + delay - 1 (its recursion adds S[t - 1] at t); spikes pushed past the recording drop out (past the
+    // buffers, with a self-delay: those bins past T only serve X_i ahead of T - 1, i.e. the self term)
     P.delay_bins = c->delay_req;
     std::vector<int64_t> aoffs;
     std::vector<int32_t> abins;
     if (P.delay_bins > 1) {
         aoffs.assign(n + 1, 0);
         abins.reserve(P.q);
+        const int64_t lim = P.self_shift > 0 ? P.Tpad : n_bins;
         for (int32_t i = 0; i < n; ++i) {
             for (int64_t k = offs[i]; k < offs[i + 1]; ++k) {
                 const int64_t s2 = (int64_t)bins[k] + P.delay_bins - 1;
-                if (s2 < n_bins) abins.push_back((int32_t)s2);
+                if (s2 < lim) abins.push_back((int32_t)s2);
             }
             aoffs[i + 1] = (int64_t)abins.size();
         }
@@ -661,6 +672,8 @@ int glm_set_problem_ct(glm_ctx* c, int32_t n, double t_begin, double t_end, doub
         return fail(c, GLM_ERR_INVALID_ARG, "tau must be finite and > 0, delay finite and >= 0");
     if (prec != GLM_PREC_BF16 && prec != GLM_PREC_F16)
         return fail(c, GLM_ERR_UNSUPPORTED, "the continuous-time form runs on the tensor-core precisions (bf16, f16)");
+    if (c->self_req > 0)
+        return fail(c, GLM_ERR_UNSUPPORTED, "the continuous-time form has one delay for every pair (no self-delay)");
     if (!(c->cc_major == 10 && c->cc_minor == 3))
         return fail(c, GLM_ERR_UNSUPPORTED_ARCH, "BF16/F16 tensor-core paths need an sm_103 GPU (found sm_" +
                                                      std::to_string(c->cc_major) + std::to_string(c->cc_minor) + ")");
@@ -809,6 +822,8 @@ int glm_loglik_grad(glm_ctx* c, const float* W, const float* b, double* L_rows, 
         return fail(c, GLM_ERR_UNSUPPORTED, "dL/dtau is computed by the tensor-core precisions only");
     if (gtau_host && c->pb.ct)
         return fail(c, GLM_ERR_UNSUPPORTED, "dL/dtau is computed for the grid form only");
+    if (gtau_host && c->pb.self_shift > 0)
+        return fail(c, GLM_ERR_UNSUPPORTED, "dL/dtau is not computed with a self-delay");
     DeviceGuard g(c->device);
     double* Lr = L_rows ? L_rows : c->buf.Lrows;
     if (gtau_host) {
@@ -937,6 +952,13 @@ int glm_cross_validate(glm_ctx* tr, glm_ctx* va, const glm_fit_opts_t* opts, con
     return cleanup(GLM_OK);
 }
 
+int glm_set_self_delay(glm_ctx* c, int32_t self_bins) {
+    if (!c) return GLM_ERR_INVALID_ARG;
+    if (self_bins < 0) return fail(c, GLM_ERR_INVALID_ARG, "self_bins must be >= 0");
+    c->self_req = self_bins;
+    return GLM_OK;
+}
+
 int glm_set_source_delay(glm_ctx* c, int32_t delay_bins) {
     if (!c) return GLM_ERR_INVALID_ARG;
     if (delay_bins < 1) return fail(c, GLM_ERR_INVALID_ARG, "delay_bins must be >= 1");
@@ -1041,7 +1063,7 @@ int glm_poison_caches(glm_ctx* c) {
     // times and durations (set-up data) or the optimiser state
     void* derived[] = {B.seg_carry, B.seg_first, B.pow_seg, B.C, B.C_part, B.X, B.Xlo, B.Gacc, B.E, B.part_e,
                        B.part_s, B.part_g, B.Wsplit, B.Lrows, B.scal, B.eb, B.part_tau, B.tau_rows,
-                       B.col_a, B.colc, B.seg_mul};
+                       B.col_a, B.colc, B.seg_mul, B.part_self, B.gself};
     for (void* p : derived) {
         if (!p) continue;
         for (int k = 0; k < c->n_allocs; ++k)
@@ -1073,6 +1095,18 @@ int glm_autotune(glm_ctx* c, glm_tune_report_t* rep) {
     return rc ? fail(c, rc, "autotune failed") : GLM_OK;
 }
 
+int glm_set_grad_tile(glm_ctx* c, int32_t mode, int32_t units_per_sm, int32_t* nsplit_out) {
+    if (!c) return GLM_ERR_INVALID_ARG;
+    if (!c->has_problem) return fail(c, GLM_ERR_NO_PROBLEM, "no problem set");
+    if (c->pb.prec == GLM_PREC_F32) return fail(c, GLM_ERR_UNSUPPORTED, "the tile shape is the tensor-core product's");
+    if ((mode != 1 && mode != 2) || (units_per_sm != 1 && units_per_sm != 2 && units_per_sm != 4 && units_per_sm != 8))
+        return fail(c, GLM_ERR_INVALID_ARG, "mode must be 1 or 2, units_per_sm 1, 2, 4 or 8");
+    c->g_mode = mode;
+    c->g_nsplit = glm::tc_nsplit_for(c, mode, units_per_sm);
+    if (nsplit_out) *nsplit_out = c->g_nsplit;
+    return GLM_OK;
+}
+
 int glm_fit_batch(glm_ctx* const* cs, int32_t np, const glm_fit_opts_t* opts, float* const* W, float* const* b,
                   int8_t* const* row_status, glm_fit_report_t* reps) {
     if (!cs || np < 1 || np > GLM_FIT_BATCH_MAX || !W || !b) return GLM_ERR_INVALID_ARG;
@@ -1087,6 +1121,7 @@ int glm_fit_batch(glm_ctx* const* cs, int32_t np, const glm_fit_opts_t* opts, fl
         if (c->pb.chunk) return fail(c0, GLM_ERR_UNSUPPORTED, "glm_fit_batch needs X stored (no chunking)");
         if (c->pb.ct) return fail(c0, GLM_ERR_UNSUPPORTED, "glm_fit_batch serves the grid form");
         if (c->row_r1 >= 0) return fail(c0, GLM_ERR_UNSUPPORTED, "glm_fit_batch fits whole problems (no row range)");
+        if (c->pb.self_shift > 0) return fail(c0, GLM_ERR_UNSUPPORTED, "glm_fit_batch has no self-delay");
         for (int32_t q = 0; q < p; ++q)
             if (cs[q] == c) return fail(c0, GLM_ERR_INVALID_ARG, "a context appears twice");
     }

@@ -55,6 +55,10 @@ struct Problem {
     // filter recursion); above 1 the filter reads the spikes shifted by delay_bins - 1
     int32_t delay_bins = 1;
     int64_t qa = 0;       // arrivals inside the recording
+    // self-delay (16-bit grid forms, X stored): row i's own train reaches row i after delay_bins - self_shift
+    // bins, every other train after delay_bins; X_i with the self-delay is X_i at bin t + self_shift, so the
+    // buffers extend at least self_shift bins past T (Tpad >= T + self_shift)
+    int32_t self_shift = 0;
 };
 
 // Device buffers owned by a context.  Row-major everywhere; ld* in elements.
@@ -75,6 +79,8 @@ struct Buffers {
     double* part_e = nullptr;     // [n][ntile_t]  per-(row, bin tile) sums of exp(U); continuous time:
                                   // CT_PARTS such planes, one per part of each tile's columns
     double* part_s = nullptr;     // [n][ntile_t] per-(row, bin tile) sums of U - b over the spike bins (idem)
+    double* part_self = nullptr;  // self-delay: [n][ntile] per-(row, tile) sums of dt e^U (X_i self - X_i)
+    double* gself = nullptr;      // self-delay: [n] their row sums (the diagonal's part of dL/dW_ii)
     float* part_g = nullptr;      // [nsplit][n][n] FP32 partial sums of E X^T
     void* Wsplit = nullptr;       // 16-bit: hi and lo parts of W, [2][n][ldn]
     int* flags = nullptr;         // [4] device error flags
@@ -125,6 +131,7 @@ struct glm_ctx {
     int g_nsplit = 0;      // E X^T bin splits (0: the default for g_mode)
     int64_t chunk_req = 0; // bins per chunk requested by glm_set_chunk_bins (applied by glm_set_problem)
     int32_t delay_req = 1; // source delay in bins requested by glm_set_source_delay (applied by glm_set_problem)
+    int32_t self_req = 0;  // self-delay in bins requested by glm_set_self_delay (0: as the source delay)
     int32_t row_r0 = 0, row_r1 = -1;  // evaluated and fitted rows (glm_set_row_range); r1 < 0: all rows
     std::string last_error;
     // tracing: event pairs per launched kernel group while profiling is on
@@ -193,6 +200,7 @@ cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, boo
                                  int32_t m = 0, int64_t t_base = 0, int64_t t_len = -1);
 cudaError_t launch_tc_grad(glm_ctx* c, int64_t t_len = -1, int* nsplit_used = nullptr);
 int tc_nsplit(const glm_ctx* c);
+int tc_nsplit_for(const glm_ctx* c, int mode, int units_per_sm);
 int tc_nsplit_max(const glm_ctx* c);
 int tc_autotune(glm_ctx* c, glm_tune_report_t* rep);
 int tc_autotune_batch(glm_ctx* const* cs, int np, void* dev_g, void* host_g);

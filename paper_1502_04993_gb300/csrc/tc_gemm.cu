@@ -153,6 +153,12 @@ struct TcArgs {
     const float* colc;         // CT: [Tpad][8] column constants (ct_link.cuh)
     const double* tile_span;   // CT: [ntile] seconds covered by each 256-column tile
     float ct_tau;
+    // SELF (MODE 0 grid): row i's own train with its self-delay is X_i at bin t + self_shift
+    int32_t self_shift;
+    const float* W32;          // W (FP32), for W_ii
+    const void* Xhi;           // X_hi, X_lo bin-blocked over the recording
+    const void* Xlo;
+    double* part_self;         // [n][ntile] sums of dt e^U (X_i[t + self_shift] - X_i[t]) per tile
 };
 
 struct Unit {
@@ -223,13 +229,30 @@ __device__ __forceinline__ uint32_t pack16<__half>(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+
+// w as the U product holds it: hi + lo parts, rounded as split_w_kernel rounds them (exact sum in FP32)
+template <typename T16>
+__device__ __forceinline__ float split_sum16(float w);
+template <>
+__device__ __forceinline__ float split_sum16<__nv_bfloat16>(float w) {
+    const float h = __bfloat162float(__float2bfloat16_rn(w));
+    return h + __bfloat162float(__float2bfloat16_rn(w - h));
+}
+template <>
+__device__ __forceinline__ float split_sum16<__half>(float w) {
+    const float h = __half2float(__float2half_rn(w));
+    return h + __half2float(__float2half_rn(w - h));
+}
+
 // CT (MODE 0 only): continuous-time columns.  The epilogue takes, per column m of length D_m, the exact
 // interval integral e^{b} F(u, D_m) of the rate and the interval weight E'_m = e^{b} G(u, D_m) of Eq. 14
 // (ct_link.cuh) in place of dt e^U; the per-tile sums hold e^{b} (duration + sum (F - D)) in seconds.
 // TAU (MODE 0 only): the epilogue also emits, per (row, tile), the partial sums that give dL/dtau.  With v = (W X)_i[t] = U_i[t] - b_i, Z_i[t] = a Z_i[t-1] + v[t-1] (Z = W dX/da), the
 // tile's local Z_loc starts at 0 at its first bin t0, and Z[t] = a^(t-t0) Z[t0] + Z_loc[t]; a per-row
 // combine (reduce.cu) chains the tiles.
-template <int MODE, typename T16, bool TAU, bool BATCH, bool CT = false>
+template <int MODE, typename T16, bool TAU, bool BATCH, bool CT = false, bool SELF = false>
 __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
                    const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1,
@@ -237,6 +260,7 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
     using C = Cfg<MODE>;
     using L = Layout<MODE>;
     static_assert(!CT || (MODE == 0 && !TAU), "the continuous-time epilogue is a U-product epilogue without tau partials");
+    static_assert(!SELF || (MODE == 0 && !TAU && !CT && !BATCH), "the self-delay is a grid U-product epilogue option");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * L::STAGE_BYTES);
@@ -546,11 +570,18 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                 const float dteb = (float)(A.dt * ebi);
                 double rsum = 0.0;
                 bool bad = false;
-                float zl = 0.f, pw = 1.f, p1 = 0.f, p2 = 0.f, p3 = 0.f, p4 = 0.f, spv = 0.f;
-                // the row's spike bins in this tile (tile = 256-bin segment n0 / 256): the first ST_REG in
-                // registers, relative to the tile start; any further ones are read per chunk
+                float zl = 0.f, pw = 1.f, p1 = 0.f, p2 = 0.f, p3 = 0.f, p4 = 0.f;
+                // self-delay: W_ii as the product holds it (hi + lo) and the row's X rows
+                float wii = 0.f;
+                double sself = 0.0;
+                const T16* xsh = reinterpret_cast<const T16*>(A.Xhi);
+                const T16* xsl = reinterpret_cast<const T16*>(A.Xlo);
+                if (SELF && i < A.n) wii = split_sum16<T16>(A.W32[(int64_t)i * A.n + i]);
+                // the row's spike bins in this tile (tile = 256-bin segment n0 / 256), for the spike part of
+                // dL/dtau: the first ST_REG in registers, relative to the tile start; any further ones are read
+                // per chunk.  (The spike part of L is q_i b_i + sum_j W_ij C_ij, formed in the row reduction.)
                 int64_t kb = 0, ke = 0;
-                if (i < A.n) {
+                if (TAU && i < A.n) {
                     const int64_t sgi = (int64_t)i * A.nseg + gtile, o0 = A.offs[i];
                     kb = o0 + A.seg_first[sgi];
                     ke = (gtile + 1 < A.nseg) ? o0 + A.seg_first[sgi + 1] : A.offs[i + 1];
@@ -579,6 +610,22 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                     float s = 0.f;
                     int cnt = 0;
                     uint32_t pk[16];
+                    float dxs[32];  // SELF: X_i[t + self_shift] - X_i[t] over the chunk
+                    if (SELF) {
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) {
+                            const int64_t t = gt0 + c * 32 + e;
+                            const int64_t t2 = t + A.self_shift;  // < Tpad for t < T (Tpad >= T + self_shift)
+                            dxs[e] = 0.f;
+                            if (i < A.n && t < A.T) {
+                                const int64_t o1 = ((t >> 6) * A.n + i) * 64 + (t & 63);
+                                const int64_t o2 = ((t2 >> 6) * A.n + i) * 64 + (t2 & 63);
+                                dxs[e] = (to_f(xsh[o2]) + to_f(xsl[o2])) - (to_f(xsh[o1]) + to_f(xsl[o1]));
+                            }
+                            r[e] = __float_as_uint(fmaf(wii, dxs[e], __uint_as_float(r[e])));
+                        }
+                    }
+                    float ss = 0.f;
 #pragma unroll
                     for (int e = 0; e < 32; e += 2) {
                         const int64_t t = gt0 + c * 32 + e;
@@ -600,9 +647,8 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                         } else {
                             e1 = 0.f;
                         }
-                        if (s0) spv += v0f;
-                        if (s1) spv += v1f;
                         pk[e >> 1] = pack16<T16>(dteb * e0, dteb * e1);
+                        if (SELF) ss = fmaf(e0, dxs[e], fmaf(e1, dxs[e + 1], ss));
                         if (TAU) {
                             p1 = fmaf(e0, pw, p1);
                             p2 = fmaf(e0, zl, p2);
@@ -623,6 +669,7 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                         }
                     }
                     rsum += (double)cnt + (double)s;
+                    if (SELF) sself += (double)ss;
                     if (i < A.n) {
                         uint4* dst = reinterpret_cast<uint4*>(erow + (int64_t)(c >> 1) * A.n * 64 + (c & 1) * 32);
 #pragma unroll
@@ -631,10 +678,8 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                     }
                 }
                 bad |= !(dteb <= 3.0e38f);
-                if (i < A.n) {
-                    A.part_e[(int64_t)i * A.ntile + gtile] = ebi * rsum;
-                    A.part_s[(int64_t)i * A.ntile + gtile] = (double)spv;
-                }
+                if (i < A.n) A.part_e[(int64_t)i * A.ntile + gtile] = ebi * rsum;
+                if (SELF && i < A.n) A.part_self[(int64_t)i * A.ntile + gtile] = A.dt * ebi * sself;
                 if (TAU && i < A.n) {
                     const int64_t o = (int64_t)i * A.ntile + gtile, plane = (int64_t)A.n * A.ntile;
                     A.part_tau[o] = p1;
@@ -794,7 +839,7 @@ cudaError_t tc_prepare_maps(glm_ctx* c) {
     return ok ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int MODE, typename T16, bool TAU = false, bool BATCH = false, bool CT = false>
+template <int MODE, typename T16, bool TAU = false, bool BATCH = false, bool CT = false, bool SELF = false>
 static cudaError_t run(glm_ctx* c, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0,
                        const CUtensorMap& b1, const TcArgs& A, const TcBatch* batch = nullptr, int64_t grid = 0) {
     const size_t smem = Layout<MODE>::SMEM;
@@ -802,12 +847,12 @@ static cudaError_t run(glm_ctx* c, const CUtensorMap& a0, const CUtensorMap& a1,
     cudaError_t e = cudaStreamIsCapturing(c->stream, &cap);
     if (e != cudaSuccess) return e;
     if (cap == cudaStreamCaptureStatusNone) {  // set before the first launch; not during graph capture
-        e = cudaFuncSetAttribute(tc_gemm_kernel<MODE, T16, TAU, BATCH, CT>,
+        e = cudaFuncSetAttribute(tc_gemm_kernel<MODE, T16, TAU, BATCH, CT, SELF>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     if (grid <= 0) grid = A.units < c->sm_count ? A.units : c->sm_count;
-    tc_gemm_kernel<MODE, T16, TAU, BATCH, CT><<<(unsigned)grid, kthreads<MODE, CT>(), smem, c->stream>>>(
+    tc_gemm_kernel<MODE, T16, TAU, BATCH, CT, SELF><<<(unsigned)grid, kthreads<MODE, CT>(), smem, c->stream>>>(
         a0, a1, b0, b1, A, batch);
     return cudaGetLastError();
 }
@@ -845,6 +890,11 @@ static TcArgs base_args(glm_ctx* c) {
     A.colc = c->buf.colc;
     A.tile_span = c->buf.tile_span;
     A.ct_tau = (float)P.tau;
+    A.self_shift = 0;
+    A.W32 = nullptr;
+    A.Xhi = c->buf.X;
+    A.Xlo = c->buf.Xlo;
+    A.part_self = nullptr;
     return A;
 }
 
@@ -886,9 +936,19 @@ cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, boo
         return run<0, __half, false, false, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
     }
     if (tau) {
+        if (P.self_shift > 0) return cudaErrorNotSupported;
         if (P.prec == GLM_PREC_BF16)
             return run<0, __nv_bfloat16, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
         return run<0, __half, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
+    }
+    if (P.self_shift > 0) {
+        if (P.chunk) return cudaErrorNotSupported;
+        A.self_shift = P.self_shift;
+        A.W32 = W;
+        A.part_self = c->buf.part_self;
+        if (P.prec == GLM_PREC_BF16)
+            return run<0, __nv_bfloat16, false, false, false, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
+        return run<0, __half, false, false, false, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
     }
     if (P.prec == GLM_PREC_BF16)
         return run<0, __nv_bfloat16>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
@@ -944,6 +1004,26 @@ cudaError_t launch_tc_grad(glm_ctx* c, int64_t t_len, int* nsplit_used) {
 }
 
 // With X recomputed per chunk, each chunk is filtered here first and the products add up over the chunks.
+// Self-delay: the diagonal of the spike term sums row i's own train as it reaches row i,
+// C_ii = sum_{t in sp(i)} X_i[t + shift]; the product above summed X_i[t].  Warp per row, fixed order.
+template <typename T16>
+__global__ void self_spike_diag_kernel(int32_t n, int32_t shift, const int64_t* __restrict__ offs,
+                                       const int32_t* __restrict__ bins, const T16* __restrict__ xh,
+                                       const T16* __restrict__ xl, double* __restrict__ C) {
+    const int32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    double d = 0.0;
+    for (int64_t k = offs[i] + lane; k < offs[i + 1]; k += 32) {
+        const int64_t t = bins[k], t2 = t + shift;
+        const int64_t o1 = ((t >> 6) * n + i) * 64 + (t & 63), o2 = ((t2 >> 6) * n + i) * 64 + (t2 & 63);
+        d += (double)((to_f(xh[o2]) + to_f(xl[o2])) - (to_f(xh[o1]) + to_f(xl[o1])));
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+    if (lane == 0) C[(int64_t)i * n + i] += d;
+}
+
 cudaError_t launch_tc_spike_term(glm_ctx* c) {
     const Problem& P = c->pb;
     cudaError_t e = cudaSuccess;
@@ -961,6 +1041,19 @@ cudaError_t launch_tc_spike_term(glm_ctx* c) {
         // S X_hi^T and S X_lo^T in one launch: each split runs over its bins of X_hi, then of X_lo
         if ((e = run_products(c, c->tmap[5], bins, &ns, false, &c->tmap[6])) != cudaSuccess) return e;
         if ((e = launch_sum_splits(c, ns, c->buf.C, t0 > 0)) != cudaSuccess) return e;
+    }
+    if (P.self_shift > 0) {  // X stored (no chunks): the whole recording is in the buffers
+        const unsigned blocks = (unsigned)((P.n + 7) / 8);
+        if (P.prec == GLM_PREC_BF16)
+            self_spike_diag_kernel<<<blocks, 256, 0, c->stream>>>(
+                P.n, P.self_shift, c->buf.offs, c->buf.bins, reinterpret_cast<const __nv_bfloat16*>(c->buf.X),
+                reinterpret_cast<const __nv_bfloat16*>(c->buf.Xlo), c->buf.C);
+        else
+            self_spike_diag_kernel<<<blocks, 256, 0, c->stream>>>(
+                P.n, P.self_shift, c->buf.offs, c->buf.bins, reinterpret_cast<const __half*>(c->buf.X),
+                reinterpret_cast<const __half*>(c->buf.Xlo), c->buf.C);
+        c->launches += 1;
+        e = cudaGetLastError();
     }
     return e;
 }
