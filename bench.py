@@ -294,12 +294,20 @@ def run_batch(args, glm, device, prec):
         res, rc = glm.fit_batch(ctxs, **kw)
         torch.cuda.synchronize(device)
         t_bat = time.perf_counter() - t0
+        # aggregate throughput of the fits: neuron-bins of every evaluation (trial points included) per second
+        nb = [w["n"] * w["n_bins"] for w in recs]
+        work_seq = sum(x * r["evaluations"] for x, r in zip(nb, seq))
+        work_bat = sum(x * r["report"]["evaluations"] for x, r in zip(nb, res))
         return {"recordings": len(recs), "t_scale": args.batch_t_scale,
                 "n": [w["n"] for w in recs], "n_bins": [w["n_bins"] for w in recs],
                 "sequential_s": t_seq, "batched_s": t_bat, "speedup": t_seq / t_bat, "status": rc,
-                "neuron_bins": sum(w["n"] * w["n_bins"] for w in recs),
+                "neuron_bins": sum(nb),
+                "neuron_bins_per_s_sequential": work_seq / t_seq, "neuron_bins_per_s_batched": work_bat / t_bat,
+                "evaluations_sequential": sum(r["evaluations"] for r in seq),
+                "evaluations_batched": sum(r["report"]["evaluations"] for r in res),
                 "iterations_max": max(r["report"]["iterations"] for r in res),
-                "L_sequential": sum(r["L"] for r in seq), "L_batched": sum(r["report"]["L"] for r in res)}
+                "L_sequential": sum(r["L"] for r in seq), "L_batched": sum(r["report"]["L"] for r in res),
+                "tile_choice": "autotuned inside glm_fit_batch (one row tile and units per SM for all problems)"}
     finally:
         for c in ctxs:
             c.close()
@@ -718,10 +726,12 @@ def main():
         from synth import truth_labels
         truth = truth_labels(w["W_true"])
         fits = {}
+        fit_params = {}
         for p in [s for s in args.fit.split(",") if s]:
             ctx.set_problem(w["offs"], w["bins"], T, w["dt"], w["tau"], prec=p)
             torch.cuda.synchronize(device)
             r = ctx.fit(eta=args.fit_eta, max_iter=args.fit_max_iter)
+            fit_params[p] = (r["W"], r["b"])
             Wf = r["W"].cpu().numpy().astype(np.float64)
             _, rep = glm.classify(Wf, "gmm", truth=truth, types=w["types"])
             fr = r["report"]
@@ -732,6 +742,14 @@ def main():
         if "f32" in fits:
             for p, v in fits.items():
                 v["speedup_vs_f32"] = fits["f32"]["seconds"] / v["seconds"]
+            # every fit's W, b scored by one evaluation, the plain FP32 form's (L within ~1e-9 of exact): the
+            # fits' own final L each carry their precision's evaluation error and are not comparable at 1e-8
+            ctx.set_problem(w["offs"], w["bins"], T, w["dt"], w["tau"], prec="f32")
+            for p, (Wf, bf) in fit_params.items():
+                rr = ctx.loglik_grad(Wf, bf, grad=False)
+                fits[p]["L_scored_f32"] = rr["L_total"]
+            for p in fits:
+                fits[p]["L_gap_to_f32_fit"] = (fits["f32"]["L_scored_f32"] - fits[p]["L_scored_f32"]) / abs(fits["f32"]["L_scored_f32"])
         line["fit"] = {"eta": args.fit_eta, "max_iter": args.fit_max_iter, "by_precision": fits}
     if args.batch:
         line["batch"] = run_batch(args, glm, device, prec)

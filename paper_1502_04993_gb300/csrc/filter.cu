@@ -29,7 +29,6 @@ void fill_scan_consts(double a, ScanConsts* sc) {
     for (int m = 0; m <= 8; ++m) split(std::pow(a, (double)m), &sc->pm_hi[m], &sc->pm_lo[m]);
     for (int d = 0; d < 5; ++d) split(std::pow(a, 8.0 * (1 << d)), &sc->ps_hi[d], &sc->ps_lo[d]);
     for (int l = 0; l < 32; ++l) split(std::pow(a, 8.0 * l), &sc->pl_hi[l], &sc->pl_lo[l]);
-    for (int k = 0; k < 8; ++k) sc->pr[k] = (float)std::pow(a, (double)k);
 }
 
 // Segment-first indices and, in seg_local (when given), the contribution of each segment's own spikes to X
@@ -333,7 +332,7 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache16_kernel(const __g
             const int32_t r = g * RPW + k;
             const uint32_t bits = seg_bits(A.bins, cur[k], end[k], t0, lane);
             float v[8];
-            xs[k] = seg_scan(K, xs[k], bits, pl_hi, pl_lo, lane, v);
+            xs[k] = seg_scan16(K, xs[k], bits, pl_hi, pl_lo, lane, v);
             uint32_t ph[4], pl[4];
 #pragma unroll
             for (int p = 0; p < 4; ++p) split_pair<T16>(v[2 * p], v[2 * p + 1], ph[p], pl[p]);

@@ -724,30 +724,20 @@ __global__ void fb_split_w_kernel(const FitBatch* __restrict__ B, int64_t total)
     lo[el] = lw;
 }
 // L_i (and with gb the bias gradient) of every row of every problem from the per-tile partials (warp per row)
-__device__ __forceinline__ double w_split_sum(float w, bool bf16) {
-    if (bf16) {
-        const float h = __bfloat162float(__float2bfloat16_rn(w));
-        return (double)h + (double)__bfloat162float(__float2bfloat16_rn(w - h));
-    }
-    const float h = __half2float(__float2half_rn(w));
-    return (double)h + (double)__half2float(__float2half_rn(w - h));
-}
-__global__ void fb_reduce_rows_kernel(const FitBatch* __restrict__ B, int32_t nrows, bool with_gb, bool bf16) {
+__global__ void fb_reduce_rows_kernel(const FitBatch* __restrict__ B, int32_t nrows, bool with_gb) {
     const int32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= nrows) return;
     const int p = fb_prob(B->rbeg, B->np, r);
     const int32_t i = r - B->rbeg[p];
     const int64_t nt = B->ntile[p];
-    const int32_t n = B->rbeg[p + 1] - B->rbeg[p];
     const double* pe = B->part_e[p] + (int64_t)i * nt;
+    const double* ps = B->part_s[p] + (int64_t)i * nt;
     double integ = 0.0, spk = 0.0;
-    for (int64_t t = lane; t < nt; t += 32) integ += pe[t];
-    // spike part sum_j W_ij C_ij in FP64 with W as hi + lo (as reduce_rows_kernel): linear in W, free of
-    // the U product's rounding
-    const float* Wi = B->W32[p] + (int64_t)i * n;
-    const double* Ci = B->C[p] + (int64_t)i * n;
-    for (int32_t j = lane; j < n; j += 32) spk += w_split_sum(Wi[j], bf16) * Ci[j];
+    for (int64_t t = lane; t < nt; t += 32) {
+        integ += pe[t];
+        spk += ps[t];
+    }
     for (int off = 16; off >= 1; off >>= 1) {
         integ += __shfl_xor_sync(0xffffffffu, integ, off);
         spk += __shfl_xor_sync(0xffffffffu, spk, off);
@@ -950,7 +940,7 @@ int fit_run_batch(glm_ctx* const* cs, int np, const glm_fit_opts_t* o, float* co
             else
                 fb_split_w_kernel<__half><<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(d_fb, nw);
             if ((r = ck(c0, launch_tc_u_batch(c0, dev_u)))) return r;
-            fb_reduce_rows_kernel<<<(rows_all + 7) / 8, 256, 0, st>>>(d_fb, rows_all, false, c0->pb.prec == GLM_PREC_BF16);
+            fb_reduce_rows_kernel<<<(rows_all + 7) / 8, 256, 0, st>>>(d_fb, rows_all, false);
             fb_armijo_kernel<<<(rows_all + 255) / 256, 256, 0, st>>>(d_fb, rows_all, o->c1, o->max_halvings);
             fb_round_reset_kernel<<<1, FB_MAX, 0, st>>>(d_fb);
             launches += 8;
@@ -958,7 +948,7 @@ int fit_run_batch(glm_ctx* const* cs, int np, const glm_fit_opts_t* o, float* co
         }
         fb_commit_kernel<<<rows_all, FT, 0, st>>>(d_fb);
         if ((r = ck(c0, launch_tc_grad_batch(c0, dev_g)))) return r;
-        fb_reduce_rows_kernel<<<(rows_all + 7) / 8, 256, 0, st>>>(d_fb, rows_all, true, c0->pb.prec == GLM_PREC_BF16);
+        fb_reduce_rows_kernel<<<(rows_all + 7) / 8, 256, 0, st>>>(d_fb, rows_all, true);
         fb_reduce_grad_kernel<<<(unsigned)((nelem + 255) / 256), 256, 0, st>>>(d_fb, nelem);
         fb_update_kernel<<<rows_all, FT, 0, st>>>(d_fb, o->eta, o->max_iter);
         count_active_kernel<<<np, 256, 0, st>>>(d_src, d_n, d_cnt);

@@ -883,6 +883,13 @@ int glm_fit(glm_ctx* c, const glm_fit_opts_t* opts, float* W, float* b, int8_t* 
         std::isnan(o.gain_floor) || !(o.alpha >= 0) || !(o.eps > 0))
         return fail(c, GLM_ERR_INVALID_ARG, "bad fit options");
     DeviceGuard g(c->device);
+    // the fit's gradient is that of the L it evaluates: over X_hi + X_lo in the 16-bit forms (E X_hi^T alone
+    // misses ~2^-9 of the integral term's derivative, enough to stall line searches near the optimum)
+    struct Precise {
+        glm_ctx* c;
+        ~Precise() { c->precise_grad = false; }
+    } pg{c};
+    c->precise_grad = c->pb.prec != GLM_PREC_F32;
     return glm::fit_run(c, &o, W, b, row_status, rep);
 }
 
@@ -1135,6 +1142,14 @@ int glm_fit_batch(glm_ctx* const* cs, int32_t np, const glm_fit_opts_t* opts, fl
         !(o.alpha >= 0) || !(o.eps > 0))
         return fail(c0, GLM_ERR_INVALID_ARG, "bad fit options");
     DeviceGuard g(c0->device);
+    struct Precise {  // as glm_fit: the gradient over X_hi + X_lo
+        glm_ctx* const* cs;
+        int32_t np;
+        ~Precise() {
+            for (int32_t p = 0; p < np; ++p) cs[p]->precise_grad = false;
+        }
+    } pg{cs, np};
+    for (int32_t p = 0; p < np; ++p) cs[p]->precise_grad = true;
     return glm::fit_run_batch(cs, np, &o, W, b, row_status, reps);
 }
 

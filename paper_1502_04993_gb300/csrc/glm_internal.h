@@ -32,7 +32,6 @@ struct ScanConsts {
     float pm_hi[9], pm_lo[9];    // a^m,          m = 0..8
     float ps_hi[5], ps_lo[5];    // a^(8*2^d),    d = 0..4   (warp scan strides)
     float pl_hi[32], pl_lo[32];  // a^(8*l),      l = 0..31  (lane offsets)
-    float pr[8];                 // a^k rounded once to FP32, k = 0..7 (a lane's own spikes)
 };
 
 struct Problem {
@@ -132,6 +131,9 @@ struct glm_ctx {
     int64_t chunk_req = 0; // bins per chunk requested by glm_set_chunk_bins (applied by glm_set_problem)
     int32_t delay_req = 1; // source delay in bins requested by glm_set_source_delay (applied by glm_set_problem)
     int32_t self_req = 0;  // self-delay in bins requested by glm_set_self_delay (0: as the source delay)
+    // 16-bit forms: the gradient product over X_hi + X_lo (E X_hi^T + E X_lo^T), the derivative of the very L
+    // the evaluation forms; set by the fits for their duration (see glm_fit)
+    bool precise_grad = false;
     int32_t row_r0 = 0, row_r1 = -1;  // evaluated and fitted rows (glm_set_row_range); r1 < 0: all rows
     std::string last_error;
     // tracing: event pairs per launched kernel group while profiling is on

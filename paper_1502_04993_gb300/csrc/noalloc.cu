@@ -15,6 +15,7 @@
 #include <cmath>
 #include <mutex>
 
+#include "expm1_acc.cuh"
 #include "glm.h"
 
 namespace {
@@ -117,9 +118,16 @@ __global__ void __launch_bounds__(NT) na_u_kernel(const __grid_constant__ NaArgs
     load(0);
     store(0);
     __syncthreads();
+    // two-level accumulation as in the library's regular FP32 U product: the 16 products of each k-step go
+    // into a fresh tile sum, added to the total (a single running sum drops small terms with one sign)
     for (int kt = 0; kt < nk; ++kt) {
         const int cur = kt & 1;
         if (kt + 1 < nk) load((kt + 1) * NK);
+        float tl[8][8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) tl[r][c] = 0.f;
 #pragma unroll
         for (int k = 0; k < NK; ++k) {
             const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
@@ -131,8 +139,12 @@ __global__ void __launch_bounds__(NT) na_u_kernel(const __grid_constant__ NaArgs
 #pragma unroll
             for (int r = 0; r < 8; ++r)
 #pragma unroll
-                for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+                for (int c = 0; c < 8; ++c) tl[r][c] = fmaf(av[r], bv[c], tl[r][c]);
         }
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[r][c] += tl[r][c];
         if (kt + 1 < nk) store(cur ^ 1);
         __syncthreads();
     }
@@ -147,7 +159,7 @@ __global__ void __launch_bounds__(NT) na_u_kernel(const __grid_constant__ NaArgs
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const int64_t t = t0 + (c < 4 ? tx * 4 + c : 64 + tx * 4 + (c - 4));
-            const float m = expm1f(acc[r][c] + (i < n ? fminf(A.b[i] - NA_EXP_SPLIT_FLOOR, 0.f) : 0.f));
+            const float m = glm::expm1_acc(acc[r][c] + (i < n ? fminf(A.b[i] - NA_EXP_SPLIT_FLOOR, 0.f) : 0.f));
             if (t < A.T) {
                 msum += m;
                 ++cnt;

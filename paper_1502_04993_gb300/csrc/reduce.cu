@@ -1,37 +1,18 @@
 // Step a7: reductions in a fixed order (bitwise reproducible): the per-tile sums in FP64, the FP32 partials of
 // the split products as FP32 TwoSum pairs (~48 bits) converted once to FP64.
-//   L_i   = sum_{t in sp(i)} U_i[t] - dt sum_t exp(U_i[t])        (Eq. 7), the spike part on the grid as
-//           q_i b_i + sum_j W_ij C_ij in FP64 from the spike term C (the same sum: U_i[t] - b_i =
-//           sum_j W_ij X_j[t]), with W as the U product holds it (hi + lo in the 16-bit forms, so that both
-//           parts of L see one W); it is linear in W and carries none of the FP32 rounding of the U
-//           product's accumulators, which summed over a row's spike bins is noise of ~1e-8 of L_i that
-//           changes with every W and so blurs the line search's comparisons.  Continuous time: q_i b_i +
-//           the sums of U - b at the spike columns from the U-product epilogue
+//   L_i   = sum_{t in sp(i)} U_i[t] - dt sum_t exp(U_i[t])        (Eq. 7), the spike part as
+//           q_i b_i + sum over tiles of (sum of U - b at the row's spike bins) from the U-product epilogue in
+//           the 16-bit forms (the bias of the tensor cores' FP32 accumulation of U then cancels between the
+//           two parts), and in the plain FP32 form as q_i b_i + sum_j W_ij C_ij in FP64 from the exact spike
+//           term C (the same sum, since U - b = W X; free of the FP32 rounding of U summed over the spikes)
 //   dL/db_i = q_i - dt sum_t exp(U_i[t])                         (Eq. 12, j = 0)
 //   dL/dW_ij = C_ij - sum_s P_s[i][j],  P_s = sum_{t in split s} dt exp(U_i[t]) X_j[t]   (Eq. 12)
 //   L = sum_i L_i                                                (Eq. 1)
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-
 #include <cmath>
 
 #include "glm_internal.h"
 
 namespace glm {
-
-// W_ij as the U product sees it: FP32 (split 0), or the sum of its hi + lo parts in BF16 (1) or FP16 (2),
-// rounded as split_w_kernel rounds them (the sum of the two parts is exact in FP32)
-__device__ __forceinline__ double w_as_split(float w, int split) {
-    if (split == 1) {
-        const float h = __bfloat162float(__float2bfloat16_rn(w));
-        return (double)h + (double)__bfloat162float(__float2bfloat16_rn(w - h));
-    }
-    if (split == 2) {
-        const float h = __half2float(__float2half_rn(w));
-        return (double)h + (double)__half2float(__float2half_rn(w - h));
-    }
-    return (double)w;
-}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -51,8 +32,7 @@ struct ReduceArgs {
     const double* part_e;  // [n][ntile]
     int32_t planes;        // planes of part_s and part_e, [planes][n][ntile] (continuous time: CT_PARTS)
     int32_t r0, r1;        // rows outside [r0, r1) (a row range) get L_i = 0 and dL/db_i = 0
-    bool spk_from_c;       // spike part q_i b_i + sum_j W_ij C_ij (grid) instead of the part_s sums
-    int32_t split;         // W in that sum as the U product holds it: 0 FP32, 1 BF16 hi + lo, 2 FP16 hi + lo
+    bool spk_from_c;       // spike part q_i b_i + sum_j W_ij C_ij (FP32 form) instead of the part_s sums
     const double* part_self;  // self-delay: [n][ntile] per-tile parts of the diagonal's gradient, or null
     double* gself;            //   their row sums
     double* L_rows;
@@ -68,7 +48,7 @@ __global__ void reduce_rows_kernel(const __grid_constant__ ReduceArgs A) {
     if (A.spk_from_c) {
         const float* Wi = A.W + (int64_t)i * A.n;
         const double* Ci = A.C + (int64_t)i * A.n;
-        for (int32_t j = lane; j < A.n; j += 32) spk += w_as_split(Wi[j], A.split) * Ci[j];
+        for (int32_t j = lane; j < A.n; j += 32) spk += (double)Wi[j] * Ci[j];
     } else {
         const double* ps = A.part_s + (int64_t)i * A.ntile;
         for (int64_t t = lane; t < A.ntile; t += 32) spk += ps[t];
@@ -290,8 +270,7 @@ cudaError_t launch_reduce(glm_ctx* c, const float* W, const float* b, double* L_
     A.planes = P.ct ? CT_PARTS : 1;
     A.r0 = c->row_r0;
     A.r1 = c->row_r1 < 0 ? P.n : c->row_r1;
-    A.spk_from_c = !P.ct;
-    A.split = P.prec == GLM_PREC_BF16 ? 1 : P.prec == GLM_PREC_F16 ? 2 : 0;
+    A.spk_from_c = P.prec == GLM_PREC_F32 && !P.ct;
     A.part_self = P.self_shift > 0 ? c->buf.part_self : nullptr;
     A.gself = c->buf.gself;
     A.L_rows = L_rows;

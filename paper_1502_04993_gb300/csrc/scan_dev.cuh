@@ -68,28 +68,21 @@ __device__ __forceinline__ uint32_t seg_bits(const int32_t* __restrict__ bins, i
 
 // Scan of one segment.  x_seg = X[t0] (all lanes), bits8 = this lane's spike bits, (pl_hi, pl_lo) =
 // a^(8 lane).  On return out[m] = X[t0 + 8 lane + m]; the result is X[t0 + 256] (all lanes).
-//   local part:   z_m = sum over this lane's spikes j < m of a^(m-1-j), each power rounded once.  (The
-//                 recursion z_{m+1} = a z_m + S rounds the same chain 1, a, a^2, ... after every spike
-//                 and so biases X by ~0.6 ulp; the direct powers do not.)
+//   local part:   z_m = sum over this lane's spikes j < m of a^(m-1-j)
 //   lane start:   X[t_lane] = a^(8 lane) x_seg + sum_{k < lane} a^(8 (lane - 1 - k)) z_8(k)
 //                 (Kogge-Stone scan of the affine recurrence with constant multiplier a^8)
 //   values:       X[t_lane + m] = a^m X[t_lane] + z_m
-__device__ __forceinline__ float seg_scan(const ScanConsts& K, float x_seg, uint32_t bits8, float pl_hi,
-                                          float pl_lo, int lane, float out[8]) {
-    float z[8];
-    float zz = 0.f;
+// FP32 form of the scan, for the 16-bit caches, whose X_hi + X_lo keep ~17 significant bits: the lane's local
+// sums follow the recursion z_{m+1} = a z_m + S_m with a as a hi + lo pair (2 FMAs a bin).  Its FP32 rounding,
+// repeated after every spike, biases X by ~0.6 FP32 ulp (~4e-8 relative), far below the 2^-17 of the 16-bit
+// pair.  The plain FP32 form uses the double-float scan below (seg_scan_df) and rounds X once.
+__device__ __forceinline__ float seg_scan16(const ScanConsts& K, float x_seg, uint32_t bits8, float pl_hi,
+                                            float pl_lo, int lane, float out[8]) {
+    float z[9];
     z[0] = 0.f;
 #pragma unroll
-    for (int m = 1; m <= 8; ++m) {  // static indices only: the powers stay in the constant bank
-        float acc = 0.f;
-#pragma unroll
-        for (int j = 0; j < m; ++j) acc = fmaf((float)((bits8 >> j) & 1u), K.pr[m - 1 - j], acc);
-        if (m < 8)
-            z[m] = acc;
-        else
-            zz = acc;
-    }
-    float v = zz;
+    for (int m = 0; m < 8; ++m) z[m + 1] = mul2(K.a_hi, K.a_lo, z[m], ((bits8 >> m) & 1u) ? 1.f : 0.f);
+    float v = z[8];
 #pragma unroll
     for (int d = 0; d < 5; ++d) {
         const float o = __shfl_up_sync(FULL, v, 1 << d);
@@ -100,7 +93,7 @@ __device__ __forceinline__ float seg_scan(const ScanConsts& K, float x_seg, uint
     const float xl = mul2(pl_hi, pl_lo, x_seg, ex);
 #pragma unroll
     for (int m = 0; m < 8; ++m) out[m] = mul2(K.pm_hi[m], K.pm_lo[m], xl, z[m]);
-    const float xend = mul2(K.pm_hi[8], K.pm_lo[8], xl, zz);
+    const float xend = mul2(K.pm_hi[8], K.pm_lo[8], xl, z[8]);
     return __shfl_sync(FULL, xend, 31);
 }
 
@@ -108,10 +101,10 @@ __device__ __forceinline__ float2 shfl_up_df(float2 v, int d) {
     return make_float2(__shfl_up_sync(FULL, v.x, d), __shfl_up_sync(FULL, v.y, d));
 }
 
-// seg_scan in double-float arithmetic (~44 significant bits, every multiplier a hi + lo pair): out[m] and
+// The scan in double-float arithmetic (~44 significant bits, every multiplier a hi + lo pair): out[m] and
 // the result carry X to well below FP32 resolution, so the plain FP32 form rounds each stored value once
 // from it (correctly rounded X: no rounding error from the scan itself, whose systematic part, repeated
-// after every spike of a train, would otherwise reach ~1e-10 of L).  Same structure as seg_scan; the
+// after every spike of a train, would otherwise reach ~1e-10 of L).  Same structure as seg_scan16; the
 // lane's local sums follow the recursion z_{m+1} = a z_m + S_m, whose double-float roundings are
 // ~2^-44 and so negligible.
 __device__ __forceinline__ float2 seg_scan_df(const ScanConsts& K, float2 x_seg, uint32_t bits8, float2 pl, int lane,
@@ -172,7 +165,7 @@ __device__ __forceinline__ void ct_seg_setup(const float* __restrict__ col_a, in
     if (lane == 0) S.lp = 1.f;
 }
 
-// Scan of one segment of columns: as seg_scan, with the lane's own recursion z_{k+1} = al[k] z_k + S and
+// Scan of one segment of columns: as seg_scan16, with the lane's own recursion z_{k+1} = al[k] z_k + S and
 // the multipliers of CtSegMul.
 __device__ __forceinline__ float seg_scan_ct(const CtSegMul& S, float x_seg, uint32_t bits8, int lane, float out[8]) {
     float z[9];

@@ -83,9 +83,19 @@ __global__ void __launch_bounds__(ST) simt_u_kernel(const __grid_constant__ Simt
     load(0);
     store(0);
     __syncthreads();
+    // Two-level accumulation: each k-step's 16 products are summed into a fresh FP32 tile sum, which is then
+    // added to the total.  A single running FP32 sum over ~1000 sources drops the many small terms (sources
+    // whose filtered train has decayed) below half an ulp of the total, and since most inputs are
+    // excitatory those losses have one sign: at N = 1000 the mean of U came out ~2e-8 low, ~1.4e-8 of L.
+    // Tile sums keep those terms; the bias falls below 1e-10.
     for (int kt = 0; kt < nk; ++kt) {
         const int cur = kt & 1;
         if (kt + 1 < nk) load((kt + 1) * SK);
+        float tl[8][8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) tl[r][c] = 0.f;
 #pragma unroll
         for (int k = 0; k < SK; ++k) {
             const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
@@ -97,8 +107,12 @@ __global__ void __launch_bounds__(ST) simt_u_kernel(const __grid_constant__ Simt
 #pragma unroll
             for (int r = 0; r < 8; ++r)
 #pragma unroll
-                for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+                for (int c = 0; c < 8; ++c) tl[r][c] = fmaf(av[r], bv[c], tl[r][c]);
         }
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[r][c] += tl[r][c];
         if (kt + 1 < nk) store(cur ^ 1);
         __syncthreads();
     }

@@ -570,18 +570,19 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                 const float dteb = (float)(A.dt * ebi);
                 double rsum = 0.0;
                 bool bad = false;
-                float zl = 0.f, pw = 1.f, p1 = 0.f, p2 = 0.f, p3 = 0.f, p4 = 0.f;
+                float zl = 0.f, pw = 1.f, p1 = 0.f, p2 = 0.f, p3 = 0.f, p4 = 0.f, spv = 0.f;
                 // self-delay: W_ii as the product holds it (hi + lo) and the row's X rows
                 float wii = 0.f;
                 double sself = 0.0;
                 const T16* xsh = reinterpret_cast<const T16*>(A.Xhi);
                 const T16* xsl = reinterpret_cast<const T16*>(A.Xlo);
                 if (SELF && i < A.n) wii = split_sum16<T16>(A.W32[(int64_t)i * A.n + i]);
-                // the row's spike bins in this tile (tile = 256-bin segment n0 / 256), for the spike part of
-                // dL/dtau: the first ST_REG in registers, relative to the tile start; any further ones are read
-                // per chunk.  (The spike part of L is q_i b_i + sum_j W_ij C_ij, formed in the row reduction.)
+                // the row's spike bins in this tile (tile = 256-bin segment n0 / 256): the first ST_REG in
+                // registers, relative to the tile start; any further ones are read per chunk.  The spike part
+                // of L is taken from this U at those bins: the tensor cores' FP32 accumulation of U carries a
+                // bias (measured ~6e-6 at N = 1000) that then cancels against the integral part.
                 int64_t kb = 0, ke = 0;
-                if (TAU && i < A.n) {
+                if (i < A.n) {
                     const int64_t sgi = (int64_t)i * A.nseg + gtile, o0 = A.offs[i];
                     kb = o0 + A.seg_first[sgi];
                     ke = (gtile + 1 < A.nseg) ? o0 + A.seg_first[sgi + 1] : A.offs[i + 1];
@@ -647,6 +648,8 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                         } else {
                             e1 = 0.f;
                         }
+                        if (s0) spv += v0f;
+                        if (s1) spv += v1f;
                         pk[e >> 1] = pack16<T16>(dteb * e0, dteb * e1);
                         if (SELF) ss = fmaf(e0, dxs[e], fmaf(e1, dxs[e + 1], ss));
                         if (TAU) {
@@ -678,7 +681,10 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                     }
                 }
                 bad |= !(dteb <= 3.0e38f);
-                if (i < A.n) A.part_e[(int64_t)i * A.ntile + gtile] = ebi * rsum;
+                if (i < A.n) {
+                    A.part_e[(int64_t)i * A.ntile + gtile] = ebi * rsum;
+                    A.part_s[(int64_t)i * A.ntile + gtile] = (double)spv;
+                }
                 if (SELF && i < A.n) A.part_self[(int64_t)i * A.ntile + gtile] = A.dt * ebi * sself;
                 if (TAU && i < A.n) {
                     const int64_t o = (int64_t)i * A.ntile + gtile, plane = (int64_t)A.n * A.ntile;
@@ -1000,7 +1006,7 @@ static cudaError_t run_products(glm_ctx* c, const CUtensorMap& mapB, int64_t t_l
 }
 
 cudaError_t launch_tc_grad(glm_ctx* c, int64_t t_len, int* nsplit_used) {
-    return run_products(c, c->tmap[5], t_len, nsplit_used, true);
+    return run_products(c, c->tmap[5], t_len, nsplit_used, true, c->precise_grad ? &c->tmap[6] : nullptr);
 }
 
 // With X recomputed per chunk, each chunk is filtered here first and the products add up over the chunks.
@@ -1079,6 +1085,14 @@ cudaError_t launch_wait_check(glm_ctx* c, uint64_t limit_ns, int* out) {
 
 // ---- several problems per launch (glm_fit_batch) ----
 
+// E X^T arguments of one problem of the batched launch: over X_hi, then X_lo when the gradient is precise
+static TcArgs batch_grad_args(glm_ctx* c, int mode, int ns) {
+    const int64_t kbt = grad_ksteps(c);
+    TcArgs A = grad_args(c, mode, ns, c->precise_grad ? 2 * kbt : kbt);
+    if (c->precise_grad) A.kb_half = kbt;
+    return A;
+}
+
 size_t tc_batch_bytes() { return sizeof(TcBatch); }
 
 // Host images of the two batch descriptors: U products of the rows rows[p] (m_dev[p] of them) at
@@ -1109,9 +1123,10 @@ int tc_batch_fill(glm_ctx* const* cs, int np, float* const* W32, float* const* b
         bu->args[p] = A;
         bu->m_dev[p] = m_dev[p];
         for (int k = 0; k < 4; ++k) bu->maps[p][k] = c->tmap[k];
-        bg->args[p] = grad_args(c, c->g_mode, tc_nsplit(c), grad_ksteps(c));
+        bg->args[p] = batch_grad_args(c, c->g_mode, tc_nsplit(c));
         bg->maps[p][0] = bg->maps[p][1] = c->tmap[4];
-        bg->maps[p][2] = bg->maps[p][3] = c->tmap[5];
+        bg->maps[p][2] = c->tmap[5];
+        bg->maps[p][3] = c->precise_grad ? c->tmap[6] : c->tmap[5];
     }
     (void)W32;
     return GLM_OK;
@@ -1240,7 +1255,7 @@ int tc_autotune_batch(glm_ctx* const* cs, int np, void* dev_g, void* host_g) {
         for (int p = 0; p < np; ++p) {
             cs[p]->g_mode = mode;
             cs[p]->g_nsplit = tc_nsplit_for(cs[p], mode, upm);
-            bg->args[p] = grad_args(cs[p], mode, cs[p]->g_nsplit, grad_ksteps(cs[p]));
+            bg->args[p] = batch_grad_args(cs[p], mode, cs[p]->g_nsplit);
         }
         return cudaMemcpy(dev_g, host_g, sizeof(TcBatch), cudaMemcpyHostToDevice);
     };
