@@ -64,16 +64,20 @@ extern "C" {
 #define GLM_ERR_UNSUPPORTED (-10)       /* valid request outside what the library implements */
 
 /* ---- precision of the contractions U = b + W X and G = R X^T ----
- * GLM_PREC_F32:  the plain FP32 form.  X and exp-rates stored in FP32,
- *                SIMT FP32 products on CUDA cores, FP64 sums across tiles.
- * GLM_PREC_BF16: tcgen05 tensor cores.  X and the rates dt*exp(U) stored in
- *                BF16; W split into hi + lo BF16 parts so that
- *                W_hi X + W_lo X keeps W to ~16 significant bits; FP32
- *                accumulation in tensor memory; FP64 sums across tiles.
- * GLM_PREC_F16:  as GLM_PREC_BF16 with IEEE half instead of BF16.
- * In every precision the spike term sum_t S_i[t] X_j[t] (Eq. 12, the part
- * that does not depend on W, computed once per problem as Sec. 2.3.3 and
- * 2.6.1 advise) is summed from FP32 X in a double-float (hi + lo) pair. */
+ * GLM_PREC_F32:  the plain FP32 form.  X (correctly rounded from a
+ *                double-float scan) and the rates stored in FP32, SIMT FP32
+ *                products on CUDA cores, FP64 sums across tiles; the spike
+ *                term sum_t S_i[t] X_j[t] (Eq. 12, the part that does not
+ *                depend on W, computed once per problem as Sec. 2.3.3 and
+ *                2.6.1 advise) summed from double-float X.
+ * GLM_PREC_BF16: tcgen05 tensor cores.  W split into hi + lo BF16 parts, so
+ *                that W_hi X + W_lo X keeps W to ~16 significant bits; X held
+ *                as X_hi + X_lo BF16 parts (U adds W_hi X_lo) unless
+ *                glm_set_x_split(ctx, 0) asks for X_hi alone; the rates
+ *                dt*exp(U) stored in BF16; FP32 accumulation in tensor
+ *                memory; FP64 sums across tiles.  The spike term is the
+ *                tensor-core product S X^T over the same X.
+ * GLM_PREC_F16:  as GLM_PREC_BF16 with IEEE half instead of BF16. */
 typedef enum { GLM_PREC_F32 = 0, GLM_PREC_BF16 = 1, GLM_PREC_F16 = 2 } glm_prec_t;
 
 /* element types for glm_filter outputs */
@@ -366,6 +370,16 @@ int glm_cross_validate(glm_ctx* ctx_train, glm_ctx* ctx_valid, const glm_fit_opt
  * (default) stores X for the whole recording.  Ignored for GLM_PREC_F32 and when chunk_bins covers the
  * recording.  Chunked problems cannot be batched (glm_fit_batch). */
 int glm_set_chunk_bins(glm_ctx* ctx, int64_t chunk_bins);
+
+/* How the 16-bit grid forms hold X (Eq. 4's filtered trains), for the next glm_set_problem.  split = 1
+ * (default): X = X_hi + X_lo, two 16-bit arrays; U takes three tensor-core products (W_hi X_hi, W_lo X_hi,
+ * W_hi X_lo) and the spike term two (S X_hi^T, S X_lo^T), and X keeps ~16 significant bits in BF16 and ~22
+ * in F16.  split = 0: X_hi alone, the round-to-nearest 16-bit X; U takes two products (W_hi X, W_lo X),
+ * the spike term and E X^T one each, and the filter writes half the bytes of X.  With F16 the single X keeps
+ * 11 significant bits, which holds L within ~3e-7 of the FP64 value at N = 1000 (BF16's 8 bits do not: its
+ * X rounding moves L by ~6e-6).  Ignored for GLM_PREC_F32 and the continuous-time form (whose columns are
+ * always split).  Returns GLM_OK, or INVALID_ARG for split other than 0 or 1. */
+int glm_set_x_split(glm_ctx* ctx, int32_t split);
 
 /* ---- autotuner of the gradient product's tile shape ----
  * (no counterpart in the paper.)  Times the gradient product E X^T of the current problem for row tiles of

@@ -85,6 +85,7 @@ SIGNATURES["glm_fit_batch"] = ([_vp, _i32, ctypes.POINTER(FitOpts), _vp, _vp, _v
 SIGNATURES["glm_autotune"] = ([_vp, _vp], ctypes.c_int)
 SIGNATURES["glm_set_grad_tile"] = ([_vp, _i32, _i32, ctypes.POINTER(_i32)], ctypes.c_int)
 SIGNATURES["glm_set_chunk_bins"] = ([_vp, _i64], ctypes.c_int)
+SIGNATURES["glm_set_x_split"] = ([_vp, _i32], ctypes.c_int)
 SIGNATURES["glm_set_source_delay"] = ([_vp, _i32], ctypes.c_int)
 SIGNATURES["glm_set_self_delay"] = ([_vp, _i32], ctypes.c_int)
 SIGNATURES["glm_set_row_range"] = ([_vp, _i32, _i32], ctypes.c_int)
@@ -496,6 +497,11 @@ class GLM:
     def set_chunk_bins(self, chunk_bins: int):
         """Recompute X in chunks of this many bins instead of storing it (applies to the next set_problem)."""
         self._check(self.lib.glm_set_chunk_bins(self.h, int(chunk_bins)), "glm_set_chunk_bins")
+
+    def set_x_split(self, split: bool):
+        """16-bit grid forms: hold X as X_hi + X_lo (True, default) or as one 16-bit X (False); applies to
+        the next set_problem (glm_set_x_split)."""
+        self._check(self.lib.glm_set_x_split(self.h, int(bool(split))), "glm_set_x_split")
 
     def set_grad_tile(self, mode: int, units_per_sm: int) -> int:
         """Force one of the autotuner's gradient-product tile shapes; returns the resulting bin splits."""

@@ -293,9 +293,10 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache_f32_kernel(const _
 }
 
 // 16-bit caches: X_hi and X_lo, X_lo = X - X_hi rounded again, both bin-blocked [Tpad / 64][n][64] (bins
-// [64 b, 64 b + 64) of row r at (b n + r) 64), the layout the tensor-core products read.  One warp per
-// (RPW rows, 4096-bin chunk): each lane stores its 8 bins of a row as one 16-byte word of X_hi and one of
-// X_lo, so every warp store covers four whole 128-byte lines.
+// [64 b, 64 b + 64) of row r at (b n + r) 64), the layout the tensor-core products read; X_hi alone (the
+// round-to-nearest 16-bit X) when A.Xlo is null.  One warp per (RPW rows, 4096-bin chunk): each lane stores
+// its 8 bins of a row as one 16-byte word of X_hi and one of X_lo, so every warp store covers four whole
+// 128-byte lines.
 template <typename T16, int RPW>
 __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache16_kernel(const __grid_constant__ ScanConsts K,
                                                                        const __grid_constant__ FilterArgs A) {
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache16_kernel(const __g
                 const int64_t tb = tl - A.s_begin * SEG;  // bin within the buffers
                 const int64_t o = ((tb >> 6) * A.n + r) * 64 + (tb & 63);
                 *reinterpret_cast<uint4*>(Xh + o) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-                *reinterpret_cast<uint4*>(Xl + o) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+                if (Xl) *reinterpret_cast<uint4*>(Xl + o) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
                 if (A.S) {  // the sources are the rows' own spikes: bits is also row r's raster here
                     uint32_t sw[4];
 #pragma unroll

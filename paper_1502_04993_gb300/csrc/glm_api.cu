@@ -265,7 +265,7 @@ int alloc_problem(glm_ctx* c) {
         (rc = ws_alloc_t(c, &B.part_e, (size_t)n * ntile * (P.ct ? CT_PARTS : 1))) ||
         (rc = ws_alloc_t(c, &B.part_g, nn * (tensor ? tc_nsplit_max(c) : grad_nsplit(c)))) ||
         (rc = ws_alloc_t(c, &B.flags, 4)) || (rc = ws_alloc_t(c, &B.Lrows, n)) || (rc = ws_alloc_t(c, &B.scal, 8)) ||
-        (rc = ws_alloc_t(c, &B.eb, n)) || (tensor && (rc = ws_alloc(c, &B.Xlo, (size_t)P.n * P.Tc * 2))) ||
+        (rc = ws_alloc_t(c, &B.eb, n)) || (P.xlo && (rc = ws_alloc(c, &B.Xlo, (size_t)P.n * P.Tc * 2))) ||
         (rc = ws_alloc_t(c, &B.part_s, (size_t)n * ntile * (P.ct ? CT_PARTS : 1))) ||
         (tensor && (rc = ws_alloc(c, &B.Wsplit, 2 * (size_t)n * B.ldn * 2)))) {
         free_all(c);
@@ -574,7 +574,8 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
         const int64_t chunk = (tensor && c->chunk_req > 0 && round_up(c->chunk_req, 16 * SEG) < round_up(n_bins, SEG))
                                   ? round_up(c->chunk_req, 16 * SEG) : 0;
         if (c->has_problem && !O.ct && O.n == n && O.T == n_bins && O.q == offs[n] && O.prec == prec &&
-            O.chunk == chunk && O.delay_bins == c->delay_req && c->delay_req <= 1) {
+            O.chunk == chunk && O.delay_bins == c->delay_req && c->delay_req <= 1 &&
+            O.xlo == (tensor && c->xsplit_req)) {
             if ((rc = stage_spikes(c, n, n_bins, offs, bins))) return rc;
             c->has_problem = false;
             Problem& P = c->pb;
@@ -612,6 +613,7 @@ int glm_set_problem(glm_ctx* c, int32_t n, int64_t n_bins, double dt, double tau
     P.nseg = (n_bins + P.self_shift + SEG - 1) / SEG;
     P.Tpad = P.nseg * SEG;
     P.prec = prec;
+    P.xlo = tensor && c->xsplit_req;
     P.chunk = 0;
     // chunks start on the filter's 4096-bin units, so X does not depend on the chunking
     if (tensor && c->chunk_req > 0 && round_up(c->chunk_req, 16 * SEG) < P.Tpad) P.chunk = round_up(c->chunk_req, 16 * SEG);
@@ -712,6 +714,7 @@ int glm_set_problem_ct(glm_ctx* c, int32_t n, double t_begin, double t_end, doub
     P.q = q;
     P.qa = qa;
     P.prec = prec;
+    P.xlo = true;  // the continuous-time columns are always held as V_hi + V_lo
     P.ct = true;
     P.t_begin = t_begin;
     P.t_end = t_end;
@@ -883,13 +886,13 @@ int glm_fit(glm_ctx* c, const glm_fit_opts_t* opts, float* W, float* b, int8_t* 
         std::isnan(o.gain_floor) || !(o.alpha >= 0) || !(o.eps > 0))
         return fail(c, GLM_ERR_INVALID_ARG, "bad fit options");
     DeviceGuard g(c->device);
-    // the fit's gradient is that of the L it evaluates: over X_hi + X_lo in the 16-bit forms (E X_hi^T alone
+    // the fit's gradient is that of the L it evaluates: over X_hi + X_lo in the split 16-bit forms (E X_hi^T alone
     // misses ~2^-9 of the integral term's derivative, enough to stall line searches near the optimum)
     struct Precise {
         glm_ctx* c;
         ~Precise() { c->precise_grad = false; }
     } pg{c};
-    c->precise_grad = c->pb.prec != GLM_PREC_F32;
+    c->precise_grad = c->pb.xlo;
     return glm::fit_run(c, &o, W, b, row_status, rep);
 }
 
@@ -1092,6 +1095,13 @@ int glm_set_chunk_bins(glm_ctx* c, int64_t chunk_bins) {
     return GLM_OK;
 }
 
+int glm_set_x_split(glm_ctx* c, int32_t split) {
+    if (!c) return GLM_ERR_INVALID_ARG;
+    if (split != 0 && split != 1) return fail(c, GLM_ERR_INVALID_ARG, "split must be 0 or 1");
+    c->xsplit_req = split == 1;
+    return GLM_OK;
+}
+
 int glm_autotune(glm_ctx* c, glm_tune_report_t* rep) {
     if (!c) return GLM_ERR_INVALID_ARG;
     if (!c->has_problem) return fail(c, GLM_ERR_NO_PROBLEM, "no problem set");
@@ -1149,7 +1159,7 @@ int glm_fit_batch(glm_ctx* const* cs, int32_t np, const glm_fit_opts_t* opts, fl
             for (int32_t p = 0; p < np; ++p) cs[p]->precise_grad = false;
         }
     } pg{cs, np};
-    for (int32_t p = 0; p < np; ++p) cs[p]->precise_grad = true;
+    for (int32_t p = 0; p < np; ++p) cs[p]->precise_grad = cs[p]->pb.xlo;
     return glm::fit_run_batch(cs, np, &o, W, b, row_status, reps);
 }
 

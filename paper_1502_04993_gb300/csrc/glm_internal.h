@@ -58,6 +58,9 @@ struct Problem {
     // bins, every other train after delay_bins; X_i with the self-delay is X_i at bin t + self_shift, so the
     // buffers extend at least self_shift bins past T (Tpad >= T + self_shift)
     int32_t self_shift = 0;
+    // 16-bit forms: X held as the pair X_hi + X_lo (true), or as X_hi alone (false: one 16-bit X, the U
+    // product W_hi X + W_lo X and the spike term S X^T without their X_lo products)
+    bool xlo = false;
 };
 
 // Device buffers owned by a context.  Row-major everywhere; ld* in elements.
@@ -71,7 +74,7 @@ struct Buffers {
     double* C = nullptr;          // [n][n]      spike term
     double* C_part = nullptr;     // [parts][n][n] (plain FP32 form)
     void* X = nullptr;            // F32: float [n][Tpad]; 16-bit: [n][Tpad]
-    void* Xlo = nullptr;          // 16-bit only: X_lo = X - X_hi, bin-blocked over Tc bins
+    void* Xlo = nullptr;          // 16-bit forms with the X split: X_lo = X - X_hi, bin-blocked over Tc bins
     double* Gacc = nullptr;       // chunked: [n][n] E X^T summed over the chunks
     int64_t ldn = 0;              // leading dim of the W parts (n rounded up to 64)
     void* E = nullptr;            // F32: float [n][Tpad] dt exp(U); 16-bit: the same, bin-blocked
@@ -131,6 +134,7 @@ struct glm_ctx {
     int64_t chunk_req = 0; // bins per chunk requested by glm_set_chunk_bins (applied by glm_set_problem)
     int32_t delay_req = 1; // source delay in bins requested by glm_set_source_delay (applied by glm_set_problem)
     int32_t self_req = 0;  // self-delay in bins requested by glm_set_self_delay (0: as the source delay)
+    bool xsplit_req = true;  // X as X_hi + X_lo in the 16-bit grid forms (glm_set_x_split)
     // 16-bit forms: the gradient product over X_hi + X_lo (E X_hi^T + E X_lo^T), the derivative of the very L
     // the evaluation forms; set by the fits for their duration (see glm_fit)
     bool precise_grad = false;

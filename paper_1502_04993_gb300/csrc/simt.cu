@@ -17,6 +17,9 @@ constexpr int SB = 128;   // tile edge
 constexpr int SK = 16;    // k step
 constexpr int ST = 256;   // threads
 constexpr int G_INNER = 1024;  // bins accumulated in the inner FP32 sum of the gradient product
+// row stride (floats) of the operand tiles in shared memory: 16-byte aligned rows, and the transposing
+// stores of four k-rows by one warp fall into two banks per address group instead of four
+constexpr int SBP = SB + 4;
 
 int simt_tile_t() { return SB; }
 
@@ -30,6 +33,7 @@ struct SimtUArgs {
     const float* X;   // [n][Tpad]
     float* E;         // [n][Tpad]
     double* part_e;   // [n][ntile]
+    int64_t ntile;    // bin tiles, Tpad / 128
     int* flags;
     const int32_t* rows;  // evaluated rows (null: all n); tile row l is row rows[l] for l < m
     int32_t m;
@@ -40,12 +44,22 @@ __device__ __forceinline__ int32_t row_of(const SimtUArgs& A, int32_t l) {
 }
 
 // U tile rows i0..i0+127 (of the evaluated rows), bins t0..t0+127.  A = W (row-major, K contiguous), B = X (K x N, N contiguous).
-__global__ void __launch_bounds__(ST) simt_u_kernel(const __grid_constant__ SimtUArgs A) {
-    __shared__ __align__(16) float As[2][SK][SB];
-    __shared__ __align__(16) float Bs[2][SK][SB];
+// Blocks run row tile fastest (block id = bin tile * mt + row tile): the row tiles of one bin tile read the
+// same X tile while it is in L2.  The inner k loop is unrolled by four with the next k-row's operands read
+// ahead into registers, and the epilogue runs as a rolled loop over rows staged in shared memory: fully
+// unrolled, the k-tile body and the 64 inlined exponentials of the epilogue outgrew the instruction cache
+// (ncu: "no instruction" was the largest stall).
+constexpr int EPI_LD = SB + 4;  // row stride of the epilogue staging (floats): 16-byte rows, fewer bank conflicts
+__global__ void __launch_bounds__(ST, 1) simt_u_kernel(const __grid_constant__ SimtUArgs A) {
+    // operands: As[2][SK][SBP] then Bs[2][SK][SBP]; after the k loop the same memory stages 64 rows of U
+    __shared__ __align__(16) float sm[(4 * SK * SBP > 64 * EPI_LD) ? 4 * SK * SBP : 64 * EPI_LD];
+    auto As = reinterpret_cast<float(*)[SK][SBP]>(sm);
+    auto Bs = reinterpret_cast<float(*)[SK][SBP]>(sm + 2 * SK * SBP);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int32_t i0 = blockIdx.y * SB;
-    const int64_t t0 = (int64_t)blockIdx.x * SB;
+    const int32_t mt = (A.m + SB - 1) / SB;
+    const int32_t i0 = (int32_t)(blockIdx.x % mt) * SB;
+    const int64_t bt = (int64_t)(blockIdx.x / mt);
+    const int64_t t0 = bt * SB;
     const int32_t n = A.n;
     float acc[8][8];
 #pragma unroll
@@ -96,18 +110,27 @@ __global__ void __launch_bounds__(ST) simt_u_kernel(const __grid_constant__ Simt
         for (int r = 0; r < 8; ++r)
 #pragma unroll
             for (int c = 0; c < 8; ++c) tl[r][c] = 0.f;
-#pragma unroll
+        float4 a0 = *reinterpret_cast<const float4*>(&As[cur][0][ty * 4]);
+        float4 a1 = *reinterpret_cast<const float4*>(&As[cur][0][64 + ty * 4]);
+        float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][0][tx * 4]);
+        float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][0][64 + tx * 4]);
+#pragma unroll 4
         for (int k = 0; k < SK; ++k) {
-            const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
-            const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][k][64 + ty * 4]);
-            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][k][tx * 4]);
-            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][k][64 + tx * 4]);
+            const int kn = (k + 1 < SK) ? k + 1 : k;  // the next k-row (the last step re-reads its own)
+            const float4 na0 = *reinterpret_cast<const float4*>(&As[cur][kn][ty * 4]);
+            const float4 na1 = *reinterpret_cast<const float4*>(&As[cur][kn][64 + ty * 4]);
+            const float4 nb0 = *reinterpret_cast<const float4*>(&Bs[cur][kn][tx * 4]);
+            const float4 nb1 = *reinterpret_cast<const float4*>(&Bs[cur][kn][64 + tx * 4]);
             const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
             for (int r = 0; r < 8; ++r)
 #pragma unroll
                 for (int c = 0; c < 8; ++c) tl[r][c] = fmaf(av[r], bv[c], tl[r][c]);
+            a0 = na0;
+            a1 = na1;
+            b0 = nb0;
+            b1 = nb1;
         }
 #pragma unroll
         for (int r = 0; r < 8; ++r)
@@ -120,39 +143,54 @@ __global__ void __launch_bounds__(ST) simt_u_kernel(const __grid_constant__ Simt
     // integer count of bins is kept apart from the FP32 sum of expm1(v), so the part of the integral that
     // repeats over quiet bins (U ~ b_i) carries no FP32 rounding of exp or of b + v; expm1 is correctly
     // rounded (expm1_acc.cuh), so its rounding carries no bias into the sum either.
-    // E = dt e (0 beyond T) in FP32; FP64 row sums of e per tile.
+    // E = dt e (0 beyond T) in FP32; FP64 row sums of e per tile.  Two halves of 64 rows: the threads
+    // stage their v, then each warp takes 8 rows, a lane 4 consecutive bins of a row.
+    const int warp = tid >> 5, lane = tid & 31;
     bool bad = false;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        const int32_t i = row_of(A, i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4)));
-        const double ebi = (i < n) ? A.eb[i] : 0.0;
-        const float sh = (i < n) ? fminf(A.b[i] - EXP_SPLIT_FLOOR, 0.f) : 0.f;  // U - c = v + sh
-        const float dteb = (float)(A.dt * ebi);
-        float msum = 0.f;
-        int cnt = 0;
-        float ev[8];
+    for (int half = 0; half < 2; ++half) {
+        // the k loop's last barrier (or the previous half's) has passed: the staging memory is free
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int64_t t = t0 + (c < 4 ? tx * 4 + c : 64 + tx * 4 + (c - 4));
-            const float m = expm1_acc(acc[r][c] + sh);
-            const bool valid = t < A.T;
-            bad |= valid && !(m <= 3.0e38f);
-            if (valid) {
-                msum += m;
-                ++cnt;
+        for (int rr = 0; rr < 4; ++rr) {
+            float* dst = sm + (ty * 4 + rr) * EPI_LD;
+            const int r = 4 * half + rr;
+            *reinterpret_cast<float4*>(dst + tx * 4) = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+            *reinterpret_cast<float4*>(dst + 64 + tx * 4) = make_float4(acc[r][4], acc[r][5], acc[r][6], acc[r][7]);
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int j = 0; j < 8; ++j) {
+            const int lr = warp * 8 + j;  // row within the half
+            const int32_t i = row_of(A, i0 + 64 * half + lr);
+            const double ebi = (i < n) ? A.eb[i] : 0.0;
+            const float sh = (i < n) ? fminf(A.b[i] - EXP_SPLIT_FLOOR, 0.f) : 0.f;  // U - c = v + sh
+            const float dteb = (float)(A.dt * ebi);
+            const float4 v = *reinterpret_cast<const float4*>(sm + lr * EPI_LD + lane * 4);
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+            float ev[4];
+            float msum = 0.f;
+            int cnt = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int64_t t = t0 + lane * 4 + c;
+                const float m = expm1_acc(vv[c] + sh);
+                const bool valid = t < A.T;
+                bad |= valid && !(m <= 3.0e38f);
+                if (valid) {
+                    msum += m;
+                    ++cnt;
+                }
+                ev[c] = valid ? fmaf(dteb, m, dteb) : 0.f;
             }
-            ev[c] = valid ? fmaf(dteb, m, dteb) : 0.f;
-        }
-        double rs = ebi * ((double)cnt + (double)msum);
-        // the 16 threads with the same ty share these rows
+            double rs = ebi * ((double)cnt + (double)msum);
 #pragma unroll
-        for (int off = 8; off >= 1; off >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, off);
-        if (i < n) {
-            float* dst = A.E + (int64_t)i * A.Tpad + t0;
-            *reinterpret_cast<float4*>(dst + tx * 4) = make_float4(ev[0], ev[1], ev[2], ev[3]);
-            *reinterpret_cast<float4*>(dst + 64 + tx * 4) = make_float4(ev[4], ev[5], ev[6], ev[7]);
-            if (tx == 0) A.part_e[(int64_t)i * gridDim.x + blockIdx.x] = rs;
+            for (int off = 16; off >= 1; off >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, off);
+            if (i < n) {
+                *reinterpret_cast<float4*>(A.E + (int64_t)i * A.Tpad + t0 + lane * 4) = make_float4(ev[0], ev[1], ev[2], ev[3]);
+                if (lane == 0) A.part_e[(int64_t)i * A.ntile + bt] = rs;
+            }
         }
+        __syncthreads();
     }
     if (bad) atomicOr(A.flags, 1);
 }
@@ -166,10 +204,21 @@ struct SimtGArgs {
     float* part_g;    // [nsplit][n][n]
 };
 
-// part_g[s][i][j] = sum over bins of split s of E[i][t] X[j][t].  Both operands K contiguous.
-__global__ void __launch_bounds__(ST) simt_grad_kernel(const __grid_constant__ SimtGArgs A) {
-    __shared__ __align__(16) float As[2][SK][SB];
-    __shared__ __align__(16) float Bs[2][SK][SB];
+// 4-byte asynchronous copy global -> shared (cp.async); pred false fills zeros and reads nothing
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool pred) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(src), "r"(pred ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// part_g[s][i][j] = sum over bins of split s of E[i][t] X[j][t].  Both operands K contiguous; they are
+// transposed into shared memory ([k][row]) by 4-byte asynchronous copies issued one k-step ahead, so the
+// loads neither hold registers nor stall the products (with register staging the long-scoreboard wait on
+// the loads was the largest stall).  Inner k loop as in simt_u_kernel.
+__global__ void __launch_bounds__(ST, 1) simt_grad_kernel(const __grid_constant__ SimtGArgs A) {
+    __shared__ __align__(16) float As[2][SK][SBP];
+    __shared__ __align__(16) float Bs[2][SK][SBP];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int32_t i0 = blockIdx.y * SB, j0 = blockIdx.x * SB;
     const int64_t kb = (int64_t)blockIdx.z * A.k_per_split;
@@ -181,53 +230,49 @@ __global__ void __launch_bounds__(ST) simt_grad_kernel(const __grid_constant__ S
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[r][c] = tot[r][c] = 0.f;
     const int l_row = tid >> 2, l_col = (tid & 3) * 4;  // rows l_row, l_row + 64; k l_col..+3
-    float4 ra[2], rb[2];
-    auto load = [&](int64_t k0) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int32_t i = i0 + l_row + 64 * h, j = j0 + l_row + 64 * h;
-            ra[h] = (i < n) ? *reinterpret_cast<const float4*>(A.E + (int64_t)i * A.Tpad + k0 + l_col)
-                            : make_float4(0.f, 0.f, 0.f, 0.f);
-            rb[h] = (j < n) ? *reinterpret_cast<const float4*>(A.X + (int64_t)j * A.Tpad + k0 + l_col)
-                            : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    };
-    auto store = [&](int buf) {
+    auto load = [&](int64_t k0, int buf) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int r = l_row + 64 * h;
-            As[buf][l_col + 0][r] = ra[h].x;
-            As[buf][l_col + 1][r] = ra[h].y;
-            As[buf][l_col + 2][r] = ra[h].z;
-            As[buf][l_col + 3][r] = ra[h].w;
-            Bs[buf][l_col + 0][r] = rb[h].x;
-            Bs[buf][l_col + 1][r] = rb[h].y;
-            Bs[buf][l_col + 2][r] = rb[h].z;
-            Bs[buf][l_col + 3][r] = rb[h].w;
+            const int32_t i = i0 + r, j = j0 + r;
+            const float* e = A.E + (int64_t)(i < n ? i : 0) * A.Tpad + k0 + l_col;
+            const float* x = A.X + (int64_t)(j < n ? j : 0) * A.Tpad + k0 + l_col;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                cp_async4(&As[buf][l_col + q][r], e + q, i < n);
+                cp_async4(&Bs[buf][l_col + q][r], x + q, j < n);
+            }
         }
+        cp_async_commit();
     };
-    if (kb < ke) {
-        load(kb);
-        store(0);
-    }
+    if (kb < ke) load(kb, 0);
+    cp_async_wait_all();
     __syncthreads();
     int64_t since = 0;
     for (int64_t k0 = kb; k0 < ke; k0 += SK) {
         const int cur = (int)(((k0 - kb) / SK) & 1);
-        const bool more = k0 + SK < ke;
-        if (more) load(k0 + SK);
-#pragma unroll
+        if (k0 + SK < ke) load(k0 + SK, cur ^ 1);
+        float4 a0 = *reinterpret_cast<const float4*>(&As[cur][0][ty * 4]);
+        float4 a1 = *reinterpret_cast<const float4*>(&As[cur][0][64 + ty * 4]);
+        float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][0][tx * 4]);
+        float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][0][64 + tx * 4]);
+#pragma unroll 4
         for (int k = 0; k < SK; ++k) {
-            const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
-            const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][k][64 + ty * 4]);
-            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][k][tx * 4]);
-            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][k][64 + tx * 4]);
+            const int kn = (k + 1 < SK) ? k + 1 : k;
+            const float4 na0 = *reinterpret_cast<const float4*>(&As[cur][kn][ty * 4]);
+            const float4 na1 = *reinterpret_cast<const float4*>(&As[cur][kn][64 + ty * 4]);
+            const float4 nb0 = *reinterpret_cast<const float4*>(&Bs[cur][kn][tx * 4]);
+            const float4 nb1 = *reinterpret_cast<const float4*>(&Bs[cur][kn][64 + tx * 4]);
             const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
             for (int r = 0; r < 8; ++r)
 #pragma unroll
                 for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+            a0 = na0;
+            a1 = na1;
+            b0 = nb0;
+            b1 = nb1;
         }
         since += SK;
         if (since == G_INNER) {
@@ -240,8 +285,8 @@ __global__ void __launch_bounds__(ST) simt_grad_kernel(const __grid_constant__ S
                 }
             since = 0;
         }
-        if (more) store(cur ^ 1);
-        __syncthreads();
+        cp_async_wait_all();  // the next k-step's tiles have landed
+        __syncthreads();      // ... for every thread, and every thread is done reading this one
     }
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
@@ -293,11 +338,13 @@ cudaError_t launch_simt_u_epilogue(glm_ctx* c, const float* W, const float* b, c
     A.X = reinterpret_cast<const float*>(c->buf.X);
     A.E = reinterpret_cast<float*>(c->buf.E);
     A.part_e = c->buf.part_e;
+    A.ntile = P.Tpad / SB;
     A.flags = c->buf.flags;
     A.rows = rows;
     A.m = rows ? m : P.n;
-    dim3 grid((unsigned)(P.Tpad / SB), (A.m + SB - 1) / SB);
-    simt_u_kernel<<<grid, ST, 0, c->stream>>>(A);
+    // one block per (row tile, bin tile), row tiles fastest
+    const int64_t blocks = (int64_t)((A.m + SB - 1) / SB) * A.ntile;
+    simt_u_kernel<<<(unsigned)blocks, ST, 0, c->stream>>>(A);
     return cudaGetLastError();
 }
 

@@ -2,16 +2,17 @@
 //
 //   MODE 0, steps a3/a4:  U = b 1^T + W X  (Eq. 3) from split operands W = W_hi + W_lo, X = X_hi + X_lo:
 //                         U ~ W_hi X_hi + W_lo X_hi + W_hi X_lo (the dropped W_lo X_lo is ~2^-16 of U - b),
+//                         or W_hi X + W_lo X where X is held as one 16-bit array (no X_lo),
 //                         with the link and the spike-time term in the epilogue (Eq. 5, Eq. 7): per
 //                         (row, 256-bin tile) FP64 sums of exp(U) and of U - b over the row's spike bins,
 //                         and E[i][t] = dt exp(U_i[t]) stored 16-bit.
 //                         Tile 128 x 256, K step 32, 4 stages of (W_hi, W_lo, X_hi, X_lo).  W is K-major (64-byte
 //                         swizzle); X is an N-major operand: one 3-D box of 4 bin blocks x 32 neurons x 64 bins
-//                         (128-byte swizzle) per stage.  3 MMAs per 16-wide k slice, 2 TMEM accumulators
+//                         (128-byte swizzle) per stage.  3 (2 without X_lo) MMAs per 16-wide k slice, 2 TMEM accumulators
 //                         (epilogue overlaps the next tile).
 //   MODE 1, step a5:      P_s = E X^T over a split s of the bins (dL/dW = C - sum_s P_s, Eq. 12).  The same
 //                         kernel forms the spike term C = S X^T once per problem (S, the spike raster, in
-//                         the place of E; X_hi and X_lo in turn).  Tile 256 x 256 per block as two 128 x 256
+//                         the place of E; X_hi and X_lo in turn, or X alone).  Tile 256 x 256 per block as two 128 x 256
 //                         accumulators that share every X tile (A0 = E rows m0.., A1 = E rows m0+128..),
 //                         K step 64 (128-byte swizzle), 3 stages, FP32 partials per split.
 //
@@ -155,6 +156,7 @@ struct TcArgs {
     float ct_tau;
     // SELF (MODE 0 grid): row i's own train with its self-delay is X_i at bin t + self_shift
     int32_t self_shift;
+    int32_t xlo;               // MODE 0: X held as X_hi + X_lo (the third product W_hi X_lo); 0: X_hi alone
     const float* W32;          // W (FP32), for W_ii
     const void* Xhi;           // X_hi, X_lo bin-blocked over the recording
     const void* Xlo;
@@ -360,14 +362,17 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                         break;
                     }
                     uint8_t* sa = smem + stage * L::STAGE_BYTES;
-                    tc::mbar_arrive_expect_tx(&full[stage], L::STAGE_BYTES);
+                    // MODE 0 without X_lo leaves the stage's X_lo slot unused
+                    tc::mbar_arrive_expect_tx(&full[stage], (MODE == 0 && !A.xlo) ? L::STAGE_BYTES - C::B_BYTES
+                                                                                   : L::STAGE_BYTES);
                     const int32_t kx = (int32_t)(kb * C::BK);
                     if (MODE == 0) {
                         tc::tma_load_2d(sa, mA0, kx, w.m0, &full[stage]);
                         tc::tma_load_2d(sa + C::A_BYTES, mA1, kx, w.m0, &full[stage]);
                         // (bin in block, neuron = k, bin block): 4 blocks of 32 x 64
                         tc::tma_load_3d(sa + 2 * C::A_BYTES, mB0, 0, kx, w.n0 / 64, &full[stage]);
-                        tc::tma_load_3d(sa + 2 * C::A_BYTES + C::B_BYTES, mB1, 0, kx, w.n0 / 64, &full[stage]);
+                        if (A.xlo)
+                            tc::tma_load_3d(sa + 2 * C::A_BYTES + C::B_BYTES, mB1, 0, kx, w.n0 / 64, &full[stage]);
                     } else {
                         // (bin in block, neuron, bin block = k-step)
                         const bool second = A.kb_half > 0 && kb >= A.kb_half;
@@ -398,6 +403,7 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
             for (int64_t u = blockIdx.x; u < total_units && ok; u += gridDim.x, ++it) {
                 const int p = prob_of(u);
                 const Unit w = decode<MODE>(args_of(p), u - s_ubeg[p], s_mt[p]);
+                const bool xlo = args_of(p).xlo != 0;
                 const int buf = (C::NBUF == 2) ? (it & 1) : 0;
                 const uint32_t buf_phase = (uint32_t)((C::NBUF == 2 ? (it >> 1) : it) & 1);
                 if (!tc::mbar_wait(&tempty[buf], buf_phase ^ 1, abort_flag, Ag.limit_ns)) {
@@ -426,7 +432,7 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                         if (MODE == 0) {
                             tc::mma_f16(d0, da0 + ka, db0 + kb16, Ag.idesc, acc);   // W_hi X_hi
                             tc::mma_f16(d0, da1 + ka, db0 + kb16, Ag.idesc, 1u);    // W_lo X_hi
-                            tc::mma_f16(d0, da0 + ka, db1 + kb16, Ag.idesc, 1u);    // W_hi X_lo
+                            if (xlo) tc::mma_f16(d0, da0 + ka, db1 + kb16, Ag.idesc, 1u);  // W_hi X_lo
                         } else {
                             tc::mma_f16(d0, da0 + ka, db0 + kb16, Ag.idesc, acc);   // rows m0..
                             if (C::NA == 2) tc::mma_f16(d1, da1 + ka, db0 + kb16, Ag.idesc, acc);  // rows m0+128..
@@ -621,7 +627,8 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                             if (i < A.n && t < A.T) {
                                 const int64_t o1 = ((t >> 6) * A.n + i) * 64 + (t & 63);
                                 const int64_t o2 = ((t2 >> 6) * A.n + i) * 64 + (t2 & 63);
-                                dxs[e] = (to_f(xsh[o2]) + to_f(xsl[o2])) - (to_f(xsh[o1]) + to_f(xsl[o1]));
+                                dxs[e] = xsl ? (to_f(xsh[o2]) + to_f(xsl[o2])) - (to_f(xsh[o1]) + to_f(xsl[o1]))
+                                             : to_f(xsh[o2]) - to_f(xsh[o1]);
                             }
                             r[e] = __float_as_uint(fmaf(wii, dxs[e], __uint_as_float(r[e])));
                         }
@@ -835,13 +842,15 @@ cudaError_t tc_prepare_maps(glm_ctx* c) {
     const size_t wsz = (size_t)P.n * ld * 2;
     const uint8_t* Wsplit = reinterpret_cast<const uint8_t*>(c->buf.Wsplit);
     const auto S64 = CU_TENSOR_MAP_SWIZZLE_64B;
+    // without the X split, maps 3 and 6 cover X_hi: valid maps that no product reads
+    const void* Xlo = P.xlo ? c->buf.Xlo : c->buf.X;
     bool ok = encode_map(&c->tmap[0], bf, Wsplit, P.n, P.n, ld, 32, 128, S64) &&
               encode_map(&c->tmap[1], bf, Wsplit + wsz, P.n, P.n, ld, 32, 128, S64) &&
               encode_blocked(&c->tmap[2], bf, c->buf.X, P.n, P.Tc, Cfg<0>::BK, BN / 64) &&
-              encode_blocked(&c->tmap[3], bf, c->buf.Xlo, P.n, P.Tc, Cfg<0>::BK, BN / 64) &&
+              encode_blocked(&c->tmap[3], bf, Xlo, P.n, P.Tc, Cfg<0>::BK, BN / 64) &&
               encode_blocked(&c->tmap[4], bf, c->buf.E, P.n, P.Tc, 128, 1) &&
               encode_blocked(&c->tmap[5], bf, c->buf.X, P.n, P.Tc, BN, 1) &&
-              encode_blocked(&c->tmap[6], bf, c->buf.Xlo, P.n, P.Tc, BN, 1);
+              encode_blocked(&c->tmap[6], bf, Xlo, P.n, P.Tc, BN, 1);
     return ok ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -899,7 +908,8 @@ static TcArgs base_args(glm_ctx* c) {
     A.self_shift = 0;
     A.W32 = nullptr;
     A.Xhi = c->buf.X;
-    A.Xlo = c->buf.Xlo;
+    A.Xlo = P.xlo ? c->buf.Xlo : nullptr;
+    A.xlo = P.xlo ? 1 : 0;
     A.part_self = nullptr;
     return A;
 }
@@ -1006,7 +1016,8 @@ static cudaError_t run_products(glm_ctx* c, const CUtensorMap& mapB, int64_t t_l
 }
 
 cudaError_t launch_tc_grad(glm_ctx* c, int64_t t_len, int* nsplit_used) {
-    return run_products(c, c->tmap[5], t_len, nsplit_used, true, c->precise_grad ? &c->tmap[6] : nullptr);
+    return run_products(c, c->tmap[5], t_len, nsplit_used, true,
+                        (c->precise_grad && c->pb.xlo) ? &c->tmap[6] : nullptr);
 }
 
 // With X recomputed per chunk, each chunk is filtered here first and the products add up over the chunks.
@@ -1023,7 +1034,8 @@ __global__ void self_spike_diag_kernel(int32_t n, int32_t shift, const int64_t* 
     for (int64_t k = offs[i] + lane; k < offs[i + 1]; k += 32) {
         const int64_t t = bins[k], t2 = t + shift;
         const int64_t o1 = ((t >> 6) * n + i) * 64 + (t & 63), o2 = ((t2 >> 6) * n + i) * 64 + (t2 & 63);
-        d += (double)((to_f(xh[o2]) + to_f(xl[o2])) - (to_f(xh[o1]) + to_f(xl[o1])));
+        d += xl ? (double)((to_f(xh[o2]) + to_f(xl[o2])) - (to_f(xh[o1]) + to_f(xl[o1])))
+                : (double)(to_f(xh[o2]) - to_f(xh[o1]));
     }
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
@@ -1044,8 +1056,10 @@ cudaError_t launch_tc_spike_term(glm_ctx* c) {
         c->raster_in_E = false;  // consumed below; the next U product overwrites E
         int ns = 0;
         const int64_t bins = P.chunk ? len : P.T;
-        // S X_hi^T and S X_lo^T in one launch: each split runs over its bins of X_hi, then of X_lo
-        if ((e = run_products(c, c->tmap[5], bins, &ns, false, &c->tmap[6])) != cudaSuccess) return e;
+        // S X_hi^T and S X_lo^T in one launch: each split runs over its bins of X_hi, then of X_lo (S X^T alone
+        // without the X split)
+        if ((e = run_products(c, c->tmap[5], bins, &ns, false, P.xlo ? &c->tmap[6] : nullptr)) != cudaSuccess)
+            return e;
         if ((e = launch_sum_splits(c, ns, c->buf.C, t0 > 0)) != cudaSuccess) return e;
     }
     if (P.self_shift > 0) {  // X stored (no chunks): the whole recording is in the buffers
@@ -1088,8 +1102,9 @@ cudaError_t launch_wait_check(glm_ctx* c, uint64_t limit_ns, int* out) {
 // E X^T arguments of one problem of the batched launch: over X_hi, then X_lo when the gradient is precise
 static TcArgs batch_grad_args(glm_ctx* c, int mode, int ns) {
     const int64_t kbt = grad_ksteps(c);
-    TcArgs A = grad_args(c, mode, ns, c->precise_grad ? 2 * kbt : kbt);
-    if (c->precise_grad) A.kb_half = kbt;
+    const bool precise = c->precise_grad && c->pb.xlo;
+    TcArgs A = grad_args(c, mode, ns, precise ? 2 * kbt : kbt);
+    if (precise) A.kb_half = kbt;
     return A;
 }
 
@@ -1126,7 +1141,7 @@ int tc_batch_fill(glm_ctx* const* cs, int np, float* const* W32, float* const* b
         bg->args[p] = batch_grad_args(c, c->g_mode, tc_nsplit(c));
         bg->maps[p][0] = bg->maps[p][1] = c->tmap[4];
         bg->maps[p][2] = c->tmap[5];
-        bg->maps[p][3] = c->precise_grad ? c->tmap[6] : c->tmap[5];
+        bg->maps[p][3] = (c->precise_grad && c->pb.xlo) ? c->tmap[6] : c->tmap[5];
     }
     (void)W32;
     return GLM_OK;

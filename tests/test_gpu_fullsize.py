@@ -6,13 +6,16 @@ configuration), against the FP64 oracle on the host cores:
     per-row bound, and the gradient on 32 seeded random rows (componentwise measure);
   * a seeded subset of 16 rows fitted by the oracle from W = 0 (rows are independent problems, Sec. 2.2,
     so a subset fit is exact) against the same rows of the GPU's fits of the whole network, in the plain
-    FP32 form and in BF16: the oracle's log-likelihood at the GPU's rows equals its own optimum to within
-    the stopping tolerance for the FP32 form (1e-8 of L_i), and to within 2e-6 for BF16, whose objective
-    differs from the exact one by the X_hi + X_lo rounding and the tensor cores' accumulation (its fit lands
-    ~6e-7 below the exact optimum, measured; the MER is unchanged); and the labels of each fit agree with the
+    FP32 form and in BF16.  The stopping rule of Sec. 2.6.3 bounds the relative gain of the last iteration
+    (eta = 1e-10), not the distance to the optimum: on these rows either fit ends up to ~1e-8 of L_i short
+    of it (the oracle's own fit lands 1.2e-8 below the FP32 GPU fit's point on one row, measured), so the
+    oracle's L_i at the GPU's rows and at its own rows differ by at most 2e-8 either way for the FP32 form.
+    For BF16 the GPU's fit may lie up to 2e-6 below: its objective differs from the exact one by the
+    tensor cores' FP32 accumulation (the FP16 fit lands equally far, ~6e-7 of L, so the X_hi + X_lo
+    rounding is not the cause; the MER is unchanged).  The labels of each fit agree with the
     oracle's under one classifier (the GMM fitted to the GPU's whole W), apart from entries in the band where
-    the two fits' difference can move a weight across a decision boundary (reading 11 of the design notes:
-    |W - boundary| < 10 max|dW|), which are listed.
+    the two fits' difference can move a weight across a decision boundary (|W - boundary| < 10 max|dW|),
+    which are counted.
 
 W is perturbed away from the generating weights (the optimum of the fit is not where these bounds are
 easiest)."""
@@ -63,13 +66,16 @@ def metric10(G, G_ref, C_ref):
     return float(np.max(np.abs(G - G_ref) / (mag + 1e-300)))
 
 
-@pytest.mark.parametrize("prec,tot,row,grad", [("bf16", 1e-6, 3e-5, 2e-3), ("f32", 1e-9, 5e-8, 1e-5)])
+@pytest.mark.parametrize("prec,tot,row,grad", [("bf16", 1e-6, 3e-5, 2e-3), ("f16x1", 1e-6, 3e-5, 2e-3),
+                                               ("f32", 1e-9, 5e-8, 1e-5)])
 def test_full_size_whole_network(glm, full, oracle_rows, prec, tot, row, grad):
+    """f16x1: X held as one FP16 array (no X_lo), the benchmark's default form."""
     w, W, b = full
     allL, g = oracle_rows
     q = np.diff(w["offs"]).astype(np.float64)
     with glm.GLM(0) as c:
-        c.set_problem(w["offs"], w["bins"], w["n_bins"], w["dt"], w["tau"], prec=prec)
+        c.set_x_split(not prec.endswith("x1"))
+        c.set_problem(w["offs"], w["bins"], w["n_bins"], w["dt"], w["tau"], prec=prec.replace("x1", ""))
         r = c.loglik_grad(torch.from_numpy(W).cuda(), torch.from_numpy(b).cuda())
         C = c.spike_term()[0].cpu().numpy()
         Lr = r["L_rows"].cpu().numpy()
@@ -92,14 +98,22 @@ def oracle_subset_fit(full):
     return rows, fo
 
 
-@pytest.mark.parametrize("prec,gap_bound", [("f32", 1e-8), ("bf16", 2e-6)])
-def test_full_size_subset_fit_matches_oracle(glm, full, oracle_subset_fit, prec, gap_bound):
+@pytest.mark.parametrize("prec,gap_bound,gap_low", [("f32", 2e-8, -2e-8), ("bf16", 2e-6, -2e-8),
+                                                     ("f16x1", 2e-6, -2e-8), ("f16x1+f32", 2e-8, -2e-8)])
+def test_full_size_subset_fit_matches_oracle(glm, full, oracle_subset_fit, prec, gap_bound, gap_low):
+    """"f16x1": FP16 with X as one array; "f16x1+f32": that fit finished by the FP32 form from its result
+    (warm start), which removes the 16-bit objective's offset from the exact optimum."""
     w, _, _ = full
     n, T = w["n"], w["n_bins"]
     rows, fo = oracle_subset_fit
     with glm.GLM(0) as c:
-        c.set_problem(w["offs"], w["bins"], T, w["dt"], w["tau"], prec=prec)
-        r = c.fit(eta=1e-10, max_iter=500)
+        r = None
+        for p in prec.split("+"):
+            c.set_x_split(not p.endswith("x1"))
+            c.set_problem(w["offs"], w["bins"], T, w["dt"], w["tau"], prec=p.replace("x1", ""))
+            r = c.fit(r["W"], r["b"], eta=1e-10, max_iter=500) if r is not None else c.fit(eta=1e-10, max_iter=500)
+            print(f"{p} fit: {r['report']['seconds']:.2f} s, {r['report']['iterations']} iterations, "
+                  f"{r['report']['evaluations']} evaluations, {r['report']['at_floor']} rows at the floor")
         Wg = r["W"].cpu().numpy().astype(np.float64)
         bg = r["b"].cpu().numpy().astype(np.float64)
         _, rep = glm.classify(Wg, "gmm")
@@ -112,8 +126,9 @@ def test_full_size_subset_fit_matches_oracle(glm, full, oracle_subset_fit, prec,
     Lg = oracle.eval_rows(w["offs"], w["bins"], T, w["dt"], w["tau"], Wg, bg, rows, grad=False)["L"]
     gap = (Lo - Lg) / np.abs(Lo)
     dW = np.abs(Wg[rows] - fo["W"])
-    print(f"{prec} subset fit: L_i gap oracle - GPU max {gap.max():.2e} (min {gap.min():.2e}), max |dW| {dW.max():.2e}")
-    assert np.all(gap <= gap_bound)
+    print(f"{prec} subset fit: L_i gap oracle - GPU max {gap.max():.2e} (min {gap.min():.2e}, mean {gap.mean():.2e}), "
+          f"max |dW| {dW.max():.2e}")
+    assert np.all(gap <= gap_bound) and np.all(gap >= gap_low)
     # labels under the GPU fit's mixture model, except entries near a decision boundary
     pi, mu, var = np.array(rep["weights"]), np.array(rep["centers"]), np.array(rep["variances"])
     grid = np.linspace(mu[0], mu[2], 200001)
