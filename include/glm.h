@@ -333,7 +333,7 @@ int glm_fit(glm_ctx* ctx, const glm_fit_opts_t* opts, float* W_dev, float* b_dev
  * is still open after an iteration's rounds continues in the next iteration.  All work runs on ctxs[0]'s
  * stream.  W_dev[p], b_dev[p]: as for glm_fit; row_status_host and reports: optional arrays of n_prob
  * (row_status_host[p] may be NULL).  n_prob: 1..32.  Returns the worst of the per-problem glm_fit
- * statuses or a negative GLM_ERR_* (INVALID_ARG for mixed devices or precisions, UNSUPPORTED for
+ * statuses or a negative GLM_ERR_* (INVALID_ARG for mixed devices, precisions or X splits, UNSUPPORTED for
  * GLM_PREC_F32).  Synchronises ctxs[0]'s stream. */
 #define GLM_FIT_BATCH_MAX 32
 int glm_fit_batch(glm_ctx* const* ctxs, int32_t n_prob, const glm_fit_opts_t* opts, float* const* W_dev,

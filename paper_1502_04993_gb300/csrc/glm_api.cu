@@ -1135,6 +1135,7 @@ int glm_fit_batch(glm_ctx* const* cs, int32_t np, const glm_fit_opts_t* opts, fl
         if (!c->has_problem) return fail(c0, GLM_ERR_NO_PROBLEM, "a context has no problem set");
         if (c->device != c0->device) return fail(c0, GLM_ERR_INVALID_ARG, "contexts on different devices");
         if (c->pb.prec != c0->pb.prec) return fail(c0, GLM_ERR_INVALID_ARG, "contexts with different precisions");
+        if (c->pb.xlo != c0->pb.xlo) return fail(c0, GLM_ERR_INVALID_ARG, "contexts with different X splits");
         if (c->pb.chunk) return fail(c0, GLM_ERR_UNSUPPORTED, "glm_fit_batch needs X stored (no chunking)");
         if (c->pb.ct) return fail(c0, GLM_ERR_UNSUPPORTED, "glm_fit_batch serves the grid form");
         if (c->row_r1 >= 0) return fail(c0, GLM_ERR_UNSUPPORTED, "glm_fit_batch fits whole problems (no row range)");

@@ -76,6 +76,29 @@ struct Cfg<0> {
     static constexpr uint32_t A_BYTES = 128 * BK * 2;
     static constexpr uint32_t B_BYTES = BN * BK * 2;
 };
+// MODE 3: the U product of MODE 0 over a single 16-bit X (no X_lo): a stage holds W_hi, W_lo and X only, and
+// six stages keep as many bytes in flight as MODE 0's four (its MMAs take 2/3 of the time per stage, so four
+// 32 KB stages could not cover the load latency from L2)
+template <>
+struct Cfg<3> {
+    static constexpr int BM = 128;
+    static constexpr int BK = 32;
+    static constexpr int NA = 2, NB = 1;      // W_hi, W_lo ; X
+    static constexpr int STAGES = 6;
+    static constexpr int NBUF = 2;
+    static constexpr uint32_t SWZ = 4;
+    static constexpr uint32_t SBO = 8 * 64;
+    static constexpr uint32_t A_KSTEP = 2;
+    static constexpr uint32_t B_SWZ = 2;
+    static constexpr uint32_t B_SBO = 1024;
+    static constexpr uint32_t B_LBO = BK * 128;
+    static constexpr uint32_t B_KSTEP = 128;
+    static constexpr uint32_t A_BYTES = 128 * BK * 2;
+    static constexpr uint32_t B_BYTES = BN * BK * 2;
+};
+template <int MODE>
+constexpr bool is_u() { return MODE == 0 || MODE == 3; }
+
 template <>
 struct Cfg<1> {
     static constexpr int BM = 256;            // two 128-row halves
@@ -183,7 +206,7 @@ struct TcBatch {
 template <int MODE>
 __device__ __forceinline__ Unit decode(const TcArgs& A, int64_t u, int32_t mt) {
     Unit r;
-    if (MODE == 0) {
+    if (is_u<MODE>()) {
         r.m0 = (int32_t)(u % mt) * Cfg<0>::BM;
         r.n0 = (int32_t)(u / mt) * BN;
         r.kb0 = 0;
@@ -262,7 +285,8 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
     using C = Cfg<MODE>;
     using L = Layout<MODE>;
     static_assert(!CT || (MODE == 0 && !TAU), "the continuous-time epilogue is a U-product epilogue without tau partials");
-    static_assert(!SELF || (MODE == 0 && !TAU && !CT && !BATCH), "the self-delay is a grid U-product epilogue option");
+    static_assert(!SELF || (is_u<MODE>() && !TAU && !CT && !BATCH), "the self-delay is a grid U-product epilogue option");
+    static_assert(MODE != 3 || !CT, "the continuous-time columns are always split");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * L::STAGE_BYTES);
@@ -285,7 +309,7 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
             const TcArgs& a = BATCH ? batch->args[p] : Ag;
             int32_t m = a.m_rows, mt = a.mt;
             int64_t units = a.units;
-            if (MODE == 0) {
+            if (is_u<MODE>()) {
                 if (BATCH && batch->m_dev[p]) m = *batch->m_dev[p];
                 mt = (m + Cfg<0>::BM - 1) / Cfg<0>::BM;
                 units = (int64_t)mt * a.nt;
@@ -366,12 +390,12 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                     tc::mbar_arrive_expect_tx(&full[stage], (MODE == 0 && !A.xlo) ? L::STAGE_BYTES - C::B_BYTES
                                                                                    : L::STAGE_BYTES);
                     const int32_t kx = (int32_t)(kb * C::BK);
-                    if (MODE == 0) {
+                    if (is_u<MODE>()) {
                         tc::tma_load_2d(sa, mA0, kx, w.m0, &full[stage]);
                         tc::tma_load_2d(sa + C::A_BYTES, mA1, kx, w.m0, &full[stage]);
                         // (bin in block, neuron = k, bin block): 4 blocks of 32 x 64
                         tc::tma_load_3d(sa + 2 * C::A_BYTES, mB0, 0, kx, w.n0 / 64, &full[stage]);
-                        if (A.xlo)
+                        if (C::NB == 2 && A.xlo)
                             tc::tma_load_3d(sa + 2 * C::A_BYTES + C::B_BYTES, mB1, 0, kx, w.n0 / 64, &full[stage]);
                     } else {
                         // (bin in block, neuron, bin block = k-step)
@@ -429,10 +453,10 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                     for (int k = 0; k < C::BK / 16; ++k) {
                         const uint32_t acc = (kb == w.kb0 && k == 0) ? 0u : 1u;
                         const uint64_t ka = C::A_KSTEP * k, kb16 = C::B_KSTEP * k;
-                        if (MODE == 0) {
+                        if (is_u<MODE>()) {
                             tc::mma_f16(d0, da0 + ka, db0 + kb16, Ag.idesc, acc);   // W_hi X_hi
                             tc::mma_f16(d0, da1 + ka, db0 + kb16, Ag.idesc, 1u);    // W_lo X_hi
-                            if (xlo) tc::mma_f16(d0, da0 + ka, db1 + kb16, Ag.idesc, 1u);  // W_hi X_lo
+                            if (C::NB == 2 && xlo) tc::mma_f16(d0, da0 + ka, db1 + kb16, Ag.idesc, 1u);  // W_hi X_lo
                         } else {
                             tc::mma_f16(d0, da0 + ka, db0 + kb16, Ag.idesc, acc);   // rows m0..
                             if (C::NA == 2) tc::mma_f16(d1, da1 + ka, db0 + kb16, Ag.idesc, acc);  // rows m0+128..
@@ -563,7 +587,7 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                     A.part_s[o] = (double)spv;
                 }
                 if (bad && i < A.n) atomicOr(A.flags, 1);
-            } else if constexpr (MODE == 0) {
+            } else if constexpr (is_u<MODE>()) {
                 // e^{U} = e^{b_i} e^{v}, v = (W X)_i[t]: e^{b_i} in FP64, and the row sum is kept as
                 // e^{b_i} (count + sum (e^{v} - 1)), so quiet bins (v ~ 0) add no FP32 rounding of b + v.
                 const uint32_t taddr = lane_base + (uint32_t)(buf * BN);
@@ -914,6 +938,29 @@ static TcArgs base_args(glm_ctx* c) {
     return A;
 }
 
+// the grid U product in MODE 0 (X_hi + X_lo) or MODE 3 (one X), with the tau partials or the self-delay term
+template <int MODE>
+static cudaError_t run_u(glm_ctx* c, TcArgs& A, bool tau, bool self, const float* W) {
+    const Problem& P = c->pb;
+    const bool bf = P.prec == GLM_PREC_BF16;
+    if (tau) {
+        if (self) return cudaErrorNotSupported;
+        if (bf) return run<MODE, __nv_bfloat16, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
+        return run<MODE, __half, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
+    }
+    if (self) {
+        if (P.chunk) return cudaErrorNotSupported;
+        A.self_shift = P.self_shift;
+        A.W32 = W;
+        A.part_self = c->buf.part_self;
+        if (bf)
+            return run<MODE, __nv_bfloat16, false, false, false, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
+        return run<MODE, __half, false, false, false, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
+    }
+    if (bf) return run<MODE, __nv_bfloat16>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
+    return run<MODE, __half>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
+}
+
 cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, bool tau, const int32_t* rows,
                                  int32_t m, int64_t t_base, int64_t t_len) {
     const Problem& P = c->pb;
@@ -951,24 +998,8 @@ cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, boo
             return run<0, __nv_bfloat16, false, false, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
         return run<0, __half, false, false, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
     }
-    if (tau) {
-        if (P.self_shift > 0) return cudaErrorNotSupported;
-        if (P.prec == GLM_PREC_BF16)
-            return run<0, __nv_bfloat16, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
-        return run<0, __half, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
-    }
-    if (P.self_shift > 0) {
-        if (P.chunk) return cudaErrorNotSupported;
-        A.self_shift = P.self_shift;
-        A.W32 = W;
-        A.part_self = c->buf.part_self;
-        if (P.prec == GLM_PREC_BF16)
-            return run<0, __nv_bfloat16, false, false, false, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
-        return run<0, __half, false, false, false, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
-    }
-    if (P.prec == GLM_PREC_BF16)
-        return run<0, __nv_bfloat16>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
-    return run<0, __half>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
+    if (P.xlo) return run_u<0>(c, A, tau, P.self_shift > 0, W);
+    return run_u<3>(c, A, tau, P.self_shift > 0, W);
 }
 
 // E X^T arguments of context c with its tile mode and split count
@@ -1154,8 +1185,12 @@ cudaError_t launch_tc_u_batch(glm_ctx* c0, const void* dev_u) {
     Ag.idesc |= 1u << 16;  // B (X) is N-major
     const TcBatch* b = static_cast<const TcBatch*>(dev_u);
     const CUtensorMap* m = c0->tmap;
-    if (c0->pb.prec == GLM_PREC_BF16)
-        return run<0, __nv_bfloat16, false, true>(c0, m[0], m[1], m[2], m[3], Ag, b, c0->sm_count);
+    const bool bf = c0->pb.prec == GLM_PREC_BF16;
+    if (!c0->pb.xlo) {  // every problem of a batch has the same form (checked by glm_fit_batch)
+        if (bf) return run<3, __nv_bfloat16, false, true>(c0, m[0], m[1], m[2], m[3], Ag, b, c0->sm_count);
+        return run<3, __half, false, true>(c0, m[0], m[1], m[2], m[3], Ag, b, c0->sm_count);
+    }
+    if (bf) return run<0, __nv_bfloat16, false, true>(c0, m[0], m[1], m[2], m[3], Ag, b, c0->sm_count);
     return run<0, __half, false, true>(c0, m[0], m[1], m[2], m[3], Ag, b, c0->sm_count);
 }
 

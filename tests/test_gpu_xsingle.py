@@ -7,9 +7,11 @@ N = 1000, 200 000-bin balanced network moves by 2.1e-7 of its size, rows by at m
 3e-5, gradient 2e-3) hold with room.  BF16 keeps 8 bits; the same evaluation moves L by 6.3e-6 and rows
 by 5.3e-5, beyond those bounds, so BF16 with one X is checked against bounds that its rounding allows
 (total 3e-5, rows 3e-4): it is the form the split X exists to improve on.  The spike term is compared
-element by element with the oracle's filtered trains rounded to the same 16-bit type and summed in FP64
-over the spike bins: the kernel differs from that sum only by its FP32 accumulation of at most q_i terms
-of one sign, whose relative error stays below q_i 2^-24."""
+element by element with the oracle's: each of its q_i terms X_j[t] >= 0 is the FP32 scan's value (within
+1e-7 of X) rounded to nearest in the 16-bit type (relative error at most u = 2^-11 for FP16, 2^-8 for
+BF16; below the normal range at most half the subnormal spacing), and the tensor cores accumulate the sum
+in FP32 (relative error below q_i 2^-23 even if each addition truncates), so
+|C - C_exact| <= (u + 1e-7 + q_i 2^-23) C_exact + q_i 2^-25 (FP16) or q_i 2^-134 (BF16)."""
 import numpy as np
 import pytest
 import torch
@@ -77,14 +79,15 @@ def test_single_x_matches_oracle(glm, prec, n, T, seed, scale):
     rel_tot = abs(r["L_total"] - ref["L_total"]) / abs(ref["L_total"])
     rel_rows = np.max(np.abs(r["L_rows"].cpu().numpy() - ref["L"]) / (np.abs(ref["L"]) + q))
     g = componentwise(r["G"].cpu().numpy(), ref["G"], C)
-    X16 = torch.from_numpy(oracle.filter(w["offs"], w["bins"], T, w["dt"], w["tau"])).to(TDT[prec]).double().numpy()
-    C16 = np.stack([X16[:, w["bins"][w["offs"][i]:w["offs"][i + 1]]].sum(axis=1) for i in range(n)])
-    c_err = float(np.max(np.abs(C - C16) / (C16 + 1e-300)))
-    print(f"{prec} single X n={n} T={T}: L total {rel_tot:.2e}, rows {rel_rows:.2e}, grad {g:.2e}, C {c_err:.2e}")
+    X = oracle.filter(w["offs"], w["bins"], T, w["dt"], w["tau"])
+    Cx = np.stack([X[:, w["bins"][w["offs"][i]:w["offs"][i + 1]]].sum(axis=1) for i in range(n)])
+    u, sub = (2.0 ** -11, 2.0 ** -25) if prec == "f16" else (2.0 ** -8, 2.0 ** -134)
+    bound = (u + 1e-7 + q[:, None] * 2.0 ** -23) * Cx + q[:, None] * sub
+    c_err = float(np.max(np.abs(C - Cx) / (Cx + 1e-300)))
+    print(f"{prec} single X n={n} T={T}: L total {rel_tot:.2e}, rows {rel_rows:.2e}, grad {g:.2e}, C vs exact {c_err:.2e}")
     assert rel_tot <= tol["total"] and rel_rows <= tol["row"] and g <= tol["grad"]
     assert np.all(np.abs(r["gb"].cpu().numpy() - ref["gb"]) <= tol["row"] * (q + np.abs(q - ref["gb"])) + 1e-9)
-    # FP32 accumulation of at most q_i terms of one sign: relative error below q_i 2^-24
-    assert c_err <= q.max() * 2.0 ** -24
+    assert np.all(np.abs(C - Cx) <= bound)
 
 
 def test_single_x_differs_from_split_by_the_rounding(glm):
@@ -174,7 +177,10 @@ def test_single_x_batch_matches_oracle(glm):
 
 def test_single_x_row_classes_with_self_delay(glm):
     """Row classes with their own tau, source delay and self-delay (Sec. 2.4, Sec. 3.1) over the single X,
-    against oracle.delays."""
+    against oracle.delays: every row of every class within the per-row bound, the gradient componentwise,
+    and the network's L (the sum over the classes) within the total bound.  A class's own total is a sum of
+    as few as 20 rows, whose X-rounding errors (up to ~1e-5 of a row) do not average out as over the
+    network, so it is held to the per-row bound summed over its rows."""
     classes = [(0, 50, 0.010, 2, 1), (50, 100, 0.012, 4, 1), (100, 120, 0.010, 3, 3)]
     w = workload(120, 30000, 23)
     n = w["n"]
@@ -186,6 +192,7 @@ def test_single_x_row_classes_with_self_delay(glm):
                                  b.astype(np.float64), self_delay_rows=ss)
     q = np.diff(w["offs"]).astype(np.float64)
     tol = TOL["f16"]
+    L_net = 0.0
     for r0, r1, tau, d, s in classes:
         with glm.GLM(0) as c:
             c.set_x_split(False)
@@ -201,4 +208,9 @@ def test_single_x_row_classes_with_self_delay(glm):
         rel_rows = np.max(np.abs(Lr[sl] - ref["L"][sl]) / (np.abs(ref["L"][sl]) + q[sl]))
         g = componentwise(G[sl], ref["G"][sl], C[sl])
         print(f"single X class d={d} d_s={s}: L {rel_tot:.2e}, rows {rel_rows:.2e}, grad {g:.2e}")
-        assert rel_tot <= tol["total"] and rel_rows <= tol["row"] and g <= tol["grad"]
+        assert rel_rows <= tol["row"] and g <= tol["grad"]
+        assert abs(r["L_total"] - ref["L"][sl].sum()) <= tol["row"] * (np.abs(ref["L"][sl]) + q[sl]).sum()
+        L_net += r["L_total"]
+    rel_net = abs(L_net - ref["L"].sum()) / abs(ref["L"].sum())
+    print(f"single X classes: network L {rel_net:.2e}")
+    assert rel_net <= tol["total"]
