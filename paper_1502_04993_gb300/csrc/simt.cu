@@ -215,20 +215,29 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // part_g[s][i][j] = sum over bins of split s of E[i][t] X[j][t].  Both operands K contiguous; they are
 // transposed into shared memory ([k][row]) by 4-byte asynchronous copies issued one k-step ahead, so the
 // loads neither hold registers nor stall the products (with register staging the long-scoreboard wait on
-// the loads was the largest stall).  Inner k loop as in simt_u_kernel.
-__global__ void __launch_bounds__(ST, 1) simt_grad_kernel(const __grid_constant__ SimtGArgs A) {
-    __shared__ __align__(16) float As[2][SK][SBP];
-    __shared__ __align__(16) float Bs[2][SK][SBP];
+// the loads was the largest stall).  Inner k loop as in simt_u_kernel.  The outer level of the two-level
+// sum (every G_INNER bins) lives in shared memory, one column per thread: with it in registers the kernel
+// needed 191 registers and ran one block per SM, whose eight warps could not hide the shared-memory
+// latency of the inner loop; without, two blocks fit.
+constexpr size_t G_SMEM = (size_t)(4 * SK * SBP + 64 * ST) * sizeof(float);
+__global__ void __launch_bounds__(ST, 2) simt_grad_kernel(const __grid_constant__ SimtGArgs A) {
+    extern __shared__ __align__(16) float gsm[];
+    auto As = reinterpret_cast<float(*)[SK][SBP]>(gsm);
+    auto Bs = reinterpret_cast<float(*)[SK][SBP]>(gsm + 2 * SK * SBP);
+    float* tot = gsm + 4 * SK * SBP;  // [64][ST]: element r * 8 + c of thread tid at [(r * 8 + c) * ST + tid]
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int32_t i0 = blockIdx.y * SB, j0 = blockIdx.x * SB;
     const int64_t kb = (int64_t)blockIdx.z * A.k_per_split;
     const int64_t ke = min(kb + A.k_per_split, A.Tpad);
     const int32_t n = A.n;
-    float acc[8][8], tot[8][8];
+    float acc[8][8];
 #pragma unroll
     for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[r][c] = tot[r][c] = 0.f;
+        for (int c = 0; c < 8; ++c) {
+            acc[r][c] = 0.f;
+            tot[(r * 8 + c) * ST + tid] = 0.f;
+        }
     const int l_row = tid >> 2, l_col = (tid & 3) * 4;  // rows l_row, l_row + 64; k l_col..+3
     auto load = [&](int64_t k0, int buf) {
 #pragma unroll
@@ -280,7 +289,7 @@ __global__ void __launch_bounds__(ST, 1) simt_grad_kernel(const __grid_constant_
             for (int r = 0; r < 8; ++r)
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    tot[r][c] += acc[r][c];
+                    tot[(r * 8 + c) * ST + tid] += acc[r][c];
                     acc[r][c] = 0.f;
                 }
             since = 0;
@@ -296,7 +305,7 @@ __global__ void __launch_bounds__(ST, 1) simt_grad_kernel(const __grid_constant_
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const int32_t j = j0 + (c < 4 ? tx * 4 + c : 64 + tx * 4 + (c - 4));
-            if (j < n) dst[j] = tot[r][c] + acc[r][c];
+            if (j < n) dst[j] = tot[(r * 8 + c) * ST + tid] + acc[r][c];
         }
     }
 }
@@ -361,7 +370,9 @@ cudaError_t launch_simt_grad(glm_ctx* c) {
     A.X = reinterpret_cast<const float*>(c->buf.X);
     A.part_g = c->buf.part_g;
     dim3 grid((P.n + SB - 1) / SB, (P.n + SB - 1) / SB, ns);
-    simt_grad_kernel<<<grid, ST, 0, c->stream>>>(A);
+    const cudaError_t e = cudaFuncSetAttribute(simt_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G_SMEM);
+    if (e != cudaSuccess) return e;
+    simt_grad_kernel<<<grid, ST, G_SMEM, c->stream>>>(A);
     return cudaGetLastError();
 }
 

@@ -43,13 +43,18 @@ namespace glm {
 
 namespace {
 
-// warp 0 TMA, warp 1 MMA, then the epilogue warps: 4 (one per TMEM lane quarter), or 4 CT_PARTS for the
+// warp 0 TMA, warp 1 MMA, then the epilogue warps: 4 (one per TMEM lane quarter); 4 CT_PARTS for the
 // continuous-time U product, whose epilogue does several times the grid's arithmetic per element
-// (CT_PARTS warps per lane quarter, each taking a part of the tile's columns)
-template <int MODE, bool CT>
-constexpr int epi_warps() { return (MODE == 0 && CT) ? 4 * CT_PARTS : 4; }
-template <int MODE, bool CT>
-constexpr int kthreads() { return 64 + 32 * epi_warps<MODE, CT>(); }
+// (CT_PARTS warps per lane quarter, each taking a part of the tile's columns); 8 for the plain grid U
+// product (two per lane quarter, each taking half of the tile's columns): with one warp per SM sub-partition
+// the epilogue's dependent chains are exposed, and over a single X (two products per k slice) it took
+// longer per tile than the MMAs (measured: 0.74 of the tensor peak)
+template <int MODE>
+constexpr bool is_u() { return MODE == 0 || MODE == 3; }
+template <int MODE, bool CT, bool TAU = false, bool SELF = false>
+constexpr int epi_warps() { return (MODE == 0 && CT) ? 4 * CT_PARTS : (is_u<MODE>() && !TAU && !SELF) ? 8 : 4; }
+template <int MODE, bool CT, bool TAU = false, bool SELF = false>
+constexpr int kthreads() { return 64 + 32 * epi_warps<MODE, CT, TAU, SELF>(); }
 constexpr int SP_REG = 12;  // spike bins per (row, 256-bin tile) held in registers by the epilogue
 constexpr int TUNE_UPM_MAX = 8;  // most units per SM the autotuner tries for E X^T
 constexpr uint32_t TMEM_COLS = 512;
@@ -96,9 +101,6 @@ struct Cfg<3> {
     static constexpr uint32_t A_BYTES = 128 * BK * 2;
     static constexpr uint32_t B_BYTES = BN * BK * 2;
 };
-template <int MODE>
-constexpr bool is_u() { return MODE == 0 || MODE == 3; }
-
 template <>
 struct Cfg<1> {
     static constexpr int BM = 256;            // two 128-row halves
@@ -278,7 +280,7 @@ __device__ __forceinline__ float split_sum16<__half>(float w) {
 // tile's local Z_loc starts at 0 at its first bin t0, and Z[t] = a^(t-t0) Z[t0] + Z_loc[t]; a per-row
 // combine (reduce.cu) chains the tiles.
 template <int MODE, typename T16, bool TAU, bool BATCH, bool CT = false, bool SELF = false>
-__global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
+__global__ void __launch_bounds__(kthreads<MODE, CT, TAU, SELF>(), 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
                    const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1,
                    const __grid_constant__ TcArgs Ag, const TcBatch* __restrict__ batch) {
@@ -300,6 +302,12 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
     __shared__ int64_t s_ubeg[MAX_BATCH + 1];
     __shared__ int32_t s_mt[MAX_BATCH], s_m[MAX_BATCH];
     __shared__ int s_np;
+    // two epilogue warps per lane quarter (plain grid U product): the second warp hands its row sums of a
+    // tile to the first through two slots (by tile parity); pfull: a slot's sums are written, pempty: read
+    constexpr int NPART = (is_u<MODE>() && !CT) ? epi_warps<MODE, CT, TAU, SELF>() / 4 : 1;
+    __shared__ double s_prs[NPART == 2 ? 2 : 1][128];
+    __shared__ float s_pspv[NPART == 2 ? 2 : 1][128];
+    __shared__ uint64_t s_pfull[2][4], s_pempty[2][4];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -329,9 +337,14 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
         }
         for (int a = 0; a < 2; ++a) {
             tc::mbar_init(&tfull[a], 1);
-            tc::mbar_init(&tempty[a], epi_warps<MODE, CT>());
+            tc::mbar_init(&tempty[a], epi_warps<MODE, CT, TAU, SELF>());
         }
         tc::mbar_init(done, 1);
+        for (int a = 0; a < 2; ++a)
+            for (int qq = 0; qq < 4; ++qq) {
+                tc::mbar_init(&s_pfull[a][qq], 32);
+                tc::mbar_init(&s_pempty[a][qq], 32);
+            }
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -622,8 +635,10 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                 for (int u = 0; u < SP_REG; ++u) sb[u] = (kb + u < ke) ? (int)(A.bins[kb + u] - gt0) : BN;
                 // E is bin-blocked: bins [64 b, 64 b + 64) of row i at (b n + i) 64
                 T16* erow = reinterpret_cast<T16*>(A.E) + ((int64_t)(w.n0 / 64) * A.n + i) * 64;
+                // with two warps per lane quarter, warp part 0 takes the tile's first 128 bins, part 1 the rest
+                const int part = (NPART == 2) ? ((warp - 2) >> 2) : 0;
 #pragma unroll 1
-                for (int c = 0; c < BN / 32; ++c) {
+                for (int c = part * (BN / 32) / NPART; c < (part + 1) * (BN / 32) / NPART; ++c) {
                     uint32_t r[32];
                     tc::tmem_ld32(taddr + c * 32, r);
                     tc::tmem_ld_wait();
@@ -712,7 +727,32 @@ __global__ void __launch_bounds__(kthreads<MODE, CT>(), 1)
                     }
                 }
                 bad |= !(dteb <= 3.0e38f);
-                if (i < A.n) {
+                if constexpr (NPART == 2) {
+                    // part 1 hands its sums to part 0 (bounded waits: a partner that gave up ends this too)
+                    const int slot = it & 1;
+                    const uint32_t use = (uint32_t)(it >> 1);
+                    bool ok = true;
+                    if (part == 1) {
+                        ok = use == 0 || tc::mbar_wait(&s_pempty[slot][q], (use - 1) & 1u, abort_flag, Ag.limit_ns);
+                        if (ok) {
+                            s_prs[slot][row] = rsum;
+                            s_pspv[slot][row] = spv;
+                            tc::mbar_arrive(&s_pfull[slot][q]);
+                        }
+                    } else {
+                        ok = tc::mbar_wait(&s_pfull[slot][q], use & 1u, abort_flag, Ag.limit_ns);
+                        if (ok) {
+                            rsum += s_prs[slot][row];
+                            spv += s_pspv[slot][row];
+                            tc::mbar_arrive(&s_pempty[slot][q]);
+                        }
+                    }
+                    if (!ok) {
+                        raise();
+                        break;
+                    }
+                }
+                if (part == 0 && i < A.n) {
                     A.part_e[(int64_t)i * A.ntile + gtile] = ebi * rsum;
                     A.part_s[(int64_t)i * A.ntile + gtile] = (double)spv;
                 }
@@ -891,7 +931,7 @@ static cudaError_t run(glm_ctx* c, const CUtensorMap& a0, const CUtensorMap& a1,
         if (e != cudaSuccess) return e;
     }
     if (grid <= 0) grid = A.units < c->sm_count ? A.units : c->sm_count;
-    tc_gemm_kernel<MODE, T16, TAU, BATCH, CT, SELF><<<(unsigned)grid, kthreads<MODE, CT>(), smem, c->stream>>>(
+    tc_gemm_kernel<MODE, T16, TAU, BATCH, CT, SELF><<<(unsigned)grid, kthreads<MODE, CT, TAU, SELF>(), smem, c->stream>>>(
         a0, a1, b0, b1, A, batch);
     return cudaGetLastError();
 }
