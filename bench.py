@@ -717,7 +717,7 @@ def main():
     # dram__bytes_write.sum), N = 1000 x 200 000 bins, scaled to the launch by its neuron-bins (the traffic
     # of these kernels grows in proportion: X read once, the rates written once); None for kernels not
     # captured in their present form
-    traffic_per_unit = {}
+    traffic_per_unit = {("u_epilogue", "f16x1"): (415.170048e6 + 363.148544e6) / (1000 * 200000)}
     tpu = traffic_per_unit.get((name, form))
     roof["traffic"] = tpu * n * T if tpu is not None else None
     roof["kernel"] = name

@@ -43,101 +43,109 @@ __device__ __forceinline__ int32_t row_of(const SimtUArgs& A, int32_t l) {
     return l < A.m ? (A.rows ? A.rows[l] : l) : A.n;
 }
 
+// 4-byte asynchronous copy global -> shared (cp.async); pred false fills zeros and reads nothing
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool pred) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(src), "r"(pred ? 4 : 0) : "memory");
+}
+// 16-byte asynchronous copy (both addresses 16-byte aligned), through L2 only
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, bool pred) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src), "r"(pred ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // U tile rows i0..i0+127 (of the evaluated rows), bins t0..t0+127.  A = W (row-major, K contiguous), B = X (K x N, N contiguous).
 // Blocks run row tile fastest (block id = bin tile * mt + row tile): the row tiles of one bin tile read the
-// same X tile while it is in L2.  The inner k loop is unrolled by four with the next k-row's operands read
-// ahead into registers, and the epilogue runs as a rolled loop over rows staged in shared memory: fully
-// unrolled, the k-tile body and the 64 inlined exponentials of the epilogue outgrew the instruction cache
-// (ncu: "no instruction" was the largest stall).
+// same X tile while it is in L2.  Two-level sum: the products of two k-steps (32 sources) go into a
+// register tile sum, which is added to the thread's column of totals in shared memory.  With both levels
+// in registers the kernel needed over 200 registers and ran one block (eight warps) per SM; with the totals
+// in shared memory two blocks fit, and their sixteen warps hide the shared-memory latency of the inner
+// loop.  The epilogue runs as a rolled loop over rows staged in shared memory: fully unrolled, the k-tile
+// body and the 64 inlined exponentials of the epilogue outgrew the instruction cache.
 constexpr int EPI_LD = SB + 4;  // row stride of the epilogue staging (floats): 16-byte rows, fewer bank conflicts
-__global__ void __launch_bounds__(ST, 1) simt_u_kernel(const __grid_constant__ SimtUArgs A) {
-    // operands: As[2][SK][SBP] then Bs[2][SK][SBP]; after the k loop the same memory stages 64 rows of U
-    __shared__ __align__(16) float sm[(4 * SK * SBP > 64 * EPI_LD) ? 4 * SK * SBP : 64 * EPI_LD];
+constexpr int U_FLUSH = 2;      // k-steps per register tile sum
+constexpr size_t U_SMEM = (size_t)(4 * SK * SBP + 64 * ST) * sizeof(float);
+static_assert(4 * SK * SBP >= 64 * EPI_LD, "the epilogue staging reuses the operand tiles");
+__global__ void __launch_bounds__(ST, 2) simt_u_kernel(const __grid_constant__ SimtUArgs A) {
+    // operands: As[2][SK][SBP] then Bs[2][SK][SBP] (after the k loop the same memory stages 64 rows of U);
+    // then the totals, [64][ST]: element r * 8 + c of thread tid at [(r * 8 + c) * ST + tid]
+    extern __shared__ __align__(16) float sm[];
     auto As = reinterpret_cast<float(*)[SK][SBP]>(sm);
     auto Bs = reinterpret_cast<float(*)[SK][SBP]>(sm + 2 * SK * SBP);
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    float* tot = sm + 4 * SK * SBP;
+    const int tid = threadIdx.x;
+    // thread (ty, tx) owns rows ty*4.. and 64+ty*4.., columns tx*4.. and 64+tx*4..; a warp spans 4 ty x 8 tx,
+    // so each of its four 16-byte operand loads per k covers 64 or 128 contiguous bytes: one wavefront
+    const int tx = ((tid >> 5) & 1) * 8 + (tid & 7), ty = (tid >> 6) * 4 + ((tid >> 3) & 3);
     const int32_t mt = (A.m + SB - 1) / SB;
     const int32_t i0 = (int32_t)(blockIdx.x % mt) * SB;
     const int64_t bt = (int64_t)(blockIdx.x / mt);
     const int64_t t0 = bt * SB;
     const int32_t n = A.n;
-    float acc[8][8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
     // loader mapping
     const int a_row = tid >> 2, a_col = (tid & 3) * 4;  // rows a_row and a_row + 64, k a_col..+3
     const int b_row = tid >> 5, b_col = (tid & 31) * 4; // k rows b_row and b_row + 8, bins b_col..+3
-    float ra[2][4];
-    float4 rb[2];
-    auto load = [&](int k0) {
+    // operand tiles by asynchronous copies issued one k-step ahead (no staging registers): W transposed
+    // into [k][row] 4 bytes at a time, X rows 16 bytes at a time; zeros past n
+    auto load = [&](int k0, int buf) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int32_t i = row_of(A, i0 + a_row + 64 * h);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int32_t k = k0 + a_col + q;
-                ra[h][q] = (i < n && k < n) ? A.W[(int64_t)i * n + k] : 0.f;
+                const bool ok = i < n && k < n;
+                cp_async4(&As[buf][a_col + q][a_row + 64 * h], A.W + (ok ? (int64_t)i * n + k : 0), ok);
             }
             const int32_t kb = k0 + b_row + 8 * h;
-            rb[h] = (kb < n) ? *reinterpret_cast<const float4*>(A.X + (int64_t)kb * A.Tpad + t0 + b_col)
-                             : make_float4(0.f, 0.f, 0.f, 0.f);
+            cp_async16(&Bs[buf][b_row + 8 * h][b_col], A.X + (kb < n ? (int64_t)kb * A.Tpad + t0 + b_col : 0), kb < n);
         }
-    };
-    auto store = [&](int buf) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) As[buf][a_col + q][a_row + 64 * h] = ra[h][q];
-            *reinterpret_cast<float4*>(&Bs[buf][b_row + 8 * h][b_col]) = rb[h];
-        }
+        cp_async_commit();
     };
     const int nk = (n + SK - 1) / SK;
-    load(0);
-    store(0);
+#pragma unroll
+    for (int e = 0; e < 64; ++e) tot[e * ST + tid] = 0.f;
+    load(0, 0);
+    cp_async_wait_all();
     __syncthreads();
-    // Two-level accumulation: each k-step's 16 products are summed into a fresh FP32 tile sum, which is then
-    // added to the total.  A single running FP32 sum over ~1000 sources drops the many small terms (sources
-    // whose filtered train has decayed) below half an ulp of the total, and since most inputs are
+    // Two-level accumulation: a single running FP32 sum over ~1000 sources drops the many small terms
+    // (sources whose filtered train has decayed) below half an ulp of the total, and since most inputs are
     // excitatory those losses have one sign: at N = 1000 the mean of U came out ~2e-8 low, ~1.4e-8 of L.
-    // Tile sums keep those terms; the bias falls below 1e-10.
+    // Tile sums of 32 terms keep those terms.
+    float tl[8][8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) tl[r][c] = 0.f;
     for (int kt = 0; kt < nk; ++kt) {
         const int cur = kt & 1;
-        if (kt + 1 < nk) load((kt + 1) * SK);
-        float tl[8][8];
-#pragma unroll
-        for (int r = 0; r < 8; ++r)
-#pragma unroll
-            for (int c = 0; c < 8; ++c) tl[r][c] = 0.f;
-        float4 a0 = *reinterpret_cast<const float4*>(&As[cur][0][ty * 4]);
-        float4 a1 = *reinterpret_cast<const float4*>(&As[cur][0][64 + ty * 4]);
-        float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][0][tx * 4]);
-        float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][0][64 + tx * 4]);
+        if (kt + 1 < nk) load((kt + 1) * SK, cur ^ 1);
 #pragma unroll 4
         for (int k = 0; k < SK; ++k) {
-            const int kn = (k + 1 < SK) ? k + 1 : k;  // the next k-row (the last step re-reads its own)
-            const float4 na0 = *reinterpret_cast<const float4*>(&As[cur][kn][ty * 4]);
-            const float4 na1 = *reinterpret_cast<const float4*>(&As[cur][kn][64 + ty * 4]);
-            const float4 nb0 = *reinterpret_cast<const float4*>(&Bs[cur][kn][tx * 4]);
-            const float4 nb1 = *reinterpret_cast<const float4*>(&Bs[cur][kn][64 + tx * 4]);
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][k][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][k][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][k][64 + tx * 4]);
             const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
             for (int r = 0; r < 8; ++r)
 #pragma unroll
                 for (int c = 0; c < 8; ++c) tl[r][c] = fmaf(av[r], bv[c], tl[r][c]);
-            a0 = na0;
-            a1 = na1;
-            b0 = nb0;
-            b1 = nb1;
         }
+        if ((kt + 1) % U_FLUSH == 0 || kt + 1 == nk) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r)
+            for (int r = 0; r < 8; ++r)
 #pragma unroll
-            for (int c = 0; c < 8; ++c) acc[r][c] += tl[r][c];
-        if (kt + 1 < nk) store(cur ^ 1);
-        __syncthreads();
+                for (int c = 0; c < 8; ++c) {
+                    tot[(r * 8 + c) * ST + tid] += tl[r][c];
+                    tl[r][c] = 0.f;
+                }
+        }
+        cp_async_wait_all();  // the next k-step's tiles have landed
+        __syncthreads();      // ... for every thread, and every thread is done reading this one
     }
     // epilogue.  With v = (W X)_i[t]:  e^{U} = e^{b_i} (1 + expm1(v)).  e^{b_i} comes in FP64 and the
     // integer count of bins is kept apart from the FP32 sum of expm1(v), so the part of the integral that
@@ -153,9 +161,9 @@ __global__ void __launch_bounds__(ST, 1) simt_u_kernel(const __grid_constant__ S
 #pragma unroll
         for (int rr = 0; rr < 4; ++rr) {
             float* dst = sm + (ty * 4 + rr) * EPI_LD;
-            const int r = 4 * half + rr;
-            *reinterpret_cast<float4*>(dst + tx * 4) = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
-            *reinterpret_cast<float4*>(dst + 64 + tx * 4) = make_float4(acc[r][4], acc[r][5], acc[r][6], acc[r][7]);
+            const float* v = tot + ((4 * half + rr) * 8) * ST + tid;
+            *reinterpret_cast<float4*>(dst + tx * 4) = make_float4(v[0], v[ST], v[2 * ST], v[3 * ST]);
+            *reinterpret_cast<float4*>(dst + 64 + tx * 4) = make_float4(v[4 * ST], v[5 * ST], v[6 * ST], v[7 * ST]);
         }
         __syncthreads();
 #pragma unroll 1
@@ -204,14 +212,6 @@ struct SimtGArgs {
     float* part_g;    // [nsplit][n][n]
 };
 
-// 4-byte asynchronous copy global -> shared (cp.async); pred false fills zeros and reads nothing
-__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool pred) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(src), "r"(pred ? 4 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
 // part_g[s][i][j] = sum over bins of split s of E[i][t] X[j][t].  Both operands K contiguous; they are
 // transposed into shared memory ([k][row]) by 4-byte asynchronous copies issued one k-step ahead, so the
 // loads neither hold registers nor stall the products (with register staging the long-scoreboard wait on
@@ -225,7 +225,10 @@ __global__ void __launch_bounds__(ST, 2) simt_grad_kernel(const __grid_constant_
     auto As = reinterpret_cast<float(*)[SK][SBP]>(gsm);
     auto Bs = reinterpret_cast<float(*)[SK][SBP]>(gsm + 2 * SK * SBP);
     float* tot = gsm + 4 * SK * SBP;  // [64][ST]: element r * 8 + c of thread tid at [(r * 8 + c) * ST + tid]
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int tid = threadIdx.x;
+    // thread (ty, tx) owns rows ty*4.. and 64+ty*4.., columns tx*4.. and 64+tx*4..; a warp spans 4 ty x 8 tx,
+    // so each of its four 16-byte operand loads per k covers 64 or 128 contiguous bytes: one wavefront
+    const int tx = ((tid >> 5) & 1) * 8 + (tid & 7), ty = (tid >> 6) * 4 + ((tid >> 3) & 3);
     const int32_t i0 = blockIdx.y * SB, j0 = blockIdx.x * SB;
     const int64_t kb = (int64_t)blockIdx.z * A.k_per_split;
     const int64_t ke = min(kb + A.k_per_split, A.Tpad);
@@ -353,7 +356,9 @@ cudaError_t launch_simt_u_epilogue(glm_ctx* c, const float* W, const float* b, c
     A.m = rows ? m : P.n;
     // one block per (row tile, bin tile), row tiles fastest
     const int64_t blocks = (int64_t)((A.m + SB - 1) / SB) * A.ntile;
-    simt_u_kernel<<<(unsigned)blocks, ST, 0, c->stream>>>(A);
+    const cudaError_t e = cudaFuncSetAttribute(simt_u_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)U_SMEM);
+    if (e != cudaSuccess) return e;
+    simt_u_kernel<<<(unsigned)blocks, ST, U_SMEM, c->stream>>>(A);
     return cudaGetLastError();
 }
 
