@@ -137,8 +137,9 @@ int glm_set_problem(glm_ctx* ctx, int32_t n, int64_t n_bins, double dt, double t
  *   times_host:        double[offs[n]] spike times; row i strictly increasing, each in [t_begin, t_end).
  *   prec:              GLM_PREC_BF16 or GLM_PREC_F16 (the FP32 form covers the grid only: UNSUPPORTED).
  * Afterwards glm_prepare, glm_spike_term, glm_loglik_grad (without dL/dtau), glm_fit and
- * glm_cross_validate work on the columns as they do on bins; glm_filter, glm_fit_batch, the chunked form
- * and dL/dtau return UNSUPPORTED.  The host arrays may be freed on return.
+ * glm_cross_validate work on the columns as they do on bins, and a chunk length set by glm_set_chunk_bins
+ * (in columns) recomputes v chunk by chunk as X on the grid; glm_filter, glm_fit_batch and dL/dtau return
+ * UNSUPPORTED.  The host arrays may be freed on return.
  * Errors: INVALID_ARG, UNSORTED_SPIKES, SPIKE_OUT_OF_RANGE, OOM, CUDA, UNSUPPORTED, UNSUPPORTED_ARCH. */
 int glm_set_problem_ct(glm_ctx* ctx, int32_t n, double t_begin, double t_end, double tau, double delay,
                        const int64_t* offs_host, const double* times_host, glm_prec_t prec);
@@ -368,7 +369,8 @@ int glm_cross_validate(glm_ctx* ctx_train, glm_ctx* ctx_valid, const glm_fit_opt
  * chunk_bins bins only, and every evaluation filters, multiplies and reduces one chunk after the other
  * (the filter runs once per chunk and evaluation, so an evaluation costs one filter pass more).  0
  * (default) stores X for the whole recording.  Ignored for GLM_PREC_F32 and when chunk_bins covers the
- * recording.  Chunked problems cannot be batched (glm_fit_batch). */
+ * recording.  For glm_set_problem_ct it counts event columns.  Chunked problems cannot be batched
+ * (glm_fit_batch). */
 int glm_set_chunk_bins(glm_ctx* ctx, int64_t chunk_bins);
 
 /* How the 16-bit grid forms hold X (Eq. 4's filtered trains), for the next glm_set_problem.  split = 1

@@ -18,6 +18,14 @@ The steps follow the paper:
     and its limit e^b D where u = 0 (no input yet, so U = b on the whole interval);
   * dL/dW_ij = sum_k v_j(t_ik) - e^{b_i} sum_m v_j(e_m) tau (e^u - e^{u a_m}) / u      (Eq. 12, 14)
     with the limit tau (1 - a_m) at u = 0, and dL/db_i = q_i - int exp(U_i)         (Eq. 12, j = 0).
+  * dL/dtau (the paper chooses tau by cross-validation, Sec. 3.2, and gives no derivative; this is the
+    exact derivative of the L above).  With y_j(t) = sum over arrivals (t - e) exp(-(t - e) / tau),
+    dv_j/dtau = y_j / tau^2, and z = W y follows the recurrence of u: between events z decays with u and
+    gains gap * u (z(e + g) = exp(-g / tau) (z(e) + g u(e))); arrivals add nothing to z.  Then
+      dU_i(t)/dtau = z_i(t) / tau^2,
+      d/dtau of one interval's integral e^b F(u, D) = e^b [G(u, D) z / tau^2 + (F - D e^{u a}) / tau]
+    (G the interval weight above, dF/du = G; the explicit term by parts from F = int_0^D exp(u e^{-s/tau})
+    ds), so dL_i/dtau = sum_k z_i(t_ik) / tau^2 - e^{b_i} sum_m [...].
 Ei is scipy.special.expi (a library routine, FP64).  Pins: ``tests/test_ct_oracle_pins.py`` (adaptive
 quadrature of the intensity built from its definition, finite differences, the grid form at grid-aligned
 times, closed forms).
@@ -70,8 +78,8 @@ def _interval_weight(u, a, tau):
 
 
 def loglik_grad(offs, times, t_begin: float, t_end: float, tau: float, delay: float, W, b, *, grad: bool = True):
-    """L_i, L, dL/dW, dL/db of the continuous-time model (FP64).  Returns a dict with L (rows), L_total,
-    G, gb, C (the W-independent spike term sum_k v_j(t_ik)), q and the events."""
+    """L_i, L, dL/dW, dL/db, dL/dtau of the continuous-time model (FP64).  Returns a dict with L (rows),
+    L_total, G, gb, gtau_rows, gtau, C (the W-independent spike term sum_k v_j(t_ik)), q and the events."""
     offs = np.asarray(offs, dtype=np.int64)
     times = np.asarray(times, dtype=np.float64)
     W = np.asarray(W, dtype=np.float64)
@@ -82,11 +90,16 @@ def loglik_grad(offs, times, t_begin: float, t_end: float, tau: float, delay: fl
     # Eq. 8 / Eq. 13: u = U - b and v just after the arrivals at each event
     u_ev = np.zeros((n, M))
     v_ev = np.zeros((n, M))
+    z_ev = np.zeros((n, M))  # z = W y (dL/dtau)
     u = np.zeros(n)
     v = np.zeros(n)
+    z = np.zeros(n)
     t_prev = t_begin
     for m in range(M):
-        dec = np.exp(-(ev[m] - t_prev) / tau)
+        gap = ev[m] - t_prev
+        dec = np.exp(-gap / tau)
+        z = dec * (z + gap * u)
+        z_ev[:, m] = z
         u *= dec
         v *= dec
         nj, cnt = groups[m]
@@ -110,24 +123,30 @@ def loglik_grad(offs, times, t_begin: float, t_end: float, tau: float, delay: fl
     q = np.diff(offs).astype(np.float64)
     Lsp = q * b
     C = np.zeros((n, n))
+    zsp = np.zeros(n)  # sum over the row's spikes of z_i(t_ik)
     for i in range(n):
         ts = times[offs[i]:offs[i + 1]]
         if len(ts) == 0 or M == 0:
             continue
         ms = np.searchsorted(ev, ts, side="right") - 1
         ok = ms >= 0
-        dec = np.exp(-(ts[ok] - ev[ms[ok]]) / tau)
+        gap = ts[ok] - ev[ms[ok]]
+        dec = np.exp(-gap / tau)
         Lsp[i] += np.dot(u_ev[i, ms[ok]], dec)
+        zsp[i] = np.dot(z_ev[i, ms[ok]] + gap * u_ev[i, ms[ok]], dec)
         if grad:
             C[i] = v_ev[:, ms[ok]] @ dec
     L = Lsp - integ
     out = dict(L=L, L_total=float(L.sum()), q=q, events=ev, integ=integ)
     if grad:
         gint = np.zeros((n, n))
+        gtau_rows = zsp / tau ** 2
         if M:
             Gw = _interval_weight(u_ev, aa, tau)
             gint = np.exp(b)[:, None] * (Gw @ v_ev.T)
-        out.update(G=C - gint, gb=q - integ, C=C)
+            explicit = (F - Da * np.exp(u_ev * aa)) / tau  # (F - D e^{u a}) / tau, 0 where u = 0
+            gtau_rows = gtau_rows - np.exp(b) * ((Gw * z_ev).sum(axis=1) / tau ** 2 + explicit.sum(axis=1))
+        out.update(G=C - gint, gb=q - integ, C=C, gtau_rows=gtau_rows, gtau=float(gtau_rows.sum()))
     return out
 
 

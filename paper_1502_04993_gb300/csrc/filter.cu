@@ -294,10 +294,10 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache_f32_kernel(const _
 
 // 16-bit caches: X_hi and X_lo, X_lo = X - X_hi rounded again, both bin-blocked [Tpad / 64][n][64] (bins
 // [64 b, 64 b + 64) of row r at (b n + r) 64), the layout the tensor-core products read; X_hi alone (the
-// round-to-nearest 16-bit X) when A.Xlo is null.  One warp per (RPW rows, 4096-bin chunk): each lane stores
+// round-to-nearest 16-bit X) when A.Xlo is null (XLO false).  One warp per (RPW rows, 4096-bin chunk): each lane stores
 // its 8 bins of a row as one 16-byte word of X_hi and one of X_lo, so every warp store covers four whole
 // 128-byte lines.
-template <typename T16, int RPW>
+template <typename T16, int RPW, bool XLO>
 __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache16_kernel(const __grid_constant__ ScanConsts K,
                                                                        const __grid_constant__ FilterArgs A) {
     const int lane = threadIdx.x & 31;
@@ -336,12 +336,15 @@ __global__ void __launch_bounds__(FW_WARPS * 32) filter_cache16_kernel(const __g
             xs[k] = seg_scan16(K, xs[k], bits, pl_hi, pl_lo, lane, v);
             uint32_t ph[4], pl[4];
 #pragma unroll
-            for (int p = 0; p < 4; ++p) split_pair<T16>(v[2 * p], v[2 * p + 1], ph[p], pl[p]);
+            for (int p = 0; p < 4; ++p) {
+                if (XLO) split_pair<T16>(v[2 * p], v[2 * p + 1], ph[p], pl[p]);
+                else ph[p] = pack2<T16>(v[2 * p], v[2 * p + 1]);
+            }
             if (r < A.n) {
                 const int64_t tb = tl - A.s_begin * SEG;  // bin within the buffers
                 const int64_t o = ((tb >> 6) * A.n + r) * 64 + (tb & 63);
                 *reinterpret_cast<uint4*>(Xh + o) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-                if (Xl) *reinterpret_cast<uint4*>(Xl + o) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+                if (XLO) *reinterpret_cast<uint4*>(Xl + o) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
                 if (A.S) {  // the sources are the rows' own spikes: bits is also row r's raster here
                     uint32_t sw[4];
 #pragma unroll
@@ -628,10 +631,14 @@ cudaError_t launch_filter_cache(glm_ctx* c, int64_t s_begin, int64_t s_end, void
         A.ngroups = (P.n + FW16_RPW - 1) / FW16_RPW;
         const int64_t warps = (int64_t)A.ngroups * A.nchunks;
         const int64_t blocks = (warps + FW_WARPS - 1) / FW_WARPS;
-        if (P.prec == GLM_PREC_BF16)
-            filter_cache16_kernel<__nv_bfloat16, FW16_RPW><<<(unsigned)blocks, FW_WARPS * 32, 0, c->stream>>>(c->sc, A);
-        else
-            filter_cache16_kernel<__half, FW16_RPW><<<(unsigned)blocks, FW_WARPS * 32, 0, c->stream>>>(c->sc, A);
+        const dim3 g((unsigned)blocks), bl(FW_WARPS * 32);
+        if (P.prec == GLM_PREC_BF16) {
+            if (A.Xlo) filter_cache16_kernel<__nv_bfloat16, FW16_RPW, true><<<g, bl, 0, c->stream>>>(c->sc, A);
+            else filter_cache16_kernel<__nv_bfloat16, FW16_RPW, false><<<g, bl, 0, c->stream>>>(c->sc, A);
+        } else {
+            if (A.Xlo) filter_cache16_kernel<__half, FW16_RPW, true><<<g, bl, 0, c->stream>>>(c->sc, A);
+            else filter_cache16_kernel<__half, FW16_RPW, false><<<g, bl, 0, c->stream>>>(c->sc, A);
+        }
     }
     return cudaGetLastError();
 }

@@ -751,7 +751,10 @@ int glm_set_problem_ct(glm_ctx* c, int32_t n, double t_begin, double t_end, doub
     P.T = M;
     P.nseg = (M + SEG - 1) / SEG;
     P.Tpad = P.nseg * SEG;
-    P.Tc = P.Tpad;
+    // columns recomputed chunk by chunk (glm_set_chunk_bins counts columns here), on the filter's 4096-column
+    // units as on the grid
+    P.chunk = (c->chunk_req > 0 && round_up(c->chunk_req, 16 * SEG) < P.Tpad) ? round_up(c->chunk_req, 16 * SEG) : 0;
+    P.Tc = P.chunk ? P.chunk : P.Tpad;
     if ((rc = alloc_problem(c))) return cleanup(rc);
     Buffers& B = c->buf;
     std::vector<double> qd(n);

@@ -171,3 +171,37 @@ def test_row_without_input_closed_form():
         e = e[e < t1]
         integ = np.exp(b[1]) * tau * np.sum(1.0 - np.exp(-(t1 - e) / tau))
         assert r["C"][1, j] - r["G"][1, j] == pytest.approx(integ, rel=1e-12)
+
+
+def quad_loglik(offs, times, t0, t1, tau, d, W, b, i):
+    """L_i from its definition: the spike part from Eq. 3 at each spike, the integral by adaptive quadrature
+    between the arrival breakpoints."""
+    bp = breakpoints(times, t0, t1, d)
+    integ = 0.0
+    for lo, hi in zip(bp[:-1], bp[1:]):
+        f = lambda t: np.exp(u_direct(offs, times, tau, d, W, b, i, min(max(t, lo), hi - 1e-15 * hi)))
+        integ += quad(f, lo, hi, epsabs=0.0, epsrel=1e-13, limit=200)[0]
+    spk = sum(u_direct(offs, times, tau, d, W, b, i, t) for t in times[offs[i]:offs[i + 1]])
+    return spk - integ
+
+
+@pytest.mark.parametrize("seed,delay", [(4, 0.0015), (5, 0.0)])
+def test_dtau_matches_differences_of_the_definition(seed, delay):
+    """dL_i/dtau against central differences (h = 1e-4 tau) of L_i computed from the model's definition
+    (quadrature, not the oracle's recurrence), and against differences of the oracle's own L at a finer
+    step; W = 0 makes U = b flat, so dL/dtau = 0."""
+    offs, times, t0, t1, tau, d, W, b = small_case(seed, t_end=0.3, delay=delay)
+    r = oc.loglik_grad(offs, times, t0, t1, tau, d, W, b)
+    scale = np.abs(r["gtau_rows"]).sum()
+    h = 1e-4 * tau
+    for i in range(len(b)):
+        fd = (quad_loglik(offs, times, t0, t1, tau + h, d, W, b, i)
+              - quad_loglik(offs, times, t0, t1, tau - h, d, W, b, i)) / (2 * h)
+        assert r["gtau_rows"][i] == pytest.approx(fd, rel=1e-6, abs=1e-7 * scale), (i, r["gtau_rows"][i], fd)
+    h = 1e-6 * tau
+    fd = (oc.loglik_grad(offs, times, t0, t1, tau + h, d, W, b, grad=False)["L"]
+          - oc.loglik_grad(offs, times, t0, t1, tau - h, d, W, b, grad=False)["L"]) / (2 * h)
+    assert np.all(np.abs(r["gtau_rows"] - fd) <= 1e-8 * scale)
+    assert r["gtau"] == pytest.approx(r["gtau_rows"].sum(), rel=1e-15)
+    z = oc.loglik_grad(offs, times, t0, t1, tau, d, np.zeros_like(W), b)
+    assert np.all(z["gtau_rows"] == 0.0)

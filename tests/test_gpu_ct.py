@@ -217,3 +217,38 @@ def test_ct_cross_validation_recovers_tau(glm):
                             res["W"].cpu().numpy().astype(np.float64), res["b"].cpu().numpy().astype(np.float64),
                             grad=False)["L_total"]
         assert abs(L[kt, ka] - Lo) <= 1e-6 * abs(Lo)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+def test_ct_chunked_matches_stored(glm, prec):
+    """Event columns recomputed chunk by chunk (glm_set_chunk_bins counts columns): every U-product tile sees
+    the operands of the stored form, so L_i agree to the rounding of the final sums; E'V^T is summed over
+    the chunks in another order (gradient to FP32 rounding of its partial sums); and the chunked form
+    against the oracle at the usual bounds.  The chunk (8192 columns) cuts the ~40 000 columns into five
+    chunks, the last one ragged."""
+    w = workload(130, 20000, 5, 0.001)
+    W, b = params(w, 6)
+    args = (w["offs"], w["times"], w["t_begin"], w["t_end"], w["tau"], w["delay"])
+    with glm.GLM(0) as a, glm.GLM(0) as c:
+        a.set_problem_ct(*args, prec=prec)
+        c.set_chunk_bins(8192)
+        c.set_problem_ct(*args, prec=prec)
+        M = c.columns()
+        assert M == a.columns() and M > 4 * 8192
+        ra = a.loglik_grad(to_dev(W), to_dev(b))
+        La = ra["L_rows"].cpu().numpy()
+        r, ref = check(c, w, W, b, prec, "chunked")
+        Lc = r["L_rows"].cpu().numpy()
+        q = ref["q"]
+        assert np.all(np.abs(La - Lc) <= 1e-12 * (np.abs(La) + q))
+        Ca = a.spike_term()[0].cpu().numpy()
+        assert np.max(np.abs(ra["G"].cpu().numpy() - r["G"].cpu().numpy()) / (np.abs(Ca) + 1e-9)) <= 1e-5
+        # a fit on the chunked columns reaches the stored form's optimum
+        fa = a.fit(eta=1e-10, max_iter=300)
+        fc = c.fit(eta=1e-10, max_iter=300)
+        Wa = fa["W"].cpu().numpy().astype(np.float64)
+        Wc = fc["W"].cpu().numpy().astype(np.float64)
+        La_opt = oc.loglik_grad(*args, Wa, fa["b"].cpu().numpy().astype(np.float64), grad=False)["L_total"]
+        Lc_opt = oc.loglik_grad(*args, Wc, fc["b"].cpu().numpy().astype(np.float64), grad=False)["L_total"]
+        print(f"ct chunked {prec}: fits stored {La_opt:.9f} chunked {Lc_opt:.9f}")
+        assert abs(La_opt - Lc_opt) <= 2e-6 * abs(La_opt)
