@@ -136,9 +136,9 @@ int glm_set_problem(glm_ctx* ctx, int32_t n, int64_t n_bins, double dt, double t
  *   offs_host:         int64[n + 1] CSR offsets, offs[0] = 0, non-decreasing; offs[n] < 2^30.
  *   times_host:        double[offs[n]] spike times; row i strictly increasing, each in [t_begin, t_end).
  *   prec:              GLM_PREC_BF16 or GLM_PREC_F16 (the FP32 form covers the grid only: UNSUPPORTED).
- * Afterwards glm_prepare, glm_spike_term, glm_loglik_grad (without dL/dtau), glm_fit and
+ * Afterwards glm_prepare, glm_spike_term, glm_loglik_grad (dL/dtau included), glm_fit and
  * glm_cross_validate work on the columns as they do on bins, and a chunk length set by glm_set_chunk_bins
- * (in columns) recomputes v chunk by chunk as X on the grid; glm_filter, glm_fit_batch and dL/dtau return
+ * (in columns) recomputes v chunk by chunk as X on the grid; glm_filter and glm_fit_batch return
  * UNSUPPORTED.  The host arrays may be freed on return.
  * Errors: INVALID_ARG, UNSORTED_SPIKES, SPIKE_OUT_OF_RANGE, OOM, CUDA, UNSUPPORTED, UNSUPPORTED_ARCH. */
 int glm_set_problem_ct(glm_ctx* ctx, int32_t n, double t_begin, double t_end, double tau, double delay,
@@ -157,6 +157,12 @@ int glm_problem_columns(const glm_ctx* ctx, int64_t* n_columns);
  * Host function, needs no GPU.  Errors: INVALID_ARG (D < 0, tau <= 0, non-finite u, D or tau, NULL
  * outputs). */
 int glm_ct_interval(double u, double D, double tau, double* F_host, double* G_host);
+
+/* The explicit tau-derivative of the column integral F above at fixed u, as the dL/dtau epilogue computes
+ * it in FP32: dF/dtau = (F - D e^{u a}) / tau = u int_a^1 e^{u rho} (-ln rho) d rho (by parts from the
+ * definition of F; quadrature in 1 - rho for columns with 1 - a <= 0.1, the first form otherwise).  Host
+ * function, needs no GPU.  Errors: INVALID_ARG (as glm_ct_interval). */
+int glm_ct_interval_dtau(double u, double D, double tau, double* dFdtau_host);
 
 /* e^v - 1 for each of n FP32 values, as the plain FP32 form's link epilogue evaluates it (the rate of Eq. 5
  * is e^b (1 + (e^v - 1)) with v = sum_j W_ij X_j): Cody-Waite reduction and a Taylor series in double-float,
@@ -254,9 +260,12 @@ int glm_spike_term(glm_ctx* ctx, double* C_dev, double* q_dev);
  *   gb_dev:       double[n]      dL_i / db_i            (or NULL)
  *   gtau_host:    double         dL / dtau              (or NULL; synchronises).  tau enters through
  *                 a = exp(-dt/tau) in the kernel of Eq. 3 (it is not part of theta_i, Sec. 2.2):
- *                 dL/dtau = (a dt / tau^2) sum_{i,t} R_i[t] sum_j W_ij dX_j[t]/da.  The first request
- *                 on a problem also computes its W-independent spike part.  Tensor-core precisions
- *                 only (GLM_ERR_UNSUPPORTED for GLM_PREC_F32).
+ *                 dL/dtau = (a dt / tau^2) sum_{i,t} R_i[t] sum_j W_ij dX_j[t]/da.  In continuous time
+ *                 (glm_set_problem_ct) tau also sets each column's integral: dL/dtau = sum over spikes
+ *                 of z_i / tau^2 - e^{b_i} sum_m [G_m z_m / tau^2 + dF_m/dtau at fixed u] with z = W dv/dtau
+ *                 tau^2 (see glm_ct_interval_dtau).  The first request on a problem also computes its
+ *                 W-independent spike part.  Tensor-core precisions only (GLM_ERR_UNSUPPORTED for
+ *                 GLM_PREC_F32).
  * Errors: NO_PROBLEM, INVALID_ARG, NONFINITE (exp(U) overflowed; outputs are then undefined), CUDA,
  * TIMEOUT, UNSUPPORTED, OOM. */
 int glm_loglik_grad(glm_ctx* ctx, const float* W_dev, const float* b_dev, double* L_rows_dev,

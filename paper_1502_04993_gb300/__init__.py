@@ -98,6 +98,7 @@ SIGNATURES["glm_check_wait_limit"] = ([_vp, _f64], ctypes.c_int)
 SIGNATURES["glm_set_problem_ct"] = ([_vp, _i32, _f64, _f64, _f64, _f64, _vp, _vp, ctypes.c_int], ctypes.c_int)
 SIGNATURES["glm_problem_columns"] = ([_vp, ctypes.POINTER(_i64)], ctypes.c_int)
 SIGNATURES["glm_ct_interval"] = ([_f64, _f64, _f64, ctypes.POINTER(_f64), ctypes.POINTER(_f64)], ctypes.c_int)
+SIGNATURES["glm_ct_interval_dtau"] = ([_f64, _f64, _f64, ctypes.POINTER(_f64)], ctypes.c_int)
 SIGNATURES["glm_expm1"] = ([_vp, _i64, _vp], ctypes.c_int)
 SIGNATURES["glm_cross_validate"] = ([_vp, _vp, ctypes.POINTER(FitOpts), _vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp],
                                      ctypes.c_int)
@@ -233,6 +234,16 @@ def ct_interval(u: float, D: float, tau: float):
     if rc != GLM_OK:
         raise GLMError(rc, "glm_ct_interval")
     return F.value, G.value
+
+
+def ct_interval_dtau(u: float, D: float, tau: float) -> float:
+    """dF/dtau at fixed u of one continuous-time column (glm_ct_interval_dtau; host code, no GPU needed)."""
+    lib = load_library()
+    out = ctypes.c_double()
+    rc = lib.glm_ct_interval_dtau(float(u), float(D), float(tau), ctypes.byref(out))
+    if rc != GLM_OK:
+        raise GLMError(rc, "glm_ct_interval_dtau")
+    return out.value
 
 
 def split_recording(offs, bins, n_bins: int, t_split: int):

@@ -370,3 +370,15 @@ extern "C" int glm_ct_interval(double u, double D, double tau, double* F, double
     *G = tau * (double)eg;
     return GLM_OK;
 }
+
+// dF/dtau at fixed u for one column (ct_dtau), on the host, by the same FP32 code as the epilogue.
+extern "C" int glm_ct_interval_dtau(double u, double D, double tau, double* dFdtau) {
+    if (!(D >= 0) || !(tau > 0) || !std::isfinite(u) || !std::isfinite(D) || !std::isfinite(tau) || !dFdtau)
+        return GLM_ERR_INVALID_ARG;
+    float col[8];
+    glm::ct_column(D, tau, col);
+    float dF = 0.f, eg = 0.f;
+    glm::ct_link((float)u, col, (float)tau, &dF, &eg);
+    *dFdtau = (double)glm::ct_dtau((float)u, col[0], col[1], (float)tau, dF);
+    return GLM_OK;
+}

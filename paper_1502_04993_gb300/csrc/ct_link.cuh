@@ -120,4 +120,34 @@ __host__ __device__ __forceinline__ void ct_link(float u, const float* col, floa
     }
 }
 
+// The explicit tau-derivative of one column's integral at fixed u (for dL/dtau):
+//   T(u, D) = dF/dtau at fixed u = (F - D e^{u a}) / tau = u int_a^1 e^{u rho} (-ln rho) d rho
+// (by parts from F = int_0^D exp(u e^{-s/tau}) ds; the second form by rho = e^{-s/tau}).  For a short
+// column (oma <= 0.1) the first form cancels to ~oma of its terms, so the integral is taken by 4-node
+// Gauss-Legendre quadrature in 1 - rho (panels of 4 nodes where |u| oma > 1, as in ct_link), with
+// -ln rho = -log1p(-(1 - rho)); for oma > 0.1 the first form loses less than a digit.  dF = F - D from
+// ct_link; D from the column constants (ct_length; not needed where u a = 0: then F - D e^{ua} = dF).
+__host__ __device__ __forceinline__ float ct_length(float a, float oma, float tau) {
+    return a < 0.5f ? -tau * logf(a) : -tau * log1pf(-oma);  // each form where its argument is exact
+}
+__host__ __device__ __forceinline__ float ct_dtau(float u, float a, float oma, float tau, float dF) {
+    if (oma > 0.1f) {
+        const float ua = u * a;
+        if (ua == 0.f) return dF / tau;
+        return (dF - ct_length(a, oma, tau) * expm1f(ua)) / tau;
+    }
+    const float w = fabsf(u) * oma;
+    int P = (w <= 1.f) ? 1 : (int)ceilf(w);
+    if (P > CT_PANELS_MAX) P = CT_PANELS_MAX;
+    const float h = oma / (float)P;
+    float sum = 0.f;
+    for (int p = 0; p < P; ++p) {
+        const float x0 = h * ((float)p + GL4_E0), x1 = h * ((float)p + GL4_E1);  // 1 - rho at the nodes
+        const float x2 = h * ((float)p + GL4_E2), x3 = h * ((float)p + GL4_E3);
+        sum += GL4_W0 * (ct_exp(u - u * x0) * -log1pf(-x0) + ct_exp(u - u * x3) * -log1pf(-x3)) +
+               GL4_W1 * (ct_exp(u - u * x1) * -log1pf(-x1) + ct_exp(u - u * x2) * -log1pf(-x2));
+    }
+    return u * 0.5f * h * sum;
+}
+
 }  // namespace glm

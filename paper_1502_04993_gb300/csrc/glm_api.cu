@@ -362,8 +362,9 @@ int prepare_dtau(glm_ctx* c) {
     Buffers& B = c->buf;
     const Problem& P = c->pb;
     int rc;
+    // grid: 5 sums per row and tile; continuous time: 7 per row, tile and part of a tile's columns
     if (!B.part_tau &&
-        ((rc = ws_alloc_t(c, &B.part_tau, 5 * (size_t)P.n * (P.Tpad / tc_tile_t()))) ||
+        ((rc = ws_alloc_t(c, &B.part_tau, (P.ct ? 7 * CT_PARTS : 5) * (size_t)P.n * (P.Tpad / tc_tile_t()))) ||
          (rc = ws_alloc_t(c, &B.tau_rows, P.n))))
         return rc;
     return GLM_OK;
@@ -826,8 +827,6 @@ int glm_loglik_grad(glm_ctx* c, const float* W, const float* b, double* L_rows, 
     if (!W || !b) return fail(c, GLM_ERR_INVALID_ARG, "W and b are required");
     if (gtau_host && c->pb.prec == GLM_PREC_F32)
         return fail(c, GLM_ERR_UNSUPPORTED, "dL/dtau is computed by the tensor-core precisions only");
-    if (gtau_host && c->pb.ct)
-        return fail(c, GLM_ERR_UNSUPPORTED, "dL/dtau is computed for the grid form only");
     if (gtau_host && c->pb.self_shift > 0)
         return fail(c, GLM_ERR_UNSUPPORTED, "dL/dtau is not computed with a self-delay");
     DeviceGuard g(c->device);
@@ -846,7 +845,7 @@ int glm_loglik_grad(glm_ctx* c, const float* W, const float* b, double* L_rows, 
         GLM_CK(cudaMemcpyAsync(&t, c->buf.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         GLM_CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
         const Problem& P = c->pb;
-        *gtau_host = P.a * P.dt / (P.tau * P.tau) * t;  // da/dtau = a dt / tau^2
+        *gtau_host = P.ct ? t : P.a * P.dt / (P.tau * P.tau) * t;  // grid: da/dtau = a dt / tau^2
     }
     if (L_total_host) {
         double* dtot = c->buf.scal;

@@ -246,8 +246,62 @@ __global__ void tau_rows_kernel(int32_t n, int64_t ntile, double dt, double A256
     if (lane == 0) rows[i] = spk - dt * eb[i] * integ;
 }
 
+// Continuous time: row i's dL/dtau itself, r_i = sum_{spikes} z / tau^2 - e^{c_i} (sum_m e^sh (G_m / tau) z_m /
+// tau + sum_m e^sh dF_m/dtau), with z = W y at the column starts (y = tau^2 dv/dtau).  The epilogue left,
+// per tile and part of a tile's columns (in column order: tile-major, part-minor), the sums P1, P2, Zend,
+// P3, P4, Pex and the part's decay product Aend; with z_start of the first segment 0 (no input before
+// t_begin) and z_start(next) = Aend z_start + Zend, a weight family contributes sum z_start P + P'.  The
+// chain of segments is cut into contiguous lane ranges as in tau_rows_kernel, each range's own decay
+// product composing the shuffle scan.
+__global__ void ct_tau_rows_kernel(int32_t n, int64_t ntile, double tau, const double* __restrict__ eb,
+                                   const double* __restrict__ part_tau, double* __restrict__ rows) {
+    const int32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const int64_t pl = (int64_t)CT_PARTS * n * ntile;  // one value over all parts, rows and tiles
+    const int64_t nseg = ntile * CT_PARTS;
+    const int64_t len = (nseg + 31) / 32;
+    const int64_t s0 = min((int64_t)lane * len, nseg), s1 = min(s0 + len, nseg);
+    double z = 0.0, w = 1.0, Qe = 0.0, Se = 0.0, Qs = 0.0, Ss = 0.0, Ex = 0.0;
+    for (int64_t sg = s0; sg < s1; ++sg) {
+        const int64_t tile = sg / CT_PARTS, part = sg % CT_PARTS;
+        const int64_t o = (part * n + i) * ntile + tile;
+        const double P1 = part_tau[o], P2 = part_tau[pl + o], Ze = part_tau[2 * pl + o];
+        const double P3 = part_tau[3 * pl + o], P4 = part_tau[4 * pl + o], X = part_tau[5 * pl + o];
+        const double Ae = part_tau[6 * pl + o];
+        Qe = fma(w, P1, Qe);
+        Se += fma(z, P1, P2);
+        Qs = fma(w, P3, Qs);
+        Ss += fma(z, P3, P4);
+        Ex += X;
+        z = fma(Ae, z, Ze);
+        w *= Ae;
+    }
+    double v = z, m = w;
+    for (int d = 1; d < 32; d <<= 1) {
+        const double o = __shfl_up_sync(0xffffffffu, v, d), om = __shfl_up_sync(0xffffffffu, m, d);
+        if (lane >= d) {
+            v = fma(m, o, v);
+            m *= om;
+        }
+    }
+    double zin = __shfl_up_sync(0xffffffffu, v, 1);
+    if (lane == 0) zin = 0.0;
+    double integ = fma(zin, Qe, Se);
+    double spk = fma(zin, Qs, Ss);
+    integ = warp_sum(integ);
+    spk = warp_sum(spk);
+    Ex = warp_sum(Ex);
+    if (lane == 0) rows[i] = spk / (tau * tau) - eb[i] * (integ / tau + Ex);
+}
+
 cudaError_t launch_tau_rows(glm_ctx* c, double* rows) {
     const Problem& P = c->pb;
+    if (P.ct) {
+        ct_tau_rows_kernel<<<(P.n + 7) / 8, 256, 0, c->stream>>>(P.n, P.Tpad / tc_tile_t(), P.tau, c->buf.eb,
+                                                                 c->buf.part_tau, rows);
+        return cudaGetLastError();
+    }
     const double A256 = std::exp(-(double)SEG * P.dt / P.tau);
     tau_rows_kernel<<<(P.n + 7) / 8, 256, 0, c->stream>>>(P.n, P.Tpad / tc_tile_t(), P.dt, A256, c->buf.eb,
                                                           c->buf.part_tau, rows);

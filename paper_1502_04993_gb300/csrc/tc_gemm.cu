@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kthreads<MODE, CT, TAU, SELF>(), 1)
                    const __grid_constant__ TcArgs Ag, const TcBatch* __restrict__ batch) {
     using C = Cfg<MODE>;
     using L = Layout<MODE>;
-    static_assert(!CT || (MODE == 0 && !TAU), "the continuous-time epilogue is a U-product epilogue without tau partials");
+    static_assert(!CT || MODE == 0, "the continuous-time epilogue is a U-product epilogue");
     static_assert(!SELF || (is_u<MODE>() && !TAU && !CT && !BATCH), "the self-delay is a grid U-product epilogue option");
     static_assert(MODE != 3 || !CT, "the continuous-time columns are always split");
     extern __shared__ uint8_t smem_raw[];
@@ -525,6 +525,12 @@ __global__ void __launch_bounds__(kthreads<MODE, CT, TAU, SELF>(), 1)
                 const float tgeb = (float)(ebi * (double)A.ct_tau) * esh;
                 bool bad = !(tgeb <= 3.0e38f);
                 float s = 0.f, spv = 0.f;
+                // TAU: with z = W y (y_j = sum over arrivals (t - e) exp(-(t - e) / tau), dU/dtau = z / tau^2),
+                // z at column m of the part is Pm z_start + z_loc[m], Pm the product of the part's decays so
+                // far; the part leaves P1 = sum e^sh (G / tau) Pm, P2 = sum e^sh (G / tau) z_loc, Zend, over its
+                // spike columns P3 = sum Pm and P4 = sum z_loc, Pex = sum e^sh dF/dtau at fixed u (ct_dtau), and
+                // Aend = the product of its decays; a per-row scan (reduce.cu) chains the parts and tiles
+                float zl = 0.f, pw = 1.f, p1 = 0.f, p2 = 0.f, p3 = 0.f, p4 = 0.f, pex = 0.f;
                 int64_t kb = 0, ke = 0;
                 if (i < A.n) {
                     const int64_t sgi = (int64_t)i * A.nseg + gtile, o0 = A.offs[i];
@@ -589,6 +595,24 @@ __global__ void __launch_bounds__(kthreads<MODE, CT, TAU, SELF>(), 1)
                         if ((sm >> (e + 1)) & 1u) spv += __uint_as_float(r[e + 1]);
                         pk[e >> 1] = pack16<T16>(e0, e1);
                     }
+                    if constexpr (TAU) {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            if (gt0 + c0 + e < A.T) {  // columns in order; the padding past T takes no part
+                                const float u = __uint_as_float(r[e]), ca = kc[e].x, coma = kc[e].y;
+                                const float egs = esh * gv[e];
+                                p1 = fmaf(egs, pw, p1);
+                                p2 = fmaf(egs, zl, p2);
+                                if ((sm >> e) & 1u) {
+                                    p3 += pw;
+                                    p4 += zl;
+                                }
+                                pex = fmaf(esh, ct_dtau(u, ca, coma, A.ct_tau, fv[e]), pex);
+                                zl = (ca == 0.f) ? 0.f : ca * fmaf(ct_length(ca, coma, A.ct_tau), u, zl);
+                                pw *= ca;
+                            }
+                        }
+                    }
                     if (i < A.n)
                         *reinterpret_cast<uint4*>(erow + (int64_t)(c0 >> 6) * A.n * 64 + (c0 & 63)) =
                             make_uint4(pk[0], pk[1], pk[2], pk[3]);
@@ -598,6 +622,16 @@ __global__ void __launch_bounds__(kthreads<MODE, CT, TAU, SELF>(), 1)
                     const int64_t o = (int64_t)part * A.n * A.ntile + (int64_t)i * A.ntile + gtile;
                     A.part_e[o] = ebi * rsum;
                     A.part_s[o] = (double)spv;
+                    if constexpr (TAU) {  // [7][CT_PARTS][n][ntile]
+                        const int64_t pl = (int64_t)CT_PARTS * A.n * A.ntile;
+                        A.part_tau[o] = p1;
+                        A.part_tau[pl + o] = p2;
+                        A.part_tau[2 * pl + o] = zl;
+                        A.part_tau[3 * pl + o] = p3;
+                        A.part_tau[4 * pl + o] = p4;
+                        A.part_tau[5 * pl + o] = pex;
+                        A.part_tau[6 * pl + o] = pw;
+                    }
                 }
                 if (bad && i < A.n) atomicOr(A.flags, 1);
             } else if constexpr (is_u<MODE>()) {
@@ -1033,9 +1067,11 @@ cudaError_t launch_tc_u_epilogue(glm_ctx* c, const float* W, const float* b, boo
     A.part_s = c->buf.part_s;
     A.idesc |= 1u << 16;  // B (X) is N-major
     if (P.ct) {
-        if (tau) return cudaErrorNotSupported;
-        if (P.prec == GLM_PREC_BF16)
+        if (P.prec == GLM_PREC_BF16) {
+            if (tau) return run<0, __nv_bfloat16, true, false, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
             return run<0, __nv_bfloat16, false, false, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
+        }
+        if (tau) return run<0, __half, true, false, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
         return run<0, __half, false, false, true>(c, c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], A);
     }
     if (P.xlo) return run_u<0>(c, A, tau, P.self_shift > 0, W);

@@ -252,3 +252,47 @@ def test_ct_chunked_matches_stored(glm, prec):
         Lc_opt = oc.loglik_grad(*args, Wc, fc["b"].cpu().numpy().astype(np.float64), grad=False)["L_total"]
         print(f"ct chunked {prec}: fits stored {La_opt:.9f} chunked {Lc_opt:.9f}")
         assert abs(La_opt - Lc_opt) <= 2e-6 * abs(La_opt)
+
+
+def dtau_check(ctx, w, W, b, label):
+    r = ctx.loglik_grad(to_dev(W), to_dev(b), tau_grad=True)
+    ref = oc.loglik_grad(w["offs"], w["times"], w["t_begin"], w["t_end"], w["tau"], w["delay"],
+                         W.astype(np.float64), b.astype(np.float64))
+    scale = np.abs(ref["gtau_rows"]).sum()
+    print(f"ct dL/dtau {label}: gpu {r['gtau']:.6e} oracle {ref['gtau']:.6e} scale {scale:.3e}")
+    assert abs(r["gtau"] - ref["gtau"]) <= 1e-4 * scale
+    return r, ref
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+@pytest.mark.parametrize("n,T,seed,delay", [(50, 20000, 0, 0.001), (37, 9001, 1, 0.0015), (130, 5000, 2, 0.0)])
+def test_ct_dtau_matches_oracle(ctx, prec, n, T, seed, delay):
+    """dL/dtau of the continuous-time form (the oracle's derivative is pinned to differences of the model's
+    definition) within 1e-4 of the sum of the rows' contributions, as on the grid."""
+    w = workload(n, T, seed, delay)
+    W, b = params(w, seed + 1)
+    ctx.set_problem_ct(w["offs"], w["times"], w["t_begin"], w["t_end"], w["tau"], w["delay"], prec=prec)
+    r, _ = dtau_check(ctx, w, W, b, f"{prec} n={n} T={T} d={delay}")
+    r2 = ctx.loglik_grad(to_dev(W), to_dev(b), tau_grad=True)
+    assert r2["gtau"] == r["gtau"]  # deterministic
+
+
+def test_ct_dtau_long_gaps_and_chunks(glm):
+    """Silent stretches make columns of 5 tau (1 - a = 0.99: the closed form of dF/dtau) and of 200 tau
+    (a = 0 in FP32: the decay chain restarts); the same recording with its columns in chunks gives the
+    same dL/dtau."""
+    w = workload(60, 6000, 7, 0.001)
+    times, offs = w["times"].copy(), w["offs"]
+    # a 50 ms gap after 2 s and a 2 s gap after 4 s: every later spike moves
+    times = np.where(times >= 2.0, times + 0.05, times)
+    times = np.where(times >= 4.05, times + 2.0, times)
+    w = dict(w, times=times, t_end=w["t_end"] + 2.05)
+    W, b = params(w, 8)
+    args = (w["offs"], w["times"], w["t_begin"], w["t_end"], w["tau"], w["delay"])
+    with glm.GLM(0) as a, glm.GLM(0) as c:
+        a.set_problem_ct(*args, prec="f16")
+        ra, _ = dtau_check(a, w, W, b, "gaps")
+        c.set_chunk_bins(4096)
+        c.set_problem_ct(*args, prec="f16")
+        rc = c.loglik_grad(to_dev(W), to_dev(b), tau_grad=True)
+        assert rc["gtau"] == pytest.approx(ra["gtau"], rel=1e-12, abs=1e-9)
