@@ -626,6 +626,7 @@ struct FitBatch {
     const double* C[FB_MAX];
     const float* part_g[FB_MAX];
     int64_t ntile[FB_MAX];
+    int32_t planes[FB_MAX];  // planes of part_e / part_s: 1 on the grid, CT_PARTS for event columns
     int32_t nsplit[FB_MAX];
     double dt[FB_MAX];
     int* flags[FB_MAX];
@@ -731,12 +732,15 @@ __global__ void fb_reduce_rows_kernel(const FitBatch* __restrict__ B, int32_t nr
     const int p = fb_prob(B->rbeg, B->np, r);
     const int32_t i = r - B->rbeg[p];
     const int64_t nt = B->ntile[p];
-    const double* pe = B->part_e[p] + (int64_t)i * nt;
-    const double* ps = B->part_s[p] + (int64_t)i * nt;
+    const int64_t plane = (int64_t)(B->rbeg[p + 1] - B->rbeg[p]) * nt;
     double integ = 0.0, spk = 0.0;
-    for (int64_t t = lane; t < nt; t += 32) {
-        integ += pe[t];
-        spk += ps[t];
+    for (int pl = 0; pl < B->planes[p]; ++pl) {
+        const double* pe = B->part_e[p] + pl * plane + (int64_t)i * nt;
+        const double* ps = B->part_s[p] + pl * plane + (int64_t)i * nt;
+        for (int64_t t = lane; t < nt; t += 32) {
+            integ += pe[t];
+            spk += ps[t];
+        }
     }
     for (int off = 16; off >= 1; off >>= 1) {
         integ += __shfl_xor_sync(0xffffffffu, integ, off);
@@ -909,6 +913,7 @@ int fit_run_batch(glm_ctx* const* cs, int np, const glm_fit_opts_t* o, float* co
         hb.C[p] = c->buf.C;
         hb.part_g[p] = c->buf.part_g;
         hb.ntile[p] = c->pb.Tpad / tc_tile_t();
+        hb.planes[p] = c->pb.ct ? CT_PARTS : 1;
         hb.nsplit[p] = tc_nsplit(c);
         hb.dt[p] = c->pb.dt_int;
         hb.flags[p] = c->buf.flags;
