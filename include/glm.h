@@ -138,8 +138,8 @@ int glm_set_problem(glm_ctx* ctx, int32_t n, int64_t n_bins, double dt, double t
  *   prec:              GLM_PREC_BF16 or GLM_PREC_F16 (the FP32 form covers the grid only: UNSUPPORTED).
  * Afterwards glm_prepare, glm_spike_term, glm_loglik_grad (dL/dtau included), glm_fit and
  * glm_cross_validate work on the columns as they do on bins, and a chunk length set by glm_set_chunk_bins
- * (in columns) recomputes v chunk by chunk as X on the grid, and glm_fit_batch fits several such problems
- * together; glm_filter returns UNSUPPORTED.  The host arrays may be freed on return.
+ * (in columns) recomputes v chunk by chunk as X on the grid; glm_filter and glm_fit_batch return
+ * UNSUPPORTED.  The host arrays may be freed on return.
  * Errors: INVALID_ARG, UNSORTED_SPIKES, SPIKE_OUT_OF_RANGE, OOM, CUDA, UNSUPPORTED, UNSUPPORTED_ARCH. */
 int glm_set_problem_ct(glm_ctx* ctx, int32_t n, double t_begin, double t_end, double tau, double delay,
                        const int64_t* offs_host, const double* times_host, glm_prec_t prec);
@@ -336,16 +336,15 @@ int glm_fit(glm_ctx* ctx, const glm_fit_opts_t* opts, float* W_dev, float* b_dev
             glm_fit_report_t* report);
 
 /* Fit several independent recordings together (the batched form of glm_fit).  ctxs[p] holds problem p
- * (set with glm_set_problem, or all with glm_set_problem_ct; uneven n and n_bins or columns are fine);
- * all contexts are on the same device and use the same tensor-core precision (GLM_PREC_BF16 or
- * GLM_PREC_F16).  Every evaluation is one launch of each
+ * (set with glm_set_problem; uneven n and n_bins are fine); all contexts are on the same device and use
+ * the same tensor-core precision (GLM_PREC_BF16 or GLM_PREC_F16).  Every evaluation is one launch of each
  * contraction over the tiles of all problems, and one optimiser iteration for all of them (directions,
  * line-search rounds, gradient, update) is recorded once as a CUDA graph and replayed; a line search that
  * is still open after an iteration's rounds continues in the next iteration.  All work runs on ctxs[0]'s
  * stream.  W_dev[p], b_dev[p]: as for glm_fit; row_status_host and reports: optional arrays of n_prob
  * (row_status_host[p] may be NULL).  n_prob: 1..32.  Returns the worst of the per-problem glm_fit
- * statuses or a negative GLM_ERR_* (INVALID_ARG for mixed devices, precisions, X splits, or grid and
- * continuous-time problems; UNSUPPORTED for GLM_PREC_F32, chunked problems, row ranges and self-delays).  Synchronises ctxs[0]'s stream. */
+ * statuses or a negative GLM_ERR_* (INVALID_ARG for mixed devices, precisions or X splits; UNSUPPORTED for
+ * GLM_PREC_F32, continuous-time and chunked problems, row ranges and self-delays).  Synchronises ctxs[0]'s stream. */
 #define GLM_FIT_BATCH_MAX 32
 int glm_fit_batch(glm_ctx* const* ctxs, int32_t n_prob, const glm_fit_opts_t* opts, float* const* W_dev,
                   float* const* b_dev, int8_t* const* row_status_host, glm_fit_report_t* reports);

@@ -626,7 +626,7 @@ struct FitBatch {
     const double* C[FB_MAX];
     const float* part_g[FB_MAX];
     int64_t ntile[FB_MAX];
-    int32_t planes[FB_MAX];  // planes of part_e / part_s: 1 on the grid, CT_PARTS for event columns
+    int32_t planes[FB_MAX];  // planes of part_e / part_s (1: the grid form, the only one batched)
     int32_t nsplit[FB_MAX];
     double dt[FB_MAX];
     int* flags[FB_MAX];

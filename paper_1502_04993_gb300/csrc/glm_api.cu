@@ -1139,7 +1139,7 @@ int glm_fit_batch(glm_ctx* const* cs, int32_t np, const glm_fit_opts_t* opts, fl
         if (c->pb.prec != c0->pb.prec) return fail(c0, GLM_ERR_INVALID_ARG, "contexts with different precisions");
         if (c->pb.xlo != c0->pb.xlo) return fail(c0, GLM_ERR_INVALID_ARG, "contexts with different X splits");
         if (c->pb.chunk) return fail(c0, GLM_ERR_UNSUPPORTED, "glm_fit_batch needs X stored (no chunking)");
-        if (c->pb.ct != c0->pb.ct) return fail(c0, GLM_ERR_INVALID_ARG, "grid and continuous-time problems mixed");
+        if (c->pb.ct) return fail(c0, GLM_ERR_UNSUPPORTED, "glm_fit_batch serves the grid form");
         if (c->row_r1 >= 0) return fail(c0, GLM_ERR_UNSUPPORTED, "glm_fit_batch fits whole problems (no row range)");
         if (c->pb.self_shift > 0) return fail(c0, GLM_ERR_UNSUPPORTED, "glm_fit_batch has no self-delay");
         for (int32_t q = 0; q < p; ++q)

@@ -1262,11 +1262,7 @@ cudaError_t launch_tc_u_batch(glm_ctx* c0, const void* dev_u) {
     const TcBatch* b = static_cast<const TcBatch*>(dev_u);
     const CUtensorMap* m = c0->tmap;
     const bool bf = c0->pb.prec == GLM_PREC_BF16;
-    if (c0->pb.ct) {  // every problem of a batch has the same form (checked by glm_fit_batch)
-        if (bf) return run<0, __nv_bfloat16, false, true, true>(c0, m[0], m[1], m[2], m[3], Ag, b, c0->sm_count);
-        return run<0, __half, false, true, true>(c0, m[0], m[1], m[2], m[3], Ag, b, c0->sm_count);
-    }
-    if (!c0->pb.xlo) {
+    if (!c0->pb.xlo) {  // every problem of a batch has the same form (checked by glm_fit_batch)
         if (bf) return run<3, __nv_bfloat16, false, true>(c0, m[0], m[1], m[2], m[3], Ag, b, c0->sm_count);
         return run<3, __half, false, true>(c0, m[0], m[1], m[2], m[3], Ag, b, c0->sm_count);
     }

@@ -175,12 +175,9 @@ def test_ct_error_paths(glm, ctx):
     with pytest.raises(glm.GLMError) as e:
         ctx.filter(0, 2)
     assert e.value.code == -10  # UNSUPPORTED
-    # one batch holds grid or continuous-time problems, not both
-    with glm.GLM(0) as g:
-        g.set_problem(offs, np.array([10, 20], dtype=np.int32), 100, 0.001, 0.01, prec="bf16")
-        with pytest.raises(glm.GLMError) as e:
-            glm.fit_batch([ctx, g])
-        assert e.value.code == -1  # INVALID_ARG
+    with pytest.raises(glm.GLMError) as e:
+        glm.fit_batch([ctx])
+    assert e.value.code == -10  # UNSUPPORTED: batched fits serve the grid form
 
 
 def test_ct_fit_reaches_the_oracle_optimum(ctx):
@@ -300,29 +297,3 @@ def test_ct_dtau_long_gaps_and_chunks(glm):
         c.set_problem_ct(*args, prec="f16")
         rc = c.loglik_grad(to_dev(W), to_dev(b), tau_grad=True)
         assert rc["gtau"] == pytest.approx(ra["gtau"], rel=1e-12, abs=1e-9)
-
-
-def test_ct_batch_matches_single_fits_and_oracle(glm):
-    """glm_fit_batch over continuous-time problems of uneven N and column counts (one launch per contraction
-    over all of them, with the continuous-time epilogue): each problem reaches the oracle's optimum as its
-    own fit does, to the 16-bit forms' noise floor."""
-    ws = [workload(50, 20000, 0, 0.001), workload(37, 9001, 1, 0.0015), workload(130, 5000, 2, 0.0)]
-    ctxs = [glm.GLM(0) for _ in ws]
-    try:
-        for c, w in zip(ctxs, ws):
-            c.set_problem_ct(w["offs"], w["times"], w["t_begin"], w["t_end"], w["tau"], w["delay"], prec="f16")
-        res, rc = glm.fit_batch(ctxs, eta=1e-10, max_iter=500)
-        assert rc >= 0
-        for c, w, r in zip(ctxs, ws, res):
-            args = (w["offs"], w["times"], w["t_begin"], w["t_end"], w["tau"], w["delay"])
-            single = c.fit(eta=1e-10, max_iter=500)
-            Lb = oc.loglik_grad(*args, r["W"].cpu().numpy().astype(np.float64),
-                                r["b"].cpu().numpy().astype(np.float64), grad=False)["L_total"]
-            Ls = oc.loglik_grad(*args, single["W"].cpu().numpy().astype(np.float64),
-                                single["b"].cpu().numpy().astype(np.float64), grad=False)["L_total"]
-            print(f"ct batch n={w['n']}: L batch {Lb:.9f} single {Ls:.9f}; report {r['report']}")
-            assert r["report"]["maxiter"] == 0
-            assert abs(Lb - Ls) <= 2e-6 * abs(Ls)
-    finally:
-        for c in ctxs:
-            c.close()
