@@ -388,6 +388,16 @@ def run_ct(args, glm, w, device, stream, form):
                     "u_product_roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"],
                                            "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops"],
                                            "peak_source": f"{src} bf16_tflops (burst)"}})
+        # one evaluation with dL/dtau as well (the U product's tau partials and their per-row scan)
+        ct.loglik_grad(W, b, tau_grad=True)
+        torch.cuda.synchronize(device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            r_tau = ct.loglik_grad(W, b, tau_grad=True)
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        res["with_dtau"] = {"ms_per_eval": e0.elapsed_time(e1) / k, "dL_dtau": r_tau["gtau"]}
         gr.set_problem(offs2, bins2, nb, dt, tau, prec=use_form(gr, form))
         gms, _ = timed(gr)
         res["grid_same_window"] = {"bins": nb, "ms_per_eval": gms}
