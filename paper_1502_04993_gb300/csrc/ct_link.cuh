@@ -120,14 +120,22 @@ __host__ __device__ __forceinline__ void ct_link(float u, const float* col, floa
     }
 }
 
+// -ln(1 - x) for 0 <= x <= 0.1 by its series to x^7 / 7 (remainder below 1.5e-8 of the value)
+__host__ __device__ __forceinline__ float ct_nlog1m(float x) {
+    return x * fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, 1.f / 7.f, 1.f / 6.f), 0.2f), 0.25f), 1.f / 3.f),
+                       0.5f), 1.f);
+}
+
 // The explicit tau-derivative of one column's integral at fixed u (for dL/dtau):
 //   T(u, D) = dF/dtau at fixed u = (F - D e^{u a}) / tau = u int_a^1 e^{u rho} (-ln rho) d rho
 // (by parts from F = int_0^D exp(u e^{-s/tau}) ds; the second form by rho = e^{-s/tau}).  For a short
-// column (oma <= 0.1) the first form cancels to ~oma of its terms, so the integral is taken by 4-node
-// Gauss-Legendre quadrature in 1 - rho (panels of 4 nodes where |u| oma > 1, as in ct_link), with
-// -ln rho = -log1p(-(1 - rho)); for oma > 0.1 the first form loses less than a digit.  dF = F - D from
-// ct_link; D from the column constants (ct_length; not needed where u a = 0: then F - D e^{ua} = dF).
+// column (oma <= 0.1) the first form cancels to ~oma of its terms, so the integral is taken by Gauss-Legendre
+// quadrature in x = 1 - rho over [0, oma], with -ln rho = ct_nlog1m(x): 2 nodes where the exponent moves by
+// |u| oma <= 0.1 (the usual case), 4 where it moves by at most 1, else panels of 4 (as in ct_link).  For
+// oma > 0.1 the first form loses less than a digit.  dF = F - D from ct_link; D from the column constants
+// (ct_length; not needed where u a = 0: then F - D e^{ua} = dF).
 __host__ __device__ __forceinline__ float ct_length(float a, float oma, float tau) {
+    if (oma <= 0.1f) return tau * ct_nlog1m(oma);
     return a < 0.5f ? -tau * logf(a) : -tau * log1pf(-oma);  // each form where its argument is exact
 }
 __host__ __device__ __forceinline__ float ct_dtau(float u, float a, float oma, float tau, float dF) {
@@ -137,15 +145,19 @@ __host__ __device__ __forceinline__ float ct_dtau(float u, float a, float oma, f
         return (dF - ct_length(a, oma, tau) * expm1f(ua)) / tau;
     }
     const float w = fabsf(u) * oma;
+    if (w <= CT_W2_MAX) {  // nodes at rho = a + oma eta, i.e. x = oma (1 - eta)
+        const float x0 = oma * GL2_E1, x1 = oma * GL2_E0;
+        return u * 0.5f * oma * (ct_exp(u - u * x0) * ct_nlog1m(x0) + ct_exp(u - u * x1) * ct_nlog1m(x1));
+    }
     int P = (w <= 1.f) ? 1 : (int)ceilf(w);
     if (P > CT_PANELS_MAX) P = CT_PANELS_MAX;
     const float h = oma / (float)P;
     float sum = 0.f;
     for (int p = 0; p < P; ++p) {
-        const float x0 = h * ((float)p + GL4_E0), x1 = h * ((float)p + GL4_E1);  // 1 - rho at the nodes
+        const float x0 = h * ((float)p + GL4_E0), x1 = h * ((float)p + GL4_E1);
         const float x2 = h * ((float)p + GL4_E2), x3 = h * ((float)p + GL4_E3);
-        sum += GL4_W0 * (ct_exp(u - u * x0) * -log1pf(-x0) + ct_exp(u - u * x3) * -log1pf(-x3)) +
-               GL4_W1 * (ct_exp(u - u * x1) * -log1pf(-x1) + ct_exp(u - u * x2) * -log1pf(-x2));
+        sum += GL4_W0 * (ct_exp(u - u * x0) * ct_nlog1m(x0) + ct_exp(u - u * x3) * ct_nlog1m(x3)) +
+               GL4_W1 * (ct_exp(u - u * x1) * ct_nlog1m(x1) + ct_exp(u - u * x2) * ct_nlog1m(x2));
     }
     return u * 0.5f * h * sum;
 }
