@@ -2,26 +2,29 @@
 //
 //   MODE 0, steps a3/a4:  U = b 1^T + W X  (Eq. 3) from split operands W = W_hi + W_lo, X = X_hi + X_lo:
 //                         U ~ W_hi X_hi + W_lo X_hi + W_hi X_lo (the dropped W_lo X_lo is ~2^-16 of U - b),
-//                         or W_hi X + W_lo X where X is held as one 16-bit array (no X_lo),
 //                         with the link and the spike-time term in the epilogue (Eq. 5, Eq. 7): per
 //                         (row, 256-bin tile) FP64 sums of exp(U) and of U - b over the row's spike bins,
 //                         and E[i][t] = dt exp(U_i[t]) stored 16-bit.
 //                         Tile 128 x 256, K step 32, 4 stages of (W_hi, W_lo, X_hi, X_lo).  W is K-major (64-byte
 //                         swizzle); X is an N-major operand: one 3-D box of 4 bin blocks x 32 neurons x 64 bins
-//                         (128-byte swizzle) per stage.  3 (2 without X_lo) MMAs per 16-wide k slice, 2 TMEM accumulators
-//                         (epilogue overlaps the next tile).
+//                         (128-byte swizzle) per stage.  3 MMAs per 16-wide k slice, 2 TMEM accumulators
+//                         (epilogue overlaps the next tile).  Also the continuous-time U product (CT).
+//   MODE 3:               the same U product over X held as one 16-bit array: W_hi X + W_lo X, 2 MMAs per
+//                         k slice, 6 stages of (W_hi, W_lo, X).
 //   MODE 1, step a5:      P_s = E X^T over a split s of the bins (dL/dW = C - sum_s P_s, Eq. 12).  The same
 //                         kernel forms the spike term C = S X^T once per problem (S, the spike raster, in
 //                         the place of E; X_hi and X_lo in turn, or X alone).  Tile 256 x 256 per block as two 128 x 256
 //                         accumulators that share every X tile (A0 = E rows m0.., A1 = E rows m0+128..),
 //                         K step 64 (128-byte swizzle), 3 stages, FP32 partials per split.
+//   MODE 2:               E X^T with 128-row tiles and double-buffered accumulators (small N; autotuner).
 //
-// X_hi, X_lo and E are stored bin-blocked, [Tpad / 64][n][64]: a block of 64 bins of every neuron is one
+// X (X_hi, X_lo) and E are stored bin-blocked, [Tpad / 64][n][64]: a block of 64 bins of every neuron is one
 // contiguous n x 128-byte array, so every TMA box of either product is a contiguous stretch of memory.
 //
-// One persistent block per SM, 6 warps: warp 0 issues TMA loads, warp 1 owns TMEM and issues the MMAs
-// (one thread), warps 2-5 are the epilogue (TMEM -> registers -> global).  Every mbarrier wait is bounded;
-// on a timeout the block raises flags[1], drains its own copies and MMAs, frees its TMEM and returns.
+// One persistent block per SM: warp 0 issues TMA loads, warp 1 owns TMEM and issues the MMAs (one thread),
+// the other warps are the epilogue (TMEM -> registers -> global): 4 (one per TMEM lane quarter), 8 for the
+// plain grid U product, 12 for the continuous-time one (epi_warps).  Every mbarrier wait is bounded; on a
+// timeout the block raises flags[1], drains its own copies and MMAs, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
