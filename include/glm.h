@@ -374,15 +374,15 @@ int glm_cross_validate(glm_ctx* ctx_train, glm_ctx* ctx_valid, const glm_fit_opt
 
 /* Recompute X chunk by chunk instead of storing it, for recordings whose N x n_bins outgrows device memory
  * (hour-long recordings of thousands of neurons).  chunk_bins > 0 (rounded up to a multiple of 4096) applies to the next
- * glm_set_problem of a tensor-core precision: the context then holds X_hi, X_lo and the rates for
- * chunk_bins bins only, and every evaluation filters, multiplies and reduces one chunk after the other
+ * glm_set_problem of a tensor-core precision: the context then holds X (or X_hi and X_lo) and the rates
+ * for chunk_bins bins only, and every evaluation filters, multiplies and reduces one chunk after the other
  * (the filter runs once per chunk and evaluation, so an evaluation costs one filter pass more).  0
  * (default) stores X for the whole recording.  Ignored for GLM_PREC_F32 and when chunk_bins covers the
  * recording.  For glm_set_problem_ct it counts event columns.  Chunked problems cannot be batched
  * (glm_fit_batch). */
 int glm_set_chunk_bins(glm_ctx* ctx, int64_t chunk_bins);
 
-/* How the 16-bit grid forms hold X (Eq. 4's filtered trains), for the next glm_set_problem.  split = 1
+/* How the 16-bit grid forms hold X (the filtered trains of Eq. 13), for the next glm_set_problem.  split = 1
  * (default): X = X_hi + X_lo, two 16-bit arrays; U takes three tensor-core products (W_hi X_hi, W_lo X_hi,
  * W_hi X_lo) and the spike term two (S X_hi^T, S X_lo^T), and X keeps ~16 significant bits in BF16 and ~22
  * in F16.  split = 0: X_hi alone, the round-to-nearest 16-bit X; U takes two products (W_hi X, W_lo X),
