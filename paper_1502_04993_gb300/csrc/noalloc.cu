@@ -118,8 +118,9 @@ __global__ void __launch_bounds__(NT) na_u_kernel(const __grid_constant__ NaArgs
     load(0);
     store(0);
     __syncthreads();
-    // two-level accumulation as in the library's regular FP32 U product: the 16 products of each k-step go
-    // into a fresh tile sum, added to the total (a single running sum drops small terms with one sign)
+    // two-level accumulation, as the library's regular FP32 U product does (there over 32 sources): the 16
+    // products of each k-step go into a fresh tile sum, added to the total (a single running sum drops small
+    // terms with one sign)
     for (int kt = 0; kt < nk; ++kt) {
         const int cur = kt & 1;
         if (kt + 1 < nk) load((kt + 1) * NK);
